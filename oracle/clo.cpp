@@ -1,0 +1,848 @@
+// clo.cpp -- FP64 CPU oracle for the lattice kick-drift method of the
+// CosmoLattice manual (arXiv:2102.01031).
+//
+// TEST INFRASTRUCTURE ONLY: plain, slow, unfused and single threaded, written
+// so that each step can be checked by eye against the paper.  Only tests/,
+// __graft_entry__.smoke() and bench.py (cpu_baseline leg, reference arm) may
+// load it.  It shares no code with the CUDA library.
+//
+// Where the paper is silent or garbled, the reading taken is stated at the
+// place it is used (tag "reading:").  Parity pins for every function live in
+// tests/test_oracle_*.py.
+#include "clo.h"
+
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+typedef std::complex<double> cplx;
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Round function:
+// two 32x32->64 multiplies, key added by xor, Weyl key schedule.
+// ---------------------------------------------------------------------------
+void philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Uniform deviate in (0, 1] with 53 random bits: 27 bits of `hi`, 26 of `lo`.
+double u01(uint32_t hi, uint32_t lo) {
+  uint64_t m = ((uint64_t)(hi >> 5) << 26) | (uint64_t)(lo >> 6);
+  return ((double)m + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------
+// FFT: recursive decimation in time by the smallest prime factor.  For
+// n = p*m, X[k1 + m*k2] = sum_q w_n^{q k1} w_p^{q k2} Y_q[k1], where Y_q is the
+// length-m DFT of x[q + p*j].  w_n = exp(sign*2*pi*i/n).
+// ---------------------------------------------------------------------------
+cplx root(long e, long n, int sign) {
+  e %= n;
+  if (e < 0) e += n;
+  double t = 2.0 * PI * (double)e / (double)n;
+  return cplx(std::cos(t), sign * std::sin(t));
+}
+
+void fft_rec(const cplx* x, long n, long stride, cplx* out, int sign) {
+  if (n == 1) { out[0] = x[0]; return; }
+  long p = 2;
+  while (n % p) ++p;
+  long m = n / p;
+  std::vector<cplx> Y(n);
+  for (long q = 0; q < p; ++q) fft_rec(x + q * stride, m, stride * p, &Y[q * m], sign);
+  for (long k1 = 0; k1 < m; ++k1)
+    for (long k2 = 0; k2 < p; ++k2) {
+      cplx s = 0.0;
+      for (long q = 0; q < p; ++q)
+        s += root(q * k1, n, sign) * root(q * k2, p, sign) * Y[q * m + k1];
+      out[k1 + m * k2] = s;
+    }
+}
+
+// 3-D transform as 1-D transforms along x, then y, then z (unnormalised).
+void fft3d(std::vector<cplx>& a, int N, int sign) {
+  std::vector<cplx> line(N), res(N);
+  long NN = (long)N * N;
+  for (int axis = 0; axis < 3; ++axis) {
+    long stride = axis == 0 ? 1 : (axis == 1 ? N : NN);
+    for (long u = 0; u < N; ++u)
+      for (long w = 0; w < N; ++w) {
+        long base;
+        if (axis == 0) base = N * (u + (long)N * w);
+        else if (axis == 1) base = u + NN * w;
+        else base = u + (long)N * w;
+        for (long j = 0; j < N; ++j) line[j] = a[base + j * stride];
+        fft_rec(line.data(), N, 1, res.data(), sign);
+        for (long j = 0; j < N; ++j) a[base + j * stride] = res[j];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Integrator schedules.  VV2 (Stoermer-Verlet) is the base symmetric step.
+// VV4 = Yoshida (1990) triple jump; VV6, VV8, VV10 = the same triple-jump
+// construction applied again (order 2k -> 2k+2 with z = 1/(2 - 2^{1/(2k+1)})).
+// reading: the manual names VV4..VV10 but prints no coefficients; any
+// symmetric composition of the right order is a member of "the family".
+// reading: LF is the same kick/drift stream as VV2 (kicks merged across
+// steps, momenta synchronised by a half kick before measuring).
+// ---------------------------------------------------------------------------
+void schedule(int order, double h, std::vector<double>& d) {
+  if (order <= 2) { d.push_back(h); return; }
+  double e = 1.0 / (double)(order - 1);
+  double z1 = 1.0 / (2.0 - std::pow(2.0, e));
+  double z0 = 1.0 - 2.0 * z1;
+  schedule(order - 2, z1 * h, d);
+  schedule(order - 2, z0 * h, d);
+  schedule(order - 2, z1 * h, d);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct clo_ctx {
+  int model, N, nf;   // nf: real scalar components evolved by a scalar kick
+  long V;             // N^3
+  double kIR, dx, alpha;
+  clo_params p;
+  double a, b, eta, a0, eta0, rho0;
+  double Hfix;        // fixed background: initial a'/a
+  std::vector<double> phi[2], pi[2];
+  std::vector<double> A[3], piA[3];
+  bool gauge() const { return model == CLO_MODEL_U1_HIGGS; }
+  long at(long x, long y, long z) const {
+    x %= N; if (x < 0) x += N;
+    y %= N; if (y < 0) y += N;
+    z %= N; if (z < 0) z += N;
+    return x + (long)N * (y + (long)N * z);
+  }
+  void coords(long n, long& x, long& y, long& z) const {
+    x = n % N; y = (n / N) % N; z = n / ((long)N * N);
+  }
+  long shift(long n, int dir, int s) const {
+    long x, y, z;
+    coords(n, x, y, z);
+    if (dir == 0) x += s; else if (dir == 1) y += s; else z += s;
+    return at(x, y, z);
+  }
+};
+
+namespace {
+
+int n_pot_terms(int model) { return model == CLO_MODEL_LPHI4_CHI ? 2 : 1; }
+
+// Program potential V~ term by term.  lphi4: phi^4/4 (eq. PotNat with chi = 0);
+// lphi4 + chi: phi^4/4 + (q/2) phi^2 chi^2 (eq. PotNat, q = g^2/lambda);
+// U(1) Abelian-Higgs: lam (|phi|^2 - v^2)^2 with |phi|^2 = (phi_0^2+phi_1^2)/2.
+void pot_terms(const clo_ctx* c, const double* f, double* t) {
+  if (c->model == CLO_MODEL_LPHI4) {
+    t[0] = 0.25 * f[0] * f[0] * f[0] * f[0];
+  } else if (c->model == CLO_MODEL_LPHI4_CHI) {
+    t[0] = 0.25 * f[0] * f[0] * f[0] * f[0];
+    t[1] = 0.5 * c->p.q * f[0] * f[0] * f[1] * f[1];
+  } else {
+    double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
+    double d = m2 - c->p.v * c->p.v;
+    t[0] = c->p.lam * d * d;
+  }
+}
+
+// Force terms: dV/dphi_f for singlets; for the complex field the component
+// form of (1/2) V_{,|phi|} phi/|phi| = dV/dphi^*, i.e. 2 lam (|phi|^2 - v^2) phi_c
+// (reading: written polynomially, no division by |phi|; sign as in eq.
+// higgsU1-eom, the "+" printed in eq. kernelcomplexscalar is taken as a typo).
+void pot_deriv(const clo_ctx* c, const double* f, double* d) {
+  if (c->model == CLO_MODEL_LPHI4) {
+    d[0] = f[0] * f[0] * f[0];
+  } else if (c->model == CLO_MODEL_LPHI4_CHI) {
+    d[0] = f[0] * f[0] * f[0] + c->p.q * f[0] * f[1] * f[1];
+    d[1] = c->p.q * f[0] * f[0] * f[1];
+  } else {
+    double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
+    double g = 2.0 * c->p.lam * (m2 - c->p.v * c->p.v);
+    d[0] = g * f[0];
+    d[1] = g * f[1];
+  }
+}
+
+// Effective mass squared d^2V/dphi_f^2 at the homogeneous values (eq. QuantumFlucts2).
+double mass2(const clo_ctx* c, const double* f, int k) {
+  if (c->model == CLO_MODEL_LPHI4) return 3.0 * f[0] * f[0];
+  if (c->model == CLO_MODEL_LPHI4_CHI)
+    return k == 0 ? 3.0 * f[0] * f[0] + c->p.q * f[1] * f[1] : c->p.q * f[0] * f[0];
+  double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
+  return 2.0 * c->p.lam * (m2 - c->p.v * c->p.v) + 2.0 * c->p.lam * f[k] * f[k];
+}
+
+// U(1) link phases theta = gQ dx A_i; link V_i = exp(-i theta) (U(1) toolkit).
+// Plaquette angle theta_ij(n) = gQ dx [A_i(n) + A_j(n+i) - A_i(n+j) - A_j(n)],
+// so that V_ij = V_i V_j(+i) V_i^*(+j) V_j^* = exp(-i theta_ij).
+// reading: the toolkit prints V_mu V_{mu,+mu} V*_{mu,+nu} V*_nu; the
+// SU(N) toolkit's ordering U_mu U_{nu,+mu} U^dag_{mu,+nu} U^dag_nu is used.
+double plaq(const clo_ctx* c, long n, int i, int j) {
+  double s = c->A[i][n] + c->A[j][c->shift(n, i, +1)] - c->A[i][c->shift(n, j, +1)] - c->A[j][n];
+  return c->p.gQ * c->dx * s;
+}
+
+// V_i(n) phi(n+i) in components of phi = (phi0 + i phi1)/sqrt2 (same scaling).
+void link_fwd(const clo_ctx* c, long n, int i, double& w0, double& w1) {
+  long m = c->shift(n, i, +1);
+  double th = c->p.gQ * c->dx * c->A[i][n];
+  double co = std::cos(th), si = std::sin(th);
+  double x = c->phi[0][m], y = c->phi[1][m];
+  w0 = co * x + si * y;   // (co - i si)(x + i y)
+  w1 = co * y - si * x;
+}
+// V_i^*(n-i) phi(n-i)
+void link_bwd(const clo_ctx* c, long n, int i, double& w0, double& w1) {
+  long m = c->shift(n, i, -1);
+  double th = c->p.gQ * c->dx * c->A[i][m];
+  double co = std::cos(th), si = std::sin(th);
+  double x = c->phi[0][m], y = c->phi[1][m];
+  w0 = co * x - si * y;   // (co + i si)(x + i y)
+  w1 = co * y + si * x;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels of the momenta (Sec. 3.5.2, Hamiltonian form; Sec. 4.3 for U(1)).
+// ---------------------------------------------------------------------------
+
+// K_phi = -a^{3+alpha} V_{,phi} + a^{1+alpha} Lap phi, Lap = sum_i grad^-_i grad^+_i.
+void kernel_scalars(const clo_ctx* c, std::vector<double>* K) {
+  double a1 = std::pow(c->a, 1.0 + c->alpha), a3 = std::pow(c->a, 3.0 + c->alpha);
+  double idx2 = 1.0 / (c->dx * c->dx);
+  for (long n = 0; n < c->V; ++n) {
+    double f[2] = {0, 0}, d[2] = {0, 0};
+    for (int k = 0; k < c->nf; ++k) f[k] = c->phi[k][n];
+    pot_deriv(c, f, d);
+    for (int k = 0; k < c->nf; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < 3; ++i)
+        s += c->phi[k][c->shift(n, i, +1)] + c->phi[k][c->shift(n, i, -1)] - 2.0 * c->phi[k][n];
+      K[k][n] = a1 * s * idx2 - a3 * d[k];
+    }
+  }
+}
+
+// U(1): K_phi = a^{1+alpha} D^2 phi - a^{3+alpha} dV/dphi^*, with the lattice
+// covariant Laplacian D^2 phi = sum_i [V_i phi(n+i) - 2 phi + V_i^*(n-i) phi(n-i)]/dx^2;
+// K_{A_i} = a^{1+alpha} (f*/omega*)^2 J_i + a^{alpha-1} (lattice d_j F_ji), with
+// J_i = (2 gQ/dx) Im[phi^*(n) V_i(n) phi(n+i)] and the compact curl
+// -(1/(gQ dx^3)) sum_{j != i} [sin theta_ij(n) - sin theta_ij(n-j)].
+// reading: the factor (f*/omega*)^2 on J (eq. U1eom) is kept although the
+// kernel line of Sec. 4.3 omits it; both terms follow from one lattice
+// Hamiltonian so that the lattice Gauss law is conserved exactly.
+void kernel_u1(const clo_ctx* c, std::vector<double>* Kphi, std::vector<double>* KA) {
+  double a1 = std::pow(c->a, 1.0 + c->alpha), a3 = std::pow(c->a, 3.0 + c->alpha);
+  double am1 = std::pow(c->a, c->alpha - 1.0);
+  double idx2 = 1.0 / (c->dx * c->dx);
+  double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  double gQ = c->p.gQ, dx = c->dx;
+  for (long n = 0; n < c->V; ++n) {
+    double f[2] = {c->phi[0][n], c->phi[1][n]}, d[2];
+    pot_deriv(c, f, d);
+    double D0 = 0.0, D1 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      double u0, u1, w0, w1;
+      link_fwd(c, n, i, u0, u1);
+      link_bwd(c, n, i, w0, w1);
+      D0 += u0 + w0 - 2.0 * f[0];
+      D1 += u1 + w1 - 2.0 * f[1];
+    }
+    Kphi[0][n] = a1 * D0 * idx2 - a3 * d[0];
+    Kphi[1][n] = a1 * D1 * idx2 - a3 * d[1];
+    for (int i = 0; i < 3; ++i) {
+      double u0, u1;
+      link_fwd(c, n, i, u0, u1);
+      // Im[phi^* w] with both in the sqrt2-scaled components: (f0 w1 - f1 w0)/2
+      double J = (2.0 * gQ / dx) * 0.5 * (f[0] * u1 - f[1] * u0);
+      double curl = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        if (j == i) continue;
+        curl += std::sin(plaq(c, n, i, j)) - std::sin(plaq(c, c->shift(n, j, -1), i, j));
+      }
+      curl *= -1.0 / (gQ * dx * dx * dx);
+      KA[i][n] = a1 * fo2 * J + am1 * curl;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Volume averages (eq. EK_EG_EV; eq. energy-contrib for U(1)).
+// reading: the gradient energy uses forward differences grad^+, so that
+// sum_n (grad^+ phi)^2 = -sum_n phi Lap phi matches the kick's Laplacian.
+// ---------------------------------------------------------------------------
+struct Avg {
+  double EK[4], EG[4], EV[4], EKA, EGA;
+  double mphi[4], mphi2[4], mpi[4], mpi2[4];
+};
+
+void averages(const clo_ctx* c, Avg& r) {
+  std::memset(&r, 0, sizeof(r));
+  double sp2[2] = {0, 0}, sg[2] = {0, 0}, sv[4] = {0, 0, 0, 0};
+  double spA = 0.0, smag = 0.0;
+  for (long n = 0; n < c->V; ++n) {
+    double f[2] = {0, 0}, t[4] = {0, 0, 0, 0};
+    for (int k = 0; k < c->nf; ++k) {
+      f[k] = c->phi[k][n];
+      double pv = c->pi[k][n];
+      sp2[k] += pv * pv;
+      r.mphi[k] += f[k];
+      r.mphi2[k] += f[k] * f[k];
+      r.mpi[k] += pv;
+      r.mpi2[k] += pv * pv;
+    }
+    pot_terms(c, f, t);
+    for (int m = 0; m < n_pot_terms(c->model); ++m) sv[m] += t[m];
+    if (!c->gauge()) {
+      for (int k = 0; k < c->nf; ++k)
+        for (int i = 0; i < 3; ++i) {
+          double g = c->phi[k][c->shift(n, i, +1)] - c->phi[k][n];
+          sg[k] += g * g;
+        }
+    } else {
+      for (int i = 0; i < 3; ++i) {
+        double u0, u1;
+        link_fwd(c, n, i, u0, u1);
+        sg[0] += (u0 - f[0]) * (u0 - f[0]) + (u1 - f[1]) * (u1 - f[1]);
+        spA += c->piA[i][n] * c->piA[i][n];
+        for (int j = i + 1; j < 3; ++j) smag += 1.0 - std::cos(plaq(c, n, i, j));
+      }
+    }
+  }
+  double V = (double)c->V, a = c->a;
+  double a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
+  if (!c->gauge()) {
+    for (int k = 0; k < c->nf; ++k) {
+      r.EK[k] = sp2[k] / (2.0 * a6 * V);
+      r.EG[k] = sg[k] / (2.0 * a2 * c->dx * c->dx * V);
+    }
+  } else {
+    r.EK[0] = (sp2[0] + sp2[1]) / (2.0 * a6 * V);
+    r.EG[0] = sg[0] / (2.0 * a2 * c->dx * c->dx * V);
+    double of2 = 1.0 / (c->p.fstar_over_omegastar * c->p.fstar_over_omegastar);
+    double gdx2 = c->p.gQ * c->dx * c->dx;
+    r.EKA = of2 * spA / (2.0 * a4 * V);
+    r.EGA = of2 * smag / (a4 * gdx2 * gdx2 * V);
+  }
+  for (int m = 0; m < n_pot_terms(c->model); ++m) r.EV[m] = sv[m] / V;
+  for (int k = 0; k < c->nf; ++k) {
+    r.mphi[k] /= V; r.mphi2[k] /= V; r.mpi[k] /= V; r.mpi2[k] /= V;
+  }
+}
+
+double sum4(const double* x) { return x[0] + x[1] + x[2] + x[3]; }
+
+// b' = K_a = a^{2alpha+1}/3 (f*/m_p)^2 [(alpha-2)E_K + alpha E_G
+//            + (alpha-1)(E_K^A + E_G^A) + (alpha+1) E_V]   (Sec. 4.3)
+double kernel_a(const clo_ctx* c, const Avg& r) {
+  double al = c->alpha, fm = c->p.fstar_over_mp;
+  double br = (al - 2.0) * sum4(r.EK) + al * sum4(r.EG) + (al - 1.0) * (r.EKA + r.EGA) +
+              (al + 1.0) * sum4(r.EV);
+  return std::pow(c->a, 2.0 * al + 1.0) / 3.0 * fm * fm * br;
+}
+
+// Fixed power-law background, eq. ScaleFactorPowerLaw (a_* = a0 at eta_*).
+double a_fixed(const clo_ctx* c, double eta) {
+  double p = 2.0 / (3.0 * (1.0 + c->p.omega_eos) - 2.0 * c->alpha);
+  return c->a0 * std::pow(1.0 + c->Hfix * (eta - c->eta0) / p, p);
+}
+double H_fixed(const clo_ctx* c, double eta) {
+  double p = 2.0 / (3.0 * (1.0 + c->p.omega_eos) - 2.0 * c->alpha);
+  return c->Hfix / (1.0 + c->Hfix * (eta - c->eta0) / p);
+}
+
+// ---------------------------------------------------------------------------
+// The three moves of the velocity-Verlet step (Sec. 3.5.2).
+// reading (the manual defers the discrete scheme to its companion paper):
+//   kick-in (h/2):  pi += h/2 K[a, phi];   b += h/2 K_a(a, E_K(pi_new), E_G, E_V)
+//   drift (h):      a1 = a + h b;  phi += h abar^{alpha-3} pi,  abar = (a+a1)/2
+//                   (U(1) links: A += h abar^{alpha-1} pi_A);   a = a1
+//   kick-out (h/2): b += h/2 K_a(a, E_K(pi), E_G, E_V);  pi += h/2 K[a, phi]
+// kick-out is the reverse of kick-in and the drift is symmetric, so the
+// step is time reversible and second order.
+// ---------------------------------------------------------------------------
+void kick_fields(clo_ctx* c, double w) {
+  if (!c->gauge()) {
+    std::vector<double> K[2];
+    for (int k = 0; k < c->nf; ++k) K[k].assign(c->V, 0.0);
+    kernel_scalars(c, K);
+    for (int k = 0; k < c->nf; ++k)
+      for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * K[k][n];
+  } else {
+    std::vector<double> Kp[2], KA[3];
+    for (int k = 0; k < 2; ++k) Kp[k].assign(c->V, 0.0);
+    for (int i = 0; i < 3; ++i) KA[i].assign(c->V, 0.0);
+    kernel_u1(c, Kp, KA);
+    for (int k = 0; k < 2; ++k)
+      for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * Kp[k][n];
+    for (int i = 0; i < 3; ++i)
+      for (long n = 0; n < c->V; ++n) c->piA[i][n] += w * KA[i][n];
+  }
+}
+
+void kick_scale(clo_ctx* c, double w) {
+  if (c->p.expansion != CLO_EXP_SELF) return;
+  Avg r;
+  averages(c, r);
+  c->b += w * kernel_a(c, r);
+}
+
+void drift(clo_ctx* c, double w) {
+  double a1, abar;
+  if (c->p.expansion == CLO_EXP_SELF) {
+    a1 = c->a + w * c->b;
+  } else if (c->p.expansion == CLO_EXP_FIXED) {
+    a1 = a_fixed(c, c->eta + w);
+  } else {
+    a1 = c->a;
+  }
+  abar = 0.5 * (c->a + a1);
+  double cphi = w * std::pow(abar, c->alpha - 3.0);
+  for (int k = 0; k < c->nf; ++k)
+    for (long n = 0; n < c->V; ++n) c->phi[k][n] += cphi * c->pi[k][n];
+  if (c->gauge()) {
+    double cA = w * std::pow(abar, c->alpha - 1.0);
+    for (int i = 0; i < 3; ++i)
+      for (long n = 0; n < c->V; ++n) c->A[i][n] += cA * c->piA[i][n];
+  }
+  c->a = a1;
+  c->eta += w;
+  if (c->p.expansion == CLO_EXP_FIXED) c->b = a1 * H_fixed(c, c->eta);
+}
+
+void vv2(clo_ctx* c, double h) {
+  kick_fields(c, 0.5 * h);
+  kick_scale(c, 0.5 * h);
+  drift(c, h);
+  kick_scale(c, 0.5 * h);
+  kick_fields(c, 0.5 * h);
+}
+
+double rho_of(const Avg& r) { return sum4(r.EK) + sum4(r.EG) + sum4(r.EV) + r.EKA + r.EGA; }
+
+// ---------------------------------------------------------------------------
+// Initial conditions (Sec. 3.5.1 eqs. fpr_influct, fpr_influct2,
+// QuantumFlucts2; Sec. 4.4.1 for the charged field and the gauge momenta).
+// reading of the generator (the manual fixes the distributions, not the
+// generator): for field component f and Fourier site with linear index idx
+// (x fastest, wave numbers n~_i in (-N/2, N/2]), with key (seed lo, seed hi),
+//   r = Philox(idx, f, 0, 0): u1 = u01(r0,r1), u2 = u01(r2,r3)  (amplitudes)
+//   s = Philox(idx, f, 1, 0): v1 = u01(s0,s1), v2 = u01(s2,s3)  (phases)
+//   |d_j| = sqrt(-P ln u_j) (Rayleigh, <|d|^2> = P), theta_j = 2 pi v_j,
+//   P = fluct_amp2 (N/dx)^3 / (2 a^2 omega_k), omega_k = sqrt(k^2 + a^2 m^2), k = kIR |n~|.
+// Only the member of each (n~, -n~) pair with the smaller linear index is
+// drawn; the other is set to its complex conjugate so that the field is real;
+// self-conjugate sites keep the real part; n~ = 0, k > kcut and omega_k^2 <= 0
+// are set to zero.
+// ---------------------------------------------------------------------------
+long partner_index(const clo_ctx* c, long idx) {
+  long x, y, z;
+  c->coords(idx, x, y, z);
+  return c->at(-x, -y, -z);
+}
+double mode_k(const clo_ctx* c, long idx) {
+  long x, y, z;
+  c->coords(idx, x, y, z);
+  long n[3] = {x, y, z};
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    long w = n[i] <= c->N / 2 ? n[i] : n[i] - c->N;
+    s += (double)(w * w);
+  }
+  return c->kIR * std::sqrt(s);
+}
+
+void draw4(uint64_t seed, long idx, int f, int j, double u[2]) {
+  uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)f, (uint32_t)j, 0u};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  philox(ctr, key, r);
+  u[0] = u01(r[0], r[1]);
+  u[1] = u01(r[2], r[3]);
+}
+
+// Fourier modes of the field fluctuation (F) and of its time derivative (G).
+void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F,
+                 std::vector<cplx>* G) {
+  double a = c->a, al = c->alpha, amp2 = c->p.fluct_amp2;
+  double vol = std::pow((double)c->N / c->dx, 3.0);
+  const double isq2 = 1.0 / std::sqrt(2.0);
+  double m2[2];
+  for (int k = 0; k < c->nf; ++k) m2[k] = mass2(c, c->p.phi0, k);
+  for (int k = 0; k < c->nf; ++k) {
+    F[k].assign(c->V, cplx(0, 0));
+    G[k].assign(c->V, cplx(0, 0));
+  }
+  for (long idx = 1; idx < c->V; ++idx) {
+    long pid = partner_index(c, idx);
+    if (pid < idx) continue;
+    bool selfc = pid == idx;
+    if (selfc && c->gauge()) continue;  // reading: keeps the charge density's zero mode exactly 0
+    double k = mode_k(c, idx);
+    if (c->p.kcut >= 0.0 && k > c->p.kcut) continue;
+    if (amp2 <= 0.0) continue;
+    cplx z1[2], z2[2];
+    double om[2];
+    bool ok = true;
+    for (int f = 0; f < c->nf; ++f) {
+      double w2 = k * k + a * a * m2[f];
+      if (w2 <= 0.0) { ok = false; break; }
+      om[f] = std::sqrt(w2);
+    }
+    if (!ok) continue;
+    if (!c->gauge()) {
+      for (int f = 0; f < c->nf; ++f) {
+        double P = amp2 * vol / (2.0 * a * a * om[f]);
+        double u[2], v[2];
+        draw4(seed, idx, f, 0, u);
+        draw4(seed, idx, f, 1, v);
+        z1[f] = std::polar(std::sqrt(-P * std::log(u[0])), 2.0 * PI * v[0]);
+        z2[f] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
+      }
+    } else {
+      // eqs. InConstr:1-2: |d_{c1}| = |d_{c2}|, theta_12 = theta_02 + theta_11 - theta_01
+      double P0 = amp2 * vol / (2.0 * a * a * om[0]);
+      double P1 = amp2 * vol / (2.0 * a * a * om[1]);
+      double u0[2], v0[2], u1[2], v1[2];
+      draw4(seed, idx, 0, 0, u0);
+      draw4(seed, idx, 0, 1, v0);
+      draw4(seed, idx, 1, 0, u1);
+      draw4(seed, idx, 1, 1, v1);
+      double r0 = std::sqrt(-P0 * std::log(u0[0]));
+      double r1 = std::sqrt(-P1 * std::log(u1[0]));
+      double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1], t11 = 2.0 * PI * v1[0];
+      double t12 = t02 + t11 - t01;
+      z1[0] = std::polar(r0, t01); z2[0] = std::polar(r0, t02);
+      z1[1] = std::polar(r1, t11); z2[1] = std::polar(r1, t12);
+    }
+    for (int f = 0; f < c->nf; ++f) {
+      cplx df = (z1[f] + z2[f]) * isq2;
+      cplx dv = std::pow(a, al - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
+      if (selfc) { df = cplx(df.real(), 0.0); dv = cplx(dv.real(), 0.0); }
+      F[f][idx] = df; G[f][idx] = dv;
+      F[f][pid] = std::conj(df); G[f][pid] = std::conj(dv);
+    }
+  }
+}
+
+// Gauss-law momenta for the U(1) links (eq. GaugeCurrentFluc, on the lattice).
+// reading: the lattice backward-difference symbol kappa_i = (1 - e^{-2 pi i n_i/N})/dx
+// replaces the continuum k_i, so that sum_i grad^-_i pi_A,i equals the charge
+// density to roundoff:  pi_A,i(k) = kappa_i^* rho(k)/|kappa|^2, rho(0) -> 0.
+void gauss_momenta(clo_ctx* c) {
+  double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  std::vector<cplx> rho(c->V);
+  for (long n = 0; n < c->V; ++n)
+    rho[n] = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+  fft3d(rho, c->N, -1);
+  for (int i = 0; i < 3; ++i) {
+    std::vector<cplx> E(c->V);
+    for (long idx = 1; idx < c->V; ++idx) {
+      long x, y, z;
+      c->coords(idx, x, y, z);
+      long nn[3] = {x, y, z};
+      double kk = 0.0;
+      cplx ki;
+      for (int j = 0; j < 3; ++j) {
+        double t = 2.0 * PI * (double)nn[j] / (double)c->N;
+        cplx kap = (1.0 - cplx(std::cos(t), -std::sin(t))) / c->dx;
+        kk += std::norm(kap);
+        if (j == i) ki = kap;
+      }
+      E[idx] = std::conj(ki) * rho[idx] / kk;
+    }
+    fft3d(E, c->N, +1);
+    for (long n = 0; n < c->V; ++n) c->piA[i][n] = E[n].real() / (double)c->V;
+  }
+}
+
+double homogeneous_rho(const clo_ctx* c) {
+  double f[2] = {0, 0}, t[4] = {0, 0, 0, 0};
+  double kin = 0.0;
+  for (int k = 0; k < c->nf; ++k) {
+    f[k] = c->p.phi0[k];
+    kin += 0.5 * c->p.dphi0[k] * c->p.dphi0[k];
+  }
+  pot_terms(c, f, t);
+  return kin / std::pow(c->a, 2.0 * c->alpha) + sum4(t);
+}
+
+double b_from_hubble(const clo_ctx* c, double rho) {
+  double fm = c->p.fstar_over_mp;
+  double r = std::pow(c->a, 2.0 * c->alpha + 2.0) / 3.0 * fm * fm * rho;
+  return r > 0.0 ? std::sqrt(r) : 0.0;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface
+// ===========================================================================
+extern "C" {
+
+void clo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  philox(ctr, key, out);
+}
+double clo_u01(uint32_t hi, uint32_t lo) { return u01(hi, lo); }
+
+int clo_fft3d(double* re, double* im, int N, int sign) {
+  if (N < 1 || (sign != 1 && sign != -1)) return -1;
+  long V = (long)N * N * N;
+  std::vector<cplx> a(V);
+  for (long n = 0; n < V; ++n) a[n] = cplx(re[n], im[n]);
+  fft3d(a, N, sign);
+  for (long n = 0; n < V; ++n) { re[n] = a[n].real(); im[n] = a[n].imag(); }
+  return 0;
+}
+
+// Definition of the 3-D DFT written out, O(N^6); for tiny N only.
+int clo_dft3d_naive(const double* re, const double* im, double* ore, double* oim, int N,
+                    int sign) {
+  if (N < 1 || N > 16) return -1;
+  long V = (long)N * N * N;
+  for (long k = 0; k < V; ++k) {
+    long kx = k % N, ky = (k / N) % N, kz = k / ((long)N * N);
+    cplx s = 0.0;
+    for (long n = 0; n < V; ++n) {
+      long x = n % N, y = (n / N) % N, z = n / ((long)N * N);
+      long e = (kx * x + ky * y + kz * z) % N;
+      s += cplx(re[n], im[n]) * root(e, N, sign);
+    }
+    ore[k] = s.real(); oim[k] = s.imag();
+  }
+  return 0;
+}
+
+int clo_schedule(int integrator, double h, double* drifts, int cap) {
+  std::vector<double> d;
+  int order = integrator == CLO_LF ? 2 : integrator;
+  if (order != 2 && order != 4 && order != 6 && order != 8 && order != 10) return -1;
+  schedule(order, h, d);
+  if ((int)d.size() > cap) return -2;
+  for (size_t i = 0; i < d.size(); ++i) drifts[i] = d[i];
+  return (int)d.size();
+}
+
+int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
+             const clo_params* p) {
+  if (!out || !p) return -1;
+  if (model < CLO_MODEL_LPHI4 || model > CLO_MODEL_U1_HIGGS) return -1;
+  if (N < 2 || kIR <= 0.0) return -1;
+  clo_ctx* c = new clo_ctx();
+  c->model = model;
+  c->N = N;
+  c->V = (long)N * N * N;
+  c->nf = model == CLO_MODEL_LPHI4 ? 1 : 2;
+  c->kIR = kIR;
+  c->dx = 2.0 * PI / ((double)N * kIR);
+  c->alpha = alpha;
+  c->p = *p;
+  c->a = c->a0 = 1.0;
+  c->eta = c->eta0 = 0.0;
+  for (int k = 0; k < c->nf; ++k) {
+    c->phi[k].assign(c->V, 0.0);
+    c->pi[k].assign(c->V, 0.0);
+  }
+  if (c->gauge())
+    for (int i = 0; i < 3; ++i) {
+      c->A[i].assign(c->V, 0.0);
+      c->piA[i].assign(c->V, 0.0);
+    }
+  // initial a' (Sec. 5.2 ScaleFactorInitializer: from homogeneous values)
+  double rho_h = homogeneous_rho(c);
+  if (p->expansion == CLO_EXP_SELF) {
+    c->b = b_from_hubble(c, rho_h);
+  } else if (p->expansion == CLO_EXP_FIXED) {
+    c->Hfix = p->H0 > 0.0 ? p->H0 : b_from_hubble(c, rho_h) / c->a;
+    c->b = c->a * c->Hfix;
+  } else {
+    c->b = 0.0;
+  }
+  double H = c->b / c->a;
+  // fluctuations
+  std::vector<cplx> F[2], G[2];
+  fluct_modes(c, seed, H, F, G);
+  double a3ma = std::pow(c->a, 3.0 - alpha);
+  for (int k = 0; k < c->nf; ++k) {
+    fft3d(F[k], N, +1);
+    fft3d(G[k], N, +1);
+    for (long n = 0; n < c->V; ++n) {
+      c->phi[k][n] = p->phi0[k] + F[k][n].real() / (double)c->V;
+      c->pi[k][n] = a3ma * (p->dphi0[k] + G[k][n].real() / (double)c->V);
+    }
+  }
+  if (c->gauge()) gauss_momenta(c);
+  Avg r;
+  averages(c, r);
+  if (p->expansion == CLO_EXP_SELF && p->b0_mode == 1) c->b = b_from_hubble(c, rho_of(r));
+  c->rho0 = rho_of(r);
+  *out = c;
+  return 0;
+}
+
+int clo_free(clo_ctx* c) {
+  delete c;
+  return 0;
+}
+
+int clo_step_h(clo_ctx* c, int n, double h) {
+  if (!c || n < 0) return -1;
+  std::vector<double> d;
+  int order = c->p.integrator == CLO_LF ? 2 : c->p.integrator;
+  if (order != 2 && order != 4 && order != 6 && order != 8 && order != 10) return -1;
+  schedule(order, h, d);
+  for (int s = 0; s < n; ++s)
+    for (size_t j = 0; j < d.size(); ++j) vv2(c, d[j]);
+  return 0;
+}
+
+int clo_step(clo_ctx* c, int n) { return c ? clo_step_h(c, n, c->p.dt) : -1; }
+
+int clo_energies(clo_ctx* c, clo_energies_t* o) {
+  if (!c || !o) return -1;
+  Avg r;
+  averages(c, r);
+  std::memset(o, 0, sizeof(*o));
+  o->eta = c->eta; o->a = c->a; o->b = c->b;
+  for (int k = 0; k < 4; ++k) {
+    o->EK[k] = r.EK[k]; o->EG[k] = r.EG[k]; o->EV[k] = r.EV[k];
+    o->mean_phi[k] = r.mphi[k]; o->mean_phi2[k] = r.mphi2[k];
+    o->mean_pi[k] = r.mpi[k]; o->mean_pi2[k] = r.mpi2[k];
+  }
+  o->EKA = r.EKA; o->EGA = r.EGA;
+  o->rho = rho_of(r);
+  // Hubble constraint eq. NewFriedmannEQsI and its monitor (Sec. 3.3.2 outputs)
+  double fm = c->p.fstar_over_mp;
+  o->hubble_lhs = c->b * c->b;
+  o->hubble_rhs = std::pow(c->a, 2.0 * c->alpha + 2.0) / 3.0 * fm * fm * o->rho;
+  double den = o->hubble_lhs + o->hubble_rhs;
+  o->hubble_viol = den > 0.0 ? (o->hubble_lhs - o->hubble_rhs) / den : 0.0;
+  o->energy_cons = c->rho0 != 0.0 ? 1.0 - o->rho / c->rho0 : 0.0;
+  return 0;
+}
+
+static std::vector<double>* field_ptr(const clo_ctx* c, int field, int what) {
+  clo_ctx* m = const_cast<clo_ctx*>(c);
+  if (what != 0 && what != 1) return nullptr;
+  if (field >= 0 && field < c->nf) return what == 0 ? &m->phi[field] : &m->pi[field];
+  if (c->gauge() && field >= 2 && field < 5) return what == 0 ? &m->A[field - 2] : &m->piA[field - 2];
+  return nullptr;
+}
+
+int clo_get_state(const clo_ctx* c, int field, int what, double* out) {
+  if (!c || !out) return -1;
+  std::vector<double>* v = field_ptr(c, field, what);
+  if (!v) return -1;
+  std::memcpy(out, v->data(), sizeof(double) * c->V);
+  return 0;
+}
+
+int clo_set_state(clo_ctx* c, int field, int what, const double* in) {
+  if (!c || !in) return -1;
+  std::vector<double>* v = field_ptr(c, field, what);
+  if (!v) return -1;
+  std::memcpy(v->data(), in, sizeof(double) * c->V);
+  return 0;
+}
+
+int clo_get_scalars(const clo_ctx* c, double* eta, double* a, double* b) {
+  if (!c) return -1;
+  if (eta) *eta = c->eta;
+  if (a) *a = c->a;
+  if (b) *b = c->b;
+  return 0;
+}
+
+int clo_set_scalars(clo_ctx* c, double eta, double a, double b) {
+  if (!c) return -1;
+  c->eta = eta; c->a = a; c->b = b;
+  return 0;
+}
+
+int clo_nfields(const clo_ctx* c) { return c ? (c->gauge() ? 5 : c->nf) : -1; }
+
+// Gauss-law monitor (Sec. 4.5 output "average_gauss"): LHS = sum_i grad^-_i pi_A,i,
+// RHS = (f*/omega*)^2 2 gQ Im[phi^* pi_phi]; rel = <|L-R|>/<|L+R|>.
+int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
+                         double* max_abs) {
+  if (!c || !c->gauge()) return -1;
+  double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  double sd = 0.0, ss = 0.0, mx = 0.0;
+  for (long n = 0; n < c->V; ++n) {
+    double L = 0.0;
+    for (int i = 0; i < 3; ++i) L += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
+    double R = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+    sd += std::fabs(L - R);
+    ss += std::fabs(L + R);
+    if (std::fabs(L - R) > mx) mx = std::fabs(L - R);
+  }
+  double V = (double)c->V;
+  if (lhs_abs) *lhs_abs = sd / V;
+  if (rhs_abs) *rhs_abs = ss / V;
+  if (rel) *rel = ss > 0.0 ? sd / ss : 0.0;
+  if (max_abs) *max_abs = mx;
+  return 0;
+}
+
+// Binned power spectrum, eqs. discretePS and discretePSII.
+// Bins b = floor(|n~|/dk_bin) over n~ != 0; n~_b = mean |n~| in the bin;
+// k_b = kIR n~_b; Delta_b = k_b^3/(2 pi^2) (dx/N)^3 sum_b |f(n~)|^2 / (4 pi n~_b^2).
+int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
+                 double* delta, int64_t* mult, int cap, int* nbins) {
+  if (!c || dk_bin <= 0.0) return -1;
+  std::vector<double>* v = field_ptr(c, field, what);
+  if (!v) return -1;
+  int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  if (nbins) *nbins = nb;
+  if (nb > cap) return -2;
+  std::vector<cplx> a(c->V);
+  for (long n = 0; n < c->V; ++n) a[n] = cplx((*v)[n], 0.0);
+  fft3d(a, c->N, -1);
+  std::vector<double> sp(nb, 0.0), sn(nb, 0.0);
+  std::vector<int64_t> cnt(nb, 0);
+  for (long idx = 1; idx < c->V; ++idx) {
+    double nn = mode_k(c, idx) / c->kIR;
+    int b = (int)std::floor(nn / dk_bin);
+    if (b >= nb) b = nb - 1;
+    sp[b] += std::norm(a[idx]);
+    sn[b] += nn;
+    cnt[b] += 1;
+  }
+  double fac = std::pow(c->dx / (double)c->N, 3.0);
+  for (int b = 0; b < nb; ++b) {
+    if (cnt[b] == 0) { k[b] = 0.0; delta[b] = 0.0; mult[b] = 0; continue; }
+    double nbar = sn[b] / (double)cnt[b];
+    double kb = c->kIR * nbar;
+    k[b] = kb;
+    delta[b] = kb * kb * kb / (2.0 * PI * PI) * fac * sp[b] / (4.0 * PI * nbar * nbar);
+    mult[b] = cnt[b];
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+/*
+ * clo.h -- C interface of the FP64 CPU oracle for the lattice kick-drift method
+ * of the CosmoLattice manual (arXiv:2102.01031).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle is a plain, slow, unfused, single
+ * threaded FP64 restatement of the method, written to be checked by eye
+ * against the paper.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference arm may load it.  It shares no code with the CUDA
+ * library (paper_2102_01031_gb300/csrc, include/cl.h) and must never be used
+ * as a fallback for it.
+ *
+ * Notation: f_s, omega_s are the manual's f_* and omega_*.
+ * Conventions (all quantities in program variables, Sec. 3.1 eq.
+ * FieldSpaceTimeNaturalVariables and Sec. 4.1 eq. GaugeProgramVar):
+ *   - lattice site n = (x,y,z), linear index x + N*(y + N*z), periodic;
+ *   - dx = 2*pi/(N*kIR) (Sec. 2.2 "Basic lattice definitions");
+ *   - DFT: forward sum_n f(n) e^{-2 pi i n.k/N}, inverse with 1/N^3 and e^{+...}
+ *     (the manual's two printed sign conventions conflict; this one is used);
+ *   - scalar models: field f in [0, nf); U(1) model: f = 0,1 are the real
+ *     components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2) and
+ *     f = 2,3,4 are the link fields A_x, A_y, A_z (non-compact storage).
+ *
+ * Every function returns 0 on success and a negative code on error.
+ */
+#ifndef CLO_H
+#define CLO_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { CLO_MODEL_LPHI4 = 1, CLO_MODEL_LPHI4_CHI = 2, CLO_MODEL_U1_HIGGS = 3 };
+enum { CLO_LF = 0, CLO_VV2 = 2, CLO_VV4 = 4, CLO_VV6 = 6, CLO_VV8 = 8, CLO_VV10 = 10 };
+enum { CLO_EXP_OFF = 0, CLO_EXP_SELF = 1, CLO_EXP_FIXED = 2 };
+
+typedef struct {
+  double dt;                    /* time step (program units) */
+  double q;                     /* resonance parameter g^2/lambda (lphi4 + chi) */
+  double fluct_amp2;            /* (omega_s/f_s)^2 in the vacuum amplitude, eq. QuantumFlucts2 */
+  double fstar_over_mp;         /* f_s/m_p in the Friedmann equations */
+  double phi0[4];               /* homogeneous initial field values */
+  double dphi0[4];              /* homogeneous initial derivatives phi' */
+  double lam, v;                /* U(1) model: V = lam (|phi|^2 - v^2)^2 */
+  double gQ;                    /* U(1) gauge coupling times charge */
+  double fstar_over_omegastar;  /* f_s/omega_s (U(1) model) */
+  double kcut;                  /* initial-spectrum cutoff; < 0 means none */
+  double omega_eos;             /* fixed background: equation of state w */
+  double H0;                    /* fixed background: initial a'/a; <= 0 -> from Hubble law */
+  int integrator;               /* CLO_LF, CLO_VV2 ... CLO_VV10 */
+  int expansion;                /* CLO_EXP_OFF / SELF / FIXED */
+  int b0_mode;                  /* 0: a' from homogeneous values; 1: from lattice averages */
+  int pad_;
+} clo_params;
+
+typedef struct {
+  double eta, a, b;             /* time, scale factor, b = a' */
+  double EK[4], EG[4];          /* kinetic / gradient energy per scalar species */
+  double EV[4];                 /* potential energy per potential term */
+  double EKA, EGA;              /* U(1) electric and magnetic energies */
+  double rho;                   /* total energy density (program units) */
+  double hubble_lhs, hubble_rhs, hubble_viol; /* a'^2, RHS of eq. NewFriedmannEQsI, (L-R)/(L+R) */
+  double energy_cons;           /* 1 - rho/rho(t0) */
+  double mean_phi[4], mean_phi2[4], mean_pi[4], mean_pi2[4];
+} clo_energies_t;
+
+typedef struct clo_ctx clo_ctx;
+
+int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha,
+             uint64_t seed, const clo_params* p);
+int clo_free(clo_ctx* c);
+int clo_step(clo_ctx* c, int n);
+int clo_step_h(clo_ctx* c, int n, double h);      /* n steps with an explicit step size */
+int clo_energies(clo_ctx* c, clo_energies_t* out);
+int clo_get_state(const clo_ctx* c, int field, int what, double* out);
+int clo_set_state(clo_ctx* c, int field, int what, const double* in);
+int clo_get_scalars(const clo_ctx* c, double* eta, double* a, double* b);
+int clo_set_scalars(clo_ctx* c, double eta, double a, double b);
+int clo_nfields(const clo_ctx* c);
+int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
+                         double* max_abs);
+int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
+                 double* delta, int64_t* mult, int cap, int* nbins);
+
+/* pieces exposed for the pin tests */
+void clo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double clo_u01(uint32_t hi, uint32_t lo);
+int clo_fft3d(double* re, double* im, int N, int sign);      /* in place, unnormalised */
+int clo_dft3d_naive(const double* re, const double* im, double* ore, double* oim, int N, int sign);
+int clo_schedule(int integrator, double h, double* drifts, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,549 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every test here checks the oracle (``oracle/``) against something other than
+itself: published known-answer vectors, closed forms (lattice dispersion of a
+free field, Jacobi cn for the homogeneous quartic oscillator), an independent
+ODE integrator (scipy) on the continuum equations of motion with potential
+derivatives taken symbolically (sympy), brute force (naive DFT), invariants
+(Parseval, summation by parts, time reversibility, Gauss law, gauge
+invariance) and convergence orders.  No GPU is used.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+scipy = pytest.importorskip("scipy")
+from scipy.integrate import solve_ivp  # noqa: E402
+from scipy.special import ellipj  # noqa: E402
+
+import oracle as O  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def k_lat(m, N, dx):
+    """Lattice momentum of grad^+/grad^- (eq. ForwardBackwardMomentum)."""
+    return 2.0 * np.sin(np.pi * np.asarray(m, dtype=float) / N) / dx
+
+
+def plane_wave(N, m, amp=1.0):
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    return amp * np.cos(2 * np.pi * (m[0] * x + m[1] * y + m[2] * z) / N)
+
+
+def verlet_matrix(w2, h):
+    """Stoermer-Verlet map of x'' = -w2 x: kick(h/2) drift(h) kick(h/2)."""
+    K = np.array([[1.0, 0.0], [-0.5 * h * w2, 1.0]])
+    D = np.array([[1.0, h], [0.0, 1.0]])
+    return K @ D @ K
+
+
+# --------------------------------------------------------------------------
+# generator and FFT
+# --------------------------------------------------------------------------
+def test_philox_known_answers(oracle_mod):
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(t, 16) for t in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert O.philox4x32_10(r[0:4], r[4:6]) == tuple(r[6:10])
+
+
+def test_u01_range_and_mean(oracle_mod):
+    assert O.u01(0, 0) == 2.0 ** -53
+    assert O.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0
+    rng = np.random.default_rng(1)
+    words = rng.integers(0, 2 ** 32, size=(4000, 2), dtype=np.uint64)
+    u = np.array([O.u01(int(a), int(b)) for a, b in words])
+    assert u.min() > 0.0 and u.max() <= 1.0
+    assert abs(u.mean() - 0.5) < 0.02
+
+
+@pytest.mark.parametrize("N", [4, 6, 8, 12])
+def test_fft_against_naive_dft_and_numpy(oracle_mod, N):
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((N, N, N)) + 1j * rng.standard_normal((N, N, N))
+    ref = np.fft.fftn(x)
+    got = O.fft3d(x, -1)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.abs(O.fft3d(x, +1) - np.fft.ifftn(x) * N ** 3).max() < 1e-12 * np.abs(ref).max()
+    if N <= 8:
+        naive = O.dft3d_naive(x, -1)
+        assert np.abs(got - naive).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_schedules(oracle_mod):
+    d2 = O.schedule(O.VV2, 0.1)
+    assert np.allclose(d2, [0.1])
+    assert np.allclose(O.schedule(O.LF, 0.1), [0.1])
+    w1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    assert np.allclose(O.schedule(O.VV4, 1.0), [w1, 1 - 2 * w1, w1], rtol=0, atol=1e-15)
+    for order, n in [(6, 9), (8, 27), (10, 81)]:
+        d = O.schedule(order, 1.0)
+        assert len(d) == n and abs(d.sum() - 1.0) < 1e-12
+        assert np.allclose(d, d[::-1])  # symmetric composition
+
+
+# --------------------------------------------------------------------------
+# free field: lattice dispersion and the velocity-Verlet map, exactly
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("integ", [O.VV2, O.VV4, O.LF])
+def test_free_field_dispersion(oracle_mod, integ):
+    N, kIR, h, nsteps = 16, 0.5, 0.05, 40
+    dx = 2 * np.pi / (N * kIR)
+    m = (1, 2, 3)
+    p = O.make_params(dt=h, integrator=integ, q=7.0)
+    L = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, p)
+    zero = np.zeros((N, N, N))
+    wave = plane_wave(N, m, 0.3)
+    L.set(0, 0, zero); L.set(0, 1, zero)   # phi = 0 leaves chi free and massless
+    L.set(1, 0, wave); L.set(1, 1, zero)
+    L.step(nsteps)
+    w2 = float(np.sum(k_lat(m, N, dx) ** 2))
+    M = np.eye(2)
+    for d in O.schedule(integ, h):
+        M = verlet_matrix(w2, d) @ M
+    st = np.linalg.matrix_power(M, nsteps) @ np.array([1.0, 0.0])
+    assert np.abs(L.get(1, 0) - st[0] * wave).max() < 1e-12
+    assert np.abs(L.get(1, 1) - st[1] * wave).max() < 1e-12
+    assert np.abs(L.get(0, 0)).max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# homogeneous quartic oscillator: phi'' = -phi^3, phi = cn(t, 1/2)
+# --------------------------------------------------------------------------
+def cn_error(integ, dt, T=7.4163):
+    p = O.make_params(dt=dt, integrator=integ, phi0=[1.0])
+    L = O.Oracle(O.MODEL_LPHI4, 4, 1.0, 1.0, 1, p)
+    n = int(round(T / dt))
+    L.step(n)
+    phi = L.get(0, 0)[0, 0, 0]
+    sn, cn, dn, _ = ellipj(n * dt, 0.5)
+    dphi = -sn * dn
+    return max(abs(phi - cn), abs(L.get(0, 1)[0, 0, 0] - dphi))
+
+
+@pytest.mark.parametrize("integ,order", [(O.VV2, 2), (O.VV4, 4), (O.VV6, 6)])
+def test_cn_oscillation_order(oracle_mod, integ, order):
+    dts = [0.08, 0.04] if order >= 6 else [0.04, 0.02]
+    e1, e2 = cn_error(integ, dts[0]), cn_error(integ, dts[1])
+    slope = math.log(e1 / e2, 2)
+    assert abs(slope - order) < 0.35, (e1, e2, slope)
+    assert e2 < (2e-4 if order == 2 else 1e-6)
+
+
+# --------------------------------------------------------------------------
+# two fields + self-consistent expansion vs an independent ODE integration of
+# the continuum equations (eqs. EOMscalarContinuumNat, NewFriedmannEQsII),
+# potential derivatives taken symbolically from eq. PotNat
+# --------------------------------------------------------------------------
+def sympy_forces(expr_fn, nvar):
+    sympy = pytest.importorskip("sympy")
+    xs = sympy.symbols("x0:%d" % nvar)
+    V = expr_fn(*xs)
+    grads = [sympy.diff(V, x) for x in xs]
+    return sympy.lambdify(xs, V, "math"), [sympy.lambdify(xs, g, "math") for g in grads]
+
+
+def two_field_ode(q, alpha, fm, y0, T):
+    Vf, dV = sympy_forces(lambda p, c: p ** 4 / 4 + q / 2 * p ** 2 * c ** 2, 2)
+
+    def rhs(t, y):
+        p, c, dp, dc, a, da = y
+        H = da / a
+        EK = (dp ** 2 + dc ** 2) / (2 * a ** (2 * alpha))
+        EV = Vf(p, c)
+        ddp = -(3 - alpha) * H * dp - a ** (2 * alpha) * dV[0](p, c)
+        ddc = -(3 - alpha) * H * dc - a ** (2 * alpha) * dV[1](p, c)
+        dda = a * a ** (2 * alpha) / 3 * fm ** 2 * ((alpha - 2) * EK + (alpha + 1) * EV)
+        return [dp, dc, ddp, ddc, da, dda]
+
+    sol = solve_ivp(rhs, (0, T), y0, method="DOP853", rtol=1e-13, atol=1e-14)
+    return sol.y[:, -1], Vf
+
+
+def run_two_field(integ, dt, T, q, alpha, fm):
+    p = O.make_params(dt=dt, integrator=integ, q=q, phi0=[1.0, 0.3], dphi0=[0.1, -0.2],
+                      expansion=O.EXP_SELF, fstar_over_mp=fm)
+    L = O.Oracle(O.MODEL_LPHI4_CHI, 2, 1.0, alpha, 1, p)
+    b0 = L.scalars()[2]
+    L.step(int(round(T / dt)))
+    eta, a, b = L.scalars()
+    phi, chi = L.get(0, 0)[0, 0, 0], L.get(1, 0)[0, 0, 0]
+    fac = a ** (alpha - 3)
+    return np.array([phi, chi, fac * L.get(0, 1)[0, 0, 0], fac * L.get(1, 1)[0, 0, 0], a, b]), b0
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.0])
+def test_two_field_expansion_vs_ode(oracle_mod, alpha):
+    q, fm, T = 2.0, 0.6, 2.0
+    _, b0 = run_two_field(O.VV4, 0.05, 0.0, q, alpha, fm)
+    y0 = [1.0, 0.3, 0.1, -0.2, 1.0, b0]
+    yT, Vf = two_field_ode(q, alpha, fm, y0, T)
+    # the oracle's a'(0) from the Hubble law must keep the constraint along the exact flow
+    p_, c_, dp_, dc_, a_, da_ = yT
+    rhs = a_ ** (2 * alpha + 2) / 3 * fm ** 2 * ((dp_ ** 2 + dc_ ** 2) / (2 * a_ ** (2 * alpha))
+                                                 + Vf(p_, c_))
+    assert abs(da_ ** 2 - rhs) / rhs < 1e-9
+    errs = {}
+    for integ in (O.VV2, O.VV4):
+        e = []
+        for dt in (0.04, 0.02):
+            got, _ = run_two_field(integ, dt, T, q, alpha, fm)
+            e.append(np.abs(got - yT).max())
+        errs[integ] = e
+    s2 = math.log(errs[O.VV2][0] / errs[O.VV2][1], 2)
+    s4 = math.log(errs[O.VV4][0] / errs[O.VV4][1], 2)
+    assert abs(s2 - 2) < 0.3 and abs(s4 - 4) < 0.4, (errs, s2, s4)
+    assert errs[O.VV4][1] < 1e-7
+
+
+def test_fixed_background_vs_ode(oracle_mod):
+    alpha, w, H0, T, dt = 1.0, 1.0 / 3.0, 0.5, 3.0, 0.01
+    pexp = 2.0 / (3 * (1 + w) - 2 * alpha)
+    p = O.make_params(dt=dt, integrator=O.VV4, phi0=[1.0], dphi0=[0.3], expansion=O.EXP_FIXED,
+                      omega_eos=w, H0=H0)
+    L = O.Oracle(O.MODEL_LPHI4, 2, 1.0, alpha, 1, p)
+    L.step(int(round(T / dt)))
+    eta, a, b = L.scalars()
+
+    def afix(t):
+        return (1 + H0 * t / pexp) ** pexp
+
+    assert abs(a - afix(T)) < 1e-12
+    Vf, dV = sympy_forces(lambda x: x ** 4 / 4, 1)
+
+    def rhs(t, y):
+        a_ = afix(t)
+        H = H0 / (1 + H0 * t / pexp)
+        return [y[1], -(3 - alpha) * H * y[1] - a_ ** (2 * alpha) * dV[0](y[0])]
+
+    sol = solve_ivp(rhs, (0, T), [1.0, 0.3], method="DOP853", rtol=1e-13, atol=1e-14)
+    phi = L.get(0, 0)[0, 0, 0]
+    dphi = a ** (alpha - 3) * L.get(0, 1)[0, 0, 0]
+    assert abs(phi - sol.y[0, -1]) < 1e-7 and abs(dphi - sol.y[1, -1]) < 1e-7
+
+
+# --------------------------------------------------------------------------
+# lattice with fluctuations: Hubble-constraint convergence, reversibility,
+# Minkowski energy conservation, closed-form energies
+# --------------------------------------------------------------------------
+def fluct_lattice(integ, dt, N=8, expansion=O.EXP_SELF, amp=3e-2, seed=3):
+    p = O.make_params(dt=dt, integrator=integ, q=100.0, phi0=[1.0, 0.0], fluct_amp2=amp,
+                      expansion=expansion, fstar_over_mp=0.5, b0_mode=1)
+    return O.Oracle(O.MODEL_LPHI4_CHI, N, 1.0, 1.0, seed, p)
+
+
+@pytest.mark.parametrize("integ,order", [(O.VV2, 2), (O.VV4, 4)])
+def test_hubble_constraint_order(oracle_mod, integ, order):
+    T = 0.8
+    v = []
+    for dt in (0.04, 0.02):
+        L = fluct_lattice(integ, dt)
+        assert abs(L.energies()["hubble_viol"]) < 1e-14
+        L.step(int(round(T / dt)))
+        v.append(abs(L.energies()["hubble_viol"]))
+    slope = math.log(v[0] / v[1], 2)
+    assert abs(slope - order) < 0.4, (v, slope)
+
+
+@pytest.mark.parametrize("integ", [O.VV2, O.VV4])
+def test_time_reversibility(oracle_mod, integ):
+    L = fluct_lattice(integ, 0.02)
+    s0 = [L.get(f, w).copy() for f in range(2) for w in range(2)]
+    e0, a0, b0 = L.scalars()
+    L.step(30)
+    assert abs(L.scalars()[1] - a0) > 1e-3
+    L.step(30, h=-0.02)
+    s1 = [L.get(f, w) for f in range(2) for w in range(2)]
+    for x, y in zip(s0, s1):
+        assert np.abs(x - y).max() < 1e-11 * max(1.0, np.abs(x).max())
+    e1, a1, b1 = L.scalars()
+    assert abs(a1 - a0) < 1e-13 and abs(b1 - b0) < 1e-13 and abs(e1 - e0) < 1e-13
+
+
+def test_minkowski_energy_conservation_order(oracle_mod):
+    T, v = 1.0, []
+    for dt in (0.04, 0.02):
+        L = fluct_lattice(O.VV2, dt, expansion=O.EXP_OFF, amp=0.3)
+        L.step(int(round(T / dt)))
+        v.append(abs(L.energies()["energy_cons"]))
+    assert abs(math.log(v[0] / v[1], 2) - 2) < 0.4, v
+
+
+def test_plane_wave_energies(oracle_mod):
+    N, kIR, A = 16, 0.5, 0.7
+    dx = 2 * np.pi / (N * kIR)
+    m = (1, 2, 3)
+    L = O.Oracle(O.MODEL_LPHI4, N, kIR, 1.0, 1, O.make_params())
+    L.set(0, 0, plane_wave(N, m, A))
+    L.set(0, 1, np.full((N, N, N), 0.25))
+    e = L.energies()
+    assert abs(e["EG"][0] - 0.25 * A * A * np.sum(k_lat(m, N, dx) ** 2)) < 1e-13
+    assert abs(e["EV"][0] - A ** 4 * 3.0 / 32.0) < 1e-14
+    assert abs(e["EK"][0] - 0.25 ** 2 / 2) < 1e-15
+
+
+def test_gradient_energy_summation_by_parts(oracle_mod):
+    """sum (grad^+ phi)^2 = -sum phi Lap phi: E_G is the energy whose force the kick applies."""
+    N, kIR = 8, 1.0
+    dx = 2 * np.pi / (N * kIR)
+    rng = np.random.default_rng(5)
+    phi = rng.standard_normal((N, N, N))
+    L = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, O.make_params(dt=1.0, q=0.0))
+    L.set(0, 0, np.zeros((N, N, N))); L.set(0, 1, np.zeros((N, N, N)))
+    L.set(1, 0, phi); L.set(1, 1, np.zeros((N, N, N)))
+    EG = L.energies()["EG"][1]
+    # one drift-free probe: kick with h=1 (VV2 half kicks) gives pi = Lap(phi) when phi is frozen
+    L2 = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, O.make_params(dt=1.0, q=0.0))
+    L2.set(1, 0, phi)
+    L2.step(1, h=1e-30)   # kick weights 0.5e-30 each: pi = 1e-30 * Lap(phi)
+    lap = L2.get(1, 1) / 1e-30
+    assert abs(EG - (-np.sum(phi * lap) / (2 * N ** 3))) < 1e-12 * abs(EG)
+
+
+# --------------------------------------------------------------------------
+# spectra: Parseval identity (eq. discretePSII), single-bin plane wave
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dk", [1.0, 2.0])
+def test_spectrum_parseval(oracle_mod, dk):
+    N, kIR = 16, 0.3
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal((N, N, N)) + 0.4
+    L = O.Oracle(O.MODEL_LPHI4, N, kIR, 1.0, 1, O.make_params())
+    L.set(0, 0, f)
+    k, d, m = L.spectrum(0, 0, dk)
+    nz = m > 0
+    lhs = np.sum(kIR / k[nz] * d[nz])
+    assert abs(lhs - (np.mean(f ** 2) - np.mean(f) ** 2)) < 1e-12
+    # multiplicities: brute-force count of integer wave vectors per shell
+    n = np.fft.fftfreq(N, 1.0 / N)
+    nn = np.sqrt(n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2).reshape(-1)
+    nn = nn[nn > 0]
+    cnt = np.bincount(np.floor(nn / dk).astype(int), minlength=len(m))
+    assert np.array_equal(cnt[: len(m)], m)
+
+
+def test_spectrum_plane_wave_single_bin(oracle_mod):
+    N, kIR, A = 16, 0.3, 0.8
+    L = O.Oracle(O.MODEL_LPHI4, N, kIR, 1.0, 1, O.make_params())
+    L.set(0, 0, plane_wave(N, (3, 0, 0), A))
+    k, d, m = L.spectrum(0, 0, 1.0)
+    assert np.count_nonzero(np.abs(d) > 1e-20) == 1 and abs(d[3]) > 0
+    n = np.fft.fftfreq(N, 1.0 / N)
+    nn = np.sqrt(n[:, None, None] ** 2 + n[None, :, None] ** 2 + n[None, None, :] ** 2).reshape(-1)
+    shell = nn[(nn >= 3) & (nn < 4)]
+    assert abs(k[3] - kIR * shell.mean()) < 1e-12 * kIR
+    assert abs(kIR / k[3] * d[3] - A * A / 2) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# initial conditions (eqs. fpr_influct, fpr_influct2, QuantumFlucts2)
+# --------------------------------------------------------------------------
+def ic_modes(N=16, kIR=0.5, seed=7, amp=1.0, kcut=-1.0):
+    p = O.make_params(dt=0.01, q=100.0, phi0=[1.0, 0.0], fluct_amp2=amp, kcut=kcut)
+    L = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed, p)
+    dx = 2 * np.pi / (N * kIR)
+    n = np.fft.fftfreq(N, 1.0 / N)
+    kk = kIR * np.sqrt(n[None, None, :] ** 2 + n[None, :, None] ** 2 + n[:, None, None] ** 2)
+    out = []
+    for f, m2 in ((0, 3.0), (1, 100.0)):
+        F = np.fft.fftn(L.get(f, 0) - (1.0 if f == 0 else 0.0))
+        G = np.fft.fftn(L.get(f, 1))
+        w = np.sqrt(kk ** 2 + m2)
+        P = amp * (N / dx) ** 3 / (2 * w)
+        out.append((F, G, w, P, kk))
+    return L, out
+
+
+def interior_mask(N):
+    idx = np.arange(N ** 3).reshape(N, N, N)
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    pid = ((-x) % N) + N * (((-y) % N) + N * ((-z) % N))
+    return pid != idx
+
+
+def test_ic_amplitudes_and_phases(oracle_mod):
+    stats = pytest.importorskip("scipy.stats")
+    N = 16
+    L, modes = ic_modes(N)
+    mask = interior_mask(N)
+    for F, G, w, P, kk in modes:
+        r = (np.abs(F) ** 2 / P)[mask]
+        assert abs(r.mean() - 1.0) < 0.08
+        # |d phi(k)|^2 / P is exponential(1): Rayleigh amplitudes, uniform phases
+        assert stats.kstest(r, "expon").pvalue > 1e-3
+        ph = np.angle(F[mask])
+        assert stats.kstest((ph + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
+        g = (np.abs(G) ** 2 / (w ** 2 * P))[mask]
+        assert abs(g.mean() - 1.0) < 0.08
+        c = (F * np.conj(G) / (w * P))[mask]
+        assert abs(c.mean()) < 0.08
+        assert abs(F[0, 0, 0]) < 1e-9 and abs(G[0, 0, 0]) < 1e-9
+
+
+def test_ic_variance_over_seeds(oracle_mod):
+    """<dphi^2>_V averaged over seeds -> (omega*/f*)^2 L^-3 sum_{k != 0} 1/(2 a^2 omega_k)."""
+    N, kIR = 8, 0.5
+    dx = 2 * np.pi / (N * kIR)
+    n = np.fft.fftfreq(N, 1.0 / N)
+    kk = kIR * np.sqrt(n[None, None, :] ** 2 + n[None, :, None] ** 2 + n[:, None, None] ** 2)
+    w = np.sqrt(kk ** 2 + 3.0)
+    sc = ~interior_mask(N)
+    terms = 1.0 / (2 * w)
+    terms[sc] *= 0.5      # self-conjugate sites keep only the real part
+    terms[0, 0, 0] = 0.0
+    expect = np.sum(terms) / (N * dx) ** 3
+    vals = []
+    for seed in range(1, 41):
+        p = O.make_params(q=100.0, phi0=[1.0, 0.0], fluct_amp2=1.0)
+        L = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed, p)
+        vals.append(np.mean((L.get(0, 0) - 1.0) ** 2))
+    vals = np.array(vals)
+    assert abs(vals.mean() - expect) < 4 * vals.std() / np.sqrt(len(vals))
+
+
+def test_ic_seed_and_cutoff(oracle_mod):
+    La, ma = ic_modes(8, seed=11)
+    Lb, mb = ic_modes(8, seed=11)
+    Lc, mc = ic_modes(8, seed=12)
+    assert np.array_equal(La.get(0, 0), Lb.get(0, 0))
+    assert not np.allclose(La.get(0, 0), Lc.get(0, 0))
+    Lk, mk = ic_modes(16, seed=11, kcut=1.5)
+    for F, G, w, P, kk in mk:
+        assert np.abs(F[kk > 1.5 + 1e-12]).max() < 1e-9
+        assert np.abs(F[(kk > 0) & (kk <= 1.5)]).min() > 0
+
+
+# --------------------------------------------------------------------------
+# U(1) Abelian-Higgs: Gauss law, gauge invariance, free gauge waves,
+# homogeneous charged field vs ODE, energy conservation, reversibility
+# --------------------------------------------------------------------------
+def u1_lattice(N=8, dt=0.05, integ=O.LF, amp=0.05, seed=5, gQ=0.5, fo=0.8, expansion=O.EXP_OFF):
+    p = O.make_params(dt=dt, integrator=integ, lam=1.0, v=1.0, gQ=gQ, fstar_over_omegastar=fo,
+                      phi0=[1.0, 1.0], fluct_amp2=amp, expansion=expansion, fstar_over_mp=0.5)
+    return O.Oracle(O.MODEL_U1_HIGGS, N, 1.0, 1.0, seed, p)
+
+
+def test_u1_gauss_law_preserved(oracle_mod):
+    L = u1_lattice()
+    r0, l0, s0, m0 = L.gauss()
+    assert s0 > 1e-6 and r0 < 1e-13
+    L.step(200)
+    r1, l1, s1, m1 = L.gauss()
+    assert r1 < 1e-12, (r0, r1)
+    assert np.abs(L.get(2, 0)).max() > 1e-4    # links have moved
+
+
+def test_u1_gauss_law_with_expansion(oracle_mod):
+    L = u1_lattice(integ=O.VV4, expansion=O.EXP_SELF)
+    L.step(50)
+    assert L.scalars()[1] > 1.005
+    assert L.gauss()[0] < 1e-12
+
+
+def gauge_transform(L, alpha_n, gQ, N, dx, sign=+1.0):
+    th = gQ * alpha_n
+    c, s = np.cos(th), np.sin(th)
+    for what in (0, 1):
+        x, y = L.get(0, what), L.get(1, what)
+        L.set(0, what, c * x - s * y)
+        L.set(1, what, s * x + c * y)
+    for i, ax in enumerate((2, 1, 0)):   # arrays are [z][y][x]
+        grad = (np.roll(alpha_n, -1, axis=ax) - alpha_n) / dx
+        L.set(2 + i, 0, L.get(2 + i, 0) + sign * grad)
+
+
+def test_u1_gauge_invariance(oracle_mod):
+    N, gQ = 8, 0.5
+    dx = 2 * np.pi / N
+    L1, L2 = u1_lattice(N=N, gQ=gQ), u1_lattice(N=N, gQ=gQ)
+    L1.step(5); L2.step(5)
+    rng = np.random.default_rng(9)
+    al = rng.standard_normal((N, N, N))
+    gauge_transform(L2, al, gQ, N, dx)
+    keys = ("EK", "EG", "EV")
+    e1, e2 = L1.energies(), L2.energies()
+    for k in keys:
+        assert abs(e1[k][0] - e2[k][0]) < 1e-12 * abs(e1[k][0])
+    assert abs(e1["EGA"] - e2["EGA"]) < 1e-12 * max(abs(e1["EGA"]), 1e-30) + 1e-16
+    L1.step(20); L2.step(20)
+    e1, e2 = L1.energies(), L2.energies()
+    for k in keys:
+        assert abs(e1[k][0] - e2[k][0]) < 1e-10 * abs(e1[k][0])
+    for i in range(3):
+        assert np.abs(L1.get(2 + i, 1) - L2.get(2 + i, 1)).max() < 1e-10
+    mod1 = L1.get(0, 0) ** 2 + L1.get(1, 0) ** 2
+    mod2 = L2.get(0, 0) ** 2 + L2.get(1, 0) ** 2
+    assert np.abs(mod1 - mod2).max() < 1e-10
+    # the sign printed in the toolkit (A -> A - grad alpha) does not leave the energy invariant
+    L3 = u1_lattice(N=N, gQ=gQ)
+    L3.step(5)
+    gauge_transform(L3, al, gQ, N, dx, sign=-1.0)
+    e0 = u1_lattice(N=N, gQ=gQ)
+    e0.step(5)
+    assert abs(L3.energies()["EG"][0] - e0.energies()["EG"][0]) > 1e-3 * e0.energies()["EG"][0]
+
+
+@pytest.mark.parametrize("integ", [O.LF, O.VV4])
+def test_u1_free_gauge_wave(oracle_mod, integ):
+    """phi = 0: transverse link waves obey the lattice dispersion 2 sin(k dx/2)/dx."""
+    N, h, nsteps, eps = 16, 0.1, 30, 1e-6
+    dx = 2 * np.pi / N
+    p = O.make_params(dt=h, integrator=integ, lam=1.0, v=1.0, gQ=0.7, phi0=[0.0, 0.0])
+    L = O.Oracle(O.MODEL_U1_HIGGS, N, 1.0, 1.0, 1, p)
+    wave = plane_wave(N, (2, 0, 0), eps)   # A_y(x)
+    L.set(3, 0, wave)
+    L.step(nsteps)
+    w2 = float(k_lat(2, N, dx) ** 2)
+    M = np.eye(2)
+    for d in O.schedule(integ, h):
+        M = verlet_matrix(w2, d) @ M
+    st = np.linalg.matrix_power(M, nsteps) @ np.array([1.0, 0.0])
+    assert np.abs(L.get(3, 0) - st[0] * wave).max() < 1e-9 * eps
+    assert np.abs(L.get(3, 1) - st[1] * wave).max() < 1e-9 * eps
+    assert np.abs(L.get(2, 0)).max() == 0.0 and np.abs(L.get(0, 0)).max() == 0.0
+
+
+def test_u1_homogeneous_charged_field_vs_ode(oracle_mod):
+    lam, v, T, dt = 1.0, 1.0, 3.0, 0.01
+    p = O.make_params(dt=dt, integrator=O.VV4, lam=lam, v=v, gQ=0.5,
+                      phi0=[1.3, 0.4], dphi0=[0.2, -0.5])
+    L = O.Oracle(O.MODEL_U1_HIGGS, 2, 1.0, 1.0, 1, p)
+    # V = lam (|phi|^2 - v^2)^2, |phi|^2 = (phi_0^2 + phi_1^2)/2 (eq. ChargedScalars)
+    Vf, dV = sympy_forces(lambda a, b: lam * ((a ** 2 + b ** 2) / 2 - v ** 2) ** 2, 2)
+    e0 = L.energies()
+    assert abs(e0["EV"][0] - Vf(1.3, 0.4)) < 1e-14
+    assert abs(e0["EK"][0] - (0.2 ** 2 + 0.5 ** 2) / 2) < 1e-14
+    L.step(int(round(T / dt)))
+
+    def rhs(t, y):
+        return [y[2], y[3], -dV[0](y[0], y[1]), -dV[1](y[0], y[1])]
+
+    sol = solve_ivp(rhs, (0, T), [1.3, 0.4, 0.2, -0.5], method="DOP853", rtol=1e-13, atol=1e-14)
+    got = [L.get(0, 0)[0, 0, 0], L.get(1, 0)[0, 0, 0], L.get(0, 1)[0, 0, 0], L.get(1, 1)[0, 0, 0]]
+    assert np.abs(np.array(got) - sol.y[:, -1]).max() < 1e-7
+
+
+def test_u1_energy_conservation_order(oracle_mod):
+    T, v = 1.0, []
+    for dt in (0.08, 0.04):
+        L = u1_lattice(dt=dt, integ=O.VV2, amp=0.3)
+        L.step(int(round(T / dt)))
+        v.append(abs(L.energies()["energy_cons"]))
+    assert abs(math.log(v[0] / v[1], 2) - 2) < 0.4, v
+
+
+def test_u1_reversibility(oracle_mod):
+    L = u1_lattice(integ=O.VV4, expansion=O.EXP_SELF)
+    s0 = [L.get(f, w).copy() for f in range(5) for w in range(2)]
+    L.step(20)
+    L.step(20, h=-0.05)
+    s1 = [L.get(f, w) for f in range(5) for w in range(2)]
+    for x, y in zip(s0, s1):
+        assert np.abs(x - y).max() < 1e-11 * max(1.0, np.abs(x).max())
