@@ -1,0 +1,177 @@
+/*
+ * cl.h -- C ABI of the GB300 (sm_103a) lattice kick-drift library.
+ *
+ * The library evolves interacting scalar fields, and U(1) gauge links, on a
+ * periodic N^3 lattice in an expanding background, as described in the
+ * CosmoLattice manual (arXiv:2102.01031): the Hamiltonian form of the field
+ * and Friedmann equations in program variables (Sec. 3.5.2 for singlets,
+ * Sec. 4.3 for the U(1) sector), advanced by velocity-Verlet / leapfrog
+ * kick-drift steps and their symmetric compositions (VV4..VV10, Sec. 3.3.1
+ * "evolver"), with vacuum-fluctuation initial conditions (Sec. 3.5.1 eqs.
+ * fpr_influct, fpr_influct2, QuantumFlucts2; Sec. 4.4.1 for charged fields)
+ * and the binned power spectrum of eq. discretePS.
+ *
+ * Conventions shared by every entry point
+ *   - Status codes only (cl_status); nothing aborts or traps.  A failed call
+ *     leaves a message retrievable with cl_last_error(ctx).
+ *   - All device memory is owned by the context: allocated by cl_init,
+ *     released by cl_free.  Host arrays passed in or out are owned by the
+ *     caller and must hold the stated number of elements.
+ *   - Lattice arrays are N^3 values, row major with x fastest: site
+ *     (x, y, z) is element x + N*(y + N*z).
+ *   - Field indices: scalar models: 0 .. nf-1 (phi, chi).  U(1) model:
+ *     0, 1 = real components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2),
+ *     2, 3, 4 = link fields A_x, A_y, A_z (stored non-compactly, the link is
+ *     exp(-i gQ dx A_i)).  `what`: 0 = field, 1 = conjugate momentum
+ *     (pi = a^{3-alpha} phi' for scalars, pi_A = a^{1-alpha} F_0i for links).
+ *   - Work is enqueued on params.stream (a cudaStream_t, e.g. the current
+ *     torch stream; NULL = legacy default stream).  cl_step only enqueues;
+ *     every call that returns data to the host synchronises that stream.
+ *   - Momenta run half a kick ahead of the fields between cl_step calls (the
+ *     kicks of consecutive steps are merged); calls that observe the state
+ *     first close the stream of kicks with a half kick (the manual's `sync`,
+ *     Sec. 5.1), after which fields and momenta are at the same time.
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef CL_H
+#define CL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cl_ctx cl_ctx;
+
+typedef enum {
+  CL_OK = 0,
+  CL_EINVAL = 1,        /* bad argument */
+  CL_ENOMEM = 2,        /* device allocation failed */
+  CL_ECUDA = 3,         /* CUDA runtime error (message in cl_last_error) */
+  CL_ESTATE = 4,        /* call not valid in the context's current state */
+  CL_ETIMEOUT = 5,      /* a bounded device-side wait gave up; context unusable */
+  CL_ENONFINITE = 6,    /* a measured quantity was NaN/Inf; data still returned */
+  CL_EUNSUPPORTED = 7   /* combination of options not built */
+} cl_status;
+
+enum { CL_MODEL_LPHI4 = 1,      /* V = phi^4/4                              (eq. PotNat, chi = 0) */
+       CL_MODEL_LPHI4_CHI = 2,  /* V = phi^4/4 + (q/2) phi^2 chi^2          (eq. PotNat) */
+       CL_MODEL_U1_HIGGS = 3 }; /* V = lam (|phi|^2 - v^2)^2 + U(1) links    (Sec. 4) */
+
+enum { CL_LF = 0, CL_VV2 = 2, CL_VV4 = 4, CL_VV6 = 6, CL_VV8 = 8, CL_VV10 = 10 };
+enum { CL_FP64 = 0,             /* fields, momenta and arithmetic in FP64 */
+       CL_FP32 = 1 };           /* fields and momenta stored and updated in FP32;
+                                   reductions, a, b and constraints in FP64 */
+enum { CL_EXP_OFF = 0, CL_EXP_SELF = 1, CL_EXP_FIXED = 2 };
+
+/* Run parameters (subset of the manual's RunParameters and model variables,
+ * Appendix "Parameters"; all in program units).  f_s, omega_s below are the
+ * manual's f_* and omega_*. */
+typedef struct {
+  double dt;                    /* time step */
+  double q;                     /* resonance parameter g^2/lambda (CL_MODEL_LPHI4_CHI) */
+  double fluct_amp2;            /* (omega_s/f_s)^2 in eq. QuantumFlucts2; 0 = no fluctuations */
+  double fstar_over_mp;         /* f_s/m_p in the Friedmann equations */
+  double phi0[4];               /* homogeneous initial values (per field / component) */
+  double dphi0[4];              /* homogeneous initial phi' */
+  double lam, v;                /* U(1) model potential lam (|phi|^2 - v^2)^2 */
+  double gQ;                    /* U(1) coupling times charge */
+  double fstar_over_omegastar;  /* f_s/omega_s (U(1) model) */
+  double kcut;                  /* initial-spectrum cutoff (eq. kCutOff); < 0 = none */
+  double omega_eos;             /* fixed background: equation of state w */
+  double H0;                    /* fixed background: initial a'/a; <= 0 -> Hubble law */
+  int integrator;               /* CL_LF, CL_VV2, CL_VV4 .. CL_VV10 */
+  int expansion;                /* CL_EXP_OFF, CL_EXP_SELF, CL_EXP_FIXED */
+  int b0_mode;                  /* 0: a'(t0) from homogeneous values (Sec. 5.2); 1: from averages */
+  int precision;                /* CL_FP64 or CL_FP32 */
+  void* stream;                 /* cudaStream_t */
+} cl_params;
+
+/* Volume averages at a synchronised time (eqs. EK_EG_EV, energy-contrib). */
+typedef struct {
+  double eta, a, b;             /* time, scale factor, b = a' */
+  double EK[4], EG[4];          /* kinetic / gradient energy per scalar species */
+  double EV[4];                 /* potential energy per potential term */
+  double EKA, EGA;              /* U(1) electric / magnetic energy */
+  double rho;                   /* total energy density */
+  double hubble_lhs, hubble_rhs, hubble_viol; /* a'^2, RHS of eq. NewFriedmannEQsI, (L-R)/(L+R) */
+  double energy_cons;           /* 1 - rho/rho(t0) (meaningful without expansion) */
+  double mean_phi[4], mean_phi2[4], mean_pi[4], mean_pi2[4];
+  int64_t nonfinite;            /* number of non-finite momenta seen in the last measurement */
+} cl_energies_t;
+
+/* Create a lattice of N^3 sites with kIR (so dx = 2 pi/(N kIR)), alpha of
+ * eq. FieldSpaceTimeNaturalVariables, and vacuum fluctuations drawn from
+ * `seed` (Sec. 3.5.1), all generated on the GPU.  N must be a multiple of 8,
+ * at most 512, with no prime factor above 3.  Returns CL_EINVAL for bad
+ * arguments, CL_ENOMEM / CL_ECUDA on device failure (*out is then NULL). */
+cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
+                  const cl_params* p);
+cl_status cl_free(cl_ctx* ctx);
+
+/* Enqueue n full time steps of params.dt (n >= 0); cl_step_h uses step h
+ * (negative h runs the integrator backwards).  Asynchronous. */
+cl_status cl_step(cl_ctx* ctx, int n);
+cl_status cl_step_h(cl_ctx* ctx, int n, double h);
+
+/* Close the stream of kicks so that fields and momenta are at the same time
+ * (the manual's `sync`).  Asynchronous; a no-op when already closed. */
+cl_status cl_sync(cl_ctx* ctx);
+
+/* Energies and means at the current (synchronised) time.  Synchronises the
+ * stream.  Returns CL_ENONFINITE (with *out filled) if non-finite momenta were
+ * seen. */
+cl_status cl_energies(cl_ctx* ctx, cl_energies_t* out);
+
+/* U(1) Gauss-law monitor (Sec. 4.5, average_gauss): LHS = sum_i grad^-_i pi_A,i,
+ * RHS = (f_s/omega_s)^2 2 gQ Im[phi^* pi_phi]; rel = <|L-R|>/<|L+R|>.
+ * CL_EUNSUPPORTED for models without links.  Synchronises the stream. */
+cl_status cl_gauss_constraint(cl_ctx* ctx, double* rel, double* lhs_abs, double* rhs_abs,
+                              double* max_abs);
+
+/* Binned power spectrum of eq. discretePS of field `field`, what = 0 (field)
+ * or 1 (momentum), with bin width dk_bin in units of kIR: bins b =
+ * floor(|n~|/dk_bin) over n~ != 0, k_b = kIR <|n~|>_b, delta_b =
+ * k_b^3/(2 pi^2) (dx/N)^3 sum_b |f(n~)|^2 / (4 pi <|n~|>_b^2), mult_b = sites in
+ * the bin.  Arrays k, delta, mult hold `cap` entries; *nbins receives the bin
+ * count (CL_EINVAL if cap is too small).  Synchronises the stream. */
+cl_status cl_spectrum(cl_ctx* ctx, int field, int what, double dk_bin, double* k, double* delta,
+                      int64_t* mult, int cap, int* nbins);
+
+/* Copy one lattice array to / from the host as FP64 (N^3 values).  Both
+ * synchronise the kick stream first; set_state stores in the context's
+ * precision. */
+cl_status cl_get_state(cl_ctx* ctx, int field, int what, double* host_out);
+cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
+
+/* Scale factor, its derivative and the time.  cl_set_scalars also resets the
+ * reference energy of energy_cons to the current state. */
+cl_status cl_get_scalars(cl_ctx* ctx, double* eta, double* a, double* b);
+cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
+
+/* Raw state transfer in the storage precision, for end-to-end use: the whole
+ * state (every field and momentum array, in field order, field then
+ * momentum) is `*bytes` long.  Host buffers should be pinned for speed.
+ * Both synchronise the kick stream first; the copies are enqueued on the
+ * context stream (cl_download_state waits for its copy to finish). */
+cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
+cl_status cl_upload_state(cl_ctx* ctx, const void* host, size_t bytes);
+cl_status cl_download_state(cl_ctx* ctx, void* host, size_t bytes);
+
+int cl_nfields(const cl_ctx* ctx);           /* lattice arrays per kind (what=0 or 1) */
+int64_t cl_kernel_launches(const cl_ctx* ctx); /* kernels this context has launched */
+const char* cl_last_error(const cl_ctx* ctx);  /* never NULL; ctx may be NULL */
+
+/* Timing hook for measurement tools: a CUDA event pair is recorded on the
+ * context stream around every DK pass launch when enabled; the summed
+ * device time of those passes (ms) and their count since the last reset are
+ * returned by cl_pass_timing.  Disabled by default (no events recorded). */
+cl_status cl_enable_pass_timing(cl_ctx* ctx, int enable);
+cl_status cl_pass_timing(cl_ctx* ctx, double* ms_total, int64_t* passes, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -114,6 +114,9 @@ def lib():
             L.clo_fft3d.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int]
             L.clo_dft3d_naive.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_int]
             L.clo_schedule.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int]
+            L.clo_ic_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64), dp]
             _lib = L
         return _lib
 
@@ -255,6 +258,19 @@ def dft3d_naive(x, sign):
     if lib().clo_dft3d_naive(_dp(re), _dp(im), _dp(ore), _dp(oim), N, sign) != 0:
         raise ValueError("dft3d_naive")
     return (ore + 1j * oim).reshape(x.shape)
+
+
+def ic_sample(model, N, kIR, alpha, seed, params, idx):
+    """Initial Fourier values (F, G) per field at the given linear site indices."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    nf = 1 if model == MODEL_LPHI4 else 2
+    out = np.zeros(idx.size * nf * 4)
+    rc = lib().clo_ic_sample(model, N, kIR, alpha, seed, ctypes.byref(params), idx.size,
+                             idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    if rc != 0:
+        raise ValueError("clo_ic_sample")
+    o = out.reshape(idx.size, nf, 4)
+    return o[..., 0] + 1j * o[..., 1], o[..., 2] + 1j * o[..., 3]
 
 
 def schedule(integrator, h):

@@ -486,14 +486,65 @@ void draw4(uint64_t seed, long idx, int f, int j, double u[2]) {
   u[1] = u01(r[2], r[3]);
 }
 
-// Fourier modes of the field fluctuation (F) and of its time derivative (G).
-void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F,
-                 std::vector<cplx>* G) {
+// Fourier values of the fluctuation (F[f]) and of its time derivative (G[f])
+// at the canonical site idx (idx <= partner).  Returns false for sites that
+// stay zero.
+bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, cplx* G) {
   double a = c->a, al = c->alpha, amp2 = c->p.fluct_amp2;
   double vol = std::pow((double)c->N / c->dx, 3.0);
   const double isq2 = 1.0 / std::sqrt(2.0);
-  double m2[2];
-  for (int k = 0; k < c->nf; ++k) m2[k] = mass2(c, c->p.phi0, k);
+  if (idx == 0) return false;
+  long pid = partner_index(c, idx);
+  bool selfc = pid == idx;
+  if (selfc && c->gauge()) return false;  // reading: keeps the charge density's zero mode exactly 0
+  double k = mode_k(c, idx);
+  if (c->p.kcut >= 0.0 && k > c->p.kcut) return false;
+  if (amp2 <= 0.0) return false;
+  cplx z1[2], z2[2];
+  double om[2];
+  for (int f = 0; f < c->nf; ++f) {
+    double w2 = k * k + a * a * mass2(c, c->p.phi0, f);
+    if (w2 <= 0.0) return false;
+    om[f] = std::sqrt(w2);
+  }
+  if (!c->gauge()) {
+    for (int f = 0; f < c->nf; ++f) {
+      double P = amp2 * vol / (2.0 * a * a * om[f]);
+      double u[2], v[2];
+      draw4(seed, idx, f, 0, u);
+      draw4(seed, idx, f, 1, v);
+      z1[f] = std::polar(std::sqrt(-P * std::log(u[0])), 2.0 * PI * v[0]);
+      z2[f] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
+    }
+  } else {
+    // eqs. InConstr:1-2: |d_{c1}| = |d_{c2}|, theta_12 = theta_02 + theta_11 - theta_01
+    double P0 = amp2 * vol / (2.0 * a * a * om[0]);
+    double P1 = amp2 * vol / (2.0 * a * a * om[1]);
+    double u0[2], v0[2], u1[2], v1[2];
+    draw4(seed, idx, 0, 0, u0);
+    draw4(seed, idx, 0, 1, v0);
+    draw4(seed, idx, 1, 0, u1);
+    draw4(seed, idx, 1, 1, v1);
+    double r0 = std::sqrt(-P0 * std::log(u0[0]));
+    double r1 = std::sqrt(-P1 * std::log(u1[0]));
+    double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1], t11 = 2.0 * PI * v1[0];
+    double t12 = t02 + t11 - t01;
+    z1[0] = std::polar(r0, t01); z2[0] = std::polar(r0, t02);
+    z1[1] = std::polar(r1, t11); z2[1] = std::polar(r1, t12);
+  }
+  for (int f = 0; f < c->nf; ++f) {
+    cplx df = (z1[f] + z2[f]) * isq2;
+    cplx dv = std::pow(a, al - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
+    if (selfc) { df = cplx(df.real(), 0.0); dv = cplx(dv.real(), 0.0); }
+    F[f] = df;
+    G[f] = dv;
+  }
+  return true;
+}
+
+// Fourier modes of the field fluctuation (F) and of its time derivative (G).
+void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F,
+                 std::vector<cplx>* G) {
   for (int k = 0; k < c->nf; ++k) {
     F[k].assign(c->V, cplx(0, 0));
     G[k].assign(c->V, cplx(0, 0));
@@ -501,51 +552,11 @@ void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F
   for (long idx = 1; idx < c->V; ++idx) {
     long pid = partner_index(c, idx);
     if (pid < idx) continue;
-    bool selfc = pid == idx;
-    if (selfc && c->gauge()) continue;  // reading: keeps the charge density's zero mode exactly 0
-    double k = mode_k(c, idx);
-    if (c->p.kcut >= 0.0 && k > c->p.kcut) continue;
-    if (amp2 <= 0.0) continue;
-    cplx z1[2], z2[2];
-    double om[2];
-    bool ok = true;
-    for (int f = 0; f < c->nf; ++f) {
-      double w2 = k * k + a * a * m2[f];
-      if (w2 <= 0.0) { ok = false; break; }
-      om[f] = std::sqrt(w2);
-    }
-    if (!ok) continue;
-    if (!c->gauge()) {
-      for (int f = 0; f < c->nf; ++f) {
-        double P = amp2 * vol / (2.0 * a * a * om[f]);
-        double u[2], v[2];
-        draw4(seed, idx, f, 0, u);
-        draw4(seed, idx, f, 1, v);
-        z1[f] = std::polar(std::sqrt(-P * std::log(u[0])), 2.0 * PI * v[0]);
-        z2[f] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
-      }
-    } else {
-      // eqs. InConstr:1-2: |d_{c1}| = |d_{c2}|, theta_12 = theta_02 + theta_11 - theta_01
-      double P0 = amp2 * vol / (2.0 * a * a * om[0]);
-      double P1 = amp2 * vol / (2.0 * a * a * om[1]);
-      double u0[2], v0[2], u1[2], v1[2];
-      draw4(seed, idx, 0, 0, u0);
-      draw4(seed, idx, 0, 1, v0);
-      draw4(seed, idx, 1, 0, u1);
-      draw4(seed, idx, 1, 1, v1);
-      double r0 = std::sqrt(-P0 * std::log(u0[0]));
-      double r1 = std::sqrt(-P1 * std::log(u1[0]));
-      double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1], t11 = 2.0 * PI * v1[0];
-      double t12 = t02 + t11 - t01;
-      z1[0] = std::polar(r0, t01); z2[0] = std::polar(r0, t02);
-      z1[1] = std::polar(r1, t11); z2[1] = std::polar(r1, t12);
-    }
-    for (int f = 0; f < c->nf; ++f) {
-      cplx df = (z1[f] + z2[f]) * isq2;
-      cplx dv = std::pow(a, al - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
-      if (selfc) { df = cplx(df.real(), 0.0); dv = cplx(dv.real(), 0.0); }
-      F[f][idx] = df; G[f][idx] = dv;
-      F[f][pid] = std::conj(df); G[f][pid] = std::conj(dv);
+    cplx f[2], g[2];
+    if (!mode_values(c, seed, H, idx, f, g)) continue;
+    for (int k = 0; k < c->nf; ++k) {
+      F[k][idx] = f[k]; G[k][idx] = g[k];
+      F[k][pid] = std::conj(f[k]); G[k][pid] = std::conj(g[k]);
     }
   }
 }
@@ -684,17 +695,24 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
     c->b = 0.0;
   }
   double H = c->b / c->a;
-  // fluctuations
-  std::vector<cplx> F[2], G[2];
-  fluct_modes(c, seed, H, F, G);
   double a3ma = std::pow(c->a, 3.0 - alpha);
-  for (int k = 0; k < c->nf; ++k) {
-    fft3d(F[k], N, +1);
-    fft3d(G[k], N, +1);
-    for (long n = 0; n < c->V; ++n) {
-      c->phi[k][n] = p->phi0[k] + F[k][n].real() / (double)c->V;
-      c->pi[k][n] = a3ma * (p->dphi0[k] + G[k][n].real() / (double)c->V);
+  if (p->fluct_amp2 > 0.0) {
+    std::vector<cplx> F[2], G[2];
+    fluct_modes(c, seed, H, F, G);
+    for (int k = 0; k < c->nf; ++k) {
+      fft3d(F[k], N, +1);
+      fft3d(G[k], N, +1);
+      for (long n = 0; n < c->V; ++n) {
+        c->phi[k][n] = p->phi0[k] + F[k][n].real() / (double)c->V;
+        c->pi[k][n] = a3ma * (p->dphi0[k] + G[k][n].real() / (double)c->V);
+      }
     }
+  } else {  // no fluctuations: every Fourier mode but the homogeneous one is zero
+    for (int k = 0; k < c->nf; ++k)
+      for (long n = 0; n < c->V; ++n) {
+        c->phi[k][n] = p->phi0[k];
+        c->pi[k][n] = a3ma * p->dphi0[k];
+      }
   }
   if (c->gauge()) gauss_momenta(c);
   Avg r;
@@ -702,6 +720,45 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
   if (p->expansion == CLO_EXP_SELF && p->b0_mode == 1) c->b = b_from_hubble(c, rho_of(r));
   c->rho0 = rho_of(r);
   *out = c;
+  return 0;
+}
+
+// Fourier values of the initial fluctuations at selected sites, without
+// building the lattice: out[(i*nf + f)*4 + {0,1,2,3}] = Re F, Im F, Re G, Im G
+// of field f at site idx[i] (same conventions as clo_init).
+int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
+                  int n, const int64_t* idx, double* out) {
+  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_U1_HIGGS) return -1;
+  clo_ctx c;
+  c.model = model;
+  c.N = N;
+  c.V = (long)N * N * N;
+  c.nf = model == CLO_MODEL_LPHI4 ? 1 : 2;
+  c.kIR = kIR;
+  c.dx = 2.0 * PI / ((double)N * kIR);
+  c.alpha = alpha;
+  c.p = *p;
+  c.a = c.a0 = 1.0;
+  c.eta = c.eta0 = 0.0;
+  double rho_h = homogeneous_rho(&c);
+  if (p->expansion == CLO_EXP_SELF) c.b = b_from_hubble(&c, rho_h);
+  else if (p->expansion == CLO_EXP_FIXED) c.b = c.a * (p->H0 > 0.0 ? p->H0 : b_from_hubble(&c, rho_h) / c.a);
+  else c.b = 0.0;
+  for (int i = 0; i < n; ++i) {
+    long id = (long)idx[i];
+    if (id < 0 || id >= c.V) return -1;
+    long pid = partner_index(&c, id);
+    cplx f[2] = {0, 0}, g[2] = {0, 0};
+    bool conj = pid < id;
+    if (!mode_values(&c, seed, c.b / c.a, conj ? pid : id, f, g)) {
+      f[0] = f[1] = g[0] = g[1] = cplx(0, 0);
+    }
+    for (int k = 0; k < c.nf; ++k) {
+      cplx F = conj ? std::conj(f[k]) : f[k], G = conj ? std::conj(g[k]) : g[k];
+      double* o = out + ((size_t)i * c.nf + k) * 4;
+      o[0] = F.real(); o[1] = F.imag(); o[2] = G.real(); o[3] = G.imag();
+    }
+  }
   return 0;
 }
 

@@ -81,6 +81,8 @@ int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double*
                          double* max_abs);
 int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
                  double* delta, int64_t* mult, int cap, int* nbins);
+int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
+                  int n, const int64_t* idx, double* out);
 
 /* pieces exposed for the pin tests */
 void clo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

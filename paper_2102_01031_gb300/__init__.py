@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) lattice kick-drift library: Python binding of ``include/cl.h``.
+
+The library evolves scalar fields (and U(1) gauge links) on a periodic N^3
+lattice in an expanding universe with the velocity-Verlet / leapfrog
+kick-drift integrators of the CosmoLattice manual (arXiv:2102.01031).  Every
+step of the method runs in the CUDA kernels of ``libclgb300.so``; this module
+only marshals arguments through ctypes.  There is no CPU fallback: importing
+works without a GPU, but creating a lattice fails loudly when the library or
+the GPU is missing.
+
+Functions carry the names of the C ABI (``cl_init``, ``cl_step``,
+``cl_energies``, ``cl_gauss_constraint``, ``cl_spectrum``, ...); ``Lattice``
+wraps one context.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libclgb300.so")
+
+CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ESTATE, CL_ETIMEOUT, CL_ENONFINITE, CL_EUNSUPPORTED = range(8)
+MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS = 1, 2, 3
+LF, VV2, VV4, VV6, VV8, VV10 = 0, 2, 4, 6, 8, 10
+FP64, FP32 = 0, 1
+EXP_OFF, EXP_SELF, EXP_FIXED = 0, 1, 2
+
+# every entry point declared in include/cl.h
+EXPORTS = (
+    "cl_init", "cl_free", "cl_step", "cl_step_h", "cl_sync", "cl_energies", "cl_gauss_constraint",
+    "cl_spectrum", "cl_get_state", "cl_set_state", "cl_get_scalars", "cl_set_scalars",
+    "cl_state_bytes", "cl_upload_state", "cl_download_state", "cl_nfields", "cl_kernel_launches",
+    "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing",
+)
+
+
+class ClError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("cl status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("fluct_amp2", ctypes.c_double),
+        ("fstar_over_mp", ctypes.c_double),
+        ("phi0", ctypes.c_double * 4),
+        ("dphi0", ctypes.c_double * 4),
+        ("lam", ctypes.c_double),
+        ("v", ctypes.c_double),
+        ("gQ", ctypes.c_double),
+        ("fstar_over_omegastar", ctypes.c_double),
+        ("kcut", ctypes.c_double),
+        ("omega_eos", ctypes.c_double),
+        ("H0", ctypes.c_double),
+        ("integrator", ctypes.c_int),
+        ("expansion", ctypes.c_int),
+        ("b0_mode", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Energies(ctypes.Structure):
+    _fields_ = [
+        ("eta", ctypes.c_double), ("a", ctypes.c_double), ("b", ctypes.c_double),
+        ("EK", ctypes.c_double * 4), ("EG", ctypes.c_double * 4), ("EV", ctypes.c_double * 4),
+        ("EKA", ctypes.c_double), ("EGA", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("hubble_lhs", ctypes.c_double), ("hubble_rhs", ctypes.c_double),
+        ("hubble_viol", ctypes.c_double), ("energy_cons", ctypes.c_double),
+        ("mean_phi", ctypes.c_double * 4), ("mean_phi2", ctypes.c_double * 4),
+        ("mean_pi", ctypes.c_double * 4), ("mean_pi2", ctypes.c_double * 4),
+        ("nonfinite", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else (int(v) if name == "nonfinite" else float(v))
+        return d
+
+
+_lib = None
+
+
+def build(force=False):
+    """Compile csrc/*.cu for sm_103a into _build/libclgb300.so (see builder.py)."""
+    from . import builder
+    return builder.build(force=force)
+
+
+def lib():
+    """Load libclgb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("CUDA library not built: %s (run __graft_entry__.build())" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    L.cl_init.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                          ctypes.POINTER(Params)]
+    L.cl_free.argtypes = [vp]
+    L.cl_step.argtypes = [vp, ip]
+    L.cl_step_h.argtypes = [vp, ip, ctypes.c_double]
+    L.cl_sync.argtypes = [vp]
+    L.cl_energies.argtypes = [vp, ctypes.POINTER(Energies)]
+    L.cl_gauss_constraint.argtypes = [vp, dp, dp, dp, dp]
+    L.cl_spectrum.argtypes = [vp, ip, ip, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int64), ip,
+                              ctypes.POINTER(ctypes.c_int)]
+    L.cl_get_state.argtypes = [vp, ip, ip, dp]
+    L.cl_set_state.argtypes = [vp, ip, ip, dp]
+    L.cl_get_scalars.argtypes = [vp, dp, dp, dp]
+    L.cl_set_scalars.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.cl_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.cl_upload_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.cl_download_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.cl_nfields.argtypes = [vp]
+    L.cl_kernel_launches.argtypes = [vp]
+    L.cl_kernel_launches.restype = ctypes.c_int64
+    L.cl_last_error.argtypes = [vp]
+    L.cl_last_error.restype = ctypes.c_char_p
+    L.cl_enable_pass_timing.argtypes = [vp, ip]
+    L.cl_pass_timing.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ip]
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(**kw):
+    """cl_params with defaults; keywords override (stream: int handle or None)."""
+    p = Params()
+    p.dt = kw.pop("dt", 0.01)
+    p.q = kw.pop("q", 100.0)
+    p.fluct_amp2 = kw.pop("fluct_amp2", 0.0)
+    p.fstar_over_mp = kw.pop("fstar_over_mp", 0.0)
+    for name in ("phi0", "dphi0"):
+        vals = list(kw.pop(name, [0.0] * 4)) + [0.0] * 4
+        arr = getattr(p, name)
+        for i in range(4):
+            arr[i] = vals[i]
+    p.lam = kw.pop("lam", 1.0)
+    p.v = kw.pop("v", 1.0)
+    p.gQ = kw.pop("gQ", 0.5)
+    p.fstar_over_omegastar = kw.pop("fstar_over_omegastar", 1.0)
+    p.kcut = kw.pop("kcut", -1.0)
+    p.omega_eos = kw.pop("omega_eos", 0.0)
+    p.H0 = kw.pop("H0", 0.0)
+    p.integrator = kw.pop("integrator", VV2)
+    p.expansion = kw.pop("expansion", EXP_OFF)
+    p.b0_mode = kw.pop("b0_mode", 0)
+    p.precision = kw.pop("precision", FP64)
+    st = kw.pop("stream", None)
+    p.stream = ctypes.c_void_p(int(st) if st else 0)
+    if kw:
+        raise TypeError("unknown params: %s" % sorted(kw))
+    return p
+
+
+def torch_stream():
+    """Handle of torch's current CUDA stream (PyTorch supplies streams only)."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(L, h, rc, what):
+    if rc != CL_OK:
+        msg = L.cl_last_error(h).decode(errors="replace")
+        raise ClError(rc, "%s: %s" % (what, msg))
+
+
+class Lattice:
+    """One lattice context of the CUDA library (cl_init ... cl_free)."""
+
+    def __init__(self, model, N, kIR, alpha, seed, params):
+        self.L = lib()
+        self.N = N
+        self.V = N ** 3
+        self.params = params
+        h = ctypes.c_void_p()
+        rc = self.L.cl_init(ctypes.byref(h), model, N, kIR, alpha, seed, ctypes.byref(params))
+        if rc != CL_OK:
+            raise ClError(rc, "cl_init: " + self.L.cl_last_error(None).decode(errors="replace"))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cl_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def nfields(self):
+        return self.L.cl_nfields(self.h)
+
+    def step(self, n, h=None):
+        rc = self.L.cl_step(self.h, n) if h is None else self.L.cl_step_h(self.h, n, h)
+        _check(self.L, self.h, rc, "cl_step")
+
+    def sync(self):
+        _check(self.L, self.h, self.L.cl_sync(self.h), "cl_sync")
+
+    def energies(self, allow_nonfinite=False):
+        e = Energies()
+        rc = self.L.cl_energies(self.h, ctypes.byref(e))
+        if not (allow_nonfinite and rc == CL_ENONFINITE):
+            _check(self.L, self.h, rc, "cl_energies")
+        return e.as_dict()
+
+    def get(self, field, what=0):
+        out = np.empty(self.V, dtype=np.float64)
+        _check(self.L, self.h, self.L.cl_get_state(self.h, field, what, _dp(out)), "cl_get_state")
+        return out.reshape(self.N, self.N, self.N)  # [z][y][x]
+
+    def set(self, field, what, arr):
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+        if a.size != self.V:
+            raise ValueError("need %d values" % self.V)
+        _check(self.L, self.h, self.L.cl_set_state(self.h, field, what, _dp(a)), "cl_set_state")
+
+    def scalars(self):
+        e, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.L, self.h, self.L.cl_get_scalars(self.h, ctypes.byref(e), ctypes.byref(a),
+                                                     ctypes.byref(b)), "cl_get_scalars")
+        return e.value, a.value, b.value
+
+    def set_scalars(self, eta, a, b):
+        _check(self.L, self.h, self.L.cl_set_scalars(self.h, eta, a, b), "cl_set_scalars")
+
+    def gauss(self):
+        r, l, s, m = (ctypes.c_double() for _ in range(4))
+        _check(self.L, self.h, self.L.cl_gauss_constraint(self.h, ctypes.byref(r), ctypes.byref(l),
+                                                          ctypes.byref(s), ctypes.byref(m)),
+               "cl_gauss_constraint")
+        return r.value, l.value, s.value, m.value
+
+    def spectrum(self, field, what=0, dk_bin=1.0):
+        cap = 4096
+        k = np.zeros(cap)
+        d = np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.cl_spectrum(self.h, field, what, dk_bin, _dp(k), _dp(d),
+                                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_spectrum")
+        n = nb.value
+        return k[:n].copy(), d[:n].copy(), m[:n].copy()
+
+    def state_bytes(self):
+        n = ctypes.c_size_t()
+        _check(self.L, self.h, self.L.cl_state_bytes(self.h, ctypes.byref(n)), "cl_state_bytes")
+        return n.value
+
+    def upload(self, host_ptr, nbytes):
+        _check(self.L, self.h, self.L.cl_upload_state(self.h, ctypes.c_void_p(host_ptr), nbytes),
+               "cl_upload_state")
+
+    def download(self, host_ptr, nbytes):
+        _check(self.L, self.h, self.L.cl_download_state(self.h, ctypes.c_void_p(host_ptr), nbytes),
+               "cl_download_state")
+
+    def launches(self):
+        return int(self.L.cl_kernel_launches(self.h))
+
+    def enable_pass_timing(self, on=True):
+        _check(self.L, self.h, self.L.cl_enable_pass_timing(self.h, 1 if on else 0), "timing")
+
+    def pass_timing(self, reset=False):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self.L, self.h, self.L.cl_pass_timing(self.h, ctypes.byref(ms), ctypes.byref(n),
+                                                     1 if reset else 0), "timing")
+        return ms.value, n.value

@@ -1,0 +1,723 @@
+// capi.cu -- the C ABI of include/cl.h: context management, the work list of
+// the DK passes, the kick/drift schedule of the integrators and the launches.
+// Host code only marshals parameters and orders launches; every step of the
+// method (initial conditions, FFTs, passes, reductions, Friedmann updates,
+// spectra) runs in the kernels of this library.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cl.h"
+#include "common.cuh"
+
+namespace clg {
+
+// kernels defined in the other translation units
+typedef void (*PassKernel)(const PassArgs);
+PassKernel scalar_pass_kernel(int fp32, int nf, int red);
+PassKernel u1_pass_kernel(int fp32, int red);
+
+cudaError_t launch_init_scalars(const LatConst*, LatScalars*, const ICArgs&, cudaStream_t);
+cudaError_t launch_ic_modes(double2*, double2*, const LatConst*, const LatScalars*, const ICArgs&,
+                            int, long long, cudaStream_t);
+cudaError_t launch_ic_assemble(int, void*, void*, const double2*, const double2*, const LatConst*,
+                               const LatScalars*, double, double, long long, cudaStream_t);
+cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
+cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
+cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
+                        cudaStream_t);
+cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
+cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
+                                 void*, long long, int, cudaStream_t);
+cudaError_t launch_u1_gauss_monitor(const LatConst*, int, double*, int, long long, cudaStream_t);
+__global__ void set_scalars_kernel(const LatConst*, LatScalars*, double, double, double);
+__global__ void b_from_obs_kernel(const LatConst*, LatScalars*);
+
+}  // namespace clg
+
+using namespace clg;
+
+struct cl_ctx {
+  int model, N, nf, narr, fp32, esz;
+  long long V;
+  double kIR, dx, alpha;
+  cl_params p;
+  cudaStream_t stream;
+  int dev, nsm;
+  size_t smem_optin;
+  // device memory
+  void* slab = nullptr;            // 2 x narr lattice arrays
+  LatConst* d_lat = nullptr;
+  LatScalars* d_sc = nullptr;
+  Seg* d_segs = nullptr;
+  int* d_cta = nullptr;
+  double* d_part = nullptr;
+  unsigned* d_cnt = nullptr;
+  double* d_tmp = nullptr;         // scratch for conversions / spectra (V doubles)
+  double2* d_cplx = nullptr;       // scratch complex (2 V)
+  double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk) + output
+  LatConst hlat;
+  int grid = 0, nseg = 0, stages = 0;
+  unsigned stage_bytes = 0;
+  size_t smem_bytes = 0;
+  // schedule state
+  int parity = 0;
+  bool open = false;
+  double dprev = 0.0;
+  bool obs_valid = false;
+  long long launches = 0;
+  // timing hook
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  double timing_ms = 0.0;
+  long long timing_passes = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+cl_status fail(cl_ctx* c, cl_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_init_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? CL_ENOMEM : CL_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+  } while (0)
+
+#define CHECK_LAUNCH() CU(cudaGetLastError())
+
+bool good_N(int N) {
+  if (N < 8 || N > 512 || N % 8) return false;
+  int m = N;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+// Symmetric compositions: VV2 = one Stoermer-Verlet step; each higher order
+// is the triple jump z1, 1 - 2 z1, z1 of the previous one, z1 = 1/(2 - 2^{1/(k+1)}).
+void schedule(int order, double h, std::vector<double>& d) {
+  if (order <= 2) {
+    d.push_back(h);
+    return;
+  }
+  const double z1 = 1.0 / (2.0 - std::pow(2.0, 1.0 / (double)(order - 1)));
+  schedule(order - 2, z1 * h, d);
+  schedule(order - 2, (1.0 - 2.0 * z1) * h, d);
+  schedule(order - 2, z1 * h, d);
+}
+
+void fft_radices(int N, FftPlan& pl) {
+  pl.nrad = 0;
+  int m = N;
+  while (m % 4 == 0) { pl.rad[pl.nrad++] = 4; m /= 4; }
+  while (m % 2 == 0) { pl.rad[pl.nrad++] = 2; m /= 2; }
+  while (m % 3 == 0) { pl.rad[pl.nrad++] = 3; m /= 3; }
+}
+
+void* arr_ptr(cl_ctx* c, int parity, int a) {
+  return (char*)c->slab + ((size_t)parity * c->narr + a) * (size_t)c->V * c->esz;
+}
+
+cl_status fft3d(cl_ctx* c, double2* data, int sign) {
+  FftPlan pl;
+  pl.N = c->N;
+  pl.sign = sign;
+  fft_radices(c->N, pl);
+  for (int axis = 0; axis < 3; ++axis) {
+    pl.axis = axis;
+    CU(launch_fft_axis(data, pl, c->stream));
+    ++c->launches;
+  }
+  return CL_OK;
+}
+
+PassKernel pick_kernel(cl_ctx* c, int red) {
+  if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red);
+  return scalar_pass_kernel(c->fp32, c->nf, red);
+}
+
+cl_status run_pass(cl_ctx* c, double ck, double wout, double win, double dnext, int red, int write,
+                   int set_rho0) {
+  PassArgs A;
+  A.lat = c->d_lat;
+  A.sc = c->d_sc;
+  A.segs = c->d_segs;
+  A.cta_seg = c->d_cta;
+  A.partials = c->d_part;
+  A.counters = c->d_cnt;
+  A.ck = ck;
+  A.wout = wout;
+  A.win = win;
+  A.dnext = dnext;
+  A.parity = c->parity;
+  A.write = write;
+  A.set_rho0 = set_rho0;
+  A.stages = c->stages;
+  A.stage_bytes_max = c->stage_bytes;
+  A.pad = 0;
+  A.wait_limit_ns = 2000000000ull;  // 2 s
+  PassKernel k = pick_kernel(c, red);
+  if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    CU(cudaEventRecord(e0, c->stream));
+  }
+  k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
+  CHECK_LAUNCH();
+  ++c->launches;
+  if (c->timing) {
+    CU(cudaEventRecord(e1, c->stream));
+    c->ev_pending.push_back(std::make_pair(e0, e1));
+  }
+  if (write) c->parity ^= 1;
+  return CL_OK;
+}
+
+int red_for_step(const cl_ctx* c) { return c->p.expansion == CL_EXP_SELF ? 1 : 0; }
+
+cl_status close_stream(cl_ctx* c) {
+  if (!c->open) return CL_OK;
+  cl_status s = run_pass(c, 0.5 * c->dprev, 0.5 * c->dprev, 0.0, 0.0, 2, 1, 0);
+  if (s != CL_OK) return s;
+  c->open = false;
+  c->obs_valid = true;
+  return CL_OK;
+}
+
+cl_status measure(cl_ctx* c, int set_rho0) {
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  if (!c->obs_valid || set_rho0) {
+    s = run_pass(c, 0.0, 0.0, 0.0, 0.0, 2, 0, set_rho0);
+    if (s != CL_OK) return s;
+    c->obs_valid = true;
+  }
+  return CL_OK;
+}
+
+cl_status check_status(cl_ctx* c) {
+  int st = 0;
+  CU(cudaMemcpyAsync(&st, &c->d_sc->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (st == CL_ETIMEOUT) return fail(c, CL_ETIMEOUT, "a bounded device wait timed out");
+  return CL_OK;
+}
+
+// Work list: the YT*N plane tasks (y-tile major) are cut into `grid` equal
+// runs, one per CTA; a run is split into segments at y-tile boundaries.  Odd
+// CTAs march down so that neighbouring runs reach their shared boundary
+// plane at the same time (halo planes then come from L2).
+void build_worklist(int N, int BY, int grid, int lat, int seg_offset, std::vector<Seg>& segs,
+                    std::vector<int>& cta_first, std::vector<int>& cta_count) {
+  const long long YT = N / BY, T = YT * N;
+  for (int cta = 0; cta < grid; ++cta) {
+    const long long b = T * cta / grid, e = T * (cta + 1) / grid;
+    const int dir = (cta & 1) ? -1 : +1;
+    cta_first.push_back((int)segs.size() + seg_offset);
+    int cnt = 0;
+    for (long long t = b; t < e;) {
+      const int yt = (int)(t / N), z = (int)(t % N);
+      const int len = (int)std::min<long long>(e - t, N - z);
+      Seg s;
+      s.lat = lat;
+      s.ytile = yt;
+      s.z0 = z;
+      s.nz = len;
+      s.dir = dir;
+      s.pad = 0;
+      segs.push_back(s);
+      ++cnt;
+      t += len;
+    }
+    if (dir < 0) std::reverse(segs.end() - cnt, segs.end());
+    cta_count.push_back(cnt);
+  }
+}
+
+}  // namespace
+
+namespace clg {
+// Small scalar kernels (host-side setup lives here to keep the ABI in one unit).
+__global__ void set_scalars_kernel(const LatConst* Lc, LatScalars* S, double eta, double a, double b) {
+  if (threadIdx.x | blockIdx.x) return;
+  const double al = Lc->alpha;
+  S->eta = eta;
+  S->a = a;
+  S->b = b;
+  S->cd = S->cdA = 0.0;
+  S->apow1 = pow(a, 1.0 + al);
+  S->apow3 = pow(a, 3.0 + al);
+  S->apowm1 = pow(a, al - 1.0);
+}
+
+// a' from the Hubble law (eq. NewFriedmannEQsI) with the measured averages.
+__global__ void b_from_obs_kernel(const LatConst* Lc, LatScalars* S) {
+  if (threadIdx.x | blockIdx.x) return;
+  const double r = pow(S->a, 2.0 * Lc->alpha + 2.0) / 3.0 * Lc->fm2 * S->obs.rho;
+  S->b = r > 0.0 ? sqrt(r) : 0.0;
+}
+}  // namespace clg
+
+extern "C" {
+
+const char* cl_last_error(const cl_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+int cl_nfields(const cl_ctx* c) { return c ? c->narr / 2 : -1; }
+
+int64_t cl_kernel_launches(const cl_ctx* c) { return c ? (int64_t)c->launches : -1; }
+
+cl_status cl_free(cl_ctx* c) {
+  if (!c) return CL_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& pr : c->ev_pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  cudaFree(c->slab);
+  cudaFree(c->d_lat);
+  cudaFree(c->d_sc);
+  cudaFree(c->d_segs);
+  cudaFree(c->d_cta);
+  cudaFree(c->d_part);
+  cudaFree(c->d_cnt);
+  cudaFree(c->d_tmp);
+  cudaFree(c->d_cplx);
+  cudaFree(c->d_spec);
+  delete c;
+  return CL_OK;
+}
+
+static cl_status init_impl(cl_ctx* c, uint64_t seed);
+
+cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
+                  const cl_params* p) {
+  if (!out) return fail(nullptr, CL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, CL_EINVAL, "params is NULL");
+  if (model < CL_MODEL_LPHI4 || model > CL_MODEL_U1_HIGGS)
+    return fail(nullptr, CL_EINVAL, "unknown model %d", model);
+  if (!good_N(N)) return fail(nullptr, CL_EINVAL, "N=%d: need 8 <= N <= 512, N %% 8 == 0, factors 2,3", N);
+  if (!(kIR > 0.0) || !std::isfinite(alpha)) return fail(nullptr, CL_EINVAL, "bad kIR/alpha");
+  if (p->precision != CL_FP64 && p->precision != CL_FP32)
+    return fail(nullptr, CL_EINVAL, "unknown precision %d", p->precision);
+  const int ig = p->integrator;
+  if (!(ig == CL_LF || ig == CL_VV2 || ig == CL_VV4 || ig == CL_VV6 || ig == CL_VV8 || ig == CL_VV10))
+    return fail(nullptr, CL_EINVAL, "unknown integrator %d", ig);
+  if (p->expansion < CL_EXP_OFF || p->expansion > CL_EXP_FIXED)
+    return fail(nullptr, CL_EINVAL, "unknown expansion mode %d", p->expansion);
+  if (!(p->dt == p->dt)) return fail(nullptr, CL_EINVAL, "dt is NaN");
+  cl_ctx* c = new cl_ctx();
+  c->model = model;
+  c->N = N;
+  c->V = (long long)N * N * N;
+  c->nf = model == CL_MODEL_LPHI4 ? 1 : 2;
+  c->narr = model == CL_MODEL_U1_HIGGS ? 10 : 2 * c->nf;
+  c->fp32 = p->precision == CL_FP32;
+  c->esz = c->fp32 ? 4 : 8;
+  c->kIR = kIR;
+  c->dx = 2.0 * M_PI / ((double)N * kIR);
+  c->alpha = alpha;
+  c->p = *p;
+  c->stream = (cudaStream_t)p->stream;
+  cl_status s = init_impl(c, seed);
+  if (s != CL_OK) {
+    g_init_err = c->err;
+    cl_free(c);
+    return s;
+  }
+  *out = c;
+  return CL_OK;
+}
+
+static cl_status init_impl(cl_ctx* c, uint64_t seed) {
+  CU(cudaGetDevice(&c->dev));
+  CU(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
+  int optin = 0;
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+  c->smem_optin = (size_t)optin;
+  const int N = c->N;
+  // tile shape: full x-rows of N/VX threads, BY rows per CTA (BY divides N)
+  const int VX = 16 / c->esz;
+  const int TX = N / VX;
+  int BY = 0;
+  for (int by = std::min(N, THREADS / TX); by >= 1; --by)
+    if (N % by == 0) { BY = by; break; }
+  if (BY == 0) return fail(c, CL_EUNSUPPORTED, "no tile shape for N=%d", N);
+  const int narr_pass = c->narr;
+  const size_t stage = ((size_t)(BY + 2) * N * narr_pass * c->esz + 127) / 128 * 128;
+  const size_t extra = 8 * 8 + 33 * NQ * 8 + 64;
+  int S = (int)std::min<size_t>(4, (c->smem_optin - extra) / stage);
+  if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for N=%d", N);
+  c->stages = S;
+  c->stage_bytes = (unsigned)stage;
+  c->smem_bytes = (size_t)S * stage + extra;
+  for (int red = 0; red < 3; ++red) {
+    PassKernel k = pick_kernel(c, red);
+    if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
+    CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)c->smem_bytes));
+  }
+  // work list
+  const long long tasks = (long long)(N / BY) * N;
+  c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
+  std::vector<Seg> segs;
+  std::vector<int> first, count;
+  build_worklist(N, BY, c->grid, 0, 0, segs, first, count);
+  std::vector<int> cta(c->grid + 1);
+  for (int i = 0; i < c->grid; ++i) cta[i] = first[i];
+  cta[c->grid] = (int)segs.size();
+  c->nseg = (int)segs.size();
+  // device memory
+  const size_t arr_bytes = (size_t)c->V * c->esz;
+  CU(cudaMalloc(&c->slab, 2 * (size_t)c->narr * arr_bytes));
+  CU(cudaMemsetAsync(c->slab, 0, 2 * (size_t)c->narr * arr_bytes, c->stream));
+  CU(cudaMalloc(&c->d_lat, sizeof(LatConst)));
+  CU(cudaMalloc(&c->d_sc, sizeof(LatScalars)));
+  CU(cudaMemsetAsync(c->d_sc, 0, sizeof(LatScalars), c->stream));
+  CU(cudaMalloc(&c->d_segs, segs.size() * sizeof(Seg)));
+  CU(cudaMalloc(&c->d_cta, cta.size() * sizeof(int)));
+  CU(cudaMalloc(&c->d_part, (size_t)c->nseg * NQ * sizeof(double)));
+  CU(cudaMalloc(&c->d_cnt, sizeof(unsigned)));
+  CU(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned), c->stream));
+  LatConst& L = c->hlat;
+  memset(&L, 0, sizeof(L));
+  L.N = N;
+  L.BY = BY;
+  L.YT = N / BY;
+  L.model = c->model;
+  L.nf = c->nf;
+  L.narr = c->narr;
+  L.expansion = c->p.expansion;
+  L.seg_begin = 0;
+  L.seg_end = c->nseg;
+  L.esz = c->esz;
+  L.V = c->V;
+  L.dx = c->dx;
+  L.alpha = c->alpha;
+  L.q = c->p.q;
+  L.lam = c->p.lam;
+  L.v = c->p.v;
+  L.gQ = c->p.gQ;
+  L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
+  L.omega_eos = c->p.omega_eos;
+  for (int par = 0; par < 2; ++par)
+    for (int a = 0; a < c->narr; ++a) L.buf[par][a] = arr_ptr(c, par, a);
+  CU(cudaMemcpyAsync(c->d_lat, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  // initial conditions
+  ICArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int k = 0; k < 4; ++k) {
+    A.phi0[k] = c->p.phi0[k];
+    A.dphi0[k] = c->p.dphi0[k];
+  }
+  A.amp2 = c->p.fluct_amp2;
+  A.kcut = c->p.kcut;
+  A.kIR = c->kIR;
+  A.H0 = c->p.H0;
+  A.q = c->p.q;
+  A.lam = c->p.lam;
+  A.v = c->p.v;
+  A.seed = seed;
+  A.model = c->model;
+  A.nf = c->nf;
+  CU(launch_init_scalars(c->d_lat, c->d_sc, A, c->stream));
+  ++c->launches;
+  CU(cudaMalloc(&c->d_cplx, 2 * (size_t)c->V * sizeof(double2)));
+  CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)c->V, 1 << 16) * sizeof(double)));
+  double2* F = c->d_cplx;
+  double2* G = c->d_cplx + c->V;
+  for (int f = 0; f < c->nf; ++f) {
+    CU(cudaMemsetAsync(c->d_cplx, 0, 2 * (size_t)c->V * sizeof(double2), c->stream));
+    CU(launch_ic_modes(F, G, c->d_lat, c->d_sc, A, f, c->V, c->stream));
+    ++c->launches;
+    cl_status s = fft3d(c, F, +1);
+    if (s != CL_OK) return s;
+    s = fft3d(c, G, +1);
+    if (s != CL_OK) return s;
+    CU(launch_ic_assemble(c->fp32, arr_ptr(c, 0, 2 * f), arr_ptr(c, 0, 2 * f + 1), F, G, c->d_lat,
+                          c->d_sc, c->p.phi0[f], c->p.dphi0[f], c->V, c->stream));
+    ++c->launches;
+  }
+  if (c->model == CL_MODEL_U1_HIGGS) {
+    // links start at zero (eq. Inflc1); their momenta solve the lattice Gauss law
+    double2* rho = c->d_cplx;
+    double2* E = c->d_cplx + c->V;
+    CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, 0, c->dx, c->fp32, nullptr, c->V, 0, c->stream));
+    ++c->launches;
+    cl_status s = fft3d(c, rho, -1);
+    if (s != CL_OK) return s;
+    for (int i = 0; i < 3; ++i) {
+      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, c->dx, c->fp32, nullptr, c->V, 1, c->stream));
+      ++c->launches;
+      s = fft3d(c, E, +1);
+      if (s != CL_OK) return s;
+      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, c->dx, c->fp32, arr_ptr(c, 0, 2 * (2 + i) + 1),
+                              c->V, 2, c->stream));
+      ++c->launches;
+    }
+  }
+  c->parity = 0;
+  c->open = false;
+  cl_status s = measure(c, 1);
+  if (s != CL_OK) return s;
+  if (c->p.expansion == CL_EXP_SELF && c->p.b0_mode == 1) {
+    b_from_obs_kernel<<<1, 32, 0, c->stream>>>(c->d_lat, c->d_sc);
+    CHECK_LAUNCH();
+    ++c->launches;
+    c->obs_valid = false;
+    s = measure(c, 1);
+    if (s != CL_OK) return s;
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+cl_status cl_step_h(cl_ctx* c, int n, double h) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (n < 0 || !std::isfinite(h)) return fail(c, CL_EINVAL, "bad n/h");
+  if (n == 0) return CL_OK;
+  std::vector<double> d1;
+  schedule(c->p.integrator == CL_LF ? 2 : c->p.integrator, h, d1);
+  const int red = red_for_step(c);
+  for (int s = 0; s < n; ++s)
+    for (double d : d1) {
+      cl_status st;
+      if (!c->open) {
+        st = run_pass(c, 0.5 * d, 0.0, 0.5 * d, d, red, 1, 0);
+        c->open = true;
+      } else {
+        st = run_pass(c, 0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d, red, 1, 0);
+      }
+      if (st != CL_OK) return st;
+      c->dprev = d;
+    }
+  c->obs_valid = false;
+  return CL_OK;
+}
+
+cl_status cl_step(cl_ctx* c, int n) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  return cl_step_h(c, n, c->p.dt);
+}
+
+cl_status cl_sync(cl_ctx* c) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  return close_stream(c);
+}
+
+cl_status cl_energies(cl_ctx* c, cl_energies_t* out) {
+  if (!c || !out) return fail(c, CL_EINVAL, "NULL argument");
+  cl_status s = measure(c, 0);
+  if (s != CL_OK) return s;
+  CU(cudaMemcpyAsync(out, &c->d_sc->obs, sizeof(cl_energies_t), cudaMemcpyDeviceToHost, c->stream));
+  s = check_status(c);
+  if (s != CL_OK) return s;
+  if (out->nonfinite > 0) return fail(c, CL_ENONFINITE, "%lld non-finite momenta", (long long)out->nonfinite);
+  return CL_OK;
+}
+
+static cl_status array_index(cl_ctx* c, int field, int what, int* a) {
+  if (what != 0 && what != 1) return fail(c, CL_EINVAL, "what must be 0 or 1");
+  if (field < 0 || field >= c->narr / 2) return fail(c, CL_EINVAL, "field %d out of range", field);
+  *a = 2 * field + what;
+  return CL_OK;
+}
+
+cl_status cl_get_state(cl_ctx* c, int field, int what, double* host_out) {
+  if (!c || !host_out) return fail(c, CL_EINVAL, "NULL argument");
+  int a;
+  cl_status s = array_index(c, field, what, &a);
+  if (s != CL_OK) return s;
+  s = close_stream(c);
+  if (s != CL_OK) return s;
+  CU(launch_convert(c->fp32, 1, arr_ptr(c, c->parity, a), c->d_tmp, c->V, c->stream));
+  ++c->launches;
+  CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)c->V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+cl_status cl_set_state(cl_ctx* c, int field, int what, const double* host_in) {
+  if (!c || !host_in) return fail(c, CL_EINVAL, "NULL argument");
+  int a;
+  cl_status s = array_index(c, field, what, &a);
+  if (s != CL_OK) return s;
+  s = close_stream(c);
+  if (s != CL_OK) return s;
+  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)c->V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, c->parity, a), c->V, c->stream));
+  ++c->launches;
+  CU(cudaStreamSynchronize(c->stream));
+  c->obs_valid = false;
+  return CL_OK;
+}
+
+cl_status cl_get_scalars(cl_ctx* c, double* eta, double* a, double* b) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  double v[3];
+  CU(cudaMemcpyAsync(v, c->d_sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (a) *a = v[0];
+  if (b) *b = v[1];
+  if (eta) *eta = v[2];
+  return check_status(c);
+}
+
+cl_status cl_set_scalars(cl_ctx* c, double eta, double a, double b) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (!(a > 0.0)) return fail(c, CL_EINVAL, "a must be positive");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  set_scalars_kernel<<<1, 32, 0, c->stream>>>(c->d_lat, c->d_sc, eta, a, b);
+  CHECK_LAUNCH();
+  ++c->launches;
+  c->obs_valid = false;
+  s = measure(c, 1);
+  if (s != CL_OK) return s;
+  CU(cudaStreamSynchronize(c->stream));
+  return check_status(c);
+}
+
+cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, double* delta,
+                      int64_t* mult, int cap, int* nbins) {
+  if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+  if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
+  int a;
+  cl_status s = array_index(c, field, what, &a);
+  if (s != CL_OK) return s;
+  const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  *nbins = nb;
+  if (nb > cap) return fail(c, CL_EINVAL, "cap %d < %d bins", cap, nb);
+  if (nb > 2048) return fail(c, CL_EINVAL, "too many bins (dk_bin too small)");
+  s = close_stream(c);
+  if (s != CL_OK) return s;
+  double2* F = c->d_cplx;
+  CU(launch_to_complex(c->fp32, arr_ptr(c, c->parity, a), F, c->V, c->stream));
+  ++c->launches;
+  s = fft3d(c, F, -1);
+  if (s != CL_OK) return s;
+  const int nblk = 2 * c->nsm;
+  if (!c->d_spec) CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + 3 * 2048) * sizeof(double)));
+  double* part = c->d_spec;
+  double* outb = c->d_spec + (size_t)3 * 2048 * nblk;
+  CU(launch_bins(F, c->N, dk_bin, nb, nblk, part, c->kIR, c->dx, outb, c->stream));
+  c->launches += 2;
+  std::vector<double> h(3 * nb);
+  CU(cudaMemcpyAsync(h.data(), outb, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < nb; ++b) {
+    k[b] = h[b];
+    delta[b] = h[nb + b];
+    mult[b] = (int64_t)h[2 * nb + b];
+  }
+  return check_status(c);
+}
+
+cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
+                              double* max_abs) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (c->model != CL_MODEL_U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "model has no gauge field");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  const int nblk = 2 * c->nsm;
+  double* part = c->d_tmp;
+  CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->V, c->stream));
+  c->launches += 2;
+  double h[4];
+  CU(cudaMemcpyAsync(h, part + 3 * nblk, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (rel) *rel = h[0];
+  if (lhs_abs) *lhs_abs = h[1];
+  if (rhs_abs) *rhs_abs = h[2];
+  if (max_abs) *max_abs = h[3];
+  return check_status(c);
+}
+
+cl_status cl_state_bytes(cl_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(c, CL_EINVAL, "NULL argument");
+  *bytes = (size_t)c->narr * c->V * c->esz;
+  return CL_OK;
+}
+
+cl_status cl_upload_state(cl_ctx* c, const void* host, size_t bytes) {
+  if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
+  if (bytes != (size_t)c->narr * c->V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  const size_t ab = (size_t)c->V * c->esz;
+  for (int a = 0; a < c->narr; ++a)
+    CU(cudaMemcpyAsync(arr_ptr(c, c->parity, a), (const char*)host + a * ab, ab, cudaMemcpyHostToDevice, c->stream));
+  c->obs_valid = false;
+  return CL_OK;
+}
+
+cl_status cl_download_state(cl_ctx* c, void* host, size_t bytes) {
+  if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
+  if (bytes != (size_t)c->narr * c->V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  const size_t ab = (size_t)c->V * c->esz;
+  for (int a = 0; a < c->narr; ++a)
+    CU(cudaMemcpyAsync((char*)host + a * ab, arr_ptr(c, c->parity, a), ab, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return CL_OK;
+}
+
+cl_status cl_enable_pass_timing(cl_ctx* c, int enable) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  c->timing = enable != 0;
+  return CL_OK;
+}
+
+cl_status cl_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  CU(cudaStreamSynchronize(c->stream));
+  for (auto& pr : c->ev_pending) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    c->timing_ms += ms;
+    c->timing_passes += 1;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  c->ev_pending.clear();
+  if (ms_total) *ms_total = c->timing_ms;
+  if (passes) *passes = c->timing_passes;
+  if (reset) {
+    c->timing_ms = 0.0;
+    c->timing_passes = 0;
+  }
+  return CL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// common.cuh -- device-side structures and PTX helpers shared by the kernels
+// of the lattice kick-drift library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cl.h"
+
+namespace clg {
+
+constexpr int NQ = 16;       // partial-sum slots per work segment
+constexpr int MAX_ARR = 10;  // lattice arrays per buffer (U(1): 5 fields + 5 momenta)
+constexpr int THREADS = 512; // threads per DK-pass CTA
+
+// Per-lattice constants, read-only during a pass.
+struct LatConst {
+  int N, BY, YT, model, nf, narr, expansion, seg_begin, seg_end, esz;
+  long long V;
+  double dx, alpha, q, lam, v, gQ, fo2, fm2, omega_eos;
+  void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
+};
+
+// Per-lattice evolving scalars (device resident, FP64).
+struct LatScalars {
+  double a, b, eta;
+  double cd, cdA;                 // drift coefficients for the next pass (fields, links)
+  double apow1, apow3, apowm1;    // a^{1+alpha}, a^{3+alpha}, a^{alpha-1} at the current a
+  double a0, eta0, Hfix, rho0;
+  cl_energies_t obs;              // last measurement
+  int status, pad;
+};
+
+// One work segment: planes [z0, z0+nz) of y-tile `ytile` of lattice `lat`,
+// marched in direction dir (+1 up, -1 down).
+struct Seg {
+  int lat, ytile, z0, nz, dir, pad;
+};
+
+struct PassArgs {
+  const LatConst* lat;
+  LatScalars* sc;
+  const Seg* segs;
+  const int* cta_seg;        // [gridDim.x + 1]
+  double* partials;          // [nseg][NQ]
+  unsigned* counters;        // [nlat]
+  double ck, wout, win, dnext;
+  int parity, write, set_rho0, stages;
+  unsigned stage_bytes_max;  // bytes of one stage (max over lattices)
+  unsigned pad;
+  unsigned long long wait_limit_ns;  // bound of every mbarrier wait
+};
+
+// Initial-condition parameters (program units).
+struct ICArgs {
+  double phi0[4], dphi0[4];
+  double amp2, kcut, kIR, H0, q, lam, v;
+  unsigned long long seed;
+  int model, nf;
+};
+
+// One batched 1-D FFT along `axis` of an N^3 complex array.
+struct FftPlan {
+  int N, nrad, axis, sign;
+  int rad[16];
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk async copy (TMA, 1-D) helpers, inline PTX.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up (returns false) after `limit_ns`
+// nanoseconds or 2^30 unsuccessful try_wait rounds, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 0; i < (1u << 30); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+// 16-byte vector of T
+template <typename T> struct V16;
+template <> struct V16<float> { typedef float4 type; static constexpr int n = 4; };
+template <> struct V16<double> { typedef double2 type; static constexpr int n = 2; };
+
+// Kahan-compensated accumulator (FP32 storage path) / plain (FP64 path).
+template <typename T> struct Acc {
+  T s, c;
+  __device__ __forceinline__ void zero() { s = 0; c = 0; }
+  __device__ __forceinline__ void add(T x) {
+    T y = x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct Acc<double> {
+  double s;
+  __device__ __forceinline__ void zero() { s = 0; }
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+}  // namespace clg

@@ -1,0 +1,431 @@
+// ic_fft.cu -- initial conditions, 3-D FFT and binned power spectra, all on
+// the GPU (outside the timed evolution loop).
+//
+// Initial conditions (CosmoLattice manual Sec. 3.5.1, eqs. fpr_influct,
+// fpr_influct2, QuantumFlucts2; Sec. 4.4.1 eqs. InConstr:1-2 for the charged
+// field): in Fourier space each mode gets two left/right moving waves with
+// Rayleigh amplitudes (<|d|^2> = P) and uniform phases,
+//   P = (omega_s/f_s)^2 (N/dx)^3 / (2 a^2 omega_k),  omega_k = sqrt(k^2 + a^2 m^2),
+// drawn from the counter-based generator Philox4x32-10 (Salmon et al., SC'11)
+// keyed by the seed, with counter (Fourier index, field, draw, 0).  Only the
+// member of each (n, -n) pair with the smaller index is drawn; its partner is
+// the complex conjugate so that the field is real.
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace clg {
+
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10: 10 rounds of (two 32x32 -> 64 bit products, xor with the
+// other words and the round key), key advanced by the Weyl constants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// (0, 1] with 53 bits: top 27 bits of the first word, top 26 of the second.
+__device__ __forceinline__ double unit_open0(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = ((unsigned long long)(hi >> 5) << 26) | (unsigned long long)(lo >> 6);
+  return ((double)m + 1.0) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ void draw_pair(unsigned long long seed, unsigned idx, int f, int j,
+                                          double& u0, double& u1) {
+  uint32_t c[4] = {idx, (uint32_t)f, (uint32_t)j, 0u};
+  philox4x32_10(c, (uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+  u0 = unit_open0(c[0], c[1]);
+  u1 = unit_open0(c[2], c[3]);
+}
+
+// Potential of each model at homogeneous values, and d^2V/dphi_f^2 (the
+// initial effective masses of eq. QuantumFlucts2).
+__device__ double pot_hom(const ICArgs& A) {
+  const double* f = A.phi0;
+  if (A.model == CL_MODEL_LPHI4) return 0.25 * f[0] * f[0] * f[0] * f[0];
+  if (A.model == CL_MODEL_LPHI4_CHI)
+    return 0.25 * f[0] * f[0] * f[0] * f[0] + 0.5 * A.q * f[0] * f[0] * f[1] * f[1];
+  const double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]) - A.v * A.v;
+  return A.lam * m2 * m2;
+}
+
+__device__ double mass2_hom(const ICArgs& A, int k) {
+  const double* f = A.phi0;
+  if (A.model == CL_MODEL_LPHI4) return 3.0 * f[0] * f[0];
+  if (A.model == CL_MODEL_LPHI4_CHI)
+    return k == 0 ? 3.0 * f[0] * f[0] + A.q * f[1] * f[1] : A.q * f[0] * f[0];
+  const double r2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
+  return 2.0 * A.lam * (r2 - A.v * A.v) + 2.0 * A.lam * f[k] * f[k];
+}
+
+// Scale factor and b = a' at t0 (ScalarFactorInitializer: homogeneous values).
+__global__ void init_scalars_kernel(const LatConst* Lc, LatScalars* Sc, const ICArgs A) {
+  if (threadIdx.x | blockIdx.x) return;
+  const LatConst& L = *Lc;
+  LatScalars& S = *Sc;
+  const double al = L.alpha;
+  S.a = S.a0 = 1.0;
+  S.eta = S.eta0 = 0.0;
+  S.cd = S.cdA = 0.0;
+  S.apow1 = S.apow3 = S.apowm1 = 1.0;
+  S.status = 0;
+  S.rho0 = 0.0;
+  double kin = 0.0;
+  for (int k = 0; k < A.nf; ++k) kin += 0.5 * A.dphi0[k] * A.dphi0[k];
+  const double rho = kin / pow(S.a, 2.0 * al) + pot_hom(A);
+  const double r = pow(S.a, 2.0 * al + 2.0) / 3.0 * L.fm2 * rho;
+  const double bh = r > 0.0 ? sqrt(r) : 0.0;
+  if (L.expansion == CL_EXP_SELF) {
+    S.Hfix = 0.0;
+    S.b = bh;
+  } else if (L.expansion == CL_EXP_FIXED) {
+    S.Hfix = A.H0 > 0.0 ? A.H0 : bh / S.a;
+    S.b = S.a * S.Hfix;
+  } else {
+    S.Hfix = 0.0;
+    S.b = 0.0;
+  }
+}
+
+// Fourier modes of the fluctuation of component f (F) and of its derivative (G).
+// Buffers are zeroed by the caller; only drawn modes are written.
+__global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, const LatScalars* Sc,
+                                const ICArgs A, int f) {
+  const LatConst& L = *Lc;
+  const int N = L.N;
+  const long long V = L.V;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= V || idx == 0) return;
+  const int x = (int)(idx % N), y = (int)((idx / N) % N), z = (int)(idx / ((long long)N * N));
+  const int px = x ? N - x : 0, py = y ? N - y : 0, pz = z ? N - z : 0;
+  const long long pid = px + (long long)N * (py + (long long)N * pz);
+  if (pid < idx) return;
+  const bool selfc = pid == idx;
+  const bool charged = A.model == CL_MODEL_U1_HIGGS;
+  if (selfc && charged) return;  // keeps the charge density's zero mode at 0
+  const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+  const double k = A.kIR * sqrt((double)(nx * nx + ny * ny + nz * nz));
+  if (A.kcut >= 0.0 && k > A.kcut) return;
+  if (A.amp2 <= 0.0) return;
+  const double a = Sc->a, al = L.alpha;
+  // every component must have a real frequency for the mode to be populated
+  double om[2] = {0.0, 0.0};
+  for (int c = 0; c < A.nf; ++c) {
+    const double w2 = k * k + a * a * mass2_hom(A, c);
+    if (w2 <= 0.0) return;
+    om[c] = sqrt(w2);
+  }
+  const double vol = (double)N / L.dx;
+  const double P = A.amp2 * vol * vol * vol / (2.0 * a * a * om[f]);
+  double r1, r2, t1, t2;
+  if (!charged) {
+    double u0, u1, v0, v1;
+    draw_pair(A.seed, (unsigned)idx, f, 0, u0, u1);
+    draw_pair(A.seed, (unsigned)idx, f, 1, v0, v1);
+    r1 = sqrt(-P * log(u0));
+    r2 = sqrt(-P * log(u1));
+    t1 = 2.0 * v0;  // phases in units of pi
+    t2 = 2.0 * v1;
+  } else {
+    // eqs. InConstr:1-2: equal amplitudes per component, theta_12 = theta_02 + theta_11 - theta_01
+    double u0, u1, v0, v1;
+    draw_pair(A.seed, (unsigned)idx, f, 0, u0, u1);
+    r1 = r2 = sqrt(-P * log(u0));
+    draw_pair(A.seed, (unsigned)idx, 0, 1, v0, v1);  // theta_01, theta_02
+    if (f == 0) {
+      t1 = 2.0 * v0;
+      t2 = 2.0 * v1;
+    } else {
+      double w0, w1;
+      draw_pair(A.seed, (unsigned)idx, 1, 1, w0, w1);  // theta_11
+      t1 = 2.0 * w0;
+      t2 = 2.0 * v1 + 2.0 * w0 - 2.0 * v0;
+    }
+  }
+  double s1, c1, s2, c2;
+  sincospi(t1, &s1, &c1);
+  sincospi(t2, &s2, &c2);
+  const double isq2 = 0.70710678118654752440;
+  const double z1r = r1 * c1, z1i = r1 * s1, z2r = r2 * c2, z2i = r2 * s2;
+  double fr = (z1r + z2r) * isq2, fi = (z1i + z2i) * isq2;
+  // derivative: a^{alpha-1} i omega (z1 - z2)/sqrt2 - H dphi, H = b/a
+  const double pre = pow(a, al - 1.0) * om[f] * isq2;
+  const double H = Sc->b / a;
+  double gr = -pre * (z1i - z2i) - H * fr;
+  double gi = pre * (z1r - z2r) - H * fi;
+  if (selfc) {
+    fi = 0.0;
+    gi = 0.0;
+  }
+  F[idx] = make_double2(fr, fi);
+  G[idx] = make_double2(gr, gi);
+  F[pid] = make_double2(fr, -fi);
+  G[pid] = make_double2(gr, -gi);
+}
+
+// phi = phi0 + Re(F)/V, pi = a^{3-alpha} (phi0' + Re(G)/V), stored in T.
+template <typename T>
+__global__ void ic_assemble_kernel(T* phi, T* pi, const double2* F, const double2* G,
+                                   const LatConst* Lc, const LatScalars* Sc, double phi0,
+                                   double dphi0) {
+  const long long V = Lc->V;
+  const double invV = 1.0 / (double)V;
+  const double a3 = pow(Sc->a, 3.0 - Lc->alpha);
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    phi[n] = (T)(phi0 + F[n].x * invV);
+    pi[n] = (T)(a3 * (dphi0 + G[n].x * invV));
+  }
+}
+template __global__ void ic_assemble_kernel<float>(float*, float*, const double2*, const double2*,
+                                                   const LatConst*, const LatScalars*, double, double);
+template __global__ void ic_assemble_kernel<double>(double*, double*, const double2*, const double2*,
+                                                    const LatConst*, const LatScalars*, double,
+                                                    double);
+
+// ---------------------------------------------------------------------------
+// 3-D FFT: batched 1-D transforms along one axis, one CTA per line, self
+// sorting Stockham passes of radix 4, 2 and 3 in shared memory.  Stage with
+// radix R after sub-length Ns: for j < N/R, k = j mod Ns,
+//   v_r = x[j + r N/R] w^{k r},  w = exp(sign 2 pi i/(Ns R)),
+//   y[(j/Ns) Ns R + k + q Ns] = sum_r v_r exp(sign 2 pi i r q / R).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
+  extern __shared__ double2 fbuf[];
+  const int N = plan.N;
+  double2* a = fbuf;
+  double2* b = fbuf + N;
+  const long long line = blockIdx.x;
+  const long long u = line % N, w = line / N;
+  long long base, stride;
+  if (plan.axis == 0) {
+    base = (long long)N * (u + (long long)N * w);
+    stride = 1;
+  } else if (plan.axis == 1) {
+    base = u + (long long)N * N * w;
+    stride = N;
+  } else {
+    base = u + (long long)N * w;
+    stride = (long long)N * N;
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = data[base + j * stride];
+  __syncthreads();
+  int Ns = 1;
+  for (int s = 0; s < plan.nrad; ++s) {
+    const int R = plan.rad[s];
+    const int NR = N / R;
+    const int L = Ns * R;
+    for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+      const int k = j % Ns;
+      double2 v[4];
+      for (int r = 0; r < R; ++r) {
+        double2 x = a[j + r * NR];
+        if (k != 0 && r != 0) {
+          const int e = (k * r) % L;
+          double sn, cs;
+          sincospi(2.0 * (double)e / (double)L, &sn, &cs);
+          x = cmul(x, make_double2(cs, plan.sign * sn));
+        }
+        v[r] = x;
+      }
+      double2 o[4];
+      if (R == 2) {
+        o[0] = make_double2(v[0].x + v[1].x, v[0].y + v[1].y);
+        o[1] = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+      } else if (R == 4) {
+        // j = sign * i
+        const double2 t0 = make_double2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const double2 t1 = make_double2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const double2 t2 = make_double2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const double2 d = make_double2(v[1].x - v[3].x, v[1].y - v[3].y);
+        const double2 t3 = make_double2(-plan.sign * d.y, plan.sign * d.x);  // j*(v1 - v3)
+        o[0] = make_double2(t0.x + t2.x, t0.y + t2.y);
+        o[1] = make_double2(t1.x + t3.x, t1.y + t3.y);
+        o[2] = make_double2(t0.x - t2.x, t0.y - t2.y);
+        o[3] = make_double2(t1.x - t3.x, t1.y - t3.y);
+      } else {  // R == 3, w = (-1/2, sign sqrt3/2)
+        const double h = 0.86602540378443864676 * plan.sign;
+        const double2 s = make_double2(v[1].x + v[2].x, v[1].y + v[2].y);
+        const double2 d = make_double2(v[1].x - v[2].x, v[1].y - v[2].y);
+        const double2 m = make_double2(v[0].x - 0.5 * s.x, v[0].y - 0.5 * s.y);
+        o[0] = make_double2(v[0].x + s.x, v[0].y + s.y);
+        o[1] = make_double2(m.x - h * d.y, m.y + h * d.x);
+        o[2] = make_double2(m.x + h * d.y, m.y - h * d.x);
+      }
+      const int idxD = (j / Ns) * L + k;
+      for (int q2 = 0; q2 < R; ++q2) b[idxD + q2 * Ns] = o[q2];
+    }
+    __syncthreads();
+    double2* t = a;
+    a = b;
+    b = t;
+    Ns = L;
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) data[base + j * stride] = a[j];
+}
+
+template <typename T>
+__global__ void to_complex_kernel(const T* f, double2* out, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x)
+    out[n] = make_double2((double)f[n], 0.0);
+}
+template __global__ void to_complex_kernel<float>(const float*, double2*, long long);
+template __global__ void to_complex_kernel<double>(const double*, double2*, long long);
+
+// Shell binning of |F(n)|^2, bins b = floor(|n|/dk) over n != 0.  Each block
+// accumulates in shared memory and writes its own partial row (3 x nb).
+__global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, double* part) {
+  extern __shared__ double sb[];
+  double* sp = sb;
+  double* sn = sb + nb;
+  double* sc = sb + 2 * nb;
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  const long long V = (long long)N * N * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < V;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (idx == 0) continue;
+    const int x = (int)(idx % N), y = (int)((idx / N) % N), z = (int)(idx / ((long long)N * N));
+    const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+    const double nn = sqrt((double)(nx * nx + ny * ny + nz * nz));
+    int b = (int)floor(nn / dk);
+    if (b >= nb) b = nb - 1;
+    const double2 v = F[idx];
+    atomicAdd(&sp[b], v.x * v.x + v.y * v.y);
+    atomicAdd(&sn[b], nn);
+    atomicAdd(&sc[b], 1.0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 3 * nb + i] = sb[i];
+}
+
+// Sum the block rows in a fixed order and form eq. discretePS per bin.
+__global__ void bin_final_kernel(const double* part, int nblk, int nb, double kIR, double dx, int N,
+                                 double* k, double* delta, double* mult) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double sp = 0.0, sn = 0.0, sc = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    const double* r = part + (size_t)i * 3 * nb;
+    sp += r[b];
+    sn += r[nb + b];
+    sc += r[2 * nb + b];
+  }
+  if (sc == 0.0) {
+    k[b] = 0.0;
+    delta[b] = 0.0;
+    mult[b] = 0.0;
+    return;
+  }
+  const double nbar = sn / sc;
+  const double kb = kIR * nbar;
+  const double fac = pow(dx / (double)N, 3.0);
+  const double pi = 3.14159265358979323846;
+  k[b] = kb;
+  delta[b] = kb * kb * kb / (2.0 * pi * pi) * fac * sp / (4.0 * pi * nbar * nbar);
+  mult[b] = sc;
+}
+
+// FP64 <-> storage conversion for state transfer.
+template <typename T>
+__global__ void convert_to_double_kernel(const T* in, double* out, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x)
+    out[n] = (double)in[n];
+}
+template <typename T>
+__global__ void convert_from_double_kernel(const double* in, T* out, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x)
+    out[n] = (T)in[n];
+}
+template __global__ void convert_to_double_kernel<float>(const float*, double*, long long);
+template __global__ void convert_to_double_kernel<double>(const double*, double*, long long);
+template __global__ void convert_from_double_kernel<float>(const double*, float*, long long);
+template __global__ void convert_from_double_kernel<double>(const double*, double*, long long);
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (the kernels above are launched only through these).
+// ---------------------------------------------------------------------------
+namespace {
+int grid_for(long long n, int tb) { long long b = (n + tb - 1) / tb; return (int)(b < 65536 ? b : 65536); }
+}
+
+cudaError_t launch_init_scalars(const LatConst* L, LatScalars* S, const ICArgs& A, cudaStream_t st) {
+  init_scalars_kernel<<<1, 32, 0, st>>>(L, S, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic_modes(double2* F, double2* G, const LatConst* L, const LatScalars* S,
+                            const ICArgs& A, int f, long long V, cudaStream_t st) {
+  const int tb = 256;
+  ic_modes_kernel<<<(unsigned)((V + tb - 1) / tb), tb, 0, st>>>(F, G, L, S, A, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic_assemble(int fp32, void* phi, void* pi, const double2* F, const double2* G,
+                               const LatConst* L, const LatScalars* S, double phi0, double dphi0,
+                               long long V, cudaStream_t st) {
+  const int tb = 256;
+  if (fp32)
+    ic_assemble_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((float*)phi, (float*)pi, F, G, L, S, phi0, dphi0);
+  else
+    ic_assemble_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((double*)phi, (double*)pi, F, G, L, S, phi0, dphi0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_axis(double2* data, const FftPlan& pl, cudaStream_t st) {
+  const int threads = pl.N / 2 < 32 ? 32 : (pl.N / 2 > 256 ? 256 : pl.N / 2);
+  fft_lines_kernel<<<(unsigned)((long long)pl.N * pl.N), threads, 2 * pl.N * sizeof(double2), st>>>(data, pl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_complex(int fp32, const void* f, double2* out, long long V, cudaStream_t st) {
+  const int tb = 256;
+  if (fp32) to_complex_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const float*)f, out, V);
+  else to_complex_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)f, out, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bins(const double2* F, int N, double dk, int nb, int nblk, double* part,
+                        double kIR, double dx, double* out, cudaStream_t st) {
+  bin_partial_kernel<<<nblk, 256, 3 * nb * sizeof(double), st>>>(F, N, dk, nb, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bin_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, kIR, dx, N, out, out + nb, out + 2 * nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int fp32, int to_double, const void* in, void* out, long long V, cudaStream_t st) {
+  const int tb = 256;
+  if (to_double) {
+    if (fp32) convert_to_double_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const float*)in, (double*)out, V);
+    else convert_to_double_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)in, (double*)out, V);
+  } else {
+    if (fp32) convert_from_double_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const double*)in, (float*)out, V);
+    else convert_from_double_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)in, (double*)out, V);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace clg

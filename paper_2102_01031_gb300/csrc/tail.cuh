@@ -1,0 +1,110 @@
+// tail.cuh -- per-lattice scalar update run by the last CTA of a DK pass:
+// Friedmann kicks of b = a', the next drift coefficient, and the packaging of
+// measured volume averages.  FP64 throughout.
+#pragma once
+
+#include "common.cuh"
+
+namespace clg {
+
+// Energy sums of one pass for one lattice, already summed over the lattice.
+struct PassSums {
+  double EKpre, EKpost, EG, EV;   // normalised energies (pre / post kick)
+  double EKA, EGA;                // U(1) electric (post kick) and magnetic
+  double EKApre;                  // U(1) electric before the kick
+};
+
+__device__ __forceinline__ double fixed_p(const LatConst& L) {
+  return 2.0 / (3.0 * (1.0 + L.omega_eos) - 2.0 * L.alpha);
+}
+
+// Fixed power-law background, eq. ScaleFactorPowerLaw.
+__device__ __forceinline__ double a_fixed(const LatConst& L, const LatScalars& S, double eta) {
+  double p = fixed_p(L);
+  return S.a0 * pow(1.0 + S.Hfix * (eta - S.eta0) / p, p);
+}
+__device__ __forceinline__ double H_fixed(const LatConst& L, const LatScalars& S, double eta) {
+  double p = fixed_p(L);
+  return S.Hfix / (1.0 + S.Hfix * (eta - S.eta0) / p);
+}
+
+// b' = K_a (Sec. 3.5.2 / Sec. 4.3): a^{2alpha+1}/3 (f_s/m_p)^2 [(alpha-2) E_K + alpha E_G
+//        + (alpha-1)(E_K^A + E_G^A) + (alpha+1) E_V]
+__device__ __forceinline__ double kernel_a(const LatConst& L, double a, double EK, double EG,
+                                           double EV, double EKA, double EGA) {
+  const double al = L.alpha;
+  return pow(a, 2.0 * al + 1.0) / 3.0 * L.fm2 *
+         ((al - 2.0) * EK + al * EG + (al - 1.0) * (EKA + EGA) + (al + 1.0) * EV);
+}
+
+// Friedmann kicks of b (kick-out with the pre-kick momenta, then kick-in with
+// the post-kick momenta, as in the velocity-Verlet step), then the drift of a
+// by P.dnext and the drift coefficients of the next pass.
+__device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, LatScalars& S,
+                                       const PassSums& E, bool have_sums) {
+  const double a = S.a;
+  if (have_sums && L.expansion == CL_EXP_SELF) {
+    S.b += P.wout * kernel_a(L, a, E.EKpre, E.EG, E.EV, E.EKApre, E.EGA);
+    S.b += P.win * kernel_a(L, a, E.EKpost, E.EG, E.EV, E.EKA, E.EGA);
+  }
+}
+
+__device__ inline void advance_drift(const PassArgs& P, const LatConst& L, LatScalars& S) {
+  const double a = S.a, al = L.alpha;
+  if (P.dnext != 0.0) {
+    double an;
+    if (L.expansion == CL_EXP_SELF) an = a + P.dnext * S.b;
+    else if (L.expansion == CL_EXP_FIXED) an = a_fixed(L, S, S.eta + P.dnext);
+    else an = a;
+    const double abar = 0.5 * (a + an);
+    S.cd = P.dnext * pow(abar, al - 3.0);
+    S.cdA = P.dnext * pow(abar, al - 1.0);
+    S.a = an;
+    S.eta += P.dnext;
+    if (L.expansion == CL_EXP_FIXED) S.b = an * H_fixed(L, S, S.eta);
+    S.apow1 = pow(an, 1.0 + al);
+    S.apow3 = pow(an, 3.0 + al);
+    S.apowm1 = pow(an, al - 1.0);
+  } else {
+    S.cd = 0.0;
+    S.cdA = 0.0;
+  }
+}
+
+// Hubble-constraint monitor and energy bookkeeping of a measurement.
+__device__ inline void finish_obs(const PassArgs& P, const LatConst& L, LatScalars& S) {
+  cl_energies_t& o = S.obs;
+  double rho = o.EKA + o.EGA;
+  for (int k = 0; k < 4; ++k) rho += o.EK[k] + o.EG[k] + o.EV[k];
+  o.rho = rho;
+  o.hubble_lhs = S.b * S.b;
+  o.hubble_rhs = pow(S.a, 2.0 * L.alpha + 2.0) / 3.0 * L.fm2 * rho;
+  const double den = o.hubble_lhs + o.hubble_rhs;
+  o.hubble_viol = den > 0.0 ? (o.hubble_lhs - o.hubble_rhs) / den : 0.0;
+  if (P.set_rho0) S.rho0 = rho;
+  o.energy_cons = S.rho0 != 0.0 ? 1.0 - rho / S.rho0 : 0.0;
+  o.eta = S.eta;
+  o.a = S.a;
+  o.b = S.b;
+}
+
+// Block-wide FP64 sum of `vals[0..NQ)` over all threads into red[0..NQ).
+__device__ inline void block_reduce_nq(double (&vals)[NQ], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double v = vals[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp * NQ + q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * NQ + threadIdx.x];
+    red[32 * NQ + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+}  // namespace clg
