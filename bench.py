@@ -1,0 +1,352 @@
+"""Throughput of the lattice kick-drift step on GB300.
+
+Workload (one GPU): two scalar fields, V = phi^4/4 + (q/2) phi^2 chi^2 with
+q = 100, 256^3 periodic lattice, kIR = 0.1, alpha = 1, self-consistent
+expansion (f*/m_p = 0.5), Yoshida-4 composition of velocity Verlet (VV4),
+dt = 0.005, vacuum-fluctuation initial conditions from seed 1
+((omega*/f*)^2 = 1e-4).  Headline: fields and momenta stored in FP32 with FP64
+reductions; the plain FP64 path is timed on the same workload beside it.
+
+A step is one full dt of the integrator (three fused drift+kick passes over
+the whole lattice); value = site-updates/s = sites x steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/, FP64, one thread) on a
+bounded sample of the same workload.  Under torchrun (N > 1) every rank
+advances its own independent lattice (replicas, different seeds): there is
+no exchange between ranks on the data path.
+"""
+import argparse
+import hashlib
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s, 2-field φ⁴ 256³: FP32-store vs FP64 plain, % of HBM roofline"
+N_LAT, KIR, ALPHA, SEED = 256, 0.1, 1.0, 1
+PARAMS = dict(dt=0.005, integrator=4, q=100.0, phi0=[1.0, 0.0], fluct_amp2=1e-4, expansion=1,
+              fstar_over_mp=0.5)
+WORKLOAD = ("lphi4+chi q=100, 256^3, kIR=0.1, alpha=1, VV4 dt=0.005, self-consistent expansion, "
+            "vacuum fluctuations (omega*/f*)^2=1e-4 seed 1")
+# bytes one DK pass must move: 2 fields x (field, momentum) x (read + write)
+PASS_BYTES_PER_SITE = {"f32": 2 * 2 * 2 * 4, "f64": 2 * 2 * 2 * 8}
+PASSES_PER_STEP = 3
+# DRAM bytes (read + write) per DK-pass launch from the ncu capture summarised in
+# profiles/dk_pass_fp32_256_ncu.md, valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {"f32": {"source_hash": "2f62b055c964d9a5", "bytes_per_launch": 551128832}}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("pass_scalar.cu", "common.cuh", "tail.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per launch of the DK pass from the last ncu capture, or None
+    if the kernel source changed since the capture."""
+    e = NCU_TRAFFIC.get(prec)
+    if not e or e["source_hash"] != kernel_source_hash():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(budget_s, steps_hint=None):
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    model and lattice spacing on a smaller periodic box; site-updates/s."""
+    import oracle as O
+    sizes = [16, 24, 32, 48, 64, 96, 128]
+    rate_guess = 1.0e6
+    if steps_hint is None:
+        n_ref = 128
+        steps = max(1, int(budget_s * rate_guess / n_ref ** 3))
+    else:
+        steps = steps_hint
+        n_ref = max([s for s in sizes if s ** 3 * steps <= budget_s * rate_guess] or [16])
+    kir = KIR * N_LAT / n_ref   # same dx as the 256^3 workload
+    p = O.make_params(**PARAMS)
+    L = O.Oracle(O.MODEL_LPHI4_CHI, n_ref, kir, ALPHA, SEED, p)
+    return L, n_ref, steps
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O  # noqa: F401
+    budget = 150.0
+    L, n_ref, _ = cpu_oracle_rate(budget, steps_hint=args.steps + args.warmup)
+    for _ in range(args.warmup):
+        L.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.step(1)
+    dt = time.perf_counter() - t0
+    value = n_ref ** 3 * args.steps / dt
+    sample = ("each step: one VV4 step of the same model on a %d^3 periodic box with the 256^3 "
+              "lattice spacing (kIR=%.4g), oracle FP64 single thread" % (n_ref, KIR * N_LAT / n_ref))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded vacuum fluctuations)",
+        "config": {"workload": WORKLOAD, "sample_lattice": n_ref},
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def time_device(P, torch, lat, steps, warmup, rank, ws):
+    """K steps bracketed by barrier + synchronize, CUDA events on the lattice stream."""
+    stream = torch.cuda.current_stream()
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat.pass_timing(reset=True)
+    lat.enable_pass_timing(True)
+    n0 = lat.launches()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lat.enable_pass_timing(False)
+    launches = lat.launches() - n0
+    ms = e0.elapsed_time(e1)
+    pass_ms, npass = lat.pass_timing(reset=True)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, launches, pass_ms / max(npass, 1), npass
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2102_01031_gb300 as P
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    P.build()
+    stream = P.torch_stream()
+    sites = N_LAT ** 3
+    peak, peak_kind = peaks()
+
+    def make(prec, seed):
+        return P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, seed,
+                         P.make_params(precision=prec, stream=stream, **PARAMS))
+
+    results = {}
+    for prec, name in ((P.FP32, "f32"), (P.FP64, "f64")):
+        lat = make(prec, SEED + rank)
+        steps = args.steps if name == "f32" else max(1, min(args.steps, args.fp64_steps))
+        sampler = ClockSampler(local if ws > 1 else 0)
+        if name == "f32":
+            sampler.start()
+        ms, launches, pass_ms, npass = time_device(P, torch, lat, steps, args.warmup, rank, ws)
+        clocks = sampler.stop() if name == "f32" else None
+        e = lat.energies(allow_nonfinite=True)
+        results[name] = dict(ms=ms, steps=steps, launches=launches, pass_ms=pass_ms, npass=npass,
+                             clocks=clocks, rho=e["rho"], a=e["a"], nonfinite=e["nonfinite"])
+        if name == "f32":
+            # end to end through the C ABI: state uploaded from pinned host memory,
+            # one step, energies read back, every step
+            nbytes = lat.state_bytes()
+            host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            lat.download(host.data_ptr(), nbytes)
+            k2 = max(1, min(args.steps, args.e2e_steps))
+            for _ in range(2):
+                lat.upload(host.data_ptr(), nbytes)
+                lat.step(1)
+                lat.energies(allow_nonfinite=True)
+            torch.cuda.synchronize()
+            if ws > 1:
+                torch.distributed.barrier()
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                lat.upload(host.data_ptr(), nbytes)
+                lat.step(1)
+                lat.energies(allow_nonfinite=True)
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
+            if ws > 1:
+                t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                t_e2e = float(t.item())
+            results["e2e"] = dict(value=ws * sites * k2 / t_e2e, h2d=nbytes,
+                                  d2h=ctypes_sizeof_energies(P), steps=k2)
+        lat.close()
+        del lat
+        torch.cuda.synchronize()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    f32, f64 = results["f32"], results["f64"]
+    value = ws * sites * f32["steps"] / (f32["ms"] * 1e-3)
+    v64 = ws * sites * f64["steps"] / (f64["ms"] * 1e-3)
+    bpl = PASS_BYTES_PER_SITE["f32"] * sites
+    achieved = bpl / (f32["pass_ms"] * 1e-3) / 1e9
+    bpl64 = PASS_BYTES_PER_SITE["f64"] * sites
+    achieved64 = bpl64 / (f64["pass_ms"] * 1e-3) / 1e9
+    traffic = ncu_traffic("f32")
+    budget = float(args.cpu_budget)
+    L, n_ref, csteps = cpu_oracle_rate(budget)
+    t0 = time.perf_counter()
+    L.step(csteps)
+    cdt = time.perf_counter() - t0
+    cpu_value = n_ref ** 3 * csteps / cdt
+    line = {
+        "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws,
+        "steps": f32["steps"], "warmup": args.warmup, "ms_per_step": f32["ms"] / f32["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: vacuum-fluctuation initial conditions generated on the GPU from the seed",
+        "config": {"workload": WORKLOAD, "storage": "fp32 fields/momenta, fp64 reductions and a, a'",
+                   "replicas": ws, "sites": sites, "passes_per_step": PASSES_PER_STEP,
+                   "l2": "no flush: each pass streams 537 MB (> 126 MB L2) through ping-pong buffers"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "dk_pass_scalar<float,2,1>", "bytes_per_launch": bpl,
+                     "avg_launch_ms": f32["pass_ms"], "launches_timed": f32["npass"],
+                     "peak_kind": peak_kind},
+        "cpu_baseline": {"value": cpu_value, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d VV4 steps of the same model on a %d^3 box with the same "
+                                   "lattice spacing, oracle FP64 single thread" % (csteps, n_ref)},
+        "e2e": {"value": results["e2e"]["value"], "unit": "site-updates/s",
+                "h2d_bytes_per_step": results["e2e"]["h2d"],
+                "d2h_bytes_per_step": results["e2e"]["d2h"], "steps": results["e2e"]["steps"]},
+        "gpu_launches": f32["launches"],
+        "clocks": f32["clocks"],
+        "fp64_plain": {"value": v64, "unit": "site-updates/s", "steps": f64["steps"],
+                       "ms_per_step": f64["ms"] / f64["steps"], "achieved_gbs": achieved64,
+                       "frac_hbm": achieved64 / peak, "avg_launch_ms": f64["pass_ms"],
+                       "fp32_speedup": value / v64},
+        "sanity": {"rho_f32": f32["rho"], "rho_f64": f64["rho"], "a_f32": f32["a"],
+                   "nonfinite": f32["nonfinite"] + f64["nonfinite"]},
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def ctypes_sizeof_energies(P):
+    import ctypes
+    return ctypes.sizeof(P.Energies)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=1000)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

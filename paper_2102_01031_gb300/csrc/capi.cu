@@ -181,8 +181,14 @@ cl_status run_pass(cl_ctx* c, double ck, double wout, double win, double dnext, 
   if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    for (cudaEvent_t* e : {&e0, &e1}) {
+      if (!c->ev_pool.empty()) {
+        *e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+      } else {
+        CU(cudaEventCreate(e));
+      }
+    }
     CU(cudaEventRecord(e0, c->stream));
   }
   k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
@@ -296,6 +302,7 @@ cl_status cl_free(cl_ctx* c) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   cudaFree(c->slab);
   cudaFree(c->d_lat);
   cudaFree(c->d_sc);
@@ -707,8 +714,8 @@ cl_status cl_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset
     CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
     c->timing_ms += ms;
     c->timing_passes += 1;
-    cudaEventDestroy(pr.first);
-    cudaEventDestroy(pr.second);
+    c->ev_pool.push_back(pr.first);
+    c->ev_pool.push_back(pr.second);
   }
   c->ev_pending.clear();
   if (ms_total) *ms_total = c->timing_ms;
