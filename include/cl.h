@@ -171,6 +171,40 @@ const char* cl_last_error(const cl_ctx* ctx);  /* never NULL; ctx may be NULL */
 cl_status cl_enable_pass_timing(cl_ctx* ctx, int enable);
 cl_status cl_pass_timing(cl_ctx* ctx, double* ms_total, int64_t* passes, int reset);
 
+/* ---------------------------------------------------------------------------
+ * Volume averages without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- programs
+ * that give the library all of their device memory up front (a fixed budget,
+ * or another framework's memory pool) and loops that must not synchronise the
+ * device, which cudaMalloc / cudaFree may do.  It computes, for a scalar-field
+ * state (CL_MODEL_LPHI4 or CL_MODEL_LPHI4_CHI) held in the caller's device
+ * memory, the same volume averages cl_energies reports, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   arrays : host array of 2*nf device pointers {phi_0, pi_0[, phi_1, pi_1]},
+ *            each N^3 values (x fastest) of float (CL_FP32) or double (CL_FP64).
+ *   a      : scale factor of the state; kIR gives dx = 2 pi/(N kIR); q as in
+ *            cl_params (used by CL_MODEL_LPHI4_CHI).
+ *   out    : device pointer to CL_NOALLOC_OUT doubles, written in order
+ *            E_K[2], E_G[2], E_V[2], <phi>[2], <phi^2>[2], <pi>[2], <pi^2>[2],
+ *            rho, count of non-finite momenta (entries of absent fields are 0).
+ *   stream : cudaStream_t the two kernels are enqueued on (asynchronous).
+ *
+ * Partial sums live in one file-scope device array of CL_NOALLOC_MAX_BLOCKS x
+ * CL_NOALLOC_OUT doubles (128 KiB), held by every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address with the device current; make that first call before any
+ * stream capture.  Every call shares the array (each row a call reads is
+ * written earlier in the same call), so calls that overlap on the GPU race.
+ * Returns CL_EINVAL for N > CL_NOALLOC_MAX_N (the no-allocation limit) or bad
+ * arguments, CL_ECUDA if a launch or the address lookup fails. */
+#define CL_NOALLOC_MAX_BLOCKS 1024
+#define CL_NOALLOC_OUT 16
+#define CL_NOALLOC_MAX_N 512
+cl_status cl_volume_averages_noalloc(int model, int N, double kIR, double a, double q,
+                                     int precision, const void* const* arrays, double* out,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

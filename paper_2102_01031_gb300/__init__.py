@@ -31,7 +31,7 @@ EXPORTS = (
     "cl_init", "cl_free", "cl_step", "cl_step_h", "cl_sync", "cl_energies", "cl_gauss_constraint",
     "cl_spectrum", "cl_get_state", "cl_set_state", "cl_get_scalars", "cl_set_scalars",
     "cl_state_bytes", "cl_upload_state", "cl_download_state", "cl_nfields", "cl_kernel_launches",
-    "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing",
+    "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
 )
 
 
@@ -127,6 +127,8 @@ def lib():
     L.cl_last_error.restype = ctypes.c_char_p
     L.cl_enable_pass_timing.argtypes = [vp, ip]
     L.cl_pass_timing.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ip]
+    L.cl_volume_averages_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ip, ctypes.POINTER(vp), vp, vp]
     _lib = L
     return L
 
