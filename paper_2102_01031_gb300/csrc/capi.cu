@@ -63,7 +63,7 @@ struct cl_ctx {
   double2* d_cplx = nullptr;       // scratch complex (2 V)
   double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk) + output
   LatConst hlat;
-  int grid = 0, nseg = 0, stages = 0;
+  int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
   // schedule state
@@ -232,35 +232,73 @@ cl_status check_status(cl_ctx* c) {
   return CL_OK;
 }
 
-// Work list: the YT*N plane tasks (y-tile major) are cut into `grid` equal
-// runs, one per CTA; a run is split into segments at y-tile boundaries.  Odd
-// CTAs march down so that neighbouring runs reach their shared boundary
-// plane at the same time (halo planes then come from L2).
-void build_worklist(int N, int BY, int grid, int lat, int seg_offset, std::vector<Seg>& segs,
-                    std::vector<int>& cta_first, std::vector<int>& cta_count) {
-  const long long YT = N / BY, T = YT * N;
+// Work list.  The plane tasks of all lattices (lattice-major, then y-tile,
+// then z) are cut into `grid` equal contiguous runs, one per CTA; a run is
+// split into segments at y-tile and lattice boundaries.  Odd CTAs march down
+// (and take their segments in reverse order) so that neighbouring runs reach
+// their shared boundary plane at the same time, when halo planes come from L2.
+// Each CTA accumulates one partial-sum slot per lattice it touches; slots are
+// numbered lattice-major so that a lattice's slots are contiguous.
+struct LatTiles {
+  int N, BY;
+};
+
+bool build_worklist(const std::vector<LatTiles>& lats, int grid, std::vector<Seg>& segs,
+                    std::vector<int>& cta_first, std::vector<int>& slot_begin,
+                    std::vector<int>& slot_end) {
+  std::vector<long long> toff(lats.size() + 1, 0);
+  for (size_t l = 0; l < lats.size(); ++l)
+    toff[l + 1] = toff[l] + (long long)(lats[l].N / lats[l].BY) * lats[l].N;
+  const long long T = toff.back();
+  segs.clear();
+  cta_first.assign(grid + 1, 0);
   for (int cta = 0; cta < grid; ++cta) {
     const long long b = T * cta / grid, e = T * (cta + 1) / grid;
     const int dir = (cta & 1) ? -1 : +1;
-    cta_first.push_back((int)segs.size() + seg_offset);
-    int cnt = 0;
+    cta_first[cta] = (int)segs.size();
+    size_t l = 0;
     for (long long t = b; t < e;) {
-      const int yt = (int)(t / N), z = (int)(t % N);
+      while (t >= toff[l + 1]) ++l;
+      const int N = lats[l].N;
+      const long long u = t - toff[l];
+      const int yt = (int)(u / N), z = (int)(u % N);
       const int len = (int)std::min<long long>(e - t, N - z);
-      Seg s;
-      s.lat = lat;
-      s.ytile = yt;
-      s.z0 = z;
-      s.nz = len;
-      s.dir = dir;
-      s.pad = 0;
-      segs.push_back(s);
-      ++cnt;
+      Seg sg;
+      sg.lat = (int)l;
+      sg.ytile = yt;
+      sg.z0 = z;
+      sg.nz = len;
+      sg.dir = dir;
+      sg.slot = -1;
+      sg.flush = 0;
+      sg.pad = 0;
+      segs.push_back(sg);
       t += len;
     }
-    if (dir < 0) std::reverse(segs.end() - cnt, segs.end());
-    cta_count.push_back(cnt);
+    if (dir < 0) std::reverse(segs.begin() + cta_first[cta], segs.end());
+    const int n = (int)segs.size() - cta_first[cta];
+    if (n > MAX_SEG_PER_CTA) return false;
+    for (int i = cta_first[cta]; i < (int)segs.size(); ++i)
+      segs[i].flush = (i + 1 == (int)segs.size() || segs[i + 1].lat != segs[i].lat) ? 1 : 0;
   }
+  cta_first[grid] = (int)segs.size();
+  slot_begin.assign(lats.size(), 0);
+  slot_end.assign(lats.size(), 0);
+  int next = 0;
+  for (size_t l = 0; l < lats.size(); ++l) {
+    slot_begin[l] = next;
+    for (int cta = 0; cta < grid; ++cta) {
+      bool used = false;
+      for (int i = cta_first[cta]; i < cta_first[cta + 1]; ++i)
+        if (segs[i].lat == (int)l) {
+          segs[i].slot = next;
+          used = true;
+        }
+      if (used) ++next;
+    }
+    slot_end[l] = next;
+  }
+  return true;
 }
 
 }  // namespace
@@ -370,13 +408,13 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   const int VX = 16 / c->esz;
   const int TX = N / VX;
   int BY = 0;
-  for (int by = std::min(N, THREADS / TX); by >= 1; --by)
+  for (int by = std::min(N, 32 * CONSUMER_WARPS / TX); by >= 1; --by)
     if (N % by == 0) { BY = by; break; }
   if (BY == 0) return fail(c, CL_EUNSUPPORTED, "no tile shape for N=%d", N);
   const int narr_pass = c->narr;
   const size_t stage = ((size_t)(BY + 2) * N * narr_pass * c->esz + 127) / 128 * 128;
-  const size_t extra = 8 * 8 + 33 * NQ * 8 + 64;
-  int S = (int)std::min<size_t>(4, (c->smem_optin - extra) / stage);
+  const size_t extra = SM_TAIL_BYTES;  // mbarriers, release counts, offsets, sums, flags, copy info
+  int S = (int)std::min<size_t>(6, (c->smem_optin - extra) / stage);
   if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for N=%d", N);
   c->stages = S;
   c->stage_bytes = (unsigned)stage;
@@ -391,12 +429,11 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   const long long tasks = (long long)(N / BY) * N;
   c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
   std::vector<Seg> segs;
-  std::vector<int> first, count;
-  build_worklist(N, BY, c->grid, 0, 0, segs, first, count);
-  std::vector<int> cta(c->grid + 1);
-  for (int i = 0; i < c->grid; ++i) cta[i] = first[i];
-  cta[c->grid] = (int)segs.size();
+  std::vector<int> cta, sbeg, send;
+  if (!build_worklist({LatTiles{N, BY}}, c->grid, segs, cta, sbeg, send))
+    return fail(c, CL_EUNSUPPORTED, "work split needs more than %d segments per CTA", MAX_SEG_PER_CTA);
   c->nseg = (int)segs.size();
+  c->nslot = send[0];
   // device memory
   const size_t arr_bytes = (size_t)c->V * c->esz;
   CU(cudaMalloc(&c->slab, 2 * (size_t)c->narr * arr_bytes));
@@ -406,7 +443,7 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   CU(cudaMemsetAsync(c->d_sc, 0, sizeof(LatScalars), c->stream));
   CU(cudaMalloc(&c->d_segs, segs.size() * sizeof(Seg)));
   CU(cudaMalloc(&c->d_cta, cta.size() * sizeof(int)));
-  CU(cudaMalloc(&c->d_part, (size_t)c->nseg * NQ * sizeof(double)));
+  CU(cudaMalloc(&c->d_part, (size_t)c->nslot * NQ * sizeof(double)));
   CU(cudaMalloc(&c->d_cnt, sizeof(unsigned)));
   CU(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned), c->stream));
   LatConst& L = c->hlat;
@@ -418,9 +455,12 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   L.nf = c->nf;
   L.narr = c->narr;
   L.expansion = c->p.expansion;
-  L.seg_begin = 0;
-  L.seg_end = c->nseg;
+  L.slot_begin = sbeg[0];
+  L.slot_end = send[0];
   L.esz = c->esz;
+  L.int_alpha = (c->alpha == std::floor(c->alpha) && std::fabs(c->alpha) <= 4.0) ? 1 : 0;
+  L.inv_V = 1.0 / (double)c->V;
+  L.inv_dx2 = 1.0 / (c->dx * c->dx);
   L.V = c->V;
   L.dx = c->dx;
   L.alpha = c->alpha;

@@ -11,13 +11,18 @@ namespace clg {
 
 constexpr int NQ = 16;       // partial-sum slots per work segment
 constexpr int MAX_ARR = 10;  // lattice arrays per buffer (U(1): 5 fields + 5 momenta)
-constexpr int THREADS = 512; // threads per DK-pass CTA
+constexpr int CONSUMER_WARPS = 16;           // warps per DK-pass CTA
+constexpr int THREADS = 32 * CONSUMER_WARPS;
+static_assert(CONSUMER_WARPS >= NQ, "the tail sums one slot per warp");
 
 // Per-lattice constants, read-only during a pass.
 struct LatConst {
-  int N, BY, YT, model, nf, narr, expansion, seg_begin, seg_end, esz;
+  int N, BY, YT, model, nf, narr, expansion, esz;
+  int slot_begin, slot_end;  // partial-sum slots of this lattice: [slot_begin, slot_end)
+  int int_alpha, pad;        // int_alpha: alpha is an integer in [-4, 4] (powers by multiplication)
   long long V;
   double dx, alpha, q, lam, v, gQ, fo2, fm2, omega_eos;
+  double inv_V, inv_dx2;
   void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
 };
 
@@ -32,17 +37,35 @@ struct LatScalars {
 };
 
 // One work segment: planes [z0, z0+nz) of y-tile `ytile` of lattice `lat`,
-// marched in direction dir (+1 up, -1 down).
+// marched in direction dir (+1 up, -1 down).  Consecutive segments of one CTA
+// on one lattice accumulate into partial-sum slot `slot`; `flush` marks the
+// last segment of such a run.
 struct Seg {
-  int lat, ytile, z0, nz, dir, pad;
+  int lat, ytile, z0, nz, dir, slot, flush, pad;
 };
+constexpr int MAX_SEG_PER_CTA = 16;
+
+// What a refill needs to know about a segment, cached in shared memory.
+struct IssueInfo {
+  int z0, nz, dir, ylo, N, rows, pad0, pad1;
+  const void* src[MAX_ARR];
+};
+
+// Shared-memory layout behind the stage ring of a DK pass (byte offsets).
+constexpr size_t SM_FULL = 0;                                   // 8 mbarriers
+constexpr size_t SM_RELEASED = 64;                              // 8 release counts
+constexpr size_t SM_OFF = 128;                                  // MAX_SEG_PER_CTA + 1 plane offsets
+constexpr size_t SM_RED = 256;                                  // 33 x NQ doubles
+constexpr size_t SM_FLAG = SM_RED + 33 * NQ * 8;                // 4 ints
+constexpr size_t SM_INFO = (SM_FLAG + 16 + 127) / 128 * 128;    // MAX_SEG_PER_CTA IssueInfo
+constexpr size_t SM_TAIL_BYTES = SM_INFO + MAX_SEG_PER_CTA * sizeof(IssueInfo);
 
 struct PassArgs {
   const LatConst* lat;
   LatScalars* sc;
   const Seg* segs;
   const int* cta_seg;        // [gridDim.x + 1]
-  double* partials;          // [nseg][NQ]
+  double* partials;          // [nslot][NQ]
   unsigned* counters;        // [nlat]
   double ck, wout, win, dnext;
   int parity, write, set_rho0, stages;
@@ -93,6 +116,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
       : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -134,6 +164,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Fused multiply-add in the storage precision (fmaf for float, never promoted to double).
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// Error-free transformation of a + b (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // 16-byte vector of T
 template <typename T> struct V16;
 template <> struct V16<float> { typedef float4 type; static constexpr int n = 4; };
@@ -157,5 +198,28 @@ template <> struct Acc<double> {
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
 };
+
+// Warp sum of one accumulator, returned on lane 0.  FP32 storage: the
+// (sum, -compensation) pairs of the lanes are combined pairwise with TwoSum
+// in FP32 and converted to FP64 once; FP64 storage: plain FP64 tree.
+__device__ __forceinline__ double warp_sum(const Acc<float>& a) {
+  float hi = a.s, lo = -a.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = lo + l2 + e;
+  }
+  return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_sum(const Acc<double>& a) {
+  double v = a.s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
 
 }  // namespace clg

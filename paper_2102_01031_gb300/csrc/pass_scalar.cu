@@ -3,18 +3,26 @@
 //
 //   drift (deferred from the previous pass):  phi += cd * pi,   cd = h abar^{alpha-3}
 //   kick:   pi += c_k [ a^{1+alpha} Lap phi - a^{3+alpha} V_{,phi} ]
-//   Lap phi = sum_i [phi(n+i) - 2 phi(n) + phi(n-i)] / dx^2       (eq. neutrald/forwardbackwardd)
-//   sums:   sum pi^2 before / after the kick, sum_i (grad^+_i phi)^2, sum V, means
+//   Lap phi = sum_i [phi(n+i) - 2 phi(n) + phi(n-i)] / dx^2       (eqs. neutrald, forwardbackwardd)
+//   sums:   sum pi^2 before / after the kick, sum_i (grad^+_i phi)^2, sum V (+ means)
 //
 // One pass per integrator stage: each field and momentum array is read once
-// from HBM and written once.  A CTA owns a tile of BY full x-rows and marches
-// along z over a run of planes ("segment"); every plane tile (with one halo
-// row on each side in y) of every array arrives in shared memory by 1-D bulk
-// async copies (TMA) into a ring of stages, completion tracked by mbarriers.
-// The drift is applied in shared memory, z-neighbours live in registers, y
-// neighbours come from the stage, x neighbours from warp shuffles.  Partial
-// sums go to one slot per segment; the last segment of a lattice to finish
-// reduces them in a fixed order and runs the Friedmann update (tail.cuh).
+// from HBM and written once.  A CTA owns runs of (y-tile, z-plane) tasks
+// ("segments"): BY full x-rows marched along z.  Its segments form one
+// continuous sequence of planes (each segment adds a halo plane at both
+// ends); every plane tile (plus one halo row on each side in y) of every
+// array streams into a ring of shared-memory stages by 1-D bulk async copies
+// (TMA), completion counted on the stage's mbarrier.  The 16 warps never meet
+// at a block barrier while marching: each waits for the stage it needs,
+// applies the drift in registers as it reads (z-neighbours stay in registers,
+// y-neighbours come from the stage, x-neighbours from warp shuffles), kicks,
+// stores, and releases the stage; the last warp to release a stage (shared
+// memory count) issues the copies of the plane S places further in the
+// sequence, so the ring runs on across segment boundaries.  Sums are formed
+// per plane in the storage precision, added once per plane to compensated
+// (FP32) or plain (FP64) accumulators and flushed once per run into the run's
+// slot; the last slot of a lattice to be written reduces all of them in a
+// fixed order and runs the Friedmann update (tail.cuh).
 #include "common.cuh"
 #include "tail.cuh"
 
@@ -43,6 +51,21 @@ template <> struct ScalarPot<2> {
   }
 };
 
+template <typename T, int VX>
+__device__ __forceinline__ void ld_vec(T (&v)[VX], const T* p) {
+  *reinterpret_cast<typename V16<T>::type*>(v) = *reinterpret_cast<const typename V16<T>::type*>(p);
+}
+template <typename T, int VX>
+__device__ __forceinline__ void st_vec(T* p, const T (&v)[VX]) {
+  *reinterpret_cast<typename V16<T>::type*>(p) = *reinterpret_cast<const typename V16<T>::type*>(v);
+}
+
+// z of plane j of a segment (j = 0 and nz + 1 are its halo planes)
+__device__ __forceinline__ int seg_plane_z(const Seg& sg, int N, int j) {
+  const int z = sg.dir > 0 ? sg.z0 - 1 + j : sg.z0 + sg.nz - j;
+  return z < 0 ? z + N : (z >= N ? z - N : z);
+}
+
 // RED: 0 = no sums, 1 = sums for the Friedmann kick, 2 = full measurement.
 template <typename T, int NF, int RED>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
@@ -50,328 +73,392 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   constexpr int NA = 2 * NF;
   constexpr int NPOT = ScalarPot<NF>::NPOT;
   constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 4 : 6 * NF + NPOT);
-  typedef typename V16<T>::type VT;
+  // slots a pass reduces: the Friedmann sums, or every measured sum plus the
+  // non-finite count (slot NQ - 1)
+  constexpr int NUSED = RED == 0 ? 0 : (RED == 1 ? 4 : NQ);
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = P.stages;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)S * P.stage_bytes_max);
-  double* red = reinterpret_cast<double*>(bar + 8);  // [33][NQ]
-  volatile int* flag = reinterpret_cast<volatile int*>(red + 33 * NQ);
-  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned char* tail = smem + (size_t)S * P.stage_bytes_max;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tail + SM_FULL);
+  unsigned* released = reinterpret_cast<unsigned*>(tail + SM_RELEASED);  // warps done with a stage
+  int* off = reinterpret_cast<int*>(tail + SM_OFF);                      // plane offsets of segments
+  double* red = reinterpret_cast<double*>(tail + SM_RED);                // [33][NQ]
+  volatile int* flag = reinterpret_cast<volatile int*>(tail + SM_FLAG);
+  IssueInfo* info = reinterpret_cast<IssueInfo*>(tail + SM_INFO);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sb = P.cta_seg[blockIdx.x], ns = P.cta_seg[blockIdx.x + 1] - sb;
 
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      released[s] = 0u;
+    }
     fence_mbar_init();
     flag[0] = 0;
     flag[1] = 0;
+    flag[2] = ns > 0 ? P.segs[sb].lat : 0;
+    off[0] = 0;
+    for (int i = 0; i < ns; ++i) {
+      const Seg& sg = P.segs[sb + i];
+      const LatConst& L = P.lat[sg.lat];
+      off[i + 1] = off[i] + sg.nz + 2;
+      IssueInfo& in = info[i];
+      in.z0 = sg.z0;
+      in.nz = sg.nz;
+      in.dir = sg.dir;
+      in.ylo = sg.ytile * L.BY;
+      in.N = L.N;
+      in.rows = L.BY + 2;
+      for (int a = 0; a < NA; ++a) in.src[a] = L.buf[P.parity][a];
+    }
   }
   __syncthreads();
+  const int ptot = off[ns];
 
-  unsigned long long jg = 0;  // planes consumed by this CTA so far: stage/phase bookkeeping
-  const int seg_end = P.cta_seg[blockIdx.x + 1];
-  for (int si = P.cta_seg[blockIdx.x]; si < seg_end; ++si) {
-    const Seg sg = P.segs[si];
+  // bulk copies of plane g of this CTA's sequence into stage g mod S
+  auto issue = [&](int g) {
+    int i = 0;
+    while (g >= off[i + 1]) ++i;
+    const IssueInfo& in = info[i];
+    const int N = in.N, rows = in.rows, ylo = in.ylo, arr_elems = rows * N;
+    const int s = g % S;
+    T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max);
+    const int j = g - off[i];
+    int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
+    zp = zp < 0 ? zp + N : (zp >= N ? zp - N : zp);
+    const long long zoff = (long long)zp * N * N;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
+    int r = 0;
+    while (r < rows) {
+      int g2 = ylo - 1 + r;
+      g2 = g2 < 0 ? g2 + N : (g2 >= N ? g2 - N : g2);
+      int run = 1;
+      while (r + run < rows && g2 + run < N) ++run;
+#pragma unroll
+      for (int a = 0; a < NA; ++a)
+        bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N,
+                 reinterpret_cast<const T*>(in.src[a]) + zoff + (long long)g2 * N,
+                 (uint32_t)(run * N * sizeof(T)), &full[s]);
+      r += run;
+    }
+  };
+  // a warp is done with plane g (in stage s); the last of the 16 refills s with plane g + S
+  auto release = [&](int g, int s) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const unsigned prev = atomicAdd(&released[s], 1u);
+      if (prev == CONSUMER_WARPS - 1u) {
+        released[s] = 0u;
+        if (g + S < ptot && !flag[0]) issue(g + S);
+      }
+    }
+    __syncwarp();
+  };
+  auto wait_full = [&](int s, uint32_t par) {
+    if (flag[0]) return;
+    if (!mbar_wait_bounded(&full[s], par, P.wait_limit_ns)) flag[0] = 1;
+  };
+  auto stage_ptr = [&](int s) -> const T* {
+    return reinterpret_cast<const T*>(smem + (size_t)s * P.stage_bytes_max);
+  };
+
+  if (tid == 0)
+    for (int g = 0; g < S && g < ptot; ++g) issue(g);
+
+  // stage and full-barrier phase of the current plane, advanced without divisions
+  int s_cur = 0;
+  uint32_t p_cur = 0u;
+  auto advance = [&](int& s, uint32_t& p) {
+    if (++s == S) {
+      s = 0;
+      p ^= 1u;
+    }
+  };
+
+  Acc<T> acc[NACC];
+  float nonfinite = 0.f;
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k].zero();
+
+  for (int i = 0; i < ns; ++i) {
+    const Seg sg = P.segs[sb + i];
     const LatConst& L = P.lat[sg.lat];
-    if (tid == 0) flag[2] = sg.lat;
     const int N = L.N, BY = L.BY, TX = N / VX;
     const int tx = tid % TX, ty = tid / TX;
-    const bool active = ty < BY;
-    const unsigned amask = __ballot_sync(0xffffffffu, active);  // active threads are 0 .. TX*BY-1
+    const bool active = ty < BY;  // active threads are 0 .. TX*BY-1
     const int x0 = tx * VX;
-    const int ylo = sg.ytile * BY, y = ylo + ty;
+    const int y = sg.ytile * BY + ty;
+    const int arr_elems = (BY + 2) * N;
+    const long long NN = (long long)N * N;
+    const int g0 = off[i];
     const LatScalars& SC = P.sc[sg.lat];
-    const double dx = L.dx;
     const T cd = (T)SC.cd;
-    const T A1 = (T)(P.ck * SC.apow1 / (dx * dx));
+    const bool drifting = SC.cd != 0.0;
+    const T A1 = (T)(P.ck * SC.apow1 * L.inv_dx2);
     const T A3 = (T)(P.ck * SC.apow3);
     const T q = (T)L.q;
-    const int rows = BY + 2;
-    const int arr_elems = rows * N;
-    const int nplanes = sg.nz + 2;
-    const long long NN = (long long)N * N;
-    const T* src[NA];
+    const unsigned amask = __ballot_sync(0xffffffffu, active);
     T* dst[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      src[a] = reinterpret_cast<const T*>(L.buf[P.parity][a]);
-      dst[a] = reinterpret_cast<T*>(L.buf[P.parity ^ 1][a]);
-    }
-    auto plane_z = [&](int j) -> int {
-      int z = sg.dir > 0 ? sg.z0 - 1 + j : sg.z0 + sg.nz - j;
-      z %= N;
-      return z < 0 ? z + N : z;
-    };
-    auto stage = [&](int j) -> T* {
-      return reinterpret_cast<T*>(smem + (size_t)((jg + j) % S) * P.stage_bytes_max);
-    };
-    auto issue = [&](int j) {  // thread 0 only
-      T* st = stage(j);
-      uint64_t* b = &bar[(jg + j) % S];
-      const long long zoff = (long long)plane_z(j) * NN;
-      mbar_arrive_expect_tx(b, (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
-      int r = 0;
-      while (r < rows) {
-        int g = ylo - 1 + r;
-        g = g < 0 ? g + N : (g >= N ? g - N : g);
-        int run = 1;
-        while (r + run < rows && g + run < N) ++run;
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-          bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N, src[a] + zoff + (long long)g * N,
-                   (uint32_t)(run * N * sizeof(T)), b);
-        r += run;
-      }
-    };
-    auto wait = [&](int j) {
-      uint64_t* b = &bar[(jg + j) % S];
-      const uint32_t par = (uint32_t)(((jg + j) / S) & 1ull);
-      if (!mbar_wait_bounded(b, par, P.wait_limit_ns)) flag[0] = 1;
-    };
-    auto drift = [&](int j) {  // phi += cd * pi over the whole stage, in shared memory
-      if (cd == T(0)) return;
-      T* st = stage(j);
+    for (int a = 0; a < NA; ++a) dst[a] = reinterpret_cast<T*>(L.buf[P.parity ^ 1][a]);
+    const int own = (ty + 1) * N + x0;
+
+    // own values of a stage, drifted: phi + cd * pi
+    auto read_own = [&](const T* st, T (&ph)[NF][VX], T (&pm)[NF][VX]) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        T* ph = st + (size_t)(2 * f) * arr_elems;
-        const T* pm = st + (size_t)(2 * f + 1) * arr_elems;
-        for (int e = tid * VX; e < arr_elems; e += blockDim.x * VX) {
-          T p[VX], m[VX];
-          *reinterpret_cast<VT*>(p) = *reinterpret_cast<const VT*>(ph + e);
-          *reinterpret_cast<VT*>(m) = *reinterpret_cast<const VT*>(pm + e);
+        ld_vec<T, VX>(ph[f], st + (size_t)(2 * f) * arr_elems + own);
+        ld_vec<T, VX>(pm[f], st + (size_t)(2 * f + 1) * arr_elems + own);
+        if (drifting) {
 #pragma unroll
-          for (int v = 0; v < VX; ++v) p[v] = fma(cd, m[v], p[v]);
-          *reinterpret_cast<VT*>(ph + e) = *reinterpret_cast<VT*>(p);
+          for (int v = 0; v < VX; ++v) ph[f][v] = fmaT(cd, pm[f][v], ph[f][v]);
         }
       }
     };
 
-    // prologue
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      const int npre = nplanes < S ? nplanes : S;
-      for (int j = 0; j < npre; ++j) issue(j);
-    }
-    wait(0);
-    wait(1);
-    drift(0);
-    drift(1);
-    __syncthreads();
-    if (flag[0]) goto timeout;
+    T below[NF][VX], cur[NF][VX], above[NF][VX], pic[NF][VX], pia[NF][VX];
+    // planes 0 and 1 of the segment
+    wait_full(s_cur, p_cur);
+    if (active && !flag[0]) read_own(stage_ptr(s_cur), below, pia);
+    release(g0, s_cur);
+    advance(s_cur, p_cur);
+    wait_full(s_cur, p_cur);
+    if (active && !flag[0]) read_own(stage_ptr(s_cur), cur, pic);
+    int s_nxt = s_cur;
+    uint32_t p_nxt = p_cur;
+    advance(s_nxt, p_nxt);
 
-    {
-      T below[NF][VX], cur[NF][VX], above[NF][VX], pic[NF][VX], pia[NF][VX];
-      Acc<T> acc[NACC];
-      float nonfinite = 0.f;
+    for (int j = 1; j <= sg.nz; ++j) {  // plane j in stage s_cur, plane j + 1 in s_nxt
+      wait_full(s_nxt, p_nxt);
+      if (active && !flag[0]) {
+        const T* sa = stage_ptr(s_nxt);
+        const T* sc = stage_ptr(s_cur);
+        read_own(sa, above, pia);
+        T lap[NF][VX], g2[VX];
 #pragma unroll
-      for (int k = 0; k < NACC; ++k) acc[k].zero();
-      if (active) {
-        const T* s0 = stage(0);
-        const T* s1 = stage(1);
-        const int own = (ty + 1) * N + x0;
+        for (int v = 0; v < VX; ++v) g2[v] = T(0);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          *reinterpret_cast<VT*>(below[f]) =
-              *reinterpret_cast<const VT*>(s0 + (size_t)(2 * f) * arr_elems + own);
-          *reinterpret_cast<VT*>(cur[f]) =
-              *reinterpret_cast<const VT*>(s1 + (size_t)(2 * f) * arr_elems + own);
-          *reinterpret_cast<VT*>(pic[f]) =
-              *reinterpret_cast<const VT*>(s1 + (size_t)(2 * f + 1) * arr_elems + own);
-        }
-      }
-
-      for (int j = 1; j <= sg.nz; ++j) {
-        wait(j + 1);
-        drift(j + 1);
-        __syncthreads();
-        if (flag[0]) goto timeout;
-        if (tid == 0 && j - 1 + S < nplanes) {
-          fence_proxy_async_smem();
-          issue(j - 1 + S);
-        }
-        if (active) {
-          const T* sa = stage(j + 1);
-          const T* sc = stage(j);
-          const int own = (ty + 1) * N + x0;
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            *reinterpret_cast<VT*>(above[f]) =
-                *reinterpret_cast<const VT*>(sa + (size_t)(2 * f) * arr_elems + own);
-            *reinterpret_cast<VT*>(pia[f]) =
-                *reinterpret_cast<const VT*>(sa + (size_t)(2 * f + 1) * arr_elems + own);
-          }
-          T lap[NF][VX], g2[VX];
-#pragma unroll
-          for (int v = 0; v < VX; ++v) g2[v] = T(0);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            const T* ph = sc + (size_t)(2 * f) * arr_elems;
-            T yl[VX], yh[VX];
-            *reinterpret_cast<VT*>(yl) = *reinterpret_cast<const VT*>(ph + ty * N + x0);
-            *reinterpret_cast<VT*>(yh) = *reinterpret_cast<const VT*>(ph + (ty + 2) * N + x0);
-            T left = __shfl_up_sync(amask, cur[f][VX - 1], 1);
-            T right = __shfl_down_sync(amask, cur[f][0], 1);
-            if (tx == 0 || lane == 0) left = ph[(ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1)];
-            if (tx == TX - 1 || lane == 31)
-              right = ph[(ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX)];
+          const T* ph = sc + (size_t)(2 * f) * arr_elems;
+          const T* pm = sc + (size_t)(2 * f + 1) * arr_elems;
+          T yl[VX], yh[VX];
+          ld_vec<T, VX>(yl, ph + ty * N + x0);
+          ld_vec<T, VX>(yh, ph + (ty + 2) * N + x0);
+          if (drifting) {
+            T ml[VX], mh[VX];
+            ld_vec<T, VX>(ml, pm + ty * N + x0);
+            ld_vec<T, VX>(mh, pm + (ty + 2) * N + x0);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
-              const T c = cur[f][v];
-              const T xl = v == 0 ? left : cur[f][v - 1];
-              const T xr = v == VX - 1 ? right : cur[f][v + 1];
-              const T zl = below[f][v], zh = above[f][v];
-              lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
-                          ((zl + zh) - T(2) * c);
-              if (RED > 0) {
-                const T zp = sg.dir > 0 ? zh : zl;
-                const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
-                const T gg = gx * gx + gy * gy + gz * gz;
-                if (RED == 2) acc[6 * f + 2].add(gg);
-                else g2[v] += gg;
-              }
+              yl[v] = fmaT(cd, ml[v], yl[v]);
+              yh[v] = fmaT(cd, mh[v], yh[v]);
             }
           }
-          T pn[NF][VX];
+          T left = __shfl_up_sync(amask, cur[f][VX - 1], 1);
+          T right = __shfl_down_sync(amask, cur[f][0], 1);
+          if (tx == 0 || lane == 0) {
+            const int e = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1);
+            left = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
+          }
+          if (tx == TX - 1 || lane == 31) {
+            const int e = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
+            right = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
+          }
+          T gf = T(0);
 #pragma unroll
           for (int v = 0; v < VX; ++v) {
-            T fv[NF], dv[NF], tv[NPOT];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) fv[f] = cur[f][v];
-            ScalarPot<NF>::eval(fv, q, dv, tv);
-#pragma unroll
-            for (int f = 0; f < NF; ++f) pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
-            if (RED == 1) {
-              T spre = T(0), spost = T(0), vs = T(0);
-#pragma unroll
-              for (int f = 0; f < NF; ++f) {
-                spre += pic[f][v] * pic[f][v];
-                spost += pn[f][v] * pn[f][v];
-                if (!isfinite(pn[f][v])) nonfinite += 1.f;
-              }
-#pragma unroll
-              for (int t = 0; t < NPOT; ++t) vs += tv[t];
-              acc[0].add(spre);
-              acc[1].add(spost);
-              acc[2].add(g2[v]);
-              acc[3].add(vs);
-            } else if (RED == 2) {
-#pragma unroll
-              for (int f = 0; f < NF; ++f) {
-                acc[6 * f + 0].add(pic[f][v] * pic[f][v]);
-                acc[6 * f + 1].add(pn[f][v] * pn[f][v]);
-                acc[6 * f + 3].add(fv[f]);
-                acc[6 * f + 4].add(fv[f] * fv[f]);
-                acc[6 * f + 5].add(pn[f][v]);
-                if (!isfinite(pn[f][v])) nonfinite += 1.f;
-              }
-#pragma unroll
-              for (int t = 0; t < NPOT; ++t) acc[6 * NF + t].add(tv[t]);
+            const T c = cur[f][v];
+            const T xl = v == 0 ? left : cur[f][v - 1];
+            const T xr = v == VX - 1 ? right : cur[f][v + 1];
+            const T zl = below[f][v], zh = above[f][v];
+            lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
+                        ((zl + zh) - T(2) * c);
+            if (RED > 0) {
+              const T zp = sg.dir > 0 ? zh : zl;
+              const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
+              const T gg = gx * gx + gy * gy + gz * gz;
+              if (RED == 2) gf += gg;
+              else g2[v] += gg;
             }
           }
-          if (P.write) {
-            const long long gi = (long long)plane_z(j) * NN + (long long)y * N + x0;
+          if (RED == 2) acc[6 * f + 2].add(gf);
+        }
+        T pn[NF][VX];
+        T spre = T(0), spost = T(0), vs = T(0), gsum = T(0);
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+          T fv[NF], dv[NF], tv[NPOT];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) fv[f] = cur[f][v];
+          ScalarPot<NF>::eval(fv, q, dv, tv);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
+          if (RED == 1) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-              *reinterpret_cast<VT*>(dst[2 * f] + gi) = *reinterpret_cast<VT*>(cur[f]);
-              *reinterpret_cast<VT*>(dst[2 * f + 1] + gi) = *reinterpret_cast<VT*>(pn[f]);
+              spre = fmaT(pic[f][v], pic[f][v], spre);
+              spost = fmaT(pn[f][v], pn[f][v], spost);
             }
+#pragma unroll
+            for (int t = 0; t < NPOT; ++t) vs += tv[t];
+            gsum += g2[v];
+          } else if (RED == 2) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              acc[6 * f + 0].add(pic[f][v] * pic[f][v]);
+              acc[6 * f + 1].add(pn[f][v] * pn[f][v]);
+              acc[6 * f + 3].add(fv[f]);
+              acc[6 * f + 4].add(fv[f] * fv[f]);
+              acc[6 * f + 5].add(pn[f][v]);
+              if (!isfinite(pn[f][v])) nonfinite += 1.f;
+            }
+#pragma unroll
+            for (int t = 0; t < NPOT; ++t) acc[6 * NF + t].add(tv[t]);
           }
-#pragma unroll
-          for (int f = 0; f < NF; ++f)
-#pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              below[f][v] = cur[f][v];
-              cur[f][v] = above[f][v];
-              pic[f][v] = pia[f][v];
-            }
         }
+        if (RED == 1) {
+          acc[0].add(spre);
+          acc[1].add(spost);
+          acc[2].add(gsum);
+          acc[3].add(vs);
+        }
+        if (P.write) {
+          const long long gi = (long long)seg_plane_z(sg, N, j) * NN + (long long)y * N + x0;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            st_vec<T, VX>(dst[2 * f] + gi, cur[f]);
+            st_vec<T, VX>(dst[2 * f + 1] + gi, pn[f]);
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+          for (int v = 0; v < VX; ++v) {
+            below[f][v] = cur[f][v];
+            cur[f][v] = above[f][v];
+            pic[f][v] = pia[f][v];
+          }
       }
-      jg += (unsigned long long)nplanes;
+      release(g0 + j, s_cur);
+      s_cur = s_nxt;
+      p_cur = p_nxt;
+      advance(s_nxt, p_nxt);
+    }
+    release(g0 + sg.nz + 1, s_cur);
+    advance(s_cur, p_cur);
 
-      // segment partial sums -> slot si; last segment of the lattice runs the tail
-      double vals[NQ];
+    if (!sg.flush) continue;
+
+    // ---- end of this CTA's run on the lattice: flush the sums into its slot ----
+    if (RED > 0) {
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) vals[k] = 0.0;
-      if (RED > 0) {
+      for (int k = 0; k < NUSED; ++k) {
+        double v = 0.0;
+        if (k < NACC) {
+          v = warp_sum(acc[k]);
+        } else if (k == NQ - 1) {
+          float c = nonfinite;
 #pragma unroll
-        for (int k = 0; k < NACC; ++k) vals[k] = acc[k].value();
-        vals[NQ - 1] = (double)nonfinite;
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+          v = (double)c;
+        }
+        if (lane == 0) red[warp * NQ + k] = v;
       }
-      block_reduce_nq(vals, red);
-      if (tid < NQ) {
-        P.partials[(size_t)si * NQ + tid] = red[32 * NQ + tid];
+    }
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k].zero();
+    nonfinite = 0.f;
+    __syncthreads();
+    if (flag[0]) goto timeout;
+    if (warp < NUSED) {  // warp k: fixed shuffle tree over the 16 warp partials of slot k
+      double v = lane < CONSUMER_WARPS ? red[lane * NQ + warp] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        P.partials[(size_t)sg.slot * NQ + warp] = v;
         __threadfence();
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
+      const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
+      flag[1] = (prev == nslot - 1u) ? 1 : 0;
+      flag[2] = sg.lat;
+    }
+    __syncthreads();
+    if (flag[1]) {
+      __threadfence();
+      // warp k sums slot k over the lattice's runs (lanes stride, then a fixed
+      // shuffle tree: the order does not depend on timing)
+      if (warp < NUSED) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
+          s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[32 * NQ + warp] = s;
       }
       __syncthreads();
       if (tid == 0) {
-        const unsigned nseg = (unsigned)(L.seg_end - L.seg_begin);
-        const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
-        flag[1] = (prev == nseg - 1u) ? 1 : 0;
-      }
-      __syncthreads();
-      if (flag[1]) {
-        __threadfence();
-        if (tid < NQ) {
-          double s = 0.0;
-          for (int k = L.seg_begin; k < L.seg_end; ++k) s += __ldcg(&P.partials[(size_t)k * NQ + tid]);
-          red[32 * NQ + tid] = s;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          LatScalars& W = P.sc[sg.lat];
-          const double* sum = red + 32 * NQ;
-          const double a = W.a, V = (double)L.V;
-          const double a2 = a * a, a6 = a2 * a2 * a2;
-          PassSums E = {0, 0, 0, 0, 0, 0, 0};
-          if (RED > 0) {
-            double spre = 0, spost = 0, gg = 0, vs = 0;
-            if (RED == 1) {
-              spre = sum[0]; spost = sum[1]; gg = sum[2]; vs = sum[3];
-            } else {
-              for (int f = 0; f < NF; ++f) {
-                spre += sum[6 * f]; spost += sum[6 * f + 1]; gg += sum[6 * f + 2];
-              }
-              for (int t = 0; t < NPOT; ++t) vs += sum[6 * NF + t];
-            }
-            E.EKpre = spre / (2.0 * a6 * V);
-            E.EKpost = spost / (2.0 * a6 * V);
-            E.EG = gg / (2.0 * a2 * dx * dx * V);
-            E.EV = vs / V;
-          }
-          advance_scalars(P, L, W, E, RED > 0);
-          if (RED == 2) {
-            cl_energies_t& o = W.obs;
-            for (int k = 0; k < 4; ++k) {
-              o.EK[k] = o.EG[k] = o.EV[k] = 0.0;
-              o.mean_phi[k] = o.mean_phi2[k] = o.mean_pi[k] = o.mean_pi2[k] = 0.0;
-            }
-            o.EKA = o.EGA = 0.0;
+        LatScalars& W = P.sc[sg.lat];
+        const double* sum = red + 32 * NQ;
+        const double a = W.a, a2 = a * a, a6 = a2 * a2 * a2;
+        const double ck = 0.5 * L.inv_V / a6, cg = 0.5 * L.inv_V * L.inv_dx2 / a2;
+        PassSums E = {0, 0, 0, 0, 0, 0, 0};
+        if (RED > 0) {
+          double spre = 0, spost = 0, gg = 0, vs = 0;
+          if (RED == 1) {
+            spre = sum[0]; spost = sum[1]; gg = sum[2]; vs = sum[3];
+          } else {
             for (int f = 0; f < NF; ++f) {
-              o.EK[f] = sum[6 * f + 1] / (2.0 * a6 * V);
-              o.EG[f] = sum[6 * f + 2] / (2.0 * a2 * dx * dx * V);
-              o.mean_phi[f] = sum[6 * f + 3] / V;
-              o.mean_phi2[f] = sum[6 * f + 4] / V;
-              o.mean_pi[f] = sum[6 * f + 5] / V;
-              o.mean_pi2[f] = sum[6 * f + 1] / V;
+              spre += sum[6 * f]; spost += sum[6 * f + 1]; gg += sum[6 * f + 2];
             }
-            for (int t = 0; t < NPOT; ++t) o.EV[t] = sum[6 * NF + t] / V;
-            o.nonfinite = (int64_t)sum[NQ - 1];
-            finish_obs(P, L, W);
+            for (int t = 0; t < NPOT; ++t) vs += sum[6 * NF + t];
           }
-          advance_drift(P, L, W);
-          P.counters[sg.lat] = 0u;
+          E.EKpre = spre * ck;
+          E.EKpost = spost * ck;
+          E.EG = gg * cg;
+          E.EV = vs * L.inv_V;
         }
+        advance_scalars(P, L, W, E, RED > 0);
+        if (RED == 2) {
+          cl_energies_t& o = W.obs;
+          for (int k = 0; k < 4; ++k) {
+            o.EK[k] = o.EG[k] = o.EV[k] = 0.0;
+            o.mean_phi[k] = o.mean_phi2[k] = o.mean_pi[k] = o.mean_pi2[k] = 0.0;
+          }
+          o.EKA = o.EGA = 0.0;
+          for (int f = 0; f < NF; ++f) {
+            o.EK[f] = sum[6 * f + 1] * ck;
+            o.EG[f] = sum[6 * f + 2] * cg;
+            o.mean_phi[f] = sum[6 * f + 3] * L.inv_V;
+            o.mean_phi2[f] = sum[6 * f + 4] * L.inv_V;
+            o.mean_pi[f] = sum[6 * f + 5] * L.inv_V;
+            o.mean_pi2[f] = sum[6 * f + 1] * L.inv_V;
+          }
+          for (int t = 0; t < NPOT; ++t) o.EV[t] = sum[6 * NF + t] * L.inv_V;
+          o.nonfinite = (int64_t)sum[NQ - 1];
+          finish_obs(P, L, W);
+        }
+        advance_drift(P, L, W);
+        P.counters[sg.lat] = 0u;
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
   return;
 
 timeout:
-  // A bounded wait gave up: record it, wait (bounded) for this CTA's copies
-  // in flight so that no bulk copy targets freed shared memory, and leave.
+  // A bounded wait gave up: record it, wait (bounded) for copies still in
+  // flight so that none lands in shared memory after exit, and leave.
   if (tid == 0) {
     for (int s = 0; s < S; ++s)
-      for (int par = 0; par < 2; ++par) mbar_wait_bounded(&bar[s], (uint32_t)par, 1000000ull);
+      for (int par = 0; par < 2; ++par) mbar_wait_bounded(&full[s], (uint32_t)par, 1000000ull);
     P.sc[flag[2]].status = CL_ETIMEOUT;
   }
   __syncthreads();

@@ -14,6 +14,26 @@ struct PassSums {
   double EKApre;                  // U(1) electric before the kick
 };
 
+// a^(alpha + k): by repeated multiplication when alpha is a small integer
+// (alpha = 1 or 0 in the manual's scenarios), pow otherwise.  Double pow has
+// a long dependent latency and this runs between two passes.
+__device__ __forceinline__ double apow(const LatConst& L, double a, int m, int k) {
+  // exponent m * alpha + k
+  if (L.int_alpha) {
+    int e = m * (int)L.alpha + k;
+    const bool neg = e < 0;
+    e = neg ? -e : e;
+    double x = 1.0, b = a;
+    while (e) {
+      if (e & 1) x *= b;
+      b *= b;
+      e >>= 1;
+    }
+    return neg ? 1.0 / x : x;
+  }
+  return pow(a, m * L.alpha + k);
+}
+
 __device__ __forceinline__ double fixed_p(const LatConst& L) {
   return 2.0 / (3.0 * (1.0 + L.omega_eos) - 2.0 * L.alpha);
 }
@@ -33,7 +53,7 @@ __device__ __forceinline__ double H_fixed(const LatConst& L, const LatScalars& S
 __device__ __forceinline__ double kernel_a(const LatConst& L, double a, double EK, double EG,
                                            double EV, double EKA, double EGA) {
   const double al = L.alpha;
-  return pow(a, 2.0 * al + 1.0) / 3.0 * L.fm2 *
+  return apow(L, a, 2, 1) * (1.0 / 3.0) * L.fm2 *
          ((al - 2.0) * EK + al * EG + (al - 1.0) * (EKA + EGA) + (al + 1.0) * EV);
 }
 
@@ -50,21 +70,21 @@ __device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, Lat
 }
 
 __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, LatScalars& S) {
-  const double a = S.a, al = L.alpha;
+  const double a = S.a;
   if (P.dnext != 0.0) {
     double an;
     if (L.expansion == CL_EXP_SELF) an = a + P.dnext * S.b;
     else if (L.expansion == CL_EXP_FIXED) an = a_fixed(L, S, S.eta + P.dnext);
     else an = a;
     const double abar = 0.5 * (a + an);
-    S.cd = P.dnext * pow(abar, al - 3.0);
-    S.cdA = P.dnext * pow(abar, al - 1.0);
+    S.cd = P.dnext * apow(L, abar, 1, -3);
+    S.cdA = P.dnext * apow(L, abar, 1, -1);
     S.a = an;
     S.eta += P.dnext;
     if (L.expansion == CL_EXP_FIXED) S.b = an * H_fixed(L, S, S.eta);
-    S.apow1 = pow(an, 1.0 + al);
-    S.apow3 = pow(an, 3.0 + al);
-    S.apowm1 = pow(an, al - 1.0);
+    S.apow1 = apow(L, an, 1, 1);
+    S.apow3 = apow(L, an, 1, 3);
+    S.apowm1 = apow(L, an, 1, -1);
   } else {
     S.cd = 0.0;
     S.cdA = 0.0;
@@ -78,7 +98,7 @@ __device__ inline void finish_obs(const PassArgs& P, const LatConst& L, LatScala
   for (int k = 0; k < 4; ++k) rho += o.EK[k] + o.EG[k] + o.EV[k];
   o.rho = rho;
   o.hubble_lhs = S.b * S.b;
-  o.hubble_rhs = pow(S.a, 2.0 * L.alpha + 2.0) / 3.0 * L.fm2 * rho;
+  o.hubble_rhs = apow(L, S.a, 2, 2) * (1.0 / 3.0) * L.fm2 * rho;
   const double den = o.hubble_lhs + o.hubble_rhs;
   o.hubble_viol = den > 0.0 ? (o.hubble_lhs - o.hubble_rhs) / den : 0.0;
   if (P.set_rho0) S.rho0 = rho;
