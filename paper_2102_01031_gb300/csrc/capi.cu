@@ -62,6 +62,9 @@ struct cl_ctx {
   double* d_tmp = nullptr;         // scratch for conversions / spectra (V doubles)
   double2* d_cplx = nullptr;       // scratch complex (2 V)
   double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk) + output
+  unsigned* d_gsync = nullptr;     // arrival counters of multi-pass launches
+  bool coop = false;               // multi-pass cooperative launches possible
+  std::vector<std::pair<std::vector<PassStep>, void*>> step_cache;
   LatConst hlat;
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
@@ -76,6 +79,7 @@ struct cl_ctx {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+  std::vector<int> ev_npass;
   double timing_ms = 0.0;
   long long timing_passes = 0;
   std::string err;
@@ -157,28 +161,59 @@ PassKernel pick_kernel(cl_ctx* c, int red) {
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
 
-cl_status run_pass(cl_ctx* c, double ck, double wout, double win, double dnext, int red, int write,
-                   int set_rho0) {
+// Launch `n` passes of the given weights.  One pass: a plain launch.  Several:
+// one cooperative launch of the same kernel (all CTAs resident) that runs
+// them back to back, its per-pass weights read from a device copy of `st`
+// (cached by content) and its two arrival counters zeroed first.
+cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write, int set_rho0) {
+  PassKernel k = pick_kernel(c, red);
+  if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
   PassArgs A;
+  memset(&A, 0, sizeof(A));
   A.lat = c->d_lat;
   A.sc = c->d_sc;
   A.segs = c->d_segs;
   A.cta_seg = c->d_cta;
   A.partials = c->d_part;
   A.counters = c->d_cnt;
-  A.ck = ck;
-  A.wout = wout;
-  A.win = win;
-  A.dnext = dnext;
+  A.ck = st[0].ck;
+  A.wout = st[0].wout;
+  A.win = st[0].win;
+  A.dnext = st[0].dnext;
   A.parity = c->parity;
   A.write = write;
   A.set_rho0 = set_rho0;
   A.stages = c->stages;
   A.stage_bytes_max = c->stage_bytes;
-  A.pad = 0;
+  A.nlat = 1;
   A.wait_limit_ns = 2000000000ull;  // 2 s
-  PassKernel k = pick_kernel(c, red);
-  if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
+  A.steps = nullptr;
+  A.npass = 1;
+  A.gsync = nullptr;
+  const bool multi = n > 1 && c->coop;
+  if (multi) {
+    // device copy of the weights, cached by content
+    std::vector<PassStep> key(st, st + n);
+    const PassStep* dev = nullptr;
+    for (auto& e : c->step_cache)
+      if (e.first.size() == key.size() && memcmp(e.first.data(), key.data(), n * sizeof(PassStep)) == 0)
+        dev = static_cast<const PassStep*>(e.second);
+    if (!dev) {
+      void* d = nullptr;
+      if (c->step_cache.size() >= 8) {
+        cudaFree(c->step_cache.front().second);
+        c->step_cache.erase(c->step_cache.begin());
+      }
+      CU(cudaMalloc(&d, n * sizeof(PassStep)));
+      CU(cudaMemcpy(d, key.data(), n * sizeof(PassStep), cudaMemcpyHostToDevice));
+      c->step_cache.push_back(std::make_pair(key, d));
+      dev = static_cast<const PassStep*>(d);
+    }
+    A.steps = dev;
+    A.npass = n;
+    A.gsync = c->d_gsync;
+    CU(cudaMemsetAsync(c->d_gsync, 0, 2 * sizeof(unsigned), c->stream));
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     for (cudaEvent_t* e : {&e0, &e1}) {
@@ -191,15 +226,35 @@ cl_status run_pass(cl_ctx* c, double ck, double wout, double win, double dnext, 
     }
     CU(cudaEventRecord(e0, c->stream));
   }
-  k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
-  CHECK_LAUNCH();
-  ++c->launches;
+  if (multi) {
+    void* args[] = {&A};
+    CU(cudaLaunchCooperativeKernel((const void*)k, dim3(c->grid), dim3(THREADS), args, c->smem_bytes,
+                                   c->stream));
+  } else {
+    for (int i = 0; i < n; ++i) {
+      A.ck = st[i].ck;
+      A.wout = st[i].wout;
+      A.win = st[i].win;
+      A.dnext = st[i].dnext;
+      A.parity = c->parity ^ (write ? (i & 1) : 0);
+      k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
+      CHECK_LAUNCH();
+    }
+  }
+  c->launches += multi ? 1 : n;
   if (c->timing) {
     CU(cudaEventRecord(e1, c->stream));
     c->ev_pending.push_back(std::make_pair(e0, e1));
+    c->ev_npass.push_back(n);
   }
-  if (write) c->parity ^= 1;
+  if (write && (n & 1)) c->parity ^= 1;
   return CL_OK;
+}
+
+cl_status run_pass(cl_ctx* c, double ck, double wout, double win, double dnext, int red, int write,
+                   int set_rho0) {
+  PassStep st = {ck, wout, win, dnext};
+  return launch_passes(c, &st, 1, red, write, set_rho0);
 }
 
 int red_for_step(const cl_ctx* c) { return c->p.expansion == CL_EXP_SELF ? 1 : 0; }
@@ -351,6 +406,8 @@ cl_status cl_free(cl_ctx* c) {
   cudaFree(c->d_tmp);
   cudaFree(c->d_cplx);
   cudaFree(c->d_spec);
+  cudaFree(c->d_gsync);
+  for (auto& e : c->step_cache) cudaFree(e.second);
   delete c;
   return CL_OK;
 }
@@ -445,6 +502,14 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   CU(cudaMalloc(&c->d_cta, cta.size() * sizeof(int)));
   CU(cudaMalloc(&c->d_part, (size_t)c->nslot * NQ * sizeof(double)));
   CU(cudaMalloc(&c->d_cnt, sizeof(unsigned)));
+  CU(cudaMalloc(&c->d_gsync, 2 * sizeof(unsigned)));
+  {
+    int coop = 0, nb = 0;
+    CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)pick_kernel(c, red_for_step(c)),
+                                                     THREADS, c->smem_bytes));
+    c->coop = coop && (long long)nb * c->nsm >= c->grid;
+  }
   CU(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned), c->stream));
   LatConst& L = c->hlat;
   memset(&L, 0, sizeof(L));
@@ -554,18 +619,27 @@ cl_status cl_step_h(cl_ctx* c, int n, double h) {
   std::vector<double> d1;
   schedule(c->p.integrator == CL_LF ? 2 : c->p.integrator, h, d1);
   const int red = red_for_step(c);
+  // kick/drift weights of every pass: the first pass of a closed stream only
+  // kicks (by half the first drift); later passes merge the kick-out of the
+  // previous drift with the kick-in of the next
+  std::vector<PassStep> steps;
+  steps.reserve((size_t)n * d1.size());
   for (int s = 0; s < n; ++s)
     for (double d : d1) {
-      cl_status st;
       if (!c->open) {
-        st = run_pass(c, 0.5 * d, 0.0, 0.5 * d, d, red, 1, 0);
+        steps.push_back(PassStep{0.5 * d, 0.0, 0.5 * d, d});
         c->open = true;
       } else {
-        st = run_pass(c, 0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d, red, 1, 0);
+        steps.push_back(PassStep{0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d});
       }
-      if (st != CL_OK) return st;
       c->dprev = d;
     }
+  const int chunk = 4096;
+  for (size_t b = 0; b < steps.size(); b += chunk) {
+    const int m = (int)std::min<size_t>(chunk, steps.size() - b);
+    cl_status st = launch_passes(c, steps.data() + b, m, red, 1, 0);
+    if (st != CL_OK) return st;
+  }
   c->obs_valid = false;
   return CL_OK;
 }
@@ -749,15 +823,17 @@ cl_status cl_enable_pass_timing(cl_ctx* c, int enable) {
 cl_status cl_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   CU(cudaStreamSynchronize(c->stream));
-  for (auto& pr : c->ev_pending) {
+  for (size_t i = 0; i < c->ev_pending.size(); ++i) {
+    auto& pr = c->ev_pending[i];
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
     c->timing_ms += ms;
-    c->timing_passes += 1;
+    c->timing_passes += c->ev_npass[i];
     c->ev_pool.push_back(pr.first);
     c->ev_pool.push_back(pr.second);
   }
   c->ev_pending.clear();
+  c->ev_npass.clear();
   if (ms_total) *ms_total = c->timing_ms;
   if (passes) *passes = c->timing_passes;
   if (reset) {

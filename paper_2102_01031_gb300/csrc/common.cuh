@@ -26,12 +26,22 @@ struct LatConst {
   void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
 };
 
+// The evolving scalars of a lattice (the first members of LatScalars).
+struct ScalarState {
+  double a, b, eta;
+  double cd, cdA;
+  double apow1, apow3, apowm1;
+  double a0, eta0, Hfix, rho0;
+  double pi2;
+};
+
 // Per-lattice evolving scalars (device resident, FP64).
 struct LatScalars {
   double a, b, eta;
   double cd, cdA;                 // drift coefficients for the next pass (fields, links)
   double apow1, apow3, apowm1;    // a^{1+alpha}, a^{3+alpha}, a^{alpha-1} at the current a
   double a0, eta0, Hfix, rho0;
+  double pi2;                     // sum of pi^2 after the last kick (the next kick's pre-kick sum)
   cl_energies_t obs;              // last measurement
   int status, pad;
 };
@@ -48,7 +58,7 @@ constexpr int MAX_SEG_PER_CTA = 16;
 // What a refill needs to know about a segment, cached in shared memory.
 struct IssueInfo {
   int z0, nz, dir, ylo, N, rows, pad0, pad1;
-  const void* src[MAX_ARR];
+  const void* src[2][MAX_ARR];  // by buffer parity
 };
 
 // Shared-memory layout behind the stage ring of a DK pass (byte offsets).
@@ -56,9 +66,14 @@ constexpr size_t SM_FULL = 0;                                   // 8 mbarriers
 constexpr size_t SM_RELEASED = 64;                              // 8 release counts
 constexpr size_t SM_OFF = 128;                                  // MAX_SEG_PER_CTA + 1 plane offsets
 constexpr size_t SM_RED = 256;                                  // 33 x NQ doubles
-constexpr size_t SM_FLAG = SM_RED + 33 * NQ * 8;                // 4 ints
-constexpr size_t SM_INFO = (SM_FLAG + 16 + 127) / 128 * 128;    // MAX_SEG_PER_CTA IssueInfo
+constexpr size_t SM_FLAG = SM_RED + 33 * NQ * 8;                // 4 ints + pending tails
+constexpr size_t SM_INFO = (SM_FLAG + 16 + 4 * MAX_SEG_PER_CTA + 127) / 128 * 128;  // IssueInfo[]
 constexpr size_t SM_TAIL_BYTES = SM_INFO + MAX_SEG_PER_CTA * sizeof(IssueInfo);
+
+// Kick/drift weights of one pass (see the schedule in capi.cu).
+struct PassStep {
+  double ck, wout, win, dnext;
+};
 
 struct PassArgs {
   const LatConst* lat;
@@ -70,8 +85,13 @@ struct PassArgs {
   double ck, wout, win, dnext;
   int parity, write, set_rho0, stages;
   unsigned stage_bytes_max;  // bytes of one stage (max over lattices)
-  unsigned pad;
-  unsigned long long wait_limit_ns;  // bound of every mbarrier wait
+  int nlat;                  // lattices advanced by the launch
+  unsigned long long wait_limit_ns;  // bound of every wait
+  // several passes in one cooperative launch (npass > 1): weights per pass and
+  // two monotonic counters (writes arrived, tails done), zeroed before launch
+  const PassStep* steps;
+  int npass, pad2;
+  unsigned* gsync;
 };
 
 // Initial-condition parameters (program units).
@@ -106,6 +126,16 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -149,6 +179,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Bounded wait until the counter *c reaches `target` (other CTAs of a
+// cooperative launch increment it); false after limit_ns.
+__device__ __forceinline__ bool wait_counter(const unsigned* c, unsigned target,
+                                             unsigned long long limit_ns) {
+  if ((int)(ld_acquire_u32(c) - target) >= 0) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 0; i < (1u << 30); ++i) {
+    __nanosleep(64);
+    if ((int)(ld_acquire_u32(c) - target) >= 0) return true;
+    if ((i & 15u) == 15u && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
 }
 
 // Bounded wait on an mbarrier phase: gives up (returns false) after `limit_ns`

@@ -67,15 +67,23 @@ __device__ __forceinline__ int seg_plane_z(const Seg& sg, int N, int j) {
 }
 
 // RED: 0 = no sums, 1 = sums for the Friedmann kick, 2 = full measurement.
+// P.npass > 1: several passes in one cooperative launch; between two passes
+// every CTA signals that its writes are done, the CTAs that close a lattice's
+// sums run its Friedmann update, and every CTA prefetches the first planes of
+// the next pass as soon as all writes are done, before it waits for the
+// updated scalars.
 template <typename T, int NF, int RED>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   constexpr int VX = V16<T>::n;
   constexpr int NA = 2 * NF;
   constexpr int NPOT = ScalarPot<NF>::NPOT;
-  constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 4 : 6 * NF + NPOT);
+  // RED = 1 sums: pi^2 after the kick, (grad^+ phi)^2, V.  The pre-kick sum of
+  // pi^2 is the previous kick's post-kick sum (a drift leaves pi unchanged),
+  // carried in the lattice scalars.
+  constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 3 : 6 * NF + NPOT);
   // slots a pass reduces: the Friedmann sums, or every measured sum plus the
   // non-finite count (slot NQ - 1)
-  constexpr int NUSED = RED == 0 ? 0 : (RED == 1 ? 4 : NQ);
+  constexpr int NUSED = RED == 0 ? 0 : (RED == 1 ? 3 : NQ);
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = P.stages;
@@ -84,10 +92,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   unsigned* released = reinterpret_cast<unsigned*>(tail + SM_RELEASED);  // warps done with a stage
   int* off = reinterpret_cast<int*>(tail + SM_OFF);                      // plane offsets of segments
   double* red = reinterpret_cast<double*>(tail + SM_RED);                // [33][NQ]
-  volatile int* flag = reinterpret_cast<volatile int*>(tail + SM_FLAG);
+  volatile int* flag = reinterpret_cast<volatile int*>(tail + SM_FLAG);  // timeout, last, lattice, #pending
+  int* pend = reinterpret_cast<int*>(tail + SM_FLAG + 16);               // lattices whose tail is due
   IssueInfo* info = reinterpret_cast<IssueInfo*>(tail + SM_INFO);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sb = P.cta_seg[blockIdx.x], ns = P.cta_seg[blockIdx.x + 1] - sb;
+  const bool multi = P.npass > 1;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -98,6 +108,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     flag[0] = 0;
     flag[1] = 0;
     flag[2] = ns > 0 ? P.segs[sb].lat : 0;
+    flag[3] = 0;
     off[0] = 0;
     for (int i = 0; i < ns; ++i) {
       const Seg& sg = P.segs[sb + i];
@@ -110,19 +121,26 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       in.ylo = sg.ytile * L.BY;
       in.N = L.N;
       in.rows = L.BY + 2;
-      for (int a = 0; a < NA; ++a) in.src[a] = L.buf[P.parity][a];
+      for (int a = 0; a < NA; ++a) {
+        in.src[0][a] = L.buf[0][a];
+        in.src[1][a] = L.buf[1][a];
+      }
     }
   }
   __syncthreads();
   const int ptot = off[ns];
+  int parity = P.parity;
+  // planes of earlier passes of this launch: plane g of the current pass is
+  // plane gbase + g of the CTA's whole sequence and sits in stage (gbase+g) mod S
+  int gbase = 0;
 
-  // bulk copies of plane g of this CTA's sequence into stage g mod S
+  // bulk copies of plane g of this pass into its stage
   auto issue = [&](int g) {
     int i = 0;
     while (g >= off[i + 1]) ++i;
     const IssueInfo& in = info[i];
     const int N = in.N, rows = in.rows, ylo = in.ylo, arr_elems = rows * N;
-    const int s = g % S;
+    const int s = (gbase + g) % S;
     T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max);
     const int j = g - off[i];
     int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
 #pragma unroll
       for (int a = 0; a < NA; ++a)
         bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N,
-                 reinterpret_cast<const T*>(in.src[a]) + zoff + (long long)g2 * N,
+                 reinterpret_cast<const T*>(in.src[parity][a]) + zoff + (long long)g2 * N,
                  (uint32_t)(run * N * sizeof(T)), &full[s]);
       r += run;
     }
@@ -165,8 +183,78 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     return reinterpret_cast<const T*>(smem + (size_t)s * P.stage_bytes_max);
   };
 
-  if (tid == 0)
-    for (int g = 0; g < S && g < ptot; ++g) issue(g);
+  // Friedmann update of lattice `lat` once all its slots are written: warp k
+  // sums slot k over the lattice's runs (lanes stride, then a fixed shuffle
+  // tree, so the order does not depend on timing); thread 0 updates a, b and
+  // the coefficients of the next pass.
+  auto run_tail = [&](int lat, const PassStep& st) {
+    const LatConst& L = P.lat[lat];
+    if (warp < NUSED) {
+      double s = 0.0;
+#pragma unroll 4
+      for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
+        s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) red[32 * NQ + warp] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      PassArgs Q = P;
+      Q.ck = st.ck;
+      Q.wout = st.wout;
+      Q.win = st.win;
+      Q.dnext = st.dnext;
+      ScalarState W;
+      load_state_cg(W, &P.sc[lat]);
+      const double* sum = red + 32 * NQ;
+      const double a = W.a, a2 = a * a, a6 = a2 * a2 * a2;
+      const double ck = 0.5 * L.inv_V / a6, cg = 0.5 * L.inv_V * L.inv_dx2 / a2;
+      PassSums E = {0, 0, 0, 0, 0, 0, 0};
+      if (RED > 0) {
+        double spre = 0, spost = 0, gg = 0, vs = 0;
+        if (RED == 1) {
+          spre = W.pi2; spost = sum[0]; gg = sum[1]; vs = sum[2];
+        } else {
+          for (int f = 0; f < NF; ++f) {
+            spre += sum[6 * f]; spost += sum[6 * f + 1]; gg += sum[6 * f + 2];
+          }
+          for (int t = 0; t < NPOT; ++t) vs += sum[6 * NF + t];
+        }
+        E.EKpre = spre * ck;
+        W.pi2 = spost;
+        E.EKpost = spost * ck;
+        E.EG = gg * cg;
+        E.EV = vs * L.inv_V;
+      }
+      advance_scalars(Q, L, W, E, RED > 0);
+      if (RED == 2) {
+        cl_energies_t& o = P.sc[lat].obs;
+        for (int k = 0; k < 4; ++k) {
+          o.EK[k] = o.EG[k] = o.EV[k] = 0.0;
+          o.mean_phi[k] = o.mean_phi2[k] = o.mean_pi[k] = o.mean_pi2[k] = 0.0;
+        }
+        o.EKA = o.EGA = 0.0;
+        for (int f = 0; f < NF; ++f) {
+          o.EK[f] = sum[6 * f + 1] * ck;
+          o.EG[f] = sum[6 * f + 2] * cg;
+          o.mean_phi[f] = sum[6 * f + 3] * L.inv_V;
+          o.mean_phi2[f] = sum[6 * f + 4] * L.inv_V;
+          o.mean_pi[f] = sum[6 * f + 5] * L.inv_V;
+          o.mean_pi2[f] = sum[6 * f + 1] * L.inv_V;
+        }
+        for (int t = 0; t < NPOT; ++t) o.EV[t] = sum[6 * NF + t] * L.inv_V;
+        o.nonfinite = (int64_t)sum[NQ - 1];
+        finish_obs(Q, L, W, o);
+      }
+      advance_drift(Q, L, W);
+      store_state(&P.sc[lat], W);
+      P.counters[lat] = 0u;
+      __threadfence();
+      if (multi) atomicAdd(&P.gsync[1], 1u);
+    }
+    __syncthreads();
+  };
 
   // stage and full-barrier phase of the current plane, advanced without divisions
   int s_cur = 0;
@@ -183,273 +271,248 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k].zero();
 
-  for (int i = 0; i < ns; ++i) {
-    const Seg sg = P.segs[sb + i];
-    const LatConst& L = P.lat[sg.lat];
-    const int N = L.N, BY = L.BY, TX = N / VX;
-    const int tx = tid % TX, ty = tid / TX;
-    const bool active = ty < BY;  // active threads are 0 .. TX*BY-1
-    const int x0 = tx * VX;
-    const int y = sg.ytile * BY + ty;
-    const int arr_elems = (BY + 2) * N;
-    const long long NN = (long long)N * N;
-    const int g0 = off[i];
-    const LatScalars& SC = P.sc[sg.lat];
-    const T cd = (T)SC.cd;
-    const bool drifting = SC.cd != 0.0;
-    const T A1 = (T)(P.ck * SC.apow1 * L.inv_dx2);
-    const T A3 = (T)(P.ck * SC.apow3);
-    const T q = (T)L.q;
-    const unsigned amask = __ballot_sync(0xffffffffu, active);
-    T* dst[NA];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) dst[a] = reinterpret_cast<T*>(L.buf[P.parity ^ 1][a]);
-    const int own = (ty + 1) * N + x0;
-
-    // own values of a stage, drifted: phi + cd * pi
-    auto read_own = [&](const T* st, T (&ph)[NF][VX], T (&pm)[NF][VX]) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        ld_vec<T, VX>(ph[f], st + (size_t)(2 * f) * arr_elems + own);
-        ld_vec<T, VX>(pm[f], st + (size_t)(2 * f + 1) * arr_elems + own);
-        if (drifting) {
-#pragma unroll
-          for (int v = 0; v < VX; ++v) ph[f][v] = fmaT(cd, pm[f][v], ph[f][v]);
-        }
+  for (int pass = 0; pass < P.npass; ++pass) {
+    parity = P.parity ^ (pass & 1);
+    gbase = pass * ptot;
+    if (tid == 0) {
+      if (pass > 0) {
+        // the previous pass's writes are all done before any of its planes is read
+        if (!flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
+          flag[0] = 1;
+        fence_proxy_async_global();
       }
-    };
-
-    T below[NF][VX], cur[NF][VX], above[NF][VX], pic[NF][VX], pia[NF][VX];
-    // planes 0 and 1 of the segment
-    wait_full(s_cur, p_cur);
-    if (active && !flag[0]) read_own(stage_ptr(s_cur), below, pia);
-    release(g0, s_cur);
-    advance(s_cur, p_cur);
-    wait_full(s_cur, p_cur);
-    if (active && !flag[0]) read_own(stage_ptr(s_cur), cur, pic);
-    int s_nxt = s_cur;
-    uint32_t p_nxt = p_cur;
-    advance(s_nxt, p_nxt);
-
-    for (int j = 1; j <= sg.nz; ++j) {  // plane j in stage s_cur, plane j + 1 in s_nxt
-      wait_full(s_nxt, p_nxt);
-      if (active && !flag[0]) {
-        const T* sa = stage_ptr(s_nxt);
-        const T* sc = stage_ptr(s_cur);
-        read_own(sa, above, pia);
-        T lap[NF][VX], g2[VX];
-#pragma unroll
-        for (int v = 0; v < VX; ++v) g2[v] = T(0);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const T* ph = sc + (size_t)(2 * f) * arr_elems;
-          const T* pm = sc + (size_t)(2 * f + 1) * arr_elems;
-          T yl[VX], yh[VX];
-          ld_vec<T, VX>(yl, ph + ty * N + x0);
-          ld_vec<T, VX>(yh, ph + (ty + 2) * N + x0);
-          if (drifting) {
-            T ml[VX], mh[VX];
-            ld_vec<T, VX>(ml, pm + ty * N + x0);
-            ld_vec<T, VX>(mh, pm + (ty + 2) * N + x0);
-#pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              yl[v] = fmaT(cd, ml[v], yl[v]);
-              yh[v] = fmaT(cd, mh[v], yh[v]);
-            }
-          }
-          T left = __shfl_up_sync(amask, cur[f][VX - 1], 1);
-          T right = __shfl_down_sync(amask, cur[f][0], 1);
-          if (tx == 0 || lane == 0) {
-            const int e = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1);
-            left = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
-          }
-          if (tx == TX - 1 || lane == 31) {
-            const int e = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
-            right = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
-          }
-          T gf = T(0);
-#pragma unroll
-          for (int v = 0; v < VX; ++v) {
-            const T c = cur[f][v];
-            const T xl = v == 0 ? left : cur[f][v - 1];
-            const T xr = v == VX - 1 ? right : cur[f][v + 1];
-            const T zl = below[f][v], zh = above[f][v];
-            lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
-                        ((zl + zh) - T(2) * c);
-            if (RED > 0) {
-              const T zp = sg.dir > 0 ? zh : zl;
-              const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
-              const T gg = gx * gx + gy * gy + gz * gz;
-              if (RED == 2) gf += gg;
-              else g2[v] += gg;
-            }
-          }
-          if (RED == 2) acc[6 * f + 2].add(gf);
-        }
-        T pn[NF][VX];
-        T spre = T(0), spost = T(0), vs = T(0), gsum = T(0);
-#pragma unroll
-        for (int v = 0; v < VX; ++v) {
-          T fv[NF], dv[NF], tv[NPOT];
-#pragma unroll
-          for (int f = 0; f < NF; ++f) fv[f] = cur[f][v];
-          ScalarPot<NF>::eval(fv, q, dv, tv);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
-          if (RED == 1) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              spre = fmaT(pic[f][v], pic[f][v], spre);
-              spost = fmaT(pn[f][v], pn[f][v], spost);
-            }
-#pragma unroll
-            for (int t = 0; t < NPOT; ++t) vs += tv[t];
-            gsum += g2[v];
-          } else if (RED == 2) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              acc[6 * f + 0].add(pic[f][v] * pic[f][v]);
-              acc[6 * f + 1].add(pn[f][v] * pn[f][v]);
-              acc[6 * f + 3].add(fv[f]);
-              acc[6 * f + 4].add(fv[f] * fv[f]);
-              acc[6 * f + 5].add(pn[f][v]);
-              if (!isfinite(pn[f][v])) nonfinite += 1.f;
-            }
-#pragma unroll
-            for (int t = 0; t < NPOT; ++t) acc[6 * NF + t].add(tv[t]);
-          }
-        }
-        if (RED == 1) {
-          acc[0].add(spre);
-          acc[1].add(spost);
-          acc[2].add(gsum);
-          acc[3].add(vs);
-        }
-        if (P.write) {
-          const long long gi = (long long)seg_plane_z(sg, N, j) * NN + (long long)y * N + x0;
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            st_vec<T, VX>(dst[2 * f] + gi, cur[f]);
-            st_vec<T, VX>(dst[2 * f + 1] + gi, pn[f]);
-          }
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-#pragma unroll
-          for (int v = 0; v < VX; ++v) {
-            below[f][v] = cur[f][v];
-            cur[f][v] = above[f][v];
-            pic[f][v] = pia[f][v];
-          }
-      }
-      release(g0 + j, s_cur);
-      s_cur = s_nxt;
-      p_cur = p_nxt;
-      advance(s_nxt, p_nxt);
+      if (!flag[0])
+        for (int g = 0; g < S && g < ptot; ++g) issue(g);
+      if (pass > 0 && !flag[0] &&
+          !wait_counter(&P.gsync[1], (unsigned)P.nlat * (unsigned)pass, P.wait_limit_ns))
+        flag[0] = 1;
     }
-    release(g0 + sg.nz + 1, s_cur);
-    advance(s_cur, p_cur);
-
-    if (!sg.flush) continue;
-
-    // ---- end of this CTA's run on the lattice: flush the sums into its slot ----
-    if (RED > 0) {
-#pragma unroll
-      for (int k = 0; k < NUSED; ++k) {
-        double v = 0.0;
-        if (k < NACC) {
-          v = warp_sum(acc[k]);
-        } else if (k == NQ - 1) {
-          float c = nonfinite;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-          v = (double)c;
-        }
-        if (lane == 0) red[warp * NQ + k] = v;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) acc[k].zero();
-    nonfinite = 0.f;
     __syncthreads();
     if (flag[0]) goto timeout;
-    if (warp < NUSED) {  // warp k: fixed shuffle tree over the 16 warp partials of slot k
-      double v = lane < CONSUMER_WARPS ? red[lane * NQ + warp] : 0.0;
+
+    for (int i = 0; i < ns; ++i) {
+      const Seg sg = P.segs[sb + i];
+      const LatConst& L = P.lat[sg.lat];
+      const int N = L.N, BY = L.BY, TX = N / VX;
+      const int tx = tid % TX, ty = tid / TX;
+      const bool active = ty < BY;  // active threads are 0 .. TX*BY-1
+      const int x0 = tx * VX;
+      const int y = sg.ytile * BY + ty;
+      const int arr_elems = (BY + 2) * N;
+      const long long NN = (long long)N * N;
+      const int g0 = off[i];
+      const LatScalars* SC = &P.sc[sg.lat];
+      const double cd64 = __ldcg(&SC->cd);
+      const T cd = (T)cd64;
+      const bool drifting = cd64 != 0.0;
+      const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
+      const T A1 = (T)(ckp * __ldcg(&SC->apow1) * L.inv_dx2);
+      const T A3 = (T)(ckp * __ldcg(&SC->apow3));
+      const T q = (T)L.q;
+      const unsigned amask = __ballot_sync(0xffffffffu, active);
+      T* dst[NA];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) {
-        P.partials[(size_t)sg.slot * NQ + warp] = v;
-        __threadfence();
+      for (int a = 0; a < NA; ++a) dst[a] = reinterpret_cast<T*>(L.buf[parity ^ 1][a]);
+      const int own = (ty + 1) * N + x0;
+
+      // own values of a stage, drifted: phi + cd * pi
+      auto read_own = [&](const T* st, T (&ph)[NF][VX], T (&pm)[NF][VX]) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          ld_vec<T, VX>(ph[f], st + (size_t)(2 * f) * arr_elems + own);
+          ld_vec<T, VX>(pm[f], st + (size_t)(2 * f + 1) * arr_elems + own);
+          if (drifting) {
+#pragma unroll
+            for (int v = 0; v < VX; ++v) ph[f][v] = fmaT(cd, pm[f][v], ph[f][v]);
+          }
+        }
+      };
+
+      T below[NF][VX], cur[NF][VX], above[NF][VX], pic[NF][VX], pia[NF][VX];
+      // planes 0 and 1 of the segment
+      wait_full(s_cur, p_cur);
+      if (active && !flag[0]) read_own(stage_ptr(s_cur), below, pia);
+      release(g0, s_cur);
+      advance(s_cur, p_cur);
+      wait_full(s_cur, p_cur);
+      if (active && !flag[0]) read_own(stage_ptr(s_cur), cur, pic);
+      int s_nxt = s_cur;
+      uint32_t p_nxt = p_cur;
+      advance(s_nxt, p_nxt);
+
+      for (int j = 1; j <= sg.nz; ++j) {  // plane j in stage s_cur, plane j + 1 in s_nxt
+        wait_full(s_nxt, p_nxt);
+        if (active && !flag[0]) {
+          const T* sa = stage_ptr(s_nxt);
+          const T* sc = stage_ptr(s_cur);
+          read_own(sa, above, pia);
+          T lap[NF][VX], g2[VX];
+#pragma unroll
+          for (int v = 0; v < VX; ++v) g2[v] = T(0);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const T* ph = sc + (size_t)(2 * f) * arr_elems;
+            const T* pm = sc + (size_t)(2 * f + 1) * arr_elems;
+            T yl[VX], yh[VX];
+            ld_vec<T, VX>(yl, ph + ty * N + x0);
+            ld_vec<T, VX>(yh, ph + (ty + 2) * N + x0);
+            if (drifting) {
+              T ml[VX], mh[VX];
+              ld_vec<T, VX>(ml, pm + ty * N + x0);
+              ld_vec<T, VX>(mh, pm + (ty + 2) * N + x0);
+#pragma unroll
+              for (int v = 0; v < VX; ++v) {
+                yl[v] = fmaT(cd, ml[v], yl[v]);
+                yh[v] = fmaT(cd, mh[v], yh[v]);
+              }
+            }
+            T left = __shfl_up_sync(amask, cur[f][VX - 1], 1);
+            T right = __shfl_down_sync(amask, cur[f][0], 1);
+            if (tx == 0 || lane == 0) {
+              const int e = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1);
+              left = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
+            }
+            if (tx == TX - 1 || lane == 31) {
+              const int e = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
+              right = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
+            }
+            T gf = T(0);
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              const T c = cur[f][v];
+              const T xl = v == 0 ? left : cur[f][v - 1];
+              const T xr = v == VX - 1 ? right : cur[f][v + 1];
+              const T zl = below[f][v], zh = above[f][v];
+              lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
+                          ((zl + zh) - T(2) * c);
+              if (RED > 0) {
+                const T zp = sg.dir > 0 ? zh : zl;
+                const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
+                const T gg = gx * gx + gy * gy + gz * gz;
+                if (RED == 2) gf += gg;
+                else g2[v] += gg;
+              }
+            }
+            if (RED == 2) acc[6 * f + 2].add(gf);
+          }
+          T pn[NF][VX];
+          T spost = T(0), vs = T(0), gsum = T(0);
+#pragma unroll
+          for (int v = 0; v < VX; ++v) {
+            T fv[NF], dv[NF], tv[NPOT];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) fv[f] = cur[f][v];
+            ScalarPot<NF>::eval(fv, q, dv, tv);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
+            if (RED == 1) {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) spost = fmaT(pn[f][v], pn[f][v], spost);
+#pragma unroll
+              for (int t = 0; t < NPOT; ++t) vs += tv[t];
+              gsum += g2[v];
+            } else if (RED == 2) {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) {
+                acc[6 * f + 0].add(pic[f][v] * pic[f][v]);
+                acc[6 * f + 1].add(pn[f][v] * pn[f][v]);
+                acc[6 * f + 3].add(fv[f]);
+                acc[6 * f + 4].add(fv[f] * fv[f]);
+                acc[6 * f + 5].add(pn[f][v]);
+                if (!isfinite(pn[f][v])) nonfinite += 1.f;
+              }
+#pragma unroll
+              for (int t = 0; t < NPOT; ++t) acc[6 * NF + t].add(tv[t]);
+            }
+          }
+          if (RED == 1) {
+            acc[0].add(spost);
+            acc[1].add(gsum);
+            acc[2].add(vs);
+          }
+          if (P.write) {
+            const long long gi = (long long)seg_plane_z(sg, N, j) * NN + (long long)y * N + x0;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              st_vec<T, VX>(dst[2 * f] + gi, cur[f]);
+              st_vec<T, VX>(dst[2 * f + 1] + gi, pn[f]);
+            }
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              below[f][v] = cur[f][v];
+              cur[f][v] = above[f][v];
+              pic[f][v] = pia[f][v];
+            }
+        }
+        release(g0 + j, s_cur);
+        s_cur = s_nxt;
+        p_cur = p_nxt;
+        advance(s_nxt, p_nxt);
       }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
-      const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
-      flag[1] = (prev == nslot - 1u) ? 1 : 0;
-      flag[2] = sg.lat;
-    }
-    __syncthreads();
-    if (flag[1]) {
-      __threadfence();
-      // warp k sums slot k over the lattice's runs (lanes stride, then a fixed
-      // shuffle tree: the order does not depend on timing)
-      if (warp < NUSED) {
-        double s = 0.0;
-#pragma unroll 4
-        for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
-          s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
+      release(g0 + sg.nz + 1, s_cur);
+      advance(s_cur, p_cur);
+
+      if (!sg.flush) continue;
+
+      // ---- end of this CTA's run on the lattice: flush the sums into its slot ----
+      if (RED > 0) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[32 * NQ + warp] = s;
+        for (int k = 0; k < NUSED; ++k) {
+          double v = 0.0;
+          if (k < NACC) {
+            v = warp_sum(acc[k]);
+          } else if (k == NQ - 1) {
+            float c = nonfinite;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+            v = (double)c;
+          }
+          if (lane == 0) red[warp * NQ + k] = v;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NACC; ++k) acc[k].zero();
+      nonfinite = 0.f;
+      __syncthreads();
+      if (flag[0]) goto timeout;
+      if (warp < NUSED) {  // warp k: fixed shuffle tree over the 16 warp partials of slot k
+        double v = lane < CONSUMER_WARPS ? red[lane * NQ + warp] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+          P.partials[(size_t)sg.slot * NQ + warp] = v;
+          __threadfence();
+        }
       }
       __syncthreads();
       if (tid == 0) {
-        LatScalars& W = P.sc[sg.lat];
-        const double* sum = red + 32 * NQ;
-        const double a = W.a, a2 = a * a, a6 = a2 * a2 * a2;
-        const double ck = 0.5 * L.inv_V / a6, cg = 0.5 * L.inv_V * L.inv_dx2 / a2;
-        PassSums E = {0, 0, 0, 0, 0, 0, 0};
-        if (RED > 0) {
-          double spre = 0, spost = 0, gg = 0, vs = 0;
-          if (RED == 1) {
-            spre = sum[0]; spost = sum[1]; gg = sum[2]; vs = sum[3];
-          } else {
-            for (int f = 0; f < NF; ++f) {
-              spre += sum[6 * f]; spost += sum[6 * f + 1]; gg += sum[6 * f + 2];
-            }
-            for (int t = 0; t < NPOT; ++t) vs += sum[6 * NF + t];
-          }
-          E.EKpre = spre * ck;
-          E.EKpost = spost * ck;
-          E.EG = gg * cg;
-          E.EV = vs * L.inv_V;
-        }
-        advance_scalars(P, L, W, E, RED > 0);
-        if (RED == 2) {
-          cl_energies_t& o = W.obs;
-          for (int k = 0; k < 4; ++k) {
-            o.EK[k] = o.EG[k] = o.EV[k] = 0.0;
-            o.mean_phi[k] = o.mean_phi2[k] = o.mean_pi[k] = o.mean_pi2[k] = 0.0;
-          }
-          o.EKA = o.EGA = 0.0;
-          for (int f = 0; f < NF; ++f) {
-            o.EK[f] = sum[6 * f + 1] * ck;
-            o.EG[f] = sum[6 * f + 2] * cg;
-            o.mean_phi[f] = sum[6 * f + 3] * L.inv_V;
-            o.mean_phi2[f] = sum[6 * f + 4] * L.inv_V;
-            o.mean_pi[f] = sum[6 * f + 5] * L.inv_V;
-            o.mean_pi2[f] = sum[6 * f + 1] * L.inv_V;
-          }
-          for (int t = 0; t < NPOT; ++t) o.EV[t] = sum[6 * NF + t] * L.inv_V;
-          o.nonfinite = (int64_t)sum[NQ - 1];
-          finish_obs(P, L, W);
-        }
-        advance_drift(P, L, W);
-        P.counters[sg.lat] = 0u;
+        const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
+        const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
+        flag[2] = sg.lat;
+        if (prev == nslot - 1u) pend[flag[3]++] = sg.lat;
       }
+      __syncthreads();
     }
-    __syncthreads();
+
+    // ---- end of the pass ----
+    if (multi && tid == 0) {  // this CTA's writes are done
+      __threadfence();
+      fence_proxy_async_global();
+      atomicAdd(&P.gsync[0], 1u);
+    }
+    {
+      const int npend = flag[3];
+      const PassStep pst = P.steps ? P.steps[pass] : PassStep{P.ck, P.wout, P.win, P.dnext};
+      for (int k = 0; k < npend; ++k) {
+        __threadfence();
+        run_tail(pend[k], pst);
+      }
+      __syncthreads();
+      if (tid == 0) flag[3] = 0;
+    }
   }
   return;
 

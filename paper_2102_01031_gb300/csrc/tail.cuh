@@ -3,9 +3,29 @@
 // measured volume averages.  FP64 throughout.
 #pragma once
 
+#include <cstddef>
+
 #include "common.cuh"
 
 namespace clg {
+
+static_assert(sizeof(ScalarState) == 13 * sizeof(double) && offsetof(LatScalars, pi2) == 12 * sizeof(double),
+              "ScalarState mirrors the leading members of LatScalars");
+
+// The evolving scalars of a lattice, read past L1 (another SM may have
+// written them earlier in the same launch), and written back.
+__device__ inline void load_state_cg(ScalarState& dst, const LatScalars* src) {
+  const double* s = reinterpret_cast<const double*>(src);
+  double* d = reinterpret_cast<double*>(&dst);
+#pragma unroll
+  for (int i = 0; i < 13; ++i) d[i] = __ldcg(s + i);
+}
+__device__ inline void store_state(LatScalars* dst, const ScalarState& src) {
+  const double* s = reinterpret_cast<const double*>(&src);
+  double* d = reinterpret_cast<double*>(dst);
+#pragma unroll
+  for (int i = 0; i < 13; ++i) d[i] = s[i];
+}
 
 // Energy sums of one pass for one lattice, already summed over the lattice.
 struct PassSums {
@@ -39,11 +59,13 @@ __device__ __forceinline__ double fixed_p(const LatConst& L) {
 }
 
 // Fixed power-law background, eq. ScaleFactorPowerLaw.
-__device__ __forceinline__ double a_fixed(const LatConst& L, const LatScalars& S, double eta) {
+template <class SS>
+__device__ __forceinline__ double a_fixed(const LatConst& L, const SS& S, double eta) {
   double p = fixed_p(L);
   return S.a0 * pow(1.0 + S.Hfix * (eta - S.eta0) / p, p);
 }
-__device__ __forceinline__ double H_fixed(const LatConst& L, const LatScalars& S, double eta) {
+template <class SS>
+__device__ __forceinline__ double H_fixed(const LatConst& L, const SS& S, double eta) {
   double p = fixed_p(L);
   return S.Hfix / (1.0 + S.Hfix * (eta - S.eta0) / p);
 }
@@ -60,7 +82,8 @@ __device__ __forceinline__ double kernel_a(const LatConst& L, double a, double E
 // Friedmann kicks of b (kick-out with the pre-kick momenta, then kick-in with
 // the post-kick momenta, as in the velocity-Verlet step), then the drift of a
 // by P.dnext and the drift coefficients of the next pass.
-__device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, LatScalars& S,
+template <class SS>
+__device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, SS& S,
                                        const PassSums& E, bool have_sums) {
   const double a = S.a;
   if (have_sums && L.expansion == CL_EXP_SELF) {
@@ -69,7 +92,8 @@ __device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, Lat
   }
 }
 
-__device__ inline void advance_drift(const PassArgs& P, const LatConst& L, LatScalars& S) {
+template <class SS>
+__device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S) {
   const double a = S.a;
   if (P.dnext != 0.0) {
     double an;
@@ -92,8 +116,8 @@ __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, LatSc
 }
 
 // Hubble-constraint monitor and energy bookkeeping of a measurement.
-__device__ inline void finish_obs(const PassArgs& P, const LatConst& L, LatScalars& S) {
-  cl_energies_t& o = S.obs;
+template <class SS>
+__device__ inline void finish_obs(const PassArgs& P, const LatConst& L, SS& S, cl_energies_t& o) {
   double rho = o.EKA + o.EGA;
   for (int k = 0; k < 4; ++k) rho += o.EK[k] + o.EG[k] + o.EV[k];
   o.rho = rho;

@@ -269,10 +269,27 @@ def test_degenerate_cases(P):
     assert np.array_equal(g3.get(0, 0), s)
 
 
-def test_kernel_launch_count(P):
+def test_kernel_launch_count_and_pass_timing(P):
     g = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 1, P.make_params(**C2S))
     n0 = g.launches()
+    g.enable_pass_timing(True)
     g.step(10)
     g.sync()
-    # VV4: three merged-kick passes per step, one opening and one closing pass
-    assert g.launches() - n0 == 3 * 10 + 1
+    g.enable_pass_timing(False)
+    # VV4: 30 passes (one opening, 29 merged kicks) in one cooperative launch,
+    # then the closing half kick
+    assert g.launches() - n0 == 2
+    ms, npass = g.pass_timing(reset=True)
+    assert npass == 31 and ms > 0.0
+
+
+def test_single_pass_launches_match_multi_pass(P):
+    """cl_step(1) repeatedly (separate launches) == cl_step(n) (one cooperative launch)."""
+    a = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 8, P.make_params(**dict(C2S, integrator=O.VV2)))
+    b = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 8, P.make_params(**dict(C2S, integrator=O.VV2)))
+    a.step(12)
+    for _ in range(12):
+        b.step(1)
+    for f in range(2):
+        for w in range(2):
+            assert np.array_equal(a.get(f, w), b.get(f, w))
