@@ -291,14 +291,15 @@ cl_status check_status(cl_ctx* c) {
 // then z) are cut into `grid` equal contiguous runs, one per CTA; a run is
 // split into segments at y-tile and lattice boundaries.  Odd CTAs march down
 // (and take their segments in reverse order) so that neighbouring runs reach
-// their shared boundary plane at the same time, when halo planes come from L2.
+// their shared boundary plane at the same time, when halo planes come from L2
+// (unless up_only: the U(1) pass carries values from the plane below).
 // Each CTA accumulates one partial-sum slot per lattice it touches; slots are
 // numbered lattice-major so that a lattice's slots are contiguous.
 struct LatTiles {
   int N, BY;
 };
 
-bool build_worklist(const std::vector<LatTiles>& lats, int grid, std::vector<Seg>& segs,
+bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, std::vector<Seg>& segs,
                     std::vector<int>& cta_first, std::vector<int>& slot_begin,
                     std::vector<int>& slot_end) {
   std::vector<long long> toff(lats.size() + 1, 0);
@@ -309,7 +310,7 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, std::vector<Seg
   cta_first.assign(grid + 1, 0);
   for (int cta = 0; cta < grid; ++cta) {
     const long long b = T * cta / grid, e = T * (cta + 1) / grid;
-    const int dir = (cta & 1) ? -1 : +1;
+    const int dir = (cta & 1) && !up_only ? -1 : +1;
     cta_first[cta] = (int)segs.size();
     size_t l = 0;
     for (long long t = b; t < e;) {
@@ -431,6 +432,8 @@ cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint
   if (p->expansion < CL_EXP_OFF || p->expansion > CL_EXP_FIXED)
     return fail(nullptr, CL_EINVAL, "unknown expansion mode %d", p->expansion);
   if (!(p->dt == p->dt)) return fail(nullptr, CL_EINVAL, "dt is NaN");
+  if (model == CL_MODEL_U1_HIGGS && !(p->gQ != 0.0 && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
+    return fail(nullptr, CL_EINVAL, "U(1) needs a finite nonzero gQ and f*/omega*");
   cl_ctx* c = new cl_ctx();
   c->model = model;
   c->N = N;
@@ -461,18 +464,27 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
   c->smem_optin = (size_t)optin;
   const int N = c->N;
-  // tile shape: full x-rows of N/VX threads, BY rows per CTA (BY divides N)
-  const int VX = 16 / c->esz;
+  // tile shape: full x-rows of N/VX threads, BY rows per CTA (BY divides N),
+  // the largest BY whose stage ring (at least 3 stages of BY + 2 rows of
+  // every array) fits in shared memory
+  const bool u1 = c->model == CL_MODEL_U1_HIGGS;
+  const int VX = u1 ? u1_vx(c->esz) : 16 / c->esz;
   const int TX = N / VX;
-  int BY = 0;
-  for (int by = std::min(N, 32 * CONSUMER_WARPS / TX); by >= 1; --by)
-    if (N % by == 0) { BY = by; break; }
-  if (BY == 0) return fail(c, CL_EUNSUPPORTED, "no tile shape for N=%d", N);
-  const int narr_pass = c->narr;
-  const size_t stage = ((size_t)(BY + 2) * N * narr_pass * c->esz + 127) / 128 * 128;
   const size_t extra = SM_TAIL_BYTES;  // mbarriers, release counts, offsets, sums, flags, copy info
-  int S = (int)std::min<size_t>(6, (c->smem_optin - extra) / stage);
-  if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for N=%d", N);
+  int BY = 0, S = 0;
+  size_t stage = 0;
+  for (int by = std::min(N, THREADS / TX); by >= 1 && TX <= THREADS; --by) {
+    if (N % by) continue;
+    const size_t st = ((size_t)(by + 2) * N * c->narr * c->esz + 127) / 128 * 128;
+    const int s = (int)std::min<size_t>(6, (c->smem_optin - extra) / st);
+    if (s >= 3) {
+      BY = by;
+      S = s;
+      stage = st;
+      break;
+    }
+  }
+  if (BY == 0) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   c->stages = S;
   c->stage_bytes = (unsigned)stage;
   c->smem_bytes = (size_t)S * stage + extra;
@@ -487,7 +499,7 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
   std::vector<Seg> segs;
   std::vector<int> cta, sbeg, send;
-  if (!build_worklist({LatTiles{N, BY}}, c->grid, segs, cta, sbeg, send))
+  if (!build_worklist({LatTiles{N, BY}}, c->grid, u1, segs, cta, sbeg, send))
     return fail(c, CL_EUNSUPPORTED, "work split needs more than %d segments per CTA", MAX_SEG_PER_CTA);
   c->nseg = (int)segs.size();
   c->nslot = send[0];

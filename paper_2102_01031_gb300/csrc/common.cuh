@@ -32,7 +32,7 @@ struct ScalarState {
   double cd, cdA;
   double apow1, apow3, apowm1;
   double a0, eta0, Hfix, rho0;
-  double pi2;
+  double pi2, pi2A;
 };
 
 // Per-lattice evolving scalars (device resident, FP64).
@@ -42,6 +42,7 @@ struct LatScalars {
   double apow1, apow3, apowm1;    // a^{1+alpha}, a^{3+alpha}, a^{alpha-1} at the current a
   double a0, eta0, Hfix, rho0;
   double pi2;                     // sum of pi^2 after the last kick (the next kick's pre-kick sum)
+  double pi2A;                    // the same for the U(1) link momenta
   cl_energies_t obs;              // last measurement
   int status, pad;
 };
@@ -54,6 +55,9 @@ struct Seg {
   int lat, ytile, z0, nz, dir, slot, flush, pad;
 };
 constexpr int MAX_SEG_PER_CTA = 16;
+
+// Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
+constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
 
 // What a refill needs to know about a segment, cached in shared memory.
 struct IssueInfo {

@@ -85,6 +85,7 @@ __global__ void init_scalars_kernel(const LatConst* Lc, LatScalars* Sc, const IC
   S.status = 0;
   S.rho0 = 0.0;
   S.pi2 = 0.0;
+  S.pi2A = 0.0;
   double kin = 0.0;
   for (int k = 0; k < A.nf; ++k) kin += 0.5 * A.dphi0[k] * A.dphi0[k];
   const double rho = kin / pow(S.a, 2.0 * al) + pot_hom(A);

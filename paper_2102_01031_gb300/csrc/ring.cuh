@@ -1,0 +1,236 @@
+// ring.cuh -- the plane ring of a DK pass, as device functions: the shared
+// memory behind the stages, the bulk copies that fill a stage with one z-plane
+// tile of every array, the release count whose last warp refills the stage,
+// the per-run flush of the sums into a partial-sum slot, and the lattice-wide
+// slot reduction that precedes the Friedmann update.
+//
+// A CTA's segments form one sequence of planes (each segment adds a halo
+// plane at both ends); plane g of pass p lives in stage (p * ptot + g) mod S.
+// A stage holds, for every array, the plane's BY rows of the segment's y-tile
+// plus one halo row on each side, each row complete in x.
+#pragma once
+
+#include "common.cuh"
+
+namespace clg {
+
+struct Ring {
+  unsigned char* stages;  // S stages of stage_bytes
+  uint64_t* full;         // one mbarrier per stage: all copies of the stage landed
+  unsigned* released;     // warps done with each stage
+  int* off;               // first plane of each segment, and the total
+  double* red;            // [33][NQ] reduction scratch
+  volatile int* flag;     // [0] timed out, [1] unused, [2] lattice of the last run, [3] #pending tails
+  int* pend;              // lattices whose Friedmann update this CTA runs
+  IssueInfo* info;        // per segment: what its refills copy
+  int S;
+  unsigned stage_bytes;
+};
+
+__device__ __forceinline__ Ring ring_view(unsigned char* smem, const PassArgs& P) {
+  Ring R;
+  R.S = P.stages;
+  R.stage_bytes = P.stage_bytes_max;
+  R.stages = smem;
+  unsigned char* tail = smem + (size_t)R.S * R.stage_bytes;
+  R.full = reinterpret_cast<uint64_t*>(tail + SM_FULL);
+  R.released = reinterpret_cast<unsigned*>(tail + SM_RELEASED);
+  R.off = reinterpret_cast<int*>(tail + SM_OFF);
+  R.red = reinterpret_cast<double*>(tail + SM_RED);
+  R.flag = reinterpret_cast<volatile int*>(tail + SM_FLAG);
+  R.pend = reinterpret_cast<int*>(tail + SM_FLAG + 16);
+  R.info = reinterpret_cast<IssueInfo*>(tail + SM_INFO);
+  return R;
+}
+
+// Thread 0: barriers, counts, flags, plane offsets and the copy info of the
+// CTA's `ns` segments starting at segs[sb].
+template <int NA>
+__device__ void ring_setup(const Ring& R, const PassArgs& P, int sb, int ns) {
+  for (int s = 0; s < R.S; ++s) {
+    mbar_init(&R.full[s], 1);
+    R.released[s] = 0u;
+  }
+  fence_mbar_init();
+  R.flag[0] = 0;
+  R.flag[1] = 0;
+  R.flag[2] = ns > 0 ? P.segs[sb].lat : 0;
+  R.flag[3] = 0;
+  R.off[0] = 0;
+  for (int i = 0; i < ns; ++i) {
+    const Seg& sg = P.segs[sb + i];
+    const LatConst& L = P.lat[sg.lat];
+    R.off[i + 1] = R.off[i] + sg.nz + 2;
+    IssueInfo& in = R.info[i];
+    in.z0 = sg.z0;
+    in.nz = sg.nz;
+    in.dir = sg.dir;
+    in.ylo = sg.ytile * L.BY;
+    in.N = L.N;
+    in.rows = L.BY + 2;
+    for (int a = 0; a < NA; ++a) {
+      in.src[0][a] = L.buf[0][a];
+      in.src[1][a] = L.buf[1][a];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ const T* ring_stage(const Ring& R, int s) {
+  return reinterpret_cast<const T*>(R.stages + (size_t)s * R.stage_bytes);
+}
+
+// Bulk copies of plane g (of the current pass) into its stage; rows that
+// wrap around the periodic y boundary are split into two runs.
+template <typename T, int NA>
+__device__ void ring_issue(const Ring& R, int g, int gbase, int parity) {
+  int i = 0;
+  while (g >= R.off[i + 1]) ++i;
+  const IssueInfo& in = R.info[i];
+  const int N = in.N, rows = in.rows, ylo = in.ylo, arr_elems = rows * N;
+  const int s = (gbase + g) % R.S;
+  T* st = reinterpret_cast<T*>(R.stages + (size_t)s * R.stage_bytes);
+  const int j = g - R.off[i];
+  int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
+  zp = zp < 0 ? zp + N : (zp >= N ? zp - N : zp);
+  const long long zoff = (long long)zp * N * N;
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(&R.full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
+  int r = 0;
+  while (r < rows) {
+    int g2 = ylo - 1 + r;
+    g2 = g2 < 0 ? g2 + N : (g2 >= N ? g2 - N : g2);
+    int run = 1;
+    while (r + run < rows && g2 + run < N) ++run;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+      bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N,
+               reinterpret_cast<const T*>(in.src[parity][a]) + zoff + (long long)g2 * N,
+               (uint32_t)(run * N * sizeof(T)), &R.full[s]);
+    r += run;
+  }
+}
+
+// A warp is done with plane g (in stage s); the last of the CTA's warps
+// refills s with plane g + S of the same pass.
+template <typename T, int NA>
+__device__ __forceinline__ void ring_release(const Ring& R, int g, int s, int gbase, int parity,
+                                             int ptot, int lane) {
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence_block();
+    const unsigned prev = atomicAdd(&R.released[s], 1u);
+    if (prev == CONSUMER_WARPS - 1u) {
+      R.released[s] = 0u;
+      if (g + R.S < ptot && !R.flag[0]) ring_issue<T, NA>(R, g + R.S, gbase, parity);
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void ring_wait(const Ring& R, int s, uint32_t par,
+                                          unsigned long long limit_ns) {
+  if (R.flag[0]) return;
+  if (!mbar_wait_bounded(&R.full[s], par, limit_ns)) R.flag[0] = 1;
+}
+
+__device__ __forceinline__ void ring_advance(int S, int& s, uint32_t& p) {
+  if (++s == S) {
+    s = 0;
+    p ^= 1u;
+  }
+}
+
+// End of a CTA's run on a lattice (all threads): warp partials of the NUSED
+// slots (accumulators acc[0..NACC), slot NQ-1 = non-finite count), a fixed
+// shuffle tree over the warps per slot into P.partials, and the lattice's
+// arrival count; the CTA that completes it queues the lattice's tail.
+// Returns false if a wait of this CTA had timed out.
+template <int NACC, int NUSED, typename T>
+__device__ bool ring_flush(const Ring& R, const PassArgs& P, const Seg& sg, Acc<T> (&acc)[NACC],
+                           float& nonfinite, int warp, int lane) {
+  if (NUSED > 0) {
+#pragma unroll
+    for (int k = 0; k < NUSED; ++k) {
+      double v = 0.0;
+      if (k < NACC) {
+        v = warp_sum(acc[k]);
+      } else if (k == NQ - 1) {
+        float c = nonfinite;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        v = (double)c;
+      }
+      if (lane == 0) R.red[warp * NQ + k] = v;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k].zero();
+  nonfinite = 0.f;
+  __syncthreads();
+  if (R.flag[0]) return false;
+  if (warp < NUSED) {
+    double v = lane < CONSUMER_WARPS ? R.red[lane * NQ + warp] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      P.partials[(size_t)sg.slot * NQ + warp] = v;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const LatConst& L = P.lat[sg.lat];
+    const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
+    const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
+    R.flag[2] = sg.lat;
+    if (prev == nslot - 1u) R.pend[R.flag[3]++] = sg.lat;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Lattice-wide sums of the first NUSED slots into red[32 * NQ + k]: warp k
+// strides its lanes over the lattice's slots, then a fixed shuffle tree, so
+// the order does not depend on timing.  All threads; ends with a barrier.
+template <int NUSED>
+__device__ void ring_slot_sums(const Ring& R, const PassArgs& P, const LatConst& L, int warp,
+                               int lane) {
+  if (warp < NUSED) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
+      s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) R.red[32 * NQ + warp] = s;
+  }
+  __syncthreads();
+}
+
+// Between two passes of one launch (thread 0): the previous pass's writes
+// are all done before any of its planes is read; the first planes of the
+// pass are issued; then the updated scalars are awaited.
+template <typename T, int NA>
+__device__ void ring_pass_start(const Ring& R, const PassArgs& P, int pass, int ptot, int parity) {
+  if (pass > 0) {
+    if (!R.flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
+      R.flag[0] = 1;
+    fence_proxy_async_global();
+  }
+  if (!R.flag[0])
+    for (int g = 0; g < R.S && g < ptot; ++g) ring_issue<T, NA>(R, g, pass * ptot, parity);
+  if (pass > 0 && !R.flag[0] &&
+      !wait_counter(&P.gsync[1], (unsigned)P.nlat * (unsigned)pass, P.wait_limit_ns))
+    R.flag[0] = 1;
+}
+
+// After a timed-out wait (thread 0): wait, bounded, for copies still in
+// flight so that none lands in shared memory after exit, and record it.
+__device__ inline void ring_drain(const Ring& R, const PassArgs& P) {
+  for (int s = 0; s < R.S; ++s)
+    for (int par = 0; par < 2; ++par) mbar_wait_bounded(&R.full[s], (uint32_t)par, 1000000ull);
+  P.sc[R.flag[2]].status = CL_ETIMEOUT;
+}
+
+}  // namespace clg

@@ -9,7 +9,8 @@
 
 namespace clg {
 
-static_assert(sizeof(ScalarState) == 13 * sizeof(double) && offsetof(LatScalars, pi2) == 12 * sizeof(double),
+constexpr int kStateWords = (int)(sizeof(ScalarState) / sizeof(double));
+static_assert(kStateWords == 14 && offsetof(LatScalars, pi2A) == 13 * sizeof(double),
               "ScalarState mirrors the leading members of LatScalars");
 
 // The evolving scalars of a lattice, read past L1 (another SM may have
@@ -18,13 +19,13 @@ __device__ inline void load_state_cg(ScalarState& dst, const LatScalars* src) {
   const double* s = reinterpret_cast<const double*>(src);
   double* d = reinterpret_cast<double*>(&dst);
 #pragma unroll
-  for (int i = 0; i < 13; ++i) d[i] = __ldcg(s + i);
+  for (int i = 0; i < kStateWords; ++i) d[i] = __ldcg(s + i);
 }
 __device__ inline void store_state(LatScalars* dst, const ScalarState& src) {
   const double* s = reinterpret_cast<const double*>(&src);
   double* d = reinterpret_cast<double*>(dst);
 #pragma unroll
-  for (int i = 0; i < 13; ++i) d[i] = s[i];
+  for (int i = 0; i < kStateWords; ++i) d[i] = s[i];
 }
 
 // Energy sums of one pass for one lattice, already summed over the lattice.
@@ -130,25 +131,6 @@ __device__ inline void finish_obs(const PassArgs& P, const LatConst& L, SS& S, c
   o.eta = S.eta;
   o.a = S.a;
   o.b = S.b;
-}
-
-// Block-wide FP64 sum of `vals[0..NQ)` over all threads into red[0..NQ).
-__device__ inline void block_reduce_nq(double (&vals)[NQ], double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double v = vals[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp * NQ + q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < NQ) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w * NQ + threadIdx.x];
-    red[32 * NQ + threadIdx.x] = s;
-  }
-  __syncthreads();
 }
 
 }  // namespace clg
