@@ -32,6 +32,9 @@
  *     first close the stream of kicks with a half kick (the manual's `sync`,
  *     Sec. 5.1), after which fields and momenta are at the same time.
  *   - One context is used by one host thread at a time.
+ *   - A context holds one lattice (cl_init) or an ensemble of lattices
+ *     (cl_ensemble_init); calls without a lattice argument act on lattice 0,
+ *     except cl_step / cl_step_h / cl_sync / cl_set_scalars, which act on all.
  */
 #ifndef CL_H
 #define CL_H
@@ -87,6 +90,10 @@ typedef struct {
   int b0_mode;                  /* 0: a'(t0) from homogeneous values (Sec. 5.2); 1: from averages */
   int precision;                /* CL_FP64 or CL_FP32 */
   void* stream;                 /* cudaStream_t */
+  int autotune;                 /* nonzero: pick each lattice size's tile height by timing
+                                   candidates on the device (cached per model, precision, N) */
+  int tile_by;                  /* > 0: force this tile height (rows per CTA tile) for every
+                                   lattice; 0: autotune or the built-in choice */
 } cl_params;
 
 /* Volume averages at a synchronised time (eqs. EK_EG_EV, energy-contrib). */
@@ -170,6 +177,42 @@ const char* cl_last_error(const cl_ctx* ctx);  /* never NULL; ctx may be NULL */
  * returned by cl_pass_timing.  Disabled by default (no events recorded). */
 cl_status cl_enable_pass_timing(cl_ctx* ctx, int enable);
 cl_status cl_pass_timing(cl_ctx* ctx, double* ms_total, int64_t* passes, int reset);
+
+/* ---------------------------------------------------------------------------
+ * Ensembles (batched independent lattices).  `count` lattices of one model and
+ * one set of run parameters, lattice l with its own size Ns[l] (any admissible
+ * N, sizes may differ), kIRs[l] and seeds[l], evolved together: every DK pass
+ * of cl_step covers all lattices in one persistent cooperative launch (the
+ * plane tasks of all lattices split evenly by site count over the SMs, each
+ * lattice with its own scale factor, volume averages and Friedmann update),
+ * recorded in a CUDA graph on first use and replayed afterwards.  Lattice
+ * results do not depend on the ensemble they are part of beyond the rounding
+ * of their FP64 reductions.  The IC generator, spectra and transfers of
+ * lattice l are those of a single lattice with (Ns[l], kIRs[l], seeds[l]).
+ * Returns as cl_init; count must be 1 .. CL_MAX_LATTICES.
+ */
+#define CL_MAX_LATTICES 4096
+cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, const double* kIRs,
+                           double alpha, const uint64_t* seeds, const cl_params* p);
+int cl_ensemble_size(const cl_ctx* ctx);
+
+/* Per-lattice forms of cl_energies, cl_get_state, cl_set_state and
+ * cl_get_scalars (lat in 0 .. count-1, CL_EINVAL otherwise). */
+cl_status cl_lattice_energies(cl_ctx* ctx, int lat, cl_energies_t* out);
+cl_status cl_lattice_get_state(cl_ctx* ctx, int lat, int field, int what, double* host_out);
+cl_status cl_lattice_set_state(cl_ctx* ctx, int lat, int field, int what, const double* host_in);
+cl_status cl_lattice_scalars(cl_ctx* ctx, int lat, double* eta, double* a, double* b);
+
+/* Tile shape the passes use for lattice `lat`: its N, its tile height BY
+ * (rows of one CTA tile) and the context's number of ring stages. */
+cl_status cl_lattice_tile(cl_ctx* ctx, int lat, int* N, int* BY, int* stages);
+
+/* Ensemble-averaged binned spectrum: delta_b of cl_spectrum averaged over
+ * the lattices lats[0 .. nl) (which must share N and kIR); k and mult as in
+ * cl_spectrum (identical for those lattices).  Synchronises the stream. */
+cl_status cl_ensemble_spectrum(cl_ctx* ctx, const int* lats, int nl, int field, int what,
+                               double dk_bin, double* k, double* delta, int64_t* mult, int cap,
+                               int* nbins);
 
 /* ---------------------------------------------------------------------------
  * Volume averages without device allocation.  The paper has no counterpart:

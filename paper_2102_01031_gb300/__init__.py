@@ -32,6 +32,8 @@ EXPORTS = (
     "cl_spectrum", "cl_get_state", "cl_set_state", "cl_get_scalars", "cl_set_scalars",
     "cl_state_bytes", "cl_upload_state", "cl_download_state", "cl_nfields", "cl_kernel_launches",
     "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
+    "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
+    "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
 )
 
 
@@ -61,6 +63,8 @@ class Params(ctypes.Structure):
         ("b0_mode", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("autotune", ctypes.c_int),
+        ("tile_by", ctypes.c_int),
     ]
 
 
@@ -129,6 +133,18 @@ def lib():
     L.cl_pass_timing.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ip]
     L.cl_volume_averages_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ip, ctypes.POINTER(vp), vp, vp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.cl_ensemble_init.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.POINTER(ctypes.c_int), dp,
+                                   ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Params)]
+    L.cl_ensemble_size.argtypes = [vp]
+    L.cl_lattice_energies.argtypes = [vp, ip, ctypes.POINTER(Energies)]
+    L.cl_lattice_get_state.argtypes = [vp, ip, ip, ip, dp]
+    L.cl_lattice_set_state.argtypes = [vp, ip, ip, ip, dp]
+    L.cl_lattice_scalars.argtypes = [vp, ip, dp, dp, dp]
+    L.cl_lattice_tile.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.cl_ensemble_spectrum.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ip, ip, ctypes.c_double, dp, dp,
+                                       i64p, ip, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -160,6 +176,8 @@ def make_params(**kw):
     p.expansion = kw.pop("expansion", EXP_OFF)
     p.b0_mode = kw.pop("b0_mode", 0)
     p.precision = kw.pop("precision", FP64)
+    p.autotune = int(kw.pop("autotune", 0))
+    p.tile_by = int(kw.pop("tile_by", 0))
     st = kw.pop("stream", None)
     p.stream = ctypes.c_void_p(int(st) if st else 0)
     if kw:
@@ -269,6 +287,106 @@ class Lattice:
     def download(self, host_ptr, nbytes):
         _check(self.L, self.h, self.L.cl_download_state(self.h, ctypes.c_void_p(host_ptr), nbytes),
                "cl_download_state")
+
+    def launches(self):
+        return int(self.L.cl_kernel_launches(self.h))
+
+    def enable_pass_timing(self, on=True):
+        _check(self.L, self.h, self.L.cl_enable_pass_timing(self.h, 1 if on else 0), "timing")
+
+    def pass_timing(self, reset=False):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self.L, self.h, self.L.cl_pass_timing(self.h, ctypes.byref(ms), ctypes.byref(n),
+                                                     1 if reset else 0), "timing")
+        return ms.value, n.value
+
+
+class Ensemble:
+    """An ensemble context (cl_ensemble_init ... cl_free): lattices of sizes
+    Ns[l], kIRs[l] and seeds[l] advanced together by one launch per call."""
+
+    def __init__(self, model, Ns, kIRs, alpha, seeds, params):
+        self.L = lib()
+        self.Ns = [int(n) for n in Ns]
+        n = len(self.Ns)
+        if len(kIRs) != n or len(seeds) != n:
+            raise ValueError("Ns, kIRs and seeds need one entry per lattice")
+        self.params = params
+        ns = (ctypes.c_int * n)(*self.Ns)
+        ks = (ctypes.c_double * n)(*[float(k) for k in kIRs])
+        ss = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+        h = ctypes.c_void_p()
+        rc = self.L.cl_ensemble_init(ctypes.byref(h), model, n, ns, ks, alpha, ss, ctypes.byref(params))
+        if rc != CL_OK:
+            raise ClError(rc, "cl_ensemble_init: " + self.L.cl_last_error(None).decode(errors="replace"))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cl_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def size(self):
+        return self.L.cl_ensemble_size(self.h)
+
+    def step(self, n, h=None):
+        rc = self.L.cl_step(self.h, n) if h is None else self.L.cl_step_h(self.h, n, h)
+        _check(self.L, self.h, rc, "cl_step")
+
+    def sync(self):
+        _check(self.L, self.h, self.L.cl_sync(self.h), "cl_sync")
+
+    def energies(self, lat, allow_nonfinite=False):
+        e = Energies()
+        rc = self.L.cl_lattice_energies(self.h, lat, ctypes.byref(e))
+        if not (allow_nonfinite and rc == CL_ENONFINITE):
+            _check(self.L, self.h, rc, "cl_lattice_energies")
+        return e.as_dict()
+
+    def get(self, lat, field, what=0):
+        N = self.Ns[lat]
+        out = np.empty(N ** 3, dtype=np.float64)
+        _check(self.L, self.h, self.L.cl_lattice_get_state(self.h, lat, field, what, _dp(out)),
+               "cl_lattice_get_state")
+        return out.reshape(N, N, N)  # [z][y][x]
+
+    def set(self, lat, field, what, arr):
+        N = self.Ns[lat]
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+        if a.size != N ** 3:
+            raise ValueError("need %d values" % N ** 3)
+        _check(self.L, self.h, self.L.cl_lattice_set_state(self.h, lat, field, what, _dp(a)),
+               "cl_lattice_set_state")
+
+    def scalars(self, lat):
+        e, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.L, self.h, self.L.cl_lattice_scalars(self.h, lat, ctypes.byref(e), ctypes.byref(a),
+                                                         ctypes.byref(b)), "cl_lattice_scalars")
+        return e.value, a.value, b.value
+
+    def tile(self, lat):
+        n, by, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.L, self.h, self.L.cl_lattice_tile(self.h, lat, ctypes.byref(n), ctypes.byref(by),
+                                                      ctypes.byref(st)), "cl_lattice_tile")
+        return n.value, by.value, st.value
+
+    def spectrum_mean(self, lats, field, what=0, dk_bin=1.0):
+        cap = 4096
+        k = np.zeros(cap)
+        d = np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        ls = (ctypes.c_int * len(lats))(*[int(x) for x in lats])
+        rc = self.L.cl_ensemble_spectrum(self.h, ls, len(lats), field, what, dk_bin, _dp(k), _dp(d),
+                                         m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap,
+                                         ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_ensemble_spectrum")
+        n = nb.value
+        return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
     def launches(self):
         return int(self.L.cl_kernel_launches(self.h))

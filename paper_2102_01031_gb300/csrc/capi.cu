@@ -1,8 +1,9 @@
-// capi.cu -- the C ABI of include/cl.h: context management, the work list of
-// the DK passes, the kick/drift schedule of the integrators and the launches.
-// Host code only marshals parameters and orders launches; every step of the
-// method (initial conditions, FFTs, passes, reductions, Friedmann updates,
-// spectra) runs in the kernels of this library.
+// capi.cu -- the C ABI of include/cl.h: contexts holding one lattice or an
+// ensemble of lattices, the work list of the DK passes, the kick/drift
+// schedule of the integrators, CUDA-graph replay of multi-pass launches, and
+// the tile-shape autotuner.  Host code only marshals parameters and orders
+// launches; every step of the method (initial conditions, FFTs, passes,
+// reductions, Friedmann updates, spectra) runs in the kernels of this library.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,7 +11,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "cl.h"
@@ -32,6 +36,7 @@ cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
 cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
 cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
                         cudaStream_t);
+cudaError_t launch_spec_mean(const double*, int, int, double*, cudaStream_t);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
 cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
                                  void*, long long, int, cudaStream_t);
@@ -43,29 +48,55 @@ __global__ void b_from_obs_kernel(const LatConst*, LatScalars*);
 
 using namespace clg;
 
+namespace {
+
+// One lattice of a context (host view).
+struct LatHost {
+  int N = 0, BY = 0;
+  long long V = 0;
+  double kIR = 0.0, dx = 0.0;
+  uint64_t seed = 0;
+  void* slab = nullptr;  // 2 buffers x narr arrays of V values, array-major
+};
+
+// A multi-pass launch recorded in a CUDA graph, replayed when the same
+// passes are launched again from the same buffer parity.
+struct GraphEntry {
+  std::vector<PassStep> steps;
+  int parity, red, write, set_rho0;
+  const void* dev_steps;  // the device copy of the weights the graph reads
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
 struct cl_ctx {
-  int model, N, nf, narr, fp32, esz;
-  long long V;
-  double kIR, dx, alpha;
+  int model = 0, nf = 0, narr = 0, fp32 = 0, esz = 0, nlat = 0;
+  double alpha = 0.0;
   cl_params p;
-  cudaStream_t stream;
-  int dev, nsm;
-  size_t smem_optin;
+  cudaStream_t stream = nullptr;      // the caller's stream (may be the legacy default stream)
+  cudaStream_t cap_stream = nullptr;  // private stream that records graphs
+  int dev = 0, nsm = 0;
+  size_t smem_optin = 0;
+  std::vector<LatHost> lats;
+  std::vector<LatConst> hlat;
+  long long vmax = 0;
   // device memory
-  void* slab = nullptr;            // 2 x narr lattice arrays
-  LatConst* d_lat = nullptr;
-  LatScalars* d_sc = nullptr;
+  LatConst* d_lat = nullptr;       // [nlat]
+  LatScalars* d_sc = nullptr;      // [nlat]
   Seg* d_segs = nullptr;
   int* d_cta = nullptr;
-  double* d_part = nullptr;
-  unsigned* d_cnt = nullptr;
-  double* d_tmp = nullptr;         // scratch for conversions / spectra (V doubles)
-  double2* d_cplx = nullptr;       // scratch complex (2 V)
-  double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk) + output
+  double* d_part = nullptr;        // [nslot][NQ]
+  unsigned* d_cnt = nullptr;       // [nlat]
+  double* d_tmp = nullptr;         // scratch for conversions / monitors (vmax doubles)
+  double2* d_cplx = nullptr;       // scratch complex (2 vmax)
+  double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk), per-lattice bins, mean
+  int spec_lats = 0;               // lattices d_spec has room for
   unsigned* d_gsync = nullptr;     // arrival counters of multi-pass launches
   bool coop = false;               // multi-pass cooperative launches possible
+  bool graphs = true;              // record multi-pass launches in CUDA graphs
   std::vector<std::pair<std::vector<PassStep>, void*>> step_cache;
-  LatConst hlat;
+  std::vector<GraphEntry> graph_cache;
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
@@ -139,15 +170,16 @@ void fft_radices(int N, FftPlan& pl) {
   while (m % 3 == 0) { pl.rad[pl.nrad++] = 3; m /= 3; }
 }
 
-void* arr_ptr(cl_ctx* c, int parity, int a) {
-  return (char*)c->slab + ((size_t)parity * c->narr + a) * (size_t)c->V * c->esz;
+void* arr_ptr(cl_ctx* c, int lat, int parity, int a) {
+  const LatHost& L = c->lats[lat];
+  return (char*)L.slab + ((size_t)parity * c->narr + a) * (size_t)L.V * c->esz;
 }
 
-cl_status fft3d(cl_ctx* c, double2* data, int sign) {
+cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
   FftPlan pl;
-  pl.N = c->N;
+  pl.N = N;
   pl.sign = sign;
-  fft_radices(c->N, pl);
+  fft_radices(N, pl);
   for (int axis = 0; axis < 3; ++axis) {
     pl.axis = axis;
     CU(launch_fft_axis(data, pl, c->stream));
@@ -156,15 +188,86 @@ cl_status fft3d(cl_ctx* c, double2* data, int sign) {
   return CL_OK;
 }
 
-PassKernel pick_kernel(cl_ctx* c, int red) {
+PassKernel pick_kernel(const cl_ctx* c, int red) {
   if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red);
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
 
-// Launch `n` passes of the given weights.  One pass: a plain launch.  Several:
-// one cooperative launch of the same kernel (all CTAs resident) that runs
-// them back to back, its per-pass weights read from a device copy of `st`
-// (cached by content) and its two arrival counters zeroed first.
+int tile_vx(int model, int esz) { return model == CL_MODEL_U1_HIGGS ? u1_vx(esz) : 16 / esz; }
+
+// Bytes of one stage (BY + 2 rows of every array), 128-byte aligned.
+size_t stage_size(int N, int BY, int narr, int esz) {
+  return ((size_t)(BY + 2) * N * narr * esz + 127) / 128 * 128;
+}
+
+// Tile heights BY admissible for N: BY divides N, the BY rows of N/VX
+// threads fit in one CTA, and at least 3 stages fit in shared memory; the
+// tallest first.
+std::vector<int> tile_candidates(int model, int narr, int esz, int N, size_t smem_optin) {
+  std::vector<int> out;
+  const int TX = N / tile_vx(model, esz);
+  if (TX > THREADS) return out;
+  for (int by = std::min(N, THREADS / TX); by >= 1; --by) {
+    if (N % by) continue;
+    if ((smem_optin - SM_TAIL_BYTES) / stage_size(N, by, narr, esz) >= 3) out.push_back(by);
+  }
+  return out;
+}
+
+// Device copy of pass weights, cached by content.
+cl_status device_steps(cl_ctx* c, const PassStep* st, int n, const PassStep** out) {
+  std::vector<PassStep> key(st, st + n);
+  for (auto& e : c->step_cache)
+    if (e.first.size() == key.size() && memcmp(e.first.data(), key.data(), n * sizeof(PassStep)) == 0) {
+      *out = static_cast<const PassStep*>(e.second);
+      return CL_OK;
+    }
+  void* d = nullptr;
+  if (c->step_cache.size() >= 8) {
+    CU(cudaStreamSynchronize(c->stream));  // an evicted copy may still be read by a queued launch
+    // graphs recorded with the evicted copy must not be replayed
+    const void* gone = c->step_cache.front().second;
+    for (size_t i = 0; i < c->graph_cache.size();) {
+      if (c->graph_cache[i].dev_steps == gone) {
+        cudaGraphExecDestroy(c->graph_cache[i].exec);
+        c->graph_cache.erase(c->graph_cache.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    cudaFree(c->step_cache.front().second);
+    c->step_cache.erase(c->step_cache.begin());
+  }
+  CU(cudaMalloc(&d, n * sizeof(PassStep)));
+  CU(cudaMemcpy(d, key.data(), n * sizeof(PassStep), cudaMemcpyHostToDevice));
+  c->step_cache.push_back(std::make_pair(key, d));
+  *out = static_cast<const PassStep*>(d);
+  return CL_OK;
+}
+
+// The two nodes of a multi-pass launch: zero the arrival counters, then the
+// cooperative kernel.
+cl_status enqueue_multi(cl_ctx* c, PassKernel k, PassArgs& A, cudaStream_t st) {
+  CU(cudaMemsetAsync(c->d_gsync, 0, 2 * sizeof(unsigned), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = c->smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CU(cudaLaunchKernelEx(&cfg, k, A));
+  return CL_OK;
+}
+
+// Launch `n` passes of the given weights over every lattice of the context.
+// One pass: a plain launch.  Several: one cooperative launch of the same
+// kernel (all CTAs resident) that runs them back to back, reading the
+// per-pass weights from a device copy; it is recorded in a CUDA graph the
+// first time and the graph is replayed for the same passes later.
 cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write, int set_rho0) {
   PassKernel k = pick_kernel(c, red);
   if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
@@ -185,34 +288,52 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   A.set_rho0 = set_rho0;
   A.stages = c->stages;
   A.stage_bytes_max = c->stage_bytes;
-  A.nlat = 1;
+  A.nlat = c->nlat;
   A.wait_limit_ns = 2000000000ull;  // 2 s
   A.steps = nullptr;
   A.npass = 1;
   A.gsync = nullptr;
   const bool multi = n > 1 && c->coop;
+  cudaGraphExec_t exec = nullptr;
   if (multi) {
-    // device copy of the weights, cached by content
-    std::vector<PassStep> key(st, st + n);
     const PassStep* dev = nullptr;
-    for (auto& e : c->step_cache)
-      if (e.first.size() == key.size() && memcmp(e.first.data(), key.data(), n * sizeof(PassStep)) == 0)
-        dev = static_cast<const PassStep*>(e.second);
-    if (!dev) {
-      void* d = nullptr;
-      if (c->step_cache.size() >= 8) {
-        cudaFree(c->step_cache.front().second);
-        c->step_cache.erase(c->step_cache.begin());
-      }
-      CU(cudaMalloc(&d, n * sizeof(PassStep)));
-      CU(cudaMemcpy(d, key.data(), n * sizeof(PassStep), cudaMemcpyHostToDevice));
-      c->step_cache.push_back(std::make_pair(key, d));
-      dev = static_cast<const PassStep*>(d);
-    }
+    cl_status s = device_steps(c, st, n, &dev);
+    if (s != CL_OK) return s;
     A.steps = dev;
     A.npass = n;
     A.gsync = c->d_gsync;
-    CU(cudaMemsetAsync(c->d_gsync, 0, 2 * sizeof(unsigned), c->stream));
+    if (c->graphs) {
+      for (auto& g : c->graph_cache)
+        if (g.parity == c->parity && g.red == red && g.write == write && g.set_rho0 == set_rho0 &&
+            g.dev_steps == (const void*)dev && g.steps.size() == (size_t)n &&
+            memcmp(g.steps.data(), st, n * sizeof(PassStep)) == 0)
+          exec = g.exec;
+      if (!exec) {
+        // record on the private stream; a failed recording falls back to direct launches
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          const bool enq = enqueue_multi(c, k, A, c->cap_stream) == CL_OK;
+          ok = cudaStreamEndCapture(c->cap_stream, &graph) == cudaSuccess && enq;
+        }
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (!ok) {
+          if (exec) cudaGraphExecDestroy(exec);
+          exec = nullptr;
+          c->graphs = false;
+        } else {
+          if (c->graph_cache.size() >= 8) {
+            CU(cudaStreamSynchronize(c->stream));
+            cudaGraphExecDestroy(c->graph_cache.front().exec);
+            c->graph_cache.erase(c->graph_cache.begin());
+          }
+          c->graph_cache.push_back(GraphEntry{std::vector<PassStep>(st, st + n), c->parity, red, write,
+                                              set_rho0, (const void*)dev, exec});
+        }
+      }
+    }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
@@ -226,10 +347,11 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
     }
     CU(cudaEventRecord(e0, c->stream));
   }
-  if (multi) {
-    void* args[] = {&A};
-    CU(cudaLaunchCooperativeKernel((const void*)k, dim3(c->grid), dim3(THREADS), args, c->smem_bytes,
-                                   c->stream));
+  if (multi && exec) {
+    CU(cudaGraphLaunch(exec, c->stream));
+  } else if (multi) {
+    cl_status s = enqueue_multi(c, k, A, c->stream);
+    if (s != CL_OK) return s;
   } else {
     for (int i = 0; i < n; ++i) {
       A.ck = st[i].ck;
@@ -279,19 +401,23 @@ cl_status measure(cl_ctx* c, int set_rho0) {
   return CL_OK;
 }
 
+// Device-side status of every lattice (a bounded wait that gave up).
 cl_status check_status(cl_ctx* c) {
-  int st = 0;
-  CU(cudaMemcpyAsync(&st, &c->d_sc->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<LatScalars> h(c->nlat);
+  CU(cudaMemcpyAsync(h.data(), c->d_sc, c->nlat * sizeof(LatScalars), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  if (st == CL_ETIMEOUT) return fail(c, CL_ETIMEOUT, "a bounded device wait timed out");
+  for (int l = 0; l < c->nlat; ++l)
+    if (h[l].status == CL_ETIMEOUT)
+      return fail(c, CL_ETIMEOUT, "a bounded device wait timed out (lattice %d)", l);
   return CL_OK;
 }
 
 // Work list.  The plane tasks of all lattices (lattice-major, then y-tile,
-// then z) are cut into `grid` equal contiguous runs, one per CTA; a run is
-// split into segments at y-tile and lattice boundaries.  Odd CTAs march down
-// (and take their segments in reverse order) so that neighbouring runs reach
-// their shared boundary plane at the same time, when halo planes come from L2
+// then z; a task is BY rows x N sites of one plane) are cut into `grid`
+// contiguous runs of equal site count, one per CTA; a run is split into
+// segments at y-tile and lattice boundaries.  Odd CTAs march down (and take
+// their segments in reverse order) so that neighbouring runs reach their
+// shared boundary plane at the same time, when halo planes come from L2
 // (unless up_only: the U(1) pass carries values from the plane below).
 // Each CTA accumulates one partial-sum slot per lattice it touches; slots are
 // numbered lattice-major so that a lattice's slots are contiguous.
@@ -302,14 +428,29 @@ struct LatTiles {
 bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, std::vector<Seg>& segs,
                     std::vector<int>& cta_first, std::vector<int>& slot_begin,
                     std::vector<int>& slot_end) {
-  std::vector<long long> toff(lats.size() + 1, 0);
-  for (size_t l = 0; l < lats.size(); ++l)
-    toff[l + 1] = toff[l] + (long long)(lats[l].N / lats[l].BY) * lats[l].N;
-  const long long T = toff.back();
+  const size_t nl = lats.size();
+  std::vector<long long> toff(nl + 1, 0);
+  std::vector<double> coff(nl + 1, 0.0);  // sites before each lattice
+  for (size_t l = 0; l < nl; ++l) {
+    const long long nt = (long long)(lats[l].N / lats[l].BY) * lats[l].N;
+    toff[l + 1] = toff[l] + nt;
+    coff[l + 1] = coff[l] + (double)nt * lats[l].BY * lats[l].N;
+  }
+  // first task of CTA k: where the running site count reaches k/grid of the total
+  auto boundary = [&](int k) -> long long {
+    if (k <= 0) return 0;
+    if (k >= grid) return toff[nl];
+    const double target = coff[nl] * (double)k / (double)grid;
+    size_t l = 0;
+    while (l + 1 < nl && coff[l + 1] <= target) ++l;
+    const double per = (double)lats[l].BY * lats[l].N;
+    const long long t = toff[l] + (long long)std::llround((target - coff[l]) / per);
+    return std::min(std::max(t, toff[l]), toff[l + 1]);
+  };
   segs.clear();
   cta_first.assign(grid + 1, 0);
   for (int cta = 0; cta < grid; ++cta) {
-    const long long b = T * cta / grid, e = T * (cta + 1) / grid;
+    const long long b = boundary(cta), e = std::max(b, boundary(cta + 1));
     const int dir = (cta & 1) && !up_only ? -1 : +1;
     cta_first[cta] = (int)segs.size();
     size_t l = 0;
@@ -338,10 +479,10 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, s
       segs[i].flush = (i + 1 == (int)segs.size() || segs[i + 1].lat != segs[i].lat) ? 1 : 0;
   }
   cta_first[grid] = (int)segs.size();
-  slot_begin.assign(lats.size(), 0);
-  slot_end.assign(lats.size(), 0);
+  slot_begin.assign(nl, 0);
+  slot_end.assign(nl, 0);
   int next = 0;
-  for (size_t l = 0; l < lats.size(); ++l) {
+  for (size_t l = 0; l < nl; ++l) {
     slot_begin[l] = next;
     for (int cta = 0; cta < grid; ++cta) {
       bool used = false;
@@ -358,6 +499,61 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, s
 }
 
 }  // namespace
+
+// Autotuner: the tile height of each (model, precision, N) is the candidate
+// with the shortest measured DK pass on a scratch lattice of that size (two
+// warm-up steps, then eight VV2 steps timed with CUDA events), kept for the
+// life of the process.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+}  // namespace
+
+static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
+  const auto key = std::make_tuple(c->model, c->esz, N);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *by_out = it->second;
+      return CL_OK;
+    }
+  }
+  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
+  if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
+  if (cand.size() > 4) cand.resize(4);
+  int best = cand[0];
+  double best_t = 1e300;
+  for (int by : cand) {
+    cl_params q = c->p;
+    q.autotune = 0;
+    q.tile_by = by;
+    q.integrator = CL_VV2;
+    q.stream = c->stream;
+    cl_ctx* t = nullptr;
+    const uint64_t seed = 1;
+    cl_status s = cl_ensemble_init(&t, c->model, 1, &N, &kIR, c->alpha, &seed, &q);
+    if (s != CL_OK) return fail(c, s, "autotune: %s", cl_last_error(nullptr));
+    double ms = 0.0;
+    int64_t np = 0;
+    s = cl_step(t, 2);
+    if (s == CL_OK) s = cl_enable_pass_timing(t, 1);
+    if (s == CL_OK) s = cl_step(t, 8);
+    if (s == CL_OK) s = cl_pass_timing(t, &ms, &np, 1);
+    if (s == CL_OK) s = cl_sync(t);
+    cl_free(t);
+    if (s != CL_OK) return fail(c, s, "autotune: timing failed");
+    const double per = np > 0 ? ms / (double)np : 1e300;
+    if (per < best_t) {
+      best_t = per;
+      best = by;
+    }
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  *by_out = best;
+  return CL_OK;
+}
 
 namespace clg {
 // Small scalar kernels (host-side setup lives here to keep the ABI in one unit).
@@ -381,23 +577,28 @@ __global__ void b_from_obs_kernel(const LatConst* Lc, LatScalars* S) {
 }
 }  // namespace clg
 
+static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const uint64_t* seeds);
+
 extern "C" {
 
 const char* cl_last_error(const cl_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 
 int cl_nfields(const cl_ctx* c) { return c ? c->narr / 2 : -1; }
 
+int cl_ensemble_size(const cl_ctx* c) { return c ? c->nlat : -1; }
+
 int64_t cl_kernel_launches(const cl_ctx* c) { return c ? (int64_t)c->launches : -1; }
 
 cl_status cl_free(cl_ctx* c) {
   if (!c) return CL_OK;
-  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
   for (auto& pr : c->ev_pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  cudaFree(c->slab);
+  for (auto& g : c->graph_cache) cudaGraphExecDestroy(g.exec);
+  for (auto& L : c->lats) cudaFree(L.slab);
   cudaFree(c->d_lat);
   cudaFree(c->d_sc);
   cudaFree(c->d_segs);
@@ -409,21 +610,26 @@ cl_status cl_free(cl_ctx* c) {
   cudaFree(c->d_spec);
   cudaFree(c->d_gsync);
   for (auto& e : c->step_cache) cudaFree(e.second);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return CL_OK;
 }
 
-static cl_status init_impl(cl_ctx* c, uint64_t seed);
-
-cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
-                  const cl_params* p) {
+cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, const double* kIRs,
+                           double alpha, const uint64_t* seeds, const cl_params* p) {
   if (!out) return fail(nullptr, CL_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!p) return fail(nullptr, CL_EINVAL, "params is NULL");
+  if (!p || !Ns || !kIRs || !seeds) return fail(nullptr, CL_EINVAL, "NULL argument");
+  if (count < 1 || count > CL_MAX_LATTICES)
+    return fail(nullptr, CL_EINVAL, "count=%d: need 1..%d lattices", count, CL_MAX_LATTICES);
   if (model < CL_MODEL_LPHI4 || model > CL_MODEL_U1_HIGGS)
     return fail(nullptr, CL_EINVAL, "unknown model %d", model);
-  if (!good_N(N)) return fail(nullptr, CL_EINVAL, "N=%d: need 8 <= N <= 512, N %% 8 == 0, factors 2,3", N);
-  if (!(kIR > 0.0) || !std::isfinite(alpha)) return fail(nullptr, CL_EINVAL, "bad kIR/alpha");
+  for (int l = 0; l < count; ++l) {
+    if (!good_N(Ns[l]))
+      return fail(nullptr, CL_EINVAL, "N=%d: need 8 <= N <= 512, N %% 8 == 0, factors 2,3", Ns[l]);
+    if (!(kIRs[l] > 0.0) || !std::isfinite(kIRs[l])) return fail(nullptr, CL_EINVAL, "bad kIR");
+  }
+  if (!std::isfinite(alpha)) return fail(nullptr, CL_EINVAL, "bad alpha");
   if (p->precision != CL_FP64 && p->precision != CL_FP32)
     return fail(nullptr, CL_EINVAL, "unknown precision %d", p->precision);
   const int ig = p->integrator;
@@ -434,20 +640,18 @@ cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint
   if (!(p->dt == p->dt)) return fail(nullptr, CL_EINVAL, "dt is NaN");
   if (model == CL_MODEL_U1_HIGGS && !(p->gQ != 0.0 && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
     return fail(nullptr, CL_EINVAL, "U(1) needs a finite nonzero gQ and f*/omega*");
+  if (p->tile_by < 0) return fail(nullptr, CL_EINVAL, "tile_by must be >= 0");
   cl_ctx* c = new cl_ctx();
   c->model = model;
-  c->N = N;
-  c->V = (long long)N * N * N;
   c->nf = model == CL_MODEL_LPHI4 ? 1 : 2;
   c->narr = model == CL_MODEL_U1_HIGGS ? 10 : 2 * c->nf;
   c->fp32 = p->precision == CL_FP32;
   c->esz = c->fp32 ? 4 : 8;
-  c->kIR = kIR;
-  c->dx = 2.0 * M_PI / ((double)N * kIR);
+  c->nlat = count;
   c->alpha = alpha;
   c->p = *p;
   c->stream = (cudaStream_t)p->stream;
-  cl_status s = init_impl(c, seed);
+  cl_status s = init_impl(c, Ns, kIRs, seeds);
   if (s != CL_OK) {
     g_init_err = c->err;
     cl_free(c);
@@ -457,63 +661,86 @@ cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint
   return CL_OK;
 }
 
-static cl_status init_impl(cl_ctx* c, uint64_t seed) {
+cl_status cl_init(cl_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
+                  const cl_params* p) {
+  return cl_ensemble_init(out, model, 1, &N, &kIR, alpha, &seed, p);
+}
+
+}  // extern "C"
+
+static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const uint64_t* seeds) {
   CU(cudaGetDevice(&c->dev));
   CU(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
   int optin = 0;
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
   c->smem_optin = (size_t)optin;
-  const int N = c->N;
-  // tile shape: full x-rows of N/VX threads, BY rows per CTA (BY divides N),
-  // the largest BY whose stage ring (at least 3 stages of BY + 2 rows of
-  // every array) fits in shared memory
+  CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   const bool u1 = c->model == CL_MODEL_U1_HIGGS;
-  const int VX = u1 ? u1_vx(c->esz) : 16 / c->esz;
-  const int TX = N / VX;
-  const size_t extra = SM_TAIL_BYTES;  // mbarriers, release counts, offsets, sums, flags, copy info
-  int BY = 0, S = 0;
+  // lattices and their tile heights: full x-rows of N/VX threads, BY rows
+  // per CTA (BY divides N); given, autotuned, or the tallest that leaves at
+  // least 3 stages of BY + 2 rows of every array in shared memory
+  c->lats.resize(c->nlat);
+  std::vector<LatTiles> tiles;
   size_t stage = 0;
-  for (int by = std::min(N, THREADS / TX); by >= 1 && TX <= THREADS; --by) {
-    if (N % by) continue;
-    const size_t st = ((size_t)(by + 2) * N * c->narr * c->esz + 127) / 128 * 128;
-    const int s = (int)std::min<size_t>(6, (c->smem_optin - extra) / st);
-    if (s >= 3) {
-      BY = by;
-      S = s;
-      stage = st;
-      break;
+  for (int l = 0; l < c->nlat; ++l) {
+    LatHost& L = c->lats[l];
+    L.N = Ns[l];
+    L.V = (long long)L.N * L.N * L.N;
+    L.kIR = kIRs[l];
+    L.dx = 2.0 * M_PI / ((double)L.N * L.kIR);
+    L.seed = seeds[l];
+    c->vmax = std::max(c->vmax, L.V);
+    const std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, L.N, c->smem_optin);
+    if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", L.N);
+    if (c->p.tile_by > 0) {
+      if (std::find(cand.begin(), cand.end(), c->p.tile_by) == cand.end())
+        return fail(c, CL_EINVAL, "tile_by=%d is not a tile height for N=%d", c->p.tile_by, L.N);
+      L.BY = c->p.tile_by;
+    } else if (c->p.autotune) {
+      cl_status s = tune_tile(c, L.N, L.kIR, &L.BY);
+      if (s != CL_OK) return s;
+    } else {
+      L.BY = cand[0];
     }
+    stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
+    tiles.push_back(LatTiles{L.N, L.BY});
   }
-  if (BY == 0) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
+  const int S = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / stage);
+  if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the stage ring");
   c->stages = S;
   c->stage_bytes = (unsigned)stage;
-  c->smem_bytes = (size_t)S * stage + extra;
+  c->smem_bytes = (size_t)S * stage + SM_TAIL_BYTES;
   for (int red = 0; red < 3; ++red) {
     PassKernel k = pick_kernel(c, red);
     if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
     CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)c->smem_bytes));
   }
-  // work list
-  const long long tasks = (long long)(N / BY) * N;
+  // work list: one CTA per SM, at least 8 plane tasks each
+  long long tasks = 0;
+  for (const LatTiles& t : tiles) tasks += (long long)(t.N / t.BY) * t.N;
   c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
   std::vector<Seg> segs;
   std::vector<int> cta, sbeg, send;
-  if (!build_worklist({LatTiles{N, BY}}, c->grid, u1, segs, cta, sbeg, send))
+  if (!build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send))
     return fail(c, CL_EUNSUPPORTED, "work split needs more than %d segments per CTA", MAX_SEG_PER_CTA);
   c->nseg = (int)segs.size();
-  c->nslot = send[0];
+  c->nslot = send[c->nlat - 1];
   // device memory
-  const size_t arr_bytes = (size_t)c->V * c->esz;
-  CU(cudaMalloc(&c->slab, 2 * (size_t)c->narr * arr_bytes));
-  CU(cudaMemsetAsync(c->slab, 0, 2 * (size_t)c->narr * arr_bytes, c->stream));
-  CU(cudaMalloc(&c->d_lat, sizeof(LatConst)));
-  CU(cudaMalloc(&c->d_sc, sizeof(LatScalars)));
-  CU(cudaMemsetAsync(c->d_sc, 0, sizeof(LatScalars), c->stream));
+  for (int l = 0; l < c->nlat; ++l) {
+    LatHost& L = c->lats[l];
+    const size_t bytes = 2 * (size_t)c->narr * L.V * c->esz;
+    CU(cudaMalloc(&L.slab, bytes));
+    CU(cudaMemsetAsync(L.slab, 0, bytes, c->stream));
+  }
+  CU(cudaMalloc(&c->d_lat, c->nlat * sizeof(LatConst)));
+  CU(cudaMalloc(&c->d_sc, c->nlat * sizeof(LatScalars)));
+  CU(cudaMemsetAsync(c->d_sc, 0, c->nlat * sizeof(LatScalars), c->stream));
   CU(cudaMalloc(&c->d_segs, segs.size() * sizeof(Seg)));
   CU(cudaMalloc(&c->d_cta, cta.size() * sizeof(int)));
   CU(cudaMalloc(&c->d_part, (size_t)c->nslot * NQ * sizeof(double)));
-  CU(cudaMalloc(&c->d_cnt, sizeof(unsigned)));
+  CU(cudaMalloc(&c->d_cnt, c->nlat * sizeof(unsigned)));
+  CU(cudaMemsetAsync(c->d_cnt, 0, c->nlat * sizeof(unsigned), c->stream));
   CU(cudaMalloc(&c->d_gsync, 2 * sizeof(unsigned)));
   {
     int coop = 0, nb = 0;
@@ -522,90 +749,104 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
                                                      THREADS, c->smem_bytes));
     c->coop = coop && (long long)nb * c->nsm >= c->grid;
   }
-  CU(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned), c->stream));
-  LatConst& L = c->hlat;
-  memset(&L, 0, sizeof(L));
-  L.N = N;
-  L.BY = BY;
-  L.YT = N / BY;
-  L.model = c->model;
-  L.nf = c->nf;
-  L.narr = c->narr;
-  L.expansion = c->p.expansion;
-  L.slot_begin = sbeg[0];
-  L.slot_end = send[0];
-  L.esz = c->esz;
-  L.int_alpha = (c->alpha == std::floor(c->alpha) && std::fabs(c->alpha) <= 4.0) ? 1 : 0;
-  L.inv_V = 1.0 / (double)c->V;
-  L.inv_dx2 = 1.0 / (c->dx * c->dx);
-  L.V = c->V;
-  L.dx = c->dx;
-  L.alpha = c->alpha;
-  L.q = c->p.q;
-  L.lam = c->p.lam;
-  L.v = c->p.v;
-  L.gQ = c->p.gQ;
-  L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
-  L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
-  L.omega_eos = c->p.omega_eos;
-  for (int par = 0; par < 2; ++par)
-    for (int a = 0; a < c->narr; ++a) L.buf[par][a] = arr_ptr(c, par, a);
-  CU(cudaMemcpyAsync(c->d_lat, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
-  CU(cudaMemcpyAsync(c->d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice,
-                     c->stream));
-  CU(cudaMemcpyAsync(c->d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice,
-                     c->stream));
-  // initial conditions
-  ICArgs A;
-  memset(&A, 0, sizeof(A));
-  for (int k = 0; k < 4; ++k) {
-    A.phi0[k] = c->p.phi0[k];
-    A.dphi0[k] = c->p.dphi0[k];
+  c->hlat.resize(c->nlat);
+  for (int l = 0; l < c->nlat; ++l) {
+    const LatHost& H = c->lats[l];
+    LatConst& L = c->hlat[l];
+    memset(&L, 0, sizeof(L));
+    L.N = H.N;
+    L.BY = H.BY;
+    L.YT = H.N / H.BY;
+    L.model = c->model;
+    L.nf = c->nf;
+    L.narr = c->narr;
+    L.expansion = c->p.expansion;
+    L.slot_begin = sbeg[l];
+    L.slot_end = send[l];
+    L.esz = c->esz;
+    L.int_alpha = (c->alpha == std::floor(c->alpha) && std::fabs(c->alpha) <= 4.0) ? 1 : 0;
+    L.inv_V = 1.0 / (double)H.V;
+    L.inv_dx2 = 1.0 / (H.dx * H.dx);
+    if (u1) {
+      L.u1_gd = c->p.gQ * H.dx;
+      L.u1_cJ = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar * c->p.gQ / H.dx;
+      L.u1_cC = 1.0 / (c->p.gQ * H.dx * H.dx * H.dx);
+    }
+    L.V = H.V;
+    L.dx = H.dx;
+    L.alpha = c->alpha;
+    L.q = c->p.q;
+    L.lam = c->p.lam;
+    L.v = c->p.v;
+    L.gQ = c->p.gQ;
+    L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+    L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
+    L.omega_eos = c->p.omega_eos;
+    // one slab per lattice: array a of buffer p starts a * V values after
+    // array 0 of that buffer (the U(1) pass relies on it)
+    for (int par = 0; par < 2; ++par)
+      for (int a = 0; a < c->narr; ++a) L.buf[par][a] = arr_ptr(c, l, par, a);
   }
-  A.amp2 = c->p.fluct_amp2;
-  A.kcut = c->p.kcut;
-  A.kIR = c->kIR;
-  A.H0 = c->p.H0;
-  A.q = c->p.q;
-  A.lam = c->p.lam;
-  A.v = c->p.v;
-  A.seed = seed;
-  A.model = c->model;
-  A.nf = c->nf;
-  CU(launch_init_scalars(c->d_lat, c->d_sc, A, c->stream));
-  ++c->launches;
-  CU(cudaMalloc(&c->d_cplx, 2 * (size_t)c->V * sizeof(double2)));
-  CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)c->V, 1 << 16) * sizeof(double)));
-  double2* F = c->d_cplx;
-  double2* G = c->d_cplx + c->V;
-  for (int f = 0; f < c->nf; ++f) {
-    CU(cudaMemsetAsync(c->d_cplx, 0, 2 * (size_t)c->V * sizeof(double2), c->stream));
-    CU(launch_ic_modes(F, G, c->d_lat, c->d_sc, A, f, c->V, c->stream));
+  CU(cudaMemcpyAsync(c->d_lat, c->hlat.data(), c->nlat * sizeof(LatConst), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  // initial conditions, lattice by lattice
+  CU(cudaMalloc(&c->d_cplx, 2 * (size_t)c->vmax * sizeof(double2)));
+  CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)c->vmax, 1 << 16) * sizeof(double)));
+  for (int l = 0; l < c->nlat; ++l) {
+    const LatHost& H = c->lats[l];
+    const LatConst* dL = c->d_lat + l;
+    LatScalars* dS = c->d_sc + l;
+    ICArgs A;
+    memset(&A, 0, sizeof(A));
+    for (int k = 0; k < 4; ++k) {
+      A.phi0[k] = c->p.phi0[k];
+      A.dphi0[k] = c->p.dphi0[k];
+    }
+    A.amp2 = c->p.fluct_amp2;
+    A.kcut = c->p.kcut;
+    A.kIR = H.kIR;
+    A.H0 = c->p.H0;
+    A.q = c->p.q;
+    A.lam = c->p.lam;
+    A.v = c->p.v;
+    A.seed = H.seed;
+    A.model = c->model;
+    A.nf = c->nf;
+    CU(launch_init_scalars(dL, dS, A, c->stream));
     ++c->launches;
-    cl_status s = fft3d(c, F, +1);
-    if (s != CL_OK) return s;
-    s = fft3d(c, G, +1);
-    if (s != CL_OK) return s;
-    CU(launch_ic_assemble(c->fp32, arr_ptr(c, 0, 2 * f), arr_ptr(c, 0, 2 * f + 1), F, G, c->d_lat,
-                          c->d_sc, c->p.phi0[f], c->p.dphi0[f], c->V, c->stream));
-    ++c->launches;
-  }
-  if (c->model == CL_MODEL_U1_HIGGS) {
-    // links start at zero (eq. Inflc1); their momenta solve the lattice Gauss law
-    double2* rho = c->d_cplx;
-    double2* E = c->d_cplx + c->V;
-    CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, 0, c->dx, c->fp32, nullptr, c->V, 0, c->stream));
-    ++c->launches;
-    cl_status s = fft3d(c, rho, -1);
-    if (s != CL_OK) return s;
-    for (int i = 0; i < 3; ++i) {
-      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, c->dx, c->fp32, nullptr, c->V, 1, c->stream));
+    double2* F = c->d_cplx;
+    double2* G = c->d_cplx + H.V;
+    for (int f = 0; f < c->nf; ++f) {
+      CU(cudaMemsetAsync(c->d_cplx, 0, 2 * (size_t)H.V * sizeof(double2), c->stream));
+      CU(launch_ic_modes(F, G, dL, dS, A, f, H.V, c->stream));
       ++c->launches;
-      s = fft3d(c, E, +1);
+      cl_status s = fft3d(c, H.N, F, +1);
       if (s != CL_OK) return s;
-      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, c->dx, c->fp32, arr_ptr(c, 0, 2 * (2 + i) + 1),
-                              c->V, 2, c->stream));
+      s = fft3d(c, H.N, G, +1);
+      if (s != CL_OK) return s;
+      CU(launch_ic_assemble(c->fp32, arr_ptr(c, l, 0, 2 * f), arr_ptr(c, l, 0, 2 * f + 1), F, G, dL, dS,
+                            c->p.phi0[f], c->p.dphi0[f], H.V, c->stream));
       ++c->launches;
+    }
+    if (u1) {
+      // links start at zero (eq. Inflc1); their momenta solve the lattice Gauss law
+      double2* rho = c->d_cplx;
+      double2* E = c->d_cplx + H.V;
+      CU(launch_u1_gauss_init(dL, 0, rho, E, H.N, 0, H.dx, c->fp32, nullptr, H.V, 0, c->stream));
+      ++c->launches;
+      cl_status s = fft3d(c, H.N, rho, -1);
+      if (s != CL_OK) return s;
+      for (int i = 0; i < 3; ++i) {
+        CU(launch_u1_gauss_init(dL, 0, rho, E, H.N, i, H.dx, c->fp32, nullptr, H.V, 1, c->stream));
+        ++c->launches;
+        s = fft3d(c, H.N, E, +1);
+        if (s != CL_OK) return s;
+        CU(launch_u1_gauss_init(dL, 0, rho, E, H.N, i, H.dx, c->fp32, arr_ptr(c, l, 0, 2 * (2 + i) + 1),
+                                H.V, 2, c->stream));
+        ++c->launches;
+      }
     }
   }
   c->parity = 0;
@@ -613,9 +854,11 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   cl_status s = measure(c, 1);
   if (s != CL_OK) return s;
   if (c->p.expansion == CL_EXP_SELF && c->p.b0_mode == 1) {
-    b_from_obs_kernel<<<1, 32, 0, c->stream>>>(c->d_lat, c->d_sc);
-    CHECK_LAUNCH();
-    ++c->launches;
+    for (int l = 0; l < c->nlat; ++l) {
+      b_from_obs_kernel<<<1, 32, 0, c->stream>>>(c->d_lat + l, c->d_sc + l);
+      CHECK_LAUNCH();
+      ++c->launches;
+    }
     c->obs_valid = false;
     s = measure(c, 1);
     if (s != CL_OK) return s;
@@ -623,6 +866,8 @@ static cl_status init_impl(cl_ctx* c, uint64_t seed) {
   CU(cudaStreamSynchronize(c->stream));
   return check_status(c);
 }
+
+extern "C" {
 
 cl_status cl_step_h(cl_ctx* c, int n, double h) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
@@ -666,16 +911,23 @@ cl_status cl_sync(cl_ctx* c) {
   return close_stream(c);
 }
 
-cl_status cl_energies(cl_ctx* c, cl_energies_t* out) {
+static cl_status bad_lat(cl_ctx* c, int lat) {
+  return fail(c, CL_EINVAL, "lattice %d out of range (ensemble of %d)", lat, c->nlat);
+}
+
+cl_status cl_lattice_energies(cl_ctx* c, int lat, cl_energies_t* out) {
   if (!c || !out) return fail(c, CL_EINVAL, "NULL argument");
+  if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
   cl_status s = measure(c, 0);
   if (s != CL_OK) return s;
-  CU(cudaMemcpyAsync(out, &c->d_sc->obs, sizeof(cl_energies_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(out, &c->d_sc[lat].obs, sizeof(cl_energies_t), cudaMemcpyDeviceToHost, c->stream));
   s = check_status(c);
   if (s != CL_OK) return s;
   if (out->nonfinite > 0) return fail(c, CL_ENONFINITE, "%lld non-finite momenta", (long long)out->nonfinite);
   return CL_OK;
 }
+
+cl_status cl_energies(cl_ctx* c, cl_energies_t* out) { return cl_lattice_energies(c, 0, out); }
 
 static cl_status array_index(cl_ctx* c, int field, int what, int* a) {
   if (what != 0 && what != 1) return fail(c, CL_EINVAL, "what must be 0 or 1");
@@ -684,41 +936,54 @@ static cl_status array_index(cl_ctx* c, int field, int what, int* a) {
   return CL_OK;
 }
 
-cl_status cl_get_state(cl_ctx* c, int field, int what, double* host_out) {
+cl_status cl_lattice_get_state(cl_ctx* c, int lat, int field, int what, double* host_out) {
   if (!c || !host_out) return fail(c, CL_EINVAL, "NULL argument");
-  int a;
+  if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
+  int a = 0;
   cl_status s = array_index(c, field, what, &a);
   if (s != CL_OK) return s;
   s = close_stream(c);
   if (s != CL_OK) return s;
-  CU(launch_convert(c->fp32, 1, arr_ptr(c, c->parity, a), c->d_tmp, c->V, c->stream));
+  const long long V = c->lats[lat].V;
+  CU(launch_convert(c->fp32, 1, arr_ptr(c, lat, c->parity, a), c->d_tmp, V, c->stream));
   ++c->launches;
-  CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)c->V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return check_status(c);
 }
 
-cl_status cl_set_state(cl_ctx* c, int field, int what, const double* host_in) {
+cl_status cl_lattice_set_state(cl_ctx* c, int lat, int field, int what, const double* host_in) {
   if (!c || !host_in) return fail(c, CL_EINVAL, "NULL argument");
-  int a;
+  if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
+  int a = 0;
   cl_status s = array_index(c, field, what, &a);
   if (s != CL_OK) return s;
   s = close_stream(c);
   if (s != CL_OK) return s;
-  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)c->V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, c->parity, a), c->V, c->stream));
+  const long long V = c->lats[lat].V;
+  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, lat, c->parity, a), V, c->stream));
   ++c->launches;
   CU(cudaStreamSynchronize(c->stream));
   c->obs_valid = false;
   return CL_OK;
 }
 
-cl_status cl_get_scalars(cl_ctx* c, double* eta, double* a, double* b) {
+cl_status cl_get_state(cl_ctx* c, int field, int what, double* host_out) {
+  return cl_lattice_get_state(c, 0, field, what, host_out);
+}
+
+cl_status cl_set_state(cl_ctx* c, int field, int what, const double* host_in) {
+  return cl_lattice_set_state(c, 0, field, what, host_in);
+}
+
+cl_status cl_lattice_scalars(cl_ctx* c, int lat, double* eta, double* a, double* b) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
   double v[3];
-  CU(cudaMemcpyAsync(v, c->d_sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(v, &c->d_sc[lat], 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   if (a) *a = v[0];
   if (b) *b = v[1];
@@ -726,14 +991,20 @@ cl_status cl_get_scalars(cl_ctx* c, double* eta, double* a, double* b) {
   return check_status(c);
 }
 
+cl_status cl_get_scalars(cl_ctx* c, double* eta, double* a, double* b) {
+  return cl_lattice_scalars(c, 0, eta, a, b);
+}
+
 cl_status cl_set_scalars(cl_ctx* c, double eta, double a, double b) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (!(a > 0.0)) return fail(c, CL_EINVAL, "a must be positive");
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
-  set_scalars_kernel<<<1, 32, 0, c->stream>>>(c->d_lat, c->d_sc, eta, a, b);
-  CHECK_LAUNCH();
-  ++c->launches;
+  for (int l = 0; l < c->nlat; ++l) {
+    set_scalars_kernel<<<1, 32, 0, c->stream>>>(c->d_lat + l, c->d_sc + l, eta, a, b);
+    CHECK_LAUNCH();
+    ++c->launches;
+  }
   c->obs_valid = false;
   s = measure(c, 1);
   if (s != CL_OK) return s;
@@ -741,32 +1012,62 @@ cl_status cl_set_scalars(cl_ctx* c, double eta, double a, double b) {
   return check_status(c);
 }
 
-cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, double* delta,
-                      int64_t* mult, int cap, int* nbins) {
-  if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+cl_status cl_lattice_tile(cl_ctx* c, int lat, int* N, int* BY, int* stages) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
+  if (N) *N = c->lats[lat].N;
+  if (BY) *BY = c->lats[lat].BY;
+  if (stages) *stages = c->stages;
+  return CL_OK;
+}
+
+cl_status cl_ensemble_spectrum(cl_ctx* c, const int* lats, int nl, int field, int what, double dk_bin,
+                               double* k, double* delta, int64_t* mult, int cap, int* nbins) {
+  if (!c || !lats || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+  if (nl < 1 || nl > c->nlat) return fail(c, CL_EINVAL, "need 1..%d lattices", c->nlat);
   if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
-  int a;
+  for (int i = 0; i < nl; ++i) {
+    if (lats[i] < 0 || lats[i] >= c->nlat) return bad_lat(c, lats[i]);
+    const LatHost& A = c->lats[lats[i]];
+    const LatHost& B = c->lats[lats[0]];
+    if (A.N != B.N || A.kIR != B.kIR) return fail(c, CL_EINVAL, "averaged lattices differ in N or kIR");
+  }
+  int a = 0;
   cl_status s = array_index(c, field, what, &a);
   if (s != CL_OK) return s;
-  const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  const LatHost& H = c->lats[lats[0]];
+  const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
   *nbins = nb;
   if (nb > cap) return fail(c, CL_EINVAL, "cap %d < %d bins", cap, nb);
   if (nb > 2048) return fail(c, CL_EINVAL, "too many bins (dk_bin too small)");
   s = close_stream(c);
   if (s != CL_OK) return s;
-  double2* F = c->d_cplx;
-  CU(launch_to_complex(c->fp32, arr_ptr(c, c->parity, a), F, c->V, c->stream));
-  ++c->launches;
-  s = fft3d(c, F, -1);
-  if (s != CL_OK) return s;
   const int nblk = 2 * c->nsm;
-  if (!c->d_spec) CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + 3 * 2048) * sizeof(double)));
+  if (c->spec_lats < nl) {
+    CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_spec);
+    c->d_spec = nullptr;
+    c->spec_lats = 0;
+    CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + (size_t)(nl + 1) * 3 * 2048) * sizeof(double)));
+    c->spec_lats = nl;
+  }
   double* part = c->d_spec;
-  double* outb = c->d_spec + (size_t)3 * 2048 * nblk;
-  CU(launch_bins(F, c->N, dk_bin, nb, nblk, part, c->kIR, c->dx, outb, c->stream));
-  c->launches += 2;
+  double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [nl][3 nb]: k, delta, mult
+  double* mean = bins + (size_t)nl * 3 * nb;
+  double2* F = c->d_cplx;
+  for (int i = 0; i < nl; ++i) {
+    const int l = lats[i];
+    CU(launch_to_complex(c->fp32, arr_ptr(c, l, c->parity, a), F, c->lats[l].V, c->stream));
+    ++c->launches;
+    s = fft3d(c, H.N, F, -1);
+    if (s != CL_OK) return s;
+    CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins + (size_t)i * 3 * nb, c->stream));
+    c->launches += 2;
+  }
+  CU(launch_spec_mean(bins, nl, nb, mean, c->stream));
+  ++c->launches;
   std::vector<double> h(3 * nb);
-  CU(cudaMemcpyAsync(h.data(), outb, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(h.data(), mean, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   for (int b = 0; b < nb; ++b) {
     k[b] = h[b];
@@ -774,6 +1075,12 @@ cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, 
     mult[b] = (int64_t)h[2 * nb + b];
   }
   return check_status(c);
+}
+
+cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, double* delta,
+                      int64_t* mult, int cap, int* nbins) {
+  const int l0 = 0;
+  return cl_ensemble_spectrum(c, &l0, 1, field, what, dk_bin, k, delta, mult, cap, nbins);
 }
 
 cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
@@ -784,7 +1091,7 @@ cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* r
   if (s != CL_OK) return s;
   const int nblk = 2 * c->nsm;
   double* part = c->d_tmp;
-  CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->V, c->stream));
+  CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));
   c->launches += 2;
   double h[4];
   CU(cudaMemcpyAsync(h, part + 3 * nblk, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -798,30 +1105,34 @@ cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* r
 
 cl_status cl_state_bytes(cl_ctx* c, size_t* bytes) {
   if (!c || !bytes) return fail(c, CL_EINVAL, "NULL argument");
-  *bytes = (size_t)c->narr * c->V * c->esz;
+  *bytes = (size_t)c->narr * c->lats[0].V * c->esz;
   return CL_OK;
 }
 
 cl_status cl_upload_state(cl_ctx* c, const void* host, size_t bytes) {
   if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
-  if (bytes != (size_t)c->narr * c->V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
+  const long long V = c->lats[0].V;
+  if (bytes != (size_t)c->narr * V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
-  const size_t ab = (size_t)c->V * c->esz;
+  const size_t ab = (size_t)V * c->esz;
   for (int a = 0; a < c->narr; ++a)
-    CU(cudaMemcpyAsync(arr_ptr(c, c->parity, a), (const char*)host + a * ab, ab, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(arr_ptr(c, 0, c->parity, a), (const char*)host + a * ab, ab, cudaMemcpyHostToDevice,
+                       c->stream));
   c->obs_valid = false;
   return CL_OK;
 }
 
 cl_status cl_download_state(cl_ctx* c, void* host, size_t bytes) {
   if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
-  if (bytes != (size_t)c->narr * c->V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
+  const long long V = c->lats[0].V;
+  if (bytes != (size_t)c->narr * V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
-  const size_t ab = (size_t)c->V * c->esz;
+  const size_t ab = (size_t)V * c->esz;
   for (int a = 0; a < c->narr; ++a)
-    CU(cudaMemcpyAsync((char*)host + a * ab, arr_ptr(c, c->parity, a), ab, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync((char*)host + a * ab, arr_ptr(c, 0, c->parity, a), ab, cudaMemcpyDeviceToHost,
+                       c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return CL_OK;
 }

@@ -23,6 +23,7 @@ struct LatConst {
   long long V;
   double dx, alpha, q, lam, v, gQ, fo2, fm2, omega_eos;
   double inv_V, inv_dx2;
+  double u1_gd, u1_cJ, u1_cC;  // U(1): gQ dx, (f_s/omega_s)^2 gQ/dx, 1/(gQ dx^3)
   void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
 };
 
@@ -54,7 +55,7 @@ struct LatScalars {
 struct Seg {
   int lat, ytile, z0, nz, dir, slot, flush, pad;
 };
-constexpr int MAX_SEG_PER_CTA = 16;
+constexpr int MAX_SEG_PER_CTA = 32;
 
 // Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
 constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
@@ -69,7 +70,7 @@ struct IssueInfo {
 constexpr size_t SM_FULL = 0;                                   // 8 mbarriers
 constexpr size_t SM_RELEASED = 64;                              // 8 release counts
 constexpr size_t SM_OFF = 128;                                  // MAX_SEG_PER_CTA + 1 plane offsets
-constexpr size_t SM_RED = 256;                                  // 33 x NQ doubles
+constexpr size_t SM_RED = (SM_OFF + 4 * (MAX_SEG_PER_CTA + 1) + 127) / 128 * 128;  // 33 x NQ doubles
 constexpr size_t SM_FLAG = SM_RED + 33 * NQ * 8;                // 4 ints + pending tails
 constexpr size_t SM_INFO = (SM_FLAG + 16 + 4 * MAX_SEG_PER_CTA + 127) / 128 * 128;  // IssueInfo[]
 constexpr size_t SM_TAIL_BYTES = SM_INFO + MAX_SEG_PER_CTA * sizeof(IssueInfo);

@@ -409,6 +409,23 @@ cudaError_t launch_to_complex(int fp32, const void* f, double2* out, long long V
   return cudaGetLastError();
 }
 
+// Ensemble mean of binned spectra: rows [nl][3 nb] (k, delta, mult) of
+// lattices that share N and kIR; k and mult are those of the first.
+__global__ void spec_mean_kernel(const double* rows, int nl, int nb, double* out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double s = 0.0;
+  for (int l = 0; l < nl; ++l) s += rows[(size_t)l * 3 * nb + nb + b];
+  out[b] = rows[b];
+  out[nb + b] = s / (double)nl;
+  out[2 * nb + b] = rows[2 * nb + b];
+}
+
+cudaError_t launch_spec_mean(const double* rows, int nl, int nb, double* out, cudaStream_t st) {
+  spec_mean_kernel<<<(nb + 127) / 128, 128, 0, st>>>(rows, nl, nb, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bins(const double2* F, int N, double dk, int nb, int nblk, double* part,
                         double kIR, double dx, double* out, cudaStream_t st) {
   bin_partial_kernel<<<nblk, 256, 3 * nb * sizeof(double), st>>>(F, N, dk, nb, part);

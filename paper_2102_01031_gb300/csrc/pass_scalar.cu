@@ -301,13 +301,20 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       const int arr_elems = (BY + 2) * N;
       const long long NN = (long long)N * N;
       const int g0 = off[i];
-      const LatScalars* SC = &P.sc[sg.lat];
-      const double cd64 = __ldcg(&SC->cd);
-      const T cd = (T)cd64;
-      const bool drifting = cd64 != 0.0;
-      const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
-      const T A1 = (T)(ckp * __ldcg(&SC->apow1) * L.inv_dx2);
-      const T A3 = (T)(ckp * __ldcg(&SC->apow3));
+      // coefficients of the segment: FP64 products formed by one lane (the
+      // FP64 pipe is narrow) and broadcast in the storage precision
+      T cf[3];
+      if (lane == 0) {
+        const LatScalars* SC = &P.sc[sg.lat];
+        const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
+        cf[0] = (T)__ldcg(&SC->cd);
+        cf[1] = (T)(ckp * __ldcg(&SC->apow1) * L.inv_dx2);
+        cf[2] = (T)(ckp * __ldcg(&SC->apow3));
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
+      const T cd = cf[0], A1 = cf[1], A3 = cf[2];
+      const bool drifting = cd != T(0);
       const T q = (T)L.q;
       const unsigned amask = __ballot_sync(0xffffffffu, active);
       T* dst[NA];

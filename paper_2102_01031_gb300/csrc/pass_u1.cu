@@ -127,19 +127,27 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const int ae = (BY + 2) * N;  // elements of one array in a stage
       const long long NN = (long long)N * N;
       const int g0 = R.off[i];
-      const LatScalars* SC = &P.sc[sg.lat];
-      const double cd64 = __ldcg(&SC->cd), cdA64 = __ldcg(&SC->cdA);
-      const T cd = (T)cd64, cdA = (T)cdA64;
-      const bool drifting = cd64 != 0.0 || cdA64 != 0.0;
-      const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
-      const double ap1 = __ldcg(&SC->apow1), ap3 = __ldcg(&SC->apow3), apm1 = __ldcg(&SC->apowm1);
-      const double gQ = L.gQ, dx = L.dx;
-      const T A1 = (T)(ckp * ap1 * L.inv_dx2);
-      const T A3 = (T)(ckp * ap3);
-      const T AJ = (T)(ckp * ap1 * L.fo2 * gQ / dx);  // (2 gQ/dx) Im[...] = (gQ/dx)(phi_0 u_1 - phi_1 u_0)
-      const T AC = (T)(-ckp * apm1 / (gQ * dx * dx * dx));
-      const T gd = (T)(gQ * dx);
-      const T lam = (T)L.lam, v2 = (T)(L.v * L.v);
+      // coefficients of the segment: FP64 products formed by one lane (the
+      // FP64 pipe is narrow) and broadcast in the storage precision
+      T cf[8];
+      if (lane == 0) {
+        const LatScalars* SC = &P.sc[sg.lat];
+        const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
+        const double ap1 = __ldcg(&SC->apow1);
+        cf[0] = (T)__ldcg(&SC->cd);
+        cf[1] = (T)__ldcg(&SC->cdA);
+        cf[2] = (T)(ckp * ap1 * L.inv_dx2);
+        cf[3] = (T)(ckp * __ldcg(&SC->apow3));
+        cf[4] = (T)(ckp * ap1 * L.u1_cJ);   // (2 gQ/dx) Im[...] = (gQ/dx)(phi_0 u_1 - phi_1 u_0)
+        cf[5] = (T)(-ckp * __ldcg(&SC->apowm1) * L.u1_cC);
+        cf[6] = (T)L.u1_gd;
+        cf[7] = (T)(L.v * L.v);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
+      const T cd = cf[0], cdA = cf[1], A1 = cf[2], A3 = cf[3], AJ = cf[4], AC = cf[5], gd = cf[6], v2 = cf[7];
+      const bool drifting = cd != T(0) || cdA != T(0);
+      const T lam = (T)L.lam;
       const unsigned amask = __ballot_sync(0xffffffffu, active);
       const bool edge_l = tx == 0 || lane == 0, edge_r = tx == TX - 1 || lane == 31;
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;

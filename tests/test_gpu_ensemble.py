@@ -1,0 +1,169 @@
+"""GPU parity of batched ensembles (cl_ensemble_init): lattices of mixed
+sizes and seeds advanced by one launch per call, each against the FP64 CPU
+oracle of the same (N, kIR, seed), or against a single-lattice context.
+
+Tolerances as in the single-lattice tests: FP64 storage 1e-10 pointwise and
+on volume averages; FP32 storage 1e-4 pointwise against the oracle.  An
+ensemble member and a single-lattice context differ only in the order of
+their FP64 reductions (the work split differs), so FP32 states agree to 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2102_01031_gb300 as P
+    P.build()
+    P.lib()
+    return P
+
+
+def nrel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+C2S = dict(dt=0.005, integrator=O.VV4, q=100.0, phi0=[1.0, 0.0], fluct_amp2=1e-4,
+           expansion=O.EXP_SELF, fstar_over_mp=0.5)
+
+
+def test_mixed_sizes_match_oracle_fp64(P):
+    Ns, kIRs, seeds = [16, 24, 32, 16, 8], [0.5, 0.4, 0.5, 0.5, 1.0], [3, 4, 5, 6, 7]
+    E = P.Ensemble(O.MODEL_LPHI4_CHI, Ns, kIRs, 1.0, seeds, P.make_params(**C2S))
+    assert E.size() == 5
+    E.step(40)
+    for l, (N, k, s) in enumerate(zip(Ns, kIRs, seeds)):
+        o = O.Oracle(O.MODEL_LPHI4_CHI, N, k, 1.0, s, O.make_params(**C2S))
+        o.step(40)
+        for f in range(2):
+            for w in (0, 1):
+                assert nrel(E.get(l, f, w), o.get(f, w)) < 1e-10, (l, f, w)
+        eg, eo = E.energies(l), o.energies()
+        for key in ("a", "b", "eta", "rho"):
+            assert abs(eg[key] - eo[key]) <= 1e-10 * abs(eo[key]), (l, key)
+        assert abs(eg["hubble_viol"]) <= 1.05 * abs(eo["hubble_viol"]) + 1e-15
+        eta, a, b = E.scalars(l)
+        assert abs(a - eo["a"]) < 1e-12 and abs(eta - 40 * C2S["dt"]) < 1e-12
+
+
+def test_graph_replay_matches_one_call(P):
+    """step(10) three times (the last two replay one recorded graph) equals step(30)."""
+    kw = dict(C2S, precision=P.FP32)
+    a = P.Ensemble(O.MODEL_LPHI4_CHI, [32, 48], [0.5, 0.5], 1.0, [1, 2], P.make_params(**kw))
+    b = P.Ensemble(O.MODEL_LPHI4_CHI, [32, 48], [0.5, 0.5], 1.0, [1, 2], P.make_params(**kw))
+    n0 = a.launches()
+    for _ in range(3):
+        a.step(10)
+    assert a.launches() - n0 == 3       # one launch per call, whatever the lattice count
+    b.step(30)
+    for l in range(2):
+        for f in range(2):
+            for w in (0, 1):
+                assert np.array_equal(a.get(l, f, w), b.get(l, f, w)), (l, f, w)
+
+
+def test_member_equals_single_lattice_fp32(P):
+    kw = dict(C2S, precision=P.FP32)
+    E = P.Ensemble(O.MODEL_LPHI4_CHI, [64, 32, 96], [0.2, 0.5, 0.15], 1.0, [11, 12, 13], P.make_params(**kw))
+    E.step(25)
+    for l, (N, k, s) in enumerate([(64, 0.2, 11), (32, 0.5, 12), (96, 0.15, 13)]):
+        g = P.Lattice(O.MODEL_LPHI4_CHI, N, k, 1.0, s, P.make_params(**kw))
+        g.step(25)
+        for f in range(2):
+            for w in (0, 1):
+                assert nrel(E.get(l, f, w), g.get(f, w)) < 1e-5, (l, f, w)
+        g.close()
+
+
+def test_ensemble_spectrum_is_mean_of_members(P):
+    Ns, seeds = [16] * 4, [21, 22, 23, 24]
+    E = P.Ensemble(O.MODEL_LPHI4_CHI, Ns, [0.5] * 4, 1.0, seeds, P.make_params(**C2S))
+    E.step(20)
+    ref = []
+    for s in seeds:
+        o = O.Oracle(O.MODEL_LPHI4_CHI, 16, 0.5, 1.0, s, O.make_params(**C2S))
+        o.step(20)
+        ref.append(o.spectrum(1, 0, 1.0))
+    k, d, m = E.spectrum_mean([0, 1, 2, 3], 1, 0, 1.0)
+    ko, mo = ref[0][0], ref[0][2]
+    do = np.mean([r[1] for r in ref], axis=0)
+    assert np.array_equal(m, mo)
+    assert np.abs(k - ko).max() < 1e-12 * ko.max()
+    assert np.abs(d - do).max() < 1e-9 * np.abs(do).max()
+    with pytest.raises(P.ClError):
+        P.Ensemble(O.MODEL_LPHI4_CHI, [16, 32], [0.5, 0.5], 1.0, [1, 2],
+                   P.make_params(**C2S)).spectrum_mean([0, 1], 0)
+
+
+def test_autotuned_tiles(P):
+    kw = dict(C2S, precision=P.FP32, autotune=1)
+    E = P.Ensemble(O.MODEL_LPHI4_CHI, [32, 64], [0.5, 0.25], 1.0, [1, 2], P.make_params(**kw))
+    for l, N in enumerate((32, 64)):
+        n, by, st = E.tile(l)
+        assert n == N and N % by == 0 and (N // 4) * by <= 512 and 3 <= st <= 6
+    E.step(10)
+    o = O.Oracle(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 1, O.make_params(**C2S))
+    o.step(10)
+    for f in range(2):
+        assert nrel(E.get(0, f, 0), o.get(f, 0)) < 1e-4
+    # a forced tile height is used as given, and an inadmissible one is refused
+    F = P.Ensemble(O.MODEL_LPHI4_CHI, [32], [0.5], 1.0, [1], P.make_params(**dict(kw, autotune=0, tile_by=4)))
+    assert F.tile(0)[1] == 4
+    with pytest.raises(P.ClError) as e:
+        P.Ensemble(O.MODEL_LPHI4_CHI, [32], [0.5], 1.0, [1], P.make_params(**dict(kw, autotune=0, tile_by=5)))
+    assert e.value.status == P.CL_EINVAL
+
+
+def test_u1_ensemble_fp64(P):
+    C3 = dict(dt=0.01, integrator=O.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
+              phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=O.EXP_OFF, fstar_over_mp=0.5)
+    E = P.Ensemble(O.MODEL_U1_HIGGS, [16, 24], [0.5, 0.5], 1.0, [5, 6], P.make_params(**C3))
+    E.step(30)
+    for l, (N, s) in enumerate([(16, 5), (24, 6)]):
+        o = O.Oracle(O.MODEL_U1_HIGGS, N, 0.5, 1.0, s, O.make_params(**C3))
+        o.step(30)
+        for f in range(5):
+            for w in (0, 1):
+                ref = o.get(f, w)
+                assert nrel(E.get(l, f, w), ref) < 1e-10, (l, f, w)
+
+
+def test_batched_ensemble_64_lattices(P):
+    """The 64-lattice ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32,
+    VV4 with expansion, seeds 1..64, kIR scaled so all share one box size.
+    Members are checked against the oracle (32^3) and against single-lattice
+    contexts (128^3), the 32^3 group's averaged spectrum against the oracle's."""
+    Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
+    kIRs = [0.1 * 256 / n for n in Ns]
+    seeds = list(range(1, 65))
+    kw = dict(C2S, precision=P.FP32)
+    E = P.Ensemble(O.MODEL_LPHI4_CHI, Ns, kIRs, 1.0, seeds, P.make_params(**kw))
+    E.step(20)
+    for l in (0, 7):
+        o = O.Oracle(O.MODEL_LPHI4_CHI, 32, kIRs[l], 1.0, seeds[l], O.make_params(**C2S))
+        o.step(20)
+        for f in range(2):
+            for w in (0, 1):
+                assert nrel(E.get(l, f, w), o.get(f, w)) < 1e-4, (l, f, w)
+    g = P.Lattice(O.MODEL_LPHI4_CHI, 128, kIRs[63], 1.0, 64, P.make_params(**kw))
+    g.step(20)
+    for f in range(2):
+        assert nrel(E.get(63, f, 0), g.get(f, 0)) < 1e-5
+    g.close()
+    for l in range(64):
+        e = E.energies(l)
+        assert e["nonfinite"] == 0 and e["a"] > 1.0
+    k, d, m = E.spectrum_mean(list(range(16)), 0, 0, 1.0)
+    assert np.all(np.isfinite(d)) and m.sum() == 32 ** 3 - 1
+    ref = []
+    for l in range(3):
+        o = O.Oracle(O.MODEL_LPHI4_CHI, 32, kIRs[l], 1.0, seeds[l], O.make_params(**C2S))
+        o.step(20)
+        ref.append(o.spectrum(0, 0, 1.0)[1])
+    _, d3, _ = E.spectrum_mean([0, 1, 2], 0, 0, 1.0)
+    do = np.mean(ref, axis=0)
+    assert np.abs(d3 - do).max() < 1e-3 * np.abs(do).max()
