@@ -702,9 +702,31 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     } else {
       L.BY = cand[0];
     }
-    stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
     tiles.push_back(LatTiles{L.N, L.BY});
   }
+  // work list: one CTA per SM, at least 8 plane tasks each
+  long long tasks = 0;
+  for (const LatTiles& t : tiles) tasks += (long long)(t.N / t.BY) * t.N;
+  c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
+  std::vector<Seg> segs;
+  std::vector<int> cta, sbeg, send;
+  if (!build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send)) {
+    // tuned tiles too short for this mix of sizes: the tallest admissible ones
+    bool ok = false;
+    if (c->p.autotune && c->p.tile_by == 0) {
+      for (int l = 0; l < c->nlat; ++l) {
+        c->lats[l].BY = tile_candidates(c->model, c->narr, c->esz, c->lats[l].N, c->smem_optin)[0];
+        tiles[l].BY = c->lats[l].BY;
+      }
+      ok = build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send);
+    }
+    if (!ok)
+      return fail(c, CL_EUNSUPPORTED, "work split needs more than %d segments per CTA", MAX_SEG_PER_CTA);
+  }
+  c->nseg = (int)segs.size();
+  c->nslot = send[c->nlat - 1];
+  // stage ring: the largest lattice stage, as many stages (3 .. 6) as fit
+  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
   const int S = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / stage);
   if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the stage ring");
   c->stages = S;
@@ -716,16 +738,6 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)c->smem_bytes));
   }
-  // work list: one CTA per SM, at least 8 plane tasks each
-  long long tasks = 0;
-  for (const LatTiles& t : tiles) tasks += (long long)(t.N / t.BY) * t.N;
-  c->grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
-  std::vector<Seg> segs;
-  std::vector<int> cta, sbeg, send;
-  if (!build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send))
-    return fail(c, CL_EUNSUPPORTED, "work split needs more than %d segments per CTA", MAX_SEG_PER_CTA);
-  c->nseg = (int)segs.size();
-  c->nslot = send[c->nlat - 1];
   // device memory
   for (int l = 0; l < c->nlat; ++l) {
     LatHost& L = c->lats[l];

@@ -55,7 +55,7 @@ struct LatScalars {
 struct Seg {
   int lat, ytile, z0, nz, dir, slot, flush, pad;
 };
-constexpr int MAX_SEG_PER_CTA = 32;
+constexpr int MAX_SEG_PER_CTA = 64;
 
 // Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
 constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
