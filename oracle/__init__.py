@@ -117,6 +117,12 @@ def lib():
             L.clo_ic_sample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int64), dp]
+            L.clo_adjoint.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, dp, dp, dp]
+            L.clo_ic_amplitude_grad.argtypes = [c_p, dp, dp]
+            L.clo_ic_draws.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64), dp]
             _lib = L
         return _lib
 
@@ -223,6 +229,42 @@ class Oracle:
             raise ValueError("clo_spectrum failed (%d)" % rc)
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
+
+
+    def adjoint(self, nsteps, objective=0, field=1, what=0, dk_bin=1.0, bin=1):
+        """Discrete adjoint: (J, dJ/dq, lam) with lam[f][w] = dJ/d(field f, what w) at
+        the current state (arrays [z][y][x]); the state is left unchanged."""
+        nf = 1 if self.nfields() == 1 else 2
+        lam = np.zeros(2 * nf * self.V)
+        J, dq = ctypes.c_double(), ctypes.c_double()
+        rc = self.L.clo_adjoint(self.h, nsteps, objective, field, what, dk_bin, bin, ctypes.byref(J),
+                                ctypes.byref(dq), _dp(lam))
+        if rc != 0:
+            raise ValueError("clo_adjoint failed (%d)" % rc)
+        lam = lam.reshape(nf, 2, self.N, self.N, self.N)
+        return J.value, dq.value, lam
+
+    def ic_amplitude_grad(self, lam):
+        """dJ/d|z_j| of every canonical mode from lam (as returned by adjoint at the ICs):
+        array [field][j][z][y][x], zero at non-canonical sites."""
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
+        out = np.zeros_like(lam)
+        if self.L.clo_ic_amplitude_grad(self.h, _dp(lam), _dp(out)) != 0:
+            raise ValueError("clo_ic_amplitude_grad")
+        nf = lam.size // (2 * self.V)
+        return out.reshape(nf, 2, self.N, self.N, self.N)
+
+
+def ic_draws(model, N, kIR, alpha, seed, params, idx):
+    """(|z1|, arg z1, |z2|, arg z2, omega) per field at canonical site indices."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    nf = 1 if model == MODEL_LPHI4 else 2
+    out = np.zeros(idx.size * nf * 5)
+    rc = lib().clo_ic_draws(model, N, kIR, alpha, seed, ctypes.byref(params), idx.size,
+                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    if rc != 0:
+        raise ValueError("clo_ic_draws")
+    return out.reshape(idx.size, nf, 5)
 
 
 def philox4x32_10(ctr, key):

@@ -131,6 +131,8 @@ struct clo_ctx {
   clo_params p;
   double a, b, eta, a0, eta0, rho0;
   double Hfix;        // fixed background: initial a'/a
+  uint64_t seed;      // seed of the initial conditions
+  double H_ic;        // a'/a used by the initial conditions
   std::vector<double> phi[2], pi[2];
   std::vector<double> A[3], piA[3];
   bool gauge() const { return model == CLO_MODEL_U1_HIGGS; }
@@ -486,13 +488,12 @@ void draw4(uint64_t seed, long idx, int f, int j, double u[2]) {
   u[1] = u01(r[2], r[3]);
 }
 
-// Fourier values of the fluctuation (F[f]) and of its time derivative (G[f])
-// at the canonical site idx (idx <= partner).  Returns false for sites that
-// stay zero.
-bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, cplx* G) {
-  double a = c->a, al = c->alpha, amp2 = c->p.fluct_amp2;
+// Draws of the canonical site idx (idx <= partner): the two complex
+// amplitudes z1, z2 of each field (|z| Rayleigh, phase uniform) and the
+// frequency omega_k.  Returns false for sites that stay zero.
+bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, double* om) {
+  double a = c->a, amp2 = c->p.fluct_amp2;
   double vol = std::pow((double)c->N / c->dx, 3.0);
-  const double isq2 = 1.0 / std::sqrt(2.0);
   if (idx == 0) return false;
   long pid = partner_index(c, idx);
   bool selfc = pid == idx;
@@ -500,8 +501,6 @@ bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, c
   double k = mode_k(c, idx);
   if (c->p.kcut >= 0.0 && k > c->p.kcut) return false;
   if (amp2 <= 0.0) return false;
-  cplx z1[2], z2[2];
-  double om[2];
   for (int f = 0; f < c->nf; ++f) {
     double w2 = k * k + a * a * mass2(c, c->p.phi0, f);
     if (w2 <= 0.0) return false;
@@ -532,9 +531,21 @@ bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, c
     z1[0] = std::polar(r0, t01); z2[0] = std::polar(r0, t02);
     z1[1] = std::polar(r1, t11); z2[1] = std::polar(r1, t12);
   }
+  return true;
+}
+
+// Fourier values of the fluctuation (F[f]) and of its time derivative (G[f])
+// at the canonical site idx (idx <= partner).  Returns false for sites that
+// stay zero.
+bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, cplx* G) {
+  const double isq2 = 1.0 / std::sqrt(2.0);
+  cplx z1[2], z2[2];
+  double om[2];
+  if (!mode_draws(c, seed, idx, z1, z2, om)) return false;
+  bool selfc = partner_index(c, idx) == idx;
   for (int f = 0; f < c->nf; ++f) {
     cplx df = (z1[f] + z2[f]) * isq2;
-    cplx dv = std::pow(a, al - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
+    cplx dv = std::pow(c->a, c->alpha - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
     if (selfc) { df = cplx(df.real(), 0.0); dv = cplx(dv.real(), 0.0); }
     F[f] = df;
     G[f] = dv;
@@ -695,6 +706,8 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
     c->b = 0.0;
   }
   double H = c->b / c->a;
+  c->seed = seed;
+  c->H_ic = H;
   double a3ma = std::pow(c->a, 3.0 - alpha);
   if (p->fluct_amp2 > 0.0) {
     std::vector<cplx> F[2], G[2];
@@ -898,6 +911,269 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
     k[b] = kb;
     delta[b] = kb * kb * kb / (2.0 * PI * PI) * fac * sp[b] / (4.0 * PI * nbar * nbar);
     mult[b] = cnt[b];
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Discrete adjoint of the field evolution (gradient of a final observable),
+// written from the forward map above, for scalar models on a fixed
+// background (expansion off, or the fixed power law): there the scale factor
+// is a known function of time and each elementary move is linear or
+// site-local in the fields:
+//   kick  (w, a):  pi_f += w K_f(phi; a, q),  K_f = a^{1+alpha} Lap phi_f/dx^2 - a^{3+alpha} dV/dphi_f
+//   drift (c):     phi_f += c pi_f
+// The adjoint (lam_phi, lam_pi) = (dJ/dphi, dJ/dpi) runs the moves backwards:
+//   kick:  lam_phi_f += w [a^{1+alpha} Lap lam_pi_f/dx^2 - a^{3+alpha} sum_g V_{,fg}(phi) lam_pi_g]
+//          dJ/dq     += w (-a^{3+alpha}) sum_n sum_f lam_pi_f d(dV/dphi_f)/dq
+//   drift: lam_pi_f  += c lam_phi_f
+// (Lap is symmetric, so it is its own transpose.)  The forward run records
+// the field at every kick; nothing is recomputed.
+// ===========================================================================
+namespace {
+
+struct Move {
+  int kick;                  // 1 kick, 0 drift
+  double w, a;               // kick weight and scale factor / drift coefficient (w)
+  std::vector<double> phi[2];  // fields at the kick
+};
+
+// Hessian of the potential (eq. PotNat) at one site, and d(dV/dphi_f)/dq.
+void pot_hessian(const clo_ctx* c, const double* f, double H[2][2], double* dq) {
+  if (c->model == CLO_MODEL_LPHI4) {
+    H[0][0] = 3.0 * f[0] * f[0];
+    H[0][1] = H[1][0] = H[1][1] = 0.0;
+    dq[0] = dq[1] = 0.0;
+  } else {
+    const double q = c->p.q;
+    H[0][0] = 3.0 * f[0] * f[0] + q * f[1] * f[1];
+    H[0][1] = H[1][0] = 2.0 * q * f[0] * f[1];
+    H[1][1] = q * f[0] * f[0];
+    dq[0] = f[0] * f[1] * f[1];
+    dq[1] = f[0] * f[0] * f[1];
+  }
+}
+
+double lap_at(const clo_ctx* c, const std::vector<double>& u, long n) {
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i) s += u[c->shift(n, i, +1)] + u[c->shift(n, i, -1)] - 2.0 * u[n];
+  return s;
+}
+
+// One VV2 step of size h (the moves of vv2), recorded.
+void vv2_recorded(clo_ctx* c, double h, std::vector<Move>& moves) {
+  for (int half = 0; half < 2; ++half) {
+    if (half == 1) {
+      Move d;
+      d.kick = 0;
+      double a1 = c->p.expansion == CLO_EXP_FIXED ? a_fixed(c, c->eta + h) : c->a;
+      d.w = h * std::pow(0.5 * (c->a + a1), c->alpha - 3.0);
+      d.a = 0.0;
+      moves.push_back(std::move(d));
+      drift(c, h);
+    }
+    Move k;
+    k.kick = 1;
+    k.w = 0.5 * h;
+    k.a = c->a;
+    for (int f = 0; f < c->nf; ++f) k.phi[f] = c->phi[f];
+    moves.push_back(std::move(k));
+    kick_fields(c, 0.5 * h);
+  }
+}
+
+// Objective J at the current state and its seeds dJ/dphi_f, dJ/dpi_f and
+// explicit dJ/dq.  objective 0: chi energy fraction (E_K^chi + E_G^chi)/rho
+// (lphi4 + chi).  objective 1: delta_b of the binned spectrum of (field, what)
+// with bin width dk (as clo_spectrum).
+bool objective_seed(clo_ctx* c, int objective, int field, int what, double dk, int bin, double* J,
+                    std::vector<double>* lphi, std::vector<double>* lpi, double* dJdq) {
+  const double V = (double)c->V;
+  for (int f = 0; f < c->nf; ++f) {
+    lphi[f].assign(c->V, 0.0);
+    lpi[f].assign(c->V, 0.0);
+  }
+  *dJdq = 0.0;
+  if (objective == 0) {
+    if (c->model != CLO_MODEL_LPHI4_CHI) return false;
+    Avg r;
+    averages(c, r);
+    const double rho = rho_of(r), a = c->a;
+    const double a2 = a * a, a6 = a2 * a2 * a2;
+    *J = (r.EK[1] + r.EG[1]) / rho;
+    for (long n = 0; n < c->V; ++n) {
+      double f[2] = {c->phi[0][n], c->phi[1][n]}, d[2];
+      pot_deriv(c, f, d);
+      for (int g = 0; g < 2; ++g) {
+        const double num = g == 1 ? 1.0 : 0.0;
+        const double dEK = c->pi[g][n] / (a6 * V);
+        const double dEG = -lap_at(c, c->phi[g], n) / (a2 * c->dx * c->dx * V);
+        lpi[g][n] = (num * dEK - *J * dEK) / rho;
+        lphi[g][n] = (num * dEG - *J * (dEG + d[g] / V)) / rho;
+      }
+    }
+    double s = 0.0;
+    for (long n = 0; n < c->V; ++n) s += 0.5 * c->phi[0][n] * c->phi[0][n] * c->phi[1][n] * c->phi[1][n];
+    *dJdq = -*J / rho * s / V;
+    return true;
+  }
+  if (objective == 1) {
+    if (field < 0 || field >= c->nf || (what != 0 && what != 1) || !(dk > 0.0)) return false;
+    const std::vector<double>& u = what == 0 ? c->phi[field] : c->pi[field];
+    const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk) + 1;
+    if (bin < 0 || bin >= nb) return false;
+    std::vector<cplx> F(c->V);
+    for (long n = 0; n < c->V; ++n) F[n] = cplx(u[n], 0.0);
+    fft3d(F, c->N, -1);
+    double sp = 0.0, sn = 0.0;
+    long cnt = 0;
+    std::vector<cplx> M(c->V, cplx(0.0, 0.0));
+    for (long idx = 1; idx < c->V; ++idx) {
+      const double nn = mode_k(c, idx) / c->kIR;
+      int b = (int)std::floor(nn / dk);
+      if (b >= nb) b = nb - 1;
+      if (b != bin) continue;
+      sp += std::norm(F[idx]);
+      sn += nn;
+      ++cnt;
+      M[idx] = F[idx];
+    }
+    if (cnt == 0) return false;
+    const double nbar = sn / (double)cnt, kb = c->kIR * nbar;
+    const double Cb = kb * kb * kb / (2.0 * PI * PI) * std::pow(c->dx / (double)c->N, 3.0) /
+                      (4.0 * PI * nbar * nbar);
+    *J = Cb * sp;
+    fft3d(M, c->N, +1);
+    std::vector<double>& out = what == 0 ? lphi[field] : lpi[field];
+    for (long n = 0; n < c->V; ++n) out[n] = 2.0 * Cb * M[n].real();
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, double dk, int bin,
+                double* J, double* dJdq, double* lam) {
+  if (!c || nsteps < 0 || !J || !dJdq || !lam) return -1;
+  if (c->gauge() || c->p.expansion == CLO_EXP_SELF) return -2;  // not built: see the header
+  // state at the start, restored at the end
+  std::vector<double> phi0[2], pi0[2];
+  for (int f = 0; f < c->nf; ++f) { phi0[f] = c->phi[f]; pi0[f] = c->pi[f]; }
+  const double a0 = c->a, b0 = c->b, eta0 = c->eta;
+  std::vector<double> d;
+  schedule(c->p.integrator == CLO_LF ? 2 : c->p.integrator, c->p.dt, d);
+  std::vector<Move> moves;
+  for (int s = 0; s < nsteps; ++s)
+    for (double h : d) vv2_recorded(c, h, moves);
+  std::vector<double> lphi[2], lpi[2];
+  const bool ok = objective_seed(c, objective, field, what, dk, bin, J, lphi, lpi, dJdq);
+  if (ok) {
+    const double idx2 = 1.0 / (c->dx * c->dx);
+    for (size_t m = moves.size(); m-- > 0;) {
+      const Move& mv = moves[m];
+      if (!mv.kick) {
+        for (int f = 0; f < c->nf; ++f)
+          for (long n = 0; n < c->V; ++n) lpi[f][n] += mv.w * lphi[f][n];
+        continue;
+      }
+      const double a1 = std::pow(mv.a, 1.0 + c->alpha), a3 = std::pow(mv.a, 3.0 + c->alpha);
+      double dq = 0.0;
+      for (long n = 0; n < c->V; ++n) {
+        double f[2] = {0.0, 0.0}, H[2][2], g[2];
+        for (int k = 0; k < c->nf; ++k) f[k] = mv.phi[k][n];
+        pot_hessian(c, f, H, g);
+        for (int k = 0; k < c->nf; ++k) {
+          double hl = 0.0;
+          for (int j = 0; j < c->nf; ++j) hl += H[k][j] * lpi[j][n];
+          lphi[k][n] += mv.w * (a1 * lap_at(c, lpi[k], n) * idx2 - a3 * hl);
+          dq += lpi[k][n] * g[k];
+        }
+      }
+      *dJdq += mv.w * (-a3) * dq;
+    }
+    for (int f = 0; f < c->nf; ++f) {
+      std::memcpy(lam + (size_t)(2 * f) * c->V, lphi[f].data(), sizeof(double) * c->V);
+      std::memcpy(lam + (size_t)(2 * f + 1) * c->V, lpi[f].data(), sizeof(double) * c->V);
+    }
+  }
+  for (int f = 0; f < c->nf; ++f) { c->phi[f] = phi0[f]; c->pi[f] = pi0[f]; }
+  c->a = a0; c->b = b0; c->eta = eta0;
+  return ok ? 0 : -1;
+}
+
+// Gradient with respect to the drawn mode amplitudes |z1|, |z2| (Sec. 3.5.1):
+// with phi(x) = phi0 + (1/V) sum_n F(n) e^{+i k.x}, F = (z1 + z2)/sqrt2 and
+// pi(x) = a^{3-alpha} [phi0' + (1/V) sum_n G(n) e^{+i k.x}],
+// G = a^{alpha-1} i omega (z1 - z2)/sqrt2 - H F, a canonical mode n and its
+// conjugate partner contribute (s/V) Re[dF/d|z_j| e^{i k.x}] (s = 2; s = 1 for
+// self-conjugate sites), so
+//   dJ/d|z_j| = (s/V) Re[ e^{i th_j}/sqrt2 L_phi(n)
+//                 + a^{3-alpha} (+-a^{alpha-1} i omega - H) e^{i th_j}/sqrt2 L_pi(n) ],
+// L(n) = sum_x lam(x) e^{+i k.x}.  out[(2f + j) V + n] at canonical n, 0 elsewhere.
+int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out) {
+  if (!c || !lam || !out || c->gauge()) return -1;
+  const double V = (double)c->V, isq2 = 1.0 / std::sqrt(2.0);
+  const double a = c->a0, a3ma = std::pow(a, 3.0 - c->alpha), aam1 = std::pow(a, c->alpha - 1.0);
+  std::memset(out, 0, sizeof(double) * 2 * c->nf * c->V);
+  std::vector<cplx> L[2][2];
+  for (int f = 0; f < c->nf; ++f)
+    for (int w = 0; w < 2; ++w) {
+      L[f][w].resize(c->V);
+      for (long n = 0; n < c->V; ++n) L[f][w][n] = cplx(lam[(size_t)(2 * f + w) * c->V + n], 0.0);
+      fft3d(L[f][w], c->N, +1);
+    }
+  clo_ctx t = *c;  // draws at the initial scale factor
+  t.a = c->a0;
+  for (long idx = 1; idx < c->V; ++idx) {
+    const long pid = partner_index(c, idx);
+    if (pid < idx) continue;
+    cplx z1[2], z2[2];
+    double om[2];
+    if (!mode_draws(&t, c->seed, idx, z1, z2, om)) continue;
+    const double s = pid == idx ? 1.0 : 2.0;
+    for (int f = 0; f < c->nf; ++f)
+      for (int j = 0; j < 2; ++j) {
+        const cplx e = std::polar(1.0, std::arg(j == 0 ? z1[f] : z2[f])) * isq2;
+        const double sg = j == 0 ? 1.0 : -1.0;
+        const cplx cpi = a3ma * (sg * aam1 * cplx(0.0, om[f]) - c->H_ic) * e;
+        out[(size_t)(2 * f + j) * c->V + idx] = s / V * (e * L[f][0][idx] + cpi * L[f][1][idx]).real();
+      }
+  }
+  return 0;
+}
+
+// Drawn amplitudes of canonical sites: out[(i nf + f) 5 + {0..4}] = |z1|, arg z1,
+// |z2|, arg z2, omega_k (zeros for sites that stay zero).
+int clo_ic_draws(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p, int n,
+                 const int64_t* idx, double* out) {
+  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_U1_HIGGS) return -1;
+  clo_ctx c;
+  c.model = model;
+  c.N = N;
+  c.V = (long)N * N * N;
+  c.nf = model == CLO_MODEL_LPHI4 ? 1 : 2;
+  c.kIR = kIR;
+  c.dx = 2.0 * PI / ((double)N * kIR);
+  c.alpha = alpha;
+  c.p = *p;
+  c.a = c.a0 = 1.0;
+  for (int i = 0; i < n; ++i) {
+    cplx z1[2], z2[2];
+    double om[2];
+    const bool ok = idx[i] >= 0 && idx[i] < c.V && mode_draws(&c, seed, (long)idx[i], z1, z2, om);
+    for (int f = 0; f < c.nf; ++f) {
+      double* o = out + ((size_t)i * c.nf + f) * 5;
+      o[0] = ok ? std::abs(z1[f]) : 0.0;
+      o[1] = ok ? std::arg(z1[f]) : 0.0;
+      o[2] = ok ? std::abs(z2[f]) : 0.0;
+      o[3] = ok ? std::arg(z2[f]) : 0.0;
+      o[4] = ok ? om[f] : 0.0;
+    }
   }
   return 0;
 }

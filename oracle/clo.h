@@ -84,6 +84,19 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out);
 
+/* Discrete adjoint (scalar models, expansion off or fixed background; -2
+ * otherwise): from the current state, run nsteps, evaluate the objective
+ * (0: chi energy fraction; 1: spectrum bin `bin` of (field, what) with width
+ * dk), and return J, dJ/dq at a fixed initial state, and lam[(2f + w) V + n] =
+ * dJ/d(field f, what w)(n) at the initial state.  The state is restored. */
+int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, double dk, int bin,
+                double* J, double* dJdq, double* lam);
+/* Chain lam (as above, at the initial conditions) to dJ/d|z_j| of each canonical
+ * mode: out[(2f + j) V + n], j = 0, 1. */
+int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out);
+int clo_ic_draws(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p, int n,
+                 const int64_t* idx, double* out);
+
 /* pieces exposed for the pin tests */
 void clo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double clo_u01(uint32_t hi, uint32_t lo);
