@@ -34,7 +34,9 @@ EXPORTS = (
     "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
+    "cl_adjoint", "cl_ic_amplitude_grad",
 )
+OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
 
 class ClError(RuntimeError):
@@ -145,6 +147,8 @@ def lib():
                                   ctypes.POINTER(ctypes.c_int)]
     L.cl_ensemble_spectrum.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ip, ip, ctypes.c_double, dp, dp,
                                        i64p, ip, ctypes.POINTER(ctypes.c_int)]
+    L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp]
+    L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
     _lib = L
     return L
 
@@ -300,6 +304,25 @@ class Lattice:
         _check(self.L, self.h, self.L.cl_pass_timing(self.h, ctypes.byref(ms), ctypes.byref(n),
                                                      1 if reset else 0), "timing")
         return ms.value, n.value
+
+    def adjoint(self, nsteps, ckpt_every=500, objective=OBJ_CHI_FRACTION, field=1, what=0, dk_bin=1.0,
+                bin=1):
+        """cl_adjoint: (J, dJ/dq, lam), lam[f][w] = dJ/d(field f, what w) at the current
+        state ([z][y][x] arrays); the state is left unchanged."""
+        nf = self.nfields()
+        lam = np.zeros(2 * nf * self.V)
+        J, dq = ctypes.c_double(), ctypes.c_double()
+        rc = self.L.cl_adjoint(self.h, nsteps, ckpt_every, objective, field, what, dk_bin, bin,
+                               ctypes.byref(J), ctypes.byref(dq), _dp(lam))
+        _check(self.L, self.h, rc, "cl_adjoint")
+        return J.value, dq.value, lam.reshape(nf, 2, self.N, self.N, self.N)
+
+    def ic_amplitude_grad(self, lam):
+        """cl_ic_amplitude_grad: dJ/d|z_j| per field and draw, [f][j][z][y][x]."""
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(-1))
+        out = np.zeros_like(lam)
+        _check(self.L, self.h, self.L.cl_ic_amplitude_grad(self.h, _dp(lam), _dp(out)), "cl_ic_amplitude_grad")
+        return out.reshape(-1, 2, self.N, self.N, self.N)
 
 
 class Ensemble:

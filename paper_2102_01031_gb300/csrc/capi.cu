@@ -43,6 +43,13 @@ cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, 
 cudaError_t launch_u1_gauss_monitor(const LatConst*, int, double*, int, long long, cudaStream_t);
 __global__ void set_scalars_kernel(const LatConst*, LatScalars*, double, double, double);
 __global__ void b_from_obs_kernel(const LatConst*, LatScalars*);
+PassKernel adjoint_pass_kernel(int fp32, int nf);
+cudaError_t launch_seed_chi_fraction(int, const LatConst*, const LatScalars*, int, void* const*, double*, int,
+                                     double*, cudaStream_t);
+cudaError_t launch_spectrum_seed(int, double2*, int, double, int, int, const double*, double, double, double*,
+                                 int, void*, cudaStream_t);
+cudaError_t launch_ic_amp_grad(const double2*, const double2*, double*, double*, const LatConst*,
+                               const LatScalars*, const ICArgs&, int, long long, cudaStream_t);
 
 }  // namespace clg
 
@@ -57,6 +64,24 @@ struct LatHost {
   double kIR = 0.0, dx = 0.0;
   uint64_t seed = 0;
   void* slab = nullptr;  // 2 buffers x narr arrays of V values, array-major
+  ICArgs ic;             // what the initial conditions were drawn with
+};
+
+// Resources of the adjoint sweep (single scalar lattice), made on first use:
+// the reversed-pass kernel's own tiling over the state and adjoint arrays.
+struct AdjPlan {
+  bool ready = false;
+  int grid = 0, stages = 0;
+  unsigned stage_bytes = 0;
+  size_t smem = 0;
+  bool coop = false;
+  void* lam = nullptr;           // 2 buffers x 2 nf adjoint arrays
+  LatConst* d_lat = nullptr;     // arrays: state (2 nf) then adjoint (2 nf), by buffer
+  Seg* d_segs = nullptr;
+  int* d_cta = nullptr;
+  double* d_part = nullptr;
+  unsigned* d_cnt = nullptr;
+  double* d_out = nullptr;       // J and the explicit dJ/dq of the objective
 };
 
 // A multi-pass launch recorded in a CUDA graph, replayed when the same
@@ -97,6 +122,7 @@ struct cl_ctx {
   bool graphs = true;              // record multi-pass launches in CUDA graphs
   std::vector<std::pair<std::vector<PassStep>, void*>> step_cache;
   std::vector<GraphEntry> graph_cache;
+  AdjPlan adj;
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
@@ -268,7 +294,8 @@ cl_status enqueue_multi(cl_ctx* c, PassKernel k, PassArgs& A, cudaStream_t st) {
 // kernel (all CTAs resident) that runs them back to back, reading the
 // per-pass weights from a device copy; it is recorded in a CUDA graph the
 // first time and the graph is replayed for the same passes later.
-cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write, int set_rho0) {
+cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write, int set_rho0,
+                        double* log = nullptr, long long log_base = 0) {
   PassKernel k = pick_kernel(c, red);
   if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
   PassArgs A;
@@ -293,6 +320,8 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   A.steps = nullptr;
   A.npass = 1;
   A.gsync = nullptr;
+  A.log = log;
+  A.log_base = log_base;
   const bool multi = n > 1 && c->coop;
   cudaGraphExec_t exec = nullptr;
   if (multi) {
@@ -302,7 +331,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
     A.steps = dev;
     A.npass = n;
     A.gsync = c->d_gsync;
-    if (c->graphs) {
+    if (c->graphs && !log) {
       for (auto& g : c->graph_cache)
         if (g.parity == c->parity && g.red == red && g.write == write && g.set_rho0 == set_rho0 &&
             g.dev_steps == (const void*)dev && g.steps.size() == (size_t)n &&
@@ -359,6 +388,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
       A.win = st[i].win;
       A.dnext = st[i].dnext;
       A.parity = c->parity ^ (write ? (i & 1) : 0);
+      A.log_base = log_base + i;
       k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
       CHECK_LAUNCH();
     }
@@ -609,6 +639,13 @@ cl_status cl_free(cl_ctx* c) {
   cudaFree(c->d_cplx);
   cudaFree(c->d_spec);
   cudaFree(c->d_gsync);
+  cudaFree(c->adj.lam);
+  cudaFree(c->adj.d_lat);
+  cudaFree(c->adj.d_segs);
+  cudaFree(c->adj.d_cta);
+  cudaFree(c->adj.d_part);
+  cudaFree(c->adj.d_cnt);
+  cudaFree(c->adj.d_out);
   for (auto& e : c->step_cache) cudaFree(e.second);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
@@ -826,6 +863,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     A.seed = H.seed;
     A.model = c->model;
     A.nf = c->nf;
+    c->lats[l].ic = A;
     CU(launch_init_scalars(dL, dS, A, c->stream));
     ++c->launches;
     double2* F = c->d_cplx;
@@ -1176,6 +1214,323 @@ cl_status cl_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset
     c->timing_passes = 0;
   }
   return CL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint sweep (gradient of a final observable).
+// ---------------------------------------------------------------------------
+
+// The reversed-pass kernel's tiling: its stage carries the state and the
+// adjoint (4 nf arrays), so its tiles are shorter than the forward pass's.
+static cl_status adjoint_plan(cl_ctx* c) {
+  AdjPlan& A = c->adj;
+  if (A.ready) return CL_OK;
+  const LatHost& H = c->lats[0];
+  const int narr = 4 * c->nf;
+  const std::vector<int> cand = tile_candidates(c->model, narr, c->esz, H.N, c->smem_optin);
+  if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no adjoint tile shape for N=%d", H.N);
+  const int BY = cand[0];
+  const long long tasks = (long long)(H.N / BY) * H.N;
+  A.grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
+  std::vector<Seg> segs;
+  std::vector<int> cta, sbeg, send;
+  if (!build_worklist({LatTiles{H.N, BY}}, A.grid, false, segs, cta, sbeg, send))
+    return fail(c, CL_EUNSUPPORTED, "adjoint work split too fine");
+  A.stage_bytes = (unsigned)stage_size(H.N, BY, narr, c->esz);
+  A.stages = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / A.stage_bytes);
+  A.smem = (size_t)A.stages * A.stage_bytes + SM_TAIL_BYTES;
+  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf);
+  CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.smem));
+  const size_t ab = (size_t)H.V * c->esz;
+  CU(cudaMalloc(&A.lam, 2 * (size_t)(2 * c->nf) * ab));
+  CU(cudaMalloc(&A.d_lat, sizeof(LatConst)));
+  CU(cudaMalloc(&A.d_segs, segs.size() * sizeof(Seg)));
+  CU(cudaMalloc(&A.d_cta, cta.size() * sizeof(int)));
+  CU(cudaMalloc(&A.d_part, (size_t)send[0] * NQ * sizeof(double)));
+  CU(cudaMalloc(&A.d_cnt, sizeof(unsigned)));
+  CU(cudaMalloc(&A.d_out, 2 * sizeof(double) + 2 * c->nsm * sizeof(double)));
+  CU(cudaMemsetAsync(A.d_cnt, 0, sizeof(unsigned), c->stream));
+  LatConst L = c->hlat[0];
+  L.BY = BY;
+  L.YT = H.N / BY;
+  L.narr = narr;
+  L.slot_begin = sbeg[0];
+  L.slot_end = send[0];
+  for (int par = 0; par < 2; ++par)
+    for (int a = 0; a < 2 * c->nf; ++a) {
+      L.buf[par][a] = arr_ptr(c, 0, par, a);
+      L.buf[par][2 * c->nf + a] = (char*)A.lam + ((size_t)par * 2 * c->nf + a) * ab;
+    }
+  CU(cudaMemcpyAsync(A.d_lat, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(A.d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(A.d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  int coop = 0, nb = 0;
+  CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->dev));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, THREADS, A.smem));
+  A.coop = coop && (long long)nb * c->nsm >= A.grid;
+  CU(cudaStreamSynchronize(c->stream));
+  A.ready = true;
+  return CL_OK;
+}
+
+// n reversed passes, coefficients dev_coef[4 i .. 4 i + 3] for the i-th.
+static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
+  AdjPlan& J = c->adj;
+  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf);
+  PassArgs A;
+  memset(&A, 0, sizeof(A));
+  A.lat = J.d_lat;
+  A.sc = c->d_sc;
+  A.segs = J.d_segs;
+  A.cta_seg = J.d_cta;
+  A.partials = J.d_part;
+  A.counters = J.d_cnt;
+  A.parity = c->parity;
+  A.write = 1;
+  A.stages = J.stages;
+  A.stage_bytes_max = J.stage_bytes;
+  A.nlat = 1;
+  A.wait_limit_ns = 2000000000ull;
+  A.adj = dev_coef;
+  A.npass = 1;
+  if (n > 1 && J.coop) {
+    A.npass = n;
+    A.gsync = c->d_gsync;
+    CU(cudaMemsetAsync(c->d_gsync, 0, 2 * sizeof(unsigned), c->stream));
+    void* args[] = {&A};
+    CU(cudaLaunchCooperativeKernel((const void*)k, dim3(J.grid), dim3(THREADS), args, J.smem, c->stream));
+    ++c->launches;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      A.adj = dev_coef + 4 * i;
+      A.parity = c->parity ^ (i & 1);
+      k<<<J.grid, THREADS, J.smem, c->stream>>>(A);
+      CHECK_LAUNCH();
+      ++c->launches;
+    }
+  }
+  if (n & 1) c->parity ^= 1;
+  return CL_OK;
+}
+
+extern "C" {
+
+cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int field, int what, double dk_bin,
+                     int bin, double* J, double* dJ_dq, double* dJ_dstate) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  if (nsteps < 0 || ckpt_every < 1) return fail(c, CL_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
+  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+    return fail(c, CL_EUNSUPPORTED, "the adjoint covers single scalar lattices");
+  if (c->p.expansion == CL_EXP_SELF)
+    return fail(c, CL_EUNSUPPORTED, "the adjoint covers fixed backgrounds (expansion off or fixed)");
+  if (objective == CL_OBJ_CHI_FRACTION) {
+    if (c->model != CL_MODEL_LPHI4_CHI) return fail(c, CL_EINVAL, "the chi energy fraction needs two fields");
+  } else if (objective == CL_OBJ_SPECTRUM_BIN) {
+    if (field < 0 || field >= c->nf || (what != 0 && what != 1) || !(dk_bin > 0.0))
+      return fail(c, CL_EINVAL, "bad spectrum objective");
+    const int nb = (int)std::floor(std::sqrt(3.0) * (c->lats[0].N / 2) / dk_bin) + 1;
+    if (bin < 0 || bin >= nb || nb > 2048) return fail(c, CL_EINVAL, "bin %d out of 0..%d", bin, nb - 1);
+  } else {
+    return fail(c, CL_EINVAL, "unknown objective %d", objective);
+  }
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  s = adjoint_plan(c);
+  if (s != CL_OK) return s;
+  const LatHost& H = c->lats[0];
+  const int na = 2 * c->nf;
+  const size_t ab = (size_t)H.V * c->esz;
+  std::vector<double> dsub;
+  schedule(c->p.integrator == CL_LF ? 2 : c->p.integrator, c->p.dt, dsub);
+  const int nsub = (int)dsub.size();
+  const int nchunk = (nsteps + ckpt_every - 1) / ckpt_every;
+  const long long npass = (long long)nsteps * nsub + 1;  // with the closing half kick
+  void* ckpt = nullptr;
+  double* dlog = nullptr;
+  double* dcoef = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(ckpt);
+    cudaFree(dlog);
+    cudaFree(dcoef);
+  };
+  auto copy_state = [&](void* dst_base, int ck, bool to_ckpt) -> cl_status {
+    for (int a = 0; a < na; ++a) {
+      char* cp = (char*)dst_base + ((size_t)ck * na + a) * ab;
+      void* st = arr_ptr(c, 0, c->parity, a);
+      CU(cudaMemcpyAsync(to_ckpt ? (void*)cp : st, to_ckpt ? st : (const void*)cp, ab, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    }
+    return CL_OK;
+  };
+#define ADJ_TRY(x)          \
+  do {                      \
+    cl_status s_ = (x);     \
+    if (s_ != CL_OK) {      \
+      cleanup();            \
+      return s_;            \
+    }                       \
+  } while (0)
+  if (cudaMalloc(&ckpt, (size_t)(nchunk + 1) * na * ab) != cudaSuccess ||
+      cudaMalloc(&dlog, (size_t)npass * 4 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dcoef, (size_t)npass * 4 * sizeof(double)) != cudaSuccess) {
+    cleanup();
+    return fail(c, CL_ENOMEM, "adjoint: checkpoint / log allocation failed");
+  }
+  // ---- forward: chunks of ckpt_every steps, the state saved after each ----
+  ADJ_TRY(copy_state(ckpt, 0, true));
+  std::vector<long long> chunk_first(nchunk + 1, 0);
+  long long pc = 0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int m = std::min(ckpt_every, nsteps - ch * ckpt_every);
+    std::vector<PassStep> steps;
+    for (int st = 0; st < m; ++st)
+      for (double d : dsub) {
+        if (!c->open) {
+          steps.push_back(PassStep{0.5 * d, 0.0, 0.5 * d, d});
+          c->open = true;
+        } else {
+          steps.push_back(PassStep{0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d});
+        }
+        c->dprev = d;
+      }
+    chunk_first[ch] = pc;
+    for (size_t b = 0; b < steps.size(); b += 4096) {
+      const int mm = (int)std::min<size_t>(4096, steps.size() - b);
+      ADJ_TRY(launch_passes(c, steps.data() + b, mm, red_for_step(c), 1, 0, dlog, pc));
+      pc += mm;
+    }
+    ADJ_TRY(copy_state(ckpt, ch + 1, true));
+  }
+  chunk_first[nchunk] = pc;
+  if (c->open) {  // the closing half kick, which also measures
+    PassStep st = {0.5 * c->dprev, 0.5 * c->dprev, 0.0, 0.0};
+    ADJ_TRY(launch_passes(c, &st, 1, 2, 1, 0, dlog, pc));
+    ++pc;
+    c->open = false;
+    c->obs_valid = true;
+  } else {
+    ADJ_TRY(measure(c, 0));
+  }
+  const long long nrev = pc;  // passes to reverse
+  // ---- seed: dJ/d(final state) and the objective ----
+  void* lam[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int a = 0; a < na; ++a) lam[a] = (char*)c->adj.lam + ((size_t)c->parity * na + a) * ab;
+  if (objective == CL_OBJ_CHI_FRACTION) {
+    const int nblk = 2 * c->nsm;
+    if (cudaSuccess != launch_seed_chi_fraction(c->fp32, c->d_lat, c->d_sc, c->parity, lam, c->adj.d_out + 2, nblk,
+                                                c->adj.d_out, c->stream)) {
+      cleanup();
+      return fail(c, CL_ECUDA, "adjoint seed launch failed");
+    }
+    c->launches += 2;
+  } else {
+    for (int a = 0; a < na; ++a) CU(cudaMemsetAsync(lam[a], 0, ab, c->stream));
+    const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
+    const int nblk = 2 * c->nsm;
+    if (c->spec_lats < 1) {
+      cudaFree(c->d_spec);
+      CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + (size_t)2 * 3 * 2048) * sizeof(double)));
+      c->spec_lats = 1;
+    }
+    double* bins = c->d_spec + (size_t)3 * 2048 * nblk;
+    double2* F = c->d_cplx;
+    CU(launch_to_complex(c->fp32, arr_ptr(c, 0, c->parity, 2 * field + what), F, H.V, c->stream));
+    ADJ_TRY(fft3d(c, H.N, F, -1));
+    CU(launch_bins(F, H.N, dk_bin, nb, nblk, c->d_spec, H.kIR, H.dx, bins, c->stream));
+    CU(launch_spectrum_seed(c->fp32, F, H.N, dk_bin, nb, bin, bins, H.kIR, H.dx, c->adj.d_out, 0, nullptr,
+                            c->stream));
+    ADJ_TRY(fft3d(c, H.N, F, +1));
+    CU(launch_spectrum_seed(c->fp32, F, H.N, dk_bin, nb, bin, bins, H.kIR, H.dx, c->adj.d_out, 1,
+                            lam[2 * field + what], c->stream));
+    c->launches += 5;
+  }
+  CU(cudaMemsetAsync(&c->d_sc[0].adjq, 0, sizeof(double), c->stream));
+  // ---- reverse sweep: coefficients of the recorded passes, last first ----
+  {
+    std::vector<double> hlog((size_t)nrev * 4), hrev((size_t)nrev * 4);
+    CU(cudaMemcpyAsync(hlog.data(), dlog, hlog.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (long long i = 0; i < nrev; ++i)
+      for (int k = 0; k < 4; ++k) hrev[4 * i + k] = hlog[4 * (nrev - 1 - i) + k];
+    CU(cudaMemcpyAsync(dcoef, hrev.data(), hrev.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the closing pass, then chunk by chunk, each started from its saved end state
+    long long done = 0;
+    if (nrev > chunk_first[nchunk]) {
+      ADJ_TRY(launch_adjoint(c, dcoef, 1));
+      done = 1;
+    }
+    for (int ch = nchunk - 1; ch >= 0; --ch) {
+      ADJ_TRY(copy_state(ckpt, ch + 1, false));
+      long long left = chunk_first[ch + 1] - chunk_first[ch];
+      while (left > 0) {
+        const int mm = (int)std::min<long long>(4096, left);
+        ADJ_TRY(launch_adjoint(c, dcoef + 4 * done, mm));
+        done += mm;
+        left -= mm;
+      }
+    }
+    ADJ_TRY(copy_state(ckpt, 0, false));
+  }
+  double out[2] = {0.0, 0.0}, adjq = 0.0;
+  CU(cudaMemcpyAsync(out, c->adj.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&adjq, &c->d_sc[0].adjq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (dJ_dstate) {
+    for (int a = 0; a < na; ++a) {
+      const void* src = (char*)c->adj.lam + ((size_t)c->parity * na + a) * ab;
+      CU(launch_convert(c->fp32, 1, src, c->d_tmp, H.V, c->stream));
+      ++c->launches;
+      CU(cudaMemcpyAsync(dJ_dstate + (size_t)a * H.V, c->d_tmp, H.V * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream));
+    }
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  cleanup();
+#undef ADJ_TRY
+  c->obs_valid = false;
+  if (J) *J = out[0];
+  if (dJ_dq) *dJ_dq = out[1] + adjq;
+  return check_status(c);
+}
+
+cl_status cl_ic_amplitude_grad(cl_ctx* c, const double* dJ_dstate, double* out) {
+  if (!c || !dJ_dstate || !out) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+    return fail(c, CL_EUNSUPPORTED, "amplitude gradients cover single scalar lattices");
+  const LatHost& H = c->lats[0];
+  double2* Lf = c->d_cplx;
+  double2* Lp = c->d_cplx + H.V;
+  double* dev_out = nullptr;
+  CU(cudaMalloc(&dev_out, 2 * (size_t)H.V * sizeof(double)));
+  cl_status s = CL_OK;
+  for (int f = 0; f < c->nf && s == CL_OK; ++f) {
+    for (int w = 0; w < 2 && s == CL_OK; ++w) {
+      double2* dst = w == 0 ? Lf : Lp;
+      if (cudaMemcpyAsync(c->d_tmp, dJ_dstate + (size_t)(2 * f + w) * H.V, H.V * sizeof(double),
+                          cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+          launch_to_complex(0, c->d_tmp, dst, H.V, c->stream) != cudaSuccess) {
+        s = fail(c, CL_ECUDA, "amplitude gradient: transfer failed");
+        break;
+      }
+      ++c->launches;
+      s = fft3d(c, H.N, dst, +1);
+    }
+    if (s != CL_OK) break;
+    if (launch_ic_amp_grad(Lf, Lp, dev_out, dev_out + H.V, c->d_lat, c->d_sc, H.ic, f, H.V, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(out + (size_t)(2 * f) * H.V, dev_out, 2 * (size_t)H.V * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+      s = fail(c, CL_ECUDA, "amplitude gradient: launch failed");
+      break;
+    }
+    ++c->launches;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) s = fail(c, CL_ECUDA, "amplitude gradient: sync");
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(dev_out);
+  return s;
 }
 
 }  // extern "C"

@@ -45,6 +45,8 @@ struct LatScalars {
   double pi2;                     // sum of pi^2 after the last kick (the next kick's pre-kick sum)
   double pi2A;                    // the same for the U(1) link momenta
   cl_energies_t obs;              // last measurement
+  double adjq;                    // adjoint sweep: accumulated dJ/dq of the passes
+  double H_ic;                    // a'/a the initial conditions were drawn with
   int status, pad;
 };
 
@@ -97,6 +99,12 @@ struct PassArgs {
   const PassStep* steps;
   int npass, pad2;
   unsigned* gsync;
+  // forward passes: when set, block 0 records the coefficients each pass
+  // uses, log[4 (log_base + pass) + {0..3}] = cd, c_k, a^{1+alpha}/dx^2, a^{3+alpha}
+  double* log;
+  long long log_base;
+  // adjoint passes: the coefficients of each reversed pass, 4 per pass as in log
+  const double* adj;
 };
 
 // Initial-condition parameters (program units).

@@ -86,6 +86,7 @@ __global__ void init_scalars_kernel(const LatConst* Lc, LatScalars* Sc, const IC
   S.rho0 = 0.0;
   S.pi2 = 0.0;
   S.pi2A = 0.0;
+  S.adjq = 0.0;
   double kin = 0.0;
   for (int k = 0; k < A.nf; ++k) kin += 0.5 * A.dphi0[k] * A.dphi0[k];
   const double rho = kin / pow(S.a, 2.0 * al) + pot_hom(A);
@@ -101,39 +102,40 @@ __global__ void init_scalars_kernel(const LatConst* Lc, LatScalars* Sc, const IC
     S.Hfix = 0.0;
     S.b = 0.0;
   }
+  S.H_ic = S.b / S.a;
 }
 
 // Fourier modes of the fluctuation of component f (F) and of its derivative (G).
 // Buffers are zeroed by the caller; only drawn modes are written.
-__global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, const LatScalars* Sc,
-                                const ICArgs A, int f) {
-  const LatConst& L = *Lc;
+// Draws of component f at Fourier site idx (its canonical member: idx <=
+// partner, *pid_out receives the partner): amplitudes r1, r2, phases t1, t2
+// in units of pi, and omega_k.  False for sites that stay zero.
+__device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long long idx, int f,
+                          long long* pid_out, double& r1, double& r2, double& t1, double& t2,
+                          double& omf) {
   const int N = L.N;
-  const long long V = L.V;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= V || idx == 0) return;
+  if (idx == 0) return false;
   const int x = (int)(idx % N), y = (int)((idx / N) % N), z = (int)(idx / ((long long)N * N));
   const int px = x ? N - x : 0, py = y ? N - y : 0, pz = z ? N - z : 0;
   const long long pid = px + (long long)N * (py + (long long)N * pz);
-  if (pid < idx) return;
-  const bool selfc = pid == idx;
+  *pid_out = pid;
+  if (pid < idx) return false;
   const bool charged = A.model == CL_MODEL_U1_HIGGS;
-  if (selfc && charged) return;  // keeps the charge density's zero mode at 0
+  if (pid == idx && charged) return false;  // keeps the charge density's zero mode at 0
   const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
   const double k = A.kIR * sqrt((double)(nx * nx + ny * ny + nz * nz));
-  if (A.kcut >= 0.0 && k > A.kcut) return;
-  if (A.amp2 <= 0.0) return;
-  const double a = Sc->a, al = L.alpha;
+  if (A.kcut >= 0.0 && k > A.kcut) return false;
+  if (A.amp2 <= 0.0) return false;
   // every component must have a real frequency for the mode to be populated
   double om[2] = {0.0, 0.0};
   for (int c = 0; c < A.nf; ++c) {
     const double w2 = k * k + a * a * mass2_hom(A, c);
-    if (w2 <= 0.0) return;
+    if (w2 <= 0.0) return false;
     om[c] = sqrt(w2);
   }
+  omf = om[f];
   const double vol = (double)N / L.dx;
   const double P = A.amp2 * vol * vol * vol / (2.0 * a * a * om[f]);
-  double r1, r2, t1, t2;
   if (!charged) {
     double u0, u1, v0, v1;
     draw_pair(A.seed, (unsigned)idx, f, 0, u0, u1);
@@ -158,6 +160,19 @@ __global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, cons
       t2 = 2.0 * v1 + 2.0 * w0 - 2.0 * v0;
     }
   }
+  return true;
+}
+
+__global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, const LatScalars* Sc,
+                                const ICArgs A, int f) {
+  const LatConst& L = *Lc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.V) return;
+  const double a = Sc->a, al = L.alpha;
+  long long pid = 0;
+  double r1, r2, t1, t2, om;
+  if (!mode_draw(L, A, a, idx, f, &pid, r1, r2, t1, t2, om)) return;
+  const bool selfc = pid == idx;
   double s1, c1, s2, c2;
   sincospi(t1, &s1, &c1);
   sincospi(t2, &s2, &c2);
@@ -165,7 +180,7 @@ __global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, cons
   const double z1r = r1 * c1, z1i = r1 * s1, z2r = r2 * c2, z2i = r2 * s2;
   double fr = (z1r + z2r) * isq2, fi = (z1i + z2i) * isq2;
   // derivative: a^{alpha-1} i omega (z1 - z2)/sqrt2 - H dphi, H = b/a
-  const double pre = pow(a, al - 1.0) * om[f] * isq2;
+  const double pre = pow(a, al - 1.0) * om * isq2;
   const double H = Sc->b / a;
   double gr = -pre * (z1i - z2i) - H * fr;
   double gi = pre * (z1r - z2r) - H * fi;
@@ -177,6 +192,41 @@ __global__ void ic_modes_kernel(double2* F, double2* G, const LatConst* Lc, cons
   G[idx] = make_double2(gr, gi);
   F[pid] = make_double2(fr, -fi);
   G[pid] = make_double2(gr, -gi);
+}
+
+// Gradient of an objective with respect to the drawn amplitudes |z1|, |z2| of
+// component f, from the gradient lam with respect to the initial state:
+// Lf = sum_x lam_phi(x) e^{+ik.x}, Lp = sum_x lam_pi(x) e^{+ik.x} (unnormalised
+// transforms), and with e_j = e^{i pi t_j}/sqrt2,
+//   dJ/d|z_j| = (s/V) Re[ e_j Lf + a^{3-alpha} (+-a^{alpha-1} i omega - H_ic) e_j Lp ],
+// s = 2 for a mode and its conjugate partner, 1 for a self-conjugate site;
+// zero at non-canonical sites and at modes that were not drawn.
+__global__ void ic_amp_grad_kernel(const double2* Lf, const double2* Lp, double* out1, double* out2,
+                                   const LatConst* Lc, const LatScalars* Sc, const ICArgs A, int f) {
+  const LatConst& L = *Lc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L.V) return;
+  out1[idx] = 0.0;
+  out2[idx] = 0.0;
+  const double a = Sc->a0, al = L.alpha;
+  long long pid = 0;
+  double r1, r2, t1, t2, om;
+  if (!mode_draw(L, A, a, idx, f, &pid, r1, r2, t1, t2, om)) return;
+  const double s = (pid == idx ? 1.0 : 2.0) / (double)L.V;
+  const double isq2 = 0.70710678118654752440;
+  const double a3 = pow(a, 3.0 - al), am1 = pow(a, al - 1.0), H = Sc->H_ic;
+  const double2 F = Lf[idx], G = Lp[idx];
+  for (int j = 0; j < 2; ++j) {
+    double sn, cs;
+    sincospi(j == 0 ? t1 : t2, &sn, &cs);
+    const double er = cs * isq2, ei = sn * isq2;
+    const double sg = j == 0 ? 1.0 : -1.0;
+    // c = a^{3-alpha} (sg a^{alpha-1} i omega - H) e
+    const double wr = -a3 * H, wi = a3 * sg * am1 * om;
+    const double cr = wr * er - wi * ei, ci = wr * ei + wi * er;
+    const double v = s * ((er * F.x - ei * F.y) + (cr * G.x - ci * G.y));
+    (j == 0 ? out1 : out2)[idx] = v;
+  }
 }
 
 // phi = phi0 + Re(F)/V, pi = a^{3-alpha} (phi0' + Re(G)/V), stored in T.
@@ -423,6 +473,13 @@ __global__ void spec_mean_kernel(const double* rows, int nl, int nb, double* out
 
 cudaError_t launch_spec_mean(const double* rows, int nl, int nb, double* out, cudaStream_t st) {
   spec_mean_kernel<<<(nb + 127) / 128, 128, 0, st>>>(rows, nl, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic_amp_grad(const double2* Lf, const double2* Lp, double* out1, double* out2,
+                               const LatConst* L, const LatScalars* S, const ICArgs& A, int f,
+                               long long V, cudaStream_t st) {
+  ic_amp_grad_kernel<<<(unsigned)((V + 255) / 256), 256, 0, st>>>(Lf, Lp, out1, out2, L, S, A, f);
   return cudaGetLastError();
 }
 

@@ -289,6 +289,15 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     }
     __syncthreads();
     if (flag[0]) goto timeout;
+    if (P.log && blockIdx.x == 0 && tid == 0) {  // coefficients of this pass, for an adjoint sweep
+      const LatScalars* S0 = &P.sc[0];
+      const double ckp = P.steps ? P.steps[pass].ck : P.ck;
+      double* lg = P.log + 4 * (P.log_base + pass);
+      lg[0] = __ldcg(&S0->cd);
+      lg[1] = ckp;
+      lg[2] = ckp * __ldcg(&S0->apow1) * P.lat[0].inv_dx2;
+      lg[3] = ckp * __ldcg(&S0->apow3);
+    }
 
     for (int i = 0; i < ns; ++i) {
       const Seg sg = P.segs[sb + i];
