@@ -82,6 +82,7 @@ struct AdjPlan {
   double* d_part = nullptr;
   unsigned* d_cnt = nullptr;
   double* d_out = nullptr;       // J and the explicit dJ/dq of the objective
+  int nslot = 0;
 };
 
 // A multi-pass launch recorded in a CUDA graph, replayed when the same
@@ -305,6 +306,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   A.segs = c->d_segs;
   A.cta_seg = c->d_cta;
   A.partials = c->d_part;
+  A.nslot = c->nslot;
   A.counters = c->d_cnt;
   A.ck = st[0].ck;
   A.wout = st[0].wout;
@@ -1249,6 +1251,7 @@ static cl_status adjoint_plan(cl_ctx* c) {
   CU(cudaMalloc(&A.d_segs, segs.size() * sizeof(Seg)));
   CU(cudaMalloc(&A.d_cta, cta.size() * sizeof(int)));
   CU(cudaMalloc(&A.d_part, (size_t)send[0] * NQ * sizeof(double)));
+  A.nslot = send[0];
   CU(cudaMalloc(&A.d_cnt, sizeof(unsigned)));
   CU(cudaMalloc(&A.d_out, 2 * sizeof(double) + 2 * c->nsm * sizeof(double)));
   CU(cudaMemsetAsync(A.d_cnt, 0, sizeof(unsigned), c->stream));
@@ -1286,6 +1289,7 @@ static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
   A.segs = J.d_segs;
   A.cta_seg = J.d_cta;
   A.partials = J.d_part;
+  A.nslot = J.nslot;
   A.counters = J.d_cnt;
   A.parity = c->parity;
   A.write = 1;

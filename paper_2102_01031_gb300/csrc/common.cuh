@@ -87,12 +87,13 @@ struct PassArgs {
   LatScalars* sc;
   const Seg* segs;
   const int* cta_seg;        // [gridDim.x + 1]
-  double* partials;          // [nslot][NQ]
+  double* partials;          // [NQ][nslot]: quantity-major, so a lattice's slots are contiguous
   unsigned* counters;        // [nlat]
   double ck, wout, win, dnext;
   int parity, write, set_rho0, stages;
   unsigned stage_bytes_max;  // bytes of one stage (max over lattices)
   int nlat;                  // lattices advanced by the launch
+  int nslot;                 // partial-sum slots of the launch (all lattices)
   unsigned long long wait_limit_ns;  // bound of every wait
   // several passes in one cooperative launch (npass > 1): weights per pass and
   // two monotonic counters (writes arrived, tails done), zeroed before launch
@@ -277,6 +278,27 @@ __device__ __forceinline__ double warp_sum(const Acc<double>& a) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Fixed-order FP64 sum of part[begin .. end) over one warp (result on every
+// lane): lane l adds slots begin + l, + 32, ..., all of its first eight loads
+// issued before any add (one memory round trip for up to 256 slots), then a
+// shuffle tree.  The values were written by other CTAs of the launch (read
+// past L1).
+__device__ __forceinline__ double warp_slot_sum(const double* part, int begin, int end, int lane) {
+  double v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = begin + lane + 32 * i;
+    v[i] = k < end ? __ldcg(part + k) : 0.0;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += v[i];
+  for (int k = begin + lane + 256; k < end; k += 32) s += __ldcg(part + k);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
 }
 
 }  // namespace clg

@@ -4,7 +4,8 @@
 //   drift (deferred from the previous pass):  phi += cd * pi,   cd = h abar^{alpha-3}
 //   kick:   pi += c_k [ a^{1+alpha} Lap phi - a^{3+alpha} V_{,phi} ]
 //   Lap phi = sum_i [phi(n+i) - 2 phi(n) + phi(n-i)] / dx^2       (eqs. neutrald, forwardbackwardd)
-//   sums:   sum pi^2 before / after the kick, sum_i (grad^+_i phi)^2, sum V (+ means)
+//   sums:   sum pi^2 before / after the kick, sum_i (grad^+_i phi)^2 (as -sum phi Lap phi
+//           in the Friedmann passes), sum V (+ means in measurement passes)
 //
 // One pass per integrator stage: each field and momentum array is read once
 // from HBM and written once.  A CTA owns runs of (y-tile, z-plane) tasks
@@ -33,6 +34,11 @@ template <int NF> struct ScalarPot;
 template <> struct ScalarPot<1> {
   static constexpr int NPOT = 1;
   template <typename T>
+  __device__ __forceinline__ static T total(const T (&f)[1], T hq) {
+    const T f2 = f[0] * f[0];
+    return T(0.25) * f2 * f2;
+  }
+  template <typename T>
   __device__ __forceinline__ static void eval(const T (&f)[1], T q, T (&d)[1], T (&t)[1]) {
     const T f2 = f[0] * f[0];
     d[0] = f2 * f[0];
@@ -41,6 +47,12 @@ template <> struct ScalarPot<1> {
 };
 template <> struct ScalarPot<2> {
   static constexpr int NPOT = 2;
+  // phi^4/4 + (q/2) phi^2 chi^2 = p2 (p2/4 + (q/2) c2), hq = q/2
+  template <typename T>
+  __device__ __forceinline__ static T total(const T (&f)[2], T hq) {
+    const T p2 = f[0] * f[0], c2 = f[1] * f[1];
+    return p2 * fmaT(T(0.25), p2, hq * c2);
+  }
   template <typename T>
   __device__ __forceinline__ static void eval(const T (&f)[2], T q, T (&d)[2], T (&t)[2]) {
     const T p2 = f[0] * f[0], c2 = f[1] * f[1];
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   constexpr int VX = V16<T>::n;
   constexpr int NA = 2 * NF;
   constexpr int NPOT = ScalarPot<NF>::NPOT;
-  // RED = 1 sums: pi^2 after the kick, (grad^+ phi)^2, V.  The pre-kick sum of
+  // RED = 1 sums: pi^2 after the kick, phi Lap phi (= -(grad^+ phi)^2 summed), V.  The pre-kick sum of
   // pi^2 is the previous kick's post-kick sum (a drift leaves pi unchanged),
   // carried in the lattice scalars.
   constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 3 : 6 * NF + NPOT);
@@ -190,12 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   auto run_tail = [&](int lat, const PassStep& st) {
     const LatConst& L = P.lat[lat];
     if (warp < NUSED) {
-      double s = 0.0;
-#pragma unroll 4
-      for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
-        s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      const double s = warp_slot_sum(P.partials + (size_t)warp * P.nslot, L.slot_begin, L.slot_end, lane);
       if (lane == 0) red[32 * NQ + warp] = s;
     }
     __syncthreads();
@@ -208,13 +215,14 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       ScalarState W;
       load_state_cg(W, &P.sc[lat]);
       const double* sum = red + 32 * NQ;
-      const double a = W.a, a2 = a * a, a6 = a2 * a2 * a2;
-      const double ck = 0.5 * L.inv_V / a6, cg = 0.5 * L.inv_V * L.inv_dx2 / a2;
+      const double a = W.a, ia2 = 1.0 / (a * a), ia6 = ia2 * ia2 * ia2;
+      const double ck = 0.5 * L.inv_V * ia6, cg = 0.5 * L.inv_V * L.inv_dx2 * ia2;
       PassSums E = {0, 0, 0, 0, 0, 0, 0};
       if (RED > 0) {
         double spre = 0, spost = 0, gg = 0, vs = 0;
         if (RED == 1) {
-          spre = W.pi2; spost = sum[0]; gg = sum[1]; vs = sum[2];
+          // slot 1 holds sum phi Lap phi = -sum (grad^+ phi)^2
+          spre = W.pi2; spost = sum[0]; gg = -sum[1]; vs = sum[2];
         } else {
           for (int f = 0; f < NF; ++f) {
             spre += sum[6 * f]; spost += sum[6 * f + 1]; gg += sum[6 * f + 2];
@@ -324,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       for (int k = 0; k < 3; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
       const T cd = cf[0], A1 = cf[1], A3 = cf[2];
       const bool drifting = cd != T(0);
-      const T q = (T)L.q;
+      const T q = (T)L.q, hq = (T)(0.5 * L.q);
       const unsigned amask = __ballot_sync(0xffffffffu, active);
       T* dst[NA];
 #pragma unroll
@@ -401,12 +409,14 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
               const T zl = below[f][v], zh = above[f][v];
               lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
                           ((zl + zh) - T(2) * c);
-              if (RED > 0) {
+              if (RED == 2) {  // forward differences (eq. EK_EG_EV with grad^+)
                 const T zp = sg.dir > 0 ? zh : zl;
                 const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
-                const T gg = gx * gx + gy * gy + gz * gz;
-                if (RED == 2) gf += gg;
-                else g2[v] += gg;
+                gf += gx * gx + gy * gy + gz * gz;
+              } else if (RED == 1) {
+                // sum_n (grad^+ phi)^2 = -sum_n phi Lap phi (summation by parts on the
+                // periodic lattice): one FMA on the Laplacian the kick needs anyway
+                g2[v] = fmaT(c, lap[f][v], g2[v]);
               }
             }
             if (RED == 2) acc[6 * f + 2].add(gf);
@@ -424,8 +434,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             if (RED == 1) {
 #pragma unroll
               for (int f = 0; f < NF; ++f) spost = fmaT(pn[f][v], pn[f][v], spost);
-#pragma unroll
-              for (int t = 0; t < NPOT; ++t) vs += tv[t];
+              vs += ScalarPot<NF>::total(fv, hq);
               gsum += g2[v];
             } else if (RED == 2) {
 #pragma unroll
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) {
-          P.partials[(size_t)sg.slot * NQ + warp] = v;
+          P.partials[(size_t)warp * P.nslot + sg.slot] = v;
           __threadfence();
         }
       }

@@ -174,7 +174,7 @@ __device__ bool ring_flush(const Ring& R, const PassArgs& P, const Seg& sg, Acc<
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) {
-      P.partials[(size_t)sg.slot * NQ + warp] = v;
+      P.partials[(size_t)warp * P.nslot + sg.slot] = v;
       __threadfence();
     }
   }
@@ -190,19 +190,15 @@ __device__ bool ring_flush(const Ring& R, const PassArgs& P, const Seg& sg, Acc<
   return true;
 }
 
-// Lattice-wide sums of the first NUSED slots into red[32 * NQ + k]: warp k
-// strides its lanes over the lattice's slots, then a fixed shuffle tree, so
-// the order does not depend on timing.  All threads; ends with a barrier.
+// Lattice-wide sums of the first NUSED quantities into red[32 * NQ + k]:
+// warp k sums the lattice's slots of quantity k in a fixed order
+// (warp_slot_sum), so the result does not depend on timing.  All threads;
+// ends with a barrier.
 template <int NUSED>
 __device__ void ring_slot_sums(const Ring& R, const PassArgs& P, const LatConst& L, int warp,
                                int lane) {
   if (warp < NUSED) {
-    double s = 0.0;
-#pragma unroll 4
-    for (int k = L.slot_begin + lane; k < L.slot_end; k += 32)
-      s += __ldcg(&P.partials[(size_t)k * NQ + warp]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const double s = warp_slot_sum(P.partials + (size_t)warp * P.nslot, L.slot_begin, L.slot_end, lane);
     if (lane == 0) R.red[32 * NQ + warp] = s;
   }
   __syncthreads();

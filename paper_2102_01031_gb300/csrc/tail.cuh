@@ -88,8 +88,11 @@ __device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, SS&
                                        const PassSums& E, bool have_sums) {
   const double a = S.a;
   if (have_sums && L.expansion == CL_EXP_SELF) {
-    S.b += P.wout * kernel_a(L, a, E.EKpre, E.EG, E.EV, E.EKApre, E.EGA);
-    S.b += P.win * kernel_a(L, a, E.EKpost, E.EG, E.EV, E.EKA, E.EGA);
+    // K_a of both kicks share a^{2alpha+1}/3 (f_s/m_p)^2 (one FP64 chain on the critical path)
+    const double al = L.alpha, pref = apow(L, a, 2, 1) * (1.0 / 3.0) * L.fm2;
+    const double common = al * E.EG + (al + 1.0) * E.EV;
+    S.b += P.wout * (pref * ((al - 2.0) * E.EKpre + common + (al - 1.0) * (E.EKApre + E.EGA)));
+    S.b += P.win * (pref * ((al - 2.0) * E.EKpost + common + (al - 1.0) * (E.EKA + E.EGA)));
   }
 }
 
