@@ -41,9 +41,11 @@ WORKLOAD = ("lphi4+chi q=100, 256^3, kIR=0.1, alpha=1, VV4 dt=0.005, self-consis
 # bytes one DK pass must move: 2 fields x (field, momentum) x (read + write)
 PASS_BYTES_PER_SITE = {"f32": 2 * 2 * 2 * 4, "f64": 2 * 2 * 2 * 8}
 PASSES_PER_STEP = 3
-# DRAM bytes (read + write) per DK-pass launch from the ncu capture summarised in
-# profiles/dk_pass_fp32_256_ncu.md, valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "2f62b055c964d9a5", "bytes_per_launch": 551128832}}
+# DRAM bytes (read + write) per DK pass from the ncu capture summarised in
+# profiles/dk_pass_fp32_256_ncu.md (one cooperative launch of the three VV4
+# passes of a step, divided by 3), valid only for the kernel source it was
+# taken on.
+NCU_TRAFFIC = {"f32": {"source_hash": "6d976e92e0bdd35b", "bytes_per_launch": 579050069}}
 
 
 def peaks():
@@ -285,6 +287,7 @@ def run_ours(args):
     bpl64 = PASS_BYTES_PER_SITE["f64"] * sites
     achieved64 = bpl64 / (f64["pass_ms"] * 1e-3) / 1e9
     traffic = ncu_traffic("f32")
+    others = other_workloads(P, torch, stream, peak) if not args.no_extra else None
     budget = float(args.cpu_budget)
     L, n_ref, csteps = cpu_oracle_rate(budget)
     t0 = time.perf_counter()
@@ -318,12 +321,75 @@ def run_ours(args):
                        "fp32_speedup": value / v64},
         "sanity": {"rho_f32": f32["rho"], "rho_f64": f64["rho"], "a_f32": f32["a"],
                    "nonfinite": f32["nonfinite"] + f64["nonfinite"]},
+        "other_rows": others,
     }
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def other_workloads(P, torch, stream, peak):
+    """The other hot-path rows, timed briefly with the library's pass-timing hook
+    (CUDA events around every launch on the lattice stream): the U(1) pass at
+    256^3, the 64-lattice ensemble, and the adjoint sweep's cost at 128^3."""
+    out = {}
+    # U(1) Abelian-Higgs, 256^3, FP32, leapfrog dt = 0.01, no expansion
+    u1 = dict(dt=0.01, integrator=P.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
+              phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=P.EXP_OFF, fstar_over_mp=0.5)
+    lat = P.Lattice(P.MODEL_U1_HIGGS, 256, 0.1, 1.0, 1, P.make_params(precision=P.FP32, stream=stream, **u1))
+    lat.step(20)
+    torch.cuda.synchronize()
+    lat.pass_timing(reset=True)
+    lat.enable_pass_timing(True)
+    lat.step(500)
+    torch.cuda.synchronize()
+    ms, n = lat.pass_timing(reset=True)
+    rel = lat.gauss()[0]
+    lat.close()
+    gbs = 256 ** 3 * 10 * 2 * 4 / (ms / n * 1e-3) / 1e9
+    out["u1_higgs_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+                                   "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
+                                   "gauss_rel_after_520_steps": rel, "kernel": "dk_pass_u1<float,0>"}
+    # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
+    Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
+    E = P.Ensemble(P.MODEL_LPHI4_CHI, Ns, [KIR * N_LAT / n for n in Ns], ALPHA, list(range(1, 65)),
+                   P.make_params(precision=P.FP32, stream=stream, **PARAMS))
+    E.step(5)
+    torch.cuda.synchronize()
+    E.pass_timing(reset=True)
+    E.enable_pass_timing(True)
+    E.step(100)
+    torch.cuda.synchronize()
+    ms, n = E.pass_timing(reset=True)
+    E.close()
+    sites = sum(x ** 3 for x in Ns)
+    gbs = sites * 32 / (ms / n * 1e-3) / 1e9
+    out["ensemble_64_fp32_vv4"] = {"site_updates_per_s": sites * 100 / (ms * 1e-3), "pass_us": ms / n * 1e3,
+                                   "achieved_gbs": gbs, "frac_hbm": gbs / peak, "sites": sites,
+                                   "launches_per_step_call": 1}
+    # adjoint: 128^3 FP32, VV4 dt = 0.005, no expansion, 1000 steps, checkpoints every 500
+    adj = dict(PARAMS, expansion=P.EXP_OFF)
+    g = P.Lattice(P.MODEL_LPHI4_CHI, 128, KIR * N_LAT / 128, ALPHA, SEED,
+                  P.make_params(precision=P.FP32, stream=stream, **adj))
+    g.step(5)
+    g.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step(1000)
+    g.sync()
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J, dq, _ = g.adjoint(1000, 500)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    g.close()
+    out["adjoint_128_fp32_vv4"] = {"forward_s": t_fwd, "forward_plus_reverse_s": t_adj,
+                                   "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq,
+                                   "steps": 1000, "ckpt_every": 500}
+    return out
 
 
 def ctypes_sizeof_energies(P):
@@ -340,6 +406,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

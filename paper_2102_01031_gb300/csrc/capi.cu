@@ -446,7 +446,9 @@ cl_status check_status(cl_ctx* c) {
 
 // Work list.  The plane tasks of all lattices (lattice-major, then y-tile,
 // then z; a task is BY rows x N sites of one plane) are cut into `grid`
-// contiguous runs of equal site count, one per CTA; a run is split into
+// contiguous runs of equal cost, one per CTA (a task costs its sites, but at
+// least a whole CTA's worth: a tile of a small lattice leaves threads idle
+// and takes about as long as a full one); a run is split into
 // segments at y-tile and lattice boundaries.  Odd CTAs march down (and take
 // their segments in reverse order) so that neighbouring runs reach their
 // shared boundary plane at the same time, when halo planes come from L2
@@ -455,6 +457,7 @@ cl_status check_status(cl_ctx* c) {
 // numbered lattice-major so that a lattice's slots are contiguous.
 struct LatTiles {
   int N, BY;
+  int min_sites;  // a plane task costs at least this many sites (a task runs one CTA however few of its threads work)
 };
 
 bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, std::vector<Seg>& segs,
@@ -466,7 +469,7 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, s
   for (size_t l = 0; l < nl; ++l) {
     const long long nt = (long long)(lats[l].N / lats[l].BY) * lats[l].N;
     toff[l + 1] = toff[l] + nt;
-    coff[l + 1] = coff[l] + (double)nt * lats[l].BY * lats[l].N;
+    coff[l + 1] = coff[l] + (double)nt * std::max(lats[l].BY * lats[l].N, lats[l].min_sites);
   }
   // first task of CTA k: where the running site count reaches k/grid of the total
   auto boundary = [&](int k) -> long long {
@@ -475,7 +478,7 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, s
     const double target = coff[nl] * (double)k / (double)grid;
     size_t l = 0;
     while (l + 1 < nl && coff[l + 1] <= target) ++l;
-    const double per = (double)lats[l].BY * lats[l].N;
+    const double per = (double)std::max(lats[l].BY * lats[l].N, lats[l].min_sites);
     const long long t = toff[l] + (long long)std::llround((target - coff[l]) / per);
     return std::min(std::max(t, toff[l]), toff[l + 1]);
   };
@@ -533,9 +536,9 @@ bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, s
 }  // namespace
 
 // Autotuner: the tile height of each (model, precision, N) is the candidate
-// with the shortest measured DK pass on a scratch lattice of that size (two
-// warm-up steps, then eight VV2 steps timed with CUDA events), kept for the
-// life of the process.
+// with the shortest measured DK pass on scratch lattices of that size (as
+// many as it takes to give every SM work; two warm-up steps, then eight VV2
+// steps timed with CUDA events), kept for the life of the process.
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
@@ -556,6 +559,16 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
   if (cand.size() > 4) cand.resize(4);
   int best = cand[0];
   double best_t = 1e300;
+  // enough identical scratch lattices to give every SM at least 8 plane tasks
+  // with the tallest tile, so that the timing reflects throughput, not latency
+  const long long tasks1 = (long long)(N / cand[0]) * N;
+  const long long vbytes = (long long)N * N * N * c->narr * 2 * c->esz;
+  int m = (int)std::min<long long>(64, std::max<long long>(1, (8LL * c->nsm + tasks1 - 1) / tasks1));
+  m = (int)std::max<long long>(1, std::min<long long>(m, (1LL << 30) / std::max<long long>(1, vbytes)));
+  const std::vector<int> Ns(m, N);
+  const std::vector<double> kIRs(m, kIR);
+  std::vector<uint64_t> seeds(m);
+  for (int i = 0; i < m; ++i) seeds[i] = 1 + i;
   for (int by : cand) {
     cl_params q = c->p;
     q.autotune = 0;
@@ -563,8 +576,7 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
     q.integrator = CL_VV2;
     q.stream = c->stream;
     cl_ctx* t = nullptr;
-    const uint64_t seed = 1;
-    cl_status s = cl_ensemble_init(&t, c->model, 1, &N, &kIR, c->alpha, &seed, &q);
+    cl_status s = cl_ensemble_init(&t, c->model, m, Ns.data(), kIRs.data(), c->alpha, seeds.data(), &q);
     if (s != CL_OK) return fail(c, s, "autotune: %s", cl_last_error(nullptr));
     double ms = 0.0;
     int64_t np = 0;
@@ -741,7 +753,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     } else {
       L.BY = cand[0];
     }
-    tiles.push_back(LatTiles{L.N, L.BY});
+    tiles.push_back(LatTiles{L.N, L.BY, THREADS * tile_vx(c->model, c->esz)});
   }
   // work list: one CTA per SM, at least 8 plane tasks each
   long long tasks = 0;
@@ -1238,7 +1250,7 @@ static cl_status adjoint_plan(cl_ctx* c) {
   A.grid = (int)std::max<long long>(1, std::min<long long>(c->nsm, tasks / 8));
   std::vector<Seg> segs;
   std::vector<int> cta, sbeg, send;
-  if (!build_worklist({LatTiles{H.N, BY}}, A.grid, false, segs, cta, sbeg, send))
+  if (!build_worklist({LatTiles{H.N, BY, THREADS * tile_vx(c->model, c->esz)}}, A.grid, false, segs, cta, sbeg, send))
     return fail(c, CL_EUNSUPPORTED, "adjoint work split too fine");
   A.stage_bytes = (unsigned)stage_size(H.N, BY, narr, c->esz);
   A.stages = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / A.stage_bytes);

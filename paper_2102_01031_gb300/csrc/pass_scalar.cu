@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // slots a pass reduces: the Friedmann sums, or every measured sum plus the
   // non-finite count (slot NQ - 1)
   constexpr int NUSED = RED == 0 ? 0 : (RED == 1 ? 3 : NQ);
+  // arrivals per partial-sum slot on the lattice's count (one per quantity; one when there are none)
+  constexpr int NARRIVE = NUSED > 0 ? NUSED : 1;
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int S = P.stages;
@@ -195,18 +197,22 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     return reinterpret_cast<const T*>(smem + (size_t)s * P.stage_bytes_max);
   };
 
-  // Friedmann update of lattice `lat` once all its slots are written: warp k
-  // sums slot k over the lattice's runs (lanes stride, then a fixed shuffle
-  // tree, so the order does not depend on timing); thread 0 updates a, b and
-  // the coefficients of the next pass.
-  auto run_tail = [&](int lat, const PassStep& st) {
-    const LatConst& L = P.lat[lat];
-    if (warp < NUSED) {
-      const double s = warp_slot_sum(P.partials + (size_t)warp * P.nslot, L.slot_begin, L.slot_end, lane);
-      if (lane == 0) red[32 * NQ + warp] = s;
+  // Friedmann updates of the lattices pend[base .. base + nb) (nb <= 32) once
+  // all their slots are written: the warps share the (lattice, quantity)
+  // sums, each over the lattice's slots in a fixed order (warp_slot_sum), so
+  // the result does not depend on timing; then thread l updates a, b and the
+  // next pass's coefficients of lattice pend[base + l], all lattices at once.
+  auto run_tails = [&](int base, int nb, const PassStep& st) {
+    for (int it = warp; it < nb * NUSED; it += CONSUMER_WARPS) {
+      const int l = it / NUSED, q = it - l * NUSED;
+      const LatConst& L = P.lat[pend[base + l]];
+      const double s = warp_slot_sum(P.partials + (size_t)q * P.nslot, L.slot_begin, L.slot_end, lane);
+      if (lane == 0) red[l * NQ + q] = s;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < nb) {
+      const int lat = pend[base + tid];
+      const LatConst& L = P.lat[lat];
       PassArgs Q = P;
       Q.ck = st.ck;
       Q.wout = st.wout;
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       Q.dnext = st.dnext;
       ScalarState W;
       load_state_cg(W, &P.sc[lat]);
-      const double* sum = red + 32 * NQ;
+      const double* sum = red + tid * NQ;
       const double a = W.a, ia2 = 1.0 / (a * a), ia6 = ia2 * ia2 * ia2;
       const double ck = 0.5 * L.inv_V * ia6, cg = 0.5 * L.inv_V * L.inv_dx2 * ia2;
       PassSums E = {0, 0, 0, 0, 0, 0, 0};
@@ -276,6 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
 
   Acc<T> acc[NACC];
   float nonfinite = 0.f;
+  int fbuf = 0;
 #pragma unroll
   for (int k = 0; k < NACC; ++k) acc[k].zero();
 
@@ -483,6 +490,10 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       if (!sg.flush) continue;
 
       // ---- end of this CTA's run on the lattice: flush the sums into its slot ----
+      // (two halves of red[] alternate: a warp can reach the next flush while
+      // others still read this one, but not the one after, which waits for all)
+      double* rb = red + fbuf * CONSUMER_WARPS * NQ;
+      fbuf ^= 1;
       if (RED > 0) {
 #pragma unroll
         for (int k = 0; k < NUSED; ++k) {
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
             v = (double)c;
           }
-          if (lane == 0) red[warp * NQ + k] = v;
+          if (lane == 0) rb[warp * NQ + k] = v;
         }
       }
 #pragma unroll
@@ -503,26 +514,30 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       nonfinite = 0.f;
       __syncthreads();
       if (flag[0]) goto timeout;
-      if (warp < NUSED) {  // warp k: fixed shuffle tree over the 16 warp partials of slot k
-        double v = lane < CONSUMER_WARPS ? red[lane * NQ + warp] : 0.0;
+      // warp k: fixed shuffle tree over the 16 warp partials of quantity k, the
+      // slot's value, and one arrival on the lattice's count (no further block
+      // barrier: the next segment starts at once); the arrival that completes
+      // the count queues the lattice's tail
+      if (warp < NARRIVE) {
+        double v = 0.0;
+        if (NUSED > 0) {
+          v = lane < CONSUMER_WARPS ? rb[lane * NQ + warp] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        }
         if (lane == 0) {
-          P.partials[(size_t)warp * P.nslot + sg.slot] = v;
+          if (NUSED > 0) P.partials[(size_t)warp * P.nslot + sg.slot] = v;
           __threadfence();
+          const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
+          const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
+          if (prev == NARRIVE * nslot - 1u) pend[atomicAdd(const_cast<int*>(&flag[3]), 1)] = sg.lat;
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        const unsigned nslot = (unsigned)(L.slot_end - L.slot_begin);
-        const unsigned prev = atomicAdd(&P.counters[sg.lat], 1u);
-        flag[2] = sg.lat;
-        if (prev == nslot - 1u) pend[flag[3]++] = sg.lat;
-      }
-      __syncthreads();
+      if (tid == 0) flag[2] = sg.lat;
     }
 
     // ---- end of the pass ----
+    __syncthreads();  // every warp's writes and arrivals of the pass are done
     if (multi && tid == 0) {  // this CTA's writes are done
       __threadfence();
       fence_proxy_async_global();
@@ -531,9 +546,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     {
       const int npend = flag[3];
       const PassStep pst = P.steps ? P.steps[pass] : PassStep{P.ck, P.wout, P.win, P.dnext};
-      for (int k = 0; k < npend; ++k) {
+      for (int base = 0; base < npend; base += 32) {
         __threadfence();
-        run_tail(pend[k], pst);
+        run_tails(base, min(32, npend - base), pst);
       }
       __syncthreads();
       if (tid == 0) flag[3] = 0;
