@@ -340,11 +340,11 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       const T cd = cf[0], A1 = cf[1], A3 = cf[2];
       const bool drifting = cd != T(0);
       const T q = (T)L.q, hq = (T)(0.5 * L.q);
-      const unsigned amask = __ballot_sync(0xffffffffu, active);
       T* dst[NA];
 #pragma unroll
       for (int a = 0; a < NA; ++a) dst[a] = reinterpret_cast<T*>(L.buf[parity ^ 1][a]);
       const int own = (ty + 1) * N + x0;
+      const int exl = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1), exr = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
 
       // own values of a stage, drifted: phi + cd * pi
       auto read_own = [&](const T* st, T (&ph)[NF][VX], T (&pm)[NF][VX]) {
@@ -397,16 +397,10 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
                 yh[v] = fmaT(cd, mh[v], yh[v]);
               }
             }
-            T left = __shfl_up_sync(amask, cur[f][VX - 1], 1);
-            T right = __shfl_down_sync(amask, cur[f][0], 1);
-            if (tx == 0 || lane == 0) {
-              const int e = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1);
-              left = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
-            }
-            if (tx == TX - 1 || lane == 31) {
-              const int e = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
-              right = drifting ? fmaT(cd, pm[e], ph[e]) : ph[e];
-            }
+            // x-neighbours beyond this thread's sites, read from the stage and
+            // drifted like the owner's copy (no shuffle, no divergent edge branch)
+            const T left = drifting ? fmaT(cd, pm[exl], ph[exl]) : ph[exl];
+            const T right = drifting ? fmaT(cd, pm[exr], ph[exr]) : ph[exr];
             T gf = T(0);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {

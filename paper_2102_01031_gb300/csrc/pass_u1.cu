@@ -148,8 +148,6 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const T cd = cf[0], cdA = cf[1], A1 = cf[2], A3 = cf[3], AJ = cf[4], AC = cf[5], gd = cf[6], v2 = cf[7];
       const bool drifting = cd != T(0) || cdA != T(0);
       const T lam = (T)L.lam;
-      const unsigned amask = __ballot_sync(0xffffffffu, active);
-      const bool edge_l = tx == 0 || lane == 0, edge_r = tx == TX - 1 || lane == 31;
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;
       // output buffer: array a of a lattice buffer starts a * V elements after array 0
       T* const dbase = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
@@ -169,17 +167,11 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
         const T f = st[a * ae + row * N + x];
         return drifting ? fmaT(coef, st[(a + 1) * ae + row * N + x], f) : f;
       };
-      // value at x0 - 1 (x0 + VX) of a row whose own values this thread holds
-      auto left = [&](T last, const T* st, int a, int row, T coef) -> T {
-        T r = __shfl_up_sync(amask, last, 1);
-        if (edge_l) r = rds(st, a, row, xl, coef);
-        return r;
-      };
-      auto right = [&](T first, const T* st, int a, int row, T coef) -> T {
-        T r = __shfl_down_sync(amask, first, 1);
-        if (edge_r) r = rds(st, a, row, xr, coef);
-        return r;
-      };
+      // value at x0 - 1 (x0 + VX) of a row, read from the stage and drifted like
+      // the owning thread's own copy (no shuffles: every lane reads its own
+      // neighbour, with no divergent edge branch)
+      auto left = [&](const T* st, int a, int row, T coef) -> T { return rds(st, a, row, xl, coef); };
+      auto right = [&](const T* st, int a, int row, T coef) -> T { return rds(st, a, row, xr, coef); };
 
       // carried from the plane below: phi, the z-link phase, theta_xz and theta_yz sines
       T bF[2][VX], bCz[VX], bSz[VX], bSxz[VX], bSyz[VX];
@@ -197,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
         rdv(st, AY, ty + 1, cdA, aym);
         rdv(st, AZ, ty + 1, cdA, azm);
         rdv(st, AZ, ty + 2, cdA, azm_yp);
-        const T r = right(azm[0], st, AZ, ty + 1, cdA);
+        const T r = right(st, AZ, ty + 1, cdA);
 #pragma unroll
         for (int v = 0; v < VX; ++v) {
           azm_xp[v] = v + 1 < VX ? azm[v + 1] : r;
@@ -244,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             sincos_t(gd * cA[2][v], szv[v], czv[v]);
           }
           rdv(sc, AY, ty, cdA, ay_ym);
-          const T ax_l = left(cA[0][VX - 1], sc, AX, ty + 1, cdA);
+          const T ax_l = left(sc, AX, ty + 1, cdA);
           T s_g = T(0), s_v = T(0), s_pi = T(0);
           T Jx[VX], Jy[VX], Jz[VX];
           // ---- charged scalar: covariant Laplacian, currents, potential, kick ----
@@ -254,10 +246,10 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             rdv(sc, F1, ty, cd, fym[1]);
             rdv(sc, F0, ty + 2, cd, fyp[0]);
             rdv(sc, F1, ty + 2, cd, fyp[1]);
-            const T f0_l = left(cF[0][VX - 1], sc, F0, ty + 1, cd);
-            const T f1_l = left(cF[1][VX - 1], sc, F1, ty + 1, cd);
-            const T f0_r = right(cF[0][0], sc, F0, ty + 1, cd);
-            const T f1_r = right(cF[1][0], sc, F1, ty + 1, cd);
+            const T f0_l = left(sc, F0, ty + 1, cd);
+            const T f1_l = left(sc, F1, ty + 1, cd);
+            const T f0_r = right(sc, F0, ty + 1, cd);
+            const T f1_r = right(sc, F1, ty + 1, cd);
             T sxl, cxl;
             sincos_t(gd * ax_l, sxl, cxl);
             T p0[VX], p1[VX], pn0[VX], pn1[VX];
@@ -328,13 +320,13 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             rdv(sc, AX, ty, cdA, ax_ym);
             rdv(sc, AZ, ty + 2, cdA, az_yp);
             rdv(sc, AZ, ty, cdA, az_ym);
-            const T axzp_l = left(aA[0][VX - 1], sa, AX, ty + 1, cdA);
-            const T ay_l = left(cA[1][VX - 1], sc, AY, ty + 1, cdA);
-            const T az_l = left(cA[2][VX - 1], sc, AZ, ty + 1, cdA);
-            const T axyp_l = left(ax_yp[VX - 1], sc, AX, ty + 2, cdA);
-            const T ay_r = right(cA[1][0], sc, AY, ty + 1, cdA);
-            const T az_r = right(cA[2][0], sc, AZ, ty + 1, cdA);
-            const T ayym_r = right(ay_ym[0], sc, AY, ty, cdA);
+            const T axzp_l = left(sa, AX, ty + 1, cdA);
+            const T ay_l = left(sc, AY, ty + 1, cdA);
+            const T az_l = left(sc, AZ, ty + 1, cdA);
+            const T axyp_l = left(sc, AX, ty + 2, cdA);
+            const T ay_r = right(sc, AY, ty + 1, cdA);
+            const T az_r = right(sc, AZ, ty + 1, cdA);
+            const T ayym_r = right(sc, AY, ty, cdA);
             T pax[VX], pay[VX], paz[VX], pnx[VX], pny[VX], pnz[VX], pxy[VX];
             ldv<T>(pax, sc + PAX * ae + own);
             ldv<T>(pay, sc + PAY * ae + own);
