@@ -369,7 +369,7 @@ def other_workloads(P, torch, stream, peak):
     out["ensemble_64_fp32_vv4"] = {"site_updates_per_s": sites * 100 / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "sites": sites,
                                    "launches_per_step_call": 1}
-    # adjoint: 128^3 FP32, VV4 dt = 0.005, no expansion, 1000 steps, checkpoints every 500
+    # adjoint: 128^3 FP32, VV4 dt = 0.005, no expansion, 4000 steps, checkpoints every 500
     adj = dict(PARAMS, expansion=P.EXP_OFF)
     g = P.Lattice(P.MODEL_LPHI4_CHI, 128, KIR * N_LAT / 128, ALPHA, SEED,
                   P.make_params(precision=P.FP32, stream=stream, **adj))
@@ -377,19 +377,49 @@ def other_workloads(P, torch, stream, peak):
     g.sync()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g.step(1000)
+    g.step(4000)
     g.sync()
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
-    J, dq, _ = g.adjoint(1000, 500)
+    J, dq, _ = g.adjoint(4000, 500)
     torch.cuda.synchronize()
     t_adj = time.perf_counter() - t0
     g.close()
     out["adjoint_128_fp32_vv4"] = {"forward_s": t_fwd, "forward_plus_reverse_s": t_adj,
                                    "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq,
-                                   "steps": 1000, "ckpt_every": 500}
+                                   "steps": 4000, "ckpt_every": 500,
+                                   "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps"}
     return out
+
+
+def profile_case(name):
+    """Small cases for ncu captures: one launch of the kernel named in
+    profiles/ after a short setup (no timing, no JSON line)."""
+    import torch
+
+    import paper_2102_01031_gb300 as P
+    torch.cuda.set_device(0)
+    P.build()
+    stream = P.torch_stream()
+    if name == "scalar256":   # one cooperative launch of the three VV4 passes of a step
+        lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **PARAMS))
+        lat.step(1)
+    elif name == "u1_128":    # single-pass launches of the leapfrog U(1) pass
+        u1 = dict(dt=0.01, integrator=P.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
+                  phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=P.EXP_OFF, fstar_over_mp=0.5)
+        lat = P.Lattice(P.MODEL_U1_HIGGS, 128, 0.2, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
+        for _ in range(4):
+            lat.step(1)
+    elif name == "adj128":    # adjoint sweep of 4 VV4 steps at 128^3
+        lat = P.Lattice(P.MODEL_LPHI4_CHI, 128, 0.2, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **dict(PARAMS, expansion=P.EXP_OFF)))
+        lat.adjoint(4, 2)
+    else:
+        raise SystemExit("unknown profile case %s" % name)
+    torch.cuda.synchronize()
+    return 0
 
 
 def ctypes_sizeof_energies(P):
@@ -407,7 +437,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
+    ap.add_argument("--profile-case", choices=("scalar256", "u1_128", "adj128"),
+                    help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

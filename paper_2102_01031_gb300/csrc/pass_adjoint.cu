@@ -106,8 +106,6 @@ __global__ void __launch_bounds__(THREADS, 1) adj_pass_scalar(const PassArgs P) 
       const double* cfp = P.adj + 4 * pass;
       const T cd = (T)__ldg(cfp), A1 = (T)__ldg(cfp + 2), A3 = (T)__ldg(cfp + 3);
       const T q = (T)L.q;
-      const unsigned amask = __ballot_sync(0xffffffffu, active);
-      const bool edge_l = tx == 0 || lane == 0, edge_r = tx == TX - 1 || lane == 31;
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;
       const int own = (ty + 1) * N + x0;
 
@@ -151,10 +149,9 @@ __global__ void __launch_bounds__(THREADS, 1) adj_pass_scalar(const PassArgs P) 
               T yl[VX], yh[VX];
               ld_v<T, VX>(yl, base + ty * N + x0);
               ld_v<T, VX>(yh, base + (ty + 2) * N + x0);
-              T left = __shfl_up_sync(amask, c[VX - 1], 1);
-              T right = __shfl_down_sync(amask, c[0], 1);
-              if (edge_l) left = base[(ty + 1) * N + xl];
-              if (edge_r) right = base[(ty + 1) * N + xr];
+              // x-neighbours beyond the thread's sites, straight from the stage
+              const T left = base[(ty + 1) * N + xl];
+              const T right = base[(ty + 1) * N + xr];
 #pragma unroll
               for (int v = 0; v < VX; ++v) {
                 const T cv = c[v];
