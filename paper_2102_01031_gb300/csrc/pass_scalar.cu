@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // next pass's coefficients of lattice pend[base + l], all lattices at once.
   auto run_tails = [&](int base, int nb, const PassStep& st) {
     for (int it = warp; it < nb * NUSED; it += CONSUMER_WARPS) {
-      const int l = it / NUSED, q = it - l * NUSED;
+      constexpr int NQU = NUSED > 0 ? NUSED : 1;
+      const int l = it / NQU, q = it - l * NQU;
       const LatConst& L = P.lat[pend[base + l]];
       const double s = warp_slot_sum(P.partials + (size_t)q * P.nslot, L.slot_begin, L.slot_end, lane);
       if (lane == 0) red[l * NQ + q] = s;
@@ -347,36 +348,42 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       const int exl = (ty + 1) * N + (x0 == 0 ? N - 1 : x0 - 1), exr = (ty + 1) * N + (x0 + VX == N ? 0 : x0 + VX);
 
       // own values of a stage, drifted: phi + cd * pi
-      auto read_own = [&](const T* st, T (&ph)[NF][VX], T (&pm)[NF][VX]) {
+      auto read_own = [&](const T* st, T (&ph)[NF][VX]) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           ld_vec<T, VX>(ph[f], st + (size_t)(2 * f) * arr_elems + own);
-          ld_vec<T, VX>(pm[f], st + (size_t)(2 * f + 1) * arr_elems + own);
           if (drifting) {
+            T pm[VX];
+            ld_vec<T, VX>(pm, st + (size_t)(2 * f + 1) * arr_elems + own);
 #pragma unroll
-            for (int v = 0; v < VX; ++v) ph[f][v] = fmaT(cd, pm[f][v], ph[f][v]);
+            for (int v = 0; v < VX; ++v) ph[f][v] = fmaT(cd, pm[v], ph[f][v]);
           }
         }
       };
 
-      T below[NF][VX], cur[NF][VX], above[NF][VX], pic[NF][VX], pia[NF][VX];
+      // drifted fields of three consecutive planes; the roles below / current /
+      // above rotate through b0, b1, b2 (the march is unrolled by three, so the
+      // rotation costs no register moves)
+      T b0[NF][VX], b1[NF][VX], b2[NF][VX];
       // planes 0 and 1 of the segment
       wait_full(s_cur, p_cur);
-      if (active && !flag[0]) read_own(stage_ptr(s_cur), below, pia);
+      if (active && !flag[0]) read_own(stage_ptr(s_cur), b0);
       release(g0, s_cur);
       advance(s_cur, p_cur);
       wait_full(s_cur, p_cur);
-      if (active && !flag[0]) read_own(stage_ptr(s_cur), cur, pic);
+      if (active && !flag[0]) read_own(stage_ptr(s_cur), b1);
       int s_nxt = s_cur;
       uint32_t p_nxt = p_cur;
       advance(s_nxt, p_nxt);
 
-      for (int j = 1; j <= sg.nz; ++j) {  // plane j in stage s_cur, plane j + 1 in s_nxt
+      // plane j of the segment (stage s_cur), its neighbours below and above
+      // (the above plane is read from stage s_nxt into `above`)
+      auto plane = [&](int j, const T (&below)[NF][VX], const T (&cur)[NF][VX], T (&above)[NF][VX]) {
         wait_full(s_nxt, p_nxt);
         if (active && !flag[0]) {
           const T* sa = stage_ptr(s_nxt);
           const T* sc = stage_ptr(s_cur);
-          read_own(sa, above, pia);
+          read_own(sa, above);
           T lap[NF][VX], g2[VX];
 #pragma unroll
           for (int v = 0; v < VX; ++v) g2[v] = T(0);
@@ -422,7 +429,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             }
             if (RED == 2) acc[6 * f + 2].add(gf);
           }
-          T pn[NF][VX];
+          T pn[NF][VX], pic[NF][VX];  // momenta of the current plane, from its stage
+#pragma unroll
+          for (int f = 0; f < NF; ++f) ld_vec<T, VX>(pic[f], sc + (size_t)(2 * f + 1) * arr_elems + own);
           T spost = T(0), vs = T(0), gsum = T(0);
 #pragma unroll
           for (int v = 0; v < VX; ++v) {
@@ -464,19 +473,18 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
               st_vec<T, VX>(dst[2 * f + 1] + gi, pn[f]);
             }
           }
-#pragma unroll
-          for (int f = 0; f < NF; ++f)
-#pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              below[f][v] = cur[f][v];
-              cur[f][v] = above[f][v];
-              pic[f][v] = pia[f][v];
-            }
         }
         release(g0 + j, s_cur);
         s_cur = s_nxt;
         p_cur = p_nxt;
         advance(s_nxt, p_nxt);
+      };
+      for (int j = 1; j <= sg.nz; j += 3) {
+        plane(j, b0, b1, b2);
+        if (j + 1 > sg.nz) break;
+        plane(j + 1, b1, b2, b0);
+        if (j + 2 > sg.nz) break;
+        plane(j + 2, b2, b0, b1);
       }
       release(g0 + sg.nz + 1, s_cur);
       advance(s_cur, p_cur);
