@@ -118,7 +118,7 @@ def lib():
                                         ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int64), dp]
             L.clo_adjoint.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_double, ctypes.c_int, dp, dp, dp]
+                                      ctypes.c_double, ctypes.c_int, dp, dp, dp, dp]
             L.clo_ic_amplitude_grad.argtypes = [c_p, dp, dp]
             L.clo_ic_draws.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.POINTER(Params), ctypes.c_int,
@@ -231,17 +231,21 @@ class Oracle:
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
 
-    def adjoint(self, nsteps, objective=0, field=1, what=0, dk_bin=1.0, bin=1):
+    def adjoint(self, nsteps, objective=0, field=1, what=0, dk_bin=1.0, bin=1, scale=False):
         """Discrete adjoint: (J, dJ/dq, lam) with lam[f][w] = dJ/d(field f, what w) at
-        the current state (arrays [z][y][x]); the state is left unchanged."""
+        the current state (arrays [z][y][x]); with scale=True a fourth entry
+        (dJ/da, dJ/db) at the current state.  The state is left unchanged."""
         nf = 1 if self.nfields() == 1 else 2
         lam = np.zeros(2 * nf * self.V)
+        ab = np.zeros(2)
         J, dq = ctypes.c_double(), ctypes.c_double()
         rc = self.L.clo_adjoint(self.h, nsteps, objective, field, what, dk_bin, bin, ctypes.byref(J),
-                                ctypes.byref(dq), _dp(lam))
+                                ctypes.byref(dq), _dp(lam), _dp(ab))
         if rc != 0:
             raise ValueError("clo_adjoint failed (%d)" % rc)
         lam = lam.reshape(nf, 2, self.N, self.N, self.N)
+        if scale:
+            return J.value, dq.value, lam, (float(ab[0]), float(ab[1]))
         return J.value, dq.value, lam
 
     def ic_amplitude_grad(self, lam):

@@ -919,25 +919,39 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
 
 // ===========================================================================
 // Discrete adjoint of the field evolution (gradient of a final observable),
-// written from the forward map above, for scalar models on a fixed
-// background (expansion off, or the fixed power law): there the scale factor
-// is a known function of time and each elementary move is linear or
-// site-local in the fields:
-//   kick  (w, a):  pi_f += w K_f(phi; a, q),  K_f = a^{1+alpha} Lap phi_f/dx^2 - a^{3+alpha} dV/dphi_f
-//   drift (c):     phi_f += c pi_f
-// The adjoint (lam_phi, lam_pi) = (dJ/dphi, dJ/dpi) runs the moves backwards:
-//   kick:  lam_phi_f += w [a^{1+alpha} Lap lam_pi_f/dx^2 - a^{3+alpha} sum_g V_{,fg}(phi) lam_pi_g]
-//          dJ/dq     += w (-a^{3+alpha}) sum_n sum_f lam_pi_f d(dV/dphi_f)/dq
-//   drift: lam_pi_f  += c lam_phi_f
-// (Lap is symmetric, so it is its own transpose.)  The forward run records
-// the field at every kick; nothing is recomputed.
+// written from the forward map above for the scalar models.  The VV2 step is
+// a sequence of elementary moves (vv2: field kick, scale-factor kick, drift,
+// scale-factor kick, field kick); the adjoint
+//   (lam_phi, lam_pi, lam_a, lam_b) = dJ/d(phi, pi, a, b)
+// runs them backwards, each move applying its transposed Jacobian:
+//   field kick (w at a, phi):  pi_f += w K_f,  K_f = a^{1+alpha} Lap phi_f/dx^2 - a^{3+alpha} dV/dphi_f
+//      lam_phi_f += w [a^{1+alpha} Lap lam_pi_f/dx^2 - a^{3+alpha} sum_g V_{,fg} lam_pi_g]
+//      lam_a     += w sum_n sum_f lam_pi_f dK_f/da
+//      dJ/dq     += w sum_n sum_f lam_pi_f (-a^{3+alpha}) d(dV/dphi_f)/dq
+//   scale-factor kick (w at a, phi, pi):  b += w K_a(a, phi, pi)
+//      lam_a += w lam_b dK_a/da,  lam_phi += w lam_b dK_a/dphi,
+//      lam_pi += w lam_b dK_a/dpi, dJ/dq += w lam_b dK_a/dq
+//   drift (w from a, b):  a1 = a + w b,  phi_f += c pi_f,  c = w ((a + a1)/2)^{alpha-3}
+//      lam_pi_f += c lam_phi_f
+//      S = sum_n sum_f lam_phi_f pi_f,  c_abar = w (alpha-3) abar^{alpha-4}
+//      lam_a <- lam_a1 + S c_abar,   lam_b <- lam_b + w lam_a1 + (w/2) S c_abar
+// (Lap is symmetric, so it is its own transpose.)  With expansion off or on
+// the fixed power law the scale factor is a known function of time: the
+// scale-factor kicks are absent, lam_a and lam_b are not needed, and the
+// drift coefficient c is a number.  The forward run records what each move
+// read; nothing is recomputed.
 // ===========================================================================
 namespace {
 
+// One recorded move of the VV2 step.
+enum { MV_DRIFT = 0, MV_KICK = 1, MV_SCALE = 2 };
 struct Move {
-  int kick;                  // 1 kick, 0 drift
-  double w, a;               // kick weight and scale factor / drift coefficient (w)
-  std::vector<double> phi[2];  // fields at the kick
+  int kind;
+  double w;                    // move weight (the step fraction)
+  double a, b;                 // a at the move (drift: before it), b at a drift
+  double cd;                   // drift: coefficient of pi
+  std::vector<double> phi[2];  // kicks: fields at the move
+  std::vector<double> pi[2];   // scale-factor kicks and drifts: momenta at the move
 };
 
 // Hessian of the potential (eq. PotNat) at one site, and d(dV/dphi_f)/dq.
@@ -956,6 +970,11 @@ void pot_hessian(const clo_ctx* c, const double* f, double H[2][2], double* dq) 
   }
 }
 
+// dV/dq at one site (eq. PotNat): phi^2 chi^2/2 for lphi4 + chi, 0 for lphi4.
+double pot_dq(const clo_ctx* c, const double* f) {
+  return c->model == CLO_MODEL_LPHI4_CHI ? 0.5 * f[0] * f[0] * f[1] * f[1] : 0.0;
+}
+
 double lap_at(const clo_ctx* c, const std::vector<double>& u, long n) {
   double s = 0.0;
   for (int i = 0; i < 3; ++i) s += u[c->shift(n, i, +1)] + u[c->shift(n, i, -1)] - 2.0 * u[n];
@@ -964,38 +983,63 @@ double lap_at(const clo_ctx* c, const std::vector<double>& u, long n) {
 
 // One VV2 step of size h (the moves of vv2), recorded.
 void vv2_recorded(clo_ctx* c, double h, std::vector<Move>& moves) {
-  for (int half = 0; half < 2; ++half) {
-    if (half == 1) {
-      Move d;
-      d.kick = 0;
-      double a1 = c->p.expansion == CLO_EXP_FIXED ? a_fixed(c, c->eta + h) : c->a;
-      d.w = h * std::pow(0.5 * (c->a + a1), c->alpha - 3.0);
-      d.a = 0.0;
-      moves.push_back(std::move(d));
-      drift(c, h);
-    }
+  const bool self = c->p.expansion == CLO_EXP_SELF;
+  auto field_kick = [&](double w) {
     Move k;
-    k.kick = 1;
-    k.w = 0.5 * h;
+    k.kind = MV_KICK;
+    k.w = w;
     k.a = c->a;
     for (int f = 0; f < c->nf; ++f) k.phi[f] = c->phi[f];
     moves.push_back(std::move(k));
-    kick_fields(c, 0.5 * h);
+    kick_fields(c, w);
+  };
+  auto scale_kick = [&](double w) {
+    if (!self) return;
+    Move k;
+    k.kind = MV_SCALE;
+    k.w = w;
+    k.a = c->a;
+    for (int f = 0; f < c->nf; ++f) {
+      k.phi[f] = c->phi[f];
+      k.pi[f] = c->pi[f];
+    }
+    moves.push_back(std::move(k));
+    kick_scale(c, w);
+  };
+  field_kick(0.5 * h);
+  scale_kick(0.5 * h);
+  {
+    Move d;
+    d.kind = MV_DRIFT;
+    d.w = h;
+    d.a = c->a;
+    d.b = c->b;
+    double a1 = c->a;
+    if (self) a1 = c->a + h * c->b;
+    else if (c->p.expansion == CLO_EXP_FIXED) a1 = a_fixed(c, c->eta + h);
+    d.cd = h * std::pow(0.5 * (c->a + a1), c->alpha - 3.0);
+    if (self)
+      for (int f = 0; f < c->nf; ++f) d.pi[f] = c->pi[f];
+    moves.push_back(std::move(d));
+    drift(c, h);
   }
+  scale_kick(0.5 * h);
+  field_kick(0.5 * h);
 }
 
-// Objective J at the current state and its seeds dJ/dphi_f, dJ/dpi_f and
-// explicit dJ/dq.  objective 0: chi energy fraction (E_K^chi + E_G^chi)/rho
+// Objective J at the current state and its seeds dJ/dphi_f, dJ/dpi_f, dJ/da
+// and explicit dJ/dq.  objective 0: chi energy fraction (E_K^chi + E_G^chi)/rho
 // (lphi4 + chi).  objective 1: delta_b of the binned spectrum of (field, what)
 // with bin width dk (as clo_spectrum).
 bool objective_seed(clo_ctx* c, int objective, int field, int what, double dk, int bin, double* J,
-                    std::vector<double>* lphi, std::vector<double>* lpi, double* dJdq) {
+                    std::vector<double>* lphi, std::vector<double>* lpi, double* dJdq, double* dJda) {
   const double V = (double)c->V;
   for (int f = 0; f < c->nf; ++f) {
     lphi[f].assign(c->V, 0.0);
     lpi[f].assign(c->V, 0.0);
   }
   *dJdq = 0.0;
+  *dJda = 0.0;
   if (objective == 0) {
     if (c->model != CLO_MODEL_LPHI4_CHI) return false;
     Avg r;
@@ -1017,6 +1061,10 @@ bool objective_seed(clo_ctx* c, int objective, int field, int what, double dk, i
     double s = 0.0;
     for (long n = 0; n < c->V; ++n) s += 0.5 * c->phi[0][n] * c->phi[0][n] * c->phi[1][n] * c->phi[1][n];
     *dJdq = -*J / rho * s / V;
+    // E_K ~ a^-6 and E_G ~ a^-2 at fixed (phi, pi); E_V does not depend on a
+    const double dnum = -(6.0 * r.EK[1] + 2.0 * r.EG[1]) / a;
+    const double drho = -(6.0 * sum4(r.EK) + 2.0 * sum4(r.EG)) / a;
+    *dJda = (dnum - *J * drho) / rho;
     return true;
   }
   if (objective == 1) {
@@ -1058,9 +1106,10 @@ bool objective_seed(clo_ctx* c, int objective, int field, int what, double dk, i
 extern "C" {
 
 int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, double dk, int bin,
-                double* J, double* dJdq, double* lam) {
+                double* J, double* dJdq, double* lam, double* dJdab) {
   if (!c || nsteps < 0 || !J || !dJdq || !lam) return -1;
-  if (c->gauge() || c->p.expansion == CLO_EXP_SELF) return -2;  // not built: see the header
+  if (c->gauge()) return -2;  // not built: see the header
+  const bool self = c->p.expansion == CLO_EXP_SELF;
   // state at the start, restored at the end
   std::vector<double> phi0[2], pi0[2];
   for (int f = 0; f < c->nf; ++f) { phi0[f] = c->phi[f]; pi0[f] = c->pi[f]; }
@@ -1071,34 +1120,100 @@ int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, doub
   for (int s = 0; s < nsteps; ++s)
     for (double h : d) vv2_recorded(c, h, moves);
   std::vector<double> lphi[2], lpi[2];
-  const bool ok = objective_seed(c, objective, field, what, dk, bin, J, lphi, lpi, dJdq);
+  double la = 0.0, lb = 0.0;
+  const bool ok = objective_seed(c, objective, field, what, dk, bin, J, lphi, lpi, dJdq, &la);
+  if (!self) la = 0.0;
   if (ok) {
-    const double idx2 = 1.0 / (c->dx * c->dx);
+    const double V = (double)c->V, al = c->alpha, idx2 = 1.0 / (c->dx * c->dx);
+    const double C = c->p.fstar_over_mp * c->p.fstar_over_mp / 3.0;
     for (size_t m = moves.size(); m-- > 0;) {
       const Move& mv = moves[m];
-      if (!mv.kick) {
+      if (mv.kind == MV_DRIFT) {
+        double S = 0.0;
         for (int f = 0; f < c->nf; ++f)
-          for (long n = 0; n < c->V; ++n) lpi[f][n] += mv.w * lphi[f][n];
+          for (long n = 0; n < c->V; ++n) {
+            if (self) S += lphi[f][n] * mv.pi[f][n];
+            lpi[f][n] += mv.cd * lphi[f][n];
+          }
+        if (self) {
+          const double abar = mv.a + 0.5 * mv.w * mv.b;
+          const double cab = mv.w * (al - 3.0) * std::pow(abar, al - 4.0);
+          const double la1 = la;
+          la = la1 + S * cab;
+          lb = lb + mv.w * la1 + 0.5 * mv.w * S * cab;
+        }
         continue;
       }
-      const double a1 = std::pow(mv.a, 1.0 + c->alpha), a3 = std::pow(mv.a, 3.0 + c->alpha);
-      double dq = 0.0;
+      if (mv.kind == MV_KICK) {
+        const double a = mv.a;
+        const double a1 = std::pow(a, 1.0 + al), a3 = std::pow(a, 3.0 + al);
+        const double da1 = (1.0 + al) * std::pow(a, al), da3 = (3.0 + al) * std::pow(a, 2.0 + al);
+        double dq = 0.0, sa = 0.0;
+        for (long n = 0; n < c->V; ++n) {
+          double f[2] = {0.0, 0.0}, H[2][2], g[2], dv[2] = {0.0, 0.0};
+          for (int k = 0; k < c->nf; ++k) f[k] = mv.phi[k][n];
+          pot_hessian(c, f, H, g);
+          pot_deriv(c, f, dv);
+          for (int k = 0; k < c->nf; ++k) {
+            double hl = 0.0;
+            for (int j = 0; j < c->nf; ++j) hl += H[k][j] * lpi[j][n];
+            lphi[k][n] += mv.w * (a1 * lap_at(c, lpi[k], n) * idx2 - a3 * hl);
+            dq += lpi[k][n] * g[k];
+            if (self) sa += lpi[k][n] * (da1 * lap_at(c, mv.phi[k], n) * idx2 - da3 * dv[k]);
+          }
+        }
+        *dJdq += mv.w * (-a3) * dq;
+        if (self) la += mv.w * sa;
+        continue;
+      }
+      // scale-factor kick: K_a = C a^{2 alpha+1} [(alpha-2) E_K + alpha E_G + (alpha+1) E_V]
+      // with E_K = sum pi^2/(2 a^6 V), E_G = sum (grad^+ phi)^2/(2 a^2 dx^2 V), E_V = sum V/V
+      const double a = mv.a, wl = mv.w * lb;
+      double EK = 0.0, EG = 0.0, EV = 0.0, Vq = 0.0;
       for (long n = 0; n < c->V; ++n) {
-        double f[2] = {0.0, 0.0}, H[2][2], g[2];
-        for (int k = 0; k < c->nf; ++k) f[k] = mv.phi[k][n];
-        pot_hessian(c, f, H, g);
+        double f[2] = {0.0, 0.0}, t[4] = {0.0, 0.0, 0.0, 0.0};
         for (int k = 0; k < c->nf; ++k) {
-          double hl = 0.0;
-          for (int j = 0; j < c->nf; ++j) hl += H[k][j] * lpi[j][n];
-          lphi[k][n] += mv.w * (a1 * lap_at(c, lpi[k], n) * idx2 - a3 * hl);
-          dq += lpi[k][n] * g[k];
+          f[k] = mv.phi[k][n];
+          EK += mv.pi[k][n] * mv.pi[k][n];
+          for (int i = 0; i < 3; ++i) {
+            const double gr = mv.phi[k][c->shift(n, i, +1)] - mv.phi[k][n];
+            EG += gr * gr;
+          }
+        }
+        pot_terms(c, f, t);
+        for (int k = 0; k < n_pot_terms(c->model); ++k) EV += t[k];
+        Vq += pot_dq(c, f);
+      }
+      const double a2 = a * a, a6 = a2 * a2 * a2;
+      EK /= 2.0 * a6 * V;
+      EG /= 2.0 * a2 * c->dx * c->dx * V;
+      EV /= V;
+      const double p1 = C * std::pow(a, 2.0 * al + 1.0);
+      // d/da at fixed (phi, pi): a^{2 alpha+1} E_K ~ a^{2 alpha-5}, a^{2 alpha+1} E_G ~ a^{2 alpha-1}
+      const double dKa = C * std::pow(a, 2.0 * al) *
+                         ((2.0 * al - 5.0) * (al - 2.0) * EK + (2.0 * al - 1.0) * al * EG +
+                          (2.0 * al + 1.0) * (al + 1.0) * EV);
+      la += wl * dKa;
+      *dJdq += wl * p1 * (al + 1.0) * Vq / V;
+      for (long n = 0; n < c->V; ++n) {
+        double f[2] = {0.0, 0.0}, dv[2] = {0.0, 0.0};
+        for (int k = 0; k < c->nf; ++k) f[k] = mv.phi[k][n];
+        pot_deriv(c, f, dv);
+        for (int k = 0; k < c->nf; ++k) {
+          // dE_G/dphi(n) = -Lap phi(n)/(a^2 dx^2 V), dE_V/dphi = V_{,phi}/V, dE_K/dpi = pi/(a^6 V)
+          const double dEG = -lap_at(c, mv.phi[k], n) * idx2 / (a2 * V);
+          lphi[k][n] += wl * p1 * (al * dEG + (al + 1.0) * dv[k] / V);
+          lpi[k][n] += wl * p1 * (al - 2.0) * mv.pi[k][n] / (a6 * V);
         }
       }
-      *dJdq += mv.w * (-a3) * dq;
     }
     for (int f = 0; f < c->nf; ++f) {
       std::memcpy(lam + (size_t)(2 * f) * c->V, lphi[f].data(), sizeof(double) * c->V);
       std::memcpy(lam + (size_t)(2 * f + 1) * c->V, lpi[f].data(), sizeof(double) * c->V);
+    }
+    if (dJdab) {
+      dJdab[0] = la;
+      dJdab[1] = lb;
     }
   }
   for (int f = 0; f < c->nf; ++f) { c->phi[f] = phi0[f]; c->pi[f] = pi0[f]; }
@@ -1115,8 +1230,11 @@ int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, doub
 //   dJ/d|z_j| = (s/V) Re[ e^{i th_j}/sqrt2 L_phi(n)
 //                 + a^{3-alpha} (+-a^{alpha-1} i omega - H) e^{i th_j}/sqrt2 L_pi(n) ],
 // L(n) = sum_x lam(x) e^{+i k.x}.  out[(2f + j) V + n] at canonical n, 0 elsewhere.
+// With self-consistent expansion the initial b must not move with the
+// amplitudes (b0_mode 0: a' from the homogeneous values); b0_mode 1 is refused.
 int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out) {
   if (!c || !lam || !out || c->gauge()) return -1;
+  if (c->p.expansion == CLO_EXP_SELF && c->p.b0_mode == 1) return -2;
   const double V = (double)c->V, isq2 = 1.0 / std::sqrt(2.0);
   const double a = c->a0, a3ma = std::pow(a, 3.0 - c->alpha), aam1 = std::pow(a, c->alpha - 1.0);
   std::memset(out, 0, sizeof(double) * 2 * c->nf * c->V);

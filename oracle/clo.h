@@ -84,15 +84,18 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out);
 
-/* Discrete adjoint (scalar models, expansion off or fixed background; -2
- * otherwise): from the current state, run nsteps, evaluate the objective
- * (0: chi energy fraction; 1: spectrum bin `bin` of (field, what) with width
- * dk), and return J, dJ/dq at a fixed initial state, and lam[(2f + w) V + n] =
- * dJ/d(field f, what w)(n) at the initial state.  The state is restored. */
+/* Discrete adjoint (scalar models; -2 for U(1)): from the current state, run
+ * nsteps, evaluate the objective (0: chi energy fraction; 1: spectrum bin
+ * `bin` of (field, what) with width dk), and return J, dJ/dq at a fixed
+ * initial state (phi, pi, a, b), lam[(2f + w) V + n] = dJ/d(field f, what w)(n)
+ * at the initial state, and, if dJdab is not NULL, dJdab[0..1] = dJ/da, dJ/db
+ * at the initial state (zero unless the expansion is self-consistent).  The
+ * state is restored. */
 int clo_adjoint(clo_ctx* c, int nsteps, int objective, int field, int what, double dk, int bin,
-                double* J, double* dJdq, double* lam);
+                double* J, double* dJdq, double* lam, double* dJdab);
 /* Chain lam (as above, at the initial conditions) to dJ/d|z_j| of each canonical
- * mode: out[(2f + j) V + n], j = 0, 1. */
+ * mode: out[(2f + j) V + n], j = 0, 1.  -2 with self-consistent expansion and
+ * b0_mode 1 (the initial b then depends on the amplitudes). */
 int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out);
 int clo_ic_draws(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p, int n,
                  const int64_t* idx, double* out);

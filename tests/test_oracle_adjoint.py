@@ -176,8 +176,105 @@ def test_all_amplitudes_scaled_together(oracle_mod):
     assert abs(pred - fd) < 1e-6 * abs(fd), (pred, fd)
 
 
+SELF = dict(BASE, expansion=O.EXP_SELF, fstar_over_mp=2.0, dt=0.02)
+
+
+def run_J_self(alpha, kw, state, scal, nsteps, objective=0, spec=None, N=8, kIR=1.0, seed=3):
+    """J after nsteps from (state, (eta, a, b)) with self-consistent expansion."""
+    o = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, alpha, seed, O.make_params(**kw))
+    for f in range(len(state)):
+        for w in (0, 1):
+            o.set(f, w, state[f][w])
+    o.set_scalars(*scal)
+    o.step(nsteps)
+    if objective == 0:
+        return chi_fraction(o)
+    field, what, dk, b = spec
+    return o.spectrum(field, what, dk)[1][b]
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+@pytest.mark.parametrize("objective,spec", [(0, None), (1, (1, 1, 1.0, 2))])
+def test_self_consistent_expansion_gradients(oracle_mod, alpha, objective, spec):
+    """With a' = b evolving by the Friedmann kicks, dJ/dq, dJ/d(phi, pi) and
+    dJ/d(a, b) at the start against central differences of forward runs."""
+    N, kIR, seed, n = 8, 1.0, 3, 15
+    o = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, alpha, seed, O.make_params(**SELF))
+    s0 = state_of(o, 2)
+    sc0 = o.scalars()
+    kw = dict(objective=1, field=spec[0], what=spec[1], dk_bin=spec[2], bin=spec[3]) if objective else {}
+    J, dq, lam, (da, db) = o.adjoint(n, scale=True, **kw)
+    assert o.scalars() == sc0
+    assert abs(J - run_J_self(alpha, SELF, s0, sc0, n, objective, spec)) < 1e-14 * abs(J)
+    # the expansion matters here: a grows by several per cent
+    o.step(n)
+    assert o.scalars()[1] > 1.05
+    eps = 1e-3
+    fd = (run_J_self(alpha, dict(SELF, q=SELF["q"] + eps), s0, sc0, n, objective, spec) -
+          run_J_self(alpha, dict(SELF, q=SELF["q"] - eps), s0, sc0, n, objective, spec)) / (2 * eps)
+    assert abs(dq - fd) < 1e-6 * abs(fd) + 1e-14, (dq, fd)
+    e = 1e-6
+    eta0, a0, b0 = sc0
+    fd_a = (run_J_self(alpha, SELF, s0, (eta0, a0 + e, b0), n, objective, spec) -
+            run_J_self(alpha, SELF, s0, (eta0, a0 - e, b0), n, objective, spec)) / (2 * e)
+    fd_b = (run_J_self(alpha, SELF, s0, (eta0, a0, b0 + e), n, objective, spec) -
+            run_J_self(alpha, SELF, s0, (eta0, a0, b0 - e), n, objective, spec)) / (2 * e)
+    assert abs(da - fd_a) < 1e-6 * abs(fd_a) + 1e-13, (da, fd_a)
+    assert abs(db - fd_b) < 1e-6 * abs(fd_b) + 1e-13, (db, fd_b)
+    rng = np.random.default_rng(11)
+    v = [[rng.standard_normal((N, N, N)) for w in (0, 1)] for f in range(2)]
+    sp = [[s0[f][w] + e * v[f][w] for w in (0, 1)] for f in range(2)]
+    sm = [[s0[f][w] - e * v[f][w] for w in (0, 1)] for f in range(2)]
+    fd = (run_J_self(alpha, SELF, sp, sc0, n, objective, spec) -
+          run_J_self(alpha, SELF, sm, sc0, n, objective, spec)) / (2 * e)
+    ad = sum(float(np.sum(lam[f, w] * v[f][w])) for f in range(2) for w in (0, 1))
+    assert abs(ad - fd) < 1e-6 * abs(fd) + 1e-13, (ad, fd)
+
+
+def test_self_consistent_seed_in_a(oracle_mod):
+    """Zero steps: dJ/da is the explicit a-dependence of the energy fraction, dJ/db = 0."""
+    o = O.Oracle(O.MODEL_LPHI4_CHI, 8, 1.0, 1.0, 5, O.make_params(**SELF))
+    s0 = state_of(o, 2)
+    eta0, a0, b0 = o.scalars()
+    J, dq, lam, (da, db) = o.adjoint(0, scale=True)
+    e = 1e-6
+    fd = (run_J_self(1.0, SELF, s0, (eta0, a0 + e, b0), 0, seed=5) -
+          run_J_self(1.0, SELF, s0, (eta0, a0 - e, b0), 0, seed=5)) / (2 * e)
+    assert abs(da - fd) < 1e-8 * abs(fd)
+    assert db == 0.0
+
+
+def test_self_consistent_amplitude_gradient(oracle_mod):
+    """Self-consistent expansion with a' from the homogeneous values (b0_mode 0):
+    the ICs are drawn with H = b0/a0 != 0 and b0 does not move with the
+    amplitudes, so scaling all of them by (1 + e) is differentiated exactly by
+    the chain of lam."""
+    N, kIR, seed, n = 8, 1.0, 8, 10
+    p = O.make_params(**SELF)
+    o = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed, p)
+    assert o.scalars()[2] > 0.5
+    J, dq, lam = o.adjoint(n)
+    g = o.ic_amplitude_grad(lam).reshape(2, 2, -1)
+    dr = O.ic_draws(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed, p, np.arange(N ** 3))
+    pred = sum(float(np.sum(dr[:, f, 2 * j] * g[f, j])) for f in range(2) for j in range(2))
+    eps = 1e-4
+
+    def J_at(e):
+        q = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed,
+                     O.make_params(**dict(SELF, fluct_amp2=SELF["fluct_amp2"] * (1 + e) ** 2)))
+        q.step(n)
+        return chi_fraction(q)
+
+    fd = (J_at(eps) - J_at(-eps)) / (2 * eps)
+    assert abs(pred - fd) < 1e-6 * abs(fd), (pred, fd)
+    # a' from the lattice averages would move b0 with the amplitudes: refused
+    o1 = O.Oracle(O.MODEL_LPHI4_CHI, N, kIR, 1.0, seed, O.make_params(**dict(SELF, b0_mode=1)))
+    with pytest.raises(ValueError):
+        o1.ic_amplitude_grad(lam)
+
+
 def test_unsupported_cases(oracle_mod):
-    o = O.Oracle(O.MODEL_LPHI4_CHI, 8, 1.0, 1.0, 1, O.make_params(**dict(BASE, expansion=O.EXP_SELF)))
+    o = O.Oracle(O.MODEL_U1_HIGGS, 8, 1.0, 1.0, 1, O.make_params(**dict(BASE, gQ=0.5)))
     with pytest.raises(ValueError):
         o.adjoint(2)
     o1 = O.Oracle(O.MODEL_LPHI4, 8, 1.0, 1.0, 1, O.make_params(**dict(BASE, phi0=[1.0])))
