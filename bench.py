@@ -369,27 +369,29 @@ def other_workloads(P, torch, stream, peak):
     out["ensemble_64_fp32_vv4"] = {"site_updates_per_s": sites * 100 / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "sites": sites,
                                    "launches_per_step_call": 1}
-    # adjoint: 128^3 FP32, VV4 dt = 0.005, no expansion, 4000 steps, checkpoints every 500
-    adj = dict(PARAMS, expansion=P.EXP_OFF)
-    g = P.Lattice(P.MODEL_LPHI4_CHI, 128, KIR * N_LAT / 128, ALPHA, SEED,
-                  P.make_params(precision=P.FP32, stream=stream, **adj))
-    g.step(5)
-    g.sync()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g.step(4000)
-    g.sync()
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    J, dq, _ = g.adjoint(4000, 500)
-    torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t0
-    g.close()
-    out["adjoint_128_fp32_vv4"] = {"forward_s": t_fwd, "forward_plus_reverse_s": t_adj,
-                                   "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq,
-                                   "steps": 4000, "ckpt_every": 500,
-                                   "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps"}
+    # adjoint: 128^3 FP32, VV4 dt = 0.005, 4000 steps, checkpoints every 500, with
+    # self-consistent expansion (the model's runs) and without
+    for tag, adj in (("self", dict(PARAMS, expansion=P.EXP_SELF)), ("noexp", dict(PARAMS, expansion=P.EXP_OFF))):
+        g = P.Lattice(P.MODEL_LPHI4_CHI, 128, KIR * N_LAT / 128, ALPHA, SEED,
+                      P.make_params(precision=P.FP32, stream=stream, **adj))
+        g.step(5)
+        g.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(4000)
+        g.sync()
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        J, dq, _, ab = g.adjoint(4000, 500, scale=True)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        g.close()
+        out["adjoint_128_fp32_vv4_" + tag] = {
+            "forward_s": t_fwd, "forward_plus_reverse_s": t_adj,
+            "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq, "dJ_da": ab[0], "dJ_db": ab[1],
+            "steps": 4000, "ckpt_every": 500,
+            "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps"}
     return out
 
 
@@ -412,9 +414,10 @@ def profile_case(name):
         lat = P.Lattice(P.MODEL_U1_HIGGS, 128, 0.2, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
         for _ in range(4):
             lat.step(1)
-    elif name == "adj128":    # adjoint sweep of 4 VV4 steps at 128^3
+    elif name in ("adj128", "adj128self"):    # adjoint sweep of 4 VV4 steps at 128^3
+        exp = P.EXP_OFF if name == "adj128" else P.EXP_SELF
         lat = P.Lattice(P.MODEL_LPHI4_CHI, 128, 0.2, ALPHA, SEED,
-                        P.make_params(precision=P.FP32, stream=stream, **dict(PARAMS, expansion=P.EXP_OFF)))
+                        P.make_params(precision=P.FP32, stream=stream, **dict(PARAMS, expansion=exp)))
         lat.adjoint(4, 2)
     else:
         raise SystemExit("unknown profile case %s" % name)
@@ -437,7 +440,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "u1_128", "adj128"),
+    ap.add_argument("--profile-case", choices=("scalar256", "u1_128", "adj128", "adj128self"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -215,31 +215,38 @@ cl_status cl_ensemble_spectrum(cl_ctx* ctx, const int* lats, int nl, int field, 
                                int* nbins);
 
 /* ---------------------------------------------------------------------------
- * Adjoint (gradient of a final observable).  For a single lattice of a scalar
- * model on a fixed background (expansion CL_EXP_OFF or CL_EXP_FIXED, where the
- * scale factor does not depend on the fields; CL_EUNSUPPORTED otherwise),
+ * Adjoint (gradient of a final observable), for a single lattice of a scalar
+ * model (CL_EUNSUPPORTED for U(1) and for ensembles), with any expansion mode.
  * cl_adjoint starts from the current (synchronised) state, runs nsteps steps
- * saving the state every ckpt_every steps in device memory, evaluates the
+ * saving the fields every ckpt_every steps in device memory, evaluates the
  * objective at the synchronised end, then runs the passes backwards: each
  * reversed pass recovers the state before it (the time-reversible integrator
- * run backwards) and applies the transposed Jacobian of the pass to the
- * adjoint, and the saved states replace the recovered ones at the checkpoints
- * (where FP32 rounding breaks exact reversal).  Objectives:
+ * run backwards) and applies the transposed Jacobian of the pass (Sec. 3.5.2
+ * Hamiltonian form: drift, field kick and, with CL_EXP_SELF, the Friedmann
+ * kicks of b = a' and the drift of a) to the adjoint, and the saved fields
+ * replace the recovered ones at the checkpoints (where FP32 rounding breaks
+ * exact reversal).  Objectives:
  *   CL_OBJ_CHI_FRACTION: J = (E_K^chi + E_G^chi)/rho (CL_MODEL_LPHI4_CHI);
  *   CL_OBJ_SPECTRUM_BIN: J = delta_b of cl_spectrum(field, what, dk_bin), b = bin.
- * Returns J, dJ/dq at a fixed initial state (the coupling's effect on the
- * evolution and on the final potential energy), and, if dJ_dstate is not
- * NULL, dJ/d(initial state) in 2 nf arrays of N^3 doubles (field f: array 2f
- * = d/dphi_f, 2f + 1 = d/dpi_f).  The state is left at the starting point.
- * Allocates checkpoint storage for the duration of the call. */
+ * Returns J; dJ/dq at a fixed initial state (fields, momenta, a and b); if
+ * dJ_dstate is not NULL, dJ/d(initial state) in 2 nf arrays of N^3 doubles
+ * (field f: array 2f = d/dphi_f, 2f + 1 = d/dpi_f); and if dJ_dscale is not
+ * NULL, dJ_dscale[0..1] = dJ/da, dJ/db at the start (both 0 unless the
+ * expansion is CL_EXP_SELF, where a and b are evolved variables; a user whose
+ * b(t0) follows from the state or from q adds dJ/db times that dependence).
+ * The state, a, b and eta are left at the starting point.  Allocates
+ * checkpoint storage for the duration of the call. */
 enum { CL_OBJ_CHI_FRACTION = 0, CL_OBJ_SPECTRUM_BIN = 1 };
 cl_status cl_adjoint(cl_ctx* ctx, int nsteps, int ckpt_every, int objective, int field, int what,
-                     double dk_bin, int bin, double* J, double* dJ_dq, double* dJ_dstate);
+                     double dk_bin, int bin, double* J, double* dJ_dq, double* dJ_dstate,
+                     double* dJ_dscale);
 
 /* Chain dJ/d(initial state) (as returned by cl_adjoint started at the
  * initial conditions) through the IC map (Sec. 3.5.1) to the drawn mode
  * amplitudes: out[(2f + j) N^3 + n] = dJ/d|z_{j+1}| of field f at Fourier site
- * n (x fastest) for the drawn member of each (n, -n) pair; 0 elsewhere. */
+ * n (x fastest) for the drawn member of each (n, -n) pair; 0 elsewhere.
+ * CL_EUNSUPPORTED with CL_EXP_SELF and b0_mode 1 (b(t0) then depends on the
+ * amplitudes through the lattice averages). */
 cl_status cl_ic_amplitude_grad(cl_ctx* ctx, const double* dJ_dstate, double* out);
 
 /* ---------------------------------------------------------------------------

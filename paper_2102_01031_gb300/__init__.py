@@ -147,7 +147,7 @@ def lib():
                                   ctypes.POINTER(ctypes.c_int)]
     L.cl_ensemble_spectrum.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ip, ip, ctypes.c_double, dp, dp,
                                        i64p, ip, ctypes.POINTER(ctypes.c_int)]
-    L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp]
+    L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
     _lib = L
     return L
@@ -306,16 +306,21 @@ class Lattice:
         return ms.value, n.value
 
     def adjoint(self, nsteps, ckpt_every=500, objective=OBJ_CHI_FRACTION, field=1, what=0, dk_bin=1.0,
-                bin=1):
+                bin=1, scale=False):
         """cl_adjoint: (J, dJ/dq, lam), lam[f][w] = dJ/d(field f, what w) at the current
-        state ([z][y][x] arrays); the state is left unchanged."""
+        state ([z][y][x] arrays); with scale=True a fourth entry (dJ/da, dJ/db).
+        The state is left unchanged."""
         nf = self.nfields()
         lam = np.zeros(2 * nf * self.V)
+        ab = np.zeros(2)
         J, dq = ctypes.c_double(), ctypes.c_double()
         rc = self.L.cl_adjoint(self.h, nsteps, ckpt_every, objective, field, what, dk_bin, bin,
-                               ctypes.byref(J), ctypes.byref(dq), _dp(lam))
+                               ctypes.byref(J), ctypes.byref(dq), _dp(lam), _dp(ab))
         _check(self.L, self.h, rc, "cl_adjoint")
-        return J.value, dq.value, lam.reshape(nf, 2, self.N, self.N, self.N)
+        lam = lam.reshape(nf, 2, self.N, self.N, self.N)
+        if scale:
+            return J.value, dq.value, lam, (float(ab[0]), float(ab[1]))
+        return J.value, dq.value, lam
 
     def ic_amplitude_grad(self, lam):
         """cl_ic_amplitude_grad: dJ/d|z_j| per field and draw, [f][j][z][y][x]."""

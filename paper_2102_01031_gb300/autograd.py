@@ -1,10 +1,13 @@
 """torch.autograd binding of the adjoint sweep.
 
-``evolved_objective(q, state, spec)`` evolves the lattice state ``state``
-(tensor [nf, 2, N, N, N]: field f, 0 = field / 1 = momentum, [z][y][x]) with
-coupling ``q`` through the CUDA library and returns the final objective J as
-a 0-dim tensor.  Its backward pass returns dJ/dq and dJ/d(state) computed by
-the library's reversed-pass adjoint kernels (cl_adjoint): the forward and the
+``evolved_objective(q, state, spec, scale=None)`` evolves the lattice state
+``state`` (tensor [nf, 2, N, N, N]: field f, 0 = field / 1 = momentum,
+[z][y][x]) with coupling ``q`` through the CUDA library and returns the final
+objective J as a 0-dim tensor.  With self-consistent expansion the scale
+factor and its derivative at the start may be given as ``scale`` = (a, b)
+(else the lattice's own initial values are used, held fixed).  Its backward
+pass returns dJ/dq, dJ/d(state) and dJ/d(scale), computed at a fixed initial
+(state, a, b) by the library's reversed-pass adjoint kernels (cl_adjoint): the forward and the
 adjoint sweep run together in the forward call, and backward only scales the
 stored gradients by the incoming gradient.  PyTorch supplies the tensors and
 the autograd graph; every step of the evolution and of the adjoint runs in
@@ -48,7 +51,7 @@ class RunSpec:
 
 class EvolvedObjective(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, q, state, spec):
+    def forward(ctx, q, state, scale, spec):
         kw = dict(spec.params)
         kw["q"] = float(q.detach().cpu())
         lat = Lattice(spec.model, spec.N, spec.kIR, spec.alpha, spec.seed, make_params(**kw))
@@ -56,23 +59,34 @@ class EvolvedObjective(torch.autograd.Function):
         for f in range(host.shape[0]):
             for w in (0, 1):
                 lat.set(f, w, host[f, w])
-        J, dq, lam = lat.adjoint(spec.nsteps, spec.ckpt_every, spec.objective, spec.field, spec.what,
-                                 spec.dk_bin, spec.bin)
+        if scale is not None:
+            eta0 = lat.scalars()[0]
+            a0, b0 = (float(x) for x in scale.detach().cpu())
+            lat.set_scalars(eta0, a0, b0)
+        J, dq, lam, ab = lat.adjoint(spec.nsteps, spec.ckpt_every, spec.objective, spec.field, spec.what,
+                                     spec.dk_bin, spec.bin, scale=True)
         lat.close()
         ctx.save_for_backward(torch.tensor(dq, dtype=torch.float64),
-                              torch.from_numpy(np.ascontiguousarray(lam)))
+                              torch.from_numpy(np.ascontiguousarray(lam)),
+                              torch.tensor(ab, dtype=torch.float64))
         ctx.state_meta = (state.dtype, state.device)
+        ctx.scale_meta = None if scale is None else (scale.dtype, scale.device)
         return torch.tensor(J, dtype=torch.float64, device=state.device)
 
     @staticmethod
     def backward(ctx, g):
-        dq, lam = ctx.saved_tensors
+        dq, lam, ab = ctx.saved_tensors
         dtype, device = ctx.state_meta
-        gq = (g.detach().cpu() * dq).to(device)
-        gs = (g.detach().cpu() * lam).to(device=device, dtype=dtype)
-        return gq, gs, None
+        gc = g.detach().cpu()
+        gq = (gc * dq).to(device)
+        gs = (gc * lam).to(device=device, dtype=dtype)
+        gab = None
+        if ctx.scale_meta is not None:
+            gab = (gc * ab).to(device=ctx.scale_meta[1], dtype=ctx.scale_meta[0])
+        return gq, gs, gab, None
 
 
-def evolved_objective(q, state, spec):
-    """J of the evolution of `state` with coupling `q` (differentiable in both)."""
-    return EvolvedObjective.apply(q, state, spec)
+def evolved_objective(q, state, spec, scale=None):
+    """J of the evolution of `state` with coupling `q` (differentiable in both,
+    and in `scale` = (a, b) at the start when given)."""
+    return EvolvedObjective.apply(q, state, scale, spec)

@@ -7,7 +7,10 @@
 //   dE_V/dphi_f  = dV/dphi_f / V:
 //   dJ/dpi_f  = (delta_{f,chi} - J) pi_f/(a^6 V rho)
 //   dJ/dphi_f = [delta_{f,chi} dE_G^f/dphi_f - J (dE_G^f/dphi_f + dE_V/dphi_f)]/rho
-//   dJ/dq (explicit) = -(J/rho) <phi^2 chi^2/2>.
+//   dJ/dq (explicit) = -(J/rho) <phi^2 chi^2/2>,
+//   dJ/da = [-(6 E_K^chi + 2 E_G^chi) + J (6 E_K + 2 E_G)]/(a rho)
+// (E_K ~ a^-6, E_G ~ a^-2 at fixed phi, pi; the seed of lam_a with
+// self-consistent expansion).
 // Objective 1, one bin of the binned spectrum (eq. discretePS) of an array u:
 //   J = C_b sum_{n in b} |F(n)|^2, F = sum_x u(x) e^{-ik.x},
 //   C_b = k_b^3/(2 pi^2) (dx/N)^3/(4 pi nbar_b^2),
@@ -64,15 +67,25 @@ __global__ void seed_chi_fraction_kernel(const LatConst* Lc, const LatScalars* S
   }
 }
 
-// J and the explicit dJ/dq of objective 0: out[0] = J, out[1] = -(J/rho) <phi^2 chi^2/2>.
+// J and the explicit dJ/dq of objective 0: out[0] = J, out[1] = -(J/rho) <phi^2 chi^2/2>;
+// with self-consistent expansion also the seed of lam_a, Sc->adja = dJ/da.
 __global__ void chi_fraction_final_kernel(const double* part, int nblk, const LatConst* Lc,
-                                          const LatScalars* Sc, double* out) {
+                                          LatScalars* Sc, double* out) {
   if (threadIdx.x | blockIdx.x) return;
   double s = 0.0;
   for (int i = 0; i < nblk; ++i) s += part[i];
-  const double rho = Sc->obs.rho, J = (Sc->obs.EK[1] + Sc->obs.EG[1]) / rho;
+  const cl_energies_t& o = Sc->obs;
+  const double rho = o.rho, J = (o.EK[1] + o.EG[1]) / rho;
   out[0] = J;
   out[1] = -J / rho * s * Lc->inv_V;
+  if (Lc->expansion == CL_EXP_SELF) {
+    double ek = 0.0, eg = 0.0;
+    for (int k = 0; k < 4; ++k) {
+      ek += o.EK[k];
+      eg += o.EG[k];
+    }
+    Sc->adja = (-(6.0 * o.EK[1] + 2.0 * o.EG[1]) + J * (6.0 * ek + 2.0 * eg)) / (Sc->a * rho);
+  }
 }
 
 // Objective 1: keep bin b of F scaled by 2 C_b (zero elsewhere); bins[] holds
@@ -109,7 +122,7 @@ __global__ void real_part_kernel(const double2* F, T* out, long long V) {
     out[n] = (T)F[n].x;
 }
 
-cudaError_t launch_seed_chi_fraction(int fp32, const LatConst* L, const LatScalars* S, int parity,
+cudaError_t launch_seed_chi_fraction(int fp32, const LatConst* L, LatScalars* S, int parity,
                                      void* const* lam, double* part, int nblk, double* out,
                                      cudaStream_t st) {
   if (fp32)

@@ -43,8 +43,8 @@ cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, 
 cudaError_t launch_u1_gauss_monitor(const LatConst*, int, double*, int, long long, cudaStream_t);
 __global__ void set_scalars_kernel(const LatConst*, LatScalars*, double, double, double);
 __global__ void b_from_obs_kernel(const LatConst*, LatScalars*);
-PassKernel adjoint_pass_kernel(int fp32, int nf);
-cudaError_t launch_seed_chi_fraction(int, const LatConst*, const LatScalars*, int, void* const*, double*, int,
+PassKernel adjoint_pass_kernel(int fp32, int nf, int self);
+cudaError_t launch_seed_chi_fraction(int, const LatConst*, LatScalars*, int, void* const*, double*, int,
                                      double*, cudaStream_t);
 cudaError_t launch_spectrum_seed(int, double2*, int, double, int, int, const double*, double, double, double*,
                                  int, void*, cudaStream_t);
@@ -1255,7 +1255,7 @@ static cl_status adjoint_plan(cl_ctx* c) {
   A.stage_bytes = (unsigned)stage_size(H.N, BY, narr, c->esz);
   A.stages = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / A.stage_bytes);
   A.smem = (size_t)A.stages * A.stage_bytes + SM_TAIL_BYTES;
-  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf);
+  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf, c->p.expansion == CL_EXP_SELF);
   CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.smem));
   const size_t ab = (size_t)H.V * c->esz;
   CU(cudaMalloc(&A.lam, 2 * (size_t)(2 * c->nf) * ab));
@@ -1290,10 +1290,10 @@ static cl_status adjoint_plan(cl_ctx* c) {
   return CL_OK;
 }
 
-// n reversed passes, coefficients dev_coef[4 i .. 4 i + 3] for the i-th.
+// n reversed passes, coefficients dev_coef[ADJ_COEF_W i ..] for the i-th.
 static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
   AdjPlan& J = c->adj;
-  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf);
+  PassKernel k = adjoint_pass_kernel(c->fp32, c->nf, c->p.expansion == CL_EXP_SELF);
   PassArgs A;
   memset(&A, 0, sizeof(A));
   A.lat = J.d_lat;
@@ -1320,7 +1320,7 @@ static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
     ++c->launches;
   } else {
     for (int i = 0; i < n; ++i) {
-      A.adj = dev_coef + 4 * i;
+      A.adj = dev_coef + (size_t)ADJ_COEF_W * i;
       A.parity = c->parity ^ (i & 1);
       k<<<J.grid, THREADS, J.smem, c->stream>>>(A);
       CHECK_LAUNCH();
@@ -1334,13 +1334,12 @@ static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
 extern "C" {
 
 cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int field, int what, double dk_bin,
-                     int bin, double* J, double* dJ_dq, double* dJ_dstate) {
+                     int bin, double* J, double* dJ_dq, double* dJ_dstate, double* dJ_dscale) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, CL_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "the adjoint covers single scalar lattices");
-  if (c->p.expansion == CL_EXP_SELF)
-    return fail(c, CL_EUNSUPPORTED, "the adjoint covers fixed backgrounds (expansion off or fixed)");
+  const bool self = c->p.expansion == CL_EXP_SELF;
   if (objective == CL_OBJ_CHI_FRACTION) {
     if (c->model != CL_MODEL_LPHI4_CHI) return fail(c, CL_EINVAL, "the chi energy fraction needs two fields");
   } else if (objective == CL_OBJ_SPECTRUM_BIN) {
@@ -1363,6 +1362,12 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
   const int nsub = (int)dsub.size();
   const int nchunk = (nsteps + ckpt_every - 1) / ckpt_every;
   const long long npass = (long long)nsteps * nsub + 1;  // with the closing half kick
+  // the lattice's scalars (a, b, eta, ...) at the start, put back at the end
+  LatScalars sc0;
+  CU(cudaMemcpyAsync(&sc0, &c->d_sc[0], sizeof(sc0), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  std::vector<PassStep> fw;  // every forward pass's weights, in order
+  fw.reserve((size_t)npass);
   void* ckpt = nullptr;
   double* dlog = nullptr;
   double* dcoef = nullptr;
@@ -1390,11 +1395,12 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
     }                       \
   } while (0)
   if (cudaMalloc(&ckpt, (size_t)(nchunk + 1) * na * ab) != cudaSuccess ||
-      cudaMalloc(&dlog, (size_t)npass * 4 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dcoef, (size_t)npass * 4 * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&dlog, (size_t)npass * ADJ_LOG_W * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dcoef, (size_t)npass * ADJ_COEF_W * sizeof(double)) != cudaSuccess) {
     cleanup();
     return fail(c, CL_ENOMEM, "adjoint: checkpoint / log allocation failed");
   }
+  CU(cudaMemsetAsync(dlog, 0, (size_t)npass * ADJ_LOG_W * sizeof(double), c->stream));
   // ---- forward: chunks of ckpt_every steps, the state saved after each ----
   ADJ_TRY(copy_state(ckpt, 0, true));
   std::vector<long long> chunk_first(nchunk + 1, 0);
@@ -1413,6 +1419,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
         c->dprev = d;
       }
     chunk_first[ch] = pc;
+    fw.insert(fw.end(), steps.begin(), steps.end());
     for (size_t b = 0; b < steps.size(); b += 4096) {
       const int mm = (int)std::min<size_t>(4096, steps.size() - b);
       ADJ_TRY(launch_passes(c, steps.data() + b, mm, red_for_step(c), 1, 0, dlog, pc));
@@ -1423,6 +1430,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
   chunk_first[nchunk] = pc;
   if (c->open) {  // the closing half kick, which also measures
     PassStep st = {0.5 * c->dprev, 0.5 * c->dprev, 0.0, 0.0};
+    fw.push_back(st);
     ADJ_TRY(launch_passes(c, &st, 1, 2, 1, 0, dlog, pc));
     ++pc;
     c->open = false;
@@ -1431,7 +1439,10 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
     ADJ_TRY(measure(c, 0));
   }
   const long long nrev = pc;  // passes to reverse
-  // ---- seed: dJ/d(final state) and the objective ----
+  // ---- seed: dJ/d(final state) and the objective (dJ/dq, dJ/da, dJ/db zeroed first) ----
+  static_assert(offsetof(LatScalars, adjb) == offsetof(LatScalars, adjq) + 2 * sizeof(double),
+                "adjq, adja, adjb are consecutive");
+  CU(cudaMemsetAsync(&c->d_sc[0].adjq, 0, 3 * sizeof(double), c->stream));
   void* lam[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int a = 0; a < na; ++a) lam[a] = (char*)c->adj.lam + ((size_t)c->parity * na + a) * ab;
   if (objective == CL_OBJ_CHI_FRACTION) {
@@ -1463,14 +1474,38 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
                             lam[2 * field + what], c->stream));
     c->launches += 5;
   }
-  CU(cudaMemsetAsync(&c->d_sc[0].adjq, 0, sizeof(double), c->stream));
   // ---- reverse sweep: coefficients of the recorded passes, last first ----
   {
-    std::vector<double> hlog((size_t)nrev * 4), hrev((size_t)nrev * 4);
+    std::vector<double> hlog((size_t)nrev * ADJ_LOG_W), hrev((size_t)nrev * ADJ_COEF_W, 0.0);
     CU(cudaMemcpyAsync(hlog.data(), dlog, hlog.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    for (long long i = 0; i < nrev; ++i)
-      for (int k = 0; k < 4; ++k) hrev[4 * i + k] = hlog[4 * (nrev - 1 - i) + k];
+    const double al = c->alpha, C = c->p.fstar_over_mp * c->p.fstar_over_mp / 3.0;
+    const double iV = 1.0 / (double)H.V, idx2 = 1.0 / (H.dx * H.dx);
+    for (long long i = 0; i < nrev; ++i) {
+      const long long k = nrev - 1 - i;
+      const double* lg = &hlog[(size_t)k * ADJ_LOG_W];
+      double* rc = &hrev[(size_t)i * ADJ_COEF_W];
+      for (int m = 0; m < 4; ++m) rc[m] = lg[m];
+      if (!self) continue;
+      // Friedmann kicks of forward pass k at a = a_k (K_a = C a^{2 alpha+1} [(alpha-2) E_K + alpha E_G
+      // + (alpha+1) E_V]): dK_a/dpi = C (alpha-2) a^{2 alpha-5} pi/V, dK_a/dphi = C a^{2 alpha+1}
+      // [-alpha Lap phi/(a^2 dx^2) + (alpha+1) dV/dphi]/V, dK_a/dq = C (alpha+1) a^{2 alpha+1} dV/dq/V
+      const double a = lg[4], win = fw[(size_t)k].win, wout = fw[(size_t)k].wout;
+      const double kpi = C * (al - 2.0) * std::pow(a, 2.0 * al - 5.0) * iV;
+      rc[4] = win * kpi;
+      rc[5] = wout * kpi;
+      rc[6] = (win + wout) * C * (-al) * std::pow(a, 2.0 * al - 1.0) * idx2 * iV;
+      rc[7] = (win + wout) * C * (al + 1.0) * std::pow(a, 2.0 * al + 1.0) * iV;
+      rc[8] = 1.0 / a;
+      rc[9] = lg[5];
+      // the pass's drift: a_k = a_{k-1} + w b, cd = w abar^{alpha-3}, abar = (a_{k-1} + a_k)/2
+      const double w = k > 0 ? fw[(size_t)k - 1].dnext : 0.0;
+      if (w != 0.0) {
+        const double abar = 0.5 * (hlog[(size_t)(k - 1) * ADJ_LOG_W + 4] + a);
+        rc[10] = w * (al - 3.0) * std::pow(abar, al - 4.0);
+        rc[11] = w;
+      }
+    }
     CU(cudaMemcpyAsync(dcoef, hrev.data(), hrev.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // the closing pass, then chunk by chunk, each started from its saved end state
     long long done = 0;
@@ -1483,16 +1518,16 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
       long long left = chunk_first[ch + 1] - chunk_first[ch];
       while (left > 0) {
         const int mm = (int)std::min<long long>(4096, left);
-        ADJ_TRY(launch_adjoint(c, dcoef + 4 * done, mm));
+        ADJ_TRY(launch_adjoint(c, dcoef + (size_t)ADJ_COEF_W * done, mm));
         done += mm;
         left -= mm;
       }
     }
     ADJ_TRY(copy_state(ckpt, 0, false));
   }
-  double out[2] = {0.0, 0.0}, adjq = 0.0;
+  double out[2] = {0.0, 0.0}, adj3[3] = {0.0, 0.0, 0.0};
   CU(cudaMemcpyAsync(out, c->adj.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaMemcpyAsync(&adjq, &c->d_sc[0].adjq, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(adj3, &c->d_sc[0].adjq, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (dJ_dstate) {
     for (int a = 0; a < na; ++a) {
       const void* src = (char*)c->adj.lam + ((size_t)c->parity * na + a) * ab;
@@ -1503,18 +1538,28 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
     }
   }
   CU(cudaStreamSynchronize(c->stream));
+  const cl_status st = check_status(c);
+  if (st == CL_ETIMEOUT) sc0.status = CL_ETIMEOUT;  // kept for later calls
+  CU(cudaMemcpyAsync(&c->d_sc[0], &sc0, sizeof(sc0), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
   cleanup();
 #undef ADJ_TRY
   c->obs_valid = false;
   if (J) *J = out[0];
-  if (dJ_dq) *dJ_dq = out[1] + adjq;
-  return check_status(c);
+  if (dJ_dq) *dJ_dq = out[1] + adj3[0];
+  if (dJ_dscale) {
+    dJ_dscale[0] = self ? adj3[1] : 0.0;
+    dJ_dscale[1] = self ? adj3[2] : 0.0;
+  }
+  return st;
 }
 
 cl_status cl_ic_amplitude_grad(cl_ctx* c, const double* dJ_dstate, double* out) {
   if (!c || !dJ_dstate || !out) return fail(c, CL_EINVAL, "NULL argument");
   if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "amplitude gradients cover single scalar lattices");
+  if (c->p.expansion == CL_EXP_SELF && c->p.b0_mode == 1)
+    return fail(c, CL_EUNSUPPORTED, "with a' from lattice averages the initial b depends on the amplitudes");
   const LatHost& H = c->lats[0];
   double2* Lf = c->d_cplx;
   double2* Lp = c->d_cplx + H.V;

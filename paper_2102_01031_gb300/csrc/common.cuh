@@ -46,6 +46,7 @@ struct LatScalars {
   double pi2A;                    // the same for the U(1) link momenta
   cl_energies_t obs;              // last measurement
   double adjq;                    // adjoint sweep: accumulated dJ/dq of the passes
+  double adja, adjb;              // adjoint sweep: dJ/da, dJ/db (self-consistent expansion)
   double H_ic;                    // a'/a the initial conditions were drawn with
   int status, pad;
 };
@@ -100,13 +101,18 @@ struct PassArgs {
   const PassStep* steps;
   int npass, pad2;
   unsigned* gsync;
-  // forward passes: when set, block 0 records the coefficients each pass
-  // uses, log[4 (log_base + pass) + {0..3}] = cd, c_k, a^{1+alpha}/dx^2, a^{3+alpha}
+  // forward passes: when set, what each pass used, for an adjoint sweep (one
+  // lattice), ADJ_LOG_W words per pass at log + ADJ_LOG_W (log_base + pass):
+  // block 0 writes cd, c_k, c_k a^{1+alpha}/dx^2, c_k a^{3+alpha}, a; the tail
+  // writes the a-derivative of the pass's two Friedmann kicks,
+  // w_in dK_a/da (post-kick momenta) + w_out dK_a/da (pre-kick momenta)
   double* log;
   long long log_base;
-  // adjoint passes: the coefficients of each reversed pass, 4 per pass as in log
+  // adjoint passes: ADJ_COEF_W coefficients per reversed pass (pass_adjoint.cu)
   const double* adj;
 };
+constexpr int ADJ_LOG_W = 6;
+constexpr int ADJ_COEF_W = 12;
 
 // Initial-condition parameters (program units).
 struct ICArgs {

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // sums, each over the lattice's slots in a fixed order (warp_slot_sum), so
   // the result does not depend on timing; then thread l updates a, b and the
   // next pass's coefficients of lattice pend[base + l], all lattices at once.
-  auto run_tails = [&](int base, int nb, const PassStep& st) {
+  auto run_tails = [&](int base, int nb, const PassStep& st, double* lg) {
     for (int it = warp; it < nb * NUSED; it += CONSUMER_WARPS) {
       constexpr int NQU = NUSED > 0 ? NUSED : 1;
       const int l = it / NQU, q = it - l * NQU;
@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
         E.EV = vs * L.inv_V;
       }
       advance_scalars(Q, L, W, E, RED > 0);
+      if (lg && lat == 0)
+        lg[5] = RED > 0 && L.expansion == CL_EXP_SELF ? kernel_a_da(Q, L, W.a, E) : 0.0;
       if (RED == 2) {
         cl_energies_t& o = P.sc[lat].obs;
         for (int k = 0; k < 4; ++k) {
@@ -308,11 +310,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
     if (P.log && blockIdx.x == 0 && tid == 0) {  // coefficients of this pass, for an adjoint sweep
       const LatScalars* S0 = &P.sc[0];
       const double ckp = P.steps ? P.steps[pass].ck : P.ck;
-      double* lg = P.log + 4 * (P.log_base + pass);
+      double* lg = P.log + ADJ_LOG_W * (P.log_base + pass);
       lg[0] = __ldcg(&S0->cd);
       lg[1] = ckp;
       lg[2] = ckp * __ldcg(&S0->apow1) * P.lat[0].inv_dx2;
       lg[3] = ckp * __ldcg(&S0->apow3);
+      lg[4] = __ldcg(&S0->a);
     }
 
     for (int i = 0; i < ns; ++i) {
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       const PassStep pst = P.steps ? P.steps[pass] : PassStep{P.ck, P.wout, P.win, P.dnext};
       for (int base = 0; base < npend; base += 32) {
         __threadfence();
-        run_tails(base, min(32, npend - base), pst);
+        run_tails(base, min(32, npend - base), pst, P.log ? P.log + ADJ_LOG_W * (P.log_base + pass) : nullptr);
       }
       __syncthreads();
       if (tid == 0) flag[3] = 0;

@@ -96,6 +96,17 @@ __device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, SS&
   }
 }
 
+// w_in dK_a/da + w_out dK_a/da of the two Friedmann kicks of a pass (scalar
+// fields), at fixed fields and momenta: with E_K ~ a^-6, E_G ~ a^-2,
+//   d/da [a^{2alpha+1} E] = a^{2alpha} (2alpha+1-s) E  for E ~ a^-s.
+__device__ __forceinline__ double kernel_a_da(const PassArgs& P, const LatConst& L, double a,
+                                              const PassSums& E) {
+  const double al = L.alpha, w = P.win + P.wout;
+  return apow(L, a, 2, 0) * (1.0 / 3.0) * L.fm2 *
+         ((2.0 * al - 5.0) * (al - 2.0) * (P.win * E.EKpost + P.wout * E.EKpre) +
+          w * ((2.0 * al - 1.0) * al * E.EG + (2.0 * al + 1.0) * (al + 1.0) * E.EV));
+}
+
 template <class SS>
 __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S) {
   const double a = S.a;
