@@ -45,7 +45,7 @@ PASSES_PER_STEP = 3
 # profiles/dk_pass_fp32_256_ncu.md (one cooperative launch of the three VV4
 # passes of a step, divided by 3), valid only for the kernel source it was
 # taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "7ea3c75d659c321c", "bytes_per_launch": 578235050}}
+NCU_TRAFFIC = {"f32": {"source_hash": "8f568f07fe95550d", "bytes_per_launch": 578079232}}
 
 
 def peaks():
