@@ -113,9 +113,8 @@ __global__ void __launch_bounds__(THREADS, 1) adj_pass_scalar(const PassArgs P) 
 
   for (int pass = 0; pass < P.npass; ++pass) {
     const int parity = P.parity ^ (pass & 1);
-    const int gbase = pass * ptot;
     const double* cfp = P.adj + ADJ_COEF_W * pass;
-    if (tid == 0) ring_pass_start<T, NA>(R, P, pass, ptot, parity);
+    if (warp == 0) ring_pass_start<T, NA>(R, P, pass, ptot, parity, lane);
     __syncthreads();
     if (R.flag[0]) goto timeout;
 
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(THREADS, 1) adj_pass_scalar(const PassArgs P) 
       };
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) centre(ring_stage<T>(R, s_cur), bF, bL);
-      ring_release<T, NA>(R, g0, s_cur, gbase, parity, ptot, lane);
+      ring_release<T, NA>(R, g0, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) centre(ring_stage<T>(R, s_cur), cF, cL);
@@ -273,12 +272,12 @@ __global__ void __launch_bounds__(THREADS, 1) adj_pass_scalar(const PassArgs P) 
               cL[k][v] = aL[k][v];
             }
         }
-        ring_release<T, NA>(R, g0 + j, s_cur, gbase, parity, ptot, lane);
+        ring_release<T, NA>(R, g0 + j, s_cur, parity, ptot, lane);
         s_cur = s_nxt;
         p_cur = p_nxt;
         ring_advance(S, s_nxt, p_nxt);
       }
-      ring_release<T, NA>(R, g0 + sg.nz + 1, s_cur, gbase, parity, ptot, lane);
+      ring_release<T, NA>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
 
       if (!sg.flush) continue;

@@ -148,45 +148,51 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // plane gbase + g of the CTA's whole sequence and sits in stage (gbase+g) mod S
   int gbase = 0;
 
-  // bulk copies of plane g of this pass into its stage
-  auto issue = [&](int g) {
+  // bulk copies of plane g of this pass into stage s, issued by a whole warp:
+  // lane a + NA k copies run k of array a (a tile's rows form up to three
+  // runs where they wrap around the periodic y boundary).  Stage memory is only
+  // ever read through the generic proxy, and its reuse is ordered by the
+  // release count, so no proxy fence precedes the copies.  Warp-uniform calls.
+  auto issue_warp = [&](int g, int s) {
     int i = 0;
     while (g >= off[i + 1]) ++i;
     const IssueInfo& in = info[i];
-    const int N = in.N, rows = in.rows, ylo = in.ylo, arr_elems = rows * N;
-    const int s = (gbase + g) % S;
-    T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max);
+    const int N = in.N, rows = in.rows, arr_elems = rows * N;
     const int j = g - off[i];
     int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
     zp = zp < 0 ? zp + N : (zp >= N ? zp - N : zp);
-    const long long zoff = (long long)zp * N * N;
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
-    int r = 0;
-    while (r < rows) {
-      int g2 = ylo - 1 + r;
-      g2 = g2 < 0 ? g2 + N : (g2 >= N ? g2 - N : g2);
-      int run = 1;
-      while (r + run < rows && g2 + run < N) ++run;
-#pragma unroll
-      for (int a = 0; a < NA; ++a)
-        bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N,
-                 reinterpret_cast<const T*>(in.src[parity][a]) + zoff + (long long)g2 * N,
-                 (uint32_t)(run * N * sizeof(T)), &full[s]);
-      r += run;
+    // rows ylo-1 .. ylo+rows-2 of the plane, periodic in y: r1 rows from y1, then
+    // r2 rows from row 0, then (a tile as tall as the lattice wraps twice) r3 from row 0
+    const int y0 = in.ylo - 1;
+    const int y1 = y0 < 0 ? y0 + N : y0;
+    const int r1 = min(rows, N - y1), r2 = min(rows - r1, N), r3 = rows - r1 - r2;
+    if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
+    __syncwarp();
+    if (lane < 3 * NA) {
+      const int run = lane / NA, a = lane - run * NA;
+      const int nr = run == 0 ? r1 : (run == 1 ? r2 : r3);
+      if (nr > 0) {
+        const int d = run == 0 ? 0 : (run == 1 ? r1 : r1 + r2), ys = run == 0 ? y1 : 0;
+        T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max) + (size_t)a * arr_elems;
+        const T* src = reinterpret_cast<const T*>(in.src[parity][a]) + (long long)zp * N * N;
+        bulk_g2s(st + (size_t)d * N, src + (long long)ys * N, (uint32_t)(nr * N * sizeof(T)), &full[s]);
+      }
     }
   };
-  // a warp is done with plane g (in stage s); the last of the 16 refills s with plane g + S
+  // a warp is done with plane g (in stage s); the last of the 16 refills s with
+  // plane g + S (which belongs in the same stage)
   auto release = [&](int g, int s) {
     __syncwarp();
+    int refill = 0;
     if (lane == 0) {
       __threadfence_block();
       const unsigned prev = atomicAdd(&released[s], 1u);
       if (prev == CONSUMER_WARPS - 1u) {
         released[s] = 0u;
-        if (g + S < ptot && !flag[0]) issue(g + S);
+        refill = g + S < ptot && !flag[0];
       }
     }
+    if (__shfl_sync(0xffffffffu, refill, 0)) issue_warp(g + S, s);
     __syncwarp();
   };
   auto wait_full = [&](int s, uint32_t par) {
@@ -292,16 +298,19 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   for (int pass = 0; pass < P.npass; ++pass) {
     parity = P.parity ^ (pass & 1);
     gbase = pass * ptot;
-    if (tid == 0) {
-      if (pass > 0) {
+    if (warp == 0) {
+      int go = 0;
+      if (lane == 0) {
         // the previous pass's writes are all done before any of its planes is read
-        if (!flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
+        if (pass > 0 && !flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
           flag[0] = 1;
-        fence_proxy_async_global();
+        go = !flag[0];
       }
-      if (!flag[0])
-        for (int g = 0; g < S && g < ptot; ++g) issue(g);
-      if (pass > 0 && !flag[0] &&
+      go = __shfl_sync(0xffffffffu, go, 0);
+      if (pass > 0) fence_proxy_async_global();
+      if (go)
+        for (int g = 0; g < S && g < ptot; ++g) issue_warp(g, (gbase + g) % S);
+      if (lane == 0 && pass > 0 && !flag[0] &&
           !wait_counter(&P.gsync[1], (unsigned)P.nlat * (unsigned)pass, P.wait_limit_ns))
         flag[0] = 1;
     }

@@ -111,8 +111,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
 
   for (int pass = 0; pass < P.npass; ++pass) {
     const int parity = P.parity ^ (pass & 1);
-    const int gbase = pass * ptot;
-    if (tid == 0) ring_pass_start<T, NA>(R, P, pass, ptot, parity);
+    if (warp == 0) ring_pass_start<T, NA>(R, P, pass, ptot, parity, lane);
     __syncthreads();
     if (R.flag[0]) goto timeout;
 
@@ -196,7 +195,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
           sincos_t(gd * azm[v], bSz[v], bCz[v]);
         }
       }
-      ring_release<T, NA>(R, g0, s_cur, gbase, parity, ptot, lane);
+      ring_release<T, NA>(R, g0, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) {
@@ -401,12 +400,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             bSyz[v] = pyz[v];
           }
         }
-        ring_release<T, NA>(R, g0 + j, s_cur, gbase, parity, ptot, lane);
+        ring_release<T, NA>(R, g0 + j, s_cur, parity, ptot, lane);
         s_cur = s_nxt;
         p_cur = p_nxt;
         ring_advance(S, s_nxt, p_nxt);
       }
-      ring_release<T, NA>(R, g0 + sg.nz + 1, s_cur, gbase, parity, ptot, lane);
+      ring_release<T, NA>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
 
       if (!sg.flush) continue;

@@ -80,51 +80,56 @@ __device__ __forceinline__ const T* ring_stage(const Ring& R, int s) {
   return reinterpret_cast<const T*>(R.stages + (size_t)s * R.stage_bytes);
 }
 
-// Bulk copies of plane g (of the current pass) into its stage; rows that
-// wrap around the periodic y boundary are split into two runs.
+// Bulk copies of plane g (of the current pass) into stage s, issued by a
+// whole warp (warp-uniform call): lane a + NA k copies run k of array a (a
+// tile's rows form up to three runs where they wrap around the periodic y
+// boundary).
+// Stage memory is only read through the generic proxy and its reuse is
+// ordered by the release count, so no proxy fence precedes the copies.
 template <typename T, int NA>
-__device__ void ring_issue(const Ring& R, int g, int gbase, int parity) {
+__device__ void ring_issue_warp(const Ring& R, int g, int s, int parity, int lane) {
+  static_assert(3 * NA <= 32, "one lane per copy");
   int i = 0;
   while (g >= R.off[i + 1]) ++i;
   const IssueInfo& in = R.info[i];
-  const int N = in.N, rows = in.rows, ylo = in.ylo, arr_elems = rows * N;
-  const int s = (gbase + g) % R.S;
-  T* st = reinterpret_cast<T*>(R.stages + (size_t)s * R.stage_bytes);
+  const int N = in.N, rows = in.rows, arr_elems = rows * N;
   const int j = g - R.off[i];
   int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
   zp = zp < 0 ? zp + N : (zp >= N ? zp - N : zp);
-  const long long zoff = (long long)zp * N * N;
-  fence_proxy_async_smem();
-  mbar_arrive_expect_tx(&R.full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
-  int r = 0;
-  while (r < rows) {
-    int g2 = ylo - 1 + r;
-    g2 = g2 < 0 ? g2 + N : (g2 >= N ? g2 - N : g2);
-    int run = 1;
-    while (r + run < rows && g2 + run < N) ++run;
-#pragma unroll
-    for (int a = 0; a < NA; ++a)
-      bulk_g2s(st + (size_t)a * arr_elems + (size_t)r * N,
-               reinterpret_cast<const T*>(in.src[parity][a]) + zoff + (long long)g2 * N,
-               (uint32_t)(run * N * sizeof(T)), &R.full[s]);
-    r += run;
+  // rows ylo-1 .. ylo+rows-2 of the plane, periodic in y: r1 rows from y1, then
+  // r2 rows from row 0, then (a tile as tall as the lattice wraps twice) r3 from row 0
+  const int y0 = in.ylo - 1;
+  const int y1 = y0 < 0 ? y0 + N : y0;
+  const int r1 = min(rows, N - y1), r2 = min(rows - r1, N), r3 = rows - r1 - r2;
+  if (lane == 0) mbar_arrive_expect_tx(&R.full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
+  __syncwarp();
+  if (lane < 3 * NA) {
+    const int run = lane / NA, a = lane - run * NA;
+    const int nr = run == 0 ? r1 : (run == 1 ? r2 : r3);
+    if (nr > 0) {
+      const int d = run == 0 ? 0 : (run == 1 ? r1 : r1 + r2), ys = run == 0 ? y1 : 0;
+      T* st = reinterpret_cast<T*>(R.stages + (size_t)s * R.stage_bytes) + (size_t)a * arr_elems;
+      const T* src = reinterpret_cast<const T*>(in.src[parity][a]) + (long long)zp * N * N;
+      bulk_g2s(st + (size_t)d * N, src + (long long)ys * N, (uint32_t)(nr * N * sizeof(T)), &R.full[s]);
+    }
   }
 }
 
 // A warp is done with plane g (in stage s); the last of the CTA's warps
-// refills s with plane g + S of the same pass.
+// refills s with plane g + S of the same pass (which belongs in the same stage).
 template <typename T, int NA>
-__device__ __forceinline__ void ring_release(const Ring& R, int g, int s, int gbase, int parity,
-                                             int ptot, int lane) {
+__device__ __forceinline__ void ring_release(const Ring& R, int g, int s, int parity, int ptot, int lane) {
   __syncwarp();
+  int refill = 0;
   if (lane == 0) {
     __threadfence_block();
     const unsigned prev = atomicAdd(&R.released[s], 1u);
     if (prev == CONSUMER_WARPS - 1u) {
       R.released[s] = 0u;
-      if (g + R.S < ptot && !R.flag[0]) ring_issue<T, NA>(R, g + R.S, gbase, parity);
+      refill = g + R.S < ptot && !R.flag[0];
     }
   }
+  if (__shfl_sync(0xffffffffu, refill, 0)) ring_issue_warp<T, NA>(R, g + R.S, s, parity, lane);
   __syncwarp();
 }
 
@@ -204,19 +209,22 @@ __device__ void ring_slot_sums(const Ring& R, const PassArgs& P, const LatConst&
   __syncthreads();
 }
 
-// Between two passes of one launch (thread 0): the previous pass's writes
-// are all done before any of its planes is read; the first planes of the
-// pass are issued; then the updated scalars are awaited.
+// Between two passes of one launch (warp 0, all lanes): the previous pass's
+// writes are all done before any of its planes is read; the first planes of
+// the pass are issued; then the updated scalars are awaited.
 template <typename T, int NA>
-__device__ void ring_pass_start(const Ring& R, const PassArgs& P, int pass, int ptot, int parity) {
-  if (pass > 0) {
-    if (!R.flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
+__device__ void ring_pass_start(const Ring& R, const PassArgs& P, int pass, int ptot, int parity, int lane) {
+  int go = 0;
+  if (lane == 0) {
+    if (pass > 0 && !R.flag[0] && !wait_counter(&P.gsync[0], gridDim.x * (unsigned)pass, P.wait_limit_ns))
       R.flag[0] = 1;
-    fence_proxy_async_global();
+    go = !R.flag[0];
   }
-  if (!R.flag[0])
-    for (int g = 0; g < R.S && g < ptot; ++g) ring_issue<T, NA>(R, g, pass * ptot, parity);
-  if (pass > 0 && !R.flag[0] &&
+  go = __shfl_sync(0xffffffffu, go, 0);
+  if (pass > 0) fence_proxy_async_global();
+  if (go)
+    for (int g = 0; g < R.S && g < ptot; ++g) ring_issue_warp<T, NA>(R, g, (pass * ptot + g) % R.S, parity, lane);
+  if (lane == 0 && pass > 0 && !R.flag[0] &&
       !wait_counter(&P.gsync[1], (unsigned)P.nlat * (unsigned)pass, P.wait_limit_ns))
     R.flag[0] = 1;
 }
