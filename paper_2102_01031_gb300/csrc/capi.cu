@@ -886,6 +886,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     L.slot_end = send[l];
     L.esz = c->esz;
     L.int_alpha = (c->alpha == std::floor(c->alpha) && std::fabs(c->alpha) <= 4.0) ? 1 : 0;
+    L.alpha_i = L.int_alpha ? (int)c->alpha : 0;
     L.inv_V = 1.0 / (double)H.V;
     L.inv_dx2 = 1.0 / (H.dx * H.dx);
     if (u1) {

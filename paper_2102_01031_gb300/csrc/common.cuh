@@ -19,7 +19,7 @@ static_assert(CONSUMER_WARPS >= NQ, "the tail sums one slot per warp");
 struct LatConst {
   int N, BY, YT, model, nf, narr, expansion, esz;
   int slot_begin, slot_end;  // partial-sum slots of this lattice: [slot_begin, slot_end)
-  int int_alpha, pad;        // int_alpha: alpha is an integer in [-4, 4] (powers by multiplication)
+  int int_alpha, alpha_i;    // int_alpha: alpha is the integer alpha_i in [-4, 4] (powers by multiplication)
   long long V;
   double dx, alpha, q, lam, v, gQ, fo2, fm2, omega_eos;
   double inv_V, inv_dx2;

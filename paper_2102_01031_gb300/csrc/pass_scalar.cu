@@ -206,9 +206,29 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // Friedmann updates of the lattices pend[base .. base + nb) (nb <= 32) once
   // all their slots are written: the warps share the (lattice, quantity)
   // sums, each over the lattice's slots in a fixed order (warp_slot_sum), so
-  // the result does not depend on timing; then thread l updates a, b and the
-  // next pass's coefficients of lattice pend[base + l], all lattices at once.
+  // the result does not depend on timing; then lane l of the last warp updates
+  // a, b and the next pass's coefficients of lattice pend[base + l], all
+  // lattices at once.  That thread reads the lattice's scalars and constants
+  // into registers and forms the sum-independent factors while the slots are
+  // summed (FP64 has a long dependent latency, and this runs between passes).
   auto run_tails = [&](int base, int nb, const PassStep& st, double* lg) {
+    const bool tt = warp == CONSUMER_WARPS - 1 && lane < nb;
+    int lat = 0;
+    LatConst L;
+    ScalarState W;
+    double ck = 0.0, cg = 0.0;
+    FriedPre F = {};
+    bool self = false;
+    if (tt) {
+      lat = pend[base + lane];
+      L = P.lat[lat];
+      load_state_cg(W, &P.sc[lat]);
+      const double a = W.a, ia2 = 1.0 / (a * a);
+      ck = 0.5 * L.inv_V * (ia2 * ia2 * ia2);
+      cg = 0.5 * L.inv_V * L.inv_dx2 * ia2;
+      self = RED > 0 && L.expansion == CL_EXP_SELF;
+      if (self) F = friedmann_pre(L, a, st.wout, st.win);
+    }
     for (int it = warp; it < nb * NUSED; it += CONSUMER_WARPS) {
       constexpr int NQU = NUSED > 0 ? NUSED : 1;
       const int l = it / NQU, q = it - l * NQU;
@@ -217,19 +237,13 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       if (lane == 0) red[l * NQ + q] = s;
     }
     __syncthreads();
-    if (tid < nb) {
-      const int lat = pend[base + tid];
-      const LatConst& L = P.lat[lat];
+    if (tt) {
       PassArgs Q = P;
       Q.ck = st.ck;
       Q.wout = st.wout;
       Q.win = st.win;
       Q.dnext = st.dnext;
-      ScalarState W;
-      load_state_cg(W, &P.sc[lat]);
-      const double* sum = red + tid * NQ;
-      const double a = W.a, ia2 = 1.0 / (a * a), ia6 = ia2 * ia2 * ia2;
-      const double ck = 0.5 * L.inv_V * ia6, cg = 0.5 * L.inv_V * L.inv_dx2 * ia2;
+      const double* sum = red + lane * NQ;
       PassSums E = {0, 0, 0, 0, 0, 0, 0};
       if (RED > 0) {
         double spre = 0, spost = 0, gg = 0, vs = 0;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
         E.EG = gg * cg;
         E.EV = vs * L.inv_V;
       }
-      advance_scalars(Q, L, W, E, RED > 0);
+      if (self) W.b = friedmann_kicks_scalar(F, E, W.b);
       if (lg && lat == 0)
         lg[5] = RED > 0 && L.expansion == CL_EXP_SELF ? kernel_a_da(Q, L, W.a, E) : 0.0;
       if (RED == 2) {

@@ -35,24 +35,34 @@ struct PassSums {
   double EKApre;                  // U(1) electric before the kick
 };
 
-// a^(alpha + k): by repeated multiplication when alpha is a small integer
-// (alpha = 1 or 0 in the manual's scenarios), pow otherwise.  Double pow has
-// a long dependent latency and this runs between two passes.
-__device__ __forceinline__ double apow(const LatConst& L, double a, int m, int k) {
-  // exponent m * alpha + k
-  if (L.int_alpha) {
-    int e = m * (int)L.alpha + k;
-    const bool neg = e < 0;
-    e = neg ? -e : e;
-    double x = 1.0, b = a;
-    while (e) {
-      if (e & 1) x *= b;
-      b *= b;
-      e >>= 1;
+// The tail runs once per pass, on one thread, between passes: its cost is the
+// number of FP64 operations (each takes tens of cycles on this part, even when
+// independent), so integer powers use the fewest multiplications and general
+// powers go through one out-of-line pow.
+static __device__ __noinline__ double pow_out_of_line(double a, double e) { return pow(a, e); }
+
+// x^n by squaring with the fewest products (x^2: one, x^4: two, x^0: none).
+__device__ __forceinline__ double ipow(double x, int n) {
+  const bool neg = n < 0;
+  int m = neg ? -n : n;
+  double r = 1.0, p = x;
+  bool have = false;
+  while (m) {
+    if (m & 1) {
+      r = have ? r * p : p;
+      have = true;
     }
-    return neg ? 1.0 / x : x;
+    m >>= 1;
+    if (m) p = p * p;
   }
-  return pow(a, m * L.alpha + k);
+  return neg ? 1.0 / r : r;
+}
+
+// a^(m alpha + k): by multiplication when alpha is a small integer (alpha = 1
+// or 0 in the manual's scenarios), pow otherwise.
+__device__ __forceinline__ double apow(const LatConst& L, double a, int m, int k) {
+  if (L.int_alpha) return ipow(a, m * L.alpha_i + k);
+  return pow_out_of_line(a, m * L.alpha + k);
 }
 
 __device__ __forceinline__ double fixed_p(const LatConst& L) {
@@ -63,7 +73,7 @@ __device__ __forceinline__ double fixed_p(const LatConst& L) {
 template <class SS>
 __device__ __forceinline__ double a_fixed(const LatConst& L, const SS& S, double eta) {
   double p = fixed_p(L);
-  return S.a0 * pow(1.0 + S.Hfix * (eta - S.eta0) / p, p);
+  return S.a0 * pow_out_of_line(1.0 + S.Hfix * (eta - S.eta0) / p, p);
 }
 template <class SS>
 __device__ __forceinline__ double H_fixed(const LatConst& L, const SS& S, double eta) {
@@ -80,20 +90,51 @@ __device__ __forceinline__ double kernel_a(const LatConst& L, double a, double E
          ((al - 2.0) * EK + al * EG + (al - 1.0) * (EKA + EGA) + (al + 1.0) * EV);
 }
 
+// The factor a^{2alpha+1}/3 (f_s/m_p)^2 that both Friedmann kicks of a pass share.
+__device__ __forceinline__ double kernel_a_pref(const LatConst& L, double a) {
+  return apow(L, a, 2, 1) * (1.0 / 3.0) * L.fm2;
+}
+
 // Friedmann kicks of b (kick-out with the pre-kick momenta, then kick-in with
-// the post-kick momenta, as in the velocity-Verlet step), then the drift of a
-// by P.dnext and the drift coefficients of the next pass.
+// the post-kick momenta, as in the velocity-Verlet step), pref = kernel_a_pref
+// at the current a.
 template <class SS>
 __device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, SS& S,
-                                       const PassSums& E, bool have_sums) {
-  const double a = S.a;
+                                       const PassSums& E, bool have_sums, double pref) {
   if (have_sums && L.expansion == CL_EXP_SELF) {
-    // K_a of both kicks share a^{2alpha+1}/3 (f_s/m_p)^2 (one FP64 chain on the critical path)
-    const double al = L.alpha, pref = apow(L, a, 2, 1) * (1.0 / 3.0) * L.fm2;
+    const double al = L.alpha;
     const double common = al * E.EG + (al + 1.0) * E.EV;
     S.b += P.wout * (pref * ((al - 2.0) * E.EKpre + common + (al - 1.0) * (E.EKApre + E.EGA)));
     S.b += P.win * (pref * ((al - 2.0) * E.EKpost + common + (al - 1.0) * (E.EKA + E.EGA)));
   }
+}
+template <class SS>
+__device__ inline void advance_scalars(const PassArgs& P, const LatConst& L, SS& S,
+                                       const PassSums& E, bool have_sums) {
+  if (have_sums && L.expansion == CL_EXP_SELF) advance_scalars(P, L, S, E, true, kernel_a_pref(L, S.a));
+}
+
+// The two Friedmann kicks of a pass for the scalar models (no U(1) energies),
+// merged:  b += pref [(alpha-2)(w_out E_K^pre + w_in E_K^post) + (w_out + w_in)(alpha E_G + (alpha+1) E_V)].
+// FriedPre holds the factors that do not depend on the pass's sums.
+struct FriedPre {
+  double pref, am2, al, ap1, wout, win, ws;
+};
+__device__ __forceinline__ FriedPre friedmann_pre(const LatConst& L, double a, double wout, double win) {
+  FriedPre F;
+  F.pref = kernel_a_pref(L, a);
+  F.al = L.alpha;
+  F.am2 = L.alpha - 2.0;
+  F.ap1 = L.alpha + 1.0;
+  F.wout = wout;
+  F.win = win;
+  F.ws = wout + win;
+  return F;
+}
+__device__ __forceinline__ double friedmann_kicks_scalar(const FriedPre& F, const PassSums& E, double b) {
+  const double ek = fma(F.win, E.EKpost, F.wout * E.EKpre);
+  const double common = fma(F.ap1, E.EV, F.al * E.EG);
+  return fma(F.pref, fma(F.am2, ek, F.ws * common), b);
 }
 
 // w_in dK_a/da + w_out dK_a/da of the two Friedmann kicks of a pass (scalar
@@ -107,26 +148,49 @@ __device__ __forceinline__ double kernel_a_da(const PassArgs& P, const LatConst&
           w * ((2.0 * al - 1.0) * al * E.EG + (2.0 * al + 1.0) * (al + 1.0) * E.EV));
 }
 
+// The drift of a by P.dnext and the drift coefficients of the next pass:
+//   a' = a + dnext b (self-consistent) or a(eta + dnext) (fixed power law),
+//   cd = dnext abar^{alpha-3}, cdA = dnext abar^{alpha-1}, abar = (a + a')/2,
+//   and the kick's a'^{1+alpha}, a'^{3+alpha}, a'^{alpha-1}.
+// Few FP64 operations: alpha's exponents are read once, negative powers are
+// reciprocals of positive ones, and alpha = 1 (the manual's default) is
+// straight-line code.
 template <class SS>
 __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S) {
-  const double a = S.a;
-  if (P.dnext != 0.0) {
-    double an;
-    if (L.expansion == CL_EXP_SELF) an = a + P.dnext * S.b;
-    else if (L.expansion == CL_EXP_FIXED) an = a_fixed(L, S, S.eta + P.dnext);
-    else an = a;
-    const double abar = 0.5 * (a + an);
-    S.cd = P.dnext * apow(L, abar, 1, -3);
-    S.cdA = P.dnext * apow(L, abar, 1, -1);
-    S.a = an;
-    S.eta += P.dnext;
-    if (L.expansion == CL_EXP_FIXED) S.b = an * H_fixed(L, S, S.eta);
-    S.apow1 = apow(L, an, 1, 1);
-    S.apow3 = apow(L, an, 1, 3);
-    S.apowm1 = apow(L, an, 1, -1);
-  } else {
+  const double a = S.a, dn = P.dnext;
+  if (dn == 0.0) {
     S.cd = 0.0;
     S.cdA = 0.0;
+    return;
+  }
+  double an;
+  if (L.expansion == CL_EXP_SELF) an = fma(dn, S.b, a);
+  else if (L.expansion == CL_EXP_FIXED) an = a_fixed(L, S, S.eta + dn);
+  else an = a;
+  const double abar = 0.5 * (a + an);
+  S.a = an;
+  S.eta += dn;
+  if (L.expansion == CL_EXP_FIXED) S.b = an * H_fixed(L, S, S.eta);
+  const int ia = L.alpha_i;
+  if (L.int_alpha && ia == 1) {
+    const double an2 = an * an;
+    S.cd = dn * (1.0 / (abar * abar));
+    S.cdA = dn;
+    S.apow1 = an2;
+    S.apow3 = an2 * an2;
+    S.apowm1 = 1.0;
+  } else if (L.int_alpha) {
+    S.cd = dn * ipow(abar, ia - 3);
+    S.cdA = dn * ipow(abar, ia - 1);
+    S.apow1 = ipow(an, ia + 1);
+    S.apow3 = S.apow1 * (an * an);
+    S.apowm1 = ipow(an, ia - 1);
+  } else {
+    S.cd = dn * pow_out_of_line(abar, L.alpha - 3.0);
+    S.cdA = dn * pow_out_of_line(abar, L.alpha - 1.0);
+    S.apow1 = pow_out_of_line(an, L.alpha + 1.0);
+    S.apow3 = S.apow1 * (an * an);
+    S.apowm1 = pow_out_of_line(an, L.alpha - 1.0);
   }
 }
 
