@@ -147,6 +147,11 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // planes of earlier passes of this launch: plane g of the current pass is
   // plane gbase + g of the CTA's whole sequence and sits in stage (gbase+g) mod S
   int gbase = 0;
+  // passes reading buffer 1 march the CTA's sequence backwards (plane g is
+  // plane ptot-1-g of the forward sequence: segments in reverse order, each
+  // marched the other way), so that a pass starts on the planes the previous
+  // pass wrote last, while they are still in L2
+  bool rev = false;
 
   // bulk copies of plane g of this pass into stage s, issued by a whole warp:
   // lane a + NA k copies run k of array a (a tile's rows form up to three
@@ -154,11 +159,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
   // ever read through the generic proxy, and its reuse is ordered by the
   // release count, so no proxy fence precedes the copies.  Warp-uniform calls.
   auto issue_warp = [&](int g, int s) {
+    const int gf = rev ? ptot - 1 - g : g;  // position in the forward sequence
     int i = 0;
-    while (g >= off[i + 1]) ++i;
+    while (gf >= off[i + 1]) ++i;
     const IssueInfo& in = info[i];
     const int N = in.N, rows = in.rows, arr_elems = rows * N;
-    const int j = g - off[i];
+    const int j = gf - off[i];
     int zp = in.dir > 0 ? in.z0 - 1 + j : in.z0 + in.nz - j;
     zp = zp < 0 ? zp + N : (zp >= N ? zp - N : zp);
     // rows ylo-1 .. ylo+rows-2 of the plane, periodic in y: r1 rows from y1, then
@@ -311,6 +317,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
 
   for (int pass = 0; pass < P.npass; ++pass) {
     parity = P.parity ^ (pass & 1);
+    rev = parity != 0;
     gbase = pass * ptot;
     if (warp == 0) {
       int go = 0;
@@ -341,8 +348,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       lg[4] = __ldcg(&S0->a);
     }
 
-    for (int i = 0; i < ns; ++i) {
-      const Seg sg = P.segs[sb + i];
+    for (int ii = 0; ii < ns; ++ii) {
+      const int i = rev ? ns - 1 - ii : ii;
+      Seg sg = P.segs[sb + i];
+      // the last segment of a run on a lattice, in this pass's order
+      const bool run_end = rev ? (i == 0 || P.segs[sb + i - 1].lat != sg.lat) : sg.flush != 0;
+      if (rev) sg.dir = -sg.dir;
       const LatConst& L = P.lat[sg.lat];
       const int N = L.N, BY = L.BY, TX = N / VX;
       const int tx = tid % TX, ty = tid / TX;
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       const int y = sg.ytile * BY + ty;
       const int arr_elems = (BY + 2) * N;
       const long long NN = (long long)N * N;
-      const int g0 = off[i];
+      const int g0 = rev ? ptot - off[i + 1] : off[i];
       // coefficients of the segment: FP64 products formed by one lane (the
       // FP64 pipe is narrow) and broadcast in the storage precision
       T cf[3];
@@ -515,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       release(g0 + sg.nz + 1, s_cur);
       advance(s_cur, p_cur);
 
-      if (!sg.flush) continue;
+      if (!run_end) continue;
 
       // ---- end of this CTA's run on the lattice: flush the sums into its slot ----
       // (two halves of red[] alternate: a warp can reach the next flush while
