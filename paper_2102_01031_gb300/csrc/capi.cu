@@ -19,6 +19,7 @@
 
 #include "cl.h"
 #include "common.cuh"
+#include "worklist.h"
 
 namespace clg {
 
@@ -442,153 +443,6 @@ cl_status check_status(cl_ctx* c) {
     if (h[l].status == CL_ETIMEOUT)
       return fail(c, CL_ETIMEOUT, "a bounded device wait timed out (lattice %d)", l);
   return CL_OK;
-}
-
-// Work list.  The plane tasks of all lattices (lattice-major, then y-tile,
-// then z; a task is BY rows x N sites of one plane) are cut into `grid`
-// contiguous runs of equal cost, one per CTA (a task costs its sites, but at
-// least a whole CTA's worth: a tile of a small lattice leaves threads idle
-// and takes about as long as a full one); a run is split into
-// segments at y-tile and lattice boundaries.  Odd CTAs march down (and take
-// their segments in reverse order) so that neighbouring runs reach their
-// shared boundary plane at the same time, when halo planes come from L2
-// (unless up_only: the U(1) pass carries values from the plane below).
-// Each CTA accumulates one partial-sum slot per lattice it touches; slots are
-// numbered lattice-major so that a lattice's slots are contiguous.
-struct LatTiles {
-  int N, BY;
-  int min_sites;  // a plane task costs at least this many sites (a task runs one CTA however few of its threads work)
-};
-
-// Segments of the plane tasks [b, e) of lattice l (tasks numbered y-tile-major,
-// then z; a segment ends at a y-tile boundary), appended in march order.
-void append_run(const std::vector<LatTiles>& lats, const std::vector<long long>& toff, long long b,
-                long long e, int dir, std::vector<Seg>& segs) {
-  const size_t first = segs.size();
-  size_t l = 0;
-  for (long long t = b; t < e;) {
-    while (t >= toff[l + 1]) ++l;
-    const int N = lats[l].N;
-    const long long u = t - toff[l];
-    const int yt = (int)(u / N), z = (int)(u % N);
-    const int len = (int)std::min<long long>(e - t, N - z);
-    Seg sg;
-    sg.lat = (int)l;
-    sg.ytile = yt;
-    sg.z0 = z;
-    sg.nz = len;
-    sg.dir = dir;
-    sg.slot = -1;
-    sg.flush = 0;
-    sg.pad = 0;
-    segs.push_back(sg);
-    t += len;
-  }
-  if (dir < 0) std::reverse(segs.begin() + first, segs.end());
-}
-
-// Single lattice, block-aligned split: z is cut into nb blocks of Zb planes
-// (Zb = one CTA's share), and CTA (block, y-tile) marches its tile through
-// the block; every CTA of a block starts on the same plane in the same
-// direction, so the y-halo rows a CTA reads are the boundary rows its
-// y-neighbours load at about the same time and come from L2.  Directions
-// alternate by block so that the CTAs on both sides of a block boundary
-// reach it together.  The planes left above the last block go, y-tile-major,
-// to the remaining CTAs.  Returns false where the shape does not fit (then
-// the cost-weighted split is used).
-bool aligned_split(const LatTiles& L, int grid, std::vector<Seg>& segs, std::vector<int>& cta_first) {
-  const int N = L.N, YT = N / L.BY;
-  if (YT < 2 || L.BY * N < L.min_sites) return false;
-  const long long nt = (long long)YT * N;
-  const int Zb = (int)((nt + grid - 1) / grid);
-  const int nb = std::min(grid / YT, N / Zb);
-  const int rest = grid - nb * YT, left = N - nb * Zb;
-  if (nb < 1 || (rest > 0) != (left > 0)) return false;
-  const std::vector<LatTiles> one = {L};
-  const std::vector<long long> toff = {0, nt};
-  segs.clear();
-  cta_first.assign(grid + 1, 0);
-  for (int cta = 0; cta < nb * YT; ++cta) {
-    const int blk = cta / YT, yt = cta % YT;
-    cta_first[cta] = (int)segs.size();
-    const long long b = (long long)yt * N + (long long)blk * Zb;
-    append_run(one, toff, b, b + Zb, (blk & 1) ? -1 : +1, segs);
-  }
-  const long long nleft = (long long)YT * left;
-  const int dir = (nb & 1) ? -1 : +1;
-  for (int c = 0; c < rest; ++c) {
-    const int cta = nb * YT + c;
-    cta_first[cta] = (int)segs.size();
-    const long long b = nleft * c / rest, e = nleft * (c + 1) / rest;
-    const size_t first = segs.size();
-    for (long long u = b; u < e;) {  // u = y-tile * left + dz
-      const long long yt = u / left, dz = u % left;
-      const long long len = std::min<long long>(e - u, left - dz);
-      const long long t = yt * N + (long long)nb * Zb + dz;
-      append_run(one, toff, t, t + len, +1, segs);
-      segs.back().dir = dir;
-      u += len;
-    }
-    if (dir < 0) std::reverse(segs.begin() + first, segs.end());
-  }
-  return true;
-}
-
-bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_only, std::vector<Seg>& segs,
-                    std::vector<int>& cta_first, std::vector<int>& slot_begin,
-                    std::vector<int>& slot_end) {
-  const size_t nl = lats.size();
-  std::vector<long long> toff(nl + 1, 0);
-  std::vector<double> coff(nl + 1, 0.0);  // sites before each lattice
-  for (size_t l = 0; l < nl; ++l) {
-    const long long nt = (long long)(lats[l].N / lats[l].BY) * lats[l].N;
-    toff[l + 1] = toff[l] + nt;
-    coff[l + 1] = coff[l] + (double)nt * std::max(lats[l].BY * lats[l].N, lats[l].min_sites);
-  }
-  // first task of CTA k: where the running site count reaches k/grid of the total
-  auto boundary = [&](int k) -> long long {
-    if (k <= 0) return 0;
-    if (k >= grid) return toff[nl];
-    const double target = coff[nl] * (double)k / (double)grid;
-    size_t l = 0;
-    while (l + 1 < nl && coff[l + 1] <= target) ++l;
-    const double per = (double)std::max(lats[l].BY * lats[l].N, lats[l].min_sites);
-    const long long t = toff[l] + (long long)std::llround((target - coff[l]) / per);
-    return std::min(std::max(t, toff[l]), toff[l + 1]);
-  };
-  if (!(nl == 1 && !up_only && aligned_split(lats[0], grid, segs, cta_first))) {
-    segs.clear();
-    cta_first.assign(grid + 1, 0);
-    for (int cta = 0; cta < grid; ++cta) {
-      const long long b = boundary(cta), e = std::max(b, boundary(cta + 1));
-      cta_first[cta] = (int)segs.size();
-      append_run(lats, toff, b, e, (cta & 1) && !up_only ? -1 : +1, segs);
-    }
-  }
-  for (int cta = 0; cta < grid; ++cta) {
-    const int end = cta + 1 < grid ? cta_first[cta + 1] : (int)segs.size();
-    if (end - cta_first[cta] > MAX_SEG_PER_CTA) return false;
-    for (int i = cta_first[cta]; i < end; ++i)
-      segs[i].flush = (i + 1 == end || segs[i + 1].lat != segs[i].lat) ? 1 : 0;
-  }
-  cta_first[grid] = (int)segs.size();
-  slot_begin.assign(nl, 0);
-  slot_end.assign(nl, 0);
-  int next = 0;
-  for (size_t l = 0; l < nl; ++l) {
-    slot_begin[l] = next;
-    for (int cta = 0; cta < grid; ++cta) {
-      bool used = false;
-      for (int i = cta_first[cta]; i < cta_first[cta + 1]; ++i)
-        if (segs[i].lat == (int)l) {
-          segs[i].slot = next;
-          used = true;
-        }
-      if (used) ++next;
-    }
-    slot_end[l] = next;
-  }
-  return true;
 }
 
 }  // namespace

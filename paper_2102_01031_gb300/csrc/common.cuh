@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "worklist.h"  // Seg, MAX_SEG_PER_CTA
+
 #include "cl.h"
 
 namespace clg {
@@ -51,14 +53,6 @@ struct LatScalars {
   int status, pad;
 };
 
-// One work segment: planes [z0, z0+nz) of y-tile `ytile` of lattice `lat`,
-// marched in direction dir (+1 up, -1 down).  Consecutive segments of one CTA
-// on one lattice accumulate into partial-sum slot `slot`; `flush` marks the
-// last segment of such a run.
-struct Seg {
-  int lat, ytile, z0, nz, dir, slot, flush, pad;
-};
-constexpr int MAX_SEG_PER_CTA = 64;
 
 // Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
 constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
