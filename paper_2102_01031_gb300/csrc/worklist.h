@@ -67,7 +67,7 @@ inline void append_run(const std::vector<LatTiles>& lats, const std::vector<long
 // starts on the same plane in the same direction, so the y-halo rows a CTA
 // reads are boundary rows its y-neighbours load at about the same time and
 // come from L2.  Directions alternate by block so that the CTAs on both sides
-// of a block boundary reach it together.  The planes left above the last
+// of a block boundary reach it together (all up for an up-only pass).  The planes left above the last
 // block go, y-tile-major, to the remaining CTAs in runs of equal cost.  The
 // block heights (Zb for interior tiles, Zw for the two wrap tiles, whose
 // blocks then drift by a few planes) are chosen to minimise the largest
@@ -118,7 +118,8 @@ inline bool aligned_plan(const LatTiles& L, int grid, AlignedPlan& best) {
   return found;
 }
 
-inline bool aligned_split(const LatTiles& L, int grid, std::vector<Seg>& segs, std::vector<int>& cta_first) {
+inline bool aligned_split(const LatTiles& L, int grid, bool up_only, std::vector<Seg>& segs,
+                          std::vector<int>& cta_first) {
   AlignedPlan A;
   if (!aligned_plan(L, grid, A)) return false;
   const int N = L.N, YT = N / L.BY;
@@ -132,7 +133,7 @@ inline bool aligned_split(const LatTiles& L, int grid, std::vector<Seg>& segs, s
     const int Z = wrap(yt) ? A.Zw : A.Zb;
     cta_first[cta] = (int)segs.size();
     const long long b = (long long)yt * N + (long long)blk * Z;
-    append_run(one, toff, b, b + Z, (blk & 1) ? -1 : +1, segs);
+    append_run(one, toff, b, b + Z, (blk & 1) && !up_only ? -1 : +1, segs);
   }
   // leftover planes: tile t keeps [nb Z_t, N); runs of equal cost
   std::vector<double> cpre(YT + 1, 0.0);
@@ -150,7 +151,7 @@ inline bool aligned_split(const LatTiles& L, int grid, std::vector<Seg>& segs, s
     const int k = (int)std::llround((c - cpre[t]) / w);
     return {t, std::min(k, N - lstart[t])};
   };
-  const int dir = (A.nb & 1) ? -1 : +1;
+  const int dir = (A.nb & 1) && !up_only ? -1 : +1;
   for (int c = 0; c < A.rest; ++c) {
     const int cta = A.nb * YT + c;
     cta_first[cta] = (int)segs.size();
@@ -170,7 +171,7 @@ inline bool aligned_split(const LatTiles& L, int grid, std::vector<Seg>& segs, s
 }
 
 // The work list of a pass over `lats` on `grid` CTAs: the block-aligned split
-// for a single lattice (unless up_only), else contiguous runs of equal cost
+// for a single lattice, else contiguous runs of equal cost
 // (a task costs its sites, but at least a whole CTA's worth: a tile of a small
 // lattice leaves threads idle and takes about as long as a full one), split
 // into segments at y-tile and lattice boundaries; odd CTAs march down (and
@@ -201,7 +202,7 @@ inline bool build_worklist(const std::vector<LatTiles>& lats, int grid, bool up_
     const long long t = toff[l] + (long long)std::llround((target - coff[l]) / per);
     return std::min(std::max(t, toff[l]), toff[l + 1]);
   };
-  if (!(nl == 1 && !up_only && aligned_split(lats[0], grid, segs, cta_first))) {
+  if (!(nl == 1 && aligned_split(lats[0], grid, up_only, segs, cta_first))) {
     segs.clear();
     cta_first.assign(grid + 1, 0);
     for (int cta = 0; cta < grid; ++cta) {
