@@ -207,6 +207,21 @@ cl_status cl_lattice_scalars(cl_ctx* ctx, int lat, double* eta, double* a, doubl
  * (rows of one CTA tile) and the context's number of ring stages. */
 cl_status cl_lattice_tile(cl_ctx* ctx, int lat, int* N, int* BY, int* stages);
 
+/* Lattice occupation number of scalar field `field` (eq. OccuppationNum, with
+ * the spectrum outputs of Sec. 5.3) per bin of cl_spectrum's shells:
+ *   n_b = a^2 L^3/(2 N^6) (f_s/omega_s)^2 [ w_b <|phi_k|^2>_b
+ *                                          + a^{2(1-alpha)}/w_b <|phi'_k + (a'/a) phi_k|^2>_b ],
+ * <.>_b the mean over the bin's modes (k != 0), phi_k the forward DFT of the
+ * field, phi' = a^{alpha-3} pi, L = N dx, w_b^2 = k_b^2 + a^2 <d^2V/dphi^2>
+ * (k_b the bin's k, the volume average of the field's diagonal Hessian
+ * element at the synchronised state).  fo2 = (f_s/omega_s)^2, the square of
+ * the field over the frequency scale of the program units; fo2 <= 0 takes
+ * 1/fluct_amp2 (the IC amplitude parameter is (omega_s/f_s)^2).  k and mult as
+ * cl_spectrum; n_b is NaN where w_b^2 <= 0.  Single scalar lattices only
+ * (CL_EUNSUPPORTED otherwise).  Synchronises the stream. */
+cl_status cl_occupation(cl_ctx* ctx, int field, double dk_bin, double fo2, double* k, double* n,
+                        int64_t* mult, int cap, int* nbins);
+
 /* Ensemble-averaged binned spectrum: delta_b of cl_spectrum averaged over
  * the lattices lats[0 .. nl) (which must share N and kIR); k and mult as in
  * cl_spectrum (identical for those lattices).  Synchronises the stream. */

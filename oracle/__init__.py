@@ -107,6 +107,9 @@ def lib():
             L.clo_spectrum.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
+            L.clo_occupation.argtypes = [c_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]
             L.clo_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
             L.clo_philox4x32_10.restype = None
             L.clo_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -230,6 +233,22 @@ class Oracle:
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
+
+    def occupation(self, field, dk_bin=1.0, fo2=None):
+        """(k, n_k, multiplicity) per bin: lattice occupation number of scalar field
+        `field`; fo2 = (f*/omega*)^2, by default 1/fluct_amp2."""
+        if fo2 is None:
+            fo2 = 1.0 / self.params.fluct_amp2
+        cap = 4096
+        k, nk = np.zeros(cap), np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.clo_occupation(self.h, field, dk_bin, fo2, _dp(k), _dp(nk),
+                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        if rc != 0:
+            raise ValueError("clo_occupation failed (%d)" % rc)
+        n = nb.value
+        return k[:n].copy(), nk[:n].copy(), m[:n].copy()
 
     def adjoint(self, nsteps, objective=0, field=1, what=0, dk_bin=1.0, bin=1, scale=False):
         """Discrete adjoint: (J, dJ/dq, lam) with lam[f][w] = dJ/d(field f, what w) at

@@ -915,6 +915,63 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
   return 0;
 }
 
+// Lattice occupation number of a scalar field (eq. OccuppationNum, in the
+// outputs of the scalar-field module): per bin b of clo_spectrum's shells,
+//   n_b = a^2 L^3/(2 N^6) (f*/omega*)^2 [ w_b <|phi_k|^2>_b + a^{2(1-alpha)}/w_b <|phi'_k + (a'/a) phi_k|^2>_b ]
+// with <.>_b the mean over the bin's modes (k != 0), phi_k the forward DFT of
+// the field, phi' = a^{alpha-3} pi, L = N dx and w_b^2 = k_b^2 + a^2 <V_{,ff}>
+// (k_b = kIR times the bin's mean |n|; <V_{,ff}> the volume average of the
+// field's diagonal Hessian element).  fo2 = (f*/omega*)^2.
+// reading: w is taken at the bin's k, as the formula writes it outside the
+// shell average; bins with w_b^2 <= 0 are NaN.
+int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, double* k, double* n,
+                   int64_t* mult, int cap, int* nbins) {
+  if (!c || !(dk_bin > 0.0) || !(fo2 > 0.0) || c->gauge() || field < 0 || field >= c->nf) return -1;
+  const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  if (nbins) *nbins = nb;
+  if (nb > cap) return -2;
+  const double V = (double)c->V, a = c->a, H = c->b / c->a, al = c->alpha;
+  double m2 = 0.0;
+  for (long s = 0; s < c->V; ++s) {
+    double f[2] = {0.0, 0.0};
+    for (int q = 0; q < c->nf; ++q) f[q] = c->phi[q][s];
+    m2 += mass2(c, f, field);
+  }
+  m2 /= V;
+  std::vector<cplx> P(c->V), G(c->V);
+  const double apm = std::pow(a, al - 3.0);
+  for (long s = 0; s < c->V; ++s) {
+    P[s] = cplx(c->phi[field][s], 0.0);
+    G[s] = cplx(apm * c->pi[field][s] + H * c->phi[field][s], 0.0);
+  }
+  fft3d(P, c->N, -1);
+  fft3d(G, c->N, -1);
+  std::vector<double> s1(nb, 0.0), s2(nb, 0.0), sn(nb, 0.0);
+  std::vector<int64_t> cnt(nb, 0);
+  for (long idx = 1; idx < c->V; ++idx) {
+    const double nn = mode_k(c, idx) / c->kIR;
+    int b = (int)std::floor(nn / dk_bin);
+    if (b >= nb) b = nb - 1;
+    s1[b] += std::norm(P[idx]);
+    s2[b] += std::norm(G[idx]);
+    sn[b] += nn;
+    cnt[b] += 1;
+  }
+  const double L = c->N * c->dx, C = a * a * L * L * L / (2.0 * V * V) * fo2;
+  const double a2p = std::pow(a, 2.0 * (1.0 - al));
+  for (int b = 0; b < nb; ++b) {
+    if (cnt[b] == 0) { k[b] = 0.0; n[b] = 0.0; mult[b] = 0; continue; }
+    const double kb = c->kIR * sn[b] / (double)cnt[b];
+    const double w2 = kb * kb + a * a * m2;
+    k[b] = kb;
+    mult[b] = cnt[b];
+    if (!(w2 > 0.0)) { n[b] = std::nan(""); continue; }
+    const double w = std::sqrt(w2);
+    n[b] = C * (w * s1[b] / (double)cnt[b] + a2p * s2[b] / ((double)cnt[b] * w));
+  }
+  return 0;
+}
+
 }  // extern "C"
 
 // ===========================================================================

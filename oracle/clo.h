@@ -81,6 +81,12 @@ int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double*
                          double* max_abs);
 int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
                  double* delta, int64_t* mult, int cap, int* nbins);
+/* Lattice occupation number n_b of scalar field `field` per spectrum bin
+ * (eq. OccuppationNum); fo2 = (f_s/omega_s)^2, the square of the field and frequency
+ * scales of the program units.  k and mult as clo_spectrum;
+ * NaN where omega_b^2 <= 0.  -1 for U(1) or bad arguments, -2 if cap < nbins. */
+int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, double* k, double* n,
+                   int64_t* mult, int cap, int* nbins);
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out);
 

@@ -34,7 +34,7 @@ EXPORTS = (
     "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
-    "cl_adjoint", "cl_ic_amplitude_grad",
+    "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -149,6 +149,8 @@ def lib():
                                        i64p, ip, ctypes.POINTER(ctypes.c_int)]
     L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
+    L.cl_occupation.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp,
+                                ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -278,6 +280,19 @@ class Lattice:
         _check(self.L, self.h, rc, "cl_spectrum")
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
+
+    def occupation(self, field, dk_bin=1.0, fo2=0.0):
+        """cl_occupation: (k, n_k, multiplicity) per bin, lattice occupation number of
+        scalar field `field`; fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2)."""
+        cap = 4096
+        k, nk = np.zeros(cap), np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.cl_occupation(self.h, field, dk_bin, fo2, _dp(k), _dp(nk),
+                                  m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_occupation")
+        n = nb.value
+        return k[:n].copy(), nk[:n].copy(), m[:n].copy()
 
     def state_bytes(self):
         n = ctypes.c_size_t()

@@ -36,7 +36,9 @@ cudaError_t launch_ic_assemble(int, void*, void*, const double2*, const double2*
 cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
 cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
 cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
-                        cudaStream_t);
+                        cudaStream_t, int raw = 0);
+cudaError_t launch_combine_to_complex(int, const void*, double, const void*, double, double2*, long long,
+                                      cudaStream_t);
 cudaError_t launch_spec_mean(const double*, int, int, double*, cudaStream_t);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
 cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
@@ -1058,6 +1060,80 @@ cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, 
                       int64_t* mult, int cap, int* nbins) {
   const int l0 = 0;
   return cl_ensemble_spectrum(c, &l0, 1, field, what, dk_bin, k, delta, mult, cap, nbins);
+}
+
+cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double* k, double* n, int64_t* mult,
+                        int cap, int* nbins) {
+  if (!c || !k || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+    return fail(c, CL_EUNSUPPORTED, "occupation numbers cover single scalar lattices");
+  if (field < 0 || field >= c->nf) return fail(c, CL_EINVAL, "field %d out of range", field);
+  if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
+  if (!(fo2 > 0.0)) {
+    if (!(c->p.fluct_amp2 > 0.0)) return fail(c, CL_EINVAL, "need (f*/omega*)^2 > 0 (fluct_amp2 is 0)");
+    fo2 = 1.0 / c->p.fluct_amp2;
+  }
+  const LatHost& H = c->lats[0];
+  const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
+  *nbins = nb;
+  if (nb > cap) return fail(c, CL_EINVAL, "cap %d < %d bins", cap, nb);
+  if (nb > 2048) return fail(c, CL_EINVAL, "too many bins (dk_bin too small)");
+  cl_status s = measure(c, 0);  // the synchronised state and its volume averages
+  if (s != CL_OK) return s;
+  LatScalars S;
+  CU(cudaMemcpyAsync(&S, &c->d_sc[0], sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  const int nblk = 2 * c->nsm;
+  if (c->spec_lats < 1) {
+    CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_spec);
+    c->d_spec = nullptr;
+    CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + (size_t)2 * 3 * 2048) * sizeof(double)));
+    c->spec_lats = 1;
+  }
+  double* part = c->d_spec;
+  double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [2][3 nb]: k, shell sum, mult
+  double2* F = c->d_cplx;
+  CU(cudaStreamSynchronize(c->stream));
+  const double a = S.a, Hc = S.b / S.a, al = c->alpha;
+  const void* phi = arr_ptr(c, 0, c->parity, 2 * field);
+  const void* pi = arr_ptr(c, 0, c->parity, 2 * field + 1);
+  // |phi_k|^2, then |phi'_k + (a'/a) phi_k|^2 with phi' = a^{alpha-3} pi, binned
+  for (int r = 0; r < 2; ++r) {
+    if (r == 0) CU(launch_to_complex(c->fp32, phi, F, H.V, c->stream));
+    else CU(launch_combine_to_complex(c->fp32, pi, std::pow(a, al - 3.0), phi, Hc, F, H.V, c->stream));
+    ++c->launches;
+    s = fft3d(c, H.N, F, -1);
+    if (s != CL_OK) return s;
+    CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins + (size_t)r * 3 * nb, c->stream, 1));
+    c->launches += 2;
+  }
+  std::vector<double> h(6 * nb);
+  CU(cudaMemcpyAsync(h.data(), bins, 6 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  // volume average of the field's diagonal Hessian element (eq. PotNat), from the measured <phi_g^2>
+  const double* p2 = S.obs.mean_phi2;
+  double m2 = 0.0;
+  if (c->model == CL_MODEL_LPHI4) m2 = 3.0 * p2[0];
+  else m2 = field == 0 ? 3.0 * p2[0] + c->p.q * p2[1] : c->p.q * p2[0];
+  const double V = (double)H.V, L = H.N * H.dx;
+  const double C = a * a * L * L * L / (2.0 * V * V) * fo2, a2p = std::pow(a, 2.0 * (1.0 - al));
+  for (int b = 0; b < nb; ++b) {
+    const double cnt = h[2 * nb + b];
+    k[b] = h[b];
+    mult[b] = (int64_t)cnt;
+    if (cnt == 0.0) {
+      n[b] = 0.0;
+      continue;
+    }
+    const double w2 = h[b] * h[b] + a * a * m2;
+    if (!(w2 > 0.0)) {
+      n[b] = std::nan("");
+      continue;
+    }
+    const double w = std::sqrt(w2);
+    n[b] = C * (w * h[nb + b] / cnt + a2p * h[3 * nb + nb + b] / (cnt * w));
+  }
+  return check_status(c);
 }
 
 cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,

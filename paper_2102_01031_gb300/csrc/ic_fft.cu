@@ -344,6 +344,14 @@ __global__ void to_complex_kernel(const T* f, double2* out, long long V) {
 template __global__ void to_complex_kernel<float>(const float*, double2*, long long);
 template __global__ void to_complex_kernel<double>(const double*, double2*, long long);
 
+// out = cx x + cy y (FP64), imaginary part 0.
+template <typename T>
+__global__ void combine_to_complex_kernel(const T* x, double cx, const T* y, double cy, double2* out, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x)
+    out[n] = make_double2(cx * (double)x[n] + cy * (double)y[n], 0.0);
+}
+
 // Shell binning of |F(n)|^2, bins b = floor(|n|/dk) over n != 0.  Each block
 // accumulates in shared memory and writes its own partial row (3 x nb).
 __global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, double* part) {
@@ -371,9 +379,10 @@ __global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, d
   for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 3 * nb + i] = sb[i];
 }
 
-// Sum the block rows in a fixed order and form eq. discretePS per bin.
+// Sum the block rows in a fixed order and form eq. discretePS per bin (raw:
+// the shell sum of |F|^2 instead of delta_b).
 __global__ void bin_final_kernel(const double* part, int nblk, int nb, double kIR, double dx, int N,
-                                 double* k, double* delta, double* mult) {
+                                 double* k, double* delta, double* mult, int raw) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   double sp = 0.0, sn = 0.0, sc = 0.0;
@@ -394,7 +403,7 @@ __global__ void bin_final_kernel(const double* part, int nblk, int nb, double kI
   const double fac = pow(dx / (double)N, 3.0);
   const double pi = 3.14159265358979323846;
   k[b] = kb;
-  delta[b] = kb * kb * kb / (2.0 * pi * pi) * fac * sp / (4.0 * pi * nbar * nbar);
+  delta[b] = raw ? sp : kb * kb * kb / (2.0 * pi * pi) * fac * sp / (4.0 * pi * nbar * nbar);
   mult[b] = sc;
 }
 
@@ -484,11 +493,23 @@ cudaError_t launch_ic_amp_grad(const double2* Lf, const double2* Lp, double* out
 }
 
 cudaError_t launch_bins(const double2* F, int N, double dk, int nb, int nblk, double* part,
-                        double kIR, double dx, double* out, cudaStream_t st) {
+                        double kIR, double dx, double* out, cudaStream_t st, int raw) {
   bin_partial_kernel<<<nblk, 256, 3 * nb * sizeof(double), st>>>(F, N, dk, nb, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  bin_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, kIR, dx, N, out, out + nb, out + 2 * nb);
+  bin_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, kIR, dx, N, out, out + nb, out + 2 * nb,
+                                                     raw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_to_complex(int fp32, const void* x, double cx, const void* y, double cy, double2* out,
+                                      long long V, cudaStream_t st) {
+  const int tb = 256;
+  if (fp32)
+    combine_to_complex_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const float*)x, cx, (const float*)y, cy, out, V);
+  else
+    combine_to_complex_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)x, cx, (const double*)y, cy,
+                                                                       out, V);
   return cudaGetLastError();
 }
 

@@ -193,6 +193,54 @@ def test_spectra_match(P):
                 assert np.abs(dg - do).max() < 1e-9 * np.abs(do).max()
 
 
+@pytest.mark.parametrize("alpha", [1.0, 0.5])
+def test_occupation_number_matches(P, alpha):
+    """cl_occupation against the oracle on the same synchronised state, with
+    self-consistent expansion (a != 1, a' != 0), both fields, two bin widths."""
+    kw = dict(C2S, expansion=O.EXP_SELF, fstar_over_mp=2.0)
+    g, o = both(P, O.MODEL_LPHI4_CHI, 32, 0.5, alpha, 9, **kw)
+    g.step(40)
+    for f in range(2):
+        for w in (0, 1):
+            o.set(f, w, g.get(f, w))
+    o.set_scalars(*g.scalars())
+    assert g.scalars()[1] > 1.05
+    for f in range(2):
+        for dk in (1.0, 1.5):
+            kg, ng, mg = g.occupation(f, dk)
+            ko, no, mo = o.occupation(f, dk)
+            assert np.array_equal(mg, mo)
+            assert np.abs(kg - ko).max() < 1e-12 * ko.max()
+            assert np.abs(ng - no).max() < 1e-10 * np.abs(no).max(), (f, dk)
+
+
+def test_occupation_number_fp32_and_vacuum(P):
+    """FP32 storage: at the initial conditions the vacuum gives 1/2 per mode on
+    average, and the GPU matches the oracle on the same FP32-rounded state."""
+    kw = dict(C2S, expansion=O.EXP_SELF, fstar_over_mp=2.0)
+    g, o = both(P, O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 4, precision=1, **kw)
+    for f in range(2):
+        for w in (0, 1):
+            o.set(f, w, g.get(f, w))
+    o.set_scalars(*g.scalars())
+    for f in range(2):
+        kg, ng, mg = g.occupation(f)
+        ko, no, mo = o.occupation(f)
+        assert np.array_equal(mg, mo)
+        assert np.abs(ng - no).max() < 1e-9 * np.abs(no).max()
+        assert abs(np.sum(ng * mg) / np.sum(mg) - 0.5) < 0.05
+    # an explicit (f*/omega*)^2 scales it
+    k3, n3, m3 = g.occupation(0, 1.0, fo2=3.0 / kw["fluct_amp2"])
+    k1, n1, m1 = g.occupation(0, 1.0)
+    assert np.allclose(n3, 3.0 * n1, rtol=1e-13, atol=0)
+    u = P.Lattice(O.MODEL_U1_HIGGS, 16, 0.5, 1.0, 1,
+                  P.make_params(dt=0.01, integrator=O.LF, lam=1.0, v=1.0, gQ=0.5, phi0=[1.0, 1.0],
+                                fluct_amp2=1e-2, expansion=O.EXP_OFF))
+    with pytest.raises(P.ClError) as e:
+        u.occupation(0)
+    assert e.value.status == P.CL_EUNSUPPORTED
+
+
 # ---------------------------------------------------------------------------
 # FP32 storage with FP64 reductions
 # ---------------------------------------------------------------------------
