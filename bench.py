@@ -45,7 +45,12 @@ PASSES_PER_STEP = 3
 # profiles/dk_pass_fp32_256_ncu.md (one cooperative launch of the three VV4
 # passes of a step, divided by 3), valid only for the kernel source it was
 # taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "aa18aff657dd4d41", "bytes_per_launch": 502686891}}
+NCU_TRAFFIC = {"f32": {"source_hash": "527eaa941d8a5967", "bytes_per_launch": 503718485}}
+# FP64 instructions (DFMA, DADD, DMUL) and operations (FMA = 2) per site per pass
+# of the FP64 plain kernel, from one ncu capture of the sass instruction counters
+# (profiles/dk_pass_fp64_256_ncu.md)
+NCU_FP64_OPS = {"source_hash": "527eaa941d8a5967", "instructions_per_site_pass": 46.443,
+                "flops_per_site_pass": 60.811}
 
 
 def peaks():
@@ -58,11 +63,21 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the scalar pass kernel, its headers and the work split (what
+    decides the pass's DRAM traffic and FP64 operation count)."""
     h = hashlib.sha256()
-    for name in ("pass_scalar.cu", "common.cuh", "tail.cuh", "capi.cu"):
+    for name in ("pass_scalar.cu", "common.cuh", "tail.cuh", "worklist.h"):
         with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def ncu_fp64_ops():
+    """(FP64 instructions, FP64 operations) per site-pass of the FP64 plain kernel
+    from the last ncu capture, or (None, None) if the kernel source changed since."""
+    if NCU_FP64_OPS["source_hash"] != kernel_source_hash():
+        return None, None
+    return NCU_FP64_OPS["instructions_per_site_pass"], NCU_FP64_OPS["flops_per_site_pass"]
 
 
 def ncu_traffic(prec):
@@ -287,6 +302,11 @@ def run_ours(args):
     bpl64 = PASS_BYTES_PER_SITE["f64"] * sites
     achieved64 = bpl64 / (f64["pass_ms"] * 1e-3) / 1e9
     traffic = ncu_traffic("f32")
+    # the FP64 plain pass is bound by the FP64 pipe: roof = the measured FMA
+    # instruction rate (an FMA, an add and a multiply each take one issue slot)
+    fp64_rate = P.measure_fp64_rate(stream)
+    ins64, ops64 = ncu_fp64_ops()
+    ins_rate = None if ins64 is None else ins64 * sites / (f64["pass_ms"] * 1e-3)
     others = other_workloads(P, torch, stream, peak) if not args.no_extra else None
     budget = float(args.cpu_budget)
     L, n_ref, csteps = cpu_oracle_rate(budget)
@@ -318,7 +338,16 @@ def run_ours(args):
         "fp64_plain": {"value": v64, "unit": "site-updates/s", "steps": f64["steps"],
                        "ms_per_step": f64["ms"] / f64["steps"], "achieved_gbs": achieved64,
                        "frac_hbm": achieved64 / peak, "avg_launch_ms": f64["pass_ms"],
-                       "fp32_speedup": value / v64},
+                       "fp32_speedup": value / v64,
+                       "roofline": {"bound": "alu", "kernel": "dk_pass_scalar<double,2,1>",
+                                    "achieved": None if ins_rate is None else ins_rate / 1e9,
+                                    "peak": fp64_rate / 2 / 1e9, "unit": "G FP64 instructions/s",
+                                    "frac": None if ins_rate is None else ins_rate / (fp64_rate / 2),
+                                    "fp64_instructions_per_site_pass": ins64,
+                                    "fp64_flops_per_site_pass": ops64,
+                                    "measured_fp64_tflops": fp64_rate / 1e12,
+                                    "peak_kind": "measured: cl_measure_fp64_rate (independent FMA chains), "
+                                                 "FMA instructions per second"}},
         "sanity": {"rho_f32": f32["rho"], "rho_f64": f64["rho"], "a_f32": f32["a"],
                    "nonfinite": f32["nonfinite"] + f64["nonfinite"]},
         "other_rows": others,
@@ -414,6 +443,11 @@ def profile_case(name):
         lat = P.Lattice(P.MODEL_U1_HIGGS, 128, 0.2, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
         for _ in range(4):
             lat.step(1)
+    elif name == "scalar256_fp64":   # the FP64 plain pass: one cooperative launch of a VV4 step
+        lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
+                        P.make_params(precision=P.FP64, stream=stream, **PARAMS))
+        lat.step(1)
+        print("fp64 rate %.4g FLOP/s" % P.measure_fp64_rate(stream))
     elif name in ("adj128", "adj128self"):    # adjoint sweep of 4 VV4 steps at 128^3
         exp = P.EXP_OFF if name == "adj128" else P.EXP_SELF
         lat = P.Lattice(P.MODEL_LPHI4_CHI, 128, 0.2, ALPHA, SEED,
@@ -440,7 +474,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "u1_128", "adj128", "adj128self"),
+    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "adj128", "adj128self"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -222,6 +222,13 @@ cl_status cl_lattice_tile(cl_ctx* ctx, int lat, int* N, int* BY, int* stages);
 cl_status cl_occupation(cl_ctx* ctx, int field, double dk_bin, double fo2, double* k, double* n,
                         int64_t* mult, int cap, int* nbins);
 
+/* Measured FP64 rate of the current device (FMA counted as two operations):
+ * a full grid of independent FMA chains timed with CUDA events on `stream`
+ * (a cudaStream_t, NULL = default), best of three after a warm-up.  The roof
+ * of the FP64 plain pass, which is bound by FP64 arithmetic.  Needs no
+ * context; returns CL_ECUDA / CL_ENOMEM on failure. */
+cl_status cl_measure_fp64_rate(void* stream, double* flops_per_s);
+
 /* Ensemble-averaged binned spectrum: delta_b of cl_spectrum averaged over
  * the lattices lats[0 .. nl) (which must share N and kIR); k and mult as in
  * cl_spectrum (identical for those lattices).  Synchronises the stream. */

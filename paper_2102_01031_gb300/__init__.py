@@ -34,7 +34,7 @@ EXPORTS = (
     "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
-    "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation",
+    "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -149,6 +149,7 @@ def lib():
                                        i64p, ip, ctypes.POINTER(ctypes.c_int)]
     L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
+    L.cl_measure_fp64_rate.argtypes = [vp, dp]
     L.cl_occupation.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp,
                                 ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -189,6 +190,17 @@ def make_params(**kw):
     if kw:
         raise TypeError("unknown params: %s" % sorted(kw))
     return p
+
+
+def measure_fp64_rate(stream=None):
+    """cl_measure_fp64_rate: measured FP64 operations per second of the current
+    device (FMA = 2), the roof of the FP64 plain pass."""
+    L = lib()
+    r = ctypes.c_double()
+    rc = L.cl_measure_fp64_rate(stream, ctypes.byref(r))
+    if rc != 0:
+        raise ClError(rc, "cl_measure_fp64_rate failed")
+    return r.value
 
 
 def torch_stream():
