@@ -107,6 +107,9 @@ def lib():
             L.clo_spectrum.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
+            L.clo_em_spectrum.argtypes = [c_p, ctypes.c_int, ctypes.c_double, dp, dp,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]
             L.clo_occupation.argtypes = [c_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
@@ -233,6 +236,19 @@ class Oracle:
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
+
+    def em_spectrum(self, which, dk_bin=1.0):
+        """(k, delta, multiplicity) of the U(1) electric (which=0) or magnetic (1) field."""
+        cap = 4096
+        k, d = np.zeros(cap), np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.clo_em_spectrum(self.h, which, dk_bin, _dp(k), _dp(d),
+                                    m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        if rc != 0:
+            raise ValueError("clo_em_spectrum failed (%d)" % rc)
+        n = nb.value
+        return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
     def occupation(self, field, dk_bin=1.0, fo2=None):
         """(k, n_k, multiplicity) per bin: lattice occupation number of scalar field

@@ -915,6 +915,61 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
   return 0;
 }
 
+// Spectra of the electric and magnetic fields of the U(1) model (the gauge
+// spectra of the outputs of Sec. 5.3; defined from eq. ElectricMagneticDefs):
+//   E_i = F_0i = a^{alpha-1} pi_A,i      (pi_A = a^{1-alpha} F_0i, program units)
+//   B_i = (1/2) eps_ijk F_jk,   F_jk = sin theta_jk/(gQ dx^2)
+// with the compact plaquette angle theta_jk = gQ dx^2 F_jk of the U(1) toolkit,
+// so B_x = F_yz, B_y = -F_xz, B_z = F_xy at the plaquette's corner n.  Each
+// field's spectrum is eq. discretePS with |f(k)|^2 summed over the three
+// components, on clo_spectrum's shells.  which = 0: E, 1: B.
+// reading: the manual names these outputs without a formula; the field
+// strength from the plaquette's sine is the compact form whose small-angle
+// limit is the forward-difference curl.
+int clo_em_spectrum(const clo_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult,
+                    int cap, int* nbins) {
+  if (!c || !c->gauge() || (which != 0 && which != 1) || !(dk_bin > 0.0)) return -1;
+  const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  if (nbins) *nbins = nb;
+  if (nb > cap) return -2;
+  const double gdx2 = c->p.gQ * c->dx * c->dx, ae = std::pow(c->a, c->alpha - 1.0);
+  std::vector<double> sp(nb, 0.0), sn(nb, 0.0);
+  std::vector<int64_t> cnt(nb, 0);
+  for (int comp = 0; comp < 3; ++comp) {
+    std::vector<cplx> F(c->V);
+    for (long n = 0; n < c->V; ++n) {
+      double v;
+      if (which == 0) {
+        v = ae * c->piA[comp][n];
+      } else {
+        const int j = (comp + 1) % 3, l = (comp + 2) % 3;  // B_i = F_jl for (i, j, l) cyclic
+        v = std::sin(plaq(c, n, j, l)) / gdx2;
+      }
+      F[n] = cplx(v, 0.0);
+    }
+    fft3d(F, c->N, -1);
+    for (long idx = 1; idx < c->V; ++idx) {
+      const double nn = mode_k(c, idx) / c->kIR;
+      int b = (int)std::floor(nn / dk_bin);
+      if (b >= nb) b = nb - 1;
+      sp[b] += std::norm(F[idx]);
+      if (comp == 0) {
+        sn[b] += nn;
+        cnt[b] += 1;
+      }
+    }
+  }
+  const double fac = std::pow(c->dx / (double)c->N, 3.0);
+  for (int b = 0; b < nb; ++b) {
+    if (cnt[b] == 0) { k[b] = 0.0; delta[b] = 0.0; mult[b] = 0; continue; }
+    const double nbar = sn[b] / (double)cnt[b], kb = c->kIR * nbar;
+    k[b] = kb;
+    delta[b] = kb * kb * kb / (2.0 * PI * PI) * fac * sp[b] / (4.0 * PI * nbar * nbar);
+    mult[b] = cnt[b];
+  }
+  return 0;
+}
+
 // Lattice occupation number of a scalar field (eq. OccuppationNum, in the
 // outputs of the scalar-field module): per bin b of clo_spectrum's shells,
 //   n_b = a^2 L^3/(2 N^6) (f*/omega*)^2 [ w_b <|phi_k|^2>_b + a^{2(1-alpha)}/w_b <|phi'_k + (a'/a) phi_k|^2>_b ]

@@ -81,6 +81,11 @@ int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double*
                          double* max_abs);
 int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
                  double* delta, int64_t* mult, int cap, int* nbins);
+/* U(1) model: binned spectrum of the electric (which = 0: E_i = a^{alpha-1} pi_A,i)
+ * or magnetic (which = 1: B_i = eps_ijk sin(theta_jk)/(2 gQ dx^2)) field, |.|^2
+ * summed over components, normalised as clo_spectrum.  -1 for scalar models. */
+int clo_em_spectrum(const clo_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult,
+                    int cap, int* nbins);
 /* Lattice occupation number n_b of scalar field `field` per spectrum bin
  * (eq. OccuppationNum); fo2 = (f_s/omega_s)^2, the square of the field and frequency
  * scales of the program units.  k and mult as clo_spectrum;

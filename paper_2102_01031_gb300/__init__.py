@@ -34,7 +34,7 @@ EXPORTS = (
     "cl_last_error", "cl_enable_pass_timing", "cl_pass_timing", "cl_volume_averages_noalloc",
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
-    "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate",
+    "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -150,6 +150,8 @@ def lib():
     L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
     L.cl_measure_fp64_rate.argtypes = [vp, dp]
+    L.cl_em_spectrum.argtypes = [vp, ip, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int64), ip,
+                                 ctypes.POINTER(ctypes.c_int)]
     L.cl_occupation.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp,
                                 ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -290,6 +292,19 @@ class Lattice:
         rc = self.L.cl_spectrum(self.h, field, what, dk_bin, _dp(k), _dp(d),
                                 m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
         _check(self.L, self.h, rc, "cl_spectrum")
+        n = nb.value
+        return k[:n].copy(), d[:n].copy(), m[:n].copy()
+
+    def em_spectrum(self, which, dk_bin=1.0):
+        """cl_em_spectrum: (k, delta, multiplicity) of the U(1) electric (which=0) or
+        magnetic (which=1) field."""
+        cap = 4096
+        k, d = np.zeros(cap), np.zeros(cap)
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.cl_em_spectrum(self.h, which, dk_bin, _dp(k), _dp(d),
+                                   m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_em_spectrum")
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
 

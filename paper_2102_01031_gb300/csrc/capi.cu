@@ -39,6 +39,8 @@ cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, 
                         cudaStream_t, int raw = 0);
 cudaError_t launch_combine_to_complex(int, const void*, double, const void*, double, double2*, long long,
                                       cudaStream_t);
+cudaError_t launch_u1_plaquette_field(int, const void*, const void*, int, int, int, double, double, double2*,
+                                      cudaStream_t);
 cudaError_t launch_spec_mean(const double*, int, int, double*, cudaStream_t);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
 cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
@@ -1132,6 +1134,75 @@ cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double*
     }
     const double w = std::sqrt(w2);
     n[b] = C * (w * h[nb + b] / cnt + a2p * h[3 * nb + nb + b] / (cnt * w));
+  }
+  return check_status(c);
+}
+
+cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult, int cap,
+                         int* nbins) {
+  if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->model != CL_MODEL_U1_HIGGS || c->nlat != 1)
+    return fail(c, CL_EUNSUPPORTED, "electric and magnetic spectra need a single U(1) lattice");
+  if (which != 0 && which != 1) return fail(c, CL_EINVAL, "which must be 0 (electric) or 1 (magnetic)");
+  if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
+  const LatHost& H = c->lats[0];
+  const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
+  *nbins = nb;
+  if (nb > cap) return fail(c, CL_EINVAL, "cap %d < %d bins", cap, nb);
+  if (nb > 2048) return fail(c, CL_EINVAL, "too many bins (dk_bin too small)");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  LatScalars S;
+  CU(cudaMemcpyAsync(&S, &c->d_sc[0], sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  const int nblk = 2 * c->nsm;
+  if (c->spec_lats < 1) {
+    CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_spec);
+    c->d_spec = nullptr;
+    CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + (size_t)2 * 3 * 2048) * sizeof(double)));
+    c->spec_lats = 1;
+  }
+  double* part = c->d_spec;
+  double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [3 nb]: k, shell sum, mult
+  double2* F = c->d_cplx;
+  CU(cudaStreamSynchronize(c->stream));
+  const double gd = c->p.gQ * H.dx, inv_gdx2 = 1.0 / (c->p.gQ * H.dx * H.dx), ae = std::pow(S.a, c->alpha - 1.0);
+  // arrays: A_i = 4 + 2i, pi_A,i = 5 + 2i (phi_0, pi_0, phi_1, pi_1 first)
+  std::vector<double> sum(nb, 0.0), kk(nb, 0.0), cnt(nb, 0.0), h(3 * nb);
+  for (int comp = 0; comp < 3; ++comp) {
+    if (which == 0) {
+      const void* pa = arr_ptr(c, 0, c->parity, 5 + 2 * comp);
+      CU(launch_combine_to_complex(c->fp32, pa, ae, pa, 0.0, F, H.V, c->stream));
+    } else {  // B_i = F_jl with (i, j, l) cyclic
+      const int j = (comp + 1) % 3, l = (comp + 2) % 3;
+      CU(launch_u1_plaquette_field(c->fp32, arr_ptr(c, 0, c->parity, 4 + 2 * j), arr_ptr(c, 0, c->parity, 4 + 2 * l),
+                                   j, l, H.N, gd, inv_gdx2, F, c->stream));
+    }
+    ++c->launches;
+    s = fft3d(c, H.N, F, -1);
+    if (s != CL_OK) return s;
+    CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins, c->stream, 1));
+    c->launches += 2;
+    CU(cudaMemcpyAsync(h.data(), bins, 3 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nb; ++b) sum[b] += h[nb + b];
+    if (comp == 0)
+      for (int b = 0; b < nb; ++b) {
+        kk[b] = h[b];
+        cnt[b] = h[2 * nb + b];
+      }
+  }
+  // eq. discretePS on the summed shell sums
+  const double pi = 3.14159265358979323846, fac = std::pow(H.dx / (double)H.N, 3.0);
+  for (int b = 0; b < nb; ++b) {
+    k[b] = kk[b];
+    mult[b] = (int64_t)cnt[b];
+    if (cnt[b] == 0.0) {
+      delta[b] = 0.0;
+      continue;
+    }
+    const double nbar = kk[b] / H.kIR;
+    delta[b] = kk[b] * kk[b] * kk[b] / (2.0 * pi * pi) * fac * sum[b] / (4.0 * pi * nbar * nbar);
   }
   return check_status(c);
 }

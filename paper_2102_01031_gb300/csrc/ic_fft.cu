@@ -344,6 +344,26 @@ __global__ void to_complex_kernel(const T* f, double2* out, long long V) {
 template __global__ void to_complex_kernel<float>(const float*, double2*, long long);
 template __global__ void to_complex_kernel<double>(const double*, double2*, long long);
 
+// One component of the U(1) magnetic field, B = sin(theta_jl)/(gQ dx^2) with the
+// plaquette angle theta_jl(n) = gQ dx [A_j(n) + A_l(n+j) - A_j(n+l) - A_l(n)]
+// (directions j, l: 0 = x, 1 = y, 2 = z), in FP64, imaginary part 0.
+template <typename T>
+__global__ void u1_plaquette_field_kernel(const T* Aj, const T* Al, int j, int l, int N, double gd,
+                                          double inv_gdx2, double2* out) {
+  const long long V = (long long)N * N * N;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int c[3] = {(int)(n % N), (int)((n / N) % N), (int)(n / ((long long)N * N))};
+    auto shifted = [&](int d) -> long long {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] = cc[d] + 1 == N ? 0 : cc[d] + 1;
+      return cc[0] + (long long)N * (cc[1] + (long long)N * cc[2]);
+    };
+    const double th = gd * (((double)Aj[n] + (double)Al[shifted(j)]) - ((double)Aj[shifted(l)] + (double)Al[n]));
+    out[n] = make_double2(sin(th) * inv_gdx2, 0.0);
+  }
+}
+
 // out = cx x + cy y (FP64), imaginary part 0.
 template <typename T>
 __global__ void combine_to_complex_kernel(const T* x, double cx, const T* y, double cy, double2* out, long long V) {
@@ -499,6 +519,19 @@ cudaError_t launch_bins(const double2* F, int N, double dk, int nb, int nblk, do
   if (e != cudaSuccess) return e;
   bin_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, kIR, dx, N, out, out + nb, out + 2 * nb,
                                                      raw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_u1_plaquette_field(int fp32, const void* Aj, const void* Al, int j, int l, int N, double gd,
+                                      double inv_gdx2, double2* out, cudaStream_t st) {
+  const long long V = (long long)N * N * N;
+  const int tb = 256;
+  if (fp32)
+    u1_plaquette_field_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const float*)Aj, (const float*)Al, j, l, N,
+                                                                      gd, inv_gdx2, out);
+  else
+    u1_plaquette_field_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)Aj, (const double*)Al, j, l,
+                                                                       N, gd, inv_gdx2, out);
   return cudaGetLastError();
 }
 

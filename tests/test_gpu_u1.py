@@ -214,3 +214,28 @@ def test_errors(P):
     assert g.nfields() == NARR
     with pytest.raises(P.ClError):
         g.get(5, 0)
+
+
+@pytest.mark.parametrize("precision,alpha", [(0, 1.0), (0, 0.0), (1, 1.0)])
+def test_electric_and_magnetic_spectra_match(P, precision, alpha):
+    """cl_em_spectrum against the oracle on the same state and scalars, with
+    self-consistent expansion (a != 1 enters E through a^{alpha-1})."""
+    kw = dict(C3, expansion=O.EXP_SELF, fstar_over_mp=2.0)
+    g, o = both(P, 24, 0.5, alpha, 6, precision=precision, **kw)
+    g.step(30)
+    for f in range(NARR):
+        for w in (0, 1):
+            o.set(f, w, g.get(f, w))
+    o.set_scalars(*g.scalars())
+    assert abs(g.scalars()[1] - 1.0) > 1e-3
+    for which in (0, 1):
+        for dk in (1.0, 1.5):
+            kg, dg, mg = g.em_spectrum(which, dk)
+            ko, do, mo = o.em_spectrum(which, dk)
+            assert np.array_equal(mg, mo)
+            assert np.abs(kg - ko).max() < 1e-12 * ko.max()
+            assert np.abs(dg - do).max() < 1e-10 * np.abs(do).max(), (which, dk)
+    s = P.Lattice(O.MODEL_LPHI4, 16, 0.5, 1.0, 1, P.make_params(dt=0.01, phi0=[1.0], fluct_amp2=1e-4))
+    with pytest.raises(P.ClError) as e:
+        s.em_spectrum(0)
+    assert e.value.status == P.CL_EUNSUPPORTED
