@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS = 1, 2, 3
+MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS = 1, 2, 3, 4
 LF, VV2, VV4, VV6, VV8, VV10 = 0, 2, 4, 6, 8, 10
 EXP_OFF, EXP_SELF, EXP_FIXED = 0, 1, 2
 
@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("expansion", ctypes.c_int),
         ("b0_mode", ctypes.c_int),
         ("pad_", ctypes.c_int),
+        ("gQB", ctypes.c_double),
     ]
 
 
@@ -59,6 +60,7 @@ class Energies(ctypes.Structure):
         ("hubble_viol", ctypes.c_double), ("energy_cons", ctypes.c_double),
         ("mean_phi", ctypes.c_double * 4), ("mean_phi2", ctypes.c_double * 4),
         ("mean_pi", ctypes.c_double * 4), ("mean_pi2", ctypes.c_double * 4),
+        ("EKB", ctypes.c_double), ("EGB", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -104,6 +106,11 @@ def lib():
             L.clo_set_scalars.argtypes = [c_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.clo_nfields.argtypes = [c_p]
             L.clo_gauss_constraint.argtypes = [c_p, dp, dp, dp, dp]
+            L.clo_get_array.argtypes = [c_p, ctypes.c_int, dp]
+            L.clo_set_array.argtypes = [c_p, ctypes.c_int, dp]
+            L.clo_gauss_residual.argtypes = [c_p, ctypes.c_int, dp]
+            L.clo_su2_exp.argtypes = [dp, dp]
+            L.clo_su2_exp.restype = None
             L.clo_spectrum.argtypes = [c_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp,
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
@@ -159,6 +166,7 @@ def make_params(**kw):
     p.integrator = kw.pop("integrator", VV2)
     p.expansion = kw.pop("expansion", EXP_OFF)
     p.b0_mode = kw.pop("b0_mode", 0)
+    p.gQB = kw.pop("gQB", 0.5)
     if kw:
         raise TypeError("unknown params: %s" % sorted(kw))
     return p
@@ -206,6 +214,25 @@ class Oracle:
         a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
         if a.size != self.V or self.L.clo_set_state(self.h, field, what, _dp(a)) != 0:
             raise IndexError((field, what))
+
+    def get_array(self, a):
+        """Doublet model: array `a` in the order of clo_get_array, as [z][y][x]."""
+        out = np.empty(self.V, dtype=np.float64)
+        if self.L.clo_get_array(self.h, a, _dp(out)) != 0:
+            raise IndexError(a)
+        return out.reshape(self.N, self.N, self.N)
+
+    def set_array(self, a, arr):
+        x = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+        if x.size != self.V or self.L.clo_set_array(self.h, a, _dp(x)) != 0:
+            raise IndexError(a)
+
+    def gauss_residual(self, g=0):
+        """Per-site Gauss residual of generator g (0: U(1); 1..3: SU(2) colours)."""
+        out = np.empty(self.V, dtype=np.float64)
+        if self.L.clo_gauss_residual(self.h, g, _dp(out)) != 0:
+            raise ValueError("no such Gauss law")
+        return out.reshape(self.N, self.N, self.N)
 
     def scalars(self):
         e, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
@@ -306,6 +333,14 @@ def ic_draws(model, N, kIR, alpha, seed, params, idx):
     return out.reshape(idx.size, nf, 5)
 
 
+def su2_exp(theta):
+    """exp(-i theta.sigma/2) as (u0, u1, u2, u3), U = u0 - i u.sigma."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(3))
+    u = np.zeros(4)
+    lib().clo_su2_exp(_dp(th), _dp(u))
+    return u
+
+
 def philox4x32_10(ctr, key):
     c = (ctypes.c_uint32 * 4)(*ctr)
     k = (ctypes.c_uint32 * 2)(*key)
@@ -344,7 +379,7 @@ def dft3d_naive(x, sign):
 def ic_sample(model, N, kIR, alpha, seed, params, idx):
     """Initial Fourier values (F, G) per field at the given linear site indices."""
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
-    nf = 1 if model == MODEL_LPHI4 else 2
+    nf = 1 if model == MODEL_LPHI4 else (4 if model == MODEL_SU2U1_HIGGS else 2)
     out = np.zeros(idx.size * nf * 4)
     rc = lib().clo_ic_sample(model, N, kIR, alpha, seed, ctypes.byref(params), idx.size,
                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))

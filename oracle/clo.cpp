@@ -133,9 +133,11 @@ struct clo_ctx {
   double Hfix;        // fixed background: initial a'/a
   uint64_t seed;      // seed of the initial conditions
   double H_ic;        // a'/a used by the initial conditions
-  std::vector<double> phi[2], pi[2];
+  std::vector<double> phi[4], pi[4];
   std::vector<double> A[3], piA[3];
-  bool gauge() const { return model == CLO_MODEL_U1_HIGGS; }
+  std::vector<double> U[3][4], piB[3][3];  // SU(2) links (u0..u3) and momenta (doublet model)
+  bool gauge() const { return model == CLO_MODEL_U1_HIGGS || model == CLO_MODEL_SU2U1_HIGGS; }
+  bool su2() const { return model == CLO_MODEL_SU2U1_HIGGS; }
   long at(long x, long y, long z) const {
     x %= N; if (x < 0) x += N;
     y %= N; if (y < 0) y += N;
@@ -159,7 +161,13 @@ int n_pot_terms(int model) { return model == CLO_MODEL_LPHI4_CHI ? 2 : 1; }
 
 // Program potential V~ term by term.  lphi4: phi^4/4 (eq. PotNat with chi = 0);
 // lphi4 + chi: phi^4/4 + (q/2) phi^2 chi^2 (eq. PotNat, q = g^2/lambda);
-// U(1) Abelian-Higgs: lam (|phi|^2 - v^2)^2 with |phi|^2 = (phi_0^2+phi_1^2)/2.
+// U(1) Abelian-Higgs: lam (|phi|^2 - v^2)^2 with |phi|^2 = (phi_0^2+phi_1^2)/2;
+// SU(2) x U(1) doublet: the same with |Phi|^2 = (phi_0^2+...+phi_3^2)/2.
+double half_norm2(const clo_ctx* c, const double* f) {
+  double s = 0.0;
+  for (int k = 0; k < c->nf; ++k) s += f[k] * f[k];
+  return 0.5 * s;
+}
 void pot_terms(const clo_ctx* c, const double* f, double* t) {
   if (c->model == CLO_MODEL_LPHI4) {
     t[0] = 0.25 * f[0] * f[0] * f[0] * f[0];
@@ -167,8 +175,7 @@ void pot_terms(const clo_ctx* c, const double* f, double* t) {
     t[0] = 0.25 * f[0] * f[0] * f[0] * f[0];
     t[1] = 0.5 * c->p.q * f[0] * f[0] * f[1] * f[1];
   } else {
-    double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
-    double d = m2 - c->p.v * c->p.v;
+    double d = half_norm2(c, f) - c->p.v * c->p.v;
     t[0] = c->p.lam * d * d;
   }
 }
@@ -184,10 +191,8 @@ void pot_deriv(const clo_ctx* c, const double* f, double* d) {
     d[0] = f[0] * f[0] * f[0] + c->p.q * f[0] * f[1] * f[1];
     d[1] = c->p.q * f[0] * f[0] * f[1];
   } else {
-    double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
-    double g = 2.0 * c->p.lam * (m2 - c->p.v * c->p.v);
-    d[0] = g * f[0];
-    d[1] = g * f[1];
+    double g = 2.0 * c->p.lam * (half_norm2(c, f) - c->p.v * c->p.v);
+    for (int k = 0; k < c->nf; ++k) d[k] = g * f[k];
   }
 }
 
@@ -196,8 +201,7 @@ double mass2(const clo_ctx* c, const double* f, int k) {
   if (c->model == CLO_MODEL_LPHI4) return 3.0 * f[0] * f[0];
   if (c->model == CLO_MODEL_LPHI4_CHI)
     return k == 0 ? 3.0 * f[0] * f[0] + c->p.q * f[1] * f[1] : c->p.q * f[0] * f[0];
-  double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
-  return 2.0 * c->p.lam * (m2 - c->p.v * c->p.v) + 2.0 * c->p.lam * f[k] * f[k];
+  return 2.0 * c->p.lam * (half_norm2(c, f) - c->p.v * c->p.v) + 2.0 * c->p.lam * f[k] * f[k];
 }
 
 // U(1) link phases theta = gQ dx A_i; link V_i = exp(-i theta) (U(1) toolkit).
@@ -294,21 +298,269 @@ void kernel_u1(const clo_ctx* c, std::vector<double>* Kphi, std::vector<double>*
 }
 
 // ---------------------------------------------------------------------------
+// SU(2) x U(1) doublet model: the gauge content of the manual's lphi4SU2U1
+// example (Sec. 4.1-4.3, SU(N) toolkit of Sec. 4.2) -- a doublet Phi charged
+// under a U(1) field A_i (coupling gQ = g_A Q_A) and an SU(2) field B_i^a
+// (coupling gQB = g_B Q_B) -- with V = lam (|Phi|^2 - v^2)^2.
+// Phi = (phi0 + i phi1, phi2 + i phi3)/sqrt2; psi = sqrt2 Phi below is the
+// complex 2-vector of the stored real components.
+// SU(2) links U_i(n) = exp(-i gQB dx B_i^a T_a), T_a = sigma_a/2, stored as
+// four reals with U = u0 I - i (u1 sigma1 + u2 sigma2 + u3 sigma3), and
+// multiplied here as explicit 2x2 complex matrices.  U(1) links are
+// V_i = exp(-i gQ dx A_i) as in the U(1) model; the doublet hops with W_i = V_i U_i.
+// reading: the manual leaves the lattice equations of the non-Abelian sector
+// to its companion paper.  They are derived here, as for U(1), from one
+// lattice Hamiltonian made of the toolkit's pieces (covariant hopping terms,
+// compact U(1) plaquettes, the SU(2) plaquette trace), so that both lattice
+// Gauss laws hold exactly.  At a = 1:
+//   H = sum_n [ pi_c^2/2 + (1/(2 dx^2)) sum_i |W_i psi(n+i) - psi(n)|^2 + V ]
+//     + (omega*/f*)^2 sum_n [ pi_A^2/2 + pi_B^2/2 + sum_{i<j} (1 - cos theta_ij)/(gQ dx^2)^2
+//                             + sum_{i<j} 2 (2 - Tr U_ij)/(gQB dx^2)^2 ],
+// the last term being (1/2) sum_a (G_ij^a)^2 to leading order (toolkit
+// expansion of Tr U_ij).  The momentum pi_B,i^a(n) moves U_i(n) by left
+// multiplication with exp(-i gQB dx delta T_a); its kernel is minus
+// (f*/omega*)^2 times the derivative of H along that direction.  The powers
+// of a of the kernels are those of Sec. 4.3.
+// ---------------------------------------------------------------------------
+struct M2 {
+  cplx m[2][2];
+};
+struct D2 {
+  cplx v[2];
+};
+
+M2 m_zero() {
+  M2 r;
+  r.m[0][0] = r.m[0][1] = r.m[1][0] = r.m[1][1] = cplx(0.0, 0.0);
+  return r;
+}
+M2 mat_of(const double u[4]) {
+  const cplx I(0.0, 1.0);
+  M2 r;
+  r.m[0][0] = u[0] - I * u[3];
+  r.m[0][1] = -I * u[1] - u[2];
+  r.m[1][0] = -I * u[1] + u[2];
+  r.m[1][1] = u[0] + I * u[3];
+  return r;
+}
+// (u0, u1, u2, u3) of an SU(2) matrix (each read symmetrically from the two
+// entries that hold it)
+void quat_of(const M2& M, double u[4]) {
+  u[0] = 0.5 * (M.m[0][0].real() + M.m[1][1].real());
+  u[3] = 0.5 * (M.m[1][1].imag() - M.m[0][0].imag());
+  u[1] = -0.5 * (M.m[0][1].imag() + M.m[1][0].imag());
+  u[2] = 0.5 * (M.m[1][0].real() - M.m[0][1].real());
+}
+M2 mul(const M2& A, const M2& B) {
+  M2 r = m_zero();
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k) r.m[i][j] += A.m[i][k] * B.m[k][j];
+  return r;
+}
+M2 dag(const M2& A) {
+  M2 r;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) r.m[i][j] = std::conj(A.m[j][i]);
+  return r;
+}
+M2 add(const M2& A, const M2& B) {
+  M2 r;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) r.m[i][j] = A.m[i][j] + B.m[i][j];
+  return r;
+}
+cplx trace(const M2& A) { return A.m[0][0] + A.m[1][1]; }
+// Pauli matrix sigma_a, a = 1, 2, 3
+M2 pauli(int a) {
+  const cplx I(0.0, 1.0);
+  M2 r = m_zero();
+  if (a == 1) { r.m[0][1] = 1.0; r.m[1][0] = 1.0; }
+  if (a == 2) { r.m[0][1] = -I; r.m[1][0] = I; }
+  if (a == 3) { r.m[0][0] = 1.0; r.m[1][1] = -1.0; }
+  return r;
+}
+D2 mv(const M2& A, const D2& x) {
+  D2 r;
+  for (int i = 0; i < 2; ++i) r.v[i] = A.m[i][0] * x.v[0] + A.m[i][1] * x.v[1];
+  return r;
+}
+cplx dot(const D2& x, const D2& y) { return std::conj(x.v[0]) * y.v[0] + std::conj(x.v[1]) * y.v[1]; }
+
+// exp(-i theta.sigma/2) = cos(|theta|/2) I - i sin(|theta|/2) (theta/|theta|).sigma
+void su2_exp(const double th[3], double u[4]) {
+  const double t = std::sqrt(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+  u[0] = std::cos(0.5 * t);
+  const double s = t > 0.0 ? std::sin(0.5 * t) / t : 0.5;
+  for (int a = 0; a < 3; ++a) u[a + 1] = s * th[a];
+}
+
+M2 su2_link(const clo_ctx* c, long n, int i) {
+  double u[4];
+  for (int k = 0; k < 4; ++k) u[k] = c->U[i][k][n];
+  return mat_of(u);
+}
+D2 doublet(const clo_ctx* c, long n) {
+  D2 r;
+  r.v[0] = cplx(c->phi[0][n], c->phi[1][n]);
+  r.v[1] = cplx(c->phi[2][n], c->phi[3][n]);
+  return r;
+}
+D2 doublet_mom(const clo_ctx* c, long n) {
+  D2 r;
+  r.v[0] = cplx(c->pi[0][n], c->pi[1][n]);
+  r.v[1] = cplx(c->pi[2][n], c->pi[3][n]);
+  return r;
+}
+// W_i(n) psi(n+i) and W_i^dag(n-i) psi(n-i)
+D2 hop_fwd(const clo_ctx* c, long n, int i) {
+  const double th = c->p.gQ * c->dx * c->A[i][n];
+  D2 r = mv(su2_link(c, n, i), doublet(c, c->shift(n, i, +1)));
+  const cplx ph = std::polar(1.0, -th);
+  r.v[0] *= ph;
+  r.v[1] *= ph;
+  return r;
+}
+D2 hop_bwd(const clo_ctx* c, long n, int i) {
+  const long m = c->shift(n, i, -1);
+  const double th = c->p.gQ * c->dx * c->A[i][m];
+  D2 r = mv(dag(su2_link(c, m, i)), doublet(c, m));
+  const cplx ph = std::polar(1.0, th);
+  r.v[0] *= ph;
+  r.v[1] *= ph;
+  return r;
+}
+// SU(2) plaquette U_ij(n) = U_i(n) U_j(n+i) U_i^dag(n+j) U_j^dag(n)  (SU(N) toolkit)
+M2 su2_plaq(const clo_ctx* c, long n, int i, int j) {
+  M2 r = mul(su2_link(c, n, i), su2_link(c, c->shift(n, i, +1), j));
+  r = mul(r, dag(su2_link(c, c->shift(n, j, +1), i)));
+  return mul(r, dag(su2_link(c, n, j)));
+}
+// Staples of U_i(n): sum over j != i of U_j(n+i) U_i^dag(n+j) U_j^dag(n)
+// (plaquette U_ij(n)) and U_j^dag(n+i-j) U_i^dag(n-j) U_j(n-j) (the plaquette
+// at n-j, traversed from U_i(n)), so that Re Tr[U_i(n) S] is the sum of
+// Re Tr over the four plaquettes holding U_i(n).
+M2 su2_staples(const clo_ctx* c, long n, int i) {
+  M2 S = m_zero();
+  const long ni = c->shift(n, i, +1);
+  for (int j = 0; j < 3; ++j) {
+    if (j == i) continue;
+    const long nj = c->shift(n, j, +1), nmj = c->shift(n, j, -1), nimj = c->shift(ni, j, -1);
+    M2 up = mul(mul(su2_link(c, ni, j), dag(su2_link(c, nj, i))), dag(su2_link(c, n, j)));
+    M2 lo = mul(mul(dag(su2_link(c, nimj, j)), dag(su2_link(c, nmj, i))), su2_link(c, nmj, j));
+    S = add(S, add(up, lo));
+  }
+  return S;
+}
+
+// Kernels of the doublet model (Sec. 4.3 with the Hamiltonian above):
+//   K_c     = a^{1+alpha} (D^2 psi)_c - a^{3+alpha} 2 lam (|Phi|^2 - v^2) phi_c,
+//             D^2 psi = sum_i [W_i psi(n+i) - 2 psi + W_i^dag(n-i) psi(n-i)]/dx^2
+//   K_{A_i} = a^{1+alpha} (f*/omega*)^2 (gQ/dx) Im[psi^dag W_i psi(n+i)] + a^{alpha-1} (compact curl, as U(1))
+//   K_{B_i}^a = a^{1+alpha} (f*/omega*)^2 (gQB/(2 dx)) Im[psi^dag sigma_a W_i psi(n+i)]
+//             + a^{alpha-1} (1/(gQB dx^3)) Im Tr[sigma_a U_i(n) S_i(n)].
+// reading: the printed doublet kernel writes D_A^2; the covariant Laplacian of
+// both gauge groups is used (eq. kernelsSU21 is otherwise the U(1) form).
+// gQ = 0 switches the U(1) field off: no current, no curl, E_G^A = 0.
+void kernel_su2(const clo_ctx* c, std::vector<double>* Kphi, std::vector<double>* KA,
+                std::vector<double> (*KB)[3]) {
+  const double a1 = std::pow(c->a, 1.0 + c->alpha), a3 = std::pow(c->a, 3.0 + c->alpha);
+  const double am1 = std::pow(c->a, c->alpha - 1.0);
+  const double idx2 = 1.0 / (c->dx * c->dx);
+  const double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  const double gQ = c->p.gQ, gB = c->p.gQB, dx = c->dx;
+  for (long n = 0; n < c->V; ++n) {
+    double f[4], d[4];
+    for (int k = 0; k < 4; ++k) f[k] = c->phi[k][n];
+    pot_deriv(c, f, d);
+    const D2 psi = doublet(c, n);
+    D2 D;
+    D.v[0] = D.v[1] = cplx(0.0, 0.0);
+    for (int i = 0; i < 3; ++i) {
+      const D2 u = hop_fwd(c, n, i), w = hop_bwd(c, n, i);
+      for (int r = 0; r < 2; ++r) D.v[r] += u.v[r] + w.v[r] - 2.0 * psi.v[r];
+    }
+    const double Dc[4] = {D.v[0].real(), D.v[0].imag(), D.v[1].real(), D.v[1].imag()};
+    for (int k = 0; k < 4; ++k) Kphi[k][n] = a1 * Dc[k] * idx2 - a3 * d[k];
+    for (int i = 0; i < 3; ++i) {
+      const D2 u = hop_fwd(c, n, i);
+      const double JA = (gQ / dx) * dot(psi, u).imag();
+      double curl = 0.0;
+      for (int j = 0; j < 3 && gQ != 0.0; ++j) {
+        if (j == i) continue;
+        curl += std::sin(plaq(c, n, i, j)) - std::sin(plaq(c, c->shift(n, j, -1), i, j));
+      }
+      if (gQ != 0.0) curl *= -1.0 / (gQ * dx * dx * dx);
+      KA[i][n] = a1 * fo2 * JA + am1 * curl;
+      const M2 M = mul(su2_link(c, n, i), su2_staples(c, n, i));
+      for (int a = 1; a <= 3; ++a) {
+        const double Ja = (gB / (2.0 * dx)) * dot(psi, mv(pauli(a), u)).imag();
+        const double mag = trace(mul(pauli(a), M)).imag() / (gB * dx * dx * dx);
+        KB[i][a - 1][n] = a1 * fo2 * Ja + am1 * mag;
+      }
+    }
+  }
+}
+
+// U_i(n) <- exp(-i gQB dx w_B pi_B,i^a T_a) U_i(n)   (w_B = step abar^{alpha-1})
+void drift_su2_links(clo_ctx* c, double wB) {
+  const double e = c->p.gQB * c->dx * wB;
+  for (int i = 0; i < 3; ++i)
+    for (long n = 0; n < c->V; ++n) {
+      double th[3], g[4], u[4];
+      for (int a = 0; a < 3; ++a) th[a] = e * c->piB[i][a][n];
+      su2_exp(th, g);
+      quat_of(mul(mat_of(g), su2_link(c, n, i)), u);
+      for (int k = 0; k < 4; ++k) c->U[i][k][n] = u[k];
+    }
+}
+
+// Gauss-law residuals of the doublet model at site n (derived from the
+// invariance of H under a gauge transformation at n, SU(N) toolkit):
+//   U(1):   sum_i grad^-_i pi_A,i - (f*/omega*)^2 gQ Im[psi^dag pi_psi]
+//   SU(2):  sum_i [pi_B,i^a(n) - (U_i^dag(n-i) pi_B,i(n-i) U_i(n-i))^a]/dx
+//           - (f*/omega*)^2 (gQB/2) Im[psi^dag sigma_a pi_psi]
+// with pi_B = pi_B^b sigma_b/2 and X^a = Tr[sigma_a X].  lhs, rhs: the two sides.
+void gauss_su2_site(const clo_ctx* c, long n, int g, double& lhs, double& rhs) {
+  const double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  const D2 psi = doublet(c, n), mom = doublet_mom(c, n);
+  lhs = 0.0;
+  if (g == 0) {
+    for (int i = 0; i < 3; ++i) lhs += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
+    rhs = fo2 * c->p.gQ * dot(psi, mom).imag();
+    return;
+  }
+  for (int i = 0; i < 3; ++i) {
+    const long m = c->shift(n, i, -1);
+    M2 P = m_zero();
+    for (int b = 1; b <= 3; ++b) {
+      M2 s = pauli(b);
+      for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 2; ++q) P.m[r][q] += 0.5 * c->piB[i][b - 1][m] * s.m[r][q];
+    }
+    const M2 Um = su2_link(c, m, i);
+    const double tr = trace(mul(pauli(g), mul(dag(Um), mul(P, Um)))).real();
+    lhs += (c->piB[i][g - 1][n] - tr) / c->dx;
+  }
+  rhs = fo2 * 0.5 * c->p.gQB * dot(psi, mv(pauli(g), mom)).imag();
+}
+
+// ---------------------------------------------------------------------------
 // Volume averages (eq. EK_EG_EV; eq. energy-contrib for U(1)).
 // reading: the gradient energy uses forward differences grad^+, so that
 // sum_n (grad^+ phi)^2 = -sum_n phi Lap phi matches the kick's Laplacian.
 // ---------------------------------------------------------------------------
 struct Avg {
-  double EK[4], EG[4], EV[4], EKA, EGA;
+  double EK[4], EG[4], EV[4], EKA, EGA, EKB, EGB;
   double mphi[4], mphi2[4], mpi[4], mpi2[4];
 };
 
 void averages(const clo_ctx* c, Avg& r) {
   std::memset(&r, 0, sizeof(r));
-  double sp2[2] = {0, 0}, sg[2] = {0, 0}, sv[4] = {0, 0, 0, 0};
-  double spA = 0.0, smag = 0.0;
+  double sp2[4] = {0, 0, 0, 0}, sg[2] = {0, 0}, sv[4] = {0, 0, 0, 0};
+  double spA = 0.0, smag = 0.0, spB = 0.0, smagB = 0.0;
   for (long n = 0; n < c->V; ++n) {
-    double f[2] = {0, 0}, t[4] = {0, 0, 0, 0};
+    double f[4] = {0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
     for (int k = 0; k < c->nf; ++k) {
       f[k] = c->phi[k][n];
       double pv = c->pi[k][n];
@@ -326,13 +578,25 @@ void averages(const clo_ctx* c, Avg& r) {
           double g = c->phi[k][c->shift(n, i, +1)] - c->phi[k][n];
           sg[k] += g * g;
         }
-    } else {
+    } else if (!c->su2()) {
       for (int i = 0; i < 3; ++i) {
         double u0, u1;
         link_fwd(c, n, i, u0, u1);
         sg[0] += (u0 - f[0]) * (u0 - f[0]) + (u1 - f[1]) * (u1 - f[1]);
         spA += c->piA[i][n] * c->piA[i][n];
         for (int j = i + 1; j < 3; ++j) smag += 1.0 - std::cos(plaq(c, n, i, j));
+      }
+    } else {
+      const D2 psi = doublet(c, n);
+      for (int i = 0; i < 3; ++i) {
+        const D2 u = hop_fwd(c, n, i);
+        for (int r = 0; r < 2; ++r) sg[0] += std::norm(u.v[r] - psi.v[r]);
+        spA += c->piA[i][n] * c->piA[i][n];
+        for (int a = 0; a < 3; ++a) spB += c->piB[i][a][n] * c->piB[i][a][n];
+        for (int j = i + 1; j < 3; ++j) {
+          smag += 1.0 - std::cos(plaq(c, n, i, j));
+          smagB += 2.0 - trace(su2_plaq(c, n, i, j)).real();
+        }
       }
     }
   }
@@ -344,12 +608,18 @@ void averages(const clo_ctx* c, Avg& r) {
       r.EG[k] = sg[k] / (2.0 * a2 * c->dx * c->dx * V);
     }
   } else {
-    r.EK[0] = (sp2[0] + sp2[1]) / (2.0 * a6 * V);
+    r.EK[0] = (sp2[0] + sp2[1] + sp2[2] + sp2[3]) / (2.0 * a6 * V);
     r.EG[0] = sg[0] / (2.0 * a2 * c->dx * c->dx * V);
     double of2 = 1.0 / (c->p.fstar_over_omegastar * c->p.fstar_over_omegastar);
     double gdx2 = c->p.gQ * c->dx * c->dx;
     r.EKA = of2 * spA / (2.0 * a4 * V);
-    r.EGA = of2 * smag / (a4 * gdx2 * gdx2 * V);
+    r.EGA = gdx2 != 0.0 ? of2 * smag / (a4 * gdx2 * gdx2 * V) : 0.0;
+    if (c->su2()) {
+      // E_K^B, E_G^B: (omega*/f*)^2/a^4 times <pi_B^2/2> and <sum_{i<j} 2 (2 - Tr U_ij)>/(gQB dx^2)^2
+      double bdx2 = c->p.gQB * c->dx * c->dx;
+      r.EKB = of2 * spB / (2.0 * a4 * V);
+      r.EGB = of2 * 2.0 * smagB / (a4 * bdx2 * bdx2 * V);
+    }
   }
   for (int m = 0; m < n_pot_terms(c->model); ++m) r.EV[m] = sv[m] / V;
   for (int k = 0; k < c->nf; ++k) {
@@ -360,11 +630,11 @@ void averages(const clo_ctx* c, Avg& r) {
 double sum4(const double* x) { return x[0] + x[1] + x[2] + x[3]; }
 
 // b' = K_a = a^{2alpha+1}/3 (f*/m_p)^2 [(alpha-2)E_K + alpha E_G
-//            + (alpha-1)(E_K^A + E_G^A) + (alpha+1) E_V]   (Sec. 4.3)
+//            + (alpha-1)(E_K^A + E_G^A + E_K^B + E_G^B) + (alpha+1) E_V]   (Sec. 4.3)
 double kernel_a(const clo_ctx* c, const Avg& r) {
   double al = c->alpha, fm = c->p.fstar_over_mp;
-  double br = (al - 2.0) * sum4(r.EK) + al * sum4(r.EG) + (al - 1.0) * (r.EKA + r.EGA) +
-              (al + 1.0) * sum4(r.EV);
+  double br = (al - 2.0) * sum4(r.EK) + al * sum4(r.EG) +
+              (al - 1.0) * (r.EKA + r.EGA + r.EKB + r.EGB) + (al + 1.0) * sum4(r.EV);
   return std::pow(c->a, 2.0 * al + 1.0) / 3.0 * fm * fm * br;
 }
 
@@ -395,7 +665,7 @@ void kick_fields(clo_ctx* c, double w) {
     kernel_scalars(c, K);
     for (int k = 0; k < c->nf; ++k)
       for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * K[k][n];
-  } else {
+  } else if (!c->su2()) {
     std::vector<double> Kp[2], KA[3];
     for (int k = 0; k < 2; ++k) Kp[k].assign(c->V, 0.0);
     for (int i = 0; i < 3; ++i) KA[i].assign(c->V, 0.0);
@@ -404,6 +674,21 @@ void kick_fields(clo_ctx* c, double w) {
       for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * Kp[k][n];
     for (int i = 0; i < 3; ++i)
       for (long n = 0; n < c->V; ++n) c->piA[i][n] += w * KA[i][n];
+  } else {
+    std::vector<double> Kp[4], KA[3], KB[3][3];
+    for (int k = 0; k < 4; ++k) Kp[k].assign(c->V, 0.0);
+    for (int i = 0; i < 3; ++i) {
+      KA[i].assign(c->V, 0.0);
+      for (int a = 0; a < 3; ++a) KB[i][a].assign(c->V, 0.0);
+    }
+    kernel_su2(c, Kp, KA, KB);
+    for (int k = 0; k < 4; ++k)
+      for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * Kp[k][n];
+    for (int i = 0; i < 3; ++i) {
+      for (long n = 0; n < c->V; ++n) c->piA[i][n] += w * KA[i][n];
+      for (int a = 0; a < 3; ++a)
+        for (long n = 0; n < c->V; ++n) c->piB[i][a][n] += w * KB[i][a][n];
+    }
   }
 }
 
@@ -431,6 +716,7 @@ void drift(clo_ctx* c, double w) {
     double cA = w * std::pow(abar, c->alpha - 1.0);
     for (int i = 0; i < 3; ++i)
       for (long n = 0; n < c->V; ++n) c->A[i][n] += cA * c->piA[i][n];
+    if (c->su2()) drift_su2_links(c, cA);
   }
   c->a = a1;
   c->eta += w;
@@ -445,7 +731,9 @@ void vv2(clo_ctx* c, double h) {
   kick_fields(c, 0.5 * h);
 }
 
-double rho_of(const Avg& r) { return sum4(r.EK) + sum4(r.EG) + sum4(r.EV) + r.EKA + r.EGA; }
+double rho_of(const Avg& r) {
+  return sum4(r.EK) + sum4(r.EG) + sum4(r.EV) + r.EKA + r.EGA + r.EKB + r.EGB;
+}
 
 // ---------------------------------------------------------------------------
 // Initial conditions (Sec. 3.5.1 eqs. fpr_influct, fpr_influct2,
@@ -516,20 +804,27 @@ bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, d
       z2[f] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
     }
   } else {
-    // eqs. InConstr:1-2: |d_{c1}| = |d_{c2}|, theta_12 = theta_02 + theta_11 - theta_01
-    double P0 = amp2 * vol / (2.0 * a * a * om[0]);
-    double P1 = amp2 * vol / (2.0 * a * a * om[1]);
-    double u0[2], v0[2], u1[2], v1[2];
+    // eqs. InConstr:1-2 for the components n of the charged field:
+    // |d_{n1}| = |d_{n2}|, theta_{n2} = theta_02 + theta_{n1} - theta_01
+    double u0[2], v0[2];
     draw4(seed, idx, 0, 0, u0);
     draw4(seed, idx, 0, 1, v0);
-    draw4(seed, idx, 1, 0, u1);
-    draw4(seed, idx, 1, 1, v1);
-    double r0 = std::sqrt(-P0 * std::log(u0[0]));
-    double r1 = std::sqrt(-P1 * std::log(u1[0]));
-    double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1], t11 = 2.0 * PI * v1[0];
-    double t12 = t02 + t11 - t01;
-    z1[0] = std::polar(r0, t01); z2[0] = std::polar(r0, t02);
-    z1[1] = std::polar(r1, t11); z2[1] = std::polar(r1, t12);
+    double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1];
+    for (int f = 0; f < c->nf; ++f) {
+      double P = amp2 * vol / (2.0 * a * a * om[f]);
+      double u[2], v[2];
+      if (f == 0) {
+        u[0] = u0[0]; u[1] = u0[1]; v[0] = v0[0]; v[1] = v0[1];
+      } else {
+        draw4(seed, idx, f, 0, u);
+        draw4(seed, idx, f, 1, v);
+      }
+      double r = std::sqrt(-P * std::log(u[0]));
+      double t1 = f == 0 ? t01 : 2.0 * PI * v[0];
+      double t2 = f == 0 ? t02 : t02 + t1 - t01;
+      z1[f] = std::polar(r, t1);
+      z2[f] = std::polar(r, t2);
+    }
   }
   return true;
 }
@@ -539,8 +834,8 @@ bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, d
 // stay zero.
 bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, cplx* G) {
   const double isq2 = 1.0 / std::sqrt(2.0);
-  cplx z1[2], z2[2];
-  double om[2];
+  cplx z1[4], z2[4];
+  double om[4];
   if (!mode_draws(c, seed, idx, z1, z2, om)) return false;
   bool selfc = partner_index(c, idx) == idx;
   for (int f = 0; f < c->nf; ++f) {
@@ -563,7 +858,7 @@ void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F
   for (long idx = 1; idx < c->V; ++idx) {
     long pid = partner_index(c, idx);
     if (pid < idx) continue;
-    cplx f[2], g[2];
+    cplx f[4], g[4];
     if (!mode_values(c, seed, H, idx, f, g)) continue;
     for (int k = 0; k < c->nf; ++k) {
       F[k][idx] = f[k]; G[k][idx] = g[k];
@@ -576,11 +871,10 @@ void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F
 // reading: the lattice backward-difference symbol kappa_i = (1 - e^{-2 pi i n_i/N})/dx
 // replaces the continuum k_i, so that sum_i grad^-_i pi_A,i equals the charge
 // density to roundoff:  pi_A,i(k) = kappa_i^* rho(k)/|kappa|^2, rho(0) -> 0.
-void gauss_momenta(clo_ctx* c) {
-  double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
-  std::vector<cplx> rho(c->V);
-  for (long n = 0; n < c->V; ++n)
-    rho[n] = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+// The doublet model (links start at the identity, so both laws are linear
+// there) takes the same inversion for the U(1) density and for each SU(2)
+// colour's density.
+void invert_gauss(const clo_ctx* c, std::vector<cplx> rho, std::vector<double>* out) {
   fft3d(rho, c->N, -1);
   for (int i = 0; i < 3; ++i) {
     std::vector<cplx> E(c->V);
@@ -599,12 +893,38 @@ void gauss_momenta(clo_ctx* c) {
       E[idx] = std::conj(ki) * rho[idx] / kk;
     }
     fft3d(E, c->N, +1);
-    for (long n = 0; n < c->V; ++n) c->piA[i][n] = E[n].real() / (double)c->V;
+    for (long n = 0; n < c->V; ++n) out[i][n] = E[n].real() / (double)c->V;
+  }
+}
+
+void gauss_momenta(clo_ctx* c) {
+  std::vector<cplx> rho(c->V);
+  double lhs, rhs;
+  if (!c->su2()) {
+    double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+    for (long n = 0; n < c->V; ++n)
+      rho[n] = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+    invert_gauss(c, rho, c->piA);
+    return;
+  }
+  for (int g = 0; g < 4; ++g) {
+    for (long n = 0; n < c->V; ++n) {
+      gauss_su2_site(c, n, g, lhs, rhs);  // the density does not depend on the link momenta
+      rho[n] = rhs;
+    }
+    if (g == 0) {
+      invert_gauss(c, rho, c->piA);
+    } else {
+      std::vector<double> E[3];
+      for (int i = 0; i < 3; ++i) E[i].assign(c->V, 0.0);
+      invert_gauss(c, rho, E);
+      for (int i = 0; i < 3; ++i) c->piB[i][g - 1] = E[i];
+    }
   }
 }
 
 double homogeneous_rho(const clo_ctx* c) {
-  double f[2] = {0, 0}, t[4] = {0, 0, 0, 0};
+  double f[4] = {0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
   double kin = 0.0;
   for (int k = 0; k < c->nf; ++k) {
     f[k] = c->p.phi0[k];
@@ -673,13 +993,14 @@ int clo_schedule(int integrator, double h, double* drifts, int cap) {
 int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
              const clo_params* p) {
   if (!out || !p) return -1;
-  if (model < CLO_MODEL_LPHI4 || model > CLO_MODEL_U1_HIGGS) return -1;
+  if (model < CLO_MODEL_LPHI4 || model > CLO_MODEL_SU2U1_HIGGS) return -1;
   if (N < 2 || kIR <= 0.0) return -1;
+  if (model == CLO_MODEL_SU2U1_HIGGS && !(p->gQB != 0.0)) return -1;
   clo_ctx* c = new clo_ctx();
   c->model = model;
   c->N = N;
   c->V = (long)N * N * N;
-  c->nf = model == CLO_MODEL_LPHI4 ? 1 : 2;
+  c->nf = model == CLO_MODEL_LPHI4 ? 1 : (model == CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
   c->kIR = kIR;
   c->dx = 2.0 * PI / ((double)N * kIR);
   c->alpha = alpha;
@@ -694,6 +1015,11 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
     for (int i = 0; i < 3; ++i) {
       c->A[i].assign(c->V, 0.0);
       c->piA[i].assign(c->V, 0.0);
+    }
+  if (c->su2())  // eqs. Inflc1-4: links at the identity, momenta from the Gauss law
+    for (int i = 0; i < 3; ++i) {
+      for (int k = 0; k < 4; ++k) c->U[i][k].assign(c->V, k == 0 ? 1.0 : 0.0);
+      for (int a = 0; a < 3; ++a) c->piB[i][a].assign(c->V, 0.0);
     }
   // initial a' (Sec. 5.2 ScaleFactorInitializer: from homogeneous values)
   double rho_h = homogeneous_rho(c);
@@ -710,7 +1036,7 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
   c->H_ic = H;
   double a3ma = std::pow(c->a, 3.0 - alpha);
   if (p->fluct_amp2 > 0.0) {
-    std::vector<cplx> F[2], G[2];
+    std::vector<cplx> F[4], G[4];
     fluct_modes(c, seed, H, F, G);
     for (int k = 0; k < c->nf; ++k) {
       fft3d(F[k], N, +1);
@@ -741,12 +1067,12 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
 // of field f at site idx[i] (same conventions as clo_init).
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out) {
-  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_U1_HIGGS) return -1;
+  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_SU2U1_HIGGS) return -1;
   clo_ctx c;
   c.model = model;
   c.N = N;
   c.V = (long)N * N * N;
-  c.nf = model == CLO_MODEL_LPHI4 ? 1 : 2;
+  c.nf = model == CLO_MODEL_LPHI4 ? 1 : (model == CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
   c.kIR = kIR;
   c.dx = 2.0 * PI / ((double)N * kIR);
   c.alpha = alpha;
@@ -761,10 +1087,10 @@ int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, con
     long id = (long)idx[i];
     if (id < 0 || id >= c.V) return -1;
     long pid = partner_index(&c, id);
-    cplx f[2] = {0, 0}, g[2] = {0, 0};
+    cplx f[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
     bool conj = pid < id;
     if (!mode_values(&c, seed, c.b / c.a, conj ? pid : id, f, g)) {
-      f[0] = f[1] = g[0] = g[1] = cplx(0, 0);
+      for (int k = 0; k < 4; ++k) f[k] = g[k] = cplx(0, 0);
     }
     for (int k = 0; k < c.nf; ++k) {
       cplx F = conj ? std::conj(f[k]) : f[k], G = conj ? std::conj(g[k]) : g[k];
@@ -805,6 +1131,7 @@ int clo_energies(clo_ctx* c, clo_energies_t* o) {
     o->mean_pi[k] = r.mpi[k]; o->mean_pi2[k] = r.mpi2[k];
   }
   o->EKA = r.EKA; o->EGA = r.EGA;
+  o->EKB = r.EKB; o->EGB = r.EGB;
   o->rho = rho_of(r);
   // Hubble constraint eq. NewFriedmannEQsI and its monitor (Sec. 3.3.2 outputs)
   double fm = c->p.fstar_over_mp;
@@ -820,7 +1147,8 @@ static std::vector<double>* field_ptr(const clo_ctx* c, int field, int what) {
   clo_ctx* m = const_cast<clo_ctx*>(c);
   if (what != 0 && what != 1) return nullptr;
   if (field >= 0 && field < c->nf) return what == 0 ? &m->phi[field] : &m->pi[field];
-  if (c->gauge() && field >= 2 && field < 5) return what == 0 ? &m->A[field - 2] : &m->piA[field - 2];
+  if (c->gauge() && field >= c->nf && field < c->nf + 3)
+    return what == 0 ? &m->A[field - c->nf] : &m->piA[field - c->nf];
   return nullptr;
 }
 
@@ -854,22 +1182,75 @@ int clo_set_scalars(clo_ctx* c, double eta, double a, double b) {
   return 0;
 }
 
-int clo_nfields(const clo_ctx* c) { return c ? (c->gauge() ? 5 : c->nf) : -1; }
+int clo_nfields(const clo_ctx* c) { return c ? (c->gauge() ? c->nf + 3 : c->nf) : -1; }
+
+static std::vector<double>* array_ptr(const clo_ctx* c, int a) {
+  clo_ctx* m = const_cast<clo_ctx*>(c);
+  if (!c->su2() || a < 0 || a >= 35) return nullptr;
+  if (a < 4) return &m->phi[a];
+  if (a < 8) return &m->pi[a - 4];
+  if (a < 11) return &m->A[a - 8];
+  if (a < 14) return &m->piA[a - 11];
+  if (a < 26) return &m->U[(a - 14) / 4][(a - 14) % 4];
+  return &m->piB[(a - 26) / 3][(a - 26) % 3];
+}
+
+int clo_get_array(const clo_ctx* c, int a, double* out) {
+  if (!c || !out) return -1;
+  std::vector<double>* v = array_ptr(c, a);
+  if (!v) return -1;
+  std::memcpy(out, v->data(), sizeof(double) * c->V);
+  return 0;
+}
+
+int clo_set_array(clo_ctx* c, int a, const double* in) {
+  if (!c || !in) return -1;
+  std::vector<double>* v = array_ptr(c, a);
+  if (!v) return -1;
+  std::memcpy(v->data(), in, sizeof(double) * c->V);
+  return 0;
+}
+
+int clo_gauss_residual(const clo_ctx* c, int g, double* out) {
+  if (!c || !out || !c->gauge() || g < 0 || g > (c->su2() ? 3 : 0)) return -1;
+  const double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  for (long n = 0; n < c->V; ++n) {
+    double L = 0.0, R = 0.0;
+    if (c->su2()) {
+      gauss_su2_site(c, n, g, L, R);
+    } else {
+      for (int i = 0; i < 3; ++i) L += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
+      R = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+    }
+    out[n] = L - R;
+  }
+  return 0;
+}
+
+void clo_su2_exp(const double theta[3], double u[4]) { su2_exp(theta, u); }
 
 // Gauss-law monitor (Sec. 4.5 output "average_gauss"): LHS = sum_i grad^-_i pi_A,i,
-// RHS = (f*/omega*)^2 2 gQ Im[phi^* pi_phi]; rel = <|L-R|>/<|L+R|>.
+// RHS = (f*/omega*)^2 2 gQ Im[phi^* pi_phi]; rel = <|L-R|>/<|L+R|>.  Doublet
+// model: the sums run over the U(1) law and the three SU(2) colours.
 int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
                          double* max_abs) {
   if (!c || !c->gauge()) return -1;
   double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
   double sd = 0.0, ss = 0.0, mx = 0.0;
   for (long n = 0; n < c->V; ++n) {
-    double L = 0.0;
-    for (int i = 0; i < 3; ++i) L += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
-    double R = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
-    sd += std::fabs(L - R);
-    ss += std::fabs(L + R);
-    if (std::fabs(L - R) > mx) mx = std::fabs(L - R);
+    const int ng = c->su2() ? 4 : 1;
+    for (int g = 0; g < ng; ++g) {
+      double L = 0.0, R = 0.0;
+      if (c->su2()) {
+        gauss_su2_site(c, n, g, L, R);
+      } else {
+        for (int i = 0; i < 3; ++i) L += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
+        R = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+      }
+      sd += std::fabs(L - R);
+      ss += std::fabs(L + R);
+      if (std::fabs(L - R) > mx) mx = std::fabs(L - R);
+    }
   }
   double V = (double)c->V;
   if (lhs_abs) *lhs_abs = sd / V;

@@ -18,7 +18,11 @@
  *     (the manual's two printed sign conventions conflict; this one is used);
  *   - scalar models: field f in [0, nf); U(1) model: f = 0,1 are the real
  *     components phi_0, phi_1 of phi = (phi_0 + i phi_1)/sqrt(2) and
- *     f = 2,3,4 are the link fields A_x, A_y, A_z (non-compact storage).
+ *     f = 2,3,4 are the link fields A_x, A_y, A_z (non-compact storage);
+ *   - SU(2) x U(1) doublet model: f = 0..3 are the real components of
+ *     Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt(2), f = 4,5,6 the U(1)
+ *     link fields A_i; the SU(2) links and their momenta are reached through
+ *     clo_get_array / clo_set_array (array order below).
  *
  * Every function returns 0 on success and a negative code on error.
  */
@@ -30,7 +34,7 @@
 extern "C" {
 #endif
 
-enum { CLO_MODEL_LPHI4 = 1, CLO_MODEL_LPHI4_CHI = 2, CLO_MODEL_U1_HIGGS = 3 };
+enum { CLO_MODEL_LPHI4 = 1, CLO_MODEL_LPHI4_CHI = 2, CLO_MODEL_U1_HIGGS = 3, CLO_MODEL_SU2U1_HIGGS = 4 };
 enum { CLO_LF = 0, CLO_VV2 = 2, CLO_VV4 = 4, CLO_VV6 = 6, CLO_VV8 = 8, CLO_VV10 = 10 };
 enum { CLO_EXP_OFF = 0, CLO_EXP_SELF = 1, CLO_EXP_FIXED = 2 };
 
@@ -41,9 +45,9 @@ typedef struct {
   double fstar_over_mp;         /* f_s/m_p in the Friedmann equations */
   double phi0[4];               /* homogeneous initial field values */
   double dphi0[4];              /* homogeneous initial derivatives phi' */
-  double lam, v;                /* U(1) model: V = lam (|phi|^2 - v^2)^2 */
-  double gQ;                    /* U(1) gauge coupling times charge */
-  double fstar_over_omegastar;  /* f_s/omega_s (U(1) model) */
+  double lam, v;                /* gauge models: V = lam (|phi|^2 - v^2)^2 */
+  double gQ;                    /* U(1) gauge coupling times charge (g_A Q_A) */
+  double fstar_over_omegastar;  /* f_s/omega_s (gauge models) */
   double kcut;                  /* initial-spectrum cutoff; < 0 means none */
   double omega_eos;             /* fixed background: equation of state w */
   double H0;                    /* fixed background: initial a'/a; <= 0 -> from Hubble law */
@@ -51,6 +55,7 @@ typedef struct {
   int expansion;                /* CLO_EXP_OFF / SELF / FIXED */
   int b0_mode;                  /* 0: a' from homogeneous values; 1: from lattice averages */
   int pad_;
+  double gQB;                   /* SU(2) gauge coupling times charge (g_B Q_B), doublet model */
 } clo_params;
 
 typedef struct {
@@ -62,6 +67,7 @@ typedef struct {
   double hubble_lhs, hubble_rhs, hubble_viol; /* a'^2, RHS of eq. NewFriedmannEQsI, (L-R)/(L+R) */
   double energy_cons;           /* 1 - rho/rho(t0) */
   double mean_phi[4], mean_phi2[4], mean_pi[4], mean_pi2[4];
+  double EKB, EGB;              /* SU(2) electric and magnetic energies (doublet model) */
 } clo_energies_t;
 
 typedef struct clo_ctx clo_ctx;
@@ -92,6 +98,19 @@ int clo_em_spectrum(const clo_ctx* c, int which, double dk_bin, double* k, doubl
  * NaN where omega_b^2 <= 0.  -1 for U(1) or bad arguments, -2 if cap < nbins. */
 int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, double* k, double* n,
                    int64_t* mult, int cap, int* nbins);
+/* SU(2) x U(1) doublet model: whole arrays in the order
+ *   0..3 phi_c, 4..7 pi_c, 8..10 A_i, 11..13 pi_A,i,
+ *   14 + 4 i + k: component u_k of the SU(2) link U_i = u0 - i (u1 s1 + u2 s2 + u3 s3),
+ *   26 + 3 i + (a - 1): link momentum pi_B,i^a.
+ * -1 for other models or a bad index. */
+int clo_get_array(const clo_ctx* c, int a, double* out);
+int clo_set_array(clo_ctx* c, int a, const double* in);
+/* Gauss-law residual per site of generator g (0: the U(1) law; 1..3: the SU(2)
+ * colour a = g, doublet model only): out[n] = (lattice divergence of the
+ * electric field) - (charge density); -1 where the model has no such law. */
+int clo_gauss_residual(const clo_ctx* c, int g, double* out);
+/* exp(-i theta.sigma/2) as (u0, u1, u2, u3) in the link convention above. */
+void clo_su2_exp(const double theta[3], double u[4]);
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out);
 

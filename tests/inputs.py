@@ -38,3 +38,26 @@ def scalar_state(N, seed, nf=2, rough=False):
             pi = gen(N, seed * 103 + f, amp=0.2 if f == 0 else 0.05)
         out.append((phi, pi))
     return out
+
+
+def su2_doublet_state(N, seed, link_spread=0.4, mom=0.3, phi_offset=0.6, u1=True):
+    """Arrays of the SU(2) x U(1) doublet model in its array order (35 arrays,
+    each [z][y][x]): doublet components near phi_offset, random unit
+    quaternions spread about the identity for the SU(2) links, and random
+    momenta; with u1=False the U(1) link fields and momenta are zero."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(4):
+        out.append(phi_offset + 0.2 * rng.standard_normal((N, N, N)))
+    for c in range(4):
+        out.append(mom * rng.standard_normal((N, N, N)))
+    for i in range(6):
+        out.append((0.2 * rng.standard_normal((N, N, N))) if u1 else np.zeros((N, N, N)))
+    for i in range(3):
+        q = link_spread * rng.standard_normal((4, N, N, N))
+        q[0] += 1.0
+        q /= np.sqrt((q ** 2).sum(axis=0))
+        out.extend(list(q))
+    for i in range(9):
+        out.append(mom * rng.standard_normal((N, N, N)))
+    return out

@@ -1,0 +1,274 @@
+"""Pins of the oracle's SU(2) x U(1) doublet model (the gauge content of the
+manual's lphi4SU2U1 example, Sec. 4; links and plaquettes of the SU(N)
+toolkit, Sec. 4.2).
+
+What fixes the oracle here, independently of its own formulas:
+  * the closed-form SU(2) exponential against scipy's matrix exponential;
+  * both lattice Gauss laws conserved to roundoff on random non-Abelian
+    states (they are the generators of the gauge symmetry; a wrong sign,
+    ordering or transport in any kernel breaks them);
+  * gauge covariance under a random SU(2) x U(1) transformation;
+  * second-order energy conservation without expansion, and reversibility;
+  * the Abelian embedding: with the doublet's lower component zero, the
+    U(1) field off and diagonal links, the model is the U(1) model with
+    charge gQB/2, whose oracle is pinned separately -- fields, momenta,
+    links and the self-consistent a(t) agree to roundoff;
+  * free transverse waves of one colour obey the lattice dispersion with the
+    exact Stoermer-Verlet phase;
+  * the Gauss-law initial momenta, and the doublet's initial fluctuations
+    reducing to the U(1) model's for its upper component.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.inputs import su2_doublet_state
+
+SIG = [np.array([[0, 1], [1, 0]], complex), np.array([[0, -1j], [1j, 0]]),
+       np.array([[1, 0], [0, -1]], complex)]
+
+
+def mat(q):
+    """2x2 matrices (..., 2, 2) of quaternion arrays q[0..3] (U = u0 - i u.sigma)."""
+    m = q[0][..., None, None] * np.eye(2)
+    for a in range(3):
+        m = m - 1j * q[a + 1][..., None, None] * SIG[a]
+    return m
+
+
+def quat(m):
+    return [0.5 * (m[..., 0, 0].real + m[..., 1, 1].real), -0.5 * (m[..., 0, 1].imag + m[..., 1, 0].imag),
+            0.5 * (m[..., 1, 0].real - m[..., 0, 1].real), 0.5 * (m[..., 1, 1].imag - m[..., 0, 0].imag)]
+
+
+def su2_lattice(N=8, dt=0.02, integ=O.VV2, expansion=O.EXP_OFF, gQ=0.6, gQB=0.8, fo=1.3, amp=1e-2,
+                seed=7, phi=0.5, dphi=0.1):
+    p = O.make_params(dt=dt, integrator=integ, lam=1.0, v=0.5, gQ=gQ, gQB=gQB, fstar_over_omegastar=fo,
+                      fluct_amp2=amp, phi0=[phi] * 4, dphi0=[dphi] * 4, expansion=expansion,
+                      fstar_over_mp=0.5)
+    return O.Oracle(O.MODEL_SU2U1_HIGGS, N, 0.8, 1.0, seed, p)
+
+
+def load(L, arrays):
+    for a, x in enumerate(arrays):
+        L.set_array(a, x)
+
+
+def dump(L):
+    return [L.get_array(a).copy() for a in range(35)]
+
+
+def test_su2_exponential_matches_expm(oracle_mod):
+    from scipy.linalg import expm
+    rng = np.random.default_rng(3)
+    for th in [np.zeros(3), np.array([1e-9, 0, 0])] + [rng.normal(size=3) * s for s in (0.1, 1.0, 4.0)]:
+        u = O.su2_exp(th)
+        ref = expm(-0.5j * sum(t * s for t, s in zip(th, SIG)))
+        assert np.abs(mat([np.array(x) for x in u]) - ref).max() < 1e-14
+        assert abs(np.sum(u ** 2) - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("integ,expansion", [(O.VV2, O.EXP_OFF), (O.VV4, O.EXP_SELF), (O.LF, O.EXP_OFF)])
+def test_gauss_laws_conserved_on_random_states(oracle_mod, integ, expansion):
+    N = 8
+    L = su2_lattice(N=N, integ=integ, expansion=expansion)
+    load(L, su2_doublet_state(N, 11))
+    r0 = [L.gauss_residual(g).copy() for g in range(4)]
+    assert min(np.abs(r).max() for r in r0) > 0.1  # a random state violates the laws: they must not change
+    L.step(6)
+    for g in range(4):
+        assert np.abs(L.gauss_residual(g) - r0[g]).max() < 2e-13, g
+    # the links moved far from where they started and stay unitary
+    u = [L.get_array(14 + k) for k in range(4)]
+    assert np.abs(sum(x * x for x in u) - 1.0).max() < 1e-14
+
+
+def test_initial_momenta_satisfy_gauss(oracle_mod):
+    L = su2_lattice(amp=3e-2)
+    rel, lhs, rhs, mx = L.gauss()
+    assert rhs > 1e-4 and rel < 1e-13 and mx < 1e-13
+    assert np.abs(L.get_array(26)).max() > 1e-5       # SU(2) electric field from the Gauss law
+    for i in range(3):                                # links start at the identity (eqs. Inflc1-2)
+        assert (L.get_array(14 + 4 * i) == 1.0).all()
+        for k in range(1, 4):
+            assert (L.get_array(14 + 4 * i + k) == 0.0).all()
+    L.step(40)
+    assert L.gauss()[0] < 1e-12
+
+
+def test_doublet_ic_upper_component_is_the_u1_ic(oracle_mod):
+    N, kIR, seed = 8, 0.8, 5
+    kw = dict(fluct_amp2=0.5, lam=1.0, v=0.5, gQ=0.6, fstar_over_omegastar=1.3, phi0=[0.7, 0.3, 0.0, 0.0],
+              dphi0=[0.1, -0.2, 0.0, 0.0])
+    idx = np.arange(N ** 3, dtype=np.int64)
+    a = O.ic_sample(O.MODEL_U1_HIGGS, N, kIR, 1.0, seed, O.make_params(**kw), idx)
+    b = O.ic_sample(O.MODEL_SU2U1_HIGGS, N, kIR, 1.0, seed, O.make_params(gQB=0.8, **kw), idx)
+    for x, y in zip(a, b):                     # F and G
+        assert x.shape[1] == 2 and y.shape[1] == 4
+        assert np.array_equal(x, y[:, :2])
+        assert np.abs(y[:, 2:]).max() > 0      # the lower component fluctuates too
+
+
+def test_energy_conservation_second_order(oracle_mod):
+    N, T, errs = 8, 0.4, []
+    for dt in (0.04, 0.02, 0.01):
+        L = su2_lattice(N=N)
+        load(L, su2_doublet_state(N, 3))
+        r0 = L.energies()["rho"]
+        L.step(int(round(T / dt)), h=dt)
+        errs.append(abs(L.energies()["rho"] - r0))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert abs(math.log(e0 / e1, 2) - 2.0) < 0.05, errs
+
+
+def test_reversibility(oracle_mod):
+    N = 8
+    L = su2_lattice(N=N, integ=O.VV4, expansion=O.EXP_SELF)
+    load(L, su2_doublet_state(N, 4))
+    s0 = dump(L)
+    L.step(10, h=0.03)
+    L.step(10, h=-0.03)
+    for x, y in zip(s0, dump(L)):
+        assert np.abs(x - y).max() < 1e-12
+
+
+def gauge_transform(arrays, om, beta, gQ, dx):
+    """G(n) = exp(i beta(n)) Omega(n) applied to a doublet-model state (numpy, [z][y][x])."""
+    out = [x.copy() for x in arrays]
+    Om = mat(om)
+    ph = np.exp(1j * beta)
+    for base in (0, 4):  # doublet and its momentum
+        psi = np.stack([arrays[base] + 1j * arrays[base + 1], arrays[base + 2] + 1j * arrays[base + 3]], -1)
+        g = ph[..., None] * np.einsum("...ij,...j->...i", Om, psi)
+        out[base], out[base + 1], out[base + 2], out[base + 3] = g[..., 0].real, g[..., 0].imag, g[..., 1].real, g[..., 1].imag
+    for i, ax in enumerate((2, 1, 0)):
+        out[8 + i] = arrays[8 + i] + (np.roll(beta, -1, axis=ax) - beta) / (gQ * dx)
+        U = mat(arrays[14 + 4 * i: 18 + 4 * i])
+        Op = np.roll(Om, -1, axis=ax)
+        Un = Om @ U @ np.conj(np.swapaxes(Op, -1, -2))
+        out[14 + 4 * i: 18 + 4 * i] = quat(Un)
+        P = sum(arrays[26 + 3 * i + a][..., None, None] * SIG[a] / 2 for a in range(3))
+        Pn = Om @ P @ np.conj(np.swapaxes(Om, -1, -2))
+        for a in range(3):
+            out[26 + 3 * i + a] = np.einsum("...ij,ji->...", Pn, SIG[a]).real
+    return out
+
+
+def test_gauge_covariance(oracle_mod):
+    N, gQ = 8, 0.6
+    dx = 2 * np.pi / (N * 0.8)
+    rng = np.random.default_rng(21)
+    om = rng.standard_normal((4, N, N, N))
+    om /= np.sqrt((om ** 2).sum(0))
+    beta = rng.standard_normal((N, N, N))
+    s = su2_doublet_state(N, 8)
+    L1, L2 = su2_lattice(N=N, gQ=gQ, expansion=O.EXP_SELF), su2_lattice(N=N, gQ=gQ, expansion=O.EXP_SELF)
+    load(L1, s)
+    load(L2, gauge_transform(s, om, beta, gQ, dx))
+    e1, e2 = L1.energies(), L2.energies()
+    for k in ("EK", "EG", "EV"):
+        assert abs(e1[k][0] - e2[k][0]) < 1e-13 * abs(e1[k][0])
+    for k in ("EKA", "EGA", "EKB", "EGB"):
+        assert abs(e1[k] - e2[k]) < 1e-13 * abs(e1[k])
+    L1.step(8)
+    L2.step(8)
+    assert abs(L1.scalars()[1] - L2.scalars()[1]) < 1e-14 and L1.scalars()[1] != 1.0
+    ref = gauge_transform(dump(L1), om, beta, gQ, dx)
+    got = dump(L2)
+    for a in range(35):
+        assert np.abs(ref[a] - got[a]).max() < 1e-11, a
+    # links rotated the other way round, U -> Omega^dag(n) U Omega(n+i), with
+    # the doublet rotated by Omega: not a symmetry
+    L3 = su2_lattice(N=N, gQ=gQ)
+    bad = gauge_transform(s, om, beta, gQ, dx)
+    for i, ax in enumerate((2, 1, 0)):
+        U = mat(s[14 + 4 * i: 18 + 4 * i])
+        Om = mat(om)
+        bad[14 + 4 * i: 18 + 4 * i] = quat(np.conj(np.swapaxes(Om, -1, -2)) @ U @ np.roll(Om, -1, axis=ax))
+    load(L3, bad)
+    assert abs(L3.energies()["EG"][0] - e1["EG"][0]) > 1e-3 * e1["EG"][0]
+
+
+@pytest.mark.parametrize("integ,expansion", [(O.VV2, O.EXP_OFF), (O.VV4, O.EXP_SELF)])
+def test_abelian_embedding_is_the_u1_model(oracle_mod, integ, expansion):
+    N, g1, fo = 8, 0.45, 1.3
+    kIR = 0.8
+    dx = 2 * np.pi / (N * kIR)
+    rng = np.random.default_rng(4)
+    phi = [0.8 + 0.2 * rng.standard_normal((N, N, N)), 0.6 + 0.2 * rng.standard_normal((N, N, N))]
+    pi = [0.3 * rng.standard_normal((N, N, N)) for _ in range(2)]
+    A = [0.3 * rng.standard_normal((N, N, N)) for _ in range(3)]
+    pA = [0.3 * rng.standard_normal((N, N, N)) for _ in range(3)]
+    common = dict(dt=0.03, integrator=integ, lam=1.0, v=0.5, fstar_over_omegastar=fo, expansion=expansion,
+                  fstar_over_mp=0.5, phi0=[0.8, 0.6])
+    u1 = O.Oracle(O.MODEL_U1_HIGGS, N, kIR, 1.0, 1, O.make_params(gQ=g1, **common))
+    su = O.Oracle(O.MODEL_SU2U1_HIGGS, N, kIR, 1.0, 1, O.make_params(gQ=0.0, gQB=2 * g1, **common))
+    for f in range(2):
+        u1.set(f, 0, phi[f]); u1.set(f, 1, pi[f])
+    for i in range(3):
+        u1.set(2 + i, 0, A[i]); u1.set(2 + i, 1, pA[i])
+    zero = np.zeros((N, N, N))
+    arrays = [phi[0], phi[1], zero, zero, pi[0], pi[1], zero, zero] + [zero] * 6
+    for i in range(3):
+        th = g1 * dx * A[i]
+        arrays += [np.cos(th), zero, zero, np.sin(th)]
+    for i in range(3):
+        arrays += [zero, zero, pA[i]]
+    load(su, arrays)
+    _, a0, b0 = u1.scalars()
+    su.set_scalars(0.0, a0, b0)
+    e1, e2 = u1.energies(), su.energies()
+    assert abs(e1["EGA"] - e2["EGB"]) < 1e-13 * e1["EGA"] and abs(e1["EKA"] - e2["EKB"]) < 1e-13 * e1["EKA"]
+    assert abs(e1["EG"][0] - e2["EG"][0]) < 1e-13 * e1["EG"][0]
+    u1.step(12)
+    su.step(12)
+    assert abs(u1.scalars()[1] - su.scalars()[1]) < 1e-13
+    assert abs(u1.scalars()[2] - su.scalars()[2]) < 1e-13
+    tol = 1e-11
+    for f in range(2):
+        assert np.abs(su.get_array(f) - u1.get(f, 0)).max() < tol
+        assert np.abs(su.get_array(4 + f) - u1.get(f, 1)).max() < tol
+    for i in range(3):
+        th = g1 * dx * u1.get(2 + i, 0)
+        assert np.abs(su.get_array(14 + 4 * i) - np.cos(th)).max() < tol
+        assert np.abs(su.get_array(17 + 4 * i) - np.sin(th)).max() < tol
+        assert np.abs(su.get_array(28 + 3 * i) - u1.get(2 + i, 1)).max() < tol
+        for a in (26 + 3 * i, 27 + 3 * i, 15 + 4 * i, 16 + 4 * i, 8 + i, 11 + i):
+            assert np.abs(su.get_array(a)).max() == 0.0
+    for a in (2, 3, 6, 7):
+        assert np.abs(su.get_array(a)).max() == 0.0
+
+
+def verlet_matrix(w2, h):
+    kick = np.array([[1.0, 0.0], [-0.5 * h * w2, 1.0]])
+    drift = np.array([[1.0, h], [0.0, 1.0]])
+    return kick @ drift @ kick
+
+
+@pytest.mark.parametrize("integ", [O.LF, O.VV4])
+def test_free_colour_wave_dispersion(oracle_mod, integ):
+    """Doublet and U(1) field off: a small transverse wave of colour 1 in the
+    y-links obeys the lattice dispersion 2 sin(k dx/2)/dx with the
+    integrator's exact phase."""
+    N, h, nsteps, eps, gB = 16, 0.1, 30, 1e-6, 0.9
+    dx = 2 * np.pi / N
+    p = O.make_params(dt=h, integrator=integ, lam=1.0, v=0.0, gQ=0.0, gQB=gB, phi0=[0.0] * 4)
+    L = O.Oracle(O.MODEL_SU2U1_HIGGS, N, 1.0, 1.0, 1, p)
+    x = np.arange(N)[None, None, :] * np.ones((N, N, 1))
+    wave = eps * np.cos(2 * np.pi * 2 * x / N)
+    half = 0.5 * gB * dx * wave
+    L.set_array(18, np.cos(half))     # U_y = exp(-i gB dx B sigma_1/2)
+    L.set_array(19, np.sin(half))
+    L.step(nsteps)
+    w2 = (2.0 * np.sin(np.pi * 2 / N) / dx) ** 2
+    M = np.eye(2)
+    for d in O.schedule(integ, h):
+        M = verlet_matrix(w2, d) @ M
+    st = np.linalg.matrix_power(M, nsteps) @ np.array([1.0, 0.0])
+    B = 2.0 * np.arcsin(L.get_array(19)) / (gB * dx)
+    assert np.abs(B - st[0] * wave).max() < 1e-8 * eps
+    assert np.abs(L.get_array(29) - st[1] * wave).max() < 1e-8 * eps
+    for a in (20, 21, 30, 31):
+        assert np.abs(L.get_array(a)).max() == 0.0
