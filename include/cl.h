@@ -61,7 +61,9 @@ typedef enum {
 
 enum { CL_MODEL_LPHI4 = 1,      /* V = phi^4/4                              (eq. PotNat, chi = 0) */
        CL_MODEL_LPHI4_CHI = 2,  /* V = phi^4/4 + (q/2) phi^2 chi^2          (eq. PotNat) */
-       CL_MODEL_U1_HIGGS = 3 }; /* V = lam (|phi|^2 - v^2)^2 + U(1) links    (Sec. 4) */
+       CL_MODEL_U1_HIGGS = 3,   /* V = lam (|phi|^2 - v^2)^2 + U(1) links    (Sec. 4) */
+       CL_MODEL_SU2U1_HIGGS = 4 }; /* doublet Phi, V = lam (|Phi|^2 - v^2)^2, U(1) and SU(2)
+                                      links: the gauge content of the lphi4SU2U1 example (Sec. 4) */
 
 enum { CL_LF = 0, CL_VV2 = 2, CL_VV4 = 4, CL_VV6 = 6, CL_VV8 = 8, CL_VV10 = 10 };
 enum { CL_FP64 = 0,             /* fields, momenta and arithmetic in FP64 */
@@ -79,9 +81,9 @@ typedef struct {
   double fstar_over_mp;         /* f_s/m_p in the Friedmann equations */
   double phi0[4];               /* homogeneous initial values (per field / component) */
   double dphi0[4];              /* homogeneous initial phi' */
-  double lam, v;                /* U(1) model potential lam (|phi|^2 - v^2)^2 */
-  double gQ;                    /* U(1) coupling times charge */
-  double fstar_over_omegastar;  /* f_s/omega_s (U(1) model) */
+  double lam, v;                /* gauge models: potential lam (|phi|^2 - v^2)^2 */
+  double gQ;                    /* U(1) coupling times charge (g_A Q_A); doublet model: 0 = no U(1) field */
+  double fstar_over_omegastar;  /* f_s/omega_s (gauge models) */
   double kcut;                  /* initial-spectrum cutoff (eq. kCutOff); < 0 = none */
   double omega_eos;             /* fixed background: equation of state w */
   double H0;                    /* fixed background: initial a'/a; <= 0 -> Hubble law */
@@ -94,6 +96,7 @@ typedef struct {
                                    candidates on the device (cached per model, precision, N) */
   int tile_by;                  /* > 0: force this tile height (rows per CTA tile) for every
                                    lattice; 0: autotune or the built-in choice */
+  double gQB;                   /* SU(2) coupling times charge (g_B Q_B), CL_MODEL_SU2U1_HIGGS */
 } cl_params;
 
 /* Volume averages at a synchronised time (eqs. EK_EG_EV, energy-contrib). */
@@ -107,6 +110,7 @@ typedef struct {
   double energy_cons;           /* 1 - rho/rho(t0) (meaningful without expansion) */
   double mean_phi[4], mean_phi2[4], mean_pi[4], mean_pi2[4];
   int64_t nonfinite;            /* number of non-finite momenta seen in the last measurement */
+  double EKB, EGB;              /* SU(2) electric / magnetic energy (doublet model) */
 } cl_energies_t;
 
 /* Create a lattice of N^3 sites with kIR (so dx = 2 pi/(N kIR)), alpha of
@@ -134,6 +138,11 @@ cl_status cl_energies(cl_ctx* ctx, cl_energies_t* out);
 
 /* U(1) Gauss-law monitor (Sec. 4.5, average_gauss): LHS = sum_i grad^-_i pi_A,i,
  * RHS = (f_s/omega_s)^2 2 gQ Im[phi^* pi_phi]; rel = <|L-R|>/<|L+R|>.
+ * Doublet model: the sums run over the U(1) law and the three SU(2) laws
+ *   sum_i [pi_B,i^a(n) - (U_i^dag(n-i) pi_B,i(n-i) U_i(n-i))^a]/dx
+ *     = (f_s/omega_s)^2 (gQB/2) Im[psi^dag sigma_a pi_psi],   psi = sqrt2 Phi,
+ * with pi_B = pi_B^b sigma_b/2 and X^a = Tr[sigma_a X] (SU(N) toolkit,
+ * eq. GaussSU2-eom on the lattice).
  * CL_EUNSUPPORTED for models without links.  Synchronises the stream. */
 cl_status cl_gauss_constraint(cl_ctx* ctx, double* rel, double* lhs_abs, double* rhs_abs,
                               double* max_abs);
@@ -149,9 +158,22 @@ cl_status cl_spectrum(cl_ctx* ctx, int field, int what, double dk_bin, double* k
 
 /* Copy one lattice array to / from the host as FP64 (N^3 values).  Both
  * synchronise the kick stream first; set_state stores in the context's
- * precision. */
+ * precision.  Fields: scalar models f < nf; U(1) model 0,1 = phi_0, phi_1 and
+ * 2,3,4 = A_i; doublet model 0..3 = the components of
+ * Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt2 and 4,5,6 = A_i. */
 cl_status cl_get_state(cl_ctx* ctx, int field, int what, double* host_out);
 cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
+
+/* Doublet model: whole arrays by index, in the order
+ *   0..3 phi_c, 4..7 pi_c, 8..10 A_i, 11..13 pi_A,i,
+ *   14 + 4 i + k: component u_k of the SU(2) link U_i(n) = u0 - i (u1 s1 + u2 s2 + u3 s3)
+ *                 (s_a the Pauli matrices; U_i = exp(-i gQB dx B_i^a s_a/2)),
+ *   26 + 3 i + (a - 1): link momentum pi_B,i^a,
+ * N^3 FP64 values, x fastest.  Links are stored as given (a caller that sets
+ * them keeps them unitary).  CL_EUNSUPPORTED for other models, CL_EINVAL for
+ * a bad index.  Both synchronise the kick stream first. */
+cl_status cl_get_array(cl_ctx* ctx, int a, double* host_out);
+cl_status cl_set_array(cl_ctx* ctx, int a, const double* host_in);
 
 /* Scale factor, its derivative and the time.  cl_set_scalars also resets the
  * reference energy of energy_cons to the current state. */

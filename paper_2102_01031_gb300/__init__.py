@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libclgb300.so")
 
 CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ESTATE, CL_ETIMEOUT, CL_ENONFINITE, CL_EUNSUPPORTED = range(8)
-MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS = 1, 2, 3
+MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS = 1, 2, 3, 4
 LF, VV2, VV4, VV6, VV8, VV10 = 0, 2, 4, 6, 8, 10
 FP64, FP32 = 0, 1
 EXP_OFF, EXP_SELF, EXP_FIXED = 0, 1, 2
@@ -35,6 +35,7 @@ EXPORTS = (
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
+    "cl_get_array", "cl_set_array",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -67,6 +68,7 @@ class Params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("autotune", ctypes.c_int),
         ("tile_by", ctypes.c_int),
+        ("gQB", ctypes.c_double),
     ]
 
 
@@ -81,6 +83,7 @@ class Energies(ctypes.Structure):
         ("mean_phi", ctypes.c_double * 4), ("mean_phi2", ctypes.c_double * 4),
         ("mean_pi", ctypes.c_double * 4), ("mean_pi2", ctypes.c_double * 4),
         ("nonfinite", ctypes.c_int64),
+        ("EKB", ctypes.c_double), ("EGB", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -121,6 +124,8 @@ def lib():
                               ctypes.POINTER(ctypes.c_int)]
     L.cl_get_state.argtypes = [vp, ip, ip, dp]
     L.cl_set_state.argtypes = [vp, ip, ip, dp]
+    L.cl_get_array.argtypes = [vp, ip, dp]
+    L.cl_set_array.argtypes = [vp, ip, dp]
     L.cl_get_scalars.argtypes = [vp, dp, dp, dp]
     L.cl_set_scalars.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.cl_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -187,6 +192,7 @@ def make_params(**kw):
     p.precision = kw.pop("precision", FP64)
     p.autotune = int(kw.pop("autotune", 0))
     p.tile_by = int(kw.pop("tile_by", 0))
+    p.gQB = kw.pop("gQB", 0.5)
     st = kw.pop("stream", None)
     p.stream = ctypes.c_void_p(int(st) if st else 0)
     if kw:
@@ -266,6 +272,18 @@ class Lattice:
         if a.size != self.V:
             raise ValueError("need %d values" % self.V)
         _check(self.L, self.h, self.L.cl_set_state(self.h, field, what, _dp(a)), "cl_set_state")
+
+    def get_array(self, a):
+        """cl_get_array (doublet model): array `a` of the state as [z][y][x]."""
+        out = np.empty(self.V, dtype=np.float64)
+        _check(self.L, self.h, self.L.cl_get_array(self.h, a, _dp(out)), "cl_get_array")
+        return out.reshape(self.N, self.N, self.N)
+
+    def set_array(self, a, arr):
+        x = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+        if x.size != self.V:
+            raise ValueError("need %d values" % self.V)
+        _check(self.L, self.h, self.L.cl_set_array(self.h, a, _dp(x)), "cl_set_array")
 
     def scalars(self):
         e, a, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -27,6 +27,14 @@ namespace clg {
 typedef void (*PassKernel)(const PassArgs);
 PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red);
+PassKernel su2_pass_kernel(int fp32, int red);
+size_t su2_smem_bytes(int TX, int TY, int esz);
+cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
+cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
+                           cudaStream_t st);
+cudaError_t launch_su2_gauss_monitor(int fp32, const LatConst* L, int parity, double* part, int nblk,
+                                     long long V, cudaStream_t st);
+constexpr int SU2_PARTIALS = 24;  // partial sums per CTA of the doublet-model pass
 
 cudaError_t launch_init_scalars(const LatConst*, LatScalars*, const ICArgs&, cudaStream_t);
 cudaError_t launch_ic_modes(double2*, double2*, const LatConst*, const LatScalars*, const ICArgs&,
@@ -132,6 +140,7 @@ struct cl_ctx {
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
+  int su2_tx = 0, su2_ty = 0;      // doublet model: CTA tile (x, y) of the pass
   // schedule state
   int parity = 0;
   bool open = false;
@@ -221,6 +230,7 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
 }
 
 PassKernel pick_kernel(const cl_ctx* c, int red) {
+  if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red);
   if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red);
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
@@ -329,7 +339,8 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   A.gsync = nullptr;
   A.log = log;
   A.log_base = log_base;
-  const bool multi = n > 1 && c->coop;
+  const bool su2 = c->model == CL_MODEL_SU2U1_HIGGS;
+  const bool multi = n > 1 && c->coop && !su2;
   cudaGraphExec_t exec = nullptr;
   if (multi) {
     const PassStep* dev = nullptr;
@@ -396,7 +407,8 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
       A.dnext = st[i].dnext;
       A.parity = c->parity ^ (write ? (i & 1) : 0);
       A.log_base = log_base + i;
-      k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
+      if (su2) k<<<c->grid, dim3(c->su2_tx, c->su2_ty), c->smem_bytes, c->stream>>>(A);
+      else k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
       CHECK_LAUNCH();
     }
   }
@@ -538,12 +550,17 @@ __global__ void b_from_obs_kernel(const LatConst* Lc, LatScalars* S) {
 }  // namespace clg
 
 static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const uint64_t* seeds);
+static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed);
+static cl_status init_finish(cl_ctx* c);
 
 extern "C" {
 
 const char* cl_last_error(const cl_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 
-int cl_nfields(const cl_ctx* c) { return c ? c->narr / 2 : -1; }
+int cl_nfields(const cl_ctx* c) {
+  if (!c) return -1;
+  return c->model == CL_MODEL_SU2U1_HIGGS ? 7 : c->narr / 2;  // doublet: 4 components + 3 U(1) link fields
+}
 
 int cl_ensemble_size(const cl_ctx* c) { return c ? c->nlat : -1; }
 
@@ -589,8 +606,10 @@ cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, co
   if (!p || !Ns || !kIRs || !seeds) return fail(nullptr, CL_EINVAL, "NULL argument");
   if (count < 1 || count > CL_MAX_LATTICES)
     return fail(nullptr, CL_EINVAL, "count=%d: need 1..%d lattices", count, CL_MAX_LATTICES);
-  if (model < CL_MODEL_LPHI4 || model > CL_MODEL_U1_HIGGS)
+  if (model < CL_MODEL_LPHI4 || model > CL_MODEL_SU2U1_HIGGS)
     return fail(nullptr, CL_EINVAL, "unknown model %d", model);
+  if (model == CL_MODEL_SU2U1_HIGGS && count != 1)
+    return fail(nullptr, CL_EUNSUPPORTED, "the doublet model runs one lattice per context");
   for (int l = 0; l < count; ++l) {
     if (!good_N(Ns[l]))
       return fail(nullptr, CL_EINVAL, "N=%d: need 8 <= N <= 512, N %% 8 == 0, factors 2,3", Ns[l]);
@@ -607,11 +626,16 @@ cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, co
   if (!(p->dt == p->dt)) return fail(nullptr, CL_EINVAL, "dt is NaN");
   if (model == CL_MODEL_U1_HIGGS && !(p->gQ != 0.0 && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
     return fail(nullptr, CL_EINVAL, "U(1) needs a finite nonzero gQ and f*/omega*");
+  if (model == CL_MODEL_SU2U1_HIGGS &&
+      !(p->gQB != 0.0 && std::isfinite(p->gQB) && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
+    return fail(nullptr, CL_EINVAL, "the doublet model needs a finite nonzero gQB, a finite gQ and f*/omega*");
+  if (model == CL_MODEL_SU2U1_HIGGS && Ns[0] % 16)
+    return fail(nullptr, CL_EUNSUPPORTED, "the doublet model needs N a multiple of 16");
   if (p->tile_by < 0) return fail(nullptr, CL_EINVAL, "tile_by must be >= 0");
   cl_ctx* c = new cl_ctx();
   c->model = model;
-  c->nf = model == CL_MODEL_LPHI4 ? 1 : 2;
-  c->narr = model == CL_MODEL_U1_HIGGS ? 10 : 2 * c->nf;
+  c->nf = model == CL_MODEL_LPHI4 ? 1 : (model == CL_MODEL_SU2U1_HIGGS ? 4 : 2);
+  c->narr = model == CL_MODEL_U1_HIGGS ? 10 : (model == CL_MODEL_SU2U1_HIGGS ? 35 : 2 * c->nf);
   c->fp32 = p->precision == CL_FP32;
   c->esz = c->fp32 ? 4 : 8;
   c->nlat = count;
@@ -642,6 +666,11 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
   c->smem_optin = (size_t)optin;
   CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (c->model == CL_MODEL_SU2U1_HIGGS) {
+    cl_status s = su2_init(c, Ns[0], kIRs[0], seeds[0]);
+    if (s != CL_OK) return s;
+    return init_finish(c);
+  }
   const bool u1 = c->model == CL_MODEL_U1_HIGGS;
   // lattices and their tile heights: full x-rows of N/VX threads, BY rows
   // per CTA (BY divides N); given, autotuned, or the tallest that leaves at
@@ -830,6 +859,11 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
       }
     }
   }
+  return init_finish(c);
+}
+
+// Initial measurement (and, with b0_mode 1, a' from the lattice averages).
+static cl_status init_finish(cl_ctx* c) {
   c->parity = 0;
   c->open = false;
   cl_status s = measure(c, 1);
@@ -846,6 +880,137 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   }
   CU(cudaStreamSynchronize(c->stream));
   return check_status(c);
+}
+
+
+// Doublet model: one lattice, 35 arrays per buffer; the pass tiles x-y by
+// TX x TY (TX = 32, or 16 when N is not a multiple of 32; TY = 8) and runs as
+// many CTAs as are resident at once.  Initial conditions: the doublet's four
+// components drawn like the U(1) field's (eqs. InConstr:1-2 for n = 0..3),
+// links at the identity (eqs. Inflc1-2), and link momenta solving the U(1)
+// and the three SU(2) lattice Gauss laws (eq. GaugeCurrentFluc with the
+// backward-difference symbol; at the identity the laws are linear).
+static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
+  c->lats.resize(1);
+  LatHost& H = c->lats[0];
+  H.N = N;
+  H.V = (long long)N * N * N;
+  H.kIR = kIR;
+  H.dx = 2.0 * M_PI / ((double)N * kIR);
+  H.seed = seed;
+  H.BY = 0;
+  c->vmax = H.V;
+  c->su2_tx = N % 32 == 0 ? 32 : 16;
+  c->su2_ty = 8;
+  c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz);
+  if (c->smem_bytes > c->smem_optin) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
+  for (int red = 0; red < 3; ++red)
+    CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red),
+                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_bytes));
+  int nb = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c)),
+                                                   c->su2_tx * c->su2_ty, c->smem_bytes));
+  const long long tasks = (long long)(N / c->su2_tx) * (N / c->su2_ty) * N;
+  c->grid = (int)std::min<long long>(tasks, (long long)c->nsm * std::max(nb, 1));
+  c->nslot = c->grid;
+  c->stages = 3;
+  c->coop = false;
+  const size_t bytes = 2 * (size_t)c->narr * H.V * c->esz;
+  CU(cudaMalloc(&H.slab, bytes));
+  CU(cudaMemsetAsync(H.slab, 0, bytes, c->stream));
+  CU(cudaMalloc(&c->d_lat, sizeof(LatConst)));
+  CU(cudaMalloc(&c->d_sc, sizeof(LatScalars)));
+  CU(cudaMemsetAsync(c->d_sc, 0, sizeof(LatScalars), c->stream));
+  CU(cudaMalloc(&c->d_part, (size_t)SU2_PARTIALS * c->grid * sizeof(double)));
+  CU(cudaMalloc(&c->d_cnt, sizeof(unsigned)));
+  CU(cudaMemsetAsync(c->d_cnt, 0, sizeof(unsigned), c->stream));
+  c->hlat.resize(1);
+  LatConst& L = c->hlat[0];
+  memset(&L, 0, sizeof(L));
+  L.N = N;
+  L.model = c->model;
+  L.nf = c->nf;
+  L.narr = c->narr;
+  L.expansion = c->p.expansion;
+  L.slot_begin = 0;
+  L.slot_end = c->grid;
+  L.esz = c->esz;
+  L.int_alpha = (c->alpha == std::floor(c->alpha) && std::fabs(c->alpha) <= 4.0) ? 1 : 0;
+  L.alpha_i = L.int_alpha ? (int)c->alpha : 0;
+  L.inv_V = 1.0 / (double)H.V;
+  L.inv_dx2 = 1.0 / (H.dx * H.dx);
+  L.V = H.V;
+  L.dx = H.dx;
+  L.alpha = c->alpha;
+  L.q = c->p.q;
+  L.lam = c->p.lam;
+  L.v = c->p.v;
+  L.gQ = c->p.gQ;
+  L.gQB = c->p.gQB;
+  L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
+  L.omega_eos = c->p.omega_eos;
+  // the pass addresses array a of buffer p at buf[p][0] + a V
+  for (int par = 0; par < 2; ++par)
+    for (int a = 0; a < MAX_ARR; ++a) L.buf[par][a] = arr_ptr(c, 0, par, a);
+  CU(cudaMemcpyAsync(c->d_lat, &L, sizeof(LatConst), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMalloc(&c->d_cplx, 2 * (size_t)H.V * sizeof(double2)));
+  CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)H.V, 1 << 16) * sizeof(double)));
+  ICArgs A;
+  memset(&A, 0, sizeof(A));
+  for (int k = 0; k < 4; ++k) {
+    A.phi0[k] = c->p.phi0[k];
+    A.dphi0[k] = c->p.dphi0[k];
+  }
+  A.amp2 = c->p.fluct_amp2;
+  A.kcut = c->p.kcut;
+  A.kIR = H.kIR;
+  A.H0 = c->p.H0;
+  A.q = c->p.q;
+  A.lam = c->p.lam;
+  A.v = c->p.v;
+  A.seed = H.seed;
+  A.model = c->model;
+  A.nf = c->nf;
+  H.ic = A;
+  CU(launch_init_scalars(c->d_lat, c->d_sc, A, c->stream));
+  ++c->launches;
+  double2* F = c->d_cplx;
+  double2* G = c->d_cplx + H.V;
+  for (int f = 0; f < 4; ++f) {
+    CU(cudaMemsetAsync(c->d_cplx, 0, 2 * (size_t)H.V * sizeof(double2), c->stream));
+    CU(launch_ic_modes(F, G, c->d_lat, c->d_sc, A, f, H.V, c->stream));
+    ++c->launches;
+    cl_status s = fft3d(c, N, F, +1);
+    if (s != CL_OK) return s;
+    s = fft3d(c, N, G, +1);
+    if (s != CL_OK) return s;
+    CU(launch_ic_assemble(c->fp32, arr_ptr(c, 0, 0, f), arr_ptr(c, 0, 0, 4 + f), F, G, c->d_lat, c->d_sc,
+                          c->p.phi0[f], c->p.dphi0[f], H.V, c->stream));
+    ++c->launches;
+  }
+  CU(launch_su2_identity_links(c->fp32, arr_ptr(c, 0, 0, 0), H.V, c->stream));
+  ++c->launches;
+  double2* rho = c->d_cplx;
+  double2* E = c->d_cplx + H.V;
+  for (int g = 0; g < 4; ++g) {
+    if (g == 0 && c->p.gQ == 0.0) continue;  // no U(1) field: its momenta stay zero
+    CU(launch_su2_rho(c->fp32, c->d_lat, 0, g, rho, H.V, c->stream));
+    ++c->launches;
+    cl_status s = fft3d(c, N, rho, -1);
+    if (s != CL_OK) return s;
+    for (int i = 0; i < 3; ++i) {
+      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, H.dx, c->fp32, nullptr, H.V, 1, c->stream));
+      ++c->launches;
+      s = fft3d(c, N, E, +1);
+      if (s != CL_OK) return s;
+      const int a = g == 0 ? 11 + i : 26 + 3 * i + (g - 1);
+      CU(launch_u1_gauss_init(c->d_lat, 0, rho, E, N, i, H.dx, c->fp32, arr_ptr(c, 0, 0, a), H.V, 2,
+                              c->stream));
+      ++c->launches;
+    }
+  }
+  return CL_OK;
 }
 
 extern "C" {
@@ -912,8 +1077,33 @@ cl_status cl_energies(cl_ctx* c, cl_energies_t* out) { return cl_lattice_energie
 
 static cl_status array_index(cl_ctx* c, int field, int what, int* a) {
   if (what != 0 && what != 1) return fail(c, CL_EINVAL, "what must be 0 or 1");
+  if (c->model == CL_MODEL_SU2U1_HIGGS) {  // doublet components 0..3, U(1) link fields 4..6
+    if (field < 0 || field > 6) return fail(c, CL_EINVAL, "field %d out of range", field);
+    *a = field < 4 ? field + 4 * what : 8 + (field - 4) + 3 * what;
+    return CL_OK;
+  }
   if (field < 0 || field >= c->narr / 2) return fail(c, CL_EINVAL, "field %d out of range", field);
   *a = 2 * field + what;
+  return CL_OK;
+}
+
+// Array a of lattice 0 to / from the host (FP64), converting the storage precision.
+static cl_status copy_array(cl_ctx* c, int a, double* host_out, const double* host_in) {
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  const long long V = c->lats[0].V;
+  if (host_out) {
+    CU(launch_convert(c->fp32, 1, arr_ptr(c, 0, c->parity, a), c->d_tmp, V, c->stream));
+    ++c->launches;
+    CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return check_status(c);
+  }
+  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, 0, c->parity, a), V, c->stream));
+  ++c->launches;
+  CU(cudaStreamSynchronize(c->stream));
+  c->obs_valid = false;
   return CL_OK;
 }
 
@@ -952,6 +1142,20 @@ cl_status cl_lattice_set_state(cl_ctx* c, int lat, int field, int what, const do
 
 cl_status cl_get_state(cl_ctx* c, int field, int what, double* host_out) {
   return cl_lattice_get_state(c, 0, field, what, host_out);
+}
+
+cl_status cl_get_array(cl_ctx* c, int a, double* host_out) {
+  if (!c || !host_out) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->model != CL_MODEL_SU2U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet model");
+  if (a < 0 || a >= c->narr) return fail(c, CL_EINVAL, "array %d out of range", a);
+  return copy_array(c, a, host_out, nullptr);
+}
+
+cl_status cl_set_array(cl_ctx* c, int a, const double* host_in) {
+  if (!c || !host_in) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->model != CL_MODEL_SU2U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet model");
+  if (a < 0 || a >= c->narr) return fail(c, CL_EINVAL, "array %d out of range", a);
+  return copy_array(c, a, nullptr, host_in);
 }
 
 cl_status cl_set_state(cl_ctx* c, int field, int what, const double* host_in) {
@@ -1067,7 +1271,7 @@ cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, 
 cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double* k, double* n, int64_t* mult,
                         int cap, int* nbins) {
   if (!c || !k || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+  if (c->nlat != 1 || c->model >= CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "occupation numbers cover single scalar lattices");
   if (field < 0 || field >= c->nf) return fail(c, CL_EINVAL, "field %d out of range", field);
   if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
@@ -1210,12 +1414,16 @@ cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double*
 cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
                               double* max_abs) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
-  if (c->model != CL_MODEL_U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "model has no gauge field");
+  if (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS)
+    return fail(c, CL_EUNSUPPORTED, "model has no gauge field");
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
   const int nblk = 2 * c->nsm;
   double* part = c->d_tmp;
-  CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));
+  if (c->model == CL_MODEL_SU2U1_HIGGS)
+    CU(launch_su2_gauss_monitor(c->fp32, c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));
+  else
+    CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));
   c->launches += 2;
   double h[4];
   CU(cudaMemcpyAsync(h, part + 3 * nblk, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1397,7 +1605,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
                      int bin, double* J, double* dJ_dq, double* dJ_dstate, double* dJ_dscale) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, CL_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
-  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+  if (c->nlat != 1 || c->model >= CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "the adjoint covers single scalar lattices");
   const bool self = c->p.expansion == CL_EXP_SELF;
   if (objective == CL_OBJ_CHI_FRACTION) {
@@ -1616,7 +1824,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
 
 cl_status cl_ic_amplitude_grad(cl_ctx* c, const double* dJ_dstate, double* out) {
   if (!c || !dJ_dstate || !out) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->nlat != 1 || c->model == CL_MODEL_U1_HIGGS)
+  if (c->nlat != 1 || c->model >= CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "amplitude gradients cover single scalar lattices");
   if (c->p.expansion == CL_EXP_SELF && c->p.b0_mode == 1)
     return fail(c, CL_EUNSUPPORTED, "with a' from lattice averages the initial b depends on the amplitudes");

@@ -26,6 +26,7 @@ struct LatConst {
   double dx, alpha, q, lam, v, gQ, fo2, fm2, omega_eos;
   double inv_V, inv_dx2;
   double u1_gd, u1_cJ, u1_cC;  // U(1): gQ dx, (f_s/omega_s)^2 gQ/dx, 1/(gQ dx^3)
+  double gQB;                  // doublet model: SU(2) coupling times charge
   void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
 };
 

@@ -59,7 +59,9 @@ __device__ double pot_hom(const ICArgs& A) {
   if (A.model == CL_MODEL_LPHI4) return 0.25 * f[0] * f[0] * f[0] * f[0];
   if (A.model == CL_MODEL_LPHI4_CHI)
     return 0.25 * f[0] * f[0] * f[0] * f[0] + 0.5 * A.q * f[0] * f[0] * f[1] * f[1];
-  const double m2 = 0.5 * (f[0] * f[0] + f[1] * f[1]) - A.v * A.v;
+  double r2 = 0.0;  // |phi|^2 (|Phi|^2 for the doublet) = half the sum of squares of the components
+  for (int k = 0; k < A.nf; ++k) r2 += 0.5 * f[k] * f[k];
+  const double m2 = r2 - A.v * A.v;
   return A.lam * m2 * m2;
 }
 
@@ -68,7 +70,8 @@ __device__ double mass2_hom(const ICArgs& A, int k) {
   if (A.model == CL_MODEL_LPHI4) return 3.0 * f[0] * f[0];
   if (A.model == CL_MODEL_LPHI4_CHI)
     return k == 0 ? 3.0 * f[0] * f[0] + A.q * f[1] * f[1] : A.q * f[0] * f[0];
-  const double r2 = 0.5 * (f[0] * f[0] + f[1] * f[1]);
+  double r2 = 0.0;
+  for (int c = 0; c < A.nf; ++c) r2 += 0.5 * f[c] * f[c];
   return 2.0 * A.lam * (r2 - A.v * A.v) + 2.0 * A.lam * f[k] * f[k];
 }
 
@@ -120,14 +123,14 @@ __device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long lon
   const long long pid = px + (long long)N * (py + (long long)N * pz);
   *pid_out = pid;
   if (pid < idx) return false;
-  const bool charged = A.model == CL_MODEL_U1_HIGGS;
+  const bool charged = A.model == CL_MODEL_U1_HIGGS || A.model == CL_MODEL_SU2U1_HIGGS;
   if (pid == idx && charged) return false;  // keeps the charge density's zero mode at 0
   const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
   const double k = A.kIR * sqrt((double)(nx * nx + ny * ny + nz * nz));
   if (A.kcut >= 0.0 && k > A.kcut) return false;
   if (A.amp2 <= 0.0) return false;
   // every component must have a real frequency for the mode to be populated
-  double om[2] = {0.0, 0.0};
+  double om[4] = {0.0, 0.0, 0.0, 0.0};
   for (int c = 0; c < A.nf; ++c) {
     const double w2 = k * k + a * a * mass2_hom(A, c);
     if (w2 <= 0.0) return false;
@@ -145,7 +148,7 @@ __device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long lon
     t1 = 2.0 * v0;  // phases in units of pi
     t2 = 2.0 * v1;
   } else {
-    // eqs. InConstr:1-2: equal amplitudes per component, theta_12 = theta_02 + theta_11 - theta_01
+    // eqs. InConstr:1-2: equal amplitudes per component, theta_n2 = theta_02 + theta_n1 - theta_01
     double u0, u1, v0, v1;
     draw_pair(A.seed, (unsigned)idx, f, 0, u0, u1);
     r1 = r2 = sqrt(-P * log(u0));
@@ -155,7 +158,7 @@ __device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long lon
       t2 = 2.0 * v1;
     } else {
       double w0, w1;
-      draw_pair(A.seed, (unsigned)idx, 1, 1, w0, w1);  // theta_11
+      draw_pair(A.seed, (unsigned)idx, f, 1, w0, w1);  // theta_f1
       t1 = 2.0 * w0;
       t2 = 2.0 * v1 + 2.0 * w0 - 2.0 * v0;
     }

@@ -1,0 +1,761 @@
+// pass_su2.cu -- fused drift + kick pass of the SU(2) x U(1) doublet model
+// (the gauge content of the CosmoLattice manual's lphi4SU2U1 example: Sec. 4.1
+// action, Sec. 4.3 Hamiltonian form in temporal gauge, links, plaquettes and
+// covariant derivatives of the U(1) and SU(N) toolkits of Sec. 4.2).
+//
+// State (35 arrays of one slab, array a at a * V elements):
+//   0..3   phi_c, Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt2 (psi = sqrt2 Phi below)
+//   4..7   pi_c
+//   8..10  A_i (U(1) link fields, V_i = exp(-i gQ dx A_i)),   11..13 pi_A,i
+//   14 + 4 i + k   SU(2) link U_i = u0 - i (u1 s1 + u2 s2 + u3 s3) (s_a Pauli)
+//   26 + 3 i + (a - 1)   pi_B,i^a
+//
+//   drift (deferred from the previous pass):
+//       phi_c += cd pi_c,   A_i += cdA pi_A,i,
+//       U_i <- exp(-i (gQB dx cdA) pi_B,i^a s_a/2) U_i
+//   kick (W_i = V_i U_i, the doublet's hopping link):
+//       pi_c     += c_k [ a^{1+alpha} (D^2 psi)_c - a^{3+alpha} 2 lam (|Phi|^2 - v^2) phi_c ]
+//       pi_A,i   += c_k [ a^{1+alpha} (f_s/omega_s)^2 (gQ/dx) Im(psi^dag W_i psi(n+i)) + a^{alpha-1} C_i ]
+//       pi_B,i^a += c_k [ a^{1+alpha} (f_s/omega_s)^2 (gQB/(2dx)) Im(psi^dag s_a W_i psi(n+i))
+//                         - a^{alpha-1} (2/(gQB dx^3)) m_a(U_i S_i) ]
+//   with D^2 psi = sum_i [W_i psi(n+i) - 2 psi + W_i^dag(n-i) psi(n-i)]/dx^2, C_i the compact
+//   U(1) curl of the U(1) model, S_i the sum of the four staples of U_i(n) and m_a the
+//   vector part of a quaternion (Im Tr[s_a M] = -2 m_a).  These are the kernels of one
+//   lattice Hamiltonian (kinetic terms, covariant hopping, compact U(1) plaquettes,
+//   SU(2) plaquette traces), so that both lattice Gauss laws hold exactly.
+//
+// Kernel layout.  A CTA owns a TX x TY tile of x-y sites and marches a run of
+// z-planes of it.  Each plane of the tile plus a one-site halo (corners
+// included) is loaded from HBM, drifted in registers and kept, drifted, in a
+// three-plane shared-memory ring (links as one 16-byte quaternion per site
+// and direction, the doublet as one quaternion, the three U(1) link fields);
+// the drifted fields of the CTA's own sites are written out right away.  The
+// kick of plane z then reads every neighbour, staple and plaquette it needs
+// from the ring (the stencil reaches n +- x, n +- y, n +- z and the diagonal
+// neighbours n + i - j), and re-reads its own momenta (L2-resident).  The
+// plane-task list (tile-major, then z) is cut into equal contiguous runs, one
+// per resident CTA.  The last CTA to finish sums the per-CTA partial sums in
+// a fixed order and advances the scale factor (tail.cuh).
+#include "common.cuh"
+#include "tail.cuh"
+
+namespace clg {
+
+namespace {
+
+enum : int { SF = 0, SP = 4, SA = 8, SPA = 11, SU = 14, SPB = 26, SNARR = 35 };
+
+template <typename T> struct alignas(4 * sizeof(T)) Q4 {
+  T w, x, y, z;
+};
+
+// Quaternion algebra of the link convention U = u0 - i u.s:
+// (a0 - i a.s)(b0 - i b.s) = (a0 b0 - a.b) - i (a0 b + b0 a + a x b).s
+template <typename T>
+__device__ __forceinline__ Q4<T> qmul(const Q4<T>& a, const Q4<T>& b) {
+  Q4<T> r;
+  r.w = a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z;
+  r.x = a.w * b.x + b.w * a.x + (a.y * b.z - a.z * b.y);
+  r.y = a.w * b.y + b.w * a.y + (a.z * b.x - a.x * b.z);
+  r.z = a.w * b.z + b.w * a.z + (a.x * b.y - a.y * b.x);
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ Q4<T> qconj(const Q4<T>& a) {
+  Q4<T> r;
+  r.w = a.w;
+  r.x = -a.x;
+  r.y = -a.y;
+  r.z = -a.z;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void qadd(Q4<T>& s, const Q4<T>& a) {
+  s.w += a.w;
+  s.x += a.x;
+  s.y += a.y;
+  s.z += a.z;
+}
+
+// cos x and sin(x)/x.  FP32: for x^2 <= (pi/4)^2 their Taylor series about 0
+// in Horner form (first omitted terms below 3e-9 there), else the library;
+// the drift angles are small in practice.  FP64: the library.
+__device__ __forceinline__ void cos_sinc(float x2, float& c, float& sc) {
+  if (x2 <= 0.61685028f) {
+    c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
+                     -0.5f),
+             1.f);
+    sc = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
+  } else {
+    const float x = sqrtf(x2);
+    float s;
+    sincosf(x, &s, &c);
+    sc = s / x;
+  }
+}
+__device__ __forceinline__ void cos_sinc(double x2, double& c, double& sc) {
+  if (x2 == 0.0) {
+    c = 1.0;
+    sc = 1.0;
+    return;
+  }
+  const double x = sqrt(x2);
+  double s;
+  sincos(x, &s, &c);
+  sc = s / x;
+}
+
+// sin; FP32 as the U(1) pass (Taylor series about 0 for |x| <= pi/4).
+__device__ __forceinline__ float sin_t(float x) {
+  if (fabsf(x) <= 0.78539816f) {
+    const float x2 = x * x;
+    return x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
+  }
+  return sinf(x);
+}
+__device__ __forceinline__ double sin_t(double x) { return sin(x); }
+__device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
+  if (fabsf(x) <= 0.78539816f) {
+    const float x2 = x * x;
+    s = x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
+    c = fmaf(x2,
+             fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
+                  -0.5f),
+             1.f);
+  } else {
+    sincosf(x, &s, &c);
+  }
+}
+__device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
+
+// Renormalise a link to unit length (FP32 storage only: keeps the rounding
+// of repeated drifts from walking off the group; FP64 follows the plain
+// products).
+__device__ __forceinline__ void renorm(Q4<float>& u) {
+  const float r = rsqrtf(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
+  u.w *= r;
+  u.x *= r;
+  u.y *= r;
+  u.z *= r;
+}
+__device__ __forceinline__ void renorm(Q4<double>&) {}
+
+// U psi and U^dag psi for psi = (p, q) = (w + i x, y + i z) held in a quaternion slot
+template <typename T>
+__device__ __forceinline__ Q4<T> umul(const Q4<T>& u, const Q4<T>& f) {
+  Q4<T> r;
+  r.w = u.w * f.w + u.z * f.x - u.y * f.y + u.x * f.z;
+  r.x = u.w * f.x - u.z * f.w - u.y * f.z - u.x * f.y;
+  r.y = u.y * f.w + u.x * f.x + u.w * f.y - u.z * f.z;
+  r.z = u.y * f.x - u.x * f.w + u.w * f.z + u.z * f.y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ Q4<T> udmul(const Q4<T>& u, const Q4<T>& f) {
+  Q4<T> r;
+  r.w = u.w * f.w - u.z * f.x + u.y * f.y - u.x * f.z;
+  r.x = u.w * f.x + u.z * f.w + u.y * f.z + u.x * f.y;
+  r.y = -u.y * f.w - u.x * f.x + u.w * f.y + u.z * f.z;
+  r.z = -u.y * f.x + u.x * f.w + u.w * f.z - u.z * f.y;
+  return r;
+}
+// multiply both components by exp(-i t) given (c, s) = (cos t, sin t); (c, -s) gives exp(+i t)
+template <typename T>
+__device__ __forceinline__ void phase(Q4<T>& f, T c, T s) {
+  const T w = f.w * c + f.x * s, x = f.x * c - f.w * s;
+  const T y = f.y * c + f.z * s, z = f.z * c - f.y * s;
+  f.w = w;
+  f.x = x;
+  f.y = y;
+  f.z = z;
+}
+
+// 1 - w for a unit quaternion, without cancellation: |v|^2/(1 + w)
+template <typename T>
+__device__ __forceinline__ T one_minus_w(const Q4<T>& p) {
+  return (p.x * p.x + p.y * p.y + p.z * p.z) / (T(1) + p.w);
+}
+
+constexpr int SU2_NQ = 24;  // partial sums per CTA (the measurement pass uses 23)
+
+}  // namespace
+
+// Bytes of one ring slot: per halo site 3 links + doublet (quaternions) and 3 U(1) fields.
+__host__ __device__ inline size_t su2_slot_bytes(int TX, int TY, int esz) {
+  const size_t hs = (size_t)(TX + 2) * (TY + 2);
+  return (19 * hs * esz + 127) / 128 * 128;
+}
+
+// RED: 0 = no sums, 1 = sums for the Friedmann kicks, 2 = full measurement.
+template <typename T, int RED>
+__global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_pass_su2(const PassArgs P) {
+  constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 6 : 23);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red_s[SU2_NQ][9];
+  __shared__ unsigned last_s;
+  const LatConst& L = P.lat[0];
+  const int N = L.N;
+  const int TX = blockDim.x, TY = blockDim.y, nth = TX * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int HX = TX + 2, HS = HX * (TY + 2);
+  const int ntx = N / TX, nty = N / TY;
+  const long long NN = (long long)N * N, V = L.V;
+  const int parity = P.parity;
+  const T* const src = reinterpret_cast<const T*>(L.buf[parity][0]);
+  T* const dst = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
+  const size_t slot_b = su2_slot_bytes(TX, TY, sizeof(T));
+
+  // coefficients: FP64 products by one lane, broadcast in the storage precision
+  T cf[13];
+  if (lane == 0) {
+    const LatScalars* SC = P.sc;
+    const double ck = P.ck, ap1 = __ldcg(&SC->apow1), apm1 = __ldcg(&SC->apowm1);
+    const double cdA = __ldcg(&SC->cdA), dx = L.dx;
+    cf[0] = (T)__ldcg(&SC->cd);
+    cf[1] = (T)cdA;
+    cf[2] = (T)(0.5 * L.gQB * dx * cdA);                        // half the SU(2) drift angle per momentum
+    cf[3] = (T)(ck * ap1 * L.inv_dx2);                           // doublet Laplacian
+    cf[4] = (T)(ck * __ldcg(&SC->apow3));                        // potential force
+    cf[5] = (T)(ck * ap1 * L.fo2 * L.gQ / dx);                   // U(1) current
+    cf[6] = (T)(L.gQ != 0.0 ? -ck * apm1 / (L.gQ * dx * dx * dx) : 0.0);  // U(1) curl
+    cf[7] = (T)(ck * ap1 * L.fo2 * L.gQB / (2.0 * dx));          // SU(2) current
+    cf[8] = (T)(-2.0 * ck * apm1 / (L.gQB * dx * dx * dx));      // SU(2) plaquette force
+    cf[9] = (T)(L.gQ * dx);
+    cf[10] = (T)(L.v * L.v);
+    cf[11] = (T)L.lam;
+    cf[12] = (T)(2.0 * L.lam);
+  }
+#pragma unroll
+  for (int k = 0; k < 13; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
+  const T cd = cf[0], cdA = cf[1], hB = cf[2], A1 = cf[3], A3 = cf[4], AJA = cf[5], ACA = cf[6], AJB = cf[7],
+          AMB = cf[8], gd = cf[9], v2 = cf[10], lam = cf[11], lam2 = cf[12];
+  const bool drifting = cd != T(0) || cdA != T(0);
+
+  Acc<T> acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k].zero();
+  float nonfinite = 0.f;
+
+  // ring slot s: links [3][HS], doublet [HS], U(1) fields [3][HS]
+  auto sU = [&](int s, int i) { return reinterpret_cast<Q4<T>*>(smem + s * slot_b) + i * HS; };
+  auto sF = [&](int s) { return reinterpret_cast<Q4<T>*>(smem + s * slot_b) + 3 * HS; };
+  auto sA = [&](int s, int i) { return reinterpret_cast<T*>(smem + s * slot_b) + 16 * HS + i * HS; };
+
+  // load plane zp of tile (x0, y0) into slot s, drifted; own sites written out when `own`
+  auto load_plane = [&](int s, int x0, int y0, int zp, bool own) {
+    for (int k = tid; k < HS; k += nth) {
+      const int hx = k % HX, hy = k / HX;
+      const int gx = (x0 + hx - 1 + N) % N, gy = (y0 + hy - 1 + N) % N;
+      const long long g = (long long)zp * NN + (long long)gy * N + gx;
+      Q4<T> f, u[3];
+      T a[3];
+      f.w = src[SF * V + g];
+      f.x = src[(SF + 1) * V + g];
+      f.y = src[(SF + 2) * V + g];
+      f.z = src[(SF + 3) * V + g];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        a[i] = src[(SA + i) * V + g];
+        u[i].w = src[(SU + 4 * i) * V + g];
+        u[i].x = src[(SU + 4 * i + 1) * V + g];
+        u[i].y = src[(SU + 4 * i + 2) * V + g];
+        u[i].z = src[(SU + 4 * i + 3) * V + g];
+      }
+      if (drifting) {
+        f.w = fmaT(cd, src[SP * V + g], f.w);
+        f.x = fmaT(cd, src[(SP + 1) * V + g], f.x);
+        f.y = fmaT(cd, src[(SP + 2) * V + g], f.y);
+        f.z = fmaT(cd, src[(SP + 3) * V + g], f.z);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          a[i] = fmaT(cdA, src[(SPA + i) * V + g], a[i]);
+          // E = exp(-i hB pi.s) = (cos x, sin(x)/x hB pi), x = hB |pi|
+          const T p1 = hB * src[(SPB + 3 * i) * V + g], p2 = hB * src[(SPB + 3 * i + 1) * V + g],
+                  p3 = hB * src[(SPB + 3 * i + 2) * V + g];
+          T c, sc;
+          cos_sinc(p1 * p1 + p2 * p2 + p3 * p3, c, sc);
+          Q4<T> e;
+          e.w = c;
+          e.x = sc * p1;
+          e.y = sc * p2;
+          e.z = sc * p3;
+          u[i] = qmul(e, u[i]);
+          renorm(u[i]);
+        }
+      }
+      sF(s)[k] = f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        sU(s, i)[k] = u[i];
+        sA(s, i)[k] = a[i];
+      }
+      if (own && P.write && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
+        dst[SF * V + g] = f.w;
+        dst[(SF + 1) * V + g] = f.x;
+        dst[(SF + 2) * V + g] = f.y;
+        dst[(SF + 3) * V + g] = f.z;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dst[(SA + i) * V + g] = a[i];
+          dst[(SU + 4 * i) * V + g] = u[i].w;
+          dst[(SU + 4 * i + 1) * V + g] = u[i].x;
+          dst[(SU + 4 * i + 2) * V + g] = u[i].y;
+          dst[(SU + 4 * i + 3) * V + g] = u[i].z;
+        }
+      }
+    }
+  };
+
+  // plane tasks: tile-major (tile = by * ntx + bx), then z; one equal run per CTA
+  const long long ntask = (long long)ntx * nty * N;
+  const long long t_beg = ntask * blockIdx.x / gridDim.x, t_end = ntask * (blockIdx.x + 1) / gridDim.x;
+  for (long long t = t_beg; t < t_end;) {
+    const int tile = (int)(t / N), z0 = (int)(t % N);
+    const long long rem = t_end - t;
+    const int nz = rem < (long long)(N - z0) ? (int)rem : N - z0;
+    t += nz;
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    __syncthreads();  // the previous segment's last reads of the ring are done
+    load_plane(0, x0, y0, (z0 - 1 + N) % N, false);
+    load_plane(1, x0, y0, z0, true);
+    const int hx = tx + 1, hy = ty + 1, own = hy * HX + hx;
+    const long long gown = (long long)(y0 + ty) * N + x0 + tx;
+    for (int j = 0; j < nz; ++j) {
+      const int z = z0 + j;
+      const int sm = j % 3, sc = (j + 1) % 3, sp = (j + 2) % 3;
+      load_plane(sp, x0, y0, (z + 1) % N, j + 1 < nz);
+      __syncthreads();
+      const long long g = (long long)z * NN + gown;
+      // neighbours in the ring: (dx, dy) in the plane, slot for dz
+      auto at = [&](int ddx, int ddy) { return own + ddy * HX + ddx; };
+      const Q4<T> psi = sF(sc)[own];
+      Q4<T> D;
+      D.w = T(-6) * psi.w;
+      D.x = T(-6) * psi.x;
+      D.y = T(-6) * psi.y;
+      D.z = T(-6) * psi.z;
+      T s_g = T(0), s_pA = T(0), s_pB = T(0), s_mA = T(0), s_mB = T(0);
+      T pnA[3], pnB[3][3];
+      // U(1) plaquette sines: xy, xz, yz at n, then the lower ones
+      const T ax = sA(sc, 0)[own], ay = sA(sc, 1)[own], az = sA(sc, 2)[own];
+      T sxy = T(0), sxz = T(0), syz = T(0), Cx = T(0), Cy = T(0), Cz = T(0);
+      if (ACA != T(0) || RED > 0) {
+        const T txy = gd * ((ax + sA(sc, 1)[at(1, 0)]) - (sA(sc, 0)[at(0, 1)] + ay));
+        const T txz = gd * ((ax + sA(sc, 2)[at(1, 0)]) - (sA(sp, 0)[own] + az));
+        const T tyz = gd * ((ay + sA(sc, 2)[at(0, 1)]) - (sA(sp, 1)[own] + az));
+        sxy = sin_t(txy);
+        sxz = sin_t(txz);
+        syz = sin_t(tyz);
+        const T sxy_ym = sin_t(gd * ((sA(sc, 0)[at(0, -1)] + sA(sc, 1)[at(1, -1)]) - (ax + sA(sc, 1)[at(0, -1)])));
+        const T sxy_xm = sin_t(gd * ((sA(sc, 0)[at(-1, 0)] + ay) - (sA(sc, 0)[at(-1, 1)] + sA(sc, 1)[at(-1, 0)])));
+        const T sxz_zm = sin_t(gd * ((sA(sm, 0)[own] + sA(sm, 2)[at(1, 0)]) - (ax + sA(sm, 2)[own])));
+        const T sxz_xm = sin_t(gd * ((sA(sc, 0)[at(-1, 0)] + az) - (sA(sp, 0)[at(-1, 0)] + sA(sc, 2)[at(-1, 0)])));
+        const T syz_zm = sin_t(gd * ((sA(sm, 1)[own] + sA(sm, 2)[at(0, 1)]) - (ay + sA(sm, 2)[own])));
+        const T syz_ym = sin_t(gd * ((sA(sc, 1)[at(0, -1)] + az) - (sA(sp, 1)[at(0, -1)] + sA(sc, 2)[at(0, -1)])));
+        Cx = (sxy - sxy_ym) + (sxz - sxz_zm);
+        Cy = (sxy_xm - sxy) + (syz - syz_zm);
+        Cz = (sxz_xm - sxz) + (syz_ym - syz);
+        if constexpr (RED > 0) {
+          const T hx2 = sin_t(T(0.5) * txy), hy2 = sin_t(T(0.5) * txz), hz2 = sin_t(T(0.5) * tyz);
+          s_mA = T(2) * (hx2 * hx2 + hy2 * hy2 + hz2 * hz2);
+        }
+      }
+      const T Cc[3] = {Cx, Cy, Cz};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        // ---- doublet hops along i, currents ----
+        const Q4<T> Ui = sU(sc, i)[own];
+        const int fx = i == 0 ? 1 : 0, fy = i == 1 ? 1 : 0;
+        const Q4<T> fn = i == 2 ? sF(sp)[own] : sF(sc)[at(fx, fy)];
+        Q4<T> chi = umul(Ui, fn);
+        T c, s;
+        sincos_t(gd * sA(sc, i)[own], s, c);
+        phase(chi, c, s);
+        const int bs = i == 2 ? sm : sc;
+        const int bk = i == 2 ? own : at(-fx, -fy);
+        Q4<T> back = udmul(sU(bs, i)[bk], sF(bs)[bk]);
+        sincos_t(gd * sA(bs, i)[bk], s, c);
+        phase(back, c, -s);
+        D.w += chi.w + back.w;
+        D.x += chi.x + back.x;
+        D.y += chi.y + back.y;
+        D.z += chi.z + back.z;
+        // psi = (p, q) = (w + i x, y + i z), chi = (c1, c2)
+        const T ImA = (psi.w * chi.x - psi.x * chi.w) + (psi.y * chi.z - psi.z * chi.y);     // Im psi^dag chi
+        const T Im1 = (psi.w * chi.z - psi.x * chi.y) + (psi.y * chi.x - psi.z * chi.w);     // Im psi^dag s1 chi
+        const T Im2 = (psi.y * chi.w + psi.z * chi.x) - (psi.w * chi.y + psi.x * chi.z);     // Im psi^dag s2 chi
+        const T Im3 = (psi.w * chi.x - psi.x * chi.w) - (psi.y * chi.z - psi.z * chi.y);     // Im psi^dag s3 chi
+        if constexpr (RED > 0) {
+          const T e0 = chi.w - psi.w, e1 = chi.x - psi.x, e2 = chi.y - psi.y, e3 = chi.z - psi.z;
+          s_g += (e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3);
+        }
+        // ---- SU(2) staples of U_i(n) ----
+        Q4<T> S;
+        S.w = S.x = S.y = S.z = T(0);
+#pragma unroll
+        for (int jj = 1; jj <= 2; ++jj) {
+          const int j = (i + jj) % 3;
+          const int gx = j == 0 ? 1 : 0, gy = j == 1 ? 1 : 0;
+          // U_j(n+i), U_i(n+j), U_j(n)
+          const Q4<T> ujni = i == 2 ? sU(sp, j)[own] : sU(sc, j)[at(fx, fy)];
+          const Q4<T> uinj = j == 2 ? sU(sp, i)[own] : sU(sc, i)[at(gx, gy)];
+          const Q4<T> ujn = sU(sc, j)[own];
+          const Q4<T> up = qmul(qmul(ujni, qconj(uinj)), qconj(ujn));
+          // U_j(n+i-j), U_i(n-j), U_j(n-j)
+          Q4<T> ujnimj, uinmj, ujnmj;
+          if (j == 2) {
+            ujnimj = i == 2 ? sU(sc, j)[own] : sU(sm, j)[at(fx, fy)];
+            uinmj = sU(sm, i)[own];
+            ujnmj = sU(sm, j)[own];
+          } else if (i == 2) {
+            ujnimj = sU(sp, j)[at(-gx, -gy)];
+            uinmj = sU(sc, i)[at(-gx, -gy)];
+            ujnmj = sU(sc, j)[at(-gx, -gy)];
+          } else {
+            ujnimj = sU(sc, j)[at(fx - gx, fy - gy)];
+            uinmj = sU(sc, i)[at(-gx, -gy)];
+            ujnmj = sU(sc, j)[at(-gx, -gy)];
+          }
+          const Q4<T> lo = qmul(qmul(qconj(ujnimj), qconj(uinmj)), ujnmj);
+          qadd(S, up);
+          qadd(S, lo);
+          if constexpr (RED > 0) {
+            if (j > i) s_mB += one_minus_w(qmul(Ui, up));
+          }
+        }
+        const Q4<T> M = qmul(Ui, S);
+        // ---- link kicks ----
+        const T pA = src[(SPA + i) * V + g];
+        pnA[i] = pA + (AJA * ImA + ACA * Cc[i]);
+        const T Ims[3] = {Im1, Im2, Im3};
+        const T Ms[3] = {M.x, M.y, M.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T pB = src[(SPB + 3 * i + a) * V + g];
+          pnB[i][a] = pB + (AJB * Ims[a] + AMB * Ms[a]);
+        }
+        if constexpr (RED > 0) {
+          s_pA += pnA[i] * pnA[i];
+          s_pB += pnB[i][0] * pnB[i][0] + pnB[i][1] * pnB[i][1] + pnB[i][2] * pnB[i][2];
+        }
+      }
+      // ---- doublet kick ----
+      const T r2 = T(0.5) * ((psi.w * psi.w + psi.x * psi.x) + (psi.y * psi.y + psi.z * psi.z));
+      const T dd = r2 - v2;
+      const T gp = lam2 * dd;
+      T pn[4];
+      const T Dc[4] = {D.w, D.x, D.y, D.z};
+      const T fc[4] = {psi.w, psi.x, psi.y, psi.z};
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) pn[c2] = src[(SP + c2) * V + g] + (A1 * Dc[c2] - A3 * gp * fc[c2]);
+      if (P.write) {
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2) dst[(SP + c2) * V + g] = pn[c2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dst[(SPA + i) * V + g] = pnA[i];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dst[(SPB + 3 * i + a) * V + g] = pnB[i][a];
+        }
+      }
+      if constexpr (RED == 1) {
+        acc[0].add((pn[0] * pn[0] + pn[1] * pn[1]) + (pn[2] * pn[2] + pn[3] * pn[3]));
+        acc[1].add(s_pA + s_pB);
+        acc[2].add(s_g);
+        acc[3].add(s_mA);
+        acc[4].add(s_mB);
+        acc[5].add(lam * dd * dd);
+      } else if constexpr (RED == 2) {
+#pragma unroll
+        for (int c2 = 0; c2 < 4; ++c2) {
+          acc[c2].add(pn[c2] * pn[c2]);
+          acc[10 + c2].add(fc[c2]);
+          acc[14 + c2].add(fc[c2] * fc[c2]);
+          acc[18 + c2].add(pn[c2]);
+          if (!isfinite(pn[c2])) nonfinite += 1.f;
+        }
+        acc[4].add(s_pA);
+        acc[5].add(s_pB);
+        acc[6].add(s_g);
+        acc[7].add(s_mA);
+        acc[8].add(s_mB);
+        acc[9].add(lam * dd * dd);
+        if (!isfinite(s_pA) || !isfinite(s_pB)) nonfinite += 1.f;
+      }
+      __syncthreads();  // slot sm is overwritten by the next load
+    }
+  }
+
+  // ---- partial sums of the CTA, then the tail in the last CTA ----
+  if constexpr (RED > 0) {
+    const int nw = nth >> 5;
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) {
+      const double v = warp_sum(acc[q]);
+      if (lane == 0) red_s[q][warp] = v;
+    }
+    if constexpr (RED == 2) {
+      float nf = nonfinite;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, o);
+      if (lane == 0) red_s[NACC][warp] = (double)nf;
+    }
+    __syncthreads();
+    constexpr int NOUT = RED == 2 ? NACC + 1 : NACC;
+    if (tid < NOUT) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red_s[tid][w];
+      P.partials[(size_t)tid * gridDim.x + blockIdx.x] = s;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last_s = atomicAdd(&P.counters[0], 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  constexpr int NOUT = RED == 0 ? 0 : (RED == 2 ? NACC + 1 : NACC);
+  for (int q = warp; q < NOUT; q += nth >> 5) {
+    const double s = warp_slot_sum(P.partials, q * gridDim.x, (q + 1) * gridDim.x, lane);
+    if (lane == 0) red_s[q][0] = s;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  ScalarState W;
+  load_state_cg(W, P.sc);
+  const double a = W.a, a2 = a * a, a4 = a2 * a2, a6 = a4 * a2;
+  const double gdx2 = L.gQ * L.dx * L.dx, bdx2 = L.gQB * L.dx * L.dx;
+  const double kphi = 0.5 * L.inv_V / a6;                                  // E_K per sum of pi_c^2
+  const double gphi = 0.5 * L.inv_V * L.inv_dx2 / a2;                      // E_G per sum |W psi(n+i) - psi|^2
+  const double kA = 0.5 * L.inv_V / (L.fo2 * a4);                          // E_K^A, E_K^B per sum of momenta^2
+  const double mA = gdx2 != 0.0 ? L.inv_V / (L.fo2 * a4 * gdx2 * gdx2) : 0.0;  // E_G^A per sum (1 - cos)
+  const double mB = 4.0 * L.inv_V / (L.fo2 * a4 * bdx2 * bdx2);           // E_G^B per sum (1 - Tr U_ij/2)
+  PassSums E = {0, 0, 0, 0, 0, 0, 0};
+  double EKA = 0, EKB = 0, EGA = 0, EGB = 0;
+  if (RED > 0) {
+    double spost, slinks;
+    if (RED == 1) {
+      spost = red_s[0][0];
+      slinks = red_s[1][0];
+      E.EG = red_s[2][0] * gphi;
+      EGA = red_s[3][0] * mA;
+      EGB = red_s[4][0] * mB;
+      E.EV = red_s[5][0] * L.inv_V;
+    } else {
+      spost = red_s[0][0] + red_s[1][0] + red_s[2][0] + red_s[3][0];
+      slinks = red_s[4][0] + red_s[5][0];
+      EKA = red_s[4][0] * kA;
+      EKB = red_s[5][0] * kA;
+      E.EG = red_s[6][0] * gphi;
+      EGA = red_s[7][0] * mA;
+      EGB = red_s[8][0] * mB;
+      E.EV = red_s[9][0] * L.inv_V;
+    }
+    // the two link sectors enter the Friedmann kicks with one coefficient, (alpha - 1)
+    E.EKpre = W.pi2 * kphi;
+    E.EKpost = spost * kphi;
+    E.EKApre = W.pi2A * kA;
+    E.EKA = slinks * kA;
+    E.EGA = EGA + EGB;
+    W.pi2 = spost;
+    W.pi2A = slinks;
+  }
+  advance_scalars(P, L, W, E, RED > 0);
+  if (RED == 2) {
+    cl_energies_t& ob = P.sc->obs;
+    for (int k2 = 0; k2 < 4; ++k2) {
+      ob.EK[k2] = ob.EG[k2] = ob.EV[k2] = 0.0;
+      ob.mean_phi[k2] = red_s[10 + k2][0] * L.inv_V;
+      ob.mean_phi2[k2] = red_s[14 + k2][0] * L.inv_V;
+      ob.mean_pi[k2] = red_s[18 + k2][0] * L.inv_V;
+      ob.mean_pi2[k2] = red_s[k2][0] * L.inv_V;
+    }
+    ob.EK[0] = E.EKpost;
+    ob.EG[0] = E.EG;
+    ob.EV[0] = E.EV;
+    ob.EKA = EKA;
+    ob.EGA = EGA;
+    ob.EKB = EKB;
+    ob.EGB = EGB;
+    ob.nonfinite = (int64_t)red_s[NACC][0];
+    finish_obs(P, L, W, ob);
+  }
+  advance_drift(P, L, W);
+  store_state(P.sc, W);
+  P.counters[0] = 0u;
+  __threadfence();
+}
+
+template __global__ void dk_pass_su2<float, 0>(const PassArgs);
+template __global__ void dk_pass_su2<float, 1>(const PassArgs);
+template __global__ void dk_pass_su2<float, 2>(const PassArgs);
+template __global__ void dk_pass_su2<double, 0>(const PassArgs);
+template __global__ void dk_pass_su2<double, 1>(const PassArgs);
+template __global__ void dk_pass_su2<double, 2>(const PassArgs);
+
+typedef void (*PassKernel)(const PassArgs);
+
+PassKernel su2_pass_kernel(int fp32, int red) {
+  static const PassKernel tab[2][3] = {
+      {dk_pass_su2<double, 0>, dk_pass_su2<double, 1>, dk_pass_su2<double, 2>},
+      {dk_pass_su2<float, 0>, dk_pass_su2<float, 1>, dk_pass_su2<float, 2>}};
+  if (red < 0 || red > 2) return nullptr;
+  return tab[fp32 ? 1 : 0][red];
+}
+
+size_t su2_smem_bytes(int TX, int TY, int esz) { return 3 * su2_slot_bytes(TX, TY, esz); }
+
+// ---------------------------------------------------------------------------
+// Initial state and the Gauss-law monitor of the doublet model.
+// ---------------------------------------------------------------------------
+
+// links at the identity (eqs. Inflc1-2): u0 = 1, the rest zero (caller zeroed the slab)
+template <typename T>
+__global__ void su2_identity_links_kernel(T* base, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) base[(SU + 4 * i) * V + n] = T(1);
+}
+
+template <typename T>
+__device__ __forceinline__ Q4<double> dq(const T* b, int a, long long V, long long n) {
+  Q4<double> r;
+  r.w = (double)b[a * V + n];
+  r.x = (double)b[(a + 1) * V + n];
+  r.y = (double)b[(a + 2) * V + n];
+  r.z = (double)b[(a + 3) * V + n];
+  return r;
+}
+
+// Charge density of generator g (0: U(1); 1..3: SU(2) colour g) at site n:
+//   U(1):  (f_s/omega_s)^2 gQ Im[psi^dag pi_psi]
+//   SU(2): (f_s/omega_s)^2 (gQB/2) Im[psi^dag s_g pi_psi]
+template <typename T>
+__device__ double su2_rho(const LatConst& L, const T* b, int g, long long n) {
+  const long long V = L.V;
+  const Q4<double> f = dq(b, SF, V, n), p = dq(b, SP, V, n);
+  double im;
+  if (g == 0) im = (f.w * p.x - f.x * p.w) + (f.y * p.z - f.z * p.y);
+  else if (g == 1) im = (f.w * p.z - f.x * p.y) + (f.y * p.x - f.z * p.w);
+  else if (g == 2) im = (f.y * p.w + f.z * p.x) - (f.w * p.y + f.x * p.z);
+  else im = (f.w * p.x - f.x * p.w) - (f.y * p.z - f.z * p.y);
+  return L.fo2 * (g == 0 ? L.gQ : 0.5 * L.gQB) * im;
+}
+
+template <typename T>
+__global__ void su2_rho_kernel(const LatConst* Lc, int parity, int g, double2* rho) {
+  const LatConst& L = *Lc;
+  const T* b = reinterpret_cast<const T*>(L.buf[parity][0]);
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.V;
+       n += (long long)gridDim.x * blockDim.x)
+    rho[n] = make_double2(su2_rho<T>(L, b, g, n), 0.0);
+}
+
+// |L - R|, |L + R| summed over the four laws, and max |L - R|, per block.
+template <typename T>
+__global__ void su2_gauss_monitor_kernel(const LatConst* Lc, int parity, double* part) {
+  __shared__ double sh[3][32];
+  const LatConst& L = *Lc;
+  const T* b = reinterpret_cast<const T*>(L.buf[parity][0]);
+  const int N = L.N;
+  const long long NN = (long long)N * N, V = L.V;
+  double sd = 0.0, ss = 0.0, mx = 0.0;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(n % N), y = (int)((n / N) % N), z = (int)(n / NN);
+    const long long nm[3] = {x ? n - 1 : n + N - 1, y ? n - N : n + NN - N, z ? n - NN : n + V - NN};
+    double lhs[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < 3; ++i) {
+      const long long m = nm[i];
+      lhs[0] += (double)b[(SPA + i) * V + n] - (double)b[(SPA + i) * V + m];
+      // (U^dag P U)^a, P = p.s/2 at n - i: rotation of p by the link
+      const Q4<double> u = dq(b, SU + 4 * i, V, m);
+      Q4<double> pq;
+      pq.w = 0.0;
+      pq.x = (double)b[(SPB + 3 * i) * V + m];
+      pq.y = (double)b[(SPB + 3 * i + 1) * V + m];
+      pq.z = (double)b[(SPB + 3 * i + 2) * V + m];
+      const Q4<double> r = qmul(qmul(qconj(u), pq), u);
+      lhs[1] += (double)b[(SPB + 3 * i) * V + n] - r.x;
+      lhs[2] += (double)b[(SPB + 3 * i + 1) * V + n] - r.y;
+      lhs[3] += (double)b[(SPB + 3 * i + 2) * V + n] - r.z;
+    }
+    for (int g2 = 0; g2 < 4; ++g2) {
+      const double l = lhs[g2] / L.dx, r = su2_rho<T>(L, b, g2, n);
+      const double d = fabs(l - r);
+      sd += d;
+      ss += fabs(l + r);
+      mx = fmax(mx, d);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sd += __shfl_down_sync(0xffffffffu, sd, o);
+    ss += __shfl_down_sync(0xffffffffu, ss, o);
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][w] = sd;
+    sh[1][w] = ss;
+    sh[2][w] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0, m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += sh[0][i];
+      c += sh[1][i];
+      m = fmax(m, sh[2][i]);
+    }
+    part[3 * blockIdx.x] = a;
+    part[3 * blockIdx.x + 1] = c;
+    part[3 * blockIdx.x + 2] = m;
+  }
+}
+
+__global__ void su2_gauss_final_kernel(const double* part, int nblk, long long V, double* out) {
+  if (threadIdx.x | blockIdx.x) return;
+  double a = 0.0, b = 0.0, m = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    a += part[3 * i];
+    b += part[3 * i + 1];
+    m = fmax(m, part[3 * i + 2]);
+  }
+  out[0] = b > 0.0 ? a / b : 0.0;
+  out[1] = a / (double)V;
+  out[2] = b / (double)V;
+  out[3] = m;
+}
+
+cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st) {
+  const int tb = 256;
+  const int g = (int)((V + tb - 1) / tb < 65536 ? (V + tb - 1) / tb : 65536);
+  if (fp32) su2_identity_links_kernel<float><<<g, tb, 0, st>>>((float*)base, V);
+  else su2_identity_links_kernel<double><<<g, tb, 0, st>>>((double*)base, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
+                           cudaStream_t st) {
+  const int tb = 256;
+  const int gr = (int)((V + tb - 1) / tb < 65536 ? (V + tb - 1) / tb : 65536);
+  if (fp32) su2_rho_kernel<float><<<gr, tb, 0, st>>>(L, parity, g, rho);
+  else su2_rho_kernel<double><<<gr, tb, 0, st>>>(L, parity, g, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_su2_gauss_monitor(int fp32, const LatConst* L, int parity, double* part, int nblk,
+                                     long long V, cudaStream_t st) {
+  if (fp32) su2_gauss_monitor_kernel<float><<<nblk, 256, 0, st>>>(L, parity, part);
+  else su2_gauss_monitor_kernel<double><<<nblk, 256, 0, st>>>(L, parity, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  su2_gauss_final_kernel<<<1, 32, 0, st>>>(part, nblk, V, part + 3 * nblk);
+  return cudaGetLastError();
+}
+
+}  // namespace clg

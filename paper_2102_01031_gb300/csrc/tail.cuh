@@ -197,7 +197,7 @@ __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S
 // Hubble-constraint monitor and energy bookkeeping of a measurement.
 template <class SS>
 __device__ inline void finish_obs(const PassArgs& P, const LatConst& L, SS& S, cl_energies_t& o) {
-  double rho = o.EKA + o.EGA;
+  double rho = o.EKA + o.EGA + o.EKB + o.EGB;
   for (int k = 0; k < 4; ++k) rho += o.EK[k] + o.EG[k] + o.EV[k];
   o.rho = rho;
   o.hubble_lhs = S.b * S.b;
