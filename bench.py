@@ -359,10 +359,19 @@ def run_ours(args):
     return 0
 
 
+# SU(2) x U(1) doublet workload: equal homogeneous components, vacuum
+# fluctuations, links at the identity, electric fields from the Gauss laws
+def su2_params(P):
+    return dict(dt=0.01, integrator=P.LF, lam=1.0, v=0.5, gQ=0.6, gQB=0.8, fstar_over_omegastar=1.3,
+                phi0=[0.5] * 4, dphi0=[0.1] * 4, fluct_amp2=1e-2, expansion=P.EXP_OFF, fstar_over_mp=0.5)
+
+
 def other_workloads(P, torch, stream, peak):
     """The other hot-path rows, timed briefly with the library's pass-timing hook
-    (CUDA events around every launch on the lattice stream): the U(1) pass at
-    256^3, the 64-lattice ensemble, and the adjoint sweep's cost at 128^3."""
+    (CUDA events around every launch on the lattice stream): the U(1) and the
+    SU(2) x U(1) passes at 256^3, the 64-lattice ensemble, and the adjoint
+    sweep's cost at 128^3."""
+    SU2 = su2_params(P)
     out = {}
     # U(1) Abelian-Higgs, 256^3, FP32, leapfrog dt = 0.01, no expansion
     u1 = dict(dt=0.01, integrator=P.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
@@ -381,6 +390,21 @@ def other_workloads(P, torch, stream, peak):
     out["u1_higgs_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
                                    "gauss_rel_after_520_steps": rel, "kernel": "dk_pass_u1<float,0>"}
+    # SU(2) x U(1) doublet, 256^3, FP32, leapfrog dt = 0.01, no expansion
+    lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 256, 0.1, 1.0, 1, P.make_params(precision=P.FP32, stream=stream, **SU2))
+    lat.step(10)
+    torch.cuda.synchronize()
+    lat.pass_timing(reset=True)
+    lat.enable_pass_timing(True)
+    lat.step(200)
+    torch.cuda.synchronize()
+    ms, n = lat.pass_timing(reset=True)
+    rel = lat.gauss()[0]
+    lat.close()
+    gbs = 256 ** 3 * 35 * 2 * 4 / (ms / n * 1e-3) / 1e9
+    out["su2u1_doublet_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+                                        "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
+                                        "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0>"}
     # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
     Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
     E = P.Ensemble(P.MODEL_LPHI4_CHI, Ns, [KIR * N_LAT / n for n in Ns], ALPHA, list(range(1, 65)),
@@ -443,6 +467,11 @@ def profile_case(name):
         lat = P.Lattice(P.MODEL_U1_HIGGS, 128, 0.2, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
         for _ in range(4):
             lat.step(1)
+    elif name == "su2_128":   # single-pass launches of the leapfrog SU(2) x U(1) doublet pass
+        lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 128, 0.2, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **su2_params(P)))
+        for _ in range(4):
+            lat.step(1)
     elif name == "scalar256_fp64":   # the FP64 plain pass: one cooperative launch of a VV4 step
         lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
                         P.make_params(precision=P.FP64, stream=stream, **PARAMS))
@@ -474,7 +503,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "adj128", "adj128self"),
+    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "su2_128", "adj128", "adj128self"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -884,8 +884,8 @@ static cl_status init_finish(cl_ctx* c) {
 
 
 // Doublet model: one lattice, 35 arrays per buffer; the pass tiles x-y by
-// TX x TY (TX = 32, or 16 when N is not a multiple of 32; TY = 8) and runs as
-// many CTAs as are resident at once.  Initial conditions: the doublet's four
+// TX x TY (TX = 32, or 16 when N is not a multiple of 32; TY = 8), cuts z into
+// chunks and runs the resident CTAs over the (tile, chunk) items.  Initial conditions: the doublet's four
 // components drawn like the U(1) field's (eqs. InConstr:1-2 for n = 0..3),
 // links at the identity (eqs. Inflc1-2), and link momenta solving the U(1)
 // and the three SU(2) lattice Gauss laws (eq. GaugeCurrentFluc with the
@@ -910,8 +910,21 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   int nb = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c)),
                                                    c->su2_tx * c->su2_ty, c->smem_bytes));
-  const long long tasks = (long long)(N / c->su2_tx) * (N / c->su2_ty) * N;
-  c->grid = (int)std::min<long long>(tasks, (long long)c->nsm * std::max(nb, 1));
+  // work items (tile, z-chunk) over the resident CTAs: the number of z-chunks that
+  // minimises rounds x (planes per chunk + the 2 planes each item loads first)
+  const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);
+  const int R = c->nsm * std::max(nb, 1);
+  int nzc = 1;
+  double best = 1e300;
+  for (int k = 1; k <= std::max(1, N / 4); ++k) {
+    const double rounds = std::ceil((double)ntiles * k / R);
+    const double cost = rounds * ((double)N / k + 2.0);
+    if (cost < best - 1e-9) {
+      best = cost;
+      nzc = k;
+    }
+  }
+  c->grid = std::min(R, ntiles * nzc);
   c->nslot = c->grid;
   c->stages = 3;
   c->coop = false;
@@ -947,6 +960,7 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   L.v = c->p.v;
   L.gQ = c->p.gQ;
   L.gQB = c->p.gQB;
+  L.su2_nzc = nzc;
   L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
   L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
   L.omega_eos = c->p.omega_eos;

@@ -24,18 +24,20 @@
 //   lattice Hamiltonian (kinetic terms, covariant hopping, compact U(1) plaquettes,
 //   SU(2) plaquette traces), so that both lattice Gauss laws hold exactly.
 //
-// Kernel layout.  A CTA owns a TX x TY tile of x-y sites and marches a run of
-// z-planes of it.  Each plane of the tile plus a one-site halo (corners
-// included) is loaded from HBM, drifted in registers and kept, drifted, in a
-// three-plane shared-memory ring (links as one 16-byte quaternion per site
-// and direction, the doublet as one quaternion, the three U(1) link fields);
-// the drifted fields of the CTA's own sites are written out right away.  The
-// kick of plane z then reads every neighbour, staple and plaquette it needs
-// from the ring (the stencil reaches n +- x, n +- y, n +- z and the diagonal
-// neighbours n + i - j), and re-reads its own momenta (L2-resident).  The
-// plane-task list (tile-major, then z) is cut into equal contiguous runs, one
-// per resident CTA.  The last CTA to finish sums the per-CTA partial sums in
-// a fixed order and advances the scale factor (tail.cuh).
+// Kernel layout.  A work item is a TX x TY tile of x-y sites over a chunk of
+// z-planes; the resident CTAs (two per SM) take items in a round-robin that
+// keeps neighbouring tiles on the same planes at the same time.  Each plane of
+// the tile plus a one-site halo (corners included) is loaded from HBM (all 35
+// loads of a site in flight at once), drifted in registers and kept, drifted,
+// in a three-plane shared-memory ring (links as one 16-byte quaternion per
+// site and direction, the doublet as one quaternion, the three U(1) link
+// fields); the drifted fields of the CTA's own sites are written out right
+// away.  The kick of plane z then reads every neighbour, staple and plaquette
+// it needs from the ring (the stencil reaches n +- x, n +- y, n +- z and the
+// diagonal neighbours n + i - j), and re-reads its own momenta, prefetched
+// into L1 while the next plane loads.  The two CTAs of an SM overlap one's
+// loads with the other's arithmetic.  The last CTA to finish sums the per-CTA
+// partial sums in a fixed order and advances the scale factor (tail.cuh).
 #include "common.cuh"
 #include "tail.cuh"
 
@@ -176,6 +178,12 @@ __device__ __forceinline__ T one_minus_w(const Q4<T>& p) {
   return (p.x * p.x + p.y * p.y + p.z * p.z) / (T(1) + p.w);
 }
 
+// Bring a line into L1 (no register, no wait).
+template <typename T>
+__device__ __forceinline__ void prefetch_l1(const T* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 constexpr int SU2_NQ = 24;  // partial sums per CTA (the measurement pass uses 23)
 
 }  // namespace
@@ -242,81 +250,95 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
   auto sF = [&](int s) { return reinterpret_cast<Q4<T>*>(smem + s * slot_b) + 3 * HS; };
   auto sA = [&](int s, int i) { return reinterpret_cast<T*>(smem + s * slot_b) + 16 * HS + i * HS; };
 
-  // load plane zp of tile (x0, y0) into slot s, drifted; own sites written out when `own`
-  auto load_plane = [&](int s, int x0, int y0, int zp, bool own) {
-    for (int k = tid; k < HS; k += nth) {
-      const int hx = k % HX, hy = k / HX;
-      const int gx = (x0 + hx - 1 + N) % N, gy = (y0 + hy - 1 + N) % N;
-      const long long g = (long long)zp * NN + (long long)gy * N + gx;
-      Q4<T> f, u[3];
-      T a[3];
-      f.w = src[SF * V + g];
-      f.x = src[(SF + 1) * V + g];
-      f.y = src[(SF + 2) * V + g];
-      f.z = src[(SF + 3) * V + g];
+  // the 35 raw values of halo site k of plane zp, all loads issued before any use
+  // (the source buffer is read-only during the pass)
+  auto fetch = [&](int k, int x0, int y0, int zp, T (&r)[SNARR]) {
+    const int hx = k % HX, hy = k / HX;
+    int gx = x0 + hx - 1, gy = y0 + hy - 1;
+    gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+    gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+    const T* p = src + ((long long)zp * NN + (long long)gy * N + gx);
+#pragma unroll
+    for (int a = 0; a < SNARR; ++a) {
+      r[a] = __ldg(p);
+      p += V;
+    }
+  };
+  // drift halo site k into ring slot s; own sites written out when `own`
+  auto put = [&](int s, int k, int x0, int y0, int zp, bool own, const T (&r)[SNARR]) {
+    Q4<T> f, u[3];
+    T a[3];
+    f.w = r[SF];
+    f.x = r[SF + 1];
+    f.y = r[SF + 2];
+    f.z = r[SF + 3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a[i] = r[SA + i];
+      u[i].w = r[SU + 4 * i];
+      u[i].x = r[SU + 4 * i + 1];
+      u[i].y = r[SU + 4 * i + 2];
+      u[i].z = r[SU + 4 * i + 3];
+    }
+    if (drifting) {
+      f.w = fmaT(cd, r[SP], f.w);
+      f.x = fmaT(cd, r[SP + 1], f.x);
+      f.y = fmaT(cd, r[SP + 2], f.y);
+      f.z = fmaT(cd, r[SP + 3], f.z);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        a[i] = src[(SA + i) * V + g];
-        u[i].w = src[(SU + 4 * i) * V + g];
-        u[i].x = src[(SU + 4 * i + 1) * V + g];
-        u[i].y = src[(SU + 4 * i + 2) * V + g];
-        u[i].z = src[(SU + 4 * i + 3) * V + g];
+        a[i] = fmaT(cdA, r[SPA + i], a[i]);
+        // E = exp(-i hB pi.s) = (cos x, sin(x)/x hB pi), x = hB |pi|
+        const T p1 = hB * r[SPB + 3 * i], p2 = hB * r[SPB + 3 * i + 1], p3 = hB * r[SPB + 3 * i + 2];
+        T c, sc;
+        cos_sinc(p1 * p1 + p2 * p2 + p3 * p3, c, sc);
+        Q4<T> e;
+        e.w = c;
+        e.x = sc * p1;
+        e.y = sc * p2;
+        e.z = sc * p3;
+        u[i] = qmul(e, u[i]);
+        renorm(u[i]);
       }
-      if (drifting) {
-        f.w = fmaT(cd, src[SP * V + g], f.w);
-        f.x = fmaT(cd, src[(SP + 1) * V + g], f.x);
-        f.y = fmaT(cd, src[(SP + 2) * V + g], f.y);
-        f.z = fmaT(cd, src[(SP + 3) * V + g], f.z);
+    }
+    sF(s)[k] = f;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          a[i] = fmaT(cdA, src[(SPA + i) * V + g], a[i]);
-          // E = exp(-i hB pi.s) = (cos x, sin(x)/x hB pi), x = hB |pi|
-          const T p1 = hB * src[(SPB + 3 * i) * V + g], p2 = hB * src[(SPB + 3 * i + 1) * V + g],
-                  p3 = hB * src[(SPB + 3 * i + 2) * V + g];
-          T c, sc;
-          cos_sinc(p1 * p1 + p2 * p2 + p3 * p3, c, sc);
-          Q4<T> e;
-          e.w = c;
-          e.x = sc * p1;
-          e.y = sc * p2;
-          e.z = sc * p3;
-          u[i] = qmul(e, u[i]);
-          renorm(u[i]);
-        }
-      }
-      sF(s)[k] = f;
+    for (int i = 0; i < 3; ++i) {
+      sU(s, i)[k] = u[i];
+      sA(s, i)[k] = a[i];
+    }
+    const int hx = k % HX, hy = k / HX;
+    if (own && P.write && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
+      T* o = dst + ((long long)zp * NN + (long long)(y0 + hy - 1) * N + (x0 + hx - 1));
+      const T vals[19] = {f.w, f.x, f.y, f.z, a[0], a[1], a[2], u[0].w, u[0].x, u[0].y, u[0].z,
+                          u[1].w, u[1].x, u[1].y, u[1].z, u[2].w, u[2].x, u[2].y, u[2].z};
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        sU(s, i)[k] = u[i];
-        sA(s, i)[k] = a[i];
-      }
-      if (own && P.write && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
-        dst[SF * V + g] = f.w;
-        dst[(SF + 1) * V + g] = f.x;
-        dst[(SF + 2) * V + g] = f.y;
-        dst[(SF + 3) * V + g] = f.z;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dst[(SA + i) * V + g] = a[i];
-          dst[(SU + 4 * i) * V + g] = u[i].w;
-          dst[(SU + 4 * i + 1) * V + g] = u[i].x;
-          dst[(SU + 4 * i + 2) * V + g] = u[i].y;
-          dst[(SU + 4 * i + 3) * V + g] = u[i].z;
-        }
+      for (int m = 0; m < 19; ++m) {  // arrays 0..3, 8..10, 14..25
+        const int arr = m < 4 ? SF + m : (m < 7 ? SA + (m - 4) : SU + (m - 7));
+        o[arr * V] = vals[m];
       }
     }
   };
+  // plane zp of tile (x0, y0) into slot s, drifted
+  auto load_plane = [&](int s, int x0, int y0, int zp, bool own) {
+    for (int k = tid; k < HS; k += nth) {
+      T r0[SNARR];
+      fetch(k, x0, y0, zp, r0);
+      put(s, k, x0, y0, zp, own, r0);
+    }
+  };
 
-  // plane tasks: tile-major (tile = by * ntx + bx), then z; one equal run per CTA
-  const long long ntask = (long long)ntx * nty * N;
-  const long long t_beg = ntask * blockIdx.x / gridDim.x, t_end = ntask * (blockIdx.x + 1) / gridDim.x;
-  for (long long t = t_beg; t < t_end;) {
-    const int tile = (int)(t / N), z0 = (int)(t % N);
-    const long long rem = t_end - t;
-    const int nz = rem < (long long)(N - z0) ? (int)rem : N - z0;
-    t += nz;
+  // work items: (tile, z-chunk), tile = by * ntx + bx, numbered chunk-major; CTA b takes
+  // items b, b + gridDim.x, ...  A round of items covers about one chunk of every tile,
+  // so neighbouring tiles march the same planes at about the same time and the halo
+  // rows and columns a CTA reads come from L2 rather than DRAM.
+  const int ntiles = ntx * nty, nzc = L.su2_nzc, nitems = ntiles * nzc;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item % ntiles, chunk = item / ntiles;
+    const int z0 = (int)((long long)chunk * N / nzc);
+    const int nz = (int)((long long)(chunk + 1) * N / nzc) - z0;
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    __syncthreads();  // the previous segment's last reads of the ring are done
+    __syncthreads();  // the previous item's reads of the ring are done
     load_plane(0, x0, y0, (z0 - 1 + N) % N, false);
     load_plane(1, x0, y0, z0, true);
     const int hx = tx + 1, hy = ty + 1, own = hy * HX + hx;
@@ -324,9 +346,20 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
     for (int j = 0; j < nz; ++j) {
       const int z = z0 + j;
       const int sm = j % 3, sc = (j + 1) % 3, sp = (j + 2) % 3;
+      const long long g = (long long)z * NN + gown;
+      {  // the kick's own momenta move into L1 while the next plane loads
+        const T* pp = src + g;
+        prefetch_l1(pp + SP * V);
+        prefetch_l1(pp + (SP + 1) * V);
+        prefetch_l1(pp + (SP + 2) * V);
+        prefetch_l1(pp + (SP + 3) * V);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) prefetch_l1(pp + (SPA + m) * V);
+#pragma unroll
+        for (int m = 0; m < 9; ++m) prefetch_l1(pp + (SPB + m) * V);
+      }
       load_plane(sp, x0, y0, (z + 1) % N, j + 1 < nz);
       __syncthreads();
-      const long long g = (long long)z * NN + gown;
       // neighbours in the ring: (dx, dy) in the plane, slot for dz
       auto at = [&](int ddx, int ddy) { return own + ddy * HX + ddx; };
       const Q4<T> psi = sF(sc)[own];
@@ -426,13 +459,13 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         }
         const Q4<T> M = qmul(Ui, S);
         // ---- link kicks ----
-        const T pA = src[(SPA + i) * V + g];
+        const T pA = __ldg(src + (SPA + i) * V + g);
         pnA[i] = pA + (AJA * ImA + ACA * Cc[i]);
         const T Ims[3] = {Im1, Im2, Im3};
         const T Ms[3] = {M.x, M.y, M.z};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const T pB = src[(SPB + 3 * i + a) * V + g];
+          const T pB = __ldg(src + (SPB + 3 * i + a) * V + g);
           pnB[i][a] = pB + (AJB * Ims[a] + AMB * Ms[a]);
         }
         if constexpr (RED > 0) {
@@ -448,7 +481,7 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
       const T Dc[4] = {D.w, D.x, D.y, D.z};
       const T fc[4] = {psi.w, psi.x, psi.y, psi.z};
 #pragma unroll
-      for (int c2 = 0; c2 < 4; ++c2) pn[c2] = src[(SP + c2) * V + g] + (A1 * Dc[c2] - A3 * gp * fc[c2]);
+      for (int c2 = 0; c2 < 4; ++c2) pn[c2] = __ldg(src + (SP + c2) * V + g) + (A1 * Dc[c2] - A3 * gp * fc[c2]);
       if (P.write) {
 #pragma unroll
         for (int c2 = 0; c2 < 4; ++c2) dst[(SP + c2) * V + g] = pn[c2];
