@@ -27,7 +27,7 @@ namespace clg {
 typedef void (*PassKernel)(const PassArgs);
 PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red);
-PassKernel su2_pass_kernel(int fp32, int red);
+PassKernel su2_pass_kernel(int fp32, int red, int TX);
 size_t su2_smem_bytes(int TX, int TY, int esz);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
 cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
@@ -230,7 +230,7 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
 }
 
 PassKernel pick_kernel(const cl_ctx* c, int red) {
-  if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red);
+  if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red, c->su2_tx);
   if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red);
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
@@ -905,11 +905,12 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz);
   if (c->smem_bytes > c->smem_optin) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
   for (int red = 0; red < 3; ++red)
-    CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red),
+    CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red, c->su2_tx),
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_bytes));
   int nb = 0;
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c)),
-                                                   c->su2_tx * c->su2_ty, c->smem_bytes));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c), c->su2_tx), c->su2_tx * c->su2_ty,
+      c->smem_bytes));
   // work items (tile, z-chunk) over the resident CTAs: the number of z-chunks that
   // minimises rounds x (planes per chunk + the 2 planes each item loads first)
   const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);

@@ -189,13 +189,13 @@ constexpr int SU2_NQ = 24;  // partial sums per CTA (the measurement pass uses 2
 }  // namespace
 
 // Bytes of one ring slot: per halo site 3 links + doublet (quaternions) and 3 U(1) fields.
-__host__ __device__ inline size_t su2_slot_bytes(int TX, int TY, int esz) {
-  const size_t hs = (size_t)(TX + 2) * (TY + 2);
-  return (19 * hs * esz + 127) / 128 * 128;
+__host__ __device__ constexpr size_t su2_slot_bytes(int TX, int TY, int esz) {
+  return (19 * (size_t)(TX + 2) * (TY + 2) * esz + 127) / 128 * 128;
 }
+constexpr int SU2_TY = 8;  // tile height of the pass; the width TX (32 or 16) is a template parameter
 
 // RED: 0 = no sums, 1 = sums for the Friedmann kicks, 2 = full measurement.
-template <typename T, int RED>
+template <typename T, int RED, int TX>
 __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_pass_su2(const PassArgs P) {
   constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 6 : 23);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -203,16 +203,16 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
   __shared__ unsigned last_s;
   const LatConst& L = P.lat[0];
   const int N = L.N;
-  const int TX = blockDim.x, TY = blockDim.y, nth = TX * TY;
+  constexpr int TY = SU2_TY, nth = TX * TY;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int lane = tid & 31, warp = tid >> 5;
-  const int HX = TX + 2, HS = HX * (TY + 2);
+  constexpr int HX = TX + 2, HS = HX * (TY + 2);
   const int ntx = N / TX, nty = N / TY;
   const long long NN = (long long)N * N, V = L.V;
   const int parity = P.parity;
   const T* const src = reinterpret_cast<const T*>(L.buf[parity][0]);
   T* const dst = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
-  const size_t slot_b = su2_slot_bytes(TX, TY, sizeof(T));
+  constexpr size_t slot_b = su2_slot_bytes(TX, TY, sizeof(T));
 
   // coefficients: FP64 products by one lane, broadcast in the storage precision
   T cf[13];
@@ -622,21 +622,16 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
   __threadfence();
 }
 
-template __global__ void dk_pass_su2<float, 0>(const PassArgs);
-template __global__ void dk_pass_su2<float, 1>(const PassArgs);
-template __global__ void dk_pass_su2<float, 2>(const PassArgs);
-template __global__ void dk_pass_su2<double, 0>(const PassArgs);
-template __global__ void dk_pass_su2<double, 1>(const PassArgs);
-template __global__ void dk_pass_su2<double, 2>(const PassArgs);
-
 typedef void (*PassKernel)(const PassArgs);
 
-PassKernel su2_pass_kernel(int fp32, int red) {
-  static const PassKernel tab[2][3] = {
-      {dk_pass_su2<double, 0>, dk_pass_su2<double, 1>, dk_pass_su2<double, 2>},
-      {dk_pass_su2<float, 0>, dk_pass_su2<float, 1>, dk_pass_su2<float, 2>}};
-  if (red < 0 || red > 2) return nullptr;
-  return tab[fp32 ? 1 : 0][red];
+PassKernel su2_pass_kernel(int fp32, int red, int TX) {
+  static const PassKernel tab[2][2][3] = {
+      {{dk_pass_su2<double, 0, 16>, dk_pass_su2<double, 1, 16>, dk_pass_su2<double, 2, 16>},
+       {dk_pass_su2<float, 0, 16>, dk_pass_su2<float, 1, 16>, dk_pass_su2<float, 2, 16>}},
+      {{dk_pass_su2<double, 0, 32>, dk_pass_su2<double, 1, 32>, dk_pass_su2<double, 2, 32>},
+       {dk_pass_su2<float, 0, 32>, dk_pass_su2<float, 1, 32>, dk_pass_su2<float, 2, 32>}}};
+  if (red < 0 || red > 2 || (TX != 16 && TX != 32)) return nullptr;
+  return tab[TX == 32 ? 1 : 0][fp32 ? 1 : 0][red];
 }
 
 size_t su2_smem_bytes(int TX, int TY, int esz) { return 3 * su2_slot_bytes(TX, TY, esz); }
