@@ -45,12 +45,29 @@ PASSES_PER_STEP = 3
 # profiles/dk_pass_fp32_256_ncu.md (one cooperative launch of the three VV4
 # passes of a step, divided by 3), valid only for the kernel source it was
 # taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "527eaa941d8a5967", "bytes_per_launch": 503718485}}
+NCU_TRAFFIC = {"f32": {"source_hash": "28d4993f1604ce49", "bytes_per_launch": 503003051}}
 # FP64 instructions (DFMA, DADD, DMUL) and operations (FMA = 2) per site per pass
 # of the FP64 plain kernel, from one ncu capture of the sass instruction counters
 # (profiles/dk_pass_fp64_256_ncu.md)
-NCU_FP64_OPS = {"source_hash": "527eaa941d8a5967", "instructions_per_site_pass": 46.443,
+NCU_FP64_OPS = {"source_hash": "28d4993f1604ce49", "instructions_per_site_pass": 46.443,
                 "flops_per_site_pass": 60.811}
+
+
+# Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
+# (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture
+# (profiles/dk_pass_su2_fp32_128_ncu.md), valid for the kernel source it was taken on.
+NCU_SU2 = {"source_hash": "c2e29a48ab06c597", "thread_instructions_per_site": 2042.1,
+           "dram_bytes_per_site": 279.4}
+# instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
+ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
+
+
+def su2_source_hash():
+    h = hashlib.sha256()
+    for name in ("pass_su2.cu", "common.cuh", "tail.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -402,9 +419,17 @@ def other_workloads(P, torch, stream, peak):
     rel = lat.gauss()[0]
     lat.close()
     gbs = 256 ** 3 * 35 * 2 * 4 / (ms / n * 1e-3) / 1e9
-    out["su2u1_doublet_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
-                                        "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
-                                        "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0>"}
+    row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+           "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
+           "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0,32>"}
+    if NCU_SU2["source_hash"] == su2_source_hash():
+        ipc = NCU_SU2["thread_instructions_per_site"]
+        ach = 256 ** 3 * ipc / (ms / n * 1e-3)
+        row["issue_roof"] = {"thread_instructions_per_site": ipc, "achieved_lane_instr_per_s": ach,
+                             "peak_lane_instr_per_s": ISSUE_PEAK_LANE_INSTR_PER_S,
+                             "frac": ach / ISSUE_PEAK_LANE_INSTR_PER_S,
+                             "ncu_dram_bytes_per_site": NCU_SU2["dram_bytes_per_site"]}
+    out["su2u1_doublet_256_fp32_lf"] = row
     # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
     Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
     E = P.Ensemble(P.MODEL_LPHI4_CHI, Ns, [KIR * N_LAT / n for n in Ns], ALPHA, list(range(1, 65)),
