@@ -120,6 +120,9 @@ def lib():
             L.clo_occupation.argtypes = [c_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
+            L.clo_norm_spectrum.argtypes = [c_p, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]
             L.clo_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
             L.clo_philox4x32_10.restype = None
             L.clo_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -292,6 +295,22 @@ class Oracle:
             raise ValueError("clo_occupation failed (%d)" % rc)
         n = nb.value
         return k[:n].copy(), nk[:n].copy(), m[:n].copy()
+
+    def norm_spectrum(self, dk_bin=1.0, fo2=None):
+        """(k, Delta_r, Delta_r', n, multiplicity) of the charged field's modulus r = |phi|
+        (gauge models); fo2 = (f*/omega*)^2, default 1/fluct_amp2."""
+        if fo2 is None:
+            fo2 = 1.0 / self.params.fluct_amp2
+        cap = 4096
+        k, d1, d2, n = (np.zeros(cap) for _ in range(4))
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.clo_norm_spectrum(self.h, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
+                                      m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        if rc != 0:
+            raise ValueError("clo_norm_spectrum failed (%d)" % rc)
+        b = nb.value
+        return k[:b].copy(), d1[:b].copy(), d2[:b].copy(), n[:b].copy(), m[:b].copy()
 
     def adjoint(self, nsteps, objective=0, field=1, what=0, dk_bin=1.0, bin=1, scale=False):
         """Discrete adjoint: (J, dJ/dq, lam) with lam[f][w] = dJ/d(field f, what w) at

@@ -1408,6 +1408,72 @@ int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, doubl
   return 0;
 }
 
+// Spectra of the modulus of a charged field (the "norm" spectra of the gauge
+// models' outputs, Sec. 4.5; the modulus is what the manual's `norm` gives):
+//   r = |phi| = sqrt(sum_c phi_c^2 / 2)   (U(1) field: c = 0, 1; doublet: c = 0..3),
+//   r' = sum_c phi_c phi_c' / (2 r),       phi_c' = a^{alpha-3} pi_c   (0 where r = 0),
+// delta_f, delta_fp = eq. discretePS of r and r' on clo_spectrum's shells, and n =
+// eq. OccuppationNum applied to r with w_b^2 = k_b^2 + a^2 <V''(r)>, V(r) = lam (r^2 - v^2)^2,
+// so V''(r) = lam (12 r^2 - 4 v^2), and fo2 = (f*/omega*)^2.
+// reading: the manual lists Delta, Delta' and n of these fields without formulas;
+// the modulus is gauge invariant, its components are not.
+int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
+                      double* n, int64_t* mult, int cap, int* nbins) {
+  if (!c || !c->gauge() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
+  const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
+  if (nbins) *nbins = nb;
+  if (nb > cap) return -2;
+  const double V = (double)c->V, a = c->a, H = c->b / c->a, al = c->alpha;
+  const double apm = std::pow(a, al - 3.0);
+  std::vector<cplx> R(c->V), Rp(c->V), G(c->V);
+  double m2 = 0.0;
+  for (long s = 0; s < c->V; ++s) {
+    double r2 = 0.0, rr = 0.0;
+    for (int q = 0; q < c->nf; ++q) {
+      r2 += 0.5 * c->phi[q][s] * c->phi[q][s];
+      rr += 0.5 * c->phi[q][s] * apm * c->pi[q][s];
+    }
+    const double r = std::sqrt(r2), rp = r > 0.0 ? rr / r : 0.0;
+    R[s] = cplx(r, 0.0);
+    Rp[s] = cplx(rp, 0.0);
+    G[s] = cplx(rp + H * r, 0.0);
+    m2 += c->p.lam * (12.0 * r2 - 4.0 * c->p.v * c->p.v);
+  }
+  m2 /= V;
+  fft3d(R, c->N, -1);
+  fft3d(Rp, c->N, -1);
+  fft3d(G, c->N, -1);
+  std::vector<double> s1(nb, 0.0), s1p(nb, 0.0), s2(nb, 0.0), sn(nb, 0.0);
+  std::vector<int64_t> cnt(nb, 0);
+  for (long idx = 1; idx < c->V; ++idx) {
+    const double nn = mode_k(c, idx) / c->kIR;
+    int b = (int)std::floor(nn / dk_bin);
+    if (b >= nb) b = nb - 1;
+    s1[b] += std::norm(R[idx]);
+    s1p[b] += std::norm(Rp[idx]);
+    s2[b] += std::norm(G[idx]);
+    sn[b] += nn;
+    cnt[b] += 1;
+  }
+  const double fac = std::pow(c->dx / (double)c->N, 3.0);
+  const double L = c->N * c->dx, C = a * a * L * L * L / (2.0 * V * V) * fo2;
+  const double a2p = std::pow(a, 2.0 * (1.0 - al));
+  for (int b = 0; b < nb; ++b) {
+    if (cnt[b] == 0) { k[b] = 0.0; df[b] = dfp[b] = n[b] = 0.0; mult[b] = 0; continue; }
+    const double nbar = sn[b] / (double)cnt[b], kb = c->kIR * nbar;
+    k[b] = kb;
+    mult[b] = cnt[b];
+    const double sh = kb * kb * kb / (2.0 * PI * PI) * fac / (4.0 * PI * nbar * nbar);
+    df[b] = sh * s1[b];
+    dfp[b] = sh * s1p[b];
+    const double w2 = kb * kb + a * a * m2;
+    if (!(w2 > 0.0)) { n[b] = std::nan(""); continue; }
+    const double w = std::sqrt(w2);
+    n[b] = C * (w * s1[b] / (double)cnt[b] + a2p * s2[b] / ((double)cnt[b] * w));
+  }
+  return 0;
+}
+
 }  // extern "C"
 
 // ===========================================================================
