@@ -164,6 +164,19 @@ cl_status cl_spectrum(cl_ctx* ctx, int field, int what, double dk_bin, double* k
 cl_status cl_get_state(cl_ctx* ctx, int field, int what, double* host_out);
 cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
 
+/* Gauge models (one lattice): spectra of the modulus of the charged field,
+ * r = |phi| = sqrt(sum_c phi_c^2/2) (the U(1) field's two components or the
+ * doublet's four), and of r' = sum_c phi_c phi_c'/(2 r) (phi_c' = a^{alpha-3} pi_c;
+ * 0 where r = 0): df, dfp = eq. discretePS of r and r' on cl_spectrum's shells,
+ * n = eq. OccuppationNum applied to r with w_b^2 = k_b^2 + a^2 <V''(r)>,
+ * V = lam (r^2 - v^2)^2, V'' = lam (12 r^2 - 4 v^2) (the manual's spectrum outputs
+ * of the charged scalars, Sec. 4.5, with its `norm`: the modulus, which is gauge
+ * invariant).  fo2 = (f_s/omega_s)^2; fo2 <= 0 takes 1/fluct_amp2.  k, df, dfp,
+ * n, mult hold `cap` entries; *nbins receives the bin count.  CL_EUNSUPPORTED for
+ * scalar models and ensembles.  Closes the stream of kicks; synchronises. */
+cl_status cl_norm_spectrum(cl_ctx* ctx, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,
+                           int64_t* mult, int cap, int* nbins);
+
 /* Doublet model: whole arrays by index, in the order
  *   0..3 phi_c, 4..7 pi_c, 8..10 A_i, 11..13 pi_A,i,
  *   14 + 4 i + k: component u_k of the SU(2) link U_i(n) = u0 - i (u1 s1 + u2 s2 + u3 s3)

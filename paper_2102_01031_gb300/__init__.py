@@ -35,7 +35,7 @@ EXPORTS = (
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
-    "cl_get_array", "cl_set_array",
+    "cl_get_array", "cl_set_array", "cl_norm_spectrum",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -125,6 +125,8 @@ def lib():
     L.cl_get_state.argtypes = [vp, ip, ip, dp]
     L.cl_set_state.argtypes = [vp, ip, ip, dp]
     L.cl_get_array.argtypes = [vp, ip, dp]
+    L.cl_norm_spectrum.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                   ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     L.cl_set_array.argtypes = [vp, ip, dp]
     L.cl_get_scalars.argtypes = [vp, dp, dp, dp]
     L.cl_set_scalars.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -312,6 +314,19 @@ class Lattice:
         _check(self.L, self.h, rc, "cl_spectrum")
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
+
+    def norm_spectrum(self, dk_bin=1.0, fo2=0.0):
+        """cl_norm_spectrum (gauge models): (k, Delta_r, Delta_r', n, multiplicity) of the
+        charged field's modulus r = |phi|; fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2)."""
+        cap = 4096
+        k, d1, d2, n = (np.zeros(cap) for _ in range(4))
+        m = np.zeros(cap, dtype=np.int64)
+        nb = ctypes.c_int()
+        rc = self.L.cl_norm_spectrum(self.h, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_norm_spectrum")
+        b = nb.value
+        return k[:b].copy(), d1[:b].copy(), d2[:b].copy(), n[:b].copy(), m[:b].copy()
 
     def em_spectrum(self, which, dk_bin=1.0):
         """cl_em_spectrum: (k, delta, multiplicity) of the U(1) electric (which=0) or

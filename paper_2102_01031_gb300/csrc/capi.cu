@@ -50,6 +50,8 @@ cudaError_t launch_combine_to_complex(int, const void*, double, const void*, dou
 cudaError_t launch_u1_plaquette_field(int, const void*, const void*, int, int, int, double, double, double2*,
                                       cudaStream_t);
 cudaError_t launch_spec_mean(const double*, int, int, double*, cudaStream_t);
+cudaError_t launch_norm_field(int fp32, const void* const* f, const void* const* p, int nc, double apm, double H,
+                              int mode, double2* out, long long V, cudaStream_t st);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
 cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
                                  void*, long long, int, cudaStream_t);
@@ -1353,6 +1355,93 @@ cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double*
     }
     const double w = std::sqrt(w2);
     n[b] = C * (w * h[nb + b] / cnt + a2p * h[3 * nb + nb + b] / (cnt * w));
+  }
+  return check_status(c);
+}
+
+cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,
+                           int64_t* mult, int cap, int* nbins) {
+  if (!c || !k || !df || !dfp || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->nlat != 1 || (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS))
+    return fail(c, CL_EUNSUPPORTED, "modulus spectra cover single lattices of the gauge models");
+  if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
+  if (!(fo2 > 0.0)) {
+    if (!(c->p.fluct_amp2 > 0.0)) return fail(c, CL_EINVAL, "need (f*/omega*)^2 > 0 (fluct_amp2 is 0)");
+    fo2 = 1.0 / c->p.fluct_amp2;
+  }
+  const LatHost& H = c->lats[0];
+  const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
+  *nbins = nb;
+  if (nb > cap) return fail(c, CL_EINVAL, "cap %d < %d bins", cap, nb);
+  if (nb > 2048) return fail(c, CL_EINVAL, "too many bins (dk_bin too small)");
+  cl_status s = measure(c, 0);  // the synchronised state and its volume averages
+  if (s != CL_OK) return s;
+  LatScalars S;
+  CU(cudaMemcpyAsync(&S, &c->d_sc[0], sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  const int nblk = 2 * c->nsm;
+  if (c->spec_lats < 3) {  // four rows of bins
+    CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_spec);
+    c->d_spec = nullptr;
+    c->spec_lats = 0;
+    CU(cudaMalloc(&c->d_spec, ((size_t)3 * 2048 * nblk + (size_t)4 * 3 * 2048) * sizeof(double)));
+    c->spec_lats = 3;
+  }
+  double* part = c->d_spec;
+  double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [4][3 nb]: k, delta or shell sum, mult
+  double2* F = c->d_cplx;
+  CU(cudaStreamSynchronize(c->stream));
+  const double a = S.a, Hc = S.b / S.a, al = c->alpha;
+  const bool u1 = c->model == CL_MODEL_U1_HIGGS;
+  const int nc = u1 ? 2 : 4;
+  const void* f[4];
+  const void* p[4];
+  for (int q = 0; q < nc; ++q) {
+    f[q] = arr_ptr(c, 0, c->parity, u1 ? 2 * q : q);
+    p[q] = arr_ptr(c, 0, c->parity, u1 ? 2 * q + 1 : 4 + q);
+  }
+  // rows: 0 Delta_r, 1 shell sums |r_k|^2, 2 Delta_r', 3 shell sums |r'_k + (a'/a) r_k|^2
+  for (int mode = 0; mode < 3; ++mode) {
+    CU(launch_norm_field(c->fp32, f, p, nc, std::pow(a, al - 3.0), Hc, mode, F, H.V, c->stream));
+    ++c->launches;
+    s = fft3d(c, H.N, F, -1);
+    if (s != CL_OK) return s;
+    if (mode == 0) {
+      CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins, c->stream, 0));
+      CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins + (size_t)3 * nb, c->stream, 1));
+      c->launches += 4;
+    } else {
+      CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins + (size_t)(mode + 1) * 3 * nb, c->stream,
+                     mode == 1 ? 0 : 1));
+      c->launches += 2;
+    }
+  }
+  std::vector<double> h(12 * nb);
+  CU(cudaMemcpyAsync(h.data(), bins, 12 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  // <V''(r)> = lam (12 <r^2> - 4 v^2), <r^2> = sum_c <phi_c^2>/2 from the measurement
+  double r2 = 0.0;
+  for (int q = 0; q < nc; ++q) r2 += 0.5 * S.obs.mean_phi2[q];
+  const double m2 = c->p.lam * (12.0 * r2 - 4.0 * c->p.v * c->p.v);
+  const double V = (double)H.V, L = H.N * H.dx;
+  const double C = a * a * L * L * L / (2.0 * V * V) * fo2, a2p = std::pow(a, 2.0 * (1.0 - al));
+  for (int b = 0; b < nb; ++b) {
+    const double cnt = h[2 * nb + b];
+    k[b] = h[b];
+    mult[b] = (int64_t)cnt;
+    df[b] = h[nb + b];
+    dfp[b] = h[6 * nb + nb + b];
+    if (cnt == 0.0) {
+      n[b] = 0.0;
+      continue;
+    }
+    const double w2 = h[b] * h[b] + a * a * m2;
+    if (!(w2 > 0.0)) {
+      n[b] = std::nan("");
+      continue;
+    }
+    const double w = std::sqrt(w2);
+    n[b] = C * (w * h[3 * nb + nb + b] / cnt + a2p * h[9 * nb + nb + b] / (cnt * w));
   }
   return check_status(c);
 }

@@ -549,6 +549,49 @@ cudaError_t launch_combine_to_complex(int fp32, const void* x, double cx, const 
   return cudaGetLastError();
 }
 
+// Modulus of a charged field and its time derivative (FP64 from the stored
+// values): r = sqrt(sum_c phi_c^2/2), r' = sum_c phi_c phi_c'/(2 r) with
+// phi_c' = apm pi_c (0 where r = 0).  mode 0: r; 1: r'; 2: r' + H r.
+struct NormArgs {
+  const void* f[4];
+  const void* p[4];
+  int nc, mode;
+  double apm, H;
+};
+template <typename T>
+__global__ void norm_field_kernel(const NormArgs A, double2* out, long long V) {
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    double r2 = 0.0, rr = 0.0;
+    for (int c = 0; c < A.nc; ++c) {
+      const double f = (double)reinterpret_cast<const T*>(A.f[c])[n];
+      const double q = (double)reinterpret_cast<const T*>(A.p[c])[n];
+      r2 += 0.5 * f * f;
+      rr += 0.5 * f * (A.apm * q);
+    }
+    const double r = sqrt(r2), rp = r > 0.0 ? rr / r : 0.0;
+    const double v = A.mode == 0 ? r : (A.mode == 1 ? rp : rp + A.H * r);
+    out[n] = make_double2(v, 0.0);
+  }
+}
+
+cudaError_t launch_norm_field(int fp32, const void* const* f, const void* const* p, int nc, double apm, double H,
+                              int mode, double2* out, long long V, cudaStream_t st) {
+  NormArgs A;
+  for (int c = 0; c < 4; ++c) {
+    A.f[c] = c < nc ? f[c] : nullptr;
+    A.p[c] = c < nc ? p[c] : nullptr;
+  }
+  A.nc = nc;
+  A.mode = mode;
+  A.apm = apm;
+  A.H = H;
+  const int tb = 256;
+  if (fp32) norm_field_kernel<float><<<grid_for(V, tb), tb, 0, st>>>(A, out, V);
+  else norm_field_kernel<double><<<grid_for(V, tb), tb, 0, st>>>(A, out, V);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(int fp32, int to_double, const void* in, void* out, long long V, cudaStream_t st) {
   const int tb = 256;
   if (to_double) {

@@ -249,3 +249,35 @@ def test_errors(P):
     with pytest.raises(P.ClError) as e:
         g.em_spectrum(0)
     assert e.value.status == P.CL_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_modulus_spectra_match(P, precision, tol):
+    """cl_norm_spectrum against the oracle: Delta of |Phi|, of |Phi|', and the
+    occupation number of |Phi| (self-consistent expansion, a != 1)."""
+    kw = dict(SU2, integrator=O.VV2, expansion=O.EXP_SELF)
+    g, o = both(P, 32, 0.8, 1.0, 2, precision=precision, **kw)
+    g.step(10)
+    o.step(10)
+    rg, ro = g.norm_spectrum(), o.norm_spectrum()
+    assert np.array_equal(rg[4], ro[4])
+    assert np.abs(rg[0] - ro[0]).max() < 1e-12
+    for x, y in zip(rg[1:4], ro[1:4]):
+        assert np.abs(x - y).max() <= tol * np.abs(y).max()
+
+
+def test_modulus_spectra_u1(P):
+    kw = dict(dt=0.01, integrator=O.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
+              phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=O.EXP_OFF, fstar_over_mp=0.5)
+    g = P.Lattice(O.MODEL_U1_HIGGS, 32, 0.5, 1.0, 3, P.make_params(**kw))
+    o = O.Oracle(O.MODEL_U1_HIGGS, 32, 0.5, 1.0, 3, O.make_params(**kw))
+    g.step(20)
+    o.step(20)
+    rg, ro = g.norm_spectrum(), o.norm_spectrum()
+    assert np.array_equal(rg[4], ro[4])
+    for x, y in zip(rg[1:4], ro[1:4]):
+        assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
+    s = P.Lattice(O.MODEL_LPHI4, 16, 0.5, 1.0, 1, P.make_params(fluct_amp2=1e-2))
+    with pytest.raises(P.ClError) as e:
+        s.norm_spectrum()
+    assert e.value.status == P.CL_EUNSUPPORTED
