@@ -165,6 +165,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest x over the ranks of the process group (x itself for one rank):
+    the whole job takes as long as its slowest replica."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws, units_per_rank, seconds):
+    """Whole-job throughput of ws replicas that each processed units_per_rank units,
+    over the slowest replica's time."""
+    return ws * units_per_rank / seconds
+
+
 def cpu_oracle_rate(budget_s, steps_hint=None):
     """The oracle, as it stands, on a bounded sample of the workload: the same
     model and lattice spacing on a smaller periodic box; site-updates/s."""
@@ -188,8 +205,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle as O  # noqa: F401
-    budget = 150.0
-    L, n_ref, _ = cpu_oracle_rate(budget, steps_hint=args.steps + args.warmup)
+    L, n_ref, _ = cpu_oracle_rate(args.ref_budget, steps_hint=args.steps + args.warmup)
     for _ in range(args.warmup):
         L.step(1)
     t0 = time.perf_counter()
@@ -235,10 +251,7 @@ def time_device(P, torch, lat, steps, warmup, rank, ws):
     launches = lat.launches() - n0
     ms = e0.elapsed_time(e1)
     pass_ms, npass = lat.pass_timing(reset=True)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws)
     return ms, launches, pass_ms / max(npass, 1), npass
 
 
@@ -315,18 +328,14 @@ def run_ours(args):
                 t0 = time.perf_counter()
                 fn(k2)
                 torch.cuda.synchronize()
-                t = time.perf_counter() - t0
-                if ws > 1:
-                    tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-                    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-                    t = float(tt.item())
-                return t
+                return max_over_ranks(time.perf_counter() - t0, ws)
 
             t_serial = timed(e2e_serial)
             t_pipe = timed(e2e_pipelined)
             lat2.close()
             del lat2
-            results["e2e"] = dict(value=ws * sites * k2 / t_pipe, serial=ws * sites * k2 / t_serial,
+            results["e2e"] = dict(value=replica_rate(ws, sites * k2, t_pipe),
+                                  serial=replica_rate(ws, sites * k2, t_serial),
                                   h2d=nbytes, d2h=ctypes_sizeof_energies(P), steps=k2)
         lat.close()
         del lat
@@ -339,8 +348,8 @@ def run_ours(args):
         return 0
 
     f32, f64 = results["f32"], results["f64"]
-    value = ws * sites * f32["steps"] / (f32["ms"] * 1e-3)
-    v64 = ws * sites * f64["steps"] / (f64["ms"] * 1e-3)
+    value = replica_rate(ws, sites * f32["steps"], f32["ms"] * 1e-3)
+    v64 = replica_rate(ws, sites * f64["steps"], f64["ms"] * 1e-3)
     bpl = PASS_BYTES_PER_SITE["f32"] * sites
     achieved = bpl / (f32["pass_ms"] * 1e-3) / 1e9
     bpl64 = PASS_BYTES_PER_SITE["f64"] * sites
@@ -557,6 +566,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="reference arm: site-steps budget / 1e6 that sizes its oracle box")
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
     ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "su2_128", "adj128", "adj128self"),
                     help="run one small case for an ncu capture and exit")
