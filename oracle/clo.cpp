@@ -1307,24 +1307,46 @@ int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k
 // reading: the manual names these outputs without a formula; the field
 // strength from the plaquette's sine is the compact form whose small-angle
 // limit is the forward-difference curl.
+//
+// Doublet model: which = 0, 1 are the U(1) field's E and B as above (B needs
+// gQ != 0); which = 2, 3 the SU(2) field's, summed over the 9 components (a, i):
+//   E_i^a = a^{alpha-1} pi_B,i^a,
+//   B_i^a = (1/2) eps_ijk G_jk^a,  G_jk^a = Tr[(i sigma_a/2)(U_jk - U_jk^dag)]/(gQB dx^2)
+// (the SU(N) toolkit's expression for G from the plaquette; its small-angle limit
+// is the forward-difference curl of B_i^a).
+// reading: the manual's spectra_norm_SU2 output names these without a formula;
+// the colour components are summed like the spatial ones.
 int clo_em_spectrum(const clo_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult,
                     int cap, int* nbins) {
-  if (!c || !c->gauge() || (which != 0 && which != 1) || !(dk_bin > 0.0)) return -1;
+  const int wmax = c && c->su2() ? 3 : 1;
+  if (!c || !c->gauge() || which < 0 || which > wmax || !(dk_bin > 0.0)) return -1;
+  if (which == 1 && c->p.gQ == 0.0) return -1;  // no U(1) field
   const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
   if (nbins) *nbins = nb;
   if (nb > cap) return -2;
   const double gdx2 = c->p.gQ * c->dx * c->dx, ae = std::pow(c->a, c->alpha - 1.0);
+  const double bdx2 = c->p.gQB * c->dx * c->dx;
   std::vector<double> sp(nb, 0.0), sn(nb, 0.0);
   std::vector<int64_t> cnt(nb, 0);
-  for (int comp = 0; comp < 3; ++comp) {
+  const int ncomp = which >= 2 ? 9 : 3;
+  for (int comp = 0; comp < ncomp; ++comp) {
     std::vector<cplx> F(c->V);
+    const int i = which >= 2 ? comp / 3 : comp, a = comp % 3 + 1;
+    const int j = (i + 1) % 3, l = (i + 2) % 3;  // B_i = F_jl for (i, j, l) cyclic
     for (long n = 0; n < c->V; ++n) {
       double v;
       if (which == 0) {
-        v = ae * c->piA[comp][n];
-      } else {
-        const int j = (comp + 1) % 3, l = (comp + 2) % 3;  // B_i = F_jl for (i, j, l) cyclic
+        v = ae * c->piA[i][n];
+      } else if (which == 1) {
         v = std::sin(plaq(c, n, j, l)) / gdx2;
+      } else if (which == 2) {
+        v = ae * c->piB[i][a - 1][n];
+      } else {
+        const M2 P = su2_plaq(c, n, j, l), Pd = dag(P);
+        M2 D;
+        for (int r = 0; r < 2; ++r)
+          for (int q = 0; q < 2; ++q) D.m[r][q] = P.m[r][q] - Pd.m[r][q];
+        v = (cplx(0.0, 0.5) * trace(mul(pauli(a), D))).real() / bdx2;
       }
       F[n] = cplx(v, 0.0);
     }

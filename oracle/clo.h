@@ -87,9 +87,11 @@ int clo_gauss_constraint(const clo_ctx* c, double* rel, double* lhs_abs, double*
                          double* max_abs);
 int clo_spectrum(const clo_ctx* c, int field, int what, double dk_bin, double* k,
                  double* delta, int64_t* mult, int cap, int* nbins);
-/* U(1) model: binned spectrum of the electric (which = 0: E_i = a^{alpha-1} pi_A,i)
- * or magnetic (which = 1: B_i = eps_ijk sin(theta_jk)/(2 gQ dx^2)) field, |.|^2
- * summed over components, normalised as clo_spectrum.  -1 for scalar models. */
+/* Gauge models: binned spectrum of the U(1) electric (which = 0: E_i = a^{alpha-1} pi_A,i)
+ * or magnetic (which = 1: B_i = eps_ijk sin(theta_jk)/(2 gQ dx^2)) field; doublet model
+ * also the SU(2) electric (2: E_i^a = a^{alpha-1} pi_B,i^a) or magnetic (3: B_i^a from
+ * G_jk^a = Tr[(i s_a/2)(U_jk - U_jk^dag)]/(gQB dx^2)) field; |.|^2 summed over
+ * components, normalised as clo_spectrum.  -1 for scalar models (and which = 1 with gQ = 0). */
 int clo_em_spectrum(const clo_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult,
                     int cap, int* nbins);
 /* Lattice occupation number n_b of scalar field `field` per spectrum bin
