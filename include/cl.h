@@ -257,13 +257,17 @@ cl_status cl_lattice_tile(cl_ctx* ctx, int lat, int* N, int* BY, int* stages);
 cl_status cl_occupation(cl_ctx* ctx, int field, double dk_bin, double fo2, double* k, double* n,
                         int64_t* mult, int cap, int* nbins);
 
-/* U(1) model (single lattice): binned spectrum of the electric (which = 0) or
- * magnetic (which = 1) field (eq. ElectricMagneticDefs, the gauge spectra of
+/* Gauge models (single lattice): binned spectrum of the U(1) electric (which = 0)
+ * or magnetic (which = 1) field (eq. ElectricMagneticDefs, the gauge spectra of
  * the outputs of Sec. 5.3):  E_i = F_0i = a^{alpha-1} pi_A,i;
  * B_i = (1/2) eps_ijk F_jk with the compact F_jk = sin(theta_jk)/(gQ dx^2),
- * theta_jk(n) = gQ dx [A_j(n) + A_k(n+j) - A_j(n+k) - A_k(n)].  delta_b is eq.
- * discretePS with |f(k)|^2 summed over the three components; k and mult as
- * cl_spectrum.  CL_EUNSUPPORTED for scalar models.  Synchronises the stream. */
+ * theta_jk(n) = gQ dx [A_j(n) + A_k(n+j) - A_j(n+k) - A_k(n)].  Doublet model
+ * also the SU(2) electric (which = 2: E_i^a = a^{alpha-1} pi_B,i^a) and magnetic
+ * (which = 3: B_i^a = (1/2) eps_ijk G_jk^a, G_jk^a = Tr[(i s_a/2)(U_jk - U_jk^dag)]/(gQB dx^2)
+ * from the plaquette, SU(N) toolkit) fields.  delta_b is eq. discretePS with
+ * |f(k)|^2 summed over the components (three, or nine with colour); k and mult as
+ * cl_spectrum.  CL_EUNSUPPORTED for scalar models and for which = 1 with gQ = 0.
+ * Synchronises the stream. */
 cl_status cl_em_spectrum(cl_ctx* ctx, int which, double dk_bin, double* k, double* delta, int64_t* mult,
                          int cap, int* nbins);
 

@@ -330,7 +330,8 @@ class Lattice:
 
     def em_spectrum(self, which, dk_bin=1.0):
         """cl_em_spectrum: (k, delta, multiplicity) of the U(1) electric (which=0) or
-        magnetic (which=1) field."""
+        magnetic (which=1) field; doublet model also the SU(2) electric (2) and
+        magnetic (3) fields, summed over colour."""
         cap = 4096
         k, d = np.zeros(cap), np.zeros(cap)
         m = np.zeros(cap, dtype=np.int64)

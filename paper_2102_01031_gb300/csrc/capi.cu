@@ -50,6 +50,8 @@ cudaError_t launch_combine_to_complex(int, const void*, double, const void*, dou
 cudaError_t launch_u1_plaquette_field(int, const void*, const void*, int, int, int, double, double, double2*,
                                       cudaStream_t);
 cudaError_t launch_spec_mean(const double*, int, int, double*, cudaStream_t);
+cudaError_t launch_su2_plaquette_field(int fp32, const void* Uj, const void* Ul, int j, int l, int a, int N,
+                                       double inv_bdx2, double2* out, cudaStream_t st);
 cudaError_t launch_norm_field(int fp32, const void* const* f, const void* const* p, int nc, double apm, double H,
                               int mode, double2* out, long long V, cudaStream_t st);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
@@ -1449,9 +1451,12 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
 cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult, int cap,
                          int* nbins) {
   if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->model != CL_MODEL_U1_HIGGS || c->nlat != 1)
-    return fail(c, CL_EUNSUPPORTED, "electric and magnetic spectra need a single U(1) lattice");
-  if (which != 0 && which != 1) return fail(c, CL_EINVAL, "which must be 0 (electric) or 1 (magnetic)");
+  const bool su2 = c->model == CL_MODEL_SU2U1_HIGGS;
+  if ((c->model != CL_MODEL_U1_HIGGS && !su2) || c->nlat != 1)
+    return fail(c, CL_EUNSUPPORTED, "electric and magnetic spectra need a single gauge lattice");
+  if (which < 0 || which > (su2 ? 3 : 1))
+    return fail(c, CL_EINVAL, "which must be 0 (electric) or 1 (magnetic)%s", su2 ? ", 2 or 3 (SU(2))" : "");
+  if (which == 1 && c->p.gQ == 0.0) return fail(c, CL_EUNSUPPORTED, "gQ = 0: no U(1) field");
   if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
   const LatHost& H = c->lats[0];
   const int nb = (int)std::floor(std::sqrt(3.0) * (H.N / 2) / dk_bin) + 1;
@@ -1474,17 +1479,30 @@ cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double*
   double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [3 nb]: k, shell sum, mult
   double2* F = c->d_cplx;
   CU(cudaStreamSynchronize(c->stream));
-  const double gd = c->p.gQ * H.dx, inv_gdx2 = 1.0 / (c->p.gQ * H.dx * H.dx), ae = std::pow(S.a, c->alpha - 1.0);
-  // arrays: A_i = 4 + 2i, pi_A,i = 5 + 2i (phi_0, pi_0, phi_1, pi_1 first)
+  const double gd = c->p.gQ * H.dx, ae = std::pow(S.a, c->alpha - 1.0);
+  const double inv_gdx2 = which == 1 ? 1.0 / (c->p.gQ * H.dx * H.dx) : 0.0;
+  const double inv_bdx2 = su2 ? 1.0 / (c->p.gQB * H.dx * H.dx) : 0.0;
+  // U(1) model arrays: A_i = 4 + 2i, pi_A,i = 5 + 2i; doublet model: A_i = 8 + i,
+  // pi_A,i = 11 + i, SU(2) link components 14 + 4i + k, pi_B,i^a = 26 + 3i + (a - 1)
+  auto A_arr = [&](int i) { return su2 ? 8 + i : 4 + 2 * i; };
+  auto pA_arr = [&](int i) { return su2 ? 11 + i : 5 + 2 * i; };
   std::vector<double> sum(nb, 0.0), kk(nb, 0.0), cnt(nb, 0.0), h(3 * nb);
-  for (int comp = 0; comp < 3; ++comp) {
+  const int ncomp = which >= 2 ? 9 : 3;
+  for (int comp = 0; comp < ncomp; ++comp) {
+    const int i = which >= 2 ? comp / 3 : comp, a = comp % 3 + 1;
+    const int j = (i + 1) % 3, l = (i + 2) % 3;  // B_i = F_jl with (i, j, l) cyclic
     if (which == 0) {
-      const void* pa = arr_ptr(c, 0, c->parity, 5 + 2 * comp);
+      const void* pa = arr_ptr(c, 0, c->parity, pA_arr(i));
       CU(launch_combine_to_complex(c->fp32, pa, ae, pa, 0.0, F, H.V, c->stream));
-    } else {  // B_i = F_jl with (i, j, l) cyclic
-      const int j = (comp + 1) % 3, l = (comp + 2) % 3;
-      CU(launch_u1_plaquette_field(c->fp32, arr_ptr(c, 0, c->parity, 4 + 2 * j), arr_ptr(c, 0, c->parity, 4 + 2 * l),
+    } else if (which == 1) {
+      CU(launch_u1_plaquette_field(c->fp32, arr_ptr(c, 0, c->parity, A_arr(j)), arr_ptr(c, 0, c->parity, A_arr(l)),
                                    j, l, H.N, gd, inv_gdx2, F, c->stream));
+    } else if (which == 2) {
+      const void* pb = arr_ptr(c, 0, c->parity, 26 + 3 * i + (a - 1));
+      CU(launch_combine_to_complex(c->fp32, pb, ae, pb, 0.0, F, H.V, c->stream));
+    } else {
+      CU(launch_su2_plaquette_field(c->fp32, arr_ptr(c, 0, c->parity, 14 + 4 * j),
+                                    arr_ptr(c, 0, c->parity, 14 + 4 * l), j, l, a, H.N, inv_bdx2, F, c->stream));
     }
     ++c->launches;
     s = fft3d(c, H.N, F, -1);

@@ -367,6 +367,41 @@ __global__ void u1_plaquette_field_kernel(const T* Aj, const T* Al, int j, int l
   }
 }
 
+// Colour component a (1..3) of the SU(2) field strength of plaquette (j, l) at
+// every site, G_jl^a = Tr[(i s_a/2)(U_jl - U_jl^dag)]/(gQB dx^2) = 2 p_a/(gQB dx^2),
+// with p the vector part of the plaquette U_j(n) U_l(n+j) U_j^dag(n+l) U_l^dag(n)
+// in the links' quaternion form U = u0 - i u.s (FP64 from the stored values).
+struct Quat {
+  double w, x, y, z;
+};
+__device__ inline Quat qprod(const Quat& a, const Quat& b) {
+  return Quat{a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + b.w * a.x + (a.y * b.z - a.z * b.y),
+              a.w * b.y + b.w * a.y + (a.z * b.x - a.x * b.z), a.w * b.z + b.w * a.z + (a.x * b.y - a.y * b.x)};
+}
+template <typename T>
+__global__ void su2_plaquette_field_kernel(const T* Uj, const T* Ul, int j, int l, int a, int N, double inv,
+                                           double2* out) {
+  const long long V = (long long)N * N * N;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int c[3] = {(int)(n % N), (int)((n / N) % N), (int)(n / ((long long)N * N))};
+    auto shifted = [&](int d) -> long long {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[d] = cc[d] + 1 == N ? 0 : cc[d] + 1;
+      return cc[0] + (long long)N * (cc[1] + (long long)N * cc[2]);
+    };
+    // component k of a link array block: (u0, u1, u2, u3) at k V
+    auto link = [&](const T* U, long long m, bool conj) {
+      const double s = conj ? -1.0 : 1.0;
+      return Quat{(double)U[m], s * (double)U[V + m], s * (double)U[2 * V + m], s * (double)U[3 * V + m]};
+    };
+    const Quat P = qprod(qprod(qprod(link(Uj, n, false), link(Ul, shifted(j), false)), link(Uj, shifted(l), true)),
+                         link(Ul, n, true));
+    const double pa = a == 1 ? P.x : (a == 2 ? P.y : P.z);
+    out[n] = make_double2(2.0 * pa * inv, 0.0);
+  }
+}
+
 // out = cx x + cy y (FP64), imaginary part 0.
 template <typename T>
 __global__ void combine_to_complex_kernel(const T* x, double cx, const T* y, double cy, double2* out, long long V) {
@@ -535,6 +570,19 @@ cudaError_t launch_u1_plaquette_field(int fp32, const void* Aj, const void* Al, 
   else
     u1_plaquette_field_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)Aj, (const double*)Al, j, l,
                                                                        N, gd, inv_gdx2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_su2_plaquette_field(int fp32, const void* Uj, const void* Ul, int j, int l, int a, int N,
+                                       double inv_bdx2, double2* out, cudaStream_t st) {
+  const long long V = (long long)N * N * N;
+  const int tb = 256;
+  if (fp32)
+    su2_plaquette_field_kernel<float><<<grid_for(V, tb), tb, 0, st>>>((const float*)Uj, (const float*)Ul, j, l, a, N,
+                                                                       inv_bdx2, out);
+  else
+    su2_plaquette_field_kernel<double><<<grid_for(V, tb), tb, 0, st>>>((const double*)Uj, (const double*)Ul, j, l, a,
+                                                                        N, inv_bdx2, out);
   return cudaGetLastError();
 }
 

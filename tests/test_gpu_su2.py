@@ -247,8 +247,8 @@ def test_errors(P):
     with pytest.raises(P.ClError):
         g.get(7, 0)
     with pytest.raises(P.ClError) as e:
-        g.em_spectrum(0)
-    assert e.value.status == P.CL_EUNSUPPORTED
+        g.em_spectrum(4)
+    assert e.value.status == P.CL_EINVAL
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
@@ -280,4 +280,24 @@ def test_modulus_spectra_u1(P):
     s = P.Lattice(O.MODEL_LPHI4, 16, 0.5, 1.0, 1, P.make_params(fluct_amp2=1e-2))
     with pytest.raises(P.ClError) as e:
         s.norm_spectrum()
+    assert e.value.status == P.CL_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_gauge_field_spectra_match(P, precision, tol):
+    """cl_em_spectrum of the doublet model (U(1) E, B and SU(2) E, B) against the
+    oracle, after 10 steps with self-consistent expansion."""
+    kw = dict(SU2, integrator=O.VV2, expansion=O.EXP_SELF)
+    g, o = both(P, 32, 0.8, 1.0, 4, precision=precision, **kw)
+    g.step(10)
+    o.step(10)
+    for which in range(4):
+        kg, dg, mg = g.em_spectrum(which)
+        ko, do, mo = o.em_spectrum(which)
+        assert np.array_equal(mg, mo)
+        assert np.abs(kg - ko).max() < 1e-12
+        assert np.abs(dg - do).max() <= tol * np.abs(do).max(), which
+    nou1 = P.Lattice(O.MODEL_SU2U1_HIGGS, 16, 0.8, 1.0, 1, P.make_params(**dict(SU2, gQ=0.0)))
+    with pytest.raises(P.ClError) as e:
+        nou1.em_spectrum(1)
     assert e.value.status == P.CL_EUNSUPPORTED
