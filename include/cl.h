@@ -194,8 +194,9 @@ cl_status cl_get_scalars(cl_ctx* ctx, double* eta, double* a, double* b);
 cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
 
 /* Raw state transfer in the storage precision, for end-to-end use: the whole
- * state (every field and momentum array, in field order, field then
- * momentum) is `*bytes` long.  Host buffers should be pinned for speed.
+ * state (every array of lattice 0 in storage order: field then momentum per
+ * field for the scalar and U(1) models, the order of cl_get_array for the
+ * doublet model) is `*bytes` long.  Host buffers should be pinned for speed.
  * Both synchronise the kick stream first; the copies are enqueued on the
  * context stream (cl_download_state waits for its copy to finish). */
 cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
@@ -239,7 +240,8 @@ cl_status cl_lattice_set_state(cl_ctx* ctx, int lat, int field, int what, const 
 cl_status cl_lattice_scalars(cl_ctx* ctx, int lat, double* eta, double* a, double* b);
 
 /* Tile shape the passes use for lattice `lat`: its N, its tile height BY
- * (rows of one CTA tile) and the context's number of ring stages. */
+ * (rows of one CTA tile) and the context's number of ring stages.  The doublet
+ * model's pass tiles x-y instead (BY reported as 0, 3 ring planes). */
 cl_status cl_lattice_tile(cl_ctx* ctx, int lat, int* N, int* BY, int* stages);
 
 /* Lattice occupation number of scalar field `field` (eq. OccuppationNum, with
