@@ -19,6 +19,7 @@
 
 #include "cl.h"
 #include "common.cuh"
+#include "su2_work.h"
 #include "worklist.h"
 
 namespace clg {
@@ -915,20 +916,10 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c), c->su2_tx), c->su2_tx * c->su2_ty,
       c->smem_bytes));
-  // work items (tile, z-chunk) over the resident CTAs: the number of z-chunks that
-  // minimises rounds x (planes per chunk + the 2 planes each item loads first)
+  // work items (tile, z-chunk) over the resident CTAs (su2_work.h)
   const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);
   const int R = c->nsm * std::max(nb, 1);
-  int nzc = 1;
-  double best = 1e300;
-  for (int k = 1; k <= std::max(1, N / 4); ++k) {
-    const double rounds = std::ceil((double)ntiles * k / R);
-    const double cost = rounds * ((double)N / k + 2.0);
-    if (cost < best - 1e-9) {
-      best = cost;
-      nzc = k;
-    }
-  }
+  const int nzc = su2_z_chunks(ntiles, N, R);
   c->grid = std::min(R, ntiles * nzc);
   c->nslot = c->grid;
   c->stages = 3;

@@ -1,7 +1,8 @@
 """CPU check of the DK-pass work split (csrc/worklist.h, the host code that
 cuts the plane tasks of a pass into per-CTA segments): compiled with g++ and
 run on single lattices (block-aligned split), uneven ensembles (contiguous
-cost-weighted split) and the up-only split of the U(1) pass."""
+cost-weighted split) and the up-only split of the U(1) pass; and of the
+doublet pass's (tile, z-chunk) items (csrc/su2_work.h)."""
 import os
 import shutil
 import subprocess
@@ -26,3 +27,5 @@ def test_worklist_covers_every_task_once(tmp_path):
     # the headline shape keeps its largest per-CTA cost within 2 % of the mean
     bal = {l.split()[1]: float(l.split()[-1]) for l in lines if " balance " in l}
     assert bal["fp32_256_by8_g152"] < 1.02
+    su2 = [l for l in lines if " su2_items " in l]
+    assert len(su2) == 5

@@ -3,12 +3,14 @@
 // CTA, slots contiguous per lattice and unique per (CTA, lattice), flush flags
 // on the last segment of each run, and the balance of the block-aligned split.
 // Prints one line per case: "OK <name> ..." or "FAIL <name>: <reason>".
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <set>
 #include <string>
 #include <vector>
 
+#include "su2_work.h"
 #include "worklist.h"
 
 using namespace clg;
@@ -104,6 +106,43 @@ int main() {
     std::printf("%s aligned_blocks Zb %d Zw %d nb %d rest %d max_cost %.2f\n", al ? "OK" : "FAIL", A.Zb, A.Zw, A.nb,
                 A.rest, A.max_cost);
     ok &= al;
+  }
+  // doublet-model items: chunk-major (tile, z-chunk) items cover every (tile,
+  // plane) once with at least one plane each (the pass's chunk arithmetic), the
+  // round-robin over R CTAs leaves no CTA idle, and at 256^3 (32 x 8 tiles, two
+  // CTAs on 152 SMs) the chosen split is within 10 % of perfect balance
+  struct Case {
+    const char* name;
+    int N, TX, TY, R;
+  };
+  for (const Case& cs : {Case{"su2_256_g304", 256, 32, 8, 304}, Case{"su2_128_g304", 128, 32, 8, 304},
+                         Case{"su2_48_g304", 48, 16, 8, 304}, Case{"su2_16_g304", 16, 16, 8, 304},
+                         Case{"su2_64_fp64_g152", 64, 32, 8, 152}}) {
+    const int ntiles = (cs.N / cs.TX) * (cs.N / cs.TY);
+    const int nzc = su2_z_chunks(ntiles, cs.N, cs.R);
+    const int nitems = ntiles * nzc, grid = std::min(cs.R, nitems);
+    std::vector<int> cover((size_t)ntiles * cs.N, 0);
+    std::vector<long> per_cta(grid, 0);
+    bool good = nzc >= 1 && nzc <= std::max(1, cs.N / 4);
+    for (int item = 0; item < nitems; ++item) {
+      const int tile = item % ntiles, chunk = item / ntiles;
+      const int z0 = (int)((long long)chunk * cs.N / nzc);
+      const int nz = (int)((long long)(chunk + 1) * cs.N / nzc) - z0;
+      if (nz < 1) good = false;
+      for (int z = z0; z < z0 + nz; ++z) cover[(size_t)tile * cs.N + z] += 1;
+      per_cta[item % grid] += nz + 2;
+    }
+    for (int v : cover) good = good && v == 1;
+    long mx = 0, sum = 0;
+    for (long v : per_cta) {
+      mx = std::max(mx, v);
+      sum += v;
+      good = good && v > 0;
+    }
+    const double bal = (double)mx * grid / (double)sum;
+    if (cs.N == 256) good = good && bal < 1.10;
+    std::printf("%s su2_items %s nzc %d grid %d balance %.3f\n", good ? "OK" : "FAIL", cs.name, nzc, grid, bal);
+    ok &= good;
   }
   return ok ? 0 : 1;
 }
