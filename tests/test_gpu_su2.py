@@ -301,3 +301,20 @@ def test_gauge_field_spectra_match(P, precision, tol):
     with pytest.raises(P.ClError) as e:
         nou1.em_spectrum(1)
     assert e.value.status == P.CL_EUNSUPPORTED
+
+
+def test_largest_lattice_fp32(P):
+    """512^3 (the largest N the library takes; 37.6 GB of state): the initial
+    Gauss laws, a finite leapfrog run with both laws kept to FP32 roundoff and
+    the energy conserved to the integrator's accuracy."""
+    N = 512
+    g = P.Lattice(O.MODEL_SU2U1_HIGGS, N, 0.05, 1.0, 1, P.make_params(precision=1, **SU2))
+    e0 = g.energies()
+    r0 = g.gauss()
+    g.step(6)
+    e1 = g.energies()
+    r1 = g.gauss()
+    assert e1["nonfinite"] == 0 and e1["EKB"] > 0.0
+    assert r0[0] < 1e-6 and r1[0] < 50 * 2 ** -24 * np.sqrt(6)
+    assert abs(e1["rho"] / e0["rho"] - 1.0) < 1e-3
+    g.close()
