@@ -390,8 +390,11 @@ def run_ours(args):
                         "context's passes); every step uploads its state and reads its energies",
                 "serial_value": results["e2e"]["serial"]},
         "gpu_launches": f32["launches"],
+        # one site advanced by one DK pass (an integrator stage): VV4 has three per step
+        "stage_site_updates_per_s": value * PASSES_PER_STEP,
         "clocks": f32["clocks"],
         "fp64_plain": {"value": v64, "unit": "site-updates/s", "steps": f64["steps"],
+                       "stage_site_updates_per_s": v64 * PASSES_PER_STEP,
                        "ms_per_step": f64["ms"] / f64["steps"], "achieved_gbs": achieved64,
                        "frac_hbm": achieved64 / peak, "avg_launch_ms": f64["pass_ms"],
                        "fp32_speedup": value / v64,
