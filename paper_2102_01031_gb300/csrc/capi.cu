@@ -5,6 +5,7 @@
 // launches; every step of the method (initial conditions, FFTs, passes,
 // reductions, Friedmann updates, spectra) runs in the kernels of this library.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -165,6 +166,14 @@ struct cl_ctx {
 namespace {
 
 thread_local std::string g_init_err;
+
+// NVTX range over a C-ABI call (visible in Nsight timelines; free without a tool attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 cl_status fail(cl_ctx* c, cl_status s, const char* fmt, ...) {
   char buf[512];
@@ -606,6 +615,7 @@ cl_status cl_free(cl_ctx* c) {
 
 cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, const double* kIRs,
                            double alpha, const uint64_t* seeds, const cl_params* p) {
+  Range range_("cl_init");
   if (!out) return fail(nullptr, CL_EINVAL, "out is NULL");
   *out = nullptr;
   if (!p || !Ns || !kIRs || !seeds) return fail(nullptr, CL_EINVAL, "NULL argument");
@@ -1026,6 +1036,7 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
 extern "C" {
 
 cl_status cl_step_h(cl_ctx* c, int n, double h) {
+  Range range_("cl_step");
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (n < 0 || !std::isfinite(h)) return fail(c, CL_EINVAL, "bad n/h");
   if (n == 0) return CL_OK;
@@ -1072,6 +1083,7 @@ static cl_status bad_lat(cl_ctx* c, int lat) {
 }
 
 cl_status cl_lattice_energies(cl_ctx* c, int lat, cl_energies_t* out) {
+  Range range_("cl_energies");
   if (!c || !out) return fail(c, CL_EINVAL, "NULL argument");
   if (lat < 0 || lat >= c->nlat) return bad_lat(c, lat);
   cl_status s = measure(c, 0);
@@ -1274,12 +1286,14 @@ cl_status cl_ensemble_spectrum(cl_ctx* c, const int* lats, int nl, int field, in
 
 cl_status cl_spectrum(cl_ctx* c, int field, int what, double dk_bin, double* k, double* delta,
                       int64_t* mult, int cap, int* nbins) {
+  Range range_("cl_spectrum");
   const int l0 = 0;
   return cl_ensemble_spectrum(c, &l0, 1, field, what, dk_bin, k, delta, mult, cap, nbins);
 }
 
 cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double* k, double* n, int64_t* mult,
                         int cap, int* nbins) {
+  Range range_("cl_occupation");
   if (!c || !k || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
   if (c->nlat != 1 || c->model >= CL_MODEL_U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "occupation numbers cover single scalar lattices");
@@ -1354,6 +1368,7 @@ cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double*
 
 cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,
                            int64_t* mult, int cap, int* nbins) {
+  Range range_("cl_norm_spectrum");
   if (!c || !k || !df || !dfp || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
   if (c->nlat != 1 || (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS))
     return fail(c, CL_EUNSUPPORTED, "modulus spectra cover single lattices of the gauge models");
@@ -1441,6 +1456,7 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
 
 cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double* delta, int64_t* mult, int cap,
                          int* nbins) {
+  Range range_("cl_em_spectrum");
   if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
   const bool su2 = c->model == CL_MODEL_SU2U1_HIGGS;
   if ((c->model != CL_MODEL_U1_HIGGS && !su2) || c->nlat != 1)
@@ -1526,6 +1542,7 @@ cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double*
 
 cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* rhs_abs,
                               double* max_abs) {
+  Range range_("cl_gauss_constraint");
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS)
     return fail(c, CL_EUNSUPPORTED, "model has no gauge field");
@@ -1555,6 +1572,7 @@ cl_status cl_state_bytes(cl_ctx* c, size_t* bytes) {
 }
 
 cl_status cl_upload_state(cl_ctx* c, const void* host, size_t bytes) {
+  Range range_("cl_upload_state");
   if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
   const long long V = c->lats[0].V;
   if (bytes != (size_t)c->narr * V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
@@ -1569,6 +1587,7 @@ cl_status cl_upload_state(cl_ctx* c, const void* host, size_t bytes) {
 }
 
 cl_status cl_download_state(cl_ctx* c, void* host, size_t bytes) {
+  Range range_("cl_download_state");
   if (!c || !host) return fail(c, CL_EINVAL, "NULL argument");
   const long long V = c->lats[0].V;
   if (bytes != (size_t)c->narr * V * c->esz) return fail(c, CL_EINVAL, "wrong byte count");
@@ -1716,6 +1735,7 @@ extern "C" {
 
 cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int field, int what, double dk_bin,
                      int bin, double* J, double* dJ_dq, double* dJ_dstate, double* dJ_dscale) {
+  Range range_("cl_adjoint");
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, CL_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (c->nlat != 1 || c->model >= CL_MODEL_U1_HIGGS)

@@ -341,3 +341,23 @@ def test_single_pass_launches_match_multi_pass(P):
     for f in range(2):
         for w in range(2):
             assert np.array_equal(a.get(f, w), b.get(f, w))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_state_is_reported(P, precision):
+    """Failure detection without a GPU fault: a NaN planted in one site's
+    momentum on the host spreads through the passes; the fused measurement
+    counts the non-finite momenta and cl_energies returns CL_ENONFINITE (the
+    data are still returned); a clean context is unaffected."""
+    g = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 1, P.make_params(precision=precision, **C2S))
+    clean = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 1, P.make_params(precision=precision, **C2S))
+    pi = g.get(1, 1)
+    pi[3, 5, 7] = np.nan
+    g.set(1, 1, pi)
+    g.step(2)
+    clean.step(2)
+    with pytest.raises(P.ClError) as e:
+        g.energies()
+    assert e.value.status == P.CL_ENONFINITE
+    assert g.energies(allow_nonfinite=True)["nonfinite"] > 0
+    assert clean.energies()["nonfinite"] == 0

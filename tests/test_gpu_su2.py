@@ -318,3 +318,17 @@ def test_largest_lattice_fp32(P):
     assert r0[0] < 1e-6 and r1[0] < 50 * 2 ** -24 * np.sqrt(6)
     assert abs(e1["rho"] / e0["rho"] - 1.0) < 1e-3
     g.close()
+
+
+def test_nonfinite_link_momentum_is_reported(P):
+    """An infinite SU(2) link momentum planted on the host is counted by the
+    doublet pass's measurement and reported as CL_ENONFINITE."""
+    g = P.Lattice(O.MODEL_SU2U1_HIGGS, 16, 0.8, 1.0, 1, P.make_params(precision=1, **SU2))
+    x = g.get_array(27)
+    x[2, 3, 4] = np.inf
+    g.set_array(27, x)
+    g.step(1)
+    with pytest.raises(P.ClError) as e:
+        g.energies()
+    assert e.value.status == P.CL_ENONFINITE
+    assert g.energies(allow_nonfinite=True)["nonfinite"] > 0
