@@ -199,6 +199,16 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
  * doublet model) is `*bytes` long.  Host buffers should be pinned for speed.
  * Both synchronise the kick stream first; the copies are enqueued on the
  * context stream (cl_download_state waits for its copy to finish). */
+/* Checkpoint and resume (single lattice): cl_checkpoint_save writes the state
+ * arrays and the evolving scalars (a, a', eta, drift coefficients, carried sums,
+ * the last measurement) to `path` through a temporary file that is renamed over
+ * `path` once complete, so a failure leaves the previous checkpoint intact;
+ * cl_checkpoint_load restores them into a context made with the same model, N,
+ * precision, kIR and alpha, after which stepping continues exactly as the saved
+ * run would (the kick stream is closed at both).  CL_EINVAL for an unreadable or
+ * mismatched file, CL_EUNSUPPORTED for ensembles.  Both synchronise the stream. */
+cl_status cl_checkpoint_save(cl_ctx* ctx, const char* path);
+cl_status cl_checkpoint_load(cl_ctx* ctx, const char* path);
 cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
 cl_status cl_upload_state(cl_ctx* ctx, const void* host, size_t bytes);
 cl_status cl_download_state(cl_ctx* ctx, void* host, size_t bytes);

@@ -35,7 +35,7 @@ EXPORTS = (
     "cl_ensemble_init", "cl_ensemble_size", "cl_lattice_energies", "cl_lattice_get_state",
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
-    "cl_get_array", "cl_set_array", "cl_norm_spectrum",
+    "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -125,6 +125,8 @@ def lib():
     L.cl_get_state.argtypes = [vp, ip, ip, dp]
     L.cl_set_state.argtypes = [vp, ip, ip, dp]
     L.cl_get_array.argtypes = [vp, ip, dp]
+    L.cl_checkpoint_save.argtypes = [vp, ctypes.c_char_p]
+    L.cl_checkpoint_load.argtypes = [vp, ctypes.c_char_p]
     L.cl_norm_spectrum.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
                                    ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     L.cl_set_array.argtypes = [vp, ip, dp]
@@ -274,6 +276,14 @@ class Lattice:
         if a.size != self.V:
             raise ValueError("need %d values" % self.V)
         _check(self.L, self.h, self.L.cl_set_state(self.h, field, what, _dp(a)), "cl_set_state")
+
+    def save(self, path):
+        """cl_checkpoint_save: state and scalars to `path` (written atomically)."""
+        _check(self.L, self.h, self.L.cl_checkpoint_save(self.h, os.fsencode(path)), "cl_checkpoint_save")
+
+    def load(self, path):
+        """cl_checkpoint_load: resume from a checkpoint of a matching lattice."""
+        _check(self.L, self.h, self.L.cl_checkpoint_load(self.h, os.fsencode(path)), "cl_checkpoint_load")
 
     def get_array(self, a):
         """cl_get_array (doublet model): array `a` of the state as [z][y][x]."""

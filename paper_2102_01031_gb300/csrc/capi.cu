@@ -20,6 +20,7 @@
 
 #include "cl.h"
 #include "common.cuh"
+#include "checkpoint.h"
 #include "su2_work.h"
 #include "worklist.h"
 
@@ -1568,6 +1569,61 @@ cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* r
 cl_status cl_state_bytes(cl_ctx* c, size_t* bytes) {
   if (!c || !bytes) return fail(c, CL_EINVAL, "NULL argument");
   *bytes = (size_t)c->narr * c->lats[0].V * c->esz;
+  return CL_OK;
+}
+
+cl_status cl_checkpoint_save(cl_ctx* c, const char* path) {
+  Range range_("cl_checkpoint_save");
+  if (!c || !path) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->nlat != 1) return fail(c, CL_EUNSUPPORTED, "checkpoints cover single lattices");
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  const LatHost& H = c->lats[0];
+  const size_t ab = (size_t)H.V * c->esz, nb = (size_t)c->narr * ab;
+  std::vector<char> state(nb);
+  LatScalars S;
+  for (int a = 0; a < c->narr; ++a)
+    CU(cudaMemcpyAsync(state.data() + a * ab, arr_ptr(c, 0, c->parity, a), ab, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&S, c->d_sc, sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  s = check_status(c);
+  if (s != CL_OK) return s;
+  CkptHeader h;
+  ckpt_init_header(h);
+  h.model = c->model;
+  h.N = H.N;
+  h.narr = c->narr;
+  h.esz = c->esz;
+  h.kIR = H.kIR;
+  h.alpha = c->alpha;
+  h.seed = H.seed;
+  h.scalars_bytes = sizeof(S);
+  h.state_bytes = nb;
+  const int rc = ckpt_write_atomic(path, h, &S, state.data());
+  if (rc != 0) return fail(c, CL_EINVAL, "cannot write checkpoint %s", path);
+  return CL_OK;
+}
+
+cl_status cl_checkpoint_load(cl_ctx* c, const char* path) {
+  Range range_("cl_checkpoint_load");
+  if (!c || !path) return fail(c, CL_EINVAL, "NULL argument");
+  if (c->nlat != 1) return fail(c, CL_EUNSUPPORTED, "checkpoints cover single lattices");
+  CkptHeader h;
+  std::vector<char> sc, state;
+  if (ckpt_read(path, h, sc, state) != 0) return fail(c, CL_EINVAL, "%s is not a readable checkpoint", path);
+  const LatHost& H = c->lats[0];
+  const size_t ab = (size_t)H.V * c->esz;
+  if (h.model != c->model || h.N != H.N || h.narr != c->narr || h.esz != c->esz ||
+      h.scalars_bytes != sizeof(LatScalars) || h.state_bytes != (size_t)c->narr * ab || h.kIR != H.kIR ||
+      h.alpha != c->alpha)
+    return fail(c, CL_EINVAL, "checkpoint %s does not match this context (model, N, precision, kIR, alpha)", path);
+  cl_status s = close_stream(c);
+  if (s != CL_OK) return s;
+  for (int a = 0; a < c->narr; ++a)
+    CU(cudaMemcpyAsync(arr_ptr(c, 0, c->parity, a), state.data() + a * ab, ab, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_sc, sc.data(), sizeof(LatScalars), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->obs_valid = false;
   return CL_OK;
 }
 

@@ -1,0 +1,24 @@
+"""CPU check of the checkpoint file and its atomic write
+(paper_2102_01031_gb300/csrc/checkpoint.h, used by cl_checkpoint_save/load):
+the failure is made on the host, between the write and the rename."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_checkpoint_file_survives_a_failed_write(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    exe = tmp_path / "checkpoint_check"
+    subprocess.run([gxx, "-O2", "-std=c++17", "-Wall", "-I",
+                    os.path.join(ROOT, "paper_2102_01031_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "checkpoint_check.cpp"), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe), str(tmp_path)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = r.stdout.strip().splitlines()
+    assert len(lines) == 4 and all(l.startswith("OK") for l in lines), r.stdout

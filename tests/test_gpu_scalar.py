@@ -361,3 +361,28 @@ def test_nonfinite_state_is_reported(P, precision):
     assert e.value.status == P.CL_ENONFINITE
     assert g.energies(allow_nonfinite=True)["nonfinite"] > 0
     assert clean.energies()["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_is_exact(P, precision, tmp_path):
+    """cl_checkpoint_save / cl_checkpoint_load: a run resumed from a checkpoint
+    (into a context made with another seed) continues bit for bit like the
+    uninterrupted run, self-consistent expansion included; a checkpoint of
+    another lattice size is refused."""
+    path = str(tmp_path / "lat.ckpt")
+    a = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 3, P.make_params(precision=precision, **C2S))
+    a.step(7)
+    a.save(path)
+    a.step(9)
+    b = P.Lattice(O.MODEL_LPHI4_CHI, 32, 0.5, 1.0, 99, P.make_params(precision=precision, **C2S))
+    b.load(path)
+    b.step(9)
+    for f in range(2):
+        for w in range(2):
+            assert np.array_equal(a.get(f, w), b.get(f, w)), (f, w)
+    assert a.scalars() == b.scalars()
+    assert a.energies()["rho"] == b.energies()["rho"]
+    c = P.Lattice(O.MODEL_LPHI4_CHI, 16, 0.5, 1.0, 3, P.make_params(precision=precision, **C2S))
+    with pytest.raises(P.ClError) as e:
+        c.load(path)
+    assert e.value.status == P.CL_EINVAL

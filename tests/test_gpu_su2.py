@@ -332,3 +332,18 @@ def test_nonfinite_link_momentum_is_reported(P):
         g.energies()
     assert e.value.status == P.CL_ENONFINITE
     assert g.energies(allow_nonfinite=True)["nonfinite"] > 0
+
+
+def test_checkpoint_resume_is_exact(P, tmp_path):
+    path = str(tmp_path / "su2.ckpt")
+    kw = dict(SU2, integrator=O.VV2, expansion=O.EXP_SELF)
+    a = P.Lattice(O.MODEL_SU2U1_HIGGS, 32, 0.8, 1.0, 3, P.make_params(precision=1, **kw))
+    a.step(5)
+    a.save(path)
+    a.step(6)
+    b = P.Lattice(O.MODEL_SU2U1_HIGGS, 32, 0.8, 1.0, 8, P.make_params(precision=1, **kw))
+    b.load(path)
+    b.step(6)
+    for i in range(NA):
+        assert np.array_equal(a.get_array(i), b.get_array(i)), i
+    assert a.scalars() == b.scalars()
