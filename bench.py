@@ -56,8 +56,8 @@ NCU_FP64_OPS = {"source_hash": "28d4993f1604ce49", "instructions_per_site_pass":
 # Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
 # (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture
 # (profiles/dk_pass_su2_fp32_128_ncu.md), valid for the kernel source it was taken on.
-NCU_SU2 = {"source_hash": "c2e29a48ab06c597", "thread_instructions_per_site": 2042.1,
-           "dram_bytes_per_site": 279.4}
+NCU_SU2 = {"source_hash": "2a13872a7d1fab04", "thread_instructions_per_site": 2049.4,
+           "dram_bytes_per_site": 280.1}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
 

@@ -79,6 +79,11 @@ __device__ __forceinline__ void qadd(Q4<T>& s, const Q4<T>& a) {
   s.z += a.z;
 }
 
+// The library's FP32 sine and cosine, out of line: the passes take them only for
+// angles beyond pi/4, and one copy keeps the kernels' code small (instruction cache).
+__device__ __noinline__ float sin_slow(float x) { return sinf(x); }
+__device__ __noinline__ void sincos_slow(float x, float* s, float* c) { sincosf(x, s, c); }
+
 // cos x and sin(x)/x.  FP32: for x^2 <= (pi/4)^2 their Taylor series about 0
 // in Horner form (first omitted terms below 3e-9 there), else the library;
 // the drift angles are small in practice.  FP64: the library.
@@ -91,7 +96,7 @@ __device__ __forceinline__ void cos_sinc(float x2, float& c, float& sc) {
   } else {
     const float x = sqrtf(x2);
     float s;
-    sincosf(x, &s, &c);
+    sincos_slow(x, &s, &c);
     sc = s / x;
   }
 }
@@ -113,7 +118,7 @@ __device__ __forceinline__ float sin_t(float x) {
     const float x2 = x * x;
     return x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
   }
-  return sinf(x);
+  return sin_slow(x);
 }
 __device__ __forceinline__ double sin_t(double x) { return sin(x); }
 __device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
@@ -125,7 +130,7 @@ __device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
                   -0.5f),
              1.f);
   } else {
-    sincosf(x, &s, &c);
+    sincos_slow(x, &s, &c);
   }
 }
 __device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
