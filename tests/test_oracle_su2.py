@@ -296,3 +296,33 @@ def test_hubble_constraint_order_non_abelian(oracle_mod, integ, order):
         v.append(abs(e["hubble_viol"]))
     slope = math.log(v[0] / v[1], 2)
     assert abs(slope - order) < 0.1, (v, slope)   # measured 2.00 and 4.00
+
+
+@pytest.mark.parametrize("integ", [O.VV2, O.LF])
+def test_gauge_transformed_vacuum_stays_static(oracle_mod, integ):
+    """A random SU(2) x U(1) gauge transformation of the vacuum -- links
+    U_i(n) = Omega(n) Omega^dag(n+i), A_i = (beta(n+i) - beta(n))/(gQ dx),
+    psi(n) = e^{i beta(n)} Omega(n) psi_0 with |Phi| = v, all momenta zero --
+    has no force anywhere (covariantly constant doublet, trivial plaquettes, no
+    current, potential at its minimum), so it does not move."""
+    N = 8
+    dx = 2 * np.pi / (N * 0.8)
+    rng = np.random.default_rng(12)
+    om = rng.standard_normal((4, N, N, N))
+    om /= np.sqrt((om ** 2).sum(0))
+    beta = rng.standard_normal((N, N, N))
+    v = 0.5
+    # psi_0 = (sqrt2 v, 0): |Phi|^2 = |psi|^2/2 = v^2
+    zero = np.zeros((N, N, N))
+    vac = [np.full((N, N, N), np.sqrt(2) * v), zero, zero, zero] + [zero] * 4 + [zero] * 6
+    for i in range(3):
+        vac += [np.ones((N, N, N)), zero, zero, zero]
+    vac += [zero] * 9
+    st = gauge_transform(vac, om, beta, 0.6, dx)
+    L = su2_lattice(N=N, integ=integ)
+    load(L, st)
+    e0 = L.energies()
+    assert abs(e0["rho"]) < 1e-13   # the vacuum energy, to the rounding of the transformation
+    L.step(20)
+    for a in range(35):
+        assert np.abs(L.get_array(a) - st[a]).max() < 1e-13, a
