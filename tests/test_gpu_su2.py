@@ -347,3 +347,23 @@ def test_checkpoint_resume_is_exact(P, tmp_path):
     for i in range(NA):
         assert np.array_equal(a.get_array(i), b.get_array(i)), i
     assert a.scalars() == b.scalars()
+
+
+def test_vv6_and_raw_state_round_trip(P):
+    """The sixth-order composition on the doublet model matches the oracle, and
+    the whole 35-array state round-trips through cl_download_state /
+    cl_upload_state (the end-to-end path)."""
+    kw = dict(SU2, integrator=O.VV6)
+    g, o = both(P, 16, 0.8, 1.0, 6, **kw)
+    g.step(3)
+    o.step(3)
+    compare_state(g, o, 1e-10)
+    n = g.state_bytes()
+    import ctypes
+    buf = (ctypes.c_char * n)()
+    g.download(ctypes.addressof(buf), n)
+    s0 = [g.get_array(a) for a in range(NA)]
+    g.step(2)
+    g.upload(ctypes.addressof(buf), n)
+    for a in range(NA):
+        assert np.array_equal(g.get_array(a), s0[a]), a
