@@ -207,6 +207,15 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
  * precision, kIR and alpha, after which stepping continues exactly as the saved
  * run would (the kick stream is closed at both).  CL_EINVAL for an unreadable or
  * mismatched file, CL_EUNSUPPORTED for ensembles.  Both synchronise the stream. */
+/* The autotuner's on-disk cache (cl_params.autotune): once a file is named,
+ * tuned tile heights are read from it and new ones written to it (one line per
+ * model, precision, N and device; rewritten through a temporary file), so later
+ * processes skip the timing.  Each call forgets the heights tuned so far in
+ * this process and takes the named file's entries; an entry whose height the
+ * device cannot run is tuned afresh.  NULL or "" turns the file off.  A file
+ * that cannot be written makes the autotuning cl_init fail with CL_EINVAL.
+ * Process-wide; returns CL_OK. */
+cl_status cl_set_tune_cache(const char* path);
 cl_status cl_checkpoint_save(cl_ctx* ctx, const char* path);
 cl_status cl_checkpoint_load(cl_ctx* ctx, const char* path);
 cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);

@@ -36,6 +36,7 @@ EXPORTS = (
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
+    "cl_set_tune_cache",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -126,6 +127,7 @@ def lib():
     L.cl_set_state.argtypes = [vp, ip, ip, dp]
     L.cl_get_array.argtypes = [vp, ip, dp]
     L.cl_checkpoint_save.argtypes = [vp, ctypes.c_char_p]
+    L.cl_set_tune_cache.argtypes = [ctypes.c_char_p]
     L.cl_checkpoint_load.argtypes = [vp, ctypes.c_char_p]
     L.cl_norm_spectrum.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
                                    ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
@@ -202,6 +204,14 @@ def make_params(**kw):
     if kw:
         raise TypeError("unknown params: %s" % sorted(kw))
     return p
+
+
+def set_tune_cache(path):
+    """cl_set_tune_cache: keep autotuned tile heights in `path` (None: off)."""
+    L = lib()
+    rc = L.cl_set_tune_cache(os.fsencode(path) if path else None)
+    if rc != CL_OK:
+        raise ClError(rc, "cl_set_tune_cache")
 
 
 def measure_fp64_rate(stream=None):

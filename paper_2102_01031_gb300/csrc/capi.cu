@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "checkpoint.h"
 #include "su2_work.h"
+#include "tune_cache.h"
 #include "worklist.h"
 
 namespace clg {
@@ -481,24 +482,32 @@ cl_status check_status(cl_ctx* c) {
 // Autotuner: the tile height of each (model, precision, N) is the candidate
 // with the shortest measured DK pass on scratch lattices of that size (as
 // many as it takes to give every SM work; two warm-up steps, then eight VV2
-// steps timed with CUDA events), kept for the life of the process.
+// steps timed with CUDA events), kept for the life of the process and, once
+// cl_set_tune_cache names a file, on disk across processes (tune_cache.h; the
+// device's SM count and compute capability are part of the key).
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<TuneKey, int> g_tune;
+std::string g_tune_path;
 }  // namespace
 
 static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
-  const auto key = std::make_tuple(c->model, c->esz, N);
+  int ccmaj = 0, ccmin = 0;
+  CU(cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, c->dev));
+  CU(cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, c->dev));
+  const TuneKey key(c->model, c->esz, N, c->nsm, ccmaj, ccmin);
+  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
+  if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (!g_tune_path.empty()) tune_cache_load(g_tune_path, g_tune);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) {
+    // a height this device cannot run (an edited or foreign file) is tuned afresh
+    if (it != g_tune.end() && std::find(cand.begin(), cand.end(), it->second) != cand.end()) {
       *by_out = it->second;
       return CL_OK;
     }
   }
-  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
-  if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   if (cand.size() > 4) cand.resize(4);
   int best = cand[0];
   double best_t = 1e300;
@@ -537,8 +546,13 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
     }
   }
   std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (!g_tune_path.empty()) tune_cache_load(g_tune_path, g_tune);  // entries other processes added meanwhile
   g_tune[key] = best;
   *by_out = best;
+  if (!g_tune_path.empty()) {
+    if (tune_cache_store(g_tune_path, g_tune) != 0)
+      return fail(c, CL_EINVAL, "autotune: cannot write the cache %s", g_tune_path.c_str());
+  }
   return CL_OK;
 }
 
@@ -569,6 +583,14 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed);
 static cl_status init_finish(cl_ctx* c);
 
 extern "C" {
+
+cl_status cl_set_tune_cache(const char* path) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_path = path ? path : "";
+  g_tune.clear();  // from here on the file is the record
+  if (!g_tune_path.empty()) tune_cache_load(g_tune_path, g_tune);
+  return CL_OK;
+}
 
 const char* cl_last_error(const cl_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 

@@ -167,3 +167,26 @@ def test_batched_ensemble_64_lattices(P):
     _, d3, _ = E.spectrum_mean([0, 1, 2], 0, 0, 1.0)
     do = np.mean(ref, axis=0)
     assert np.abs(d3 - do).max() < 1e-3 * np.abs(do).max()
+
+
+def test_autotune_cache_file(P, tmp_path):
+    """cl_set_tune_cache: the tuned tile height of (model, precision, N, device)
+    is written to the file, and a later context takes it from there."""
+    path = str(tmp_path / "tune.txt")
+    P.set_tune_cache(path)
+    try:
+        kw = dict(C2S, precision=P.FP32, autotune=1)
+        E = P.Ensemble(O.MODEL_LPHI4_CHI, [48], [0.5], 1.0, [1], P.make_params(**kw))
+        rows = [l.split() for l in open(path).read().splitlines()]
+        mine = [r for r in rows if r[:3] == [str(O.MODEL_LPHI4_CHI), "4", "48"]]
+        assert len(mine) == 1 and len(mine[0]) == 7
+        by = int(mine[0][6])
+        assert 48 % by == 0 and E.tile(0)[1] == by
+        # a file entry is taken as it stands (here a different admissible height)
+        other = 4 if by != 4 else 2
+        open(path, "w").write(" ".join(mine[0][:6] + [str(other)]) + "\n")
+        P.set_tune_cache(path)
+        F = P.Ensemble(O.MODEL_LPHI4_CHI, [48], [0.5], 1.0, [2], P.make_params(**kw))
+        assert F.tile(0)[1] == other
+    finally:
+        P.set_tune_cache(None)
