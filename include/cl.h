@@ -168,10 +168,11 @@ cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
  * r = |phi| = sqrt(sum_c phi_c^2/2) (the U(1) field's two components or the
  * doublet's four), and of r' = sum_c phi_c phi_c'/(2 r) (phi_c' = a^{alpha-3} pi_c;
  * 0 where r = 0): df, dfp = eq. discretePS of r and r' on cl_spectrum's shells,
- * n = eq. OccuppationNum applied to r with w_b^2 = k_b^2 + a^2 <V''(r)>,
- * V = lam (r^2 - v^2)^2, V'' = lam (12 r^2 - 4 v^2) (the manual's spectrum outputs
- * of the charged scalars, Sec. 4.5, with its `norm`: the modulus, which is gauge
- * invariant).  fo2 = (f_s/omega_s)^2; fo2 <= 0 takes 1/fluct_amp2.  k, df, dfp,
+ * n = eq. OccuppationNum applied to the canonically normalised modulus
+ * rho = sqrt2 r = sqrt(sum_c phi_c^2) with w_b^2 = k_b^2 + a^2 <d^2V/drho^2>,
+ * V = lam (r^2 - v^2)^2, d^2V/drho^2 = V''(r)/2 = lam (6 r^2 - 2 v^2) (the manual's
+ * spectrum outputs of the charged scalars, Sec. 4.5, with its `norm`: the
+ * modulus, which is gauge invariant).  fo2 = (f_s/omega_s)^2; fo2 <= 0 takes 1/fluct_amp2.  k, df, dfp,
  * n, mult hold `cap` entries; *nbins receives the bin count.  CL_EUNSUPPORTED for
  * scalar models and ensembles.  Closes the stream of kicks; synchronises. */
 cl_status cl_norm_spectrum(cl_ctx* ctx, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,

@@ -1435,10 +1435,13 @@ int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, doubl
 //   r = |phi| = sqrt(sum_c phi_c^2 / 2)   (U(1) field: c = 0, 1; doublet: c = 0..3),
 //   r' = sum_c phi_c phi_c' / (2 r),       phi_c' = a^{alpha-3} pi_c   (0 where r = 0),
 // delta_f, delta_fp = eq. discretePS of r and r' on clo_spectrum's shells, and n =
-// eq. OccuppationNum applied to r with w_b^2 = k_b^2 + a^2 <V''(r)>, V(r) = lam (r^2 - v^2)^2,
-// so V''(r) = lam (12 r^2 - 4 v^2), and fo2 = (f*/omega*)^2.
+// eq. OccuppationNum applied to the canonically normalised modulus rho = sqrt2 r (each
+// real component phi_c has a canonical kinetic term, so the radial field with one is
+// sqrt(sum_c phi_c^2)), with w_b^2 = k_b^2 + a^2 <d^2V/drho^2>, V = lam (r^2 - v^2)^2:
+// d^2V/drho^2 = V''(r)/2 = lam (6 r^2 - 2 v^2); |rho_k|^2 = 2 |r_k|^2; fo2 = (f*/omega*)^2.
 // reading: the manual lists Delta, Delta' and n of these fields without formulas;
-// the modulus is gauge invariant, its components are not.
+// the modulus is gauge invariant, its components are not, and eq. OccuppationNum
+// is written for a canonically normalised field.
 int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
                       double* n, int64_t* mult, int cap, int* nbins) {
   if (!c || !c->gauge() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
@@ -1459,7 +1462,7 @@ int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, do
     R[s] = cplx(r, 0.0);
     Rp[s] = cplx(rp, 0.0);
     G[s] = cplx(rp + H * r, 0.0);
-    m2 += c->p.lam * (12.0 * r2 - 4.0 * c->p.v * c->p.v);
+    m2 += c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v);
   }
   m2 /= V;
   fft3d(R, c->N, -1);
@@ -1491,7 +1494,7 @@ int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, do
     const double w2 = kb * kb + a * a * m2;
     if (!(w2 > 0.0)) { n[b] = std::nan(""); continue; }
     const double w = std::sqrt(w2);
-    n[b] = C * (w * s1[b] / (double)cnt[b] + a2p * s2[b] / ((double)cnt[b] * w));
+    n[b] = 2.0 * C * (w * s1[b] / (double)cnt[b] + a2p * s2[b] / ((double)cnt[b] * w));
   }
   return 0;
 }

@@ -115,8 +115,9 @@ int clo_gauss_residual(const clo_ctx* c, int g, double* out);
 void clo_su2_exp(const double theta[3], double u[4]);
 /* Gauge models: spectra of the modulus r = |phi| = sqrt(sum_c phi_c^2/2) of the charged
  * field (U(1) field or doublet) and of r' = sum_c phi_c phi_c'/(2 r), and the occupation
- * number of r (eq. OccuppationNum with w^2 = k^2 + a^2 <V''(r)>, V = lam (r^2 - v^2)^2),
- * on clo_spectrum's shells; fo2 = (f_s/omega_s)^2.  -1 for scalar models, -2 if cap < nbins. */
+ * number of the canonical modulus rho = sqrt2 r (eq. OccuppationNum with
+ * w^2 = k^2 + a^2 <V''(r)/2>, V = lam (r^2 - v^2)^2), on clo_spectrum's shells;
+ * fo2 = (f_s/omega_s)^2.  -1 for scalar models, -2 if cap < nbins. */
 int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
                       double* n, int64_t* mult, int cap, int* nbins);
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,

@@ -1450,10 +1450,11 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
   std::vector<double> h(12 * nb);
   CU(cudaMemcpyAsync(h.data(), bins, 12 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  // <V''(r)> = lam (12 <r^2> - 4 v^2), <r^2> = sum_c <phi_c^2>/2 from the measurement
+  // n is that of the canonical modulus rho = sqrt2 r (|rho_k|^2 = 2 |r_k|^2), whose
+  // mass is <d^2V/drho^2> = <V''(r)>/2 = lam (6 <r^2> - 2 v^2), <r^2> = sum_c <phi_c^2>/2
   double r2 = 0.0;
   for (int q = 0; q < nc; ++q) r2 += 0.5 * S.obs.mean_phi2[q];
-  const double m2 = c->p.lam * (12.0 * r2 - 4.0 * c->p.v * c->p.v);
+  const double m2 = c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v);
   const double V = (double)H.V, L = H.N * H.dx;
   const double C = a * a * L * L * L / (2.0 * V * V) * fo2, a2p = std::pow(a, 2.0 * (1.0 - al));
   for (int b = 0; b < nb; ++b) {
@@ -1472,7 +1473,7 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
       continue;
     }
     const double w = std::sqrt(w2);
-    n[b] = C * (w * h[3 * nb + nb + b] / cnt + a2p * h[9 * nb + nb + b] / (cnt * w));
+    n[b] = 2.0 * C * (w * h[3 * nb + nb + b] / cnt + a2p * h[9 * nb + nb + b] / (cnt * w));
   }
   return check_status(c);
 }
