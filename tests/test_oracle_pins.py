@@ -19,6 +19,7 @@ from scipy.integrate import solve_ivp  # noqa: E402
 from scipy.special import ellipj  # noqa: E402
 
 import oracle as O  # noqa: E402
+from tests.inputs import smooth_field  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -547,3 +548,38 @@ def test_u1_reversibility(oracle_mod):
     s1 = [L.get(f, w) for f in range(5) for w in range(2)]
     for x, y in zip(s0, s1):
         assert np.abs(x - y).max() < 1e-11 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("integ,alpha", [(O.LF, 1.0), (O.VV4, 0.5)])
+def test_u1_real_field_is_the_lphi4_model(oracle_mod, integ, alpha):
+    """With phi_1 = 0 and no gauge field the U(1) model's current vanishes, the
+    links stay 1 and |phi|^2 = phi_0^2/2, so with lam = 1, v = 0 its potential is
+    phi_0^4/4: phi_0 then obeys the lphi4 model's equations, with the same
+    energies and, under self-consistent expansion, the same a and a'.  The two
+    models are separate code in the oracle (covariant hops and the modulus
+    potential against the plain Laplacian and phi^3)."""
+    N, kIR, steps = 10, 0.6, 40
+    kw = dict(dt=0.02, integrator=integ, fluct_amp2=0.0, expansion=O.EXP_SELF, fstar_over_mp=0.7)
+    S = O.Oracle(O.MODEL_LPHI4, N, kIR, alpha, 1, O.make_params(**kw))
+    U = O.Oracle(O.MODEL_U1_HIGGS, N, kIR, alpha, 1, O.make_params(lam=1.0, v=0.0, gQ=0.8, **kw))
+    phi = smooth_field(N, 11, amp=0.5, offset=1.0)
+    pi = smooth_field(N, 12, amp=0.4)
+    S.set(0, 0, phi); S.set(0, 1, pi)
+    U.set(0, 0, phi); U.set(0, 1, pi)
+    U.set(1, 0, 0 * phi); U.set(1, 1, 0 * phi)
+    for f in range(2, 5):
+        U.set(f, 0, 0 * phi); U.set(f, 1, 0 * phi)
+    S.set_scalars(0.0, 1.0, 0.3)
+    U.set_scalars(0.0, 1.0, 0.3)
+    S.step(steps)
+    U.step(steps)
+    es, eu = S.energies(), U.energies()
+    scale = np.abs(S.get(0, 0)).max()
+    assert np.abs(U.get(0, 0) - S.get(0, 0)).max() <= 1e-13 * scale
+    assert np.abs(U.get(0, 1) - S.get(0, 1)).max() <= 1e-13 * np.abs(S.get(0, 1)).max()
+    assert np.abs(U.get(1, 0)).max() == 0.0 and np.abs(U.get(2, 1)).max() == 0.0
+    _, a_s, b_s = S.scalars()
+    _, a_u, b_u = U.scalars()
+    assert a_s > 1.2 and abs(a_u - a_s) <= 1e-14 * a_s and abs(b_u - b_s) <= 1e-13 * abs(b_s)
+    for key in ("EK", "EG", "EV"):
+        assert abs(eu[key][0] - es[key][0]) <= 1e-13 * abs(es[key][0]), key
