@@ -4,9 +4,12 @@
 // A text file, one entry per line:  model esz N sm_count cc_major cc_minor BY
 // (the device's SM count and compute capability are part of the key, since the
 // best tile height depends on the GPU).  Lines that do not parse are skipped.
-// Stores rewrite the whole file through a temporary file renamed over it, so a
-// reader never sees a partial file.
+// Stores rewrite the whole file through a temporary file of the writing process
+// (`path.tmp.<pid>`) renamed over it, so a reader never sees a partial file and
+// processes that store at the same time each replace the file whole.
 #pragma once
+
+#include <unistd.h>
 
 #include <cstdio>
 #include <map>
@@ -39,7 +42,7 @@ inline int tune_cache_load(const std::string& path, std::map<TuneKey, int>& out)
 // Writes every entry of `entries` to `path` (temporary file, then rename).
 // Returns 0 on success, -1 on an I/O error (the previous file is then intact).
 inline int tune_cache_store(const std::string& path, const std::map<TuneKey, int>& entries) {
-  const std::string tmp = path + ".tmp";
+  const std::string tmp = path + ".tmp." + std::to_string((long)getpid());
   FILE* f = std::fopen(tmp.c_str(), "w");
   if (!f) return -1;
   bool ok = true;

@@ -20,4 +20,4 @@ def test_tune_cache_file(tmp_path):
     r = subprocess.run([str(exe), str(tmp_path)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     lines = r.stdout.strip().splitlines()
-    assert len(lines) == 4 and all(l.startswith("OK") for l in lines), r.stdout
+    assert len(lines) == 5 and all(l.startswith("OK") for l in lines), r.stdout
