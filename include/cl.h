@@ -300,6 +300,20 @@ cl_status cl_em_spectrum(cl_ctx* ctx, int which, double dk_bin, double* k, doubl
  * context; returns CL_ECUDA / CL_ENOMEM on failure. */
 cl_status cl_measure_fp64_rate(void* stream, double* flops_per_s);
 
+/* Self-test of the bounded device waits that the persistent passes use (no
+ * counterpart in the paper).  One GPU thread runs one wait with a limit of
+ * limit_ns nanoseconds of device time (1 .. 1e10):
+ *   kind 0: the inter-pass counter wait, on a device word holding 1 (satisfied)
+ *           or 0 (nothing ever sets it);
+ *   kind 1: the stage mbarrier wait, on a fresh barrier that expects one
+ *           arrival, which the thread gives (satisfied) or not.
+ * Returns CL_OK when the wait was satisfied, CL_ETIMEOUT when it ran out (the
+ * status the passes record), CL_EINVAL for bad arguments, CL_ENOMEM /
+ * CL_ECUDA on failure.  *elapsed_ns (may be NULL) receives the device time the
+ * wait took.  Needs no context; synchronises `stream` (a cudaStream_t, NULL =
+ * default). */
+cl_status cl_selftest_wait(void* stream, int kind, int satisfied, uint64_t limit_ns, uint64_t* elapsed_ns);
+
 /* Ensemble-averaged binned spectrum: delta_b of cl_spectrum averaged over
  * the lattices lats[0 .. nl) (which must share N and kIR); k and mult as in
  * cl_spectrum (identical for those lattices).  Synchronises the stream. */

@@ -36,7 +36,7 @@ EXPORTS = (
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
-    "cl_set_tune_cache",
+    "cl_set_tune_cache", "cl_selftest_wait",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -161,6 +161,8 @@ def lib():
     L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
     L.cl_measure_fp64_rate.argtypes = [vp, dp]
+    L.cl_selftest_wait.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_uint64)]
     L.cl_em_spectrum.argtypes = [vp, ip, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int64), ip,
                                  ctypes.POINTER(ctypes.c_int)]
     L.cl_occupation.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp,
@@ -223,6 +225,18 @@ def measure_fp64_rate(stream=None):
     if rc != 0:
         raise ClError(rc, "cl_measure_fp64_rate failed")
     return r.value
+
+
+def selftest_wait(kind, satisfied, limit_ns, stream=None):
+    """cl_selftest_wait: run one of the passes' bounded device waits (kind 0 the
+    counter wait, 1 the mbarrier wait) that is satisfied or never is; returns
+    (status, device nanoseconds the wait took), status CL_OK or CL_ETIMEOUT."""
+    L = lib()
+    ns = ctypes.c_uint64()
+    rc = L.cl_selftest_wait(stream, int(kind), 1 if satisfied else 0, int(limit_ns), ctypes.byref(ns))
+    if rc not in (CL_OK, CL_ETIMEOUT):
+        raise ClError(rc, "cl_selftest_wait")
+    return rc, ns.value
 
 
 def torch_stream():

@@ -1,9 +1,11 @@
 // probe.cu -- measured FP64 arithmetic rate of this GPU, the roof of the FP64
 // plain pass (which is bound by FP64 operations, not by HBM): every thread of
-// a full grid runs eight independent FMA chains, timed with CUDA events.
+// a full grid runs eight independent FMA chains, timed with CUDA events.  Also
+// the self-test of the bounded device waits that the persistent passes use.
 #include <cuda_runtime.h>
 
 #include "cl.h"
+#include "common.cuh"
 
 namespace {
 
@@ -23,7 +25,57 @@ __global__ void fp64_fma_kernel(double* out, int iters, double y, double z) {
   if (s == 1234.5) out[blockIdx.x] = s;  // keeps the chains live
 }
 
+// One thread runs one of the passes' bounded waits: kind 0 waits for *counter
+// to reach 1 (wait_counter), kind 1 for phase 0 of a fresh mbarrier that
+// expects one arrival (mbar_wait_bounded), given (arrive = 1) or not.
+__global__ void wait_selftest_kernel(const unsigned* counter, int kind, int arrive, unsigned long long limit_ns,
+                                     int* status, unsigned long long* elapsed_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x | blockIdx.x) return;
+  const unsigned long long t0 = clg::global_ns();
+  bool ok;
+  if (kind == 1) {
+    clg::mbar_init(&bar, 1u);
+    clg::fence_mbar_init();
+    if (arrive) clg::mbar_arrive(&bar);
+    ok = clg::mbar_wait_bounded(&bar, 0u, limit_ns);
+  } else {
+    ok = clg::wait_counter(counter, 1u, limit_ns);
+  }
+  *elapsed_ns = clg::global_ns() - t0;
+  *status = ok ? (int)CL_OK : (int)CL_ETIMEOUT;
+}
+
+struct WaitProbe {
+  unsigned counter;
+  int status;
+  unsigned long long elapsed_ns;
+};
+
 }  // namespace
+
+extern "C" cl_status cl_selftest_wait(void* stream, int kind, int satisfied, uint64_t limit_ns,
+                                      uint64_t* elapsed_ns) {
+  if ((kind != 0 && kind != 1) || limit_ns == 0 || limit_ns > 10000000000ull) return CL_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  WaitProbe h{satisfied ? 1u : 0u, -1, 0ull};
+  WaitProbe* d = nullptr;
+  if (cudaMalloc(&d, sizeof(WaitProbe)) != cudaSuccess) return CL_ENOMEM;
+  cl_status s = CL_OK;
+  if (cudaMemcpyAsync(d, &h, sizeof(WaitProbe), cudaMemcpyHostToDevice, st) != cudaSuccess) s = CL_ECUDA;
+  if (s == CL_OK) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(&d->counter, kind, satisfied ? 1 : 0, (unsigned long long)limit_ns,
+                                           &d->status, &d->elapsed_ns);
+    if (cudaGetLastError() != cudaSuccess) s = CL_ECUDA;
+  }
+  if (s == CL_OK && (cudaMemcpyAsync(&h, d, sizeof(WaitProbe), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess))
+    s = CL_ECUDA;
+  cudaFree(d);
+  if (s != CL_OK) return s;
+  if (elapsed_ns) *elapsed_ns = h.elapsed_ns;
+  return h.status == (int)CL_OK ? CL_OK : h.status == (int)CL_ETIMEOUT ? CL_ETIMEOUT : CL_ECUDA;
+}
 
 extern "C" cl_status cl_measure_fp64_rate(void* stream, double* flops_per_s) {
   if (!flops_per_s) return CL_EINVAL;
