@@ -127,6 +127,23 @@ cl_status cl_free(cl_ctx* ctx);
 cl_status cl_step(cl_ctx* ctx, int n);
 cl_status cl_step_h(cl_ctx* ctx, int n, double h);
 
+/* The kick and drift weights of the fused passes that cl_step_h launches (host
+ * arithmetic only; needs no GPU and no context).  Each step is the integrator's
+ * symmetric composition of Stoermer-Verlet substeps (Sec. 5.1; VV4..VV10 as
+ * the triple-jump compositions of Yoshida 1990), every substep d a kick d/2, a
+ * drift d and a kick d/2; a pass applies the kick-out of the previous substep,
+ * the kick-in of the next and the next drift, so one pass per substep.  For
+ * ncalls successive cl_step_h calls of steps_per_call[i] steps of size h on a
+ * stream that starts closed, followed by the closing half kick (cl_sync or a
+ * measurement), out receives 4 doubles per pass, in order:
+ *   ck = wout + win (the total kick weight), wout (kick-out of the previous
+ *   drift), win (kick-in of the next drift), dnext (that drift).
+ * *npass receives the pass count; CL_EINVAL if it exceeds cap, or for an
+ * unknown integrator, a negative count, more than 2^20 steps per call or a
+ * non-finite h. */
+cl_status cl_pass_weights(int integrator, double h, int ncalls, const int* steps_per_call, double* out, int cap,
+                          int* npass);
+
 /* Close the stream of kicks so that fields and momenta are at the same time
  * (the manual's `sync`).  Asynchronous; a no-op when already closed. */
 cl_status cl_sync(cl_ctx* ctx);

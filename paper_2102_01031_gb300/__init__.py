@@ -36,7 +36,7 @@ EXPORTS = (
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
-    "cl_set_tune_cache", "cl_selftest_wait",
+    "cl_set_tune_cache", "cl_selftest_wait", "cl_pass_weights",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -161,6 +161,8 @@ def lib():
     L.cl_adjoint.argtypes = [vp, ip, ip, ip, ip, ip, ctypes.c_double, ip, dp, dp, dp, dp]
     L.cl_ic_amplitude_grad.argtypes = [vp, dp, dp]
     L.cl_measure_fp64_rate.argtypes = [vp, dp]
+    L.cl_pass_weights.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.cl_selftest_wait.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_uint64)]
     L.cl_em_spectrum.argtypes = [vp, ip, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int64), ip,
@@ -225,6 +227,24 @@ def measure_fp64_rate(stream=None):
     if rc != 0:
         raise ClError(rc, "cl_measure_fp64_rate failed")
     return r.value
+
+
+def pass_weights(integrator, h, steps_per_call):
+    """cl_pass_weights: (npass, 4) array of (ck, wout, win, dnext) of the passes that
+    successive cl_step_h calls of these step counts launch, with the closing half kick."""
+    L = lib()
+    calls = (ctypes.c_int * max(1, len(steps_per_call)))(*steps_per_call)
+    n = ctypes.c_int()
+    cap = 16
+    while True:
+        out = np.zeros(4 * cap)
+        rc = L.cl_pass_weights(int(integrator), float(h), len(steps_per_call), calls, _dp(out), cap,
+                               ctypes.byref(n))
+        if rc == CL_OK:
+            return out[:4 * n.value].reshape(-1, 4)
+        if rc != CL_EINVAL or n.value <= cap:
+            raise ClError(rc, "cl_pass_weights")
+        cap = n.value
 
 
 def selftest_wait(kind, satisfied, limit_ns, stream=None):

@@ -219,6 +219,30 @@ void schedule(int order, double h, std::vector<double>& d) {
   schedule(order - 2, z1 * h, d);
 }
 
+// Kick/drift weights of the passes of n steps of size h, appended to `steps`:
+// the first pass of a closed stream only kicks (by half the first drift);
+// later passes merge the kick-out of the previous drift with the kick-in of
+// the next (first same as last).  `open` and `dprev` carry the stream across
+// calls.
+void append_pass_steps(int integrator, double h, int n, bool& open, double& dprev, std::vector<PassStep>& steps) {
+  std::vector<double> d1;
+  schedule(integrator == CL_LF ? 2 : integrator, h, d1);
+  steps.reserve(steps.size() + (size_t)n * d1.size());
+  for (int s = 0; s < n; ++s)
+    for (double d : d1) {
+      if (!open) {
+        steps.push_back(PassStep{0.5 * d, 0.0, 0.5 * d, d});
+        open = true;
+      } else {
+        steps.push_back(PassStep{0.5 * (dprev + d), 0.5 * dprev, 0.5 * d, d});
+      }
+      dprev = d;
+    }
+}
+
+// The pass that closes a stream: the kick-out of the last drift, no drift.
+PassStep closing_pass_step(double dprev) { return PassStep{0.5 * dprev, 0.5 * dprev, 0.0, 0.0}; }
+
 void fft_radices(int N, FftPlan& pl) {
   pl.nrad = 0;
   int m = N;
@@ -448,7 +472,8 @@ int red_for_step(const cl_ctx* c) { return c->p.expansion == CL_EXP_SELF ? 1 : 0
 
 cl_status close_stream(cl_ctx* c) {
   if (!c->open) return CL_OK;
-  cl_status s = run_pass(c, 0.5 * c->dprev, 0.5 * c->dprev, 0.0, 0.0, 2, 1, 0);
+  const PassStep cl = closing_pass_step(c->dprev);
+  cl_status s = run_pass(c, cl.ck, cl.wout, cl.win, cl.dnext, 2, 1, 0);
   if (s != CL_OK) return s;
   c->open = false;
   c->obs_valid = true;
@@ -1063,24 +1088,9 @@ cl_status cl_step_h(cl_ctx* c, int n, double h) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
   if (n < 0 || !std::isfinite(h)) return fail(c, CL_EINVAL, "bad n/h");
   if (n == 0) return CL_OK;
-  std::vector<double> d1;
-  schedule(c->p.integrator == CL_LF ? 2 : c->p.integrator, h, d1);
   const int red = red_for_step(c);
-  // kick/drift weights of every pass: the first pass of a closed stream only
-  // kicks (by half the first drift); later passes merge the kick-out of the
-  // previous drift with the kick-in of the next
   std::vector<PassStep> steps;
-  steps.reserve((size_t)n * d1.size());
-  for (int s = 0; s < n; ++s)
-    for (double d : d1) {
-      if (!c->open) {
-        steps.push_back(PassStep{0.5 * d, 0.0, 0.5 * d, d});
-        c->open = true;
-      } else {
-        steps.push_back(PassStep{0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d});
-      }
-      c->dprev = d;
-    }
+  append_pass_steps(c->p.integrator, h, n, c->open, c->dprev, steps);
   const int chunk = 4096;
   for (size_t b = 0; b < steps.size(); b += chunk) {
     const int m = (int)std::min<size_t>(chunk, steps.size() - b);
@@ -1088,6 +1098,31 @@ cl_status cl_step_h(cl_ctx* c, int n, double h) {
     if (st != CL_OK) return st;
   }
   c->obs_valid = false;
+  return CL_OK;
+}
+
+cl_status cl_pass_weights(int integrator, double h, int ncalls, const int* steps_per_call, double* out, int cap,
+                          int* npass) {
+  if (!steps_per_call || !out || !npass || ncalls < 0 || !std::isfinite(h)) return CL_EINVAL;
+  if (integrator != CL_LF && integrator != CL_VV2 && integrator != CL_VV4 && integrator != CL_VV6 &&
+      integrator != CL_VV8 && integrator != CL_VV10)
+    return CL_EINVAL;
+  bool open = false;
+  double dprev = 0.0;
+  std::vector<PassStep> steps;
+  for (int i = 0; i < ncalls; ++i) {
+    if (steps_per_call[i] < 0 || steps_per_call[i] > (1 << 20)) return CL_EINVAL;
+    append_pass_steps(integrator, h, steps_per_call[i], open, dprev, steps);
+  }
+  if (open) steps.push_back(closing_pass_step(dprev));
+  *npass = (int)steps.size();
+  if ((int)steps.size() > cap) return CL_EINVAL;
+  for (size_t j = 0; j < steps.size(); ++j) {
+    out[4 * j + 0] = steps[j].ck;
+    out[4 * j + 1] = steps[j].wout;
+    out[4 * j + 2] = steps[j].win;
+    out[4 * j + 3] = steps[j].dnext;
+  }
   return CL_OK;
 }
 

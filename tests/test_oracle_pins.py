@@ -138,6 +138,18 @@ def test_cn_oscillation_order(oracle_mod, integ, order):
     assert e2 < (2e-4 if order == 2 else 1e-6)
 
 
+@pytest.mark.parametrize("integ,order,dts", [(O.VV8, 8, [0.1, 0.05]), (O.VV10, 10, [0.12, 0.06])])
+def test_cn_oscillation_order_high(oracle_mod, integ, order, dts):
+    """The 27- and 81-stage compositions converge at their orders (measured
+    slopes 7.88 and 9.83 over two periods; a composition one level short, or
+    built with the previous level's weights, stays at order 6 or 8)."""
+    T = 2 * 7.4163
+    e1, e2 = cn_error(integ, dts[0], T), cn_error(integ, dts[1], T)
+    slope = math.log(e1 / e2, 2)
+    assert abs(slope - order) < 0.35, (e1, e2, slope)
+    assert e2 < (1e-8 if order == 8 else 1e-9)
+
+
 # --------------------------------------------------------------------------
 # two fields + self-consistent expansion vs an independent ODE integration of
 # the continuum equations (eqs. EOMscalarContinuumNat, NewFriedmannEQsII),
