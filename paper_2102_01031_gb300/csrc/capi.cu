@@ -1923,16 +1923,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
   for (int ch = 0; ch < nchunk; ++ch) {
     const int m = std::min(ckpt_every, nsteps - ch * ckpt_every);
     std::vector<PassStep> steps;
-    for (int st = 0; st < m; ++st)
-      for (double d : dsub) {
-        if (!c->open) {
-          steps.push_back(PassStep{0.5 * d, 0.0, 0.5 * d, d});
-          c->open = true;
-        } else {
-          steps.push_back(PassStep{0.5 * (c->dprev + d), 0.5 * c->dprev, 0.5 * d, d});
-        }
-        c->dprev = d;
-      }
+    append_pass_steps(c->p.integrator, c->p.dt, m, c->open, c->dprev, steps);  // the forward plan of cl_step
     chunk_first[ch] = pc;
     fw.insert(fw.end(), steps.begin(), steps.end());
     for (size_t b = 0; b < steps.size(); b += 4096) {
@@ -1944,7 +1935,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
   }
   chunk_first[nchunk] = pc;
   if (c->open) {  // the closing half kick, which also measures
-    PassStep st = {0.5 * c->dprev, 0.5 * c->dprev, 0.0, 0.0};
+    PassStep st = closing_pass_step(c->dprev);
     fw.push_back(st);
     ADJ_TRY(launch_passes(c, &st, 1, 2, 1, 0, dlog, pc));
     ++pc;
