@@ -512,6 +512,35 @@ def other_workloads(P, torch, stream, peak):
             "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq, "dJ_da": ab[0], "dJ_db": ab[1],
             "steps": 4000, "ckpt_every": 500,
             "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps"}
+    # initial conditions and spectra at 256^3, outside a run's timed loop: wall time
+    # of cl_init (allocation, Fourier-space draws, inverse FFTs, IC kernels) and of
+    # cl_spectrum of one field (complex conversion, three FFT axis passes, shell
+    # sums); a failure here leaves the other rows standing
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **PARAMS))
+        torch.cuda.synchronize()
+        t_init = time.perf_counter() - t0
+        lat.spectrum(0)
+        torch.cuda.synchronize()
+        reps = 10
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            lat.spectrum(0)
+        torch.cuda.synchronize()
+        t_spec = (time.perf_counter() - t0) / reps
+        lat.close()
+        sites = N_LAT ** 3
+        gbs = sites * 132 / t_spec / 1e9
+        out["ics_and_spectrum_256_fp32"] = {
+            "init_s": t_init, "spectrum_ms": t_spec * 1e3, "model_bytes_per_site": 132,
+            "spectrum_gbs": gbs, "frac_hbm": gbs / peak,
+            "note": "host wall time; 132 B/site = complex conversion 20 + three FFT axis passes 96 + "
+                    "shell sums 16; includes the call's read-back and synchronisation"}
+    except Exception as e:  # noqa: BLE001
+        out["ics_and_spectrum_256_fp32"] = {"error": str(e)[:300]}
     return out
 
 
