@@ -172,3 +172,25 @@ def test_modulus_occupation_is_an_adiabatic_invariant(oracle_mod, alpha):
     assert np.array_equal(m0, m1)
     rel = np.abs(n1[hit] / n0[hit] - 1.0)
     assert rel.max() < 0.01, rel
+
+
+def test_doublet_modulus_occupation_is_an_adiabatic_invariant(oracle_mod):
+    """The same radial ripple on the doublet's vacuum (real upper component, links
+    at the identity): the U(1) and SU(2) currents Im(psi^dag sigma W psi) vanish
+    for a real upper component, so the gauge fields stay zero and n of the
+    canonical modulus is conserved while a doubles (conformal time)."""
+    N, kIR, H0, dt, lam, v = 12, 0.5, 0.025, 0.05, 2.0, 1.0
+    p = O.make_params(dt=dt, integrator=O.VV4, lam=lam, v=v, gQ=0.5, gQB=0.7, fluct_amp2=0.0,
+                      phi0=[np.sqrt(2) * v, 0.0, 0.0, 0.0], expansion=O.EXP_FIXED, omega_eos=1.0 / 3.0,
+                      H0=H0, fstar_over_mp=0.5)
+    L = O.Oracle(O.MODEL_SU2U1_HIGGS, N, kIR, 1.0, 1, p)
+    L.set_array(0, np.sqrt(2) * v + plane_waves(N, [(1, 0, 0), (0, 1, 1), (1, -1, 1), (0, 2, 0)], 1e-4, 7))
+    _, _, _, n0, m0 = L.norm_spectrum(dk_bin=0.04, fo2=1.0)
+    hit = np.nonzero(n0 > 1e-20)[0]
+    assert len(hit) == 4
+    L.step(800)
+    assert abs(L.scalars()[1] - 2.0) < 1e-9
+    _, _, _, n1, m1 = L.norm_spectrum(dk_bin=0.04, fo2=1.0)
+    assert np.array_equal(m0, m1)
+    rel = np.abs(n1[hit] / n0[hit] - 1.0)
+    assert rel.max() < 0.01, rel
