@@ -298,7 +298,8 @@ class Oracle:
 
     def norm_spectrum(self, dk_bin=1.0, fo2=None):
         """(k, Delta_r, Delta_r', n, multiplicity) of the charged field's modulus r = |phi|
-        (gauge models); fo2 = (f*/omega*)^2, default 1/fluct_amp2."""
+        (gauge models; n is that of the canonical modulus sqrt2 r); fo2 = (f*/omega*)^2,
+        default 1/fluct_amp2."""
         if fo2 is None:
             fo2 = 1.0 / self.params.fluct_amp2
         cap = 4096

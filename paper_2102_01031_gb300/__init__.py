@@ -371,7 +371,8 @@ class Lattice:
 
     def norm_spectrum(self, dk_bin=1.0, fo2=0.0):
         """cl_norm_spectrum (gauge models): (k, Delta_r, Delta_r', n, multiplicity) of the
-        charged field's modulus r = |phi|; fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2)."""
+        charged field's modulus r = |phi| (n: that of the canonical modulus sqrt2 r);
+        fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2)."""
         cap = 4096
         k, d1, d2, n = (np.zeros(cap) for _ in range(4))
         m = np.zeros(cap, dtype=np.int64)
