@@ -41,21 +41,20 @@ WORKLOAD = ("lphi4+chi q=100, 256^3, kIR=0.1, alpha=1, VV4 dt=0.005, self-consis
 # bytes one DK pass must move: 2 fields x (field, momentum) x (read + write)
 PASS_BYTES_PER_SITE = {"f32": 2 * 2 * 2 * 4, "f64": 2 * 2 * 2 * 8}
 PASSES_PER_STEP = 3
-# DRAM bytes (read + write) per DK pass from the ncu capture summarised in
-# profiles/dk_pass_fp32_256_ncu.md (one cooperative launch of the three VV4
-# passes of a step, divided by 3), valid only for the kernel source it was
-# taken on.
+# DRAM bytes (read + write) per DK pass from one ncu capture of the FP32 pass
+# at 256^3 (one cooperative launch of the three VV4 passes of a step, divided
+# by 3), valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {"f32": {"source_hash": "28d4993f1604ce49", "bytes_per_launch": 503003051}}
 # FP64 instructions (DFMA, DADD, DMUL) and operations (FMA = 2) per site per pass
-# of the FP64 plain kernel, from one ncu capture of the sass instruction counters
-# (profiles/dk_pass_fp64_256_ncu.md)
+# of the FP64 plain kernel, from one ncu capture of the instruction counters of
+# the FP64 pass at 256^3
 NCU_FP64_OPS = {"source_hash": "28d4993f1604ce49", "instructions_per_site_pass": 46.443,
                 "flops_per_site_pass": 60.811}
 
 
 # Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
-# (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture
-# (profiles/dk_pass_su2_fp32_128_ncu.md), valid for the kernel source it was taken on.
+# (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture,
+# valid for the kernel source it was taken on.
 NCU_SU2 = {"source_hash": "2a13872a7d1fab04", "thread_instructions_per_site": 2049.4,
            "dram_bytes_per_site": 280.1}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock

@@ -217,6 +217,10 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
  * doublet model) is `*bytes` long.  Host buffers should be pinned for speed.
  * Both synchronise the kick stream first; the copies are enqueued on the
  * context stream (cl_download_state waits for its copy to finish). */
+cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
+cl_status cl_upload_state(cl_ctx* ctx, const void* host, size_t bytes);
+cl_status cl_download_state(cl_ctx* ctx, void* host, size_t bytes);
+
 /* Checkpoint and resume (single lattice): cl_checkpoint_save writes the state
  * arrays and the evolving scalars (a, a', eta, drift coefficients, carried sums,
  * the last measurement) to `path` through a temporary file that is renamed over
@@ -225,6 +229,9 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
  * precision, kIR and alpha, after which stepping continues exactly as the saved
  * run would (the kick stream is closed at both).  CL_EINVAL for an unreadable or
  * mismatched file, CL_EUNSUPPORTED for ensembles.  Both synchronise the stream. */
+cl_status cl_checkpoint_save(cl_ctx* ctx, const char* path);
+cl_status cl_checkpoint_load(cl_ctx* ctx, const char* path);
+
 /* The autotuner's on-disk cache (cl_params.autotune): once a file is named,
  * tuned tile heights are read from it and new ones written to it (one line per
  * model, precision, N and device; rewritten through a temporary file), so later
@@ -234,11 +241,6 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
  * that cannot be written makes the autotuning cl_init fail with CL_EINVAL.
  * Process-wide; returns CL_OK. */
 cl_status cl_set_tune_cache(const char* path);
-cl_status cl_checkpoint_save(cl_ctx* ctx, const char* path);
-cl_status cl_checkpoint_load(cl_ctx* ctx, const char* path);
-cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
-cl_status cl_upload_state(cl_ctx* ctx, const void* host, size_t bytes);
-cl_status cl_download_state(cl_ctx* ctx, void* host, size_t bytes);
 
 int cl_nfields(const cl_ctx* ctx);           /* lattice arrays per kind (what=0 or 1) */
 int64_t cl_kernel_launches(const cl_ctx* ctx); /* kernels this context has launched */
@@ -394,10 +396,13 @@ cl_status cl_ic_amplitude_grad(cl_ctx* ctx, const double* dJ_dstate, double* out
  *
  * Partial sums live in one file-scope device array of CL_NOALLOC_MAX_BLOCKS x
  * CL_NOALLOC_OUT doubles (128 KiB), held by every GPU that loads the library
- * until the process exits.  The first call on a device looks up that array's
- * device address with the device current; make that first call before any
- * stream capture.  Every call shares the array (each row a call reads is
- * written earlier in the same call), so calls that overlap on the GPU race.
+ * until the process exits.  A call whose stream is not being captured looks up
+ * that array's device address with the device current (so a device reset
+ * cannot leave a stale address in use); a call during a stream capture reuses
+ * the address the last uncaptured call on that device found, so make the first
+ * call on a device before any stream capture.  Every call shares the array
+ * (each row a call reads is written earlier in the same call), so calls that
+ * overlap on the GPU race.
  * Returns CL_EINVAL for N > CL_NOALLOC_MAX_N (the no-allocation limit) or bad
  * arguments, CL_ECUDA if a launch or the address lookup fails. */
 #define CL_NOALLOC_MAX_BLOCKS 1024

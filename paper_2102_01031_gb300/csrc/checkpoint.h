@@ -3,10 +3,12 @@
 //
 // A checkpoint is a header, the lattice's evolving scalars (the device's
 // LatScalars, bytes as stored) and its state arrays in storage order and
-// precision.  It is written to `path.tmp`, flushed, and renamed over `path`, so
-// that a failure at any point leaves either the previous checkpoint or the new
-// one, never a partial file (the manual's backup keeps the old file until the
-// new one is written, Sec. 5.3).  Reads check the magic, the version and every
+// precision.  It is written to `path.tmp`, flushed and synced to disk, and
+// renamed over `path`, after which the directory is synced too, so that a
+// failure at any point (of the process, or of the host once the data reached
+// the disk) leaves either the previous checkpoint or the new one, never a
+// partial file (the manual's backup keeps the old file until the new one is
+// written, Sec. 5.3).  Reads check the magic, the version and every
 // size against the file's length.
 #pragma once
 
@@ -15,6 +17,9 @@
 #include <cstring>
 #include <string>
 #include <vector>
+
+#include <fcntl.h>
+#include <unistd.h>
 
 namespace clg {
 
@@ -35,8 +40,16 @@ inline void ckpt_init_header(CkptHeader& h) {
   h.version = kCkptVersion;
 }
 
-// Writes header, scalars and state to path + ".tmp", flushes it and renames it
-// over `path`.  before_rename (may be null) runs between the flush and the
+// Directory part of `path` ("." when it has none).
+inline std::string ckpt_dir_of(const std::string& path) {
+  const size_t s = path.find_last_of('/');
+  if (s == std::string::npos) return ".";
+  return s == 0 ? "/" : path.substr(0, s);
+}
+
+// Writes header, scalars and state to path + ".tmp", flushes and fsyncs it,
+// renames it over `path` and fsyncs the directory, so that the rename cannot
+// reach the disk before the data.  before_rename (may be null) runs between the flush and the
 // rename; if it returns false the write is abandoned (the temporary file is
 // removed, `path` is untouched) -- the hook the tests use to fail there.
 // Returns 0 on success, -1 on an I/O error, -2 when abandoned by the hook.
@@ -49,6 +62,7 @@ inline int ckpt_write_atomic(const std::string& path, const CkptHeader& h, const
   ok = ok && (h.scalars_bytes == 0 || std::fwrite(scalars, h.scalars_bytes, 1, f) == 1);
   ok = ok && (h.state_bytes == 0 || std::fwrite(state, h.state_bytes, 1, f) == 1);
   ok = std::fflush(f) == 0 && ok;
+  ok = ok && fsync(fileno(f)) == 0;
   ok = std::fclose(f) == 0 && ok;
   if (!ok) {
     std::remove(tmp.c_str());
@@ -62,7 +76,11 @@ inline int ckpt_write_atomic(const std::string& path, const CkptHeader& h, const
     std::remove(tmp.c_str());
     return -1;
   }
-  return 0;
+  const int d = open(ckpt_dir_of(path).c_str(), O_RDONLY | O_DIRECTORY);
+  if (d < 0) return -1;
+  const bool synced = fsync(d) == 0;
+  close(d);
+  return synced ? 0 : -1;
 }
 
 // Reads a checkpoint; 0 on success, -1 when the file is missing, short, or not

@@ -56,6 +56,40 @@ struct LatScalars {
 };
 
 
+// ---------------------------------------------------------------------------
+// Sine and cosine of link and plaquette angles (the gauge passes).
+// The library's FP32 sine and cosine, out of line: the passes take them only for
+// angles beyond pi/4, and one copy keeps the kernels' code small (instruction cache).
+static __device__ __noinline__ float sin_slow(float x) { return sinf(x); }
+static __device__ __noinline__ void sincos_slow(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// FP32: for |x| <= pi/4 the Taylor series about 0 in Horner form (the first
+// omitted terms, x^11/11! and x^12/12!, stay below 2e-9 there), else the
+// library; link and plaquette angles are small in practice.  FP64: the library.
+static __device__ __forceinline__ float sin_taylor(float x2) {  // sin(x)/x from x^2
+  return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
+}
+static __device__ __forceinline__ float cos_taylor(float x2) {
+  return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
+              -0.5f),
+              1.f);
+}
+static __device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
+  if (fabsf(x) <= 0.78539816f) {
+    const float x2 = x * x;
+    s = x * sin_taylor(x2);
+    c = cos_taylor(x2);
+  } else {
+    sincos_slow(x, &s, &c);
+  }
+}
+static __device__ __forceinline__ float sin_t(float x) {
+  if (fabsf(x) <= 0.78539816f) return x * sin_taylor(x * x);
+  return sin_slow(x);
+}
+static __device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
+static __device__ __forceinline__ double sin_t(double x) { return sin(x); }
+
 // Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
 constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
 

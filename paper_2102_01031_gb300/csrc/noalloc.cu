@@ -24,8 +24,11 @@ constexpr int kThreads = 256;
 // kernel of a call before the second kernel of the same call reads them.
 static __device__ __align__(256) double g_avg_scratch[kMaxBlocks * kSlots];
 
-// Device address of g_avg_scratch for each device, looked up once per device
-// with that device current (the host-side name is only a stand-in).
+// Device address of g_avg_scratch for each device, looked up with that device
+// current (the host-side name is only a stand-in).  It is looked up again on
+// every call whose stream is not being captured, so that an address made
+// stale by a device reset (which reloads the module) is never used; a call
+// during a stream capture takes the address the last uncaptured call found.
 std::mutex g_mu;
 double* g_scratch_ptr[64] = {nullptr};
 
@@ -103,14 +106,18 @@ __global__ void avg_final_kernel(const double* rows, int nblk, int nf, int N, do
   out[15] = tot[15];
 }
 
-cl_status scratch_for_current_device(double** ptr) {
+cl_status scratch_for_current_device(cudaStream_t st, double** ptr) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CL_ECUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return CL_ECUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_avg_scratch) != cudaSuccess || !p) return CL_ECUDA;
     g_scratch_ptr[dev] = static_cast<double*>(p);
+  } else if (!g_scratch_ptr[dev]) {
+    return CL_ECUDA;  // no uncaptured call on this device yet
   }
   *ptr = g_scratch_ptr[dev];
   return CL_OK;
@@ -128,13 +135,13 @@ extern "C" cl_status cl_volume_averages_noalloc(int model, int N, double kIR, do
   const int nf = model == CL_MODEL_LPHI4 ? 1 : 2;
   for (int i = 0; i < 2 * nf; ++i)
     if (!arrays[i]) return CL_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* rows = nullptr;
-  cl_status s = scratch_for_current_device(&rows);
+  cl_status s = scratch_for_current_device(st, &rows);
   if (s != CL_OK) return s;
   const long long V = (long long)N * N * N;
   long long want = (V + kThreads - 1) / kThreads;
   const int nblk = (int)(want < kMaxBlocks ? want : kMaxBlocks);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const void* p1 = nf > 1 ? arrays[2] : arrays[0];
   const void* m1 = nf > 1 ? arrays[3] : arrays[1];
   if (precision == CL_FP32)

@@ -79,20 +79,13 @@ __device__ __forceinline__ void qadd(Q4<T>& s, const Q4<T>& a) {
   s.z += a.z;
 }
 
-// The library's FP32 sine and cosine, out of line: the passes take them only for
-// angles beyond pi/4, and one copy keeps the kernels' code small (instruction cache).
-__device__ __noinline__ float sin_slow(float x) { return sinf(x); }
-__device__ __noinline__ void sincos_slow(float x, float* s, float* c) { sincosf(x, s, c); }
-
 // cos x and sin(x)/x.  FP32: for x^2 <= (pi/4)^2 their Taylor series about 0
 // in Horner form (first omitted terms below 3e-9 there), else the library;
 // the drift angles are small in practice.  FP64: the library.
 __device__ __forceinline__ void cos_sinc(float x2, float& c, float& sc) {
   if (x2 <= 0.61685028f) {
-    c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
-                     -0.5f),
-             1.f);
-    sc = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
+    c = cos_taylor(x2);
+    sc = sin_taylor(x2);
   } else {
     const float x = sqrtf(x2);
     float s;
@@ -112,28 +105,6 @@ __device__ __forceinline__ void cos_sinc(double x2, double& c, double& sc) {
   sc = s / x;
 }
 
-// sin; FP32 as the U(1) pass (Taylor series about 0 for |x| <= pi/4).
-__device__ __forceinline__ float sin_t(float x) {
-  if (fabsf(x) <= 0.78539816f) {
-    const float x2 = x * x;
-    return x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
-  }
-  return sin_slow(x);
-}
-__device__ __forceinline__ double sin_t(double x) { return sin(x); }
-__device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
-  if (fabsf(x) <= 0.78539816f) {
-    const float x2 = x * x;
-    s = x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
-    c = fmaf(x2,
-             fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
-                  -0.5f),
-             1.f);
-  } else {
-    sincos_slow(x, &s, &c);
-  }
-}
-__device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
 
 // Renormalise a link to unit length (FP32 storage only: keeps the rounding
 // of repeated drifts from walking off the group; FP64 follows the plain

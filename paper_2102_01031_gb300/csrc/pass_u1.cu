@@ -47,36 +47,6 @@ __device__ __forceinline__ void stv(T* p, const T (&v)[U1Vec<T>::n]) {
   *reinterpret_cast<typename U1Vec<T>::type*>(p) = *reinterpret_cast<const typename U1Vec<T>::type*>(v);
 }
 
-// The library's FP32 sine and cosine, out of line: the pass takes them only for
-// angles beyond pi/4, and one copy keeps the kernel's code small (instruction cache).
-__device__ __noinline__ float sin_slow(float x) { return sinf(x); }
-__device__ __noinline__ void sincos_slow(float x, float* s, float* c) { sincosf(x, s, c); }
-
-// sin and cos.  FP32: for |x| <= pi/4 the Taylor series about 0 in Horner
-// form (the first omitted terms, x^11/11! and x^12/12!, stay below 2e-9
-// there), else the library; link and plaquette angles are small in
-// practice.  FP64: the library.
-__device__ __forceinline__ void sincos_t(float x, float& s, float& c) {
-  if (fabsf(x) <= 0.78539816f) {
-    const float x2 = x * x;
-    s = x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
-    c = fmaf(x2,
-             fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.f / 3628800.f, 1.f / 40320.f), -1.f / 720.f), 1.f / 24.f),
-                  -0.5f),
-             1.f);
-  } else {
-    sincos_slow(x, &s, &c);
-  }
-}
-__device__ __forceinline__ float sin_t(float x) {
-  if (fabsf(x) <= 0.78539816f) {
-    const float x2 = x * x;
-    return x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f), -1.f / 6.f), 1.f);
-  }
-  return sin_slow(x);
-}
-__device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
-__device__ __forceinline__ double sin_t(double x) { return sin(x); }
 
 // Plaquette angle from its four link fields, one evaluation order everywhere
 // so that a plaquette shared by several sites has one value.
