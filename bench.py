@@ -106,9 +106,12 @@ def ncu_traffic(prec):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in the
+    background; summary() keeps the samples taken inside a window of host
+    times (the timed region), so a sampler started before the warm-up does
+    not count the set-up."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -116,6 +119,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.rows = []
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -127,34 +131,44 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
-        self.t0 = time.time()
+        return self
 
     def stop(self):
-        self.t1 = time.time()
         if self.proc is not None:
             self.proc.send_signal(signal.SIGTERM)
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-        rows = []
+        self.rows = []
         try:
             with open(self.path) as f:
                 for line in f:
                     parts = [p.strip() for p in line.split(",")]
-                    if len(parts) >= 9:
-                        rows.append(parts)
+                    if len(parts) >= 10:
+                        try:
+                            t = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                            t += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                        except (ValueError, IndexError):
+                            continue
+                        self.rows.append([t] + parts[1:])
             os.unlink(self.path)
         except OSError:
             pass
+        return self
+
+    def summary(self, t0=None, t1=None):
+        rows = [r for r in self.rows if (t0 is None or r[0] >= t0) and (t1 is None or r[0] <= t1)]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
 
 
 def dist_env():
@@ -229,8 +243,12 @@ def run_reference(args):
     return 0
 
 
-def time_device(P, torch, lat, steps, warmup, rank, ws):
-    """K steps bracketed by barrier + synchronize, CUDA events on the lattice stream."""
+def time_device(P, torch, lat, steps, warmup, rank, ws, min_window_s=0.0):
+    """K steps bracketed by barrier + synchronize, CUDA events on the lattice
+    stream.  With min_window_s > 0 the same K-step region is then repeated,
+    each repeat timed alike, until that much time has passed since the timed
+    region began, so that a clock sampler running in the background sees the
+    GPU under this load (the reported time is the first region's)."""
     stream = torch.cuda.current_stream()
     lat.step(warmup)
     torch.cuda.synchronize()
@@ -242,6 +260,7 @@ def time_device(P, torch, lat, steps, warmup, rank, ws):
     lat.enable_pass_timing(True)
     n0 = lat.launches()
     torch.cuda.synchronize()
+    t_start = time.time()
     e0.record(stream)
     lat.step(steps)
     e1.record(stream)
@@ -250,8 +269,16 @@ def time_device(P, torch, lat, steps, warmup, rank, ws):
     launches = lat.launches() - n0
     ms = e0.elapsed_time(e1)
     pass_ms, npass = lat.pass_timing(reset=True)
+    repeats = []
+    while time.time() - t_start < min_window_s:
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        repeats.append(e0.elapsed_time(e1))
+    t_end = time.time()
     ms = max_over_ranks(ms, ws)
-    return ms, launches, pass_ms / max(npass, 1), npass
+    return ms, launches, pass_ms / max(npass, 1), npass, (t_start, t_end, repeats)
 
 
 def run_ours(args):
@@ -279,10 +306,18 @@ def run_ours(args):
         lat = make(prec, SEED + rank)
         steps = args.steps if name == "f32" else max(1, min(args.steps, args.fp64_steps))
         sampler = ClockSampler(local if ws > 1 else 0)
+        clocks = None
         if name == "f32":
             sampler.start()
-        ms, launches, pass_ms, npass = time_device(P, torch, lat, steps, args.warmup, rank, ws)
-        clocks = sampler.stop() if name == "f32" else None
+            time.sleep(0.3)   # nvidia-smi's first sample
+        ms, launches, pass_ms, npass, (t0, t1, repeats) = time_device(
+            P, torch, lat, steps, args.warmup, rank, ws, min_window_s=1.0 if name == "f32" else 0.0)
+        if name == "f32":
+            clocks = sampler.stop().summary(t0 - 0.05, t1 + 0.05)
+            clocks["window"] = ("the timed region and %d repeats of it (%.0f ms in all); repeat median "
+                                "%.4f ms per step" % (len(repeats), (t1 - t0) * 1e3,
+                                                      statistics.median(repeats) / steps if repeats else
+                                                      ms / steps))
         e = lat.energies(allow_nonfinite=True)
         results[name] = dict(ms=ms, steps=steps, launches=launches, pass_ms=pass_ms, npass=npass,
                              clocks=clocks, rho=e["rho"], a=e["a"], nonfinite=e["nonfinite"])
@@ -435,19 +470,28 @@ def other_workloads(P, torch, stream, peak):
     u1 = dict(dt=0.01, integrator=P.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
               phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=P.EXP_OFF, fstar_over_mp=0.5)
     lat = P.Lattice(P.MODEL_U1_HIGGS, 256, 0.1, 1.0, 1, P.make_params(precision=P.FP32, stream=stream, **u1))
+    rel0 = lat.gauss()[0]
     lat.step(20)
     torch.cuda.synchronize()
+    sampler = ClockSampler(0).start()
+    time.sleep(0.3)
     lat.pass_timing(reset=True)
     lat.enable_pass_timing(True)
+    t0 = time.time()
     lat.step(500)
     torch.cuda.synchronize()
+    t1 = time.time()
     ms, n = lat.pass_timing(reset=True)
+    lat.enable_pass_timing(False)
+    clocks = sampler.stop().summary(t0 - 0.05, t1 + 0.05)
+    lat.step(2480)   # the rest of the 3000-step run of the workload
     rel = lat.gauss()[0]
     lat.close()
     gbs = 256 ** 3 * 10 * 2 * 4 / (ms / n * 1e-3) / 1e9
     out["u1_higgs_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
-                                   "gauss_rel_after_520_steps": rel, "kernel": "dk_pass_u1<float,0>"}
+                                   "gauss_rel_at_start": rel0, "gauss_rel_after_3000_steps": rel,
+                                   "kernel": "dk_pass_u1<float,0>", "clocks": clocks}
     # SU(2) x U(1) doublet, 256^3, FP32, leapfrog dt = 0.01, no expansion
     lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 256, 0.1, 1.0, 1, P.make_params(precision=P.FP32, stream=stream, **SU2))
     lat.step(10)
@@ -501,16 +545,35 @@ def other_workloads(P, torch, stream, peak):
         g.sync()
         torch.cuda.synchronize()
         t_fwd = time.perf_counter() - t0
+        sampler = ClockSampler(0).start()
+        time.sleep(0.3)
+        g.enable_pass_timing(True)
+        g.pass_timing(reset=True)
+        g.adjoint_pass_timing(reset=True)
         t0 = time.perf_counter()
+        w0 = time.time()
         J, dq, _, ab = g.adjoint(4000, 500, scale=True)
         torch.cuda.synchronize()
         t_adj = time.perf_counter() - t0
+        w1 = time.time()
+        g.enable_pass_timing(False)
+        ams, an = g.adjoint_pass_timing(reset=True)
+        fms, fn = g.pass_timing(reset=True)
+        clocks = sampler.stop().summary(w0 - 0.05, w1 + 0.05)
         g.close()
+        sites = 128 ** 3
+        agbs = sites * 64 / (ams / an * 1e-3) / 1e9
         out["adjoint_128_fp32_vv4_" + tag] = {
             "forward_s": t_fwd, "forward_plus_reverse_s": t_adj,
             "reverse_over_forward": (t_adj - t_fwd) / t_fwd, "J": J, "dJ_dq": dq, "dJ_da": ab[0], "dJ_db": ab[1],
             "steps": 4000, "ckpt_every": 500,
-            "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps"}
+            "adjoint_pass_us": ams / an * 1e3, "adjoint_passes": an, "adjoint_bytes_per_site_pass": 64,
+            "adjoint_pass_gbs": agbs, "adjoint_frac_hbm": agbs / peak,
+            "forward_pass_us_inside_adjoint": fms / max(fn, 1) * 1e3,
+            "adjoint_pass_over_forward_pass": (ams / an) / (fms / max(fn, 1)) if fn else None,
+            "clocks": clocks,
+            "note": "reverse = the cl_adjoint call minus a plain forward run of the same steps; pass times from "
+                    "CUDA events around each launch (cl_adjoint_pass_timing)"}
     # initial conditions and spectra at 256^3, outside a run's timed loop: wall time
     # of cl_init (allocation, Fourier-space draws, inverse FFTs, IC kernels) and of
     # cl_spectrum of one field (complex conversion, three FFT axis passes, shell

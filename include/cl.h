@@ -252,6 +252,9 @@ const char* cl_last_error(const cl_ctx* ctx);  /* never NULL; ctx may be NULL */
  * returned by cl_pass_timing.  Disabled by default (no events recorded). */
 cl_status cl_enable_pass_timing(cl_ctx* ctx, int enable);
 cl_status cl_pass_timing(cl_ctx* ctx, double* ms_total, int64_t* passes, int reset);
+/* The same for the reversed (adjoint) passes that cl_adjoint launches while
+ * timing is enabled; cl_pass_timing counts only the forward DK passes. */
+cl_status cl_adjoint_pass_timing(cl_ctx* ctx, double* ms_total, int64_t* passes, int reset);
 
 /* ---------------------------------------------------------------------------
  * Ensembles (batched independent lattices).  `count` lattices of one model and
@@ -332,6 +335,24 @@ cl_status cl_measure_fp64_rate(void* stream, double* flops_per_s);
  * wait took.  Needs no context; synchronises `stream` (a cudaStream_t, NULL =
  * default). */
 cl_status cl_selftest_wait(void* stream, int kind, int satisfied, uint64_t limit_ns, uint64_t* elapsed_ns);
+
+/* The counter-based generator of the initial conditions, evaluated on the GPU
+ * by the same device code cl_init uses (Philox4x32-10 of Salmon et al., SC'11,
+ * keyed by the seed; the deviates of the Rayleigh amplitudes and uniform phases
+ * of Sec. 3.5.1, eqs. fpr_influct and QuantumFlucts2), for checks against a
+ * host implementation.  For element i of n (host arrays, caller-owned):
+ *   mode 0: out[4i..4i+3] = Philox4x32-10(counter ctr[4i..4i+3], key key[2i..2i+1]);
+ *           u[2i], u[2i+1] = the 53-bit deviates in (0, 1] made from words (0, 1)
+ *           and (2, 3): (2^26 (w_hi >> 5) + (w_lo >> 6) + 1) 2^-53;
+ *   mode 1: u[2i], u[2i+1] = the draw pair of the initial conditions at Fourier
+ *           index ctr[4i] (x fastest), component ctr[4i+1], draw ctr[4i+2]
+ *           (0 amplitudes, 1 phases) with seed key[2i] + 2^32 key[2i+1]
+ *           (counter (index, component, draw, 0)); out is zeroed.
+ * n in 0 .. 2^24.  Allocates device memory for the call; synchronises `stream`
+ * (a cudaStream_t, NULL = default).  CL_EINVAL for bad arguments, CL_ENOMEM /
+ * CL_ECUDA on failure.  Needs no context. */
+cl_status cl_philox_draws(void* stream, int mode, int n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                          double* u);
 
 /* Ensemble-averaged binned spectrum: delta_b of cl_spectrum averaged over
  * the lattices lats[0 .. nl) (which must share N and kIR); k and mult as in

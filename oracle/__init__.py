@@ -127,6 +127,9 @@ def lib():
             L.clo_philox4x32_10.restype = None
             L.clo_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
             L.clo_u01.restype = ctypes.c_double
+            L.clo_gauss_modes.argtypes = [c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
+            L.clo_draw_pairs.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
             L.clo_fft3d.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int]
             L.clo_dft3d_naive.argtypes = [dp, dp, dp, dp, ctypes.c_int, ctypes.c_int]
             L.clo_schedule.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int]
@@ -206,6 +209,19 @@ class Oracle:
         e = Energies()
         self.L.clo_energies(self.h, ctypes.byref(e))
         return e.as_dict()
+
+    def gauss_modes(self, idx):
+        """U(1) model: Fourier values (unnormalised forward transform) of the
+        Gauss-law link momenta of the current charged field at Fourier sites idx:
+        complex array (len(idx), 3)."""
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+        out = np.zeros(idx.size * 6)
+        rc = self.L.clo_gauss_modes(self.h, idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    _dp(out))
+        if rc != 0:
+            raise ValueError("clo_gauss_modes")
+        out = out.reshape(-1, 3, 2)
+        return out[:, :, 0] + 1j * out[:, :, 1]
 
     def get(self, field, what=0):
         out = np.empty(self.V, dtype=np.float64)
@@ -371,6 +387,21 @@ def philox4x32_10(ctr, key):
 
 def u01(hi, lo):
     return lib().clo_u01(hi, lo)
+
+
+def draw_pairs(seed, idx, f, j):
+    """The oracle's IC draw pairs (u1, u2) at Fourier indices idx, components f,
+    draws j (0 amplitudes, 1 phases): shape (n, 2)."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).reshape(-1))
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.int32).reshape(-1))
+    j = np.ascontiguousarray(np.asarray(j, dtype=np.int32).reshape(-1))
+    out = np.zeros((idx.size, 2))
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = lib().clo_draw_pairs(int(seed), idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              f.ctypes.data_as(ip), j.ctypes.data_as(ip), _dp(out))
+    if rc != 0:
+        raise ValueError("clo_draw_pairs")
+    return out
 
 
 def fft3d(x, sign):

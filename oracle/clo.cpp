@@ -874,36 +874,52 @@ void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F
 // The doublet model (links start at the identity, so both laws are linear
 // there) takes the same inversion for the U(1) density and for each SU(2)
 // colour's density.
+// pi_A,i at Fourier site idx from the transformed density rhok.
+cplx gauss_mode(const clo_ctx* c, const std::vector<cplx>& rhok, long idx, int i) {
+  if (idx == 0) return cplx(0.0, 0.0);
+  long x, y, z;
+  c->coords(idx, x, y, z);
+  long nn[3] = {x, y, z};
+  double kk = 0.0;
+  cplx ki;
+  for (int j = 0; j < 3; ++j) {
+    double t = 2.0 * PI * (double)nn[j] / (double)c->N;
+    cplx kap = (1.0 - cplx(std::cos(t), -std::sin(t))) / c->dx;
+    kk += std::norm(kap);
+    if (j == i) ki = kap;
+  }
+  return std::conj(ki) * rhok[idx] / kk;
+}
+
 void invert_gauss(const clo_ctx* c, std::vector<cplx> rho, std::vector<double>* out) {
+  bool zero = true;  // a zero density inverts to zero exactly: skip the transforms
+  for (long n = 0; n < c->V && zero; ++n) zero = rho[n] == cplx(0.0, 0.0);
+  if (zero) {
+    for (int i = 0; i < 3; ++i) out[i].assign(c->V, 0.0);
+    return;
+  }
   fft3d(rho, c->N, -1);
   for (int i = 0; i < 3; ++i) {
     std::vector<cplx> E(c->V);
-    for (long idx = 1; idx < c->V; ++idx) {
-      long x, y, z;
-      c->coords(idx, x, y, z);
-      long nn[3] = {x, y, z};
-      double kk = 0.0;
-      cplx ki;
-      for (int j = 0; j < 3; ++j) {
-        double t = 2.0 * PI * (double)nn[j] / (double)c->N;
-        cplx kap = (1.0 - cplx(std::cos(t), -std::sin(t))) / c->dx;
-        kk += std::norm(kap);
-        if (j == i) ki = kap;
-      }
-      E[idx] = std::conj(ki) * rho[idx] / kk;
-    }
+    for (long idx = 1; idx < c->V; ++idx) E[idx] = gauss_mode(c, rho, idx, i);
     fft3d(E, c->N, +1);
     for (long n = 0; n < c->V; ++n) out[i][n] = E[n].real() / (double)c->V;
   }
+}
+
+// Charge density of the U(1) Gauss law from the charged field and its momentum.
+void u1_charge_density(const clo_ctx* c, std::vector<cplx>& rho) {
+  double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  rho.assign(c->V, cplx(0.0, 0.0));
+  for (long n = 0; n < c->V; ++n)
+    rho[n] = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
 }
 
 void gauss_momenta(clo_ctx* c) {
   std::vector<cplx> rho(c->V);
   double lhs, rhs;
   if (!c->su2()) {
-    double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
-    for (long n = 0; n < c->V; ++n)
-      rho[n] = fo2 * c->p.gQ * (c->phi[0][n] * c->pi[1][n] - c->phi[1][n] * c->pi[0][n]);
+    u1_charge_density(c, rho);
     invert_gauss(c, rho, c->piA);
     return;
   }
@@ -1846,6 +1862,34 @@ int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out) {
         out[(size_t)(2 * f + j) * c->V + idx] = s / V * (e * L[f][0][idx] + cpi * L[f][1][idx]).real();
       }
   }
+  return 0;
+}
+
+// U(1) model: the Fourier values of the Gauss-law link momenta (the initial
+// conditions' inversion, eq. GaugeCurrentFluc on the lattice) of the context's
+// current charged field, at Fourier sites idx[i]: out[(3 i + dir) 2 + {0, 1}] =
+// Re, Im of pi_A,dir (unnormalised forward transform, like the state's FFT).
+int clo_gauss_modes(const clo_ctx* c, int n, const int64_t* idx, double* out) {
+  if (!c || c->model != CLO_MODEL_U1_HIGGS || n < 0 || (n > 0 && (!idx || !out))) return -1;
+  std::vector<cplx> rho;
+  u1_charge_density(c, rho);
+  fft3d(rho, c->N, -1);
+  for (int i = 0; i < n; ++i) {
+    if (idx[i] < 0 || idx[i] >= c->V) return -1;
+    for (int d = 0; d < 3; ++d) {
+      cplx e = gauss_mode(c, rho, (long)idx[i], d);
+      out[(3 * (size_t)i + d) * 2] = e.real();
+      out[(3 * (size_t)i + d) * 2 + 1] = e.imag();
+    }
+  }
+  return 0;
+}
+
+// The oracle's draw pair of the initial conditions (draw4) for element i:
+// Fourier index idx[i], component f[i], draw j[i], seed `seed`.
+int clo_draw_pairs(uint64_t seed, int n, const int64_t* idx, const int* f, const int* j, double* out) {
+  if (n < 0 || (n > 0 && (!idx || !f || !j || !out))) return -1;
+  for (int i = 0; i < n; ++i) draw4(seed, (long)idx[i], f[i], j[i], out + 2 * (size_t)i);
   return 0;
 }
 

@@ -142,6 +142,9 @@ int clo_ic_draws(int model, int N, double kIR, double alpha, uint64_t seed, cons
 /* pieces exposed for the pin tests */
 void clo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double clo_u01(uint32_t hi, uint32_t lo);
+int clo_gauss_modes(const clo_ctx* c, int n, const int64_t* idx, double* out); /* U(1) IC link momenta, Fourier */
+int clo_draw_pairs(uint64_t seed, int n, const int64_t* idx, const int* f, const int* j,
+                   double* out);  /* the IC draw pairs (u1, u2) */
 int clo_fft3d(double* re, double* im, int N, int sign);      /* in place, unnormalised */
 int clo_dft3d_naive(const double* re, const double* im, double* ore, double* oim, int N, int sign);
 int clo_schedule(int integrator, double h, double* drifts, int cap);

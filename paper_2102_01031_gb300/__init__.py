@@ -36,7 +36,8 @@ EXPORTS = (
     "cl_lattice_set_state", "cl_lattice_scalars", "cl_lattice_tile", "cl_ensemble_spectrum",
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
-    "cl_set_tune_cache", "cl_selftest_wait", "cl_pass_weights",
+    "cl_set_tune_cache", "cl_selftest_wait", "cl_pass_weights", "cl_philox_draws",
+    "cl_adjoint_pass_timing",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -144,6 +145,7 @@ def lib():
     L.cl_last_error.restype = ctypes.c_char_p
     L.cl_enable_pass_timing.argtypes = [vp, ip]
     L.cl_pass_timing.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ip]
+    L.cl_adjoint_pass_timing.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ip]
     L.cl_volume_averages_noalloc.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ip, ctypes.POINTER(vp), vp, vp]
     i64p = ctypes.POINTER(ctypes.c_int64)
@@ -167,6 +169,8 @@ def lib():
                                    ctypes.POINTER(ctypes.c_uint64)]
     L.cl_em_spectrum.argtypes = [vp, ip, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_int64), ip,
                                  ctypes.POINTER(ctypes.c_int)]
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    L.cl_philox_draws.argtypes = [vp, ip, ip, u32p, u32p, u32p, dp]
     L.cl_occupation.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp,
                                 ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -245,6 +249,28 @@ def pass_weights(integrator, h, steps_per_call):
         if rc != CL_EINVAL or n.value <= cap:
             raise ClError(rc, "cl_pass_weights")
         cap = n.value
+
+
+def philox_draws(mode, ctr, key, stream=None):
+    """cl_philox_draws: the initial conditions' generator on the GPU.  ctr is (n, 4)
+    and key (n, 2) uint32; returns (words (n, 4) uint32, deviates (n, 2) float64):
+    mode 0 the raw Philox4x32-10 words and their two 53-bit deviates, mode 1 the
+    draw pair of the initial conditions (ctr rows = Fourier index, component,
+    draw, unused; key rows = the seed's low and high words)."""
+    L = lib()
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    if len(c) != len(k):
+        raise ValueError("ctr and key lengths differ")
+    n = len(c)
+    out = np.zeros((n, 4), dtype=np.uint32)
+    u = np.zeros((n, 2))
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    rc = L.cl_philox_draws(stream, int(mode), n, c.ctypes.data_as(u32p), k.ctypes.data_as(u32p),
+                           out.ctypes.data_as(u32p), _dp(u))
+    if rc != CL_OK:
+        raise ClError(rc, "cl_philox_draws")
+    return out, u
 
 
 def selftest_wait(kind, satisfied, limit_ns, stream=None):
@@ -434,6 +460,14 @@ class Lattice:
         n = ctypes.c_int64()
         _check(self.L, self.h, self.L.cl_pass_timing(self.h, ctypes.byref(ms), ctypes.byref(n),
                                                      1 if reset else 0), "timing")
+        return ms.value, n.value
+
+    def adjoint_pass_timing(self, reset=False):
+        """cl_adjoint_pass_timing: (ms, passes) of the reversed passes timed so far."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self.L, self.h, self.L.cl_adjoint_pass_timing(self.h, ctypes.byref(ms), ctypes.byref(n),
+                                                             1 if reset else 0), "timing")
         return ms.value, n.value
 
     def adjoint(self, nsteps, ckpt_every=500, objective=OBJ_CHI_FRACTION, field=1, what=0, dk_bin=1.0,

@@ -160,8 +160,11 @@ struct cl_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
   std::vector<int> ev_npass;
+  std::vector<int> ev_kind;        // 0: DK passes, 1: adjoint passes
   double timing_ms = 0.0;
   long long timing_passes = 0;
+  double adj_timing_ms = 0.0;
+  long long adj_timing_passes = 0;
   std::string err;
 };
 
@@ -350,6 +353,53 @@ cl_status enqueue_multi(cl_ctx* c, PassKernel k, PassArgs& A, cudaStream_t st) {
 // kernel (all CTAs resident) that runs them back to back, reading the
 // per-pass weights from a device copy; it is recorded in a CUDA graph the
 // first time and the graph is replayed for the same passes later.
+// Timing hook: an event pair from the context's pool around a launch of n
+// passes of one kind (0 DK passes, 1 adjoint passes), read back by
+// cl_pass_timing / cl_adjoint_pass_timing.
+cl_status timing_begin(cl_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+  for (cudaEvent_t* e : {e0, e1}) {
+    if (!c->ev_pool.empty()) {
+      *e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+    } else {
+      CU(cudaEventCreate(e));
+    }
+  }
+  CU(cudaEventRecord(*e0, c->stream));
+  return CL_OK;
+}
+
+cl_status timing_end(cl_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int n, int kind) {
+  CU(cudaEventRecord(e1, c->stream));
+  c->ev_pending.push_back(std::make_pair(e0, e1));
+  c->ev_npass.push_back(n);
+  c->ev_kind.push_back(kind);
+  return CL_OK;
+}
+
+// Adds the pending event pairs to the per-kind totals (synchronises the stream).
+cl_status timing_collect(cl_ctx* c) {
+  CU(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < c->ev_pending.size(); ++i) {
+    auto& pr = c->ev_pending[i];
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    if (c->ev_kind[i] == 1) {
+      c->adj_timing_ms += ms;
+      c->adj_timing_passes += c->ev_npass[i];
+    } else {
+      c->timing_ms += ms;
+      c->timing_passes += c->ev_npass[i];
+    }
+    c->ev_pool.push_back(pr.first);
+    c->ev_pool.push_back(pr.second);
+  }
+  c->ev_pending.clear();
+  c->ev_npass.clear();
+  c->ev_kind.clear();
+  return CL_OK;
+}
+
 cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write, int set_rho0,
                         double* log = nullptr, long long log_base = 0) {
   PassKernel k = pick_kernel(c, red);
@@ -424,15 +474,8 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
-    for (cudaEvent_t* e : {&e0, &e1}) {
-      if (!c->ev_pool.empty()) {
-        *e = c->ev_pool.back();
-        c->ev_pool.pop_back();
-      } else {
-        CU(cudaEventCreate(e));
-      }
-    }
-    CU(cudaEventRecord(e0, c->stream));
+    cl_status s = timing_begin(c, &e0, &e1);
+    if (s != CL_OK) return s;
   }
   if (multi && exec) {
     CU(cudaGraphLaunch(exec, c->stream));
@@ -454,9 +497,8 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   }
   c->launches += multi ? 1 : n;
   if (c->timing) {
-    CU(cudaEventRecord(e1, c->stream));
-    c->ev_pending.push_back(std::make_pair(e0, e1));
-    c->ev_npass.push_back(n);
+    cl_status s = timing_end(c, e0, e1, n, 0);
+    if (s != CL_OK) return s;
   }
   if (write && (n & 1)) c->parity ^= 1;
   return CL_OK;
@@ -1723,23 +1765,26 @@ cl_status cl_enable_pass_timing(cl_ctx* c, int enable) {
 
 cl_status cl_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset) {
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
-  CU(cudaStreamSynchronize(c->stream));
-  for (size_t i = 0; i < c->ev_pending.size(); ++i) {
-    auto& pr = c->ev_pending[i];
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
-    c->timing_ms += ms;
-    c->timing_passes += c->ev_npass[i];
-    c->ev_pool.push_back(pr.first);
-    c->ev_pool.push_back(pr.second);
-  }
-  c->ev_pending.clear();
-  c->ev_npass.clear();
+  cl_status s = timing_collect(c);
+  if (s != CL_OK) return s;
   if (ms_total) *ms_total = c->timing_ms;
   if (passes) *passes = c->timing_passes;
   if (reset) {
     c->timing_ms = 0.0;
     c->timing_passes = 0;
+  }
+  return CL_OK;
+}
+
+cl_status cl_adjoint_pass_timing(cl_ctx* c, double* ms_total, int64_t* passes, int reset) {
+  if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
+  cl_status s = timing_collect(c);
+  if (s != CL_OK) return s;
+  if (ms_total) *ms_total = c->adj_timing_ms;
+  if (passes) *passes = c->adj_timing_passes;
+  if (reset) {
+    c->adj_timing_ms = 0.0;
+    c->adj_timing_passes = 0;
   }
   return CL_OK;
 }
@@ -1825,6 +1870,11 @@ static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
   A.wait_limit_ns = 2000000000ull;
   A.adj = dev_coef;
   A.npass = 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    cl_status s = timing_begin(c, &e0, &e1);
+    if (s != CL_OK) return s;
+  }
   if (n > 1 && J.coop) {
     A.npass = n;
     A.gsync = c->d_gsync;
@@ -1840,6 +1890,10 @@ static cl_status launch_adjoint(cl_ctx* c, const double* dev_coef, int n) {
       CHECK_LAUNCH();
       ++c->launches;
     }
+  }
+  if (c->timing) {
+    cl_status s = timing_end(c, e0, e1, n, 1);
+    if (s != CL_OK) return s;
   }
   if (n & 1) c->parity ^= 1;
   return CL_OK;

@@ -652,4 +652,61 @@ cudaError_t launch_convert(int fp32, int to_double, const void* in, void* out, l
   return cudaGetLastError();
 }
 
+
+// The generator as the initial conditions use it, for a bit-exact check
+// against the oracle: for element i, either the raw Philox4x32-10 of
+// (ctr[4i..4i+3], key[2i..2i+1]) (mode 0) or the draw pair of the initial
+// conditions at Fourier index ctr[4i], component ctr[4i+1], draw ctr[4i+2]
+// with the seed key[2i] + 2^32 key[2i+1] (mode 1, draw_pair itself).  out
+// receives the four words (mode 0) and u the two 53-bit deviates in (0, 1].
+__global__ void philox_probe_kernel(const uint32_t* ctr, const uint32_t* key, int n, int mode, uint32_t* out,
+                                    double* u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (mode == 0) {
+    uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+    for (int k = 0; k < 4; ++k) out[4 * i + k] = c[k];
+    u[2 * i] = unit_open0(c[0], c[1]);
+    u[2 * i + 1] = unit_open0(c[2], c[3]);
+  } else {
+    const unsigned long long seed = (unsigned long long)key[2 * i] | ((unsigned long long)key[2 * i + 1] << 32);
+    double u0, u1;
+    draw_pair(seed, ctr[4 * i], (int)ctr[4 * i + 1], (int)ctr[4 * i + 2], u0, u1);
+    for (int k = 0; k < 4; ++k) out[4 * i + k] = 0u;
+    u[2 * i] = u0;
+    u[2 * i + 1] = u1;
+  }
+}
+
 }  // namespace clg
+
+extern "C" cl_status cl_philox_draws(void* stream, int mode, int n, const uint32_t* ctr, const uint32_t* key,
+                                     uint32_t* out, double* u) {
+  if (n < 0 || n > (1 << 24) || (mode != 0 && mode != 1) || (n > 0 && (!ctr || !key || !out || !u)))
+    return CL_EINVAL;
+  if (n == 0) return CL_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bc = (size_t)n * 4 * sizeof(uint32_t), bk = (size_t)n * 2 * sizeof(uint32_t),
+               bu = (size_t)n * 2 * sizeof(double);
+  char* d = nullptr;
+  if (cudaMalloc(&d, 2 * bc + bk + bu) != cudaSuccess) return CL_ENOMEM;
+  uint32_t* dc = (uint32_t*)d;
+  uint32_t* dout = (uint32_t*)(d + bc);
+  uint32_t* dk = (uint32_t*)(d + 2 * bc);
+  double* du = (double*)(d + 2 * bc + bk);
+  cl_status s = CL_OK;
+  if (cudaMemcpyAsync(dc, ctr, bc, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dk, key, bk, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    s = CL_ECUDA;
+  if (s == CL_OK) {
+    clg::philox_probe_kernel<<<(n + 255) / 256, 256, 0, st>>>(dc, dk, n, mode, dout, du);
+    if (cudaGetLastError() != cudaSuccess) s = CL_ECUDA;
+  }
+  if (s == CL_OK && (cudaMemcpyAsync(out, dout, bc, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaMemcpyAsync(u, du, bu, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess))
+    s = CL_ECUDA;
+  cudaFree(d);
+  return s;
+}

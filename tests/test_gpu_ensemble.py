@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.parity import assert_bins
 
 pytestmark = pytest.mark.gpu
 
@@ -93,7 +94,7 @@ def test_ensemble_spectrum_is_mean_of_members(P):
     do = np.mean([r[1] for r in ref], axis=0)
     assert np.array_equal(m, mo)
     assert np.abs(k - ko).max() < 1e-12 * ko.max()
-    assert np.abs(d - do).max() < 1e-9 * np.abs(do).max()
+    assert_bins(d, do, 1e-9, "ensemble mean")
     with pytest.raises(P.ClError):
         P.Ensemble(O.MODEL_LPHI4_CHI, [16, 32], [0.5, 0.5], 1.0, [1, 2],
                    P.make_params(**C2S)).spectrum_mean([0, 1], 0)
@@ -166,7 +167,7 @@ def test_batched_ensemble_64_lattices(P):
         ref.append(o.spectrum(0, 0, 1.0)[1])
     _, d3, _ = E.spectrum_mean([0, 1, 2], 0, 0, 1.0)
     do = np.mean(ref, axis=0)
-    assert np.abs(d3 - do).max() < 1e-3 * np.abs(do).max()
+    assert_bins(d3, do, 1e-3, "FP32 ensemble mean")
 
 
 def test_autotune_cache_file(P, tmp_path):

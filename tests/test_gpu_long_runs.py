@@ -1,0 +1,104 @@
+"""Full-run accuracy of the scalar path, the criteria a long preheating run is
+judged by (resonant growth is chaotic, so pointwise agreement over a whole run
+is not the measure; averages, binned spectra and constraints are):
+
+  * FP64 on the GPU against the FP64 oracle over the whole single-field run
+    (32^3, VV2, dt = 0.01, 2000 steps, self-consistent expansion): the volume
+    averages E_K, E_G, E_V, a and a' and every bin of the field and momentum
+    spectra (eq. discretePS) within 1e-6 relative, bin by bin, at every 500
+    steps; the Hubble-constraint violation (Sec. 3.3.2 outputs) no worse than
+    1.05 x the oracle's.
+  * FP32 storage against the FP64 path through the resonance of the two-field
+    model (256^3, kIR = 0.1, q = 100, VV4, dt = 0.005, 5000 steps to eta = 25,
+    self-consistent expansion, the same seed): every bin of the phi and chi
+    spectra within 1 % relative after the resonance, and the FP32 run's
+    Hubble-constraint violation no worse than 1.05 x the FP64 run's.  The FP64
+    GPU path is itself held to the oracle (pointwise over 200 steps, and by the
+    first test over a full run), so it stands in for the oracle at a size the
+    oracle cannot reach in a test.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.parity import bin_rel
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(dt=0.01, integrator=O.VV2, phi0=[1.0], fluct_amp2=1e-4, expansion=O.EXP_SELF,
+          fstar_over_mp=0.5)
+C2 = dict(dt=0.005, integrator=O.VV4, q=100.0, phi0=[1.0, 0.0], fluct_amp2=1e-4,
+          expansion=O.EXP_SELF, fstar_over_mp=0.5)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2102_01031_gb300 as P
+    P.build()
+    P.lib()
+    return P
+
+
+def rel(x, y):
+    return abs(x - y) / max(abs(y), 1e-300)
+
+
+def test_c1_full_run_averages_and_spectra(P):
+    g = P.Lattice(O.MODEL_LPHI4, 32, 0.5, 1.0, 1, P.make_params(**C1))
+    o = O.Oracle(O.MODEL_LPHI4, 32, 0.5, 1.0, 1, O.make_params(**C1))
+    report = []
+    for chunk in range(4):
+        g.step(500)
+        o.step(500)
+        eg, eo = g.energies(), o.energies()
+        errs = {k: rel(eg[k][0], eo[k][0]) for k in ("EK", "EG", "EV")}
+        errs.update({k: rel(eg[k], eo[k]) for k in ("a", "b", "rho")})
+        for w, name in ((0, "spec_phi"), (1, "spec_pi")):
+            kg, dg, mg = g.spectrum(0, w)
+            ko, do, mo = o.spectrum(0, w)
+            assert np.array_equal(mg, mo)
+            errs[name] = bin_rel(dg, do)
+        errs["hubble_gpu"], errs["hubble_oracle"] = eg["hubble_viol"], eo["hubble_viol"]
+        report.append(errs)
+        print("C1 step %d: %s" % (500 * (chunk + 1), errs))
+        for k in ("EK", "EG", "EV", "a", "b", "rho", "spec_phi", "spec_pi"):
+            assert errs[k] <= 1e-6, (500 * (chunk + 1), k, errs[k])
+        assert abs(eg["hubble_viol"]) <= 1.05 * abs(eo["hubble_viol"]) + 1e-15
+    g.close()
+
+
+def test_c2_post_resonance_fp32_against_fp64_256(P):
+    N, kIR = 256, 0.1
+    lat = {prec: P.Lattice(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, P.make_params(precision=prec, **C2))
+           for prec in (P.FP64, P.FP32)}
+    history = []
+    for chunk in range(10):
+        for l in lat.values():
+            l.step(500)
+        e64, e32 = lat[P.FP64].energies(), lat[P.FP32].energies()
+        frac = (e64["EK"][1] + e64["EG"][1]) / e64["rho"]
+        history.append((500 * (chunk + 1), frac, e32["hubble_viol"], e64["hubble_viol"]))
+    for row in history:
+        print("C2 step %d: chi energy fraction %.4g, Hubble violation FP32 %.3g FP64 %.3g" % row)
+    errs = {}
+    for f in (0, 1):
+        for w in (0, 1):
+            k64, d64, m64 = lat[P.FP64].spectrum(f, w)
+            k32, d32, m32 = lat[P.FP32].spectrum(f, w)
+            assert np.array_equal(m32, m64)
+            r = np.abs(d32 - d64) / np.abs(d64)
+            errs[(f, w)] = float(r.max())
+            print("C2 spectrum field %d what %d: worst bin %d (%d modes) %.3g, median %.3g"
+                  % (f, w, int(r.argmax()), int(m64[r.argmax()]), r.max(), np.median(r)))
+    e64, e32 = lat[P.FP64].energies(), lat[P.FP32].energies()
+    for k in ("EK", "EG"):
+        for f in (0, 1):
+            print("C2 %s[%d]: FP32 %.10g FP64 %.10g rel %.3g" % (k, f, e32[k][f], e64[k][f], rel(e32[k][f], e64[k][f])))
+    # resonance happened: chi carries a sizeable share of the energy by eta = 25
+    assert history[-1][1] > 1e-2
+    for (f, w), e in errs.items():
+        if w == 0:
+            assert e <= 1e-2, (f, e)
+    assert abs(e32["hubble_viol"]) <= 1.05 * abs(e64["hubble_viol"]), (e32["hubble_viol"], e64["hubble_viol"])
+    for l in lat.values():
+        l.close()

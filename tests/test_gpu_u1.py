@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 from tests import inputs
+from tests.parity import assert_bins
 
 pytestmark = pytest.mark.gpu
 
@@ -234,7 +235,7 @@ def test_electric_and_magnetic_spectra_match(P, precision, alpha):
             ko, do, mo = o.em_spectrum(which, dk)
             assert np.array_equal(mg, mo)
             assert np.abs(kg - ko).max() < 1e-12 * ko.max()
-            assert np.abs(dg - do).max() < 1e-10 * np.abs(do).max(), (which, dk)
+            assert_bins(dg, do, 1e-10, (which, dk))
     s = P.Lattice(O.MODEL_LPHI4, 16, 0.5, 1.0, 1, P.make_params(dt=0.01, phi0=[1.0], fluct_amp2=1e-4))
     with pytest.raises(P.ClError) as e:
         s.em_spectrum(0)
