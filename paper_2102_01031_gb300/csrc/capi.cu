@@ -46,6 +46,8 @@ cudaError_t launch_ic_modes(double2*, double2*, const LatConst*, const LatScalar
 cudaError_t launch_ic_assemble(int, void*, void*, const double2*, const double2*, const LatConst*,
                                const LatScalars*, double, double, long long, cudaStream_t);
 cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
+cudaError_t launch_fft_twiddles(double2*, int, cudaStream_t);
+int fft_batch(int N);
 cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
 cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
                         cudaStream_t, int raw = 0);
@@ -137,6 +139,7 @@ struct cl_ctx {
   unsigned* d_cnt = nullptr;       // [nlat]
   double* d_tmp = nullptr;         // scratch for conversions / monitors (vmax doubles)
   double2* d_cplx = nullptr;       // scratch complex (2 vmax)
+  double2* d_tw = nullptr;         // FFT twiddle table (the largest lattice's N entries)
   double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk), per-lattice bins, mean
   int spec_lats = 0;               // lattices d_spec has room for
   unsigned* d_gsync = nullptr;     // arrival counters of multi-pass launches
@@ -263,7 +266,11 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
   FftPlan pl;
   pl.N = N;
   pl.sign = sign;
+  pl.batch = fft_batch(N);
+  pl.tw = c->d_tw;
   fft_radices(N, pl);
+  CU(launch_fft_twiddles(c->d_tw, N, c->stream));
+  ++c->launches;
   for (int axis = 0; axis < 3; ++axis) {
     pl.axis = axis;
     CU(launch_fft_axis(data, pl, c->stream));
@@ -688,6 +695,7 @@ cl_status cl_free(cl_ctx* c) {
   cudaFree(c->d_cnt);
   cudaFree(c->d_tmp);
   cudaFree(c->d_cplx);
+  cudaFree(c->d_tw);
   cudaFree(c->d_spec);
   cudaFree(c->d_gsync);
   cudaFree(c->adj.lam);
@@ -907,6 +915,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   CU(cudaMemcpyAsync(c->d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   // initial conditions, lattice by lattice
   CU(cudaMalloc(&c->d_cplx, 2 * (size_t)c->vmax * sizeof(double2)));
+  CU(cudaMalloc(&c->d_tw, 512 * sizeof(double2)));
   CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)c->vmax, 1 << 16) * sizeof(double)));
   for (int l = 0; l < c->nlat; ++l) {
     const LatHost& H = c->lats[l];
@@ -1065,6 +1074,7 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
     for (int a = 0; a < MAX_ARR; ++a) L.buf[par][a] = arr_ptr(c, 0, par, a);
   CU(cudaMemcpyAsync(c->d_lat, &L, sizeof(LatConst), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMalloc(&c->d_cplx, 2 * (size_t)H.V * sizeof(double2)));
+  CU(cudaMalloc(&c->d_tw, 512 * sizeof(double2)));
   CU(cudaMalloc(&c->d_tmp, std::max<size_t>((size_t)H.V, 1 << 16) * sizeof(double)));
   ICArgs A;
   memset(&A, 0, sizeof(A));

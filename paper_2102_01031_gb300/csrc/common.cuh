@@ -156,6 +156,8 @@ struct ICArgs {
 struct FftPlan {
   int N, nrad, axis, sign;
   int rad[16];
+  int batch;             // lines per CTA (a divisor of N)
+  const double2* tw;     // tw[e] = exp(+2 pi i e/N), e < N
 };
 
 // ---------------------------------------------------------------------------

@@ -253,53 +253,67 @@ template __global__ void ic_assemble_kernel<double>(double*, double*, const doub
                                                     double);
 
 // ---------------------------------------------------------------------------
-// 3-D FFT: batched 1-D transforms along one axis, one CTA per line, self
-// sorting Stockham passes of radix 4, 2 and 3 in shared memory.  Stage with
-// radix R after sub-length Ns: for j < N/R, k = j mod Ns,
+// 3-D FFT: batched 1-D transforms along one axis, `batch` lines per CTA
+// (consecutive in the fastest other index, so that the strided axes read whole
+// cache lines), self-sorting Stockham passes of radix 4, 2 and 3 in shared
+// memory.  Stage with radix R after sub-length Ns: for j < N/R, k = j mod Ns,
 //   v_r = x[j + r N/R] w^{k r},  w = exp(sign 2 pi i/(Ns R)),
 //   y[(j/Ns) Ns R + k + q Ns] = sum_r v_r exp(sign 2 pi i r q / R).
+// The twiddles come from a table of the N-th roots of unity (w^{k r} is root
+// (k r mod Ns R) N/(Ns R)), made once per transform by fft_twiddle_kernel.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__global__ void fft_twiddle_kernel(double2* tw, int N) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  double sn, cs;
+  sincospi(2.0 * (double)e / (double)N, &sn, &cs);
+  tw[e] = make_double2(cs, sn);
 }
 
 __global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
   extern __shared__ double2 fbuf[];
-  const int N = plan.N;
+  const int N = plan.N, B = plan.batch, Pt = N + 1;  // padded line pitch: no bank conflicts across lines
+  const int nt = blockDim.x, tid = threadIdx.x;
   double2* a = fbuf;
-  double2* b = fbuf + N;
-  const long long line = blockIdx.x;
-  const long long u = line % N, w = line / N;
-  long long base, stride;
-  if (plan.axis == 0) {
-    base = (long long)N * (u + (long long)N * w);
-    stride = 1;
-  } else if (plan.axis == 1) {
-    base = u + (long long)N * N * w;
-    stride = N;
-  } else {
-    base = u + (long long)N * w;
-    stride = (long long)N * N;
+  double2* b = fbuf + B * Pt;
+  double2* w = fbuf + 2 * B * Pt;
+  const int ng = N / B;
+  const long long u0 = (long long)(blockIdx.x % ng) * B, ww = blockIdx.x / ng;
+  const long long NN = (long long)N * N;
+  for (int e = tid; e < N; e += nt) {
+    const double2 t = plan.tw[e];
+    w[e] = make_double2(t.x, plan.sign * t.y);
   }
-  for (int j = threadIdx.x; j < N; j += blockDim.x) a[j] = data[base + j * stride];
+  // element (line u, position j): axis 0: N (u + N w) + j; axis 1: u + N j + N^2 w;
+  // axis 2: u + N w + N^2 j
+  if (plan.axis == 0) {
+    const double2* src = data + NN * ww + N * u0;  // B whole rows, contiguous
+    for (int t = tid; t < B * N; t += nt) a[(t / N) * Pt + t % N] = src[t];
+  } else {
+    const long long base = plan.axis == 1 ? NN * ww + u0 : N * ww + u0;
+    const long long js = plan.axis == 1 ? N : NN;
+    for (int t = tid; t < B * N; t += nt) a[(t % B) * Pt + t / B] = data[base + (t / B) * js + t % B];
+  }
   __syncthreads();
   int Ns = 1;
   for (int s = 0; s < plan.nrad; ++s) {
     const int R = plan.rad[s];
     const int NR = N / R;
     const int L = Ns * R;
-    for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+    const int ts = N / L;  // table stride of this stage's roots
+    for (int t = tid; t < B * NR; t += nt) {
+      const int j = t % NR, line = t / NR;
+      const double2* ai = a + line * Pt;
       const int k = j % Ns;
       double2 v[4];
       for (int r = 0; r < R; ++r) {
-        double2 x = a[j + r * NR];
-        if (k != 0 && r != 0) {
-          const int e = (k * r) % L;
-          double sn, cs;
-          sincospi(2.0 * (double)e / (double)L, &sn, &cs);
-          x = cmul(x, make_double2(cs, plan.sign * sn));
-        }
+        double2 x = ai[j + r * NR];
+        if (k != 0 && r != 0) x = cmul(x, w[((k * r) % L) * ts]);
         v[r] = x;
       }
       double2 o[4];
@@ -319,15 +333,15 @@ __global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
         o[3] = make_double2(t1.x - t3.x, t1.y - t3.y);
       } else {  // R == 3, w = (-1/2, sign sqrt3/2)
         const double h = 0.86602540378443864676 * plan.sign;
-        const double2 s = make_double2(v[1].x + v[2].x, v[1].y + v[2].y);
+        const double2 s3 = make_double2(v[1].x + v[2].x, v[1].y + v[2].y);
         const double2 d = make_double2(v[1].x - v[2].x, v[1].y - v[2].y);
-        const double2 m = make_double2(v[0].x - 0.5 * s.x, v[0].y - 0.5 * s.y);
-        o[0] = make_double2(v[0].x + s.x, v[0].y + s.y);
+        const double2 m = make_double2(v[0].x - 0.5 * s3.x, v[0].y - 0.5 * s3.y);
+        o[0] = make_double2(v[0].x + s3.x, v[0].y + s3.y);
         o[1] = make_double2(m.x - h * d.y, m.y + h * d.x);
         o[2] = make_double2(m.x + h * d.y, m.y - h * d.x);
       }
-      const int idxD = (j / Ns) * L + k;
-      for (int q2 = 0; q2 < R; ++q2) b[idxD + q2 * Ns] = o[q2];
+      double2* bo = b + line * Pt + (j / Ns) * L + k;
+      for (int q2 = 0; q2 < R; ++q2) bo[q2 * Ns] = o[q2];
     }
     __syncthreads();
     double2* t = a;
@@ -335,7 +349,14 @@ __global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
     b = t;
     Ns = L;
   }
-  for (int j = threadIdx.x; j < N; j += blockDim.x) data[base + j * stride] = a[j];
+  if (plan.axis == 0) {
+    double2* dst = data + NN * ww + N * u0;
+    for (int t = tid; t < B * N; t += nt) dst[t] = a[(t / N) * Pt + t % N];
+  } else {
+    const long long base = plan.axis == 1 ? NN * ww + u0 : N * ww + u0;
+    const long long js = plan.axis == 1 ? N : NN;
+    for (int t = tid; t < B * N; t += nt) data[base + (t / B) * js + t % B] = a[(t % B) * Pt + t / B];
+  }
 }
 
 template <typename T>
@@ -513,9 +534,30 @@ cudaError_t launch_ic_assemble(int fp32, void* phi, void* pi, const double2* F, 
   return cudaGetLastError();
 }
 
+// Lines per CTA: the largest divisor of N with batch * N <= 2048 (at most 72 KB
+// of shared memory per CTA).
+int fft_batch(int N) {
+  int b = 1;
+  for (int d = 1; d <= N && d * N <= 2048; ++d)
+    if (N % d == 0) b = d;
+  return b;
+}
+
+size_t fft_smem_bytes(int N) { return (2 * (size_t)fft_batch(N) * (N + 1) + N) * sizeof(double2); }
+
+cudaError_t launch_fft_twiddles(double2* tw, int N, cudaStream_t st) {
+  fft_twiddle_kernel<<<(N + 127) / 128, 128, 0, st>>>(tw, N);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fft_axis(double2* data, const FftPlan& pl, cudaStream_t st) {
-  const int threads = pl.N / 2 < 32 ? 32 : (pl.N / 2 > 256 ? 256 : pl.N / 2);
-  fft_lines_kernel<<<(unsigned)((long long)pl.N * pl.N), threads, 2 * pl.N * sizeof(double2), st>>>(data, pl);
+  cudaError_t e = cudaFuncSetAttribute((const void*)fft_lines_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fft_smem_bytes(pl.N));
+  if (e != cudaSuccess) return e;
+  const int work = pl.batch * pl.N / 4;
+  const int threads = work < 64 ? 64 : (work > 512 ? 512 : (work + 31) / 32 * 32);
+  const unsigned grid = (unsigned)((long long)pl.N * pl.N / pl.batch);
+  fft_lines_kernel<<<grid, threads, fft_smem_bytes(pl.N), st>>>(data, pl);
   return cudaGetLastError();
 }
 
