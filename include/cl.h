@@ -17,6 +17,13 @@
  *   - All device memory is owned by the context: allocated by cl_init,
  *     released by cl_free.  Host arrays passed in or out are owned by the
  *     caller and must hold the stated number of elements.
+ *   - The state and gradient transfers (cl_get_state, cl_set_state and their
+ *     cl_lattice_ forms, cl_get_array, cl_set_array, cl_upload_state,
+ *     cl_download_state, cl_adjoint's dJ_dstate, cl_ic_amplitude_grad) also
+ *     take device pointers (any address the CUDA runtime resolves through
+ *     unified addressing, e.g. a torch CUDA tensor's data): the copy then
+ *     stays on the GPU.  It is ordered on params.stream, so whatever writes a
+ *     device input must be ordered before the call on that stream.
  *   - Lattice arrays are N^3 values, row major with x fastest: site
  *     (x, y, z) is element x + N*(y + N*z).
  *   - Field indices: scalar models: 0 .. nf-1 (phi, chi).  U(1) model:

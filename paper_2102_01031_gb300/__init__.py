@@ -347,6 +347,19 @@ class Lattice:
             raise ValueError("need %d values" % self.V)
         _check(self.L, self.h, self.L.cl_set_state(self.h, field, what, _dp(a)), "cl_set_state")
 
+    def get_device(self, field, what, ptr):
+        """cl_get_state into device memory: `ptr` is the address of N^3 doubles on
+        the GPU (e.g. a CUDA tensor's data_ptr()); the copy stays on the device."""
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self.L, self.h, self.L.cl_get_state(self.h, field, what, ctypes.cast(ctypes.c_void_p(ptr), dp)),
+               "cl_get_state")
+
+    def set_device(self, field, what, ptr):
+        """cl_set_state from device memory (N^3 doubles at `ptr`, x fastest)."""
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self.L, self.h, self.L.cl_set_state(self.h, field, what, ctypes.cast(ctypes.c_void_p(ptr), dp)),
+               "cl_set_state")
+
     def save(self, path):
         """cl_checkpoint_save: state and scalars to `path` (written atomically)."""
         _check(self.L, self.h, self.L.cl_checkpoint_save(self.h, os.fsencode(path)), "cl_checkpoint_save")
@@ -471,18 +484,26 @@ class Lattice:
         return ms.value, n.value
 
     def adjoint(self, nsteps, ckpt_every=500, objective=OBJ_CHI_FRACTION, field=1, what=0, dk_bin=1.0,
-                bin=1, scale=False):
+                bin=1, scale=False, lam_ptr=None):
         """cl_adjoint: (J, dJ/dq, lam), lam[f][w] = dJ/d(field f, what w) at the current
         state ([z][y][x] arrays); with scale=True a fourth entry (dJ/da, dJ/db).
+        With lam_ptr (the device address of 2 nf N^3 doubles, e.g. a CUDA tensor's
+        data_ptr()) dJ/d(state) is written there on the GPU and lam is None.
         The state is left unchanged."""
         nf = self.nfields()
-        lam = np.zeros(2 * nf * self.V)
         ab = np.zeros(2)
         J, dq = ctypes.c_double(), ctypes.c_double()
+        if lam_ptr is None:
+            lam = np.zeros(2 * nf * self.V)
+            lp = _dp(lam)
+        else:
+            lam = None
+            lp = ctypes.cast(ctypes.c_void_p(lam_ptr), ctypes.POINTER(ctypes.c_double))
         rc = self.L.cl_adjoint(self.h, nsteps, ckpt_every, objective, field, what, dk_bin, bin,
-                               ctypes.byref(J), ctypes.byref(dq), _dp(lam), _dp(ab))
+                               ctypes.byref(J), ctypes.byref(dq), lp, _dp(ab))
         _check(self.L, self.h, rc, "cl_adjoint")
-        lam = lam.reshape(nf, 2, self.N, self.N, self.N)
+        if lam is not None:
+            lam = lam.reshape(nf, 2, self.N, self.N, self.N)
         if scale:
             return J.value, dq.value, lam, (float(ab[0]), float(ab[1]))
         return J.value, dq.value, lam

@@ -9,9 +9,11 @@ factor and its derivative at the start may be given as ``scale`` = (a, b)
 pass returns dJ/dq, dJ/d(state) and dJ/d(scale), computed at a fixed initial
 (state, a, b) by the library's reversed-pass adjoint kernels (cl_adjoint): the forward and the
 adjoint sweep run together in the forward call, and backward only scales the
-stored gradients by the incoming gradient.  PyTorch supplies the tensors and
-the autograd graph; every step of the evolution and of the adjoint runs in
-the library's kernels.
+stored gradients by the incoming gradient.  The state goes to the library and
+dJ/d(state) comes back in device memory (a state on the GPU never passes
+through the host); the library works on the current torch stream.  PyTorch
+supplies the tensors and the autograd graph; every step of the evolution and
+of the adjoint runs in the library's kernels.
 """
 import dataclasses
 
@@ -53,22 +55,27 @@ class EvolvedObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, q, state, scale, spec):
         kw = dict(spec.params)
-        kw["q"] = float(q.detach().cpu())
-        lat = Lattice(spec.model, spec.N, spec.kIR, spec.alpha, spec.seed, make_params(**kw))
-        host = state.detach().to("cpu", torch.float64).numpy()
-        for f in range(host.shape[0]):
-            for w in (0, 1):
-                lat.set(f, w, host[f, w])
-        if scale is not None:
-            eta0 = lat.scalars()[0]
-            a0, b0 = (float(x) for x in scale.detach().cpu())
-            lat.set_scalars(eta0, a0, b0)
-        J, dq, lam, ab = lat.adjoint(spec.nsteps, spec.ckpt_every, spec.objective, spec.field, spec.what,
-                                     spec.dk_bin, spec.bin, scale=True)
-        lat.close()
-        ctx.save_for_backward(torch.tensor(dq, dtype=torch.float64),
-                              torch.from_numpy(np.ascontiguousarray(lam)),
-                              torch.tensor(ab, dtype=torch.float64))
+        kw["q"] = float(q.detach())
+        dev = state.device if state.is_cuda else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(dev):
+            kw["stream"] = torch.cuda.current_stream(dev).cuda_stream
+            lat = Lattice(spec.model, spec.N, spec.kIR, spec.alpha, spec.seed, make_params(**kw))
+            # the state reaches the library in device memory (a CUDA input is not copied through the host)
+            st = state.detach().to(device=dev, dtype=torch.float64).contiguous()
+            nf = st.shape[0]
+            for f in range(nf):
+                for w in (0, 1):
+                    lat.set_device(f, w, st[f, w].data_ptr())
+            if scale is not None:
+                eta0 = lat.scalars()[0]
+                a0, b0 = (float(x) for x in scale.detach())
+                lat.set_scalars(eta0, a0, b0)
+            lam = torch.empty((nf, 2, spec.N, spec.N, spec.N), dtype=torch.float64, device=dev)
+            J, dq, _, ab = lat.adjoint(spec.nsteps, spec.ckpt_every, spec.objective, spec.field, spec.what,
+                                       spec.dk_bin, spec.bin, scale=True, lam_ptr=lam.data_ptr())
+            lat.close()
+        ctx.save_for_backward(torch.tensor(dq, dtype=torch.float64, device=dev), lam,
+                              torch.tensor(ab, dtype=torch.float64, device=dev))
         ctx.state_meta = (state.dtype, state.device)
         ctx.scale_meta = None if scale is None else (scale.dtype, scale.device)
         return torch.tensor(J, dtype=torch.float64, device=state.device)
@@ -77,12 +84,12 @@ class EvolvedObjective(torch.autograd.Function):
     def backward(ctx, g):
         dq, lam, ab = ctx.saved_tensors
         dtype, device = ctx.state_meta
-        gc = g.detach().cpu()
-        gq = (gc * dq).to(device)
-        gs = (gc * lam).to(device=device, dtype=dtype)
+        gd = g.detach().to(lam.device, torch.float64)
+        gq = (gd * dq).to(device)
+        gs = (gd * lam).to(device=device, dtype=dtype)
         gab = None
         if ctx.scale_meta is not None:
-            gab = (gc * ab).to(device=ctx.scale_meta[1], dtype=ctx.scale_meta[0])
+            gab = (gd * ab).to(device=ctx.scale_meta[1], dtype=ctx.scale_meta[0])
         return gq, gs, gab, None
 
 

@@ -30,7 +30,7 @@ namespace clg {
 // kernels defined in the other translation units
 typedef void (*PassKernel)(const PassArgs);
 PassKernel scalar_pass_kernel(int fp32, int nf, int red);
-PassKernel u1_pass_kernel(int fp32, int red);
+PassKernel u1_pass_kernel(int fp32, int red, int kd);
 PassKernel su2_pass_kernel(int fp32, int red, int TX);
 size_t su2_smem_bytes(int TX, int TY, int esz);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
@@ -281,7 +281,9 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
 
 PassKernel pick_kernel(const cl_ctx* c, int red) {
   if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red, c->su2_tx);
-  if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red);
+  // without expansion the U(1) passes drift right after their kick (the drift
+  // coefficient does not wait for the pass's sums)
+  if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red, c->p.expansion == CL_EXP_OFF);
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
 
@@ -843,6 +845,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   c->smem_bytes = (size_t)S * stage + SM_TAIL_BYTES;
   for (int red = 0; red < 3; ++red) {
     PassKernel k = pick_kernel(c, red);
+    if (!k && red == 1 && red_for_step(c) == 0) continue;  // Friedmann sums never taken here
     if (!k) return fail(c, CL_EUNSUPPORTED, "no pass kernel for this configuration");
     CU(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)c->smem_bytes));
@@ -1227,11 +1230,11 @@ static cl_status copy_array(cl_ctx* c, int a, double* host_out, const double* ho
   if (host_out) {
     CU(launch_convert(c->fp32, 1, arr_ptr(c, 0, c->parity, a), c->d_tmp, V, c->stream));
     ++c->launches;
-    CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDefault, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return check_status(c);
   }
-  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyDefault, c->stream));
   CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, 0, c->parity, a), V, c->stream));
   ++c->launches;
   CU(cudaStreamSynchronize(c->stream));
@@ -1250,7 +1253,7 @@ cl_status cl_lattice_get_state(cl_ctx* c, int lat, int field, int what, double* 
   const long long V = c->lats[lat].V;
   CU(launch_convert(c->fp32, 1, arr_ptr(c, lat, c->parity, a), c->d_tmp, V, c->stream));
   ++c->launches;
-  CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(host_out, c->d_tmp, (size_t)V * sizeof(double), cudaMemcpyDefault, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return check_status(c);
 }
@@ -1264,7 +1267,7 @@ cl_status cl_lattice_set_state(cl_ctx* c, int lat, int field, int what, const do
   s = close_stream(c);
   if (s != CL_OK) return s;
   const long long V = c->lats[lat].V;
-  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_tmp, host_in, (size_t)V * sizeof(double), cudaMemcpyDefault, c->stream));
   CU(launch_convert(c->fp32, 0, c->d_tmp, arr_ptr(c, lat, c->parity, a), V, c->stream));
   ++c->launches;
   CU(cudaStreamSynchronize(c->stream));
@@ -1746,7 +1749,7 @@ cl_status cl_upload_state(cl_ctx* c, const void* host, size_t bytes) {
   if (s != CL_OK) return s;
   const size_t ab = (size_t)V * c->esz;
   for (int a = 0; a < c->narr; ++a)
-    CU(cudaMemcpyAsync(arr_ptr(c, 0, c->parity, a), (const char*)host + a * ab, ab, cudaMemcpyHostToDevice,
+    CU(cudaMemcpyAsync(arr_ptr(c, 0, c->parity, a), (const char*)host + a * ab, ab, cudaMemcpyDefault,
                        c->stream));
   c->obs_valid = false;
   return CL_OK;
@@ -1761,7 +1764,7 @@ cl_status cl_download_state(cl_ctx* c, void* host, size_t bytes) {
   if (s != CL_OK) return s;
   const size_t ab = (size_t)V * c->esz;
   for (int a = 0; a < c->narr; ++a)
-    CU(cudaMemcpyAsync((char*)host + a * ab, arr_ptr(c, 0, c->parity, a), ab, cudaMemcpyDeviceToHost,
+    CU(cudaMemcpyAsync((char*)host + a * ab, arr_ptr(c, 0, c->parity, a), ab, cudaMemcpyDefault,
                        c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return CL_OK;
@@ -2103,7 +2106,7 @@ cl_status cl_adjoint(cl_ctx* c, int nsteps, int ckpt_every, int objective, int f
       const void* src = (char*)c->adj.lam + ((size_t)c->parity * na + a) * ab;
       CU(launch_convert(c->fp32, 1, src, c->d_tmp, H.V, c->stream));
       ++c->launches;
-      CU(cudaMemcpyAsync(dJ_dstate + (size_t)a * H.V, c->d_tmp, H.V * sizeof(double), cudaMemcpyDeviceToHost,
+      CU(cudaMemcpyAsync(dJ_dstate + (size_t)a * H.V, c->d_tmp, H.V * sizeof(double), cudaMemcpyDefault,
                          c->stream));
     }
   }
@@ -2140,7 +2143,7 @@ cl_status cl_ic_amplitude_grad(cl_ctx* c, const double* dJ_dstate, double* out) 
     for (int w = 0; w < 2 && s == CL_OK; ++w) {
       double2* dst = w == 0 ? Lf : Lp;
       if (cudaMemcpyAsync(c->d_tmp, dJ_dstate + (size_t)(2 * f + w) * H.V, H.V * sizeof(double),
-                          cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+                          cudaMemcpyDefault, c->stream) != cudaSuccess ||
           launch_to_complex(0, c->d_tmp, dst, H.V, c->stream) != cudaSuccess) {
         s = fail(c, CL_ECUDA, "amplitude gradient: transfer failed");
         break;
@@ -2152,7 +2155,7 @@ cl_status cl_ic_amplitude_grad(cl_ctx* c, const double* dJ_dstate, double* out) 
     if (launch_ic_amp_grad(Lf, Lp, dev_out, dev_out + H.V, c->d_lat, c->d_sc, H.ic, f, H.V, c->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(out + (size_t)(2 * f) * H.V, dev_out, 2 * (size_t)H.V * sizeof(double),
-                        cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+                        cudaMemcpyDefault, c->stream) != cudaSuccess) {
       s = fail(c, CL_ECUDA, "amplitude gradient: launch failed");
       break;
     }

@@ -58,7 +58,13 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 }  // namespace
 
 // RED: 0 = no sums, 1 = sums for the Friedmann kick, 2 = full measurement.
-template <typename T, int RED>
+// KD: the pass's own drift follows its kick at each site (kick, then drift by
+// the pass's dnext), instead of being deferred to the next pass's reads.  The
+// order of operations on every value is the same; it needs the drift
+// coefficient before the pass's sums are known, so it is taken when a(eta)
+// does not depend on them (no expansion), and saves every neighbour read its
+// momentum load and drift.
+template <typename T, int RED, bool KD>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
   constexpr int VX = U1Vec<T>::n;
   constexpr int NA = 10;
@@ -103,13 +109,23 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const int g0 = R.off[i];
       // coefficients of the segment: FP64 products formed by one lane (the
       // FP64 pipe is narrow) and broadcast in the storage precision
-      T cf[8];
+      T cf[10];
       if (lane == 0) {
         const LatScalars* SC = &P.sc[sg.lat];
         const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
         const double ap1 = __ldcg(&SC->apow1);
-        cf[0] = (T)__ldcg(&SC->cd);
-        cf[1] = (T)__ldcg(&SC->cdA);
+        if constexpr (KD) {
+          // no deferred drift to apply on read; this pass's drift, at the constant a
+          double kd, kdA;
+          drift_coefficients(L, __ldcg(&SC->a), P.steps ? __ldg(&P.steps[pass].dnext) : P.dnext, kd, kdA);
+          cf[0] = cf[1] = T(0);
+          cf[8] = (T)kd;
+          cf[9] = (T)kdA;
+        } else {
+          cf[0] = (T)__ldcg(&SC->cd);
+          cf[1] = (T)__ldcg(&SC->cdA);
+          cf[8] = cf[9] = T(0);
+        }
         cf[2] = (T)(ckp * ap1 * L.inv_dx2);
         cf[3] = (T)(ckp * __ldcg(&SC->apow3));
         cf[4] = (T)(ckp * ap1 * L.u1_cJ);   // (2 gQ/dx) Im[...] = (gQ/dx)(phi_0 u_1 - phi_1 u_0)
@@ -118,9 +134,10 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
         cf[7] = (T)(L.v * L.v);
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
+      for (int k = 0; k < 10; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
       const T cd = cf[0], cdA = cf[1], A1 = cf[2], A3 = cf[3], AJ = cf[4], AC = cf[5], gd = cf[6], v2 = cf[7];
-      const bool drifting = cd != T(0) || cdA != T(0);
+      const T kd = cf[8], kdA = cf[9];  // KD: the drift after the kick
+      const bool drifting = !KD && (cd != T(0) || cdA != T(0));
       const T lam = (T)L.lam;
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;
       // output buffer: array a of a lattice buffer starts a * V elements after array 0
@@ -275,8 +292,19 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
               }
             }
             if (P.write) {
-              stv<T>(out + F0 * Vs, cF[0]);
-              stv<T>(out + F1 * Vs, cF[1]);
+              if constexpr (KD) {
+                T d0[VX], d1[VX];
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                  d0[v] = fmaT(kd, pn0[v], cF[0][v]);
+                  d1[v] = fmaT(kd, pn1[v], cF[1][v]);
+                }
+                stv<T>(out + F0 * Vs, d0);
+                stv<T>(out + F1 * Vs, d1);
+              } else {
+                stv<T>(out + F0 * Vs, cF[0]);
+                stv<T>(out + F1 * Vs, cF[1]);
+              }
               stv<T>(out + P0 * Vs, pn0);
               stv<T>(out + P1 * Vs, pn1);
             }
@@ -340,9 +368,22 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
               }
             }
             if (P.write) {
-              stv<T>(out + AX * Vs, cA[0]);
-              stv<T>(out + AY * Vs, cA[1]);
-              stv<T>(out + AZ * Vs, cA[2]);
+              if constexpr (KD) {
+                T dx_[VX], dy_[VX], dz_[VX];
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                  dx_[v] = fmaT(kdA, pnx[v], cA[0][v]);
+                  dy_[v] = fmaT(kdA, pny[v], cA[1][v]);
+                  dz_[v] = fmaT(kdA, pnz[v], cA[2][v]);
+                }
+                stv<T>(out + AX * Vs, dx_);
+                stv<T>(out + AY * Vs, dy_);
+                stv<T>(out + AZ * Vs, dz_);
+              } else {
+                stv<T>(out + AX * Vs, cA[0]);
+                stv<T>(out + AY * Vs, cA[1]);
+                stv<T>(out + AZ * Vs, cA[2]);
+              }
               stv<T>(out + PAX * Vs, pnx);
               stv<T>(out + PAY * Vs, pny);
               stv<T>(out + PAZ * Vs, pnz);
@@ -472,21 +513,30 @@ timeout:
   __syncthreads();
 }
 
-template __global__ void dk_pass_u1<float, 0>(const PassArgs);
-template __global__ void dk_pass_u1<float, 1>(const PassArgs);
-template __global__ void dk_pass_u1<float, 2>(const PassArgs);
-template __global__ void dk_pass_u1<double, 0>(const PassArgs);
-template __global__ void dk_pass_u1<double, 1>(const PassArgs);
-template __global__ void dk_pass_u1<double, 2>(const PassArgs);
+template __global__ void dk_pass_u1<float, 0, false>(const PassArgs);
+template __global__ void dk_pass_u1<float, 1, false>(const PassArgs);
+template __global__ void dk_pass_u1<float, 2, false>(const PassArgs);
+template __global__ void dk_pass_u1<double, 0, false>(const PassArgs);
+template __global__ void dk_pass_u1<double, 1, false>(const PassArgs);
+template __global__ void dk_pass_u1<double, 2, false>(const PassArgs);
+template __global__ void dk_pass_u1<float, 0, true>(const PassArgs);
+template __global__ void dk_pass_u1<float, 2, true>(const PassArgs);
+template __global__ void dk_pass_u1<double, 0, true>(const PassArgs);
+template __global__ void dk_pass_u1<double, 2, true>(const PassArgs);
 
 typedef void (*PassKernel)(const PassArgs);
 
-PassKernel u1_pass_kernel(int fp32, int red) {
+// kd: kick-then-drift passes (only without expansion, where the Friedmann sums
+// of RED 1 are not needed).
+PassKernel u1_pass_kernel(int fp32, int red, int kd) {
   static const PassKernel tab[2][3] = {
-      {dk_pass_u1<double, 0>, dk_pass_u1<double, 1>, dk_pass_u1<double, 2>},
-      {dk_pass_u1<float, 0>, dk_pass_u1<float, 1>, dk_pass_u1<float, 2>}};
+      {dk_pass_u1<double, 0, false>, dk_pass_u1<double, 1, false>, dk_pass_u1<double, 2, false>},
+      {dk_pass_u1<float, 0, false>, dk_pass_u1<float, 1, false>, dk_pass_u1<float, 2, false>}};
+  static const PassKernel tab_kd[2][3] = {
+      {dk_pass_u1<double, 0, true>, nullptr, dk_pass_u1<double, 2, true>},
+      {dk_pass_u1<float, 0, true>, nullptr, dk_pass_u1<float, 2, true>}};
   if (red < 0 || red > 2) return nullptr;
-  return tab[fp32 ? 1 : 0][red];
+  return kd ? tab_kd[fp32 ? 1 : 0][red] : tab[fp32 ? 1 : 0][red];
 }
 
 }  // namespace clg

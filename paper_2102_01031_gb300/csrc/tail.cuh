@@ -155,6 +155,22 @@ __device__ __forceinline__ double kernel_a_da(const PassArgs& P, const LatConst&
 // Few FP64 operations: alpha's exponents are read once, negative powers are
 // reciprocals of positive ones, and alpha = 1 (the manual's default) is
 // straight-line code.
+// Drift coefficients of a drift dn at the midpoint scale factor abar: fields
+// h abar^{alpha-3}, links h abar^{alpha-1} (Sec. 3.5.2; Sec. 4.3 for the links).
+__device__ inline void drift_coefficients(const LatConst& L, double abar, double dn, double& cd, double& cdA) {
+  const int ia = L.alpha_i;
+  if (L.int_alpha && ia == 1) {
+    cd = dn * (1.0 / (abar * abar));
+    cdA = dn;
+  } else if (L.int_alpha) {
+    cd = dn * ipow(abar, ia - 3);
+    cdA = dn * ipow(abar, ia - 1);
+  } else {
+    cd = dn * pow_out_of_line(abar, L.alpha - 3.0);
+    cdA = dn * pow_out_of_line(abar, L.alpha - 1.0);
+  }
+}
+
 template <class SS>
 __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S) {
   const double a = S.a, dn = P.dnext;
@@ -172,22 +188,17 @@ __device__ inline void advance_drift(const PassArgs& P, const LatConst& L, SS& S
   S.eta += dn;
   if (L.expansion == CL_EXP_FIXED) S.b = an * H_fixed(L, S, S.eta);
   const int ia = L.alpha_i;
+  drift_coefficients(L, abar, dn, S.cd, S.cdA);
   if (L.int_alpha && ia == 1) {
     const double an2 = an * an;
-    S.cd = dn * (1.0 / (abar * abar));
-    S.cdA = dn;
     S.apow1 = an2;
     S.apow3 = an2 * an2;
     S.apowm1 = 1.0;
   } else if (L.int_alpha) {
-    S.cd = dn * ipow(abar, ia - 3);
-    S.cdA = dn * ipow(abar, ia - 1);
     S.apow1 = ipow(an, ia + 1);
     S.apow3 = S.apow1 * (an * an);
     S.apowm1 = ipow(an, ia - 1);
   } else {
-    S.cd = dn * pow_out_of_line(abar, L.alpha - 3.0);
-    S.cdA = dn * pow_out_of_line(abar, L.alpha - 1.0);
     S.apow1 = pow_out_of_line(an, L.alpha + 1.0);
     S.apow3 = S.apow1 * (an * an);
     S.apowm1 = pow_out_of_line(an, L.alpha - 1.0);

@@ -139,6 +139,34 @@ def test_autograd_function(P):
     assert np.abs(st.grad.numpy() - 3.0 * lam0).max() <= 1e-12 * np.abs(3.0 * lam0).max()
 
 
+def test_autograd_function_device_state(P, monkeypatch):
+    """A state held in CUDA tensors goes to the library and its gradient comes
+    back without passing through the host: the host transfers are switched off
+    for the call, and the result equals the host-array adjoint's."""
+    torch = pytest.importorskip("torch")
+    from paper_2102_01031_gb300.autograd import RunSpec, evolved_objective
+    N = 16
+    kw = dict(SELF)
+    g = P.Lattice(O.MODEL_LPHI4_CHI, N, 0.5, 1.0, 6, P.make_params(**kw))
+    s = np.stack([np.stack([g.get(f, w) for w in (0, 1)]) for f in range(2)])
+    J0, dq0, lam0, ab0 = g.adjoint(20, 10, scale=True)
+    spec = RunSpec.make(O.MODEL_LPHI4_CHI, N, 0.5, 1.0, 6, 20, ckpt_every=10, **kw)
+    q = torch.tensor(kw["q"], dtype=torch.float64, device="cuda", requires_grad=True)
+    st = torch.tensor(s, dtype=torch.float64, device="cuda", requires_grad=True)
+
+    def no_host(*a, **k):
+        raise AssertionError("host transfer of the state")
+    monkeypatch.setattr(P.Lattice, "set", no_host)
+    monkeypatch.setattr(P.Lattice, "get", no_host)
+    J = evolved_objective(q, st, spec)
+    (0.5 * J).backward()
+    monkeypatch.undo()
+    assert J.device.type == "cuda" and st.grad.device.type == "cuda"
+    assert abs(float(J.detach()) - J0) < 1e-14 * J0
+    assert abs(float(q.grad) - 0.5 * dq0) < 1e-12 * abs(0.5 * dq0)
+    assert np.abs(st.grad.cpu().numpy() - 0.5 * lam0).max() <= 1e-12 * np.abs(0.5 * lam0).max()
+
+
 def test_autograd_function_scale(P):
     """Self-consistent expansion: (a, b) at the start as a differentiable input."""
     torch = pytest.importorskip("torch")
