@@ -661,6 +661,12 @@ def profile_case(name):
         lat = P.Lattice(P.MODEL_U1_HIGGS, 128, 0.2, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
         for _ in range(4):
             lat.step(1)
+    elif name == "u1_256":    # single-pass launches of the leapfrog U(1) pass at the benchmark size
+        u1 = dict(dt=0.01, integrator=P.LF, lam=1.0, v=1.0, gQ=0.5, fstar_over_omegastar=1.0,
+                  phi0=[1.0, 1.0], fluct_amp2=1e-2, expansion=P.EXP_OFF, fstar_over_mp=0.5)
+        lat = P.Lattice(P.MODEL_U1_HIGGS, 256, 0.1, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream, **u1))
+        for _ in range(4):
+            lat.step(1)
     elif name == "su2_128":   # single-pass launches of the leapfrog SU(2) x U(1) doublet pass
         lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 128, 0.2, ALPHA, SEED,
                         P.make_params(precision=P.FP32, stream=stream, **su2_params(P)))
@@ -704,8 +710,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="reference arm: site-steps budget / 1e6 that sizes its oracle box")
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "su2_128", "adj128", "adj128self",
-                             "spectrum256"),
+    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "adj128",
+                             "adj128self", "spectrum256"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

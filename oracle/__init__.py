@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS = 1, 2, 3, 4
+MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS, MODEL_LPHI4_SU2U1 = 1, 2, 3, 4, 5
 LF, VV2, VV4, VV6, VV8, VV10 = 0, 2, 4, 6, 8, 10
 EXP_OFF, EXP_SELF, EXP_FIXED = 0, 1, 2
 
@@ -47,6 +47,9 @@ class Params(ctypes.Structure):
         ("b0_mode", ctypes.c_int),
         ("pad_", ctypes.c_int),
         ("gQB", ctypes.c_double),
+        ("qG", ctypes.c_double),
+        ("qH", ctypes.c_double),
+        ("Qc", ctypes.c_double),
     ]
 
 
@@ -127,6 +130,7 @@ def lib():
             L.clo_philox4x32_10.restype = None
             L.clo_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
             L.clo_u01.restype = ctypes.c_double
+            L.clo_kernel.argtypes = [c_p, ctypes.c_int, dp]
             L.clo_gauss_modes.argtypes = [c_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
             L.clo_draw_pairs.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
@@ -173,6 +177,9 @@ def make_params(**kw):
     p.expansion = kw.pop("expansion", EXP_OFF)
     p.b0_mode = kw.pop("b0_mode", 0)
     p.gQB = kw.pop("gQB", 0.5)
+    p.qG = kw.pop("qG", 0.0)
+    p.qH = kw.pop("qH", 0.0)
+    p.Qc = kw.pop("Qc", 1.0)
     if kw:
         raise TypeError("unknown params: %s" % sorted(kw))
     return p
@@ -209,6 +216,13 @@ class Oracle:
         e = Energies()
         self.L.clo_energies(self.h, ctypes.byref(e))
         return e.as_dict()
+
+    def kernel(self, a):
+        """Doublet models: the kernel K (pi' = K) of momentum array a, [z][y][x]."""
+        out = np.empty(self.V, dtype=np.float64)
+        if self.L.clo_kernel(self.h, a, _dp(out)) != 0:
+            raise IndexError(a)
+        return out.reshape(self.N, self.N, self.N)
 
     def gauss_modes(self, idx):
         """U(1) model: Fourier values (unnormalised forward transform) of the
@@ -430,7 +444,7 @@ def dft3d_naive(x, sign):
 def ic_sample(model, N, kIR, alpha, seed, params, idx):
     """Initial Fourier values (F, G) per field at the given linear site indices."""
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
-    nf = 1 if model == MODEL_LPHI4 else (4 if model == MODEL_SU2U1_HIGGS else 2)
+    nf = {MODEL_LPHI4: 1, MODEL_SU2U1_HIGGS: 4, MODEL_LPHI4_SU2U1: 7}.get(model, 2)
     out = np.zeros(idx.size * nf * 4)
     rc = lib().clo_ic_sample(model, N, kIR, alpha, seed, ctypes.byref(params), idx.size,
                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))

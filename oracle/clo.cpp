@@ -136,8 +136,11 @@ struct clo_ctx {
   std::vector<double> phi[4], pi[4];
   std::vector<double> A[3], piA[3];
   std::vector<double> U[3][4], piB[3][3];  // SU(2) links (u0..u3) and momenta (doublet model)
-  bool gauge() const { return model == CLO_MODEL_U1_HIGGS || model == CLO_MODEL_SU2U1_HIGGS; }
-  bool su2() const { return model == CLO_MODEL_SU2U1_HIGGS; }
+  std::vector<double> sph, spi;            // lphi4SU2U1: the singlet and its momentum
+  std::vector<double> cph[2], cpi[2];      // lphi4SU2U1: the U(1)-charged scalar's components
+  bool gauge() const { return model >= CLO_MODEL_U1_HIGGS; }
+  bool su2() const { return model == CLO_MODEL_SU2U1_HIGGS || model == CLO_MODEL_LPHI4_SU2U1; }
+  bool full() const { return model == CLO_MODEL_LPHI4_SU2U1; }
   long at(long x, long y, long z) const {
     x %= N; if (x < 0) x += N;
     y %= N; if (y < 0) y += N;
@@ -157,7 +160,9 @@ struct clo_ctx {
 
 namespace {
 
-int n_pot_terms(int model) { return model == CLO_MODEL_LPHI4_CHI ? 2 : 1; }
+int n_pot_terms(int model) {
+  return model == CLO_MODEL_LPHI4_CHI ? 2 : (model == CLO_MODEL_LPHI4_SU2U1 ? 3 : 1);
+}
 
 // Program potential V~ term by term.  lphi4: phi^4/4 (eq. PotNat with chi = 0);
 // lphi4 + chi: phi^4/4 + (q/2) phi^2 chi^2 (eq. PotNat, q = g^2/lambda);
@@ -195,6 +200,56 @@ void pot_deriv(const clo_ctx* c, const double* f, double* d) {
     for (int k = 0; k < c->nf; ++k) d[k] = g * f[k];
   }
 }
+
+// lphi4SU2U1 (Sec. 4.5, eq. PotGauge in program units, with the doublet's
+// quartic written lam (|Phi|^2 - v^2)^2 as in the doublet model; the manual's
+// example is lam = 1, v = 0):
+//   V = lam (|Phi|^2 - v^2)^2 + q_G |Phi|^2 phi_s^2 + 2 q_H |Phi|^2 |vphi|^2,
+// site values f[0..3] = doublet components, f[4] = phi_s, f[5], f[6] = vphi_c;
+// |Phi|^2 = sum_k f_k^2/2 (k < 4), |vphi|^2 = (f_5^2 + f_6^2)/2.
+void full_pot(const clo_ctx* c, const double* f, double* t) {
+  double P2 = 0.0;
+  for (int k = 0; k < 4; ++k) P2 += 0.5 * f[k] * f[k];
+  const double C2 = 0.5 * (f[5] * f[5] + f[6] * f[6]);
+  const double d = P2 - c->p.v * c->p.v;
+  t[0] = c->p.lam * d * d;
+  t[1] = c->p.qG * P2 * f[4] * f[4];
+  t[2] = 2.0 * c->p.qH * P2 * C2;
+}
+// dV/df_k of each real component (the doublet's and vphi's components carry
+// the canonical kinetic term of a real field, as in the doublet model).
+void full_force(const clo_ctx* c, const double* f, double* d) {
+  double P2 = 0.0;
+  for (int k = 0; k < 4; ++k) P2 += 0.5 * f[k] * f[k];
+  const double C2 = 0.5 * (f[5] * f[5] + f[6] * f[6]);
+  const double g = 2.0 * c->p.lam * (P2 - c->p.v * c->p.v) + c->p.qG * f[4] * f[4] + 2.0 * c->p.qH * C2;
+  for (int k = 0; k < 4; ++k) d[k] = g * f[k];
+  d[4] = 2.0 * c->p.qG * P2 * f[4];
+  d[5] = 2.0 * c->p.qH * P2 * f[5];
+  d[6] = 2.0 * c->p.qH * P2 * f[6];
+}
+// d^2V/df_k^2 (the initial effective masses of eq. QuantumFlucts2).
+double full_mass2(const clo_ctx* c, const double* f, int k) {
+  double P2 = 0.0;
+  for (int m = 0; m < 4; ++m) P2 += 0.5 * f[m] * f[m];
+  const double C2 = 0.5 * (f[5] * f[5] + f[6] * f[6]);
+  if (k < 4)
+    return 2.0 * c->p.lam * (P2 - c->p.v * c->p.v) + 2.0 * c->p.lam * f[k] * f[k] + c->p.qG * f[4] * f[4] +
+           2.0 * c->p.qH * C2;
+  if (k == 4) return 2.0 * c->p.qG * P2;
+  return 2.0 * c->p.qH * P2;
+}
+// The seven site values of the full model at site n.
+void full_site(const clo_ctx* c, long n, double* f) {
+  for (int k = 0; k < 4; ++k) f[k] = c->phi[k][n];
+  f[4] = c->sph[n];
+  f[5] = c->cph[0][n];
+  f[6] = c->cph[1][n];
+}
+
+// Real scalar components that get initial fluctuations: the full model adds
+// the singlet (component 4) and the charged scalar's two (5, 6) to the doublet's.
+int ncomp(const clo_ctx* c) { return c->full() ? 7 : c->nf; }
 
 // Effective mass squared d^2V/dphi_f^2 at the homogeneous values (eq. QuantumFlucts2).
 double mass2(const clo_ctx* c, const double* f, int k) {
@@ -470,9 +525,14 @@ void kernel_su2(const clo_ctx* c, std::vector<double>* Kphi, std::vector<double>
   const double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
   const double gQ = c->p.gQ, gB = c->p.gQB, dx = c->dx;
   for (long n = 0; n < c->V; ++n) {
-    double f[4], d[4];
-    for (int k = 0; k < 4; ++k) f[k] = c->phi[k][n];
-    pot_deriv(c, f, d);
+    double f[7], d[7];
+    if (c->full()) {
+      full_site(c, n, f);
+      full_force(c, f, d);
+    } else {
+      for (int k = 0; k < 4; ++k) f[k] = c->phi[k][n];
+      pot_deriv(c, f, d);
+    }
     const D2 psi = doublet(c, n);
     D2 D;
     D.v[0] = D.v[1] = cplx(0.0, 0.0);
@@ -502,6 +562,59 @@ void kernel_su2(const clo_ctx* c, std::vector<double>* Kphi, std::vector<double>
   }
 }
 
+// lphi4SU2U1: kernels of the singlet and of the U(1)-charged scalar, and the
+// charged scalar's share of the U(1) current (Sec. 4.3 Hamiltonian form):
+//   K_s     = a^{1+alpha} Lap phi_s - a^{3+alpha} dV/dphi_s,
+//   K_vphi  = a^{1+alpha} (D^2 vphi)_c/dx^2 - a^{3+alpha} dV/dvphi_c,
+//             D^2 vphi = sum_i [Vc_i vphi(n+i) - 2 vphi + Vc_i^*(n-i) vphi(n-i)],
+//             Vc_i = exp(-i Qc gQ dx A_i) (the charge Qc gQ = g_A Q_A^(vphi)),
+//   K_{A_i} += a^{1+alpha} (f*/omega*)^2 Qc (gQ/dx) (vphi_0 u_1 - vphi_1 u_0),
+//             u = Vc_i vphi(n+i) in components, as the U(1) model's current.
+// reading: the doublet's charge is the unit of U(1) charge (gQ = g_A Q_A^(Phi)
+// also scales the plaquette, as in the doublet model), and Qc is the charged
+// scalar's charge in that unit.
+void vphi_fwd(const clo_ctx* c, long n, int i, double& w0, double& w1) {
+  const long m = c->shift(n, i, +1);
+  const double th = c->p.Qc * c->p.gQ * c->dx * c->A[i][n];
+  const double co = std::cos(th), si = std::sin(th);
+  const double x = c->cph[0][m], y = c->cph[1][m];
+  w0 = co * x + si * y;
+  w1 = co * y - si * x;
+}
+void vphi_bwd(const clo_ctx* c, long n, int i, double& w0, double& w1) {
+  const long m = c->shift(n, i, -1);
+  const double th = c->p.Qc * c->p.gQ * c->dx * c->A[i][m];
+  const double co = std::cos(th), si = std::sin(th);
+  const double x = c->cph[0][m], y = c->cph[1][m];
+  w0 = co * x - si * y;
+  w1 = co * y + si * x;
+}
+void kernel_full_extra(const clo_ctx* c, std::vector<double>& Ks, std::vector<double>* Kc,
+                       std::vector<double>* KA) {
+  const double a1 = std::pow(c->a, 1.0 + c->alpha), a3 = std::pow(c->a, 3.0 + c->alpha);
+  const double idx2 = 1.0 / (c->dx * c->dx);
+  const double fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
+  const double gQc = c->p.Qc * c->p.gQ, dx = c->dx;
+  for (long n = 0; n < c->V; ++n) {
+    double f[7], d[7];
+    full_site(c, n, f);
+    full_force(c, f, d);
+    double Ls = 0.0, D0 = 0.0, D1 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      Ls += c->sph[c->shift(n, i, +1)] + c->sph[c->shift(n, i, -1)] - 2.0 * f[4];
+      double u0, u1, w0, w1;
+      vphi_fwd(c, n, i, u0, u1);
+      vphi_bwd(c, n, i, w0, w1);
+      D0 += u0 + w0 - 2.0 * f[5];
+      D1 += u1 + w1 - 2.0 * f[6];
+      KA[i][n] += a1 * fo2 * (gQc / dx) * (f[5] * u1 - f[6] * u0);
+    }
+    Ks[n] = a1 * Ls * idx2 - a3 * d[4];
+    Kc[0][n] = a1 * D0 * idx2 - a3 * d[5];
+    Kc[1][n] = a1 * D1 * idx2 - a3 * d[6];
+  }
+}
+
 // U_i(n) <- exp(-i gQB dx w_B pi_B,i^a T_a) U_i(n)   (w_B = step abar^{alpha-1})
 void drift_su2_links(clo_ctx* c, double wB) {
   const double e = c->p.gQB * c->dx * wB;
@@ -528,6 +641,8 @@ void gauss_su2_site(const clo_ctx* c, long n, int g, double& lhs, double& rhs) {
   if (g == 0) {
     for (int i = 0; i < 3; ++i) lhs += (c->piA[i][n] - c->piA[i][c->shift(n, i, -1)]) / c->dx;
     rhs = fo2 * c->p.gQ * dot(psi, mom).imag();
+    if (c->full())  // the charged scalar's charge density, U(1) model form with charge Qc
+      rhs += fo2 * c->p.Qc * c->p.gQ * (c->cph[0][n] * c->cpi[1][n] - c->cph[1][n] * c->cpi[0][n]);
     return;
   }
   for (int i = 0; i < 3; ++i) {
@@ -559,8 +674,9 @@ void averages(const clo_ctx* c, Avg& r) {
   std::memset(&r, 0, sizeof(r));
   double sp2[4] = {0, 0, 0, 0}, sg[2] = {0, 0}, sv[4] = {0, 0, 0, 0};
   double spA = 0.0, smag = 0.0, spB = 0.0, smagB = 0.0;
+  double spS = 0.0, spC = 0.0, sgS = 0.0, sgC = 0.0;  // lphi4SU2U1: singlet and charged scalar
   for (long n = 0; n < c->V; ++n) {
-    double f[4] = {0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
+    double f[7] = {0, 0, 0, 0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
     for (int k = 0; k < c->nf; ++k) {
       f[k] = c->phi[k][n];
       double pv = c->pi[k][n];
@@ -570,7 +686,21 @@ void averages(const clo_ctx* c, Avg& r) {
       r.mpi[k] += pv;
       r.mpi2[k] += pv * pv;
     }
-    pot_terms(c, f, t);
+    if (c->full()) {
+      full_site(c, n, f);
+      full_pot(c, f, t);
+      spS += c->spi[n] * c->spi[n];
+      spC += c->cpi[0][n] * c->cpi[0][n] + c->cpi[1][n] * c->cpi[1][n];
+      for (int i = 0; i < 3; ++i) {
+        const double g = c->sph[c->shift(n, i, +1)] - f[4];
+        sgS += g * g;
+        double u0, u1;
+        vphi_fwd(c, n, i, u0, u1);
+        sgC += (u0 - f[5]) * (u0 - f[5]) + (u1 - f[6]) * (u1 - f[6]);
+      }
+    } else {
+      pot_terms(c, f, t);
+    }
     for (int m = 0; m < n_pot_terms(c->model); ++m) sv[m] += t[m];
     if (!c->gauge()) {
       for (int k = 0; k < c->nf; ++k)
@@ -610,6 +740,12 @@ void averages(const clo_ctx* c, Avg& r) {
   } else {
     r.EK[0] = (sp2[0] + sp2[1] + sp2[2] + sp2[3]) / (2.0 * a6 * V);
     r.EG[0] = sg[0] / (2.0 * a2 * c->dx * c->dx * V);
+    if (c->full()) {  // E_K, E_G of the singlet [1] and of the charged scalar [2]
+      r.EK[1] = spS / (2.0 * a6 * V);
+      r.EK[2] = spC / (2.0 * a6 * V);
+      r.EG[1] = sgS / (2.0 * a2 * c->dx * c->dx * V);
+      r.EG[2] = sgC / (2.0 * a2 * c->dx * c->dx * V);
+    }
     double of2 = 1.0 / (c->p.fstar_over_omegastar * c->p.fstar_over_omegastar);
     double gdx2 = c->p.gQ * c->dx * c->dx;
     r.EKA = of2 * spA / (2.0 * a4 * V);
@@ -682,6 +818,14 @@ void kick_fields(clo_ctx* c, double w) {
       for (int a = 0; a < 3; ++a) KB[i][a].assign(c->V, 0.0);
     }
     kernel_su2(c, Kp, KA, KB);
+    if (c->full()) {
+      std::vector<double> Ks(c->V, 0.0), Kc[2];
+      for (int k = 0; k < 2; ++k) Kc[k].assign(c->V, 0.0);
+      kernel_full_extra(c, Ks, Kc, KA);
+      for (long n = 0; n < c->V; ++n) c->spi[n] += w * Ks[n];
+      for (int k = 0; k < 2; ++k)
+        for (long n = 0; n < c->V; ++n) c->cpi[k][n] += w * Kc[k][n];
+    }
     for (int k = 0; k < 4; ++k)
       for (long n = 0; n < c->V; ++n) c->pi[k][n] += w * Kp[k][n];
     for (int i = 0; i < 3; ++i) {
@@ -712,6 +856,11 @@ void drift(clo_ctx* c, double w) {
   double cphi = w * std::pow(abar, c->alpha - 3.0);
   for (int k = 0; k < c->nf; ++k)
     for (long n = 0; n < c->V; ++n) c->phi[k][n] += cphi * c->pi[k][n];
+  if (c->full()) {
+    for (long n = 0; n < c->V; ++n) c->sph[n] += cphi * c->spi[n];
+    for (int k = 0; k < 2; ++k)
+      for (long n = 0; n < c->V; ++n) c->cph[k][n] += cphi * c->cpi[k][n];
+  }
   if (c->gauge()) {
     double cA = w * std::pow(abar, c->alpha - 1.0);
     for (int i = 0; i < 3; ++i)
@@ -789,8 +938,11 @@ bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, d
   double k = mode_k(c, idx);
   if (c->p.kcut >= 0.0 && k > c->p.kcut) return false;
   if (amp2 <= 0.0) return false;
-  for (int f = 0; f < c->nf; ++f) {
-    double w2 = k * k + a * a * mass2(c, c->p.phi0, f);
+  const int nc = ncomp(c);
+  double h7[7] = {0, 0, 0, 0, 0, 0, 0};  // homogeneous values (the full model's extra fields start at 0)
+  for (int f = 0; f < c->nf; ++f) h7[f] = c->p.phi0[f];
+  for (int f = 0; f < nc; ++f) {
+    double w2 = k * k + a * a * (c->full() ? full_mass2(c, h7, f) : mass2(c, c->p.phi0, f));
     if (w2 <= 0.0) return false;
     om[f] = std::sqrt(w2);
   }
@@ -803,28 +955,42 @@ bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, d
       z1[f] = std::polar(std::sqrt(-P * std::log(u[0])), 2.0 * PI * v[0]);
       z2[f] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
     }
-  } else {
-    // eqs. InConstr:1-2 for the components n of the charged field:
-    // |d_{n1}| = |d_{n2}|, theta_{n2} = theta_02 + theta_{n1} - theta_01
+    return true;
+  }
+  // eqs. InConstr:1-2 for the components n of each charged field (components
+  // f0 .. f0 + m - 1, f0 its reference): |d_{n1}| = |d_{n2}|,
+  // theta_{n2} = theta_{f0,2} + theta_{n1} - theta_{f0,1}
+  auto charged = [&](int f0, int m) {
     double u0[2], v0[2];
-    draw4(seed, idx, 0, 0, u0);
-    draw4(seed, idx, 0, 1, v0);
+    draw4(seed, idx, f0, 0, u0);
+    draw4(seed, idx, f0, 1, v0);
     double t01 = 2.0 * PI * v0[0], t02 = 2.0 * PI * v0[1];
-    for (int f = 0; f < c->nf; ++f) {
+    for (int f = f0; f < f0 + m; ++f) {
       double P = amp2 * vol / (2.0 * a * a * om[f]);
       double u[2], v[2];
-      if (f == 0) {
+      if (f == f0) {
         u[0] = u0[0]; u[1] = u0[1]; v[0] = v0[0]; v[1] = v0[1];
       } else {
         draw4(seed, idx, f, 0, u);
         draw4(seed, idx, f, 1, v);
       }
       double r = std::sqrt(-P * std::log(u[0]));
-      double t1 = f == 0 ? t01 : 2.0 * PI * v[0];
-      double t2 = f == 0 ? t02 : t02 + t1 - t01;
+      double t1 = f == f0 ? t01 : 2.0 * PI * v[0];
+      double t2 = f == f0 ? t02 : t02 + t1 - t01;
       z1[f] = std::polar(r, t1);
       z2[f] = std::polar(r, t2);
     }
+  };
+  charged(0, c->nf);
+  if (c->full()) {
+    // the singlet (component 4): independent amplitudes and phases as a scalar singlet
+    double P = amp2 * vol / (2.0 * a * a * om[4]);
+    double u[2], v[2];
+    draw4(seed, idx, 4, 0, u);
+    draw4(seed, idx, 4, 1, v);
+    z1[4] = std::polar(std::sqrt(-P * std::log(u[0])), 2.0 * PI * v[0]);
+    z2[4] = std::polar(std::sqrt(-P * std::log(u[1])), 2.0 * PI * v[1]);
+    charged(5, 2);  // the U(1)-charged scalar
   }
   return true;
 }
@@ -834,11 +1000,11 @@ bool mode_draws(const clo_ctx* c, uint64_t seed, long idx, cplx* z1, cplx* z2, d
 // stay zero.
 bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, cplx* G) {
   const double isq2 = 1.0 / std::sqrt(2.0);
-  cplx z1[4], z2[4];
-  double om[4];
+  cplx z1[8], z2[8];
+  double om[8];
   if (!mode_draws(c, seed, idx, z1, z2, om)) return false;
   bool selfc = partner_index(c, idx) == idx;
-  for (int f = 0; f < c->nf; ++f) {
+  for (int f = 0; f < ncomp(c); ++f) {
     cplx df = (z1[f] + z2[f]) * isq2;
     cplx dv = std::pow(c->a, c->alpha - 1.0) * cplx(0.0, om[f]) * (z1[f] - z2[f]) * isq2 - H * df;
     if (selfc) { df = cplx(df.real(), 0.0); dv = cplx(dv.real(), 0.0); }
@@ -851,16 +1017,16 @@ bool mode_values(const clo_ctx* c, uint64_t seed, double H, long idx, cplx* F, c
 // Fourier modes of the field fluctuation (F) and of its time derivative (G).
 void fluct_modes(const clo_ctx* c, uint64_t seed, double H, std::vector<cplx>* F,
                  std::vector<cplx>* G) {
-  for (int k = 0; k < c->nf; ++k) {
+  for (int k = 0; k < ncomp(c); ++k) {
     F[k].assign(c->V, cplx(0, 0));
     G[k].assign(c->V, cplx(0, 0));
   }
   for (long idx = 1; idx < c->V; ++idx) {
     long pid = partner_index(c, idx);
     if (pid < idx) continue;
-    cplx f[4], g[4];
+    cplx f[8], g[8];
     if (!mode_values(c, seed, H, idx, f, g)) continue;
-    for (int k = 0; k < c->nf; ++k) {
+    for (int k = 0; k < ncomp(c); ++k) {
       F[k][idx] = f[k]; G[k][idx] = g[k];
       F[k][pid] = std::conj(f[k]); G[k][pid] = std::conj(g[k]);
     }
@@ -940,13 +1106,14 @@ void gauss_momenta(clo_ctx* c) {
 }
 
 double homogeneous_rho(const clo_ctx* c) {
-  double f[4] = {0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
+  double f[7] = {0, 0, 0, 0, 0, 0, 0}, t[4] = {0, 0, 0, 0};
   double kin = 0.0;
   for (int k = 0; k < c->nf; ++k) {
     f[k] = c->p.phi0[k];
     kin += 0.5 * c->p.dphi0[k] * c->p.dphi0[k];
   }
-  pot_terms(c, f, t);
+  if (c->full()) full_pot(c, f, t);  // singlet and charged scalar start at 0
+  else pot_terms(c, f, t);
   return kin / std::pow(c->a, 2.0 * c->alpha) + sum4(t);
 }
 
@@ -1009,14 +1176,14 @@ int clo_schedule(int integrator, double h, double* drifts, int cap) {
 int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t seed,
              const clo_params* p) {
   if (!out || !p) return -1;
-  if (model < CLO_MODEL_LPHI4 || model > CLO_MODEL_SU2U1_HIGGS) return -1;
+  if (model < CLO_MODEL_LPHI4 || model > CLO_MODEL_LPHI4_SU2U1) return -1;
   if (N < 2 || kIR <= 0.0) return -1;
-  if (model == CLO_MODEL_SU2U1_HIGGS && !(p->gQB != 0.0)) return -1;
+  if (model >= CLO_MODEL_SU2U1_HIGGS && !(p->gQB != 0.0)) return -1;
   clo_ctx* c = new clo_ctx();
   c->model = model;
   c->N = N;
   c->V = (long)N * N * N;
-  c->nf = model == CLO_MODEL_LPHI4 ? 1 : (model == CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
+  c->nf = model == CLO_MODEL_LPHI4 ? 1 : (model >= CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
   c->kIR = kIR;
   c->dx = 2.0 * PI / ((double)N * kIR);
   c->alpha = alpha;
@@ -1037,6 +1204,14 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
       for (int k = 0; k < 4; ++k) c->U[i][k].assign(c->V, k == 0 ? 1.0 : 0.0);
       for (int a = 0; a < 3; ++a) c->piB[i][a].assign(c->V, 0.0);
     }
+  if (c->full()) {  // reading: the singlet and the charged scalar start with zero homogeneous values
+    c->sph.assign(c->V, 0.0);
+    c->spi.assign(c->V, 0.0);
+    for (int k = 0; k < 2; ++k) {
+      c->cph[k].assign(c->V, 0.0);
+      c->cpi[k].assign(c->V, 0.0);
+    }
+  }
   // initial a' (Sec. 5.2 ScaleFactorInitializer: from homogeneous values)
   double rho_h = homogeneous_rho(c);
   if (p->expansion == CLO_EXP_SELF) {
@@ -1052,7 +1227,7 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
   c->H_ic = H;
   double a3ma = std::pow(c->a, 3.0 - alpha);
   if (p->fluct_amp2 > 0.0) {
-    std::vector<cplx> F[4], G[4];
+    std::vector<cplx> F[8], G[8];
     fluct_modes(c, seed, H, F, G);
     for (int k = 0; k < c->nf; ++k) {
       fft3d(F[k], N, +1);
@@ -1060,6 +1235,16 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
       for (long n = 0; n < c->V; ++n) {
         c->phi[k][n] = p->phi0[k] + F[k][n].real() / (double)c->V;
         c->pi[k][n] = a3ma * (p->dphi0[k] + G[k][n].real() / (double)c->V);
+      }
+    }
+    for (int k = 4; k < ncomp(c); ++k) {  // full model: singlet (4), charged scalar (5, 6)
+      fft3d(F[k], N, +1);
+      fft3d(G[k], N, +1);
+      std::vector<double>& fk = k == 4 ? c->sph : c->cph[k - 5];
+      std::vector<double>& pk = k == 4 ? c->spi : c->cpi[k - 5];
+      for (long n = 0; n < c->V; ++n) {
+        fk[n] = F[k][n].real() / (double)c->V;
+        pk[n] = a3ma * (G[k][n].real() / (double)c->V);
       }
     }
   } else {  // no fluctuations: every Fourier mode but the homogeneous one is zero
@@ -1083,12 +1268,12 @@ int clo_init(clo_ctx** out, int model, int N, double kIR, double alpha, uint64_t
 // of field f at site idx[i] (same conventions as clo_init).
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out) {
-  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_SU2U1_HIGGS) return -1;
+  if (!p || !idx || !out || model < CLO_MODEL_LPHI4 || model > CLO_MODEL_LPHI4_SU2U1) return -1;
   clo_ctx c;
   c.model = model;
   c.N = N;
   c.V = (long)N * N * N;
-  c.nf = model == CLO_MODEL_LPHI4 ? 1 : (model == CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
+  c.nf = model == CLO_MODEL_LPHI4 ? 1 : (model >= CLO_MODEL_SU2U1_HIGGS ? 4 : 2);
   c.kIR = kIR;
   c.dx = 2.0 * PI / ((double)N * kIR);
   c.alpha = alpha;
@@ -1103,14 +1288,15 @@ int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, con
     long id = (long)idx[i];
     if (id < 0 || id >= c.V) return -1;
     long pid = partner_index(&c, id);
-    cplx f[4] = {0, 0, 0, 0}, g[4] = {0, 0, 0, 0};
+    cplx f[8], g[8];
     bool conj = pid < id;
     if (!mode_values(&c, seed, c.b / c.a, conj ? pid : id, f, g)) {
-      for (int k = 0; k < 4; ++k) f[k] = g[k] = cplx(0, 0);
+      for (int k = 0; k < 8; ++k) f[k] = g[k] = cplx(0, 0);
     }
-    for (int k = 0; k < c.nf; ++k) {
+    const int nc = ncomp(&c);
+    for (int k = 0; k < nc; ++k) {
       cplx F = conj ? std::conj(f[k]) : f[k], G = conj ? std::conj(g[k]) : g[k];
-      double* o = out + ((size_t)i * c.nf + k) * 4;
+      double* o = out + ((size_t)i * nc + k) * 4;
       o[0] = F.real(); o[1] = F.imag(); o[2] = G.real(); o[3] = G.imag();
     }
   }
@@ -1165,6 +1351,8 @@ static std::vector<double>* field_ptr(const clo_ctx* c, int field, int what) {
   if (field >= 0 && field < c->nf) return what == 0 ? &m->phi[field] : &m->pi[field];
   if (c->gauge() && field >= c->nf && field < c->nf + 3)
     return what == 0 ? &m->A[field - c->nf] : &m->piA[field - c->nf];
+  if (c->full() && field == 7) return what == 0 ? &m->sph : &m->spi;
+  if (c->full() && (field == 8 || field == 9)) return what == 0 ? &m->cph[field - 8] : &m->cpi[field - 8];
   return nullptr;
 }
 
@@ -1198,11 +1386,16 @@ int clo_set_scalars(clo_ctx* c, double eta, double a, double b) {
   return 0;
 }
 
-int clo_nfields(const clo_ctx* c) { return c ? (c->gauge() ? c->nf + 3 : c->nf) : -1; }
+int clo_nfields(const clo_ctx* c) { return c ? (c->full() ? 10 : (c->gauge() ? c->nf + 3 : c->nf)) : -1; }
 
 static std::vector<double>* array_ptr(const clo_ctx* c, int a) {
   clo_ctx* m = const_cast<clo_ctx*>(c);
-  if (!c->su2() || a < 0 || a >= 35) return nullptr;
+  if (!c->su2() || a < 0 || a >= (c->full() ? 41 : 35)) return nullptr;
+  if (a >= 35) {  // full model: 35 phi_s, 36 pi_s, 37, 38 vphi_c, 39, 40 pi_vphi,c
+    if (a == 35) return &m->sph;
+    if (a == 36) return &m->spi;
+    return a < 39 ? &m->cph[a - 37] : &m->cpi[a - 39];
+  }
   if (a < 4) return &m->phi[a];
   if (a < 8) return &m->pi[a - 4];
   if (a < 11) return &m->A[a - 8];
@@ -1460,7 +1653,7 @@ int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, doubl
 // is written for a canonically normalised field.
 int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
                       double* n, int64_t* mult, int cap, int* nbins) {
-  if (!c || !c->gauge() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
+  if (!c || !c->gauge() || c->full() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
   const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
   if (nbins) *nbins = nb;
   if (nb > cap) return -2;
@@ -1862,6 +2055,36 @@ int clo_ic_amplitude_grad(const clo_ctx* c, const double* lam, double* out) {
         out[(size_t)(2 * f + j) * c->V + idx] = s / V * (e * L[f][0][idx] + cpi * L[f][1][idx]).real();
       }
   }
+  return 0;
+}
+
+// Doublet models: the momentum kernel K (pi' = K, the rate of one kick per unit
+// step weight) of momentum array `a` (clo_get_array order: 4..7, 11..13,
+// 26..34, and for the full model 36, 39, 40) at the current state.
+int clo_kernel(const clo_ctx* c, int a, double* out) {
+  if (!c || !out || !c->su2()) return -1;
+  const bool ok = (a >= 4 && a < 8) || (a >= 11 && a < 14) || (a >= 26 && a < 35) ||
+                  (c->full() && (a == 36 || a == 39 || a == 40));
+  if (!ok) return -1;
+  std::vector<double> Kp[4], KA[3], KB[3][3], Ks, Kc[2];
+  for (int k = 0; k < 4; ++k) Kp[k].assign(c->V, 0.0);
+  for (int i = 0; i < 3; ++i) {
+    KA[i].assign(c->V, 0.0);
+    for (int b = 0; b < 3; ++b) KB[i][b].assign(c->V, 0.0);
+  }
+  kernel_su2(c, Kp, KA, KB);
+  if (c->full()) {
+    Ks.assign(c->V, 0.0);
+    for (int k = 0; k < 2; ++k) Kc[k].assign(c->V, 0.0);
+    kernel_full_extra(c, Ks, Kc, KA);
+  }
+  const std::vector<double>* src;
+  if (a < 8) src = &Kp[a - 4];
+  else if (a < 14) src = &KA[a - 11];
+  else if (a < 35) src = &KB[(a - 26) / 3][(a - 26) % 3];
+  else if (a == 36) src = &Ks;
+  else src = &Kc[a - 39];
+  std::memcpy(out, src->data(), sizeof(double) * c->V);
   return 0;
 }
 

@@ -22,7 +22,10 @@
  *   - SU(2) x U(1) doublet model: f = 0..3 are the real components of
  *     Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt(2), f = 4,5,6 the U(1)
  *     link fields A_i; the SU(2) links and their momenta are reached through
- *     clo_get_array / clo_set_array (array order below).
+ *     clo_get_array / clo_set_array (array order below);
+ *   - lphi4SU2U1 model (Sec. 4.5: the doublet, a singlet phi_s and a U(1)-charged
+ *     scalar vphi = (vphi_0 + i vphi_1)/sqrt(2), eq. PotGauge): f = 0..6 as the
+ *     doublet model, f = 7 the singlet, f = 8, 9 the components of vphi.
  *
  * Every function returns 0 on success and a negative code on error.
  */
@@ -34,7 +37,8 @@
 extern "C" {
 #endif
 
-enum { CLO_MODEL_LPHI4 = 1, CLO_MODEL_LPHI4_CHI = 2, CLO_MODEL_U1_HIGGS = 3, CLO_MODEL_SU2U1_HIGGS = 4 };
+enum { CLO_MODEL_LPHI4 = 1, CLO_MODEL_LPHI4_CHI = 2, CLO_MODEL_U1_HIGGS = 3, CLO_MODEL_SU2U1_HIGGS = 4,
+       CLO_MODEL_LPHI4_SU2U1 = 5 };
 enum { CLO_LF = 0, CLO_VV2 = 2, CLO_VV4 = 4, CLO_VV6 = 6, CLO_VV8 = 8, CLO_VV10 = 10 };
 enum { CLO_EXP_OFF = 0, CLO_EXP_SELF = 1, CLO_EXP_FIXED = 2 };
 
@@ -56,6 +60,8 @@ typedef struct {
   int b0_mode;                  /* 0: a' from homogeneous values; 1: from lattice averages */
   int pad_;
   double gQB;                   /* SU(2) gauge coupling times charge (g_B Q_B), doublet model */
+  double qG, qH;                /* lphi4SU2U1: q_G = g^2/lambda, q_H = h^2/lambda of eq. PotGauge */
+  double Qc;                    /* lphi4SU2U1: U(1) charge of the charged scalar in units of the doublet's */
 } clo_params;
 
 typedef struct {
@@ -103,10 +109,14 @@ int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, doubl
 /* SU(2) x U(1) doublet model: whole arrays in the order
  *   0..3 phi_c, 4..7 pi_c, 8..10 A_i, 11..13 pi_A,i,
  *   14 + 4 i + k: component u_k of the SU(2) link U_i = u0 - i (u1 s1 + u2 s2 + u3 s3),
- *   26 + 3 i + (a - 1): link momentum pi_B,i^a.
+ *   26 + 3 i + (a - 1): link momentum pi_B,i^a;
+ * lphi4SU2U1 model: the same, then 35 phi_s, 36 pi_s, 37, 38 vphi_c, 39, 40 pi_vphi,c.
  * -1 for other models or a bad index. */
 int clo_get_array(const clo_ctx* c, int a, double* out);
 int clo_set_array(clo_ctx* c, int a, const double* in);
+/* Doublet models: the momentum kernel K (pi' = K) of momentum array a (the
+ * array order above) at the current state; -1 for other models or arrays. */
+int clo_kernel(const clo_ctx* c, int a, double* out);
 /* Gauss-law residual per site of generator g (0: the U(1) law; 1..3: the SU(2)
  * colour a = g, doublet model only): out[n] = (lattice divergence of the
  * electric field) - (charge density); -1 where the model has no such law. */

@@ -30,7 +30,7 @@ namespace clg {
 // kernels defined in the other translation units
 typedef void (*PassKernel)(const PassArgs);
 PassKernel scalar_pass_kernel(int fp32, int nf, int red);
-PassKernel u1_pass_kernel(int fp32, int red, int kd);
+PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256);
 PassKernel su2_pass_kernel(int fp32, int red, int TX);
 size_t su2_smem_bytes(int TX, int TY, int esz);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
@@ -283,7 +283,10 @@ PassKernel pick_kernel(const cl_ctx* c, int red) {
   if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red, c->su2_tx);
   // without expansion the U(1) passes drift right after their kick (the drift
   // coefficient does not wait for the pass's sums)
-  if (c->model == CL_MODEL_U1_HIGGS) return u1_pass_kernel(c->fp32, red, c->p.expansion == CL_EXP_OFF);
+  if (c->model == CL_MODEL_U1_HIGGS) {
+    const bool n256 = c->nlat == 1 && c->lats[0].N == 256 && c->lats[0].BY == THREADS / (256 / u1_vx(c->esz));
+    return u1_pass_kernel(c->fp32, red, c->p.expansion == CL_EXP_OFF, n256);
+  }
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }
 

@@ -64,7 +64,10 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 // coefficient before the pass's sums are known, so it is taken when a(eta)
 // does not depend on them (no expansion), and saves every neighbour read its
 // momentum load and drift.
-template <typename T, int RED, bool KD>
+// NC: 0 = lattice size and tile height from the lattice constants; > 0 = the
+// kernel is built for N = NC with full tiles of THREADS threads (every stage
+// offset a compile-time constant).
+template <typename T, int RED, bool KD, int NC>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
   constexpr int VX = U1Vec<T>::n;
   constexpr int NA = 10;
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
     for (int i = 0; i < ns; ++i) {
       const Seg sg = P.segs[sb + i];
       const LatConst& L = P.lat[sg.lat];
-      const int N = L.N, BY = L.BY, TX = N / VX;
+      const int N = NC ? NC : L.N, BY = NC ? THREADS / (NC / VX) : L.BY, TX = N / VX;
       const int tx = tid % TX, ty = tid / TX;
       const bool active = ty < BY;  // threads 0 .. TX*BY-1
       const int x0 = tx * VX;
@@ -513,29 +516,35 @@ timeout:
   __syncthreads();
 }
 
-template __global__ void dk_pass_u1<float, 0, false>(const PassArgs);
-template __global__ void dk_pass_u1<float, 1, false>(const PassArgs);
-template __global__ void dk_pass_u1<float, 2, false>(const PassArgs);
-template __global__ void dk_pass_u1<double, 0, false>(const PassArgs);
-template __global__ void dk_pass_u1<double, 1, false>(const PassArgs);
-template __global__ void dk_pass_u1<double, 2, false>(const PassArgs);
-template __global__ void dk_pass_u1<float, 0, true>(const PassArgs);
-template __global__ void dk_pass_u1<float, 2, true>(const PassArgs);
-template __global__ void dk_pass_u1<double, 0, true>(const PassArgs);
-template __global__ void dk_pass_u1<double, 2, true>(const PassArgs);
+template __global__ void dk_pass_u1<float, 0, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<float, 1, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<float, 2, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<double, 0, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<double, 1, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<double, 2, false, 0>(const PassArgs);
+template __global__ void dk_pass_u1<float, 0, true, 0>(const PassArgs);
+template __global__ void dk_pass_u1<float, 2, true, 0>(const PassArgs);
+template __global__ void dk_pass_u1<double, 0, true, 0>(const PassArgs);
+template __global__ void dk_pass_u1<double, 2, true, 0>(const PassArgs);
+template __global__ void dk_pass_u1<float, 0, true, 256>(const PassArgs);
+template __global__ void dk_pass_u1<float, 2, true, 256>(const PassArgs);
 
 typedef void (*PassKernel)(const PassArgs);
 
 // kd: kick-then-drift passes (only without expansion, where the Friedmann sums
-// of RED 1 are not needed).
-PassKernel u1_pass_kernel(int fp32, int red, int kd) {
+// of RED 1 are not needed).  n256: one FP32 lattice of N = 256 with full
+// tiles (the tile height THREADS / (N / 2)), built with its sizes as constants.
+PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256) {
   static const PassKernel tab[2][3] = {
-      {dk_pass_u1<double, 0, false>, dk_pass_u1<double, 1, false>, dk_pass_u1<double, 2, false>},
-      {dk_pass_u1<float, 0, false>, dk_pass_u1<float, 1, false>, dk_pass_u1<float, 2, false>}};
+      {dk_pass_u1<double, 0, false, 0>, dk_pass_u1<double, 1, false, 0>, dk_pass_u1<double, 2, false, 0>},
+      {dk_pass_u1<float, 0, false, 0>, dk_pass_u1<float, 1, false, 0>, dk_pass_u1<float, 2, false, 0>}};
   static const PassKernel tab_kd[2][3] = {
-      {dk_pass_u1<double, 0, true>, nullptr, dk_pass_u1<double, 2, true>},
-      {dk_pass_u1<float, 0, true>, nullptr, dk_pass_u1<float, 2, true>}};
+      {dk_pass_u1<double, 0, true, 0>, nullptr, dk_pass_u1<double, 2, true, 0>},
+      {dk_pass_u1<float, 0, true, 0>, nullptr, dk_pass_u1<float, 2, true, 0>}};
+  static const PassKernel tab_kd256[3] = {dk_pass_u1<float, 0, true, 256>, nullptr,
+                                          dk_pass_u1<float, 2, true, 256>};
   if (red < 0 || red > 2) return nullptr;
+  if (kd && n256 && fp32) return tab_kd256[red];
   return kd ? tab_kd[fp32 ? 1 : 0][red] : tab[fp32 ? 1 : 0][red];
 }
 
