@@ -300,6 +300,12 @@ size_t stage_size(int N, int BY, int narr, int esz) {
 // Tile heights BY admissible for N: BY divides N, the BY rows of N/VX
 // threads fit in one CTA, and at least 3 stages fit in shared memory; the
 // tallest first.
+// Arrays a pass keeps in its stage ring: the U(1) passes without expansion
+// (kick, then drift) stage only the five field arrays.
+int ring_narr(const cl_ctx* c) {
+  return c->model == CL_MODEL_U1_HIGGS && c->p.expansion == CL_EXP_OFF ? 5 : c->narr;
+}
+
 std::vector<int> tile_candidates(int model, int narr, int esz, int N, size_t smem_optin) {
   std::vector<int> out;
   const int TX = N / tile_vx(model, esz);
@@ -575,7 +581,7 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
   CU(cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, c->dev));
   CU(cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, c->dev));
   const TuneKey key(c->model, c->esz, N, c->nsm, ccmaj, ccmin);
-  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
+  std::vector<int> cand = tile_candidates(c->model, ring_narr(c), c->esz, N, c->smem_optin);
   if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -804,7 +810,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     L.dx = 2.0 * M_PI / ((double)L.N * L.kIR);
     L.seed = seeds[l];
     c->vmax = std::max(c->vmax, L.V);
-    const std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, L.N, c->smem_optin);
+    const std::vector<int> cand = tile_candidates(c->model, ring_narr(c), c->esz, L.N, c->smem_optin);
     if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", L.N);
     if (c->p.tile_by > 0) {
       if (std::find(cand.begin(), cand.end(), c->p.tile_by) == cand.end())
@@ -829,7 +835,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     bool ok = false;
     if (c->p.autotune && c->p.tile_by == 0) {
       for (int l = 0; l < c->nlat; ++l) {
-        c->lats[l].BY = tile_candidates(c->model, c->narr, c->esz, c->lats[l].N, c->smem_optin)[0];
+        c->lats[l].BY = tile_candidates(c->model, ring_narr(c), c->esz, c->lats[l].N, c->smem_optin)[0];
         tiles[l].BY = c->lats[l].BY;
       }
       ok = build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send);
@@ -840,7 +846,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   c->nseg = (int)segs.size();
   c->nslot = send[c->nlat - 1];
   // stage ring: the largest lattice stage, as many stages (3 .. 6) as fit
-  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
+  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, ring_narr(c), c->esz));
   const int S = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / stage);
   if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the stage ring");
   c->stages = S;

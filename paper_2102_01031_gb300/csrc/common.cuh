@@ -90,6 +90,12 @@ static __device__ __forceinline__ float sin_t(float x) {
 static __device__ __forceinline__ void sincos_t(double x, double& s, double& c) { sincos(x, &s, &c); }
 static __device__ __forceinline__ double sin_t(double x) { return sin(x); }
 
+// Bring a line into L1 (no register, no wait).
+template <typename T>
+__device__ __forceinline__ void prefetch_l1(const T* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Sites per thread along x in the U(1) pass (8-byte vectors in FP32, scalars in FP64).
 constexpr int u1_vx(int esz) { return esz == 4 ? 2 : 1; }
 

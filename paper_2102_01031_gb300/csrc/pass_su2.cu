@@ -154,12 +154,6 @@ __device__ __forceinline__ T one_minus_w(const Q4<T>& p) {
   return (p.x * p.x + p.y * p.y + p.z * p.z) / (T(1) + p.w);
 }
 
-// Bring a line into L1 (no register, no wait).
-template <typename T>
-__device__ __forceinline__ void prefetch_l1(const T* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 constexpr int SU2_NQ = 24;  // partial sums per CTA (the measurement pass uses 23)
 
 }  // namespace
