@@ -69,8 +69,12 @@ typedef enum {
 enum { CL_MODEL_LPHI4 = 1,      /* V = phi^4/4                              (eq. PotNat, chi = 0) */
        CL_MODEL_LPHI4_CHI = 2,  /* V = phi^4/4 + (q/2) phi^2 chi^2          (eq. PotNat) */
        CL_MODEL_U1_HIGGS = 3,   /* V = lam (|phi|^2 - v^2)^2 + U(1) links    (Sec. 4) */
-       CL_MODEL_SU2U1_HIGGS = 4 }; /* doublet Phi, V = lam (|Phi|^2 - v^2)^2, U(1) and SU(2)
+       CL_MODEL_SU2U1_HIGGS = 4,   /* doublet Phi, V = lam (|Phi|^2 - v^2)^2, U(1) and SU(2)
                                       links: the gauge content of the lphi4SU2U1 example (Sec. 4) */
+       CL_MODEL_LPHI4_SU2U1 = 5 }; /* the lphi4SU2U1 example (Sec. 4.5): the doublet and both gauge
+                                      fields, a singlet phi_s and a U(1)-charged scalar vphi,
+                                      V = lam (|Phi|^2 - v^2)^2 + qG |Phi|^2 phi_s^2
+                                          + 2 qH |Phi|^2 |vphi|^2  (eq. PotGauge, lam = 1, v = 0) */
 
 enum { CL_LF = 0, CL_VV2 = 2, CL_VV4 = 4, CL_VV6 = 6, CL_VV8 = 8, CL_VV10 = 10 };
 enum { CL_FP64 = 0,             /* fields, momenta and arithmetic in FP64 */
@@ -104,6 +108,10 @@ typedef struct {
   int tile_by;                  /* > 0: force this tile height (rows per CTA tile) for every
                                    lattice; 0: autotune or the built-in choice */
   double gQB;                   /* SU(2) coupling times charge (g_B Q_B), CL_MODEL_SU2U1_HIGGS */
+  double qG, qH;                /* CL_MODEL_LPHI4_SU2U1: q_G = g^2/lambda, q_H = h^2/lambda (eq. PotGauge) */
+  double Qc;                    /* CL_MODEL_LPHI4_SU2U1: U(1) charge of vphi in units of the doublet's
+                                   (vphi hops with exp(-i Qc gQ dx A_i)); the singlet and vphi start
+                                   with zero homogeneous values and vacuum fluctuations */
 } cl_params;
 
 /* Volume averages at a synchronised time (eqs. EK_EG_EV, energy-contrib). */
@@ -184,7 +192,9 @@ cl_status cl_spectrum(cl_ctx* ctx, int field, int what, double dk_bin, double* k
  * synchronise the kick stream first; set_state stores in the context's
  * precision.  Fields: scalar models f < nf; U(1) model 0,1 = phi_0, phi_1 and
  * 2,3,4 = A_i; doublet model 0..3 = the components of
- * Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt2 and 4,5,6 = A_i. */
+ * Phi = (phi_0 + i phi_1, phi_2 + i phi_3)/sqrt2 and 4,5,6 = A_i;
+ * CL_MODEL_LPHI4_SU2U1 as the doublet model, and 7 = phi_s, 8, 9 = the components
+ * of vphi = (vphi_0 + i vphi_1)/sqrt2. */
 cl_status cl_get_state(cl_ctx* ctx, int field, int what, double* host_out);
 cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
 
@@ -207,6 +217,7 @@ cl_status cl_norm_spectrum(cl_ctx* ctx, double dk_bin, double fo2, double* k, do
  *   14 + 4 i + k: component u_k of the SU(2) link U_i(n) = u0 - i (u1 s1 + u2 s2 + u3 s3)
  *                 (s_a the Pauli matrices; U_i = exp(-i gQB dx B_i^a s_a/2)),
  *   26 + 3 i + (a - 1): link momentum pi_B,i^a,
+ *   and for CL_MODEL_LPHI4_SU2U1: 35 phi_s, 36 pi_s, 37, 38 vphi_c, 39, 40 pi_vphi,c,
  * N^3 FP64 values, x fastest.  Links are stored as given (a caller that sets
  * them keeps them unitary).  CL_EUNSUPPORTED for other models, CL_EINVAL for
  * a bad index.  Both synchronise the kick stream first. */

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libclgb300.so")
 
 CL_OK, CL_EINVAL, CL_ENOMEM, CL_ECUDA, CL_ESTATE, CL_ETIMEOUT, CL_ENONFINITE, CL_EUNSUPPORTED = range(8)
-MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS = 1, 2, 3, 4
+MODEL_LPHI4, MODEL_LPHI4_CHI, MODEL_U1_HIGGS, MODEL_SU2U1_HIGGS, MODEL_LPHI4_SU2U1 = 1, 2, 3, 4, 5
 LF, VV2, VV4, VV6, VV8, VV10 = 0, 2, 4, 6, 8, 10
 FP64, FP32 = 0, 1
 EXP_OFF, EXP_SELF, EXP_FIXED = 0, 1, 2
@@ -71,6 +71,9 @@ class Params(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("tile_by", ctypes.c_int),
         ("gQB", ctypes.c_double),
+        ("qG", ctypes.c_double),
+        ("qH", ctypes.c_double),
+        ("Qc", ctypes.c_double),
     ]
 
 
@@ -207,6 +210,9 @@ def make_params(**kw):
     p.autotune = int(kw.pop("autotune", 0))
     p.tile_by = int(kw.pop("tile_by", 0))
     p.gQB = kw.pop("gQB", 0.5)
+    p.qG = kw.pop("qG", 0.0)
+    p.qH = kw.pop("qH", 0.0)
+    p.Qc = kw.pop("Qc", 1.0)
     st = kw.pop("stream", None)
     p.stream = ctypes.c_void_p(int(st) if st else 0)
     if kw:

@@ -29,16 +29,20 @@ namespace clg {
 
 // kernels defined in the other translation units
 typedef void (*PassKernel)(const PassArgs);
+
+// The models run by the doublet pass: the SU(2) x U(1) doublet alone, or with
+// the singlet and the U(1)-charged scalar of the lphi4SU2U1 example.
+inline bool is_doublet(int model) { return model == CL_MODEL_SU2U1_HIGGS || model == CL_MODEL_LPHI4_SU2U1; }
 PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256);
-PassKernel su2_pass_kernel(int fp32, int red, int TX);
-size_t su2_smem_bytes(int TX, int TY, int esz);
+PassKernel su2_pass_kernel(int fp32, int red, int TX, int full);
+size_t su2_smem_bytes(int TX, int TY, int esz, int full);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
 cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
                            cudaStream_t st);
 cudaError_t launch_su2_gauss_monitor(int fp32, const LatConst* L, int parity, double* part, int nblk,
                                      long long V, cudaStream_t st);
-constexpr int SU2_PARTIALS = 24;  // partial sums per CTA of the doublet-model pass
+constexpr int SU2_PARTIALS = 30;  // partial sums per CTA of the doublet-model pass
 
 cudaError_t launch_init_scalars(const LatConst*, LatScalars*, const ICArgs&, cudaStream_t);
 cudaError_t launch_ic_modes(double2*, double2*, const LatConst*, const LatScalars*, const ICArgs&,
@@ -280,7 +284,7 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
 }
 
 PassKernel pick_kernel(const cl_ctx* c, int red) {
-  if (c->model == CL_MODEL_SU2U1_HIGGS) return su2_pass_kernel(c->fp32, red, c->su2_tx);
+  if (is_doublet(c->model)) return su2_pass_kernel(c->fp32, red, c->su2_tx, c->model == CL_MODEL_LPHI4_SU2U1);
   // without expansion the U(1) passes drift right after their kick (the drift
   // coefficient does not wait for the pass's sums)
   if (c->model == CL_MODEL_U1_HIGGS) {
@@ -300,12 +304,6 @@ size_t stage_size(int N, int BY, int narr, int esz) {
 // Tile heights BY admissible for N: BY divides N, the BY rows of N/VX
 // threads fit in one CTA, and at least 3 stages fit in shared memory; the
 // tallest first.
-// Arrays a pass keeps in its stage ring: the U(1) passes without expansion
-// (kick, then drift) stage only the five field arrays.
-int ring_narr(const cl_ctx* c) {
-  return c->model == CL_MODEL_U1_HIGGS && c->p.expansion == CL_EXP_OFF ? 5 : c->narr;
-}
-
 std::vector<int> tile_candidates(int model, int narr, int esz, int N, size_t smem_optin) {
   std::vector<int> out;
   const int TX = N / tile_vx(model, esz);
@@ -447,7 +445,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
   A.gsync = nullptr;
   A.log = log;
   A.log_base = log_base;
-  const bool su2 = c->model == CL_MODEL_SU2U1_HIGGS;
+  const bool su2 = is_doublet(c->model);
   const bool multi = n > 1 && c->coop && !su2;
   cudaGraphExec_t exec = nullptr;
   if (multi) {
@@ -581,7 +579,7 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
   CU(cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, c->dev));
   CU(cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, c->dev));
   const TuneKey key(c->model, c->esz, N, c->nsm, ccmaj, ccmin);
-  std::vector<int> cand = tile_candidates(c->model, ring_narr(c), c->esz, N, c->smem_optin);
+  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
   if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -681,7 +679,8 @@ const char* cl_last_error(const cl_ctx* c) { return c ? c->err.c_str() : g_init_
 
 int cl_nfields(const cl_ctx* c) {
   if (!c) return -1;
-  return c->model == CL_MODEL_SU2U1_HIGGS ? 7 : c->narr / 2;  // doublet: 4 components + 3 U(1) link fields
+  // doublet: 4 components + 3 U(1) link fields (+ the singlet and vphi's 2 components for lphi4SU2U1)
+  return c->model == CL_MODEL_SU2U1_HIGGS ? 7 : (c->model == CL_MODEL_LPHI4_SU2U1 ? 10 : c->narr / 2);
 }
 
 int cl_ensemble_size(const cl_ctx* c) { return c ? c->nlat : -1; }
@@ -730,9 +729,9 @@ cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, co
   if (!p || !Ns || !kIRs || !seeds) return fail(nullptr, CL_EINVAL, "NULL argument");
   if (count < 1 || count > CL_MAX_LATTICES)
     return fail(nullptr, CL_EINVAL, "count=%d: need 1..%d lattices", count, CL_MAX_LATTICES);
-  if (model < CL_MODEL_LPHI4 || model > CL_MODEL_SU2U1_HIGGS)
+  if (model < CL_MODEL_LPHI4 || model > CL_MODEL_LPHI4_SU2U1)
     return fail(nullptr, CL_EINVAL, "unknown model %d", model);
-  if (model == CL_MODEL_SU2U1_HIGGS && count != 1)
+  if (is_doublet(model) && count != 1)
     return fail(nullptr, CL_EUNSUPPORTED, "the doublet model runs one lattice per context");
   for (int l = 0; l < count; ++l) {
     if (!good_N(Ns[l]))
@@ -750,16 +749,19 @@ cl_status cl_ensemble_init(cl_ctx** out, int model, int count, const int* Ns, co
   if (!(p->dt == p->dt)) return fail(nullptr, CL_EINVAL, "dt is NaN");
   if (model == CL_MODEL_U1_HIGGS && !(p->gQ != 0.0 && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
     return fail(nullptr, CL_EINVAL, "U(1) needs a finite nonzero gQ and f*/omega*");
-  if (model == CL_MODEL_SU2U1_HIGGS &&
+  if (is_doublet(model) &&
       !(p->gQB != 0.0 && std::isfinite(p->gQB) && std::isfinite(p->gQ) && p->fstar_over_omegastar != 0.0))
     return fail(nullptr, CL_EINVAL, "the doublet model needs a finite nonzero gQB, a finite gQ and f*/omega*");
-  if (model == CL_MODEL_SU2U1_HIGGS && Ns[0] % 16)
+  if (model == CL_MODEL_LPHI4_SU2U1 && !(std::isfinite(p->qG) && std::isfinite(p->qH) && std::isfinite(p->Qc)))
+    return fail(nullptr, CL_EINVAL, "lphi4SU2U1 needs finite qG, qH and Qc");
+  if (is_doublet(model) && Ns[0] % 16)
     return fail(nullptr, CL_EUNSUPPORTED, "the doublet model needs N a multiple of 16");
   if (p->tile_by < 0) return fail(nullptr, CL_EINVAL, "tile_by must be >= 0");
   cl_ctx* c = new cl_ctx();
   c->model = model;
-  c->nf = model == CL_MODEL_LPHI4 ? 1 : (model == CL_MODEL_SU2U1_HIGGS ? 4 : 2);
-  c->narr = model == CL_MODEL_U1_HIGGS ? 10 : (model == CL_MODEL_SU2U1_HIGGS ? 35 : 2 * c->nf);
+  c->nf = model == CL_MODEL_LPHI4 ? 1 : (is_doublet(model) ? 4 : 2);
+  c->narr = model == CL_MODEL_U1_HIGGS ? 10
+            : (model == CL_MODEL_SU2U1_HIGGS ? 35 : (model == CL_MODEL_LPHI4_SU2U1 ? 41 : 2 * c->nf));
   c->fp32 = p->precision == CL_FP32;
   c->esz = c->fp32 ? 4 : 8;
   c->nlat = count;
@@ -790,7 +792,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
   c->smem_optin = (size_t)optin;
   CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  if (c->model == CL_MODEL_SU2U1_HIGGS) {
+  if (is_doublet(c->model)) {
     cl_status s = su2_init(c, Ns[0], kIRs[0], seeds[0]);
     if (s != CL_OK) return s;
     return init_finish(c);
@@ -810,7 +812,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     L.dx = 2.0 * M_PI / ((double)L.N * L.kIR);
     L.seed = seeds[l];
     c->vmax = std::max(c->vmax, L.V);
-    const std::vector<int> cand = tile_candidates(c->model, ring_narr(c), c->esz, L.N, c->smem_optin);
+    const std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, L.N, c->smem_optin);
     if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", L.N);
     if (c->p.tile_by > 0) {
       if (std::find(cand.begin(), cand.end(), c->p.tile_by) == cand.end())
@@ -835,7 +837,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     bool ok = false;
     if (c->p.autotune && c->p.tile_by == 0) {
       for (int l = 0; l < c->nlat; ++l) {
-        c->lats[l].BY = tile_candidates(c->model, ring_narr(c), c->esz, c->lats[l].N, c->smem_optin)[0];
+        c->lats[l].BY = tile_candidates(c->model, c->narr, c->esz, c->lats[l].N, c->smem_optin)[0];
         tiles[l].BY = c->lats[l].BY;
       }
       ok = build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send);
@@ -846,7 +848,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   c->nseg = (int)segs.size();
   c->nslot = send[c->nlat - 1];
   // stage ring: the largest lattice stage, as many stages (3 .. 6) as fit
-  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, ring_narr(c), c->esz));
+  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
   const int S = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / stage);
   if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the stage ring");
   c->stages = S;
@@ -1028,14 +1030,15 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   c->vmax = H.V;
   c->su2_tx = N % 32 == 0 ? 32 : 16;
   c->su2_ty = 8;
-  c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz);
+  const int full = c->model == CL_MODEL_LPHI4_SU2U1;
+  c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz, full);
   if (c->smem_bytes > c->smem_optin) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
   for (int red = 0; red < 3; ++red)
-    CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red, c->su2_tx),
+    CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red, c->su2_tx, full),
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_bytes));
   int nb = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c), c->su2_tx), c->su2_tx * c->su2_ty,
+      &nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c), c->su2_tx, full), c->su2_tx * c->su2_ty,
       c->smem_bytes));
   // work items (tile, z-chunk) over the resident CTAs (su2_work.h)
   const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);
@@ -1077,6 +1080,9 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   L.v = c->p.v;
   L.gQ = c->p.gQ;
   L.gQB = c->p.gQB;
+  L.qG = c->p.qG;
+  L.qH = c->p.qH;
+  L.Qc = c->p.Qc;
   L.su2_nzc = nzc;
   L.fo2 = c->p.fstar_over_omegastar * c->p.fstar_over_omegastar;
   L.fm2 = c->p.fstar_over_mp * c->p.fstar_over_mp;
@@ -1104,12 +1110,16 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   A.seed = H.seed;
   A.model = c->model;
   A.nf = c->nf;
+  A.qG = c->p.qG;
+  A.qH = c->p.qH;
   H.ic = A;
   CU(launch_init_scalars(c->d_lat, c->d_sc, A, c->stream));
   ++c->launches;
   double2* F = c->d_cplx;
   double2* G = c->d_cplx + H.V;
-  for (int f = 0; f < 4; ++f) {
+  // components: the doublet's four, and for lphi4SU2U1 the singlet (4) and vphi (5, 6),
+  // which start at zero homogeneous values
+  for (int f = 0; f < (full ? 7 : 4); ++f) {
     CU(cudaMemsetAsync(c->d_cplx, 0, 2 * (size_t)H.V * sizeof(double2), c->stream));
     CU(launch_ic_modes(F, G, c->d_lat, c->d_sc, A, f, H.V, c->stream));
     ++c->launches;
@@ -1117,8 +1127,10 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
     if (s != CL_OK) return s;
     s = fft3d(c, N, G, +1);
     if (s != CL_OK) return s;
-    CU(launch_ic_assemble(c->fp32, arr_ptr(c, 0, 0, f), arr_ptr(c, 0, 0, 4 + f), F, G, c->d_lat, c->d_sc,
-                          c->p.phi0[f], c->p.dphi0[f], H.V, c->stream));
+    const int af = f < 4 ? f : (f == 4 ? 35 : 37 + (f - 5));
+    const int ap = f < 4 ? 4 + f : (f == 4 ? 36 : 39 + (f - 5));
+    CU(launch_ic_assemble(c->fp32, arr_ptr(c, 0, 0, af), arr_ptr(c, 0, 0, ap), F, G, c->d_lat, c->d_sc,
+                          f < 4 ? c->p.phi0[f] : 0.0, f < 4 ? c->p.dphi0[f] : 0.0, H.V, c->stream));
     ++c->launches;
   }
   CU(launch_su2_identity_links(c->fp32, arr_ptr(c, 0, 0, 0), H.V, c->stream));
@@ -1221,7 +1233,11 @@ cl_status cl_energies(cl_ctx* c, cl_energies_t* out) { return cl_lattice_energie
 
 static cl_status array_index(cl_ctx* c, int field, int what, int* a) {
   if (what != 0 && what != 1) return fail(c, CL_EINVAL, "what must be 0 or 1");
-  if (c->model == CL_MODEL_SU2U1_HIGGS) {  // doublet components 0..3, U(1) link fields 4..6
+  if (c->model == CL_MODEL_LPHI4_SU2U1 && field >= 7 && field <= 9) {  // singlet 7, vphi 8, 9
+    *a = field == 7 ? 35 + what : 37 + (field - 8) + 2 * what;
+    return CL_OK;
+  }
+  if (is_doublet(c->model)) {  // doublet components 0..3, U(1) link fields 4..6
     if (field < 0 || field > 6) return fail(c, CL_EINVAL, "field %d out of range", field);
     *a = field < 4 ? field + 4 * what : 8 + (field - 4) + 3 * what;
     return CL_OK;
@@ -1290,14 +1306,14 @@ cl_status cl_get_state(cl_ctx* c, int field, int what, double* host_out) {
 
 cl_status cl_get_array(cl_ctx* c, int a, double* host_out) {
   if (!c || !host_out) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->model != CL_MODEL_SU2U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet model");
+  if (!is_doublet(c->model)) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet models");
   if (a < 0 || a >= c->narr) return fail(c, CL_EINVAL, "array %d out of range", a);
   return copy_array(c, a, host_out, nullptr);
 }
 
 cl_status cl_set_array(cl_ctx* c, int a, const double* host_in) {
   if (!c || !host_in) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->model != CL_MODEL_SU2U1_HIGGS) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet model");
+  if (!is_doublet(c->model)) return fail(c, CL_EUNSUPPORTED, "array access is for the doublet models");
   if (a < 0 || a >= c->narr) return fail(c, CL_EINVAL, "array %d out of range", a);
   return copy_array(c, a, nullptr, host_in);
 }
@@ -1581,7 +1597,7 @@ cl_status cl_em_spectrum(cl_ctx* c, int which, double dk_bin, double* k, double*
                          int* nbins) {
   Range range_("cl_em_spectrum");
   if (!c || !k || !delta || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
-  const bool su2 = c->model == CL_MODEL_SU2U1_HIGGS;
+  const bool su2 = is_doublet(c->model);
   if ((c->model != CL_MODEL_U1_HIGGS && !su2) || c->nlat != 1)
     return fail(c, CL_EUNSUPPORTED, "electric and magnetic spectra need a single gauge lattice");
   if (which < 0 || which > (su2 ? 3 : 1))
@@ -1667,13 +1683,13 @@ cl_status cl_gauss_constraint(cl_ctx* c, double* rel, double* lhs_abs, double* r
                               double* max_abs) {
   Range range_("cl_gauss_constraint");
   if (!c) return fail(nullptr, CL_EINVAL, "ctx is NULL");
-  if (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS)
+  if (c->model != CL_MODEL_U1_HIGGS && !is_doublet(c->model))
     return fail(c, CL_EUNSUPPORTED, "model has no gauge field");
   cl_status s = close_stream(c);
   if (s != CL_OK) return s;
   const int nblk = 2 * c->nsm;
   double* part = c->d_tmp;
-  if (c->model == CL_MODEL_SU2U1_HIGGS)
+  if (is_doublet(c->model))
     CU(launch_su2_gauss_monitor(c->fp32, c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));
   else
     CU(launch_u1_gauss_monitor(c->d_lat, c->parity, part, nblk, c->lats[0].V, c->stream));

@@ -27,6 +27,7 @@ struct LatConst {
   double inv_V, inv_dx2;
   double u1_gd, u1_cJ, u1_cC;  // U(1): gQ dx, (f_s/omega_s)^2 gQ/dx, 1/(gQ dx^3)
   double gQB;                  // doublet model: SU(2) coupling times charge
+  double qG, qH, Qc;           // lphi4SU2U1: potential couplings, charge of vphi (units of the doublet's)
   int su2_nzc, su2_pad;        // doublet model: z-chunks of the pass's work items
   void* buf[2][MAX_ARR];  // ping-pong storage; array 2f = field f, 2f+1 = its momentum
 };
@@ -154,6 +155,7 @@ constexpr int ADJ_COEF_W = 12;
 struct ICArgs {
   double phi0[4], dphi0[4];
   double amp2, kcut, kIR, H0, q, lam, v;
+  double qG, qH;  // lphi4SU2U1 potential couplings
   unsigned long long seed;
   int model, nf;
 };

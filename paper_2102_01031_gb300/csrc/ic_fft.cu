@@ -72,6 +72,10 @@ __device__ double mass2_hom(const ICArgs& A, int k) {
     return k == 0 ? 3.0 * f[0] * f[0] + A.q * f[1] * f[1] : A.q * f[0] * f[0];
   double r2 = 0.0;
   for (int c = 0; c < A.nf; ++c) r2 += 0.5 * f[c] * f[c];
+  // lphi4SU2U1 (eq. PotGauge): the singlet (k = 4) and vphi (k = 5, 6) start at
+  // zero, so only their own masses 2 qG |Phi|^2 and 2 qH |Phi|^2 are new
+  if (A.model == CL_MODEL_LPHI4_SU2U1 && k == 4) return 2.0 * A.qG * r2;
+  if (A.model == CL_MODEL_LPHI4_SU2U1 && k > 4) return 2.0 * A.qH * r2;
   return 2.0 * A.lam * (r2 - A.v * A.v) + 2.0 * A.lam * f[k] * f[k];
 }
 
@@ -123,15 +127,21 @@ __device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long lon
   const long long pid = px + (long long)N * (py + (long long)N * pz);
   *pid_out = pid;
   if (pid < idx) return false;
-  const bool charged = A.model == CL_MODEL_U1_HIGGS || A.model == CL_MODEL_SU2U1_HIGGS;
-  if (pid == idx && charged) return false;  // keeps the charge density's zero mode at 0
+  const bool gauge = A.model == CL_MODEL_U1_HIGGS || A.model == CL_MODEL_SU2U1_HIGGS ||
+                     A.model == CL_MODEL_LPHI4_SU2U1;
+  if (pid == idx && gauge) return false;  // keeps the charge density's zero mode at 0
+  // components: the model's nf, and for lphi4SU2U1 also the singlet (4) and vphi (5, 6)
+  const int nc = A.model == CL_MODEL_LPHI4_SU2U1 ? 7 : A.nf;
+  // charged groups draw their phases under eqs. InConstr:1-2 with their first component as reference
+  const bool charged = gauge && f != 4;
+  const int fref = f < 4 ? 0 : 5;
   const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
   const double k = A.kIR * sqrt((double)(nx * nx + ny * ny + nz * nz));
   if (A.kcut >= 0.0 && k > A.kcut) return false;
   if (A.amp2 <= 0.0) return false;
   // every component must have a real frequency for the mode to be populated
-  double om[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int c = 0; c < A.nf; ++c) {
+  double om[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int c = 0; c < nc; ++c) {
     const double w2 = k * k + a * a * mass2_hom(A, c);
     if (w2 <= 0.0) return false;
     om[c] = sqrt(w2);
@@ -152,8 +162,8 @@ __device__ bool mode_draw(const LatConst& L, const ICArgs& A, double a, long lon
     double u0, u1, v0, v1;
     draw_pair(A.seed, (unsigned)idx, f, 0, u0, u1);
     r1 = r2 = sqrt(-P * log(u0));
-    draw_pair(A.seed, (unsigned)idx, 0, 1, v0, v1);  // theta_01, theta_02
-    if (f == 0) {
+    draw_pair(A.seed, (unsigned)idx, fref, 1, v0, v1);  // theta_01, theta_02 of the group
+    if (f == fref) {
       t1 = 2.0 * v0;
       t2 = 2.0 * v1;
     } else {

@@ -45,7 +45,9 @@ namespace clg {
 
 namespace {
 
-enum : int { SF = 0, SP = 4, SA = 8, SPA = 11, SU = 14, SPB = 26, SNARR = 35 };
+enum : int { SF = 0, SP = 4, SA = 8, SPA = 11, SU = 14, SPB = 26, SNARR = 35,
+              // lphi4SU2U1: singlet, its momentum, vphi components, their momenta
+              SS = 35, SPS = 36, SC = 37, SPC = 39, SNARR_FULL = 41 };
 
 template <typename T> struct alignas(4 * sizeof(T)) Q4 {
   T w, x, y, z;
@@ -154,20 +156,29 @@ __device__ __forceinline__ T one_minus_w(const Q4<T>& p) {
   return (p.x * p.x + p.y * p.y + p.z * p.z) / (T(1) + p.w);
 }
 
-constexpr int SU2_NQ = 24;  // partial sums per CTA (the measurement pass uses 23)
+constexpr int SU2_NQ = 30;  // partial sums per CTA (the measurement pass uses 23, 29 for lphi4SU2U1)
 
 }  // namespace
 
-// Bytes of one ring slot: per halo site 3 links + doublet (quaternions) and 3 U(1) fields.
-__host__ __device__ constexpr size_t su2_slot_bytes(int TX, int TY, int esz) {
-  return (19 * (size_t)(TX + 2) * (TY + 2) * esz + 127) / 128 * 128;
+// Bytes of one ring slot: per halo site 3 links + doublet (quaternions) and 3 U(1)
+// fields, and for lphi4SU2U1 also the singlet and vphi's two components.
+__host__ __device__ constexpr size_t su2_slot_bytes(int TX, int TY, int esz, bool full = false) {
+  return ((full ? 22 : 19) * (size_t)(TX + 2) * (TY + 2) * esz + 127) / 128 * 128;
 }
 constexpr int SU2_TY = 8;  // tile height of the pass; the width TX (32 or 16) is a template parameter
 
 // RED: 0 = no sums, 1 = sums for the Friedmann kicks, 2 = full measurement.
-template <typename T, int RED, int TX>
-__global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_pass_su2(const PassArgs P) {
-  constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 6 : 23);
+// FULL: the lphi4SU2U1 model (Sec. 4.5): also a singlet phi_s and a U(1)-charged
+// scalar vphi (charge Qc in units of the doublet's, hopping with exp(-i Qc gQ dx A_i)),
+// coupled through V = lam (|Phi|^2 - v^2)^2 + qG |Phi|^2 phi_s^2 + 2 qH |Phi|^2 |vphi|^2:
+//   pi_s   += c_k [a^{1+alpha} Lap phi_s - a^{3+alpha} 2 qG |Phi|^2 phi_s]
+//   pi_vc  += c_k [a^{1+alpha} (D^2 vphi)_c - a^{3+alpha} 2 qH |Phi|^2 vphi_c]
+//   pi_c   (doublet) gains - a^{3+alpha} (qG phi_s^2 + 2 qH |vphi|^2) phi_c
+//   pi_A,i gains a^{1+alpha} (f_s/omega_s)^2 Qc (gQ/dx) (vphi_0 u_1 - vphi_1 u_0), u = its hop.
+template <typename T, int RED, int TX, bool FULL>
+__global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8 || FULL) ? 1 : 2) dk_pass_su2(const PassArgs P) {
+  constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 6 : (FULL ? 29 : 23));
+  constexpr int NLD = FULL ? SNARR_FULL : SNARR;  // arrays loaded per halo site
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red_s[SU2_NQ][9];
   __shared__ unsigned last_s;
@@ -182,10 +193,10 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
   const int parity = P.parity;
   const T* const src = reinterpret_cast<const T*>(L.buf[parity][0]);
   T* const dst = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
-  constexpr size_t slot_b = su2_slot_bytes(TX, TY, sizeof(T));
+  constexpr size_t slot_b = su2_slot_bytes(TX, TY, sizeof(T), FULL);
 
   // coefficients: FP64 products by one lane, broadcast in the storage precision
-  T cf[13];
+  T cf[17];
   if (lane == 0) {
     const LatScalars* SC = P.sc;
     const double ck = P.ck, ap1 = __ldcg(&SC->apow1), apm1 = __ldcg(&SC->apowm1);
@@ -203,11 +214,16 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
     cf[10] = (T)(L.v * L.v);
     cf[11] = (T)L.lam;
     cf[12] = (T)(2.0 * L.lam);
+    cf[13] = (T)L.qG;
+    cf[14] = (T)L.qH;
+    cf[15] = (T)(L.Qc * L.gQ * dx);                              // vphi's link phase per A_i
+    cf[16] = (T)(ck * ap1 * L.fo2 * L.Qc * L.gQ / dx);            // vphi's U(1) current
   }
 #pragma unroll
-  for (int k = 0; k < 13; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
+  for (int k = 0; k < 17; ++k) cf[k] = __shfl_sync(0xffffffffu, cf[k], 0);
   const T cd = cf[0], cdA = cf[1], hB = cf[2], A1 = cf[3], A3 = cf[4], AJA = cf[5], ACA = cf[6], AJB = cf[7],
-          AMB = cf[8], gd = cf[9], v2 = cf[10], lam = cf[11], lam2 = cf[12];
+          AMB = cf[8], gd = cf[9], v2 = cf[10], lam = cf[11], lam2 = cf[12], qG = cf[13], qH = cf[14],
+          gdc = cf[15], AJC = cf[16];
   const bool drifting = cd != T(0) || cdA != T(0);
 
   Acc<T> acc[NACC];
@@ -219,23 +235,25 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
   auto sU = [&](int s, int i) { return reinterpret_cast<Q4<T>*>(smem + s * slot_b) + i * HS; };
   auto sF = [&](int s) { return reinterpret_cast<Q4<T>*>(smem + s * slot_b) + 3 * HS; };
   auto sA = [&](int s, int i) { return reinterpret_cast<T*>(smem + s * slot_b) + 16 * HS + i * HS; };
+  // FULL: the singlet (k = 0) and vphi's components (k = 1, 2)
+  auto sX = [&](int s, int k) { return reinterpret_cast<T*>(smem + s * slot_b) + 19 * HS + k * HS; };
 
   // the 35 raw values of halo site k of plane zp, all loads issued before any use
   // (the source buffer is read-only during the pass)
-  auto fetch = [&](int k, int x0, int y0, int zp, T (&r)[SNARR]) {
+  auto fetch = [&](int k, int x0, int y0, int zp, T (&r)[NLD]) {
     const int hx = k % HX, hy = k / HX;
     int gx = x0 + hx - 1, gy = y0 + hy - 1;
     gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
     gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
     const T* p = src + ((long long)zp * NN + (long long)gy * N + gx);
 #pragma unroll
-    for (int a = 0; a < SNARR; ++a) {
+    for (int a = 0; a < NLD; ++a) {
       r[a] = __ldg(p);
       p += V;
     }
   };
   // drift halo site k into ring slot s; own sites written out when `own`
-  auto put = [&](int s, int k, int x0, int y0, int zp, bool own, const T (&r)[SNARR]) {
+  auto put = [&](int s, int k, int x0, int y0, int zp, bool own, const T (&r)[NLD]) {
     Q4<T> f, u[3];
     T a[3];
     f.w = r[SF];
@@ -277,6 +295,14 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
       sU(s, i)[k] = u[i];
       sA(s, i)[k] = a[i];
     }
+    T xs[3] = {T(0), T(0), T(0)};  // FULL: phi_s, vphi_0, vphi_1, drifted
+    if constexpr (FULL) {
+      xs[0] = drifting ? fmaT(cd, r[SPS], r[SS]) : r[SS];
+      xs[1] = drifting ? fmaT(cd, r[SPC], r[SC]) : r[SC];
+      xs[2] = drifting ? fmaT(cd, r[SPC + 1], r[SC + 1]) : r[SC + 1];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) sX(s, m)[k] = xs[m];
+    }
     const int hx = k % HX, hy = k / HX;
     if (own && P.write && hx >= 1 && hx <= TX && hy >= 1 && hy <= TY) {
       T* o = dst + ((long long)zp * NN + (long long)(y0 + hy - 1) * N + (x0 + hx - 1));
@@ -287,12 +313,17 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         const int arr = m < 4 ? SF + m : (m < 7 ? SA + (m - 4) : SU + (m - 7));
         o[arr * V] = vals[m];
       }
+      if constexpr (FULL) {
+        o[SS * V] = xs[0];
+        o[SC * V] = xs[1];
+        o[(SC + 1) * V] = xs[2];
+      }
     }
   };
   // plane zp of tile (x0, y0) into slot s, drifted
   auto load_plane = [&](int s, int x0, int y0, int zp, bool own) {
     for (int k = tid; k < HS; k += nth) {
-      T r0[SNARR];
+      T r0[NLD];
       fetch(k, x0, y0, zp, r0);
       put(s, k, x0, y0, zp, own, r0);
     }
@@ -327,6 +358,11 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         for (int m = 0; m < 3; ++m) prefetch_l1(pp + (SPA + m) * V);
 #pragma unroll
         for (int m = 0; m < 9; ++m) prefetch_l1(pp + (SPB + m) * V);
+        if constexpr (FULL) {
+          prefetch_l1(pp + SPS * V);
+          prefetch_l1(pp + SPC * V);
+          prefetch_l1(pp + (SPC + 1) * V);
+        }
       }
       load_plane(sp, x0, y0, (z + 1) % N, j + 1 < nz);
       __syncthreads();
@@ -340,6 +376,16 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
       D.z = T(-6) * psi.z;
       T s_g = T(0), s_pA = T(0), s_pB = T(0), s_mA = T(0), s_mB = T(0);
       T pnA[3], pnB[3][3];
+      // FULL: the singlet's Laplacian and gradient sum, vphi's covariant Laplacian and gradient sum
+      T xs0 = T(0), xc0 = T(0), xc1 = T(0), Ls = T(0), Dv0 = T(0), Dv1 = T(0), s_gs = T(0), s_gc = T(0);
+      if constexpr (FULL) {
+        xs0 = sX(sc, 0)[own];
+        xc0 = sX(sc, 1)[own];
+        xc1 = sX(sc, 2)[own];
+        Ls = T(-6) * xs0;
+        Dv0 = T(-6) * xc0;
+        Dv1 = T(-6) * xc1;
+      }
       // U(1) plaquette sines: xy, xz, yz at n, then the lower ones
       const T ax = sA(sc, 0)[own], ay = sA(sc, 1)[own], az = sA(sc, 2)[own];
       T sxy = T(0), sxz = T(0), syz = T(0), Cx = T(0), Cy = T(0), Cz = T(0);
@@ -431,6 +477,29 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         // ---- link kicks ----
         const T pA = __ldg(src + (SPA + i) * V + g);
         pnA[i] = pA + (AJA * ImA + ACA * Cc[i]);
+        if constexpr (FULL) {
+          // singlet neighbours along i
+          const T sfw = i == 2 ? sX(sp, 0)[own] : sX(sc, 0)[at(fx, fy)];
+          const T sbw = sX(bs, 0)[bk];
+          Ls += sfw + sbw;
+          // vphi: forward hop Vc_i(n) vphi(n+i), backward hop Vc_i^*(n-i) vphi(n-i), Vc = exp(-i Qc gQ dx A)
+          const T y0 = i == 2 ? sX(sp, 1)[own] : sX(sc, 1)[at(fx, fy)];
+          const T y1 = i == 2 ? sX(sp, 2)[own] : sX(sc, 2)[at(fx, fy)];
+          T cc, sc2;
+          sincos_t(gdc * sA(sc, i)[own], sc2, cc);
+          const T u0 = cc * y0 + sc2 * y1, u1 = cc * y1 - sc2 * y0;
+          const T b0 = sX(bs, 1)[bk], b1 = sX(bs, 2)[bk];
+          sincos_t(gdc * sA(bs, i)[bk], sc2, cc);
+          const T w0 = cc * b0 - sc2 * b1, w1 = cc * b1 + sc2 * b0;
+          Dv0 += u0 + w0;
+          Dv1 += u1 + w1;
+          pnA[i] += AJC * (xc0 * u1 - xc1 * u0);
+          if constexpr (RED > 0) {
+            const T gs = sfw - xs0, g0 = u0 - xc0, g1 = u1 - xc1;
+            s_gs += gs * gs;
+            s_gc += g0 * g0 + g1 * g1;
+          }
+        }
         const T Ims[3] = {Im1, Im2, Im3};
         const T Ms[3] = {M.x, M.y, M.z};
 #pragma unroll
@@ -446,12 +515,29 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
       // ---- doublet kick ----
       const T r2 = T(0.5) * ((psi.w * psi.w + psi.x * psi.x) + (psi.y * psi.y + psi.z * psi.z));
       const T dd = r2 - v2;
-      const T gp = lam2 * dd;
+      T gp = lam2 * dd;
+      T c2v = T(0);  // FULL: |vphi|^2
+      if constexpr (FULL) {
+        c2v = T(0.5) * (xc0 * xc0 + xc1 * xc1);
+        gp += qG * xs0 * xs0 + T(2) * qH * c2v;
+      }
       T pn[4];
       const T Dc[4] = {D.w, D.x, D.y, D.z};
       const T fc[4] = {psi.w, psi.x, psi.y, psi.z};
 #pragma unroll
       for (int c2 = 0; c2 < 4; ++c2) pn[c2] = __ldg(src + (SP + c2) * V + g) + (A1 * Dc[c2] - A3 * gp * fc[c2]);
+      // FULL: kicks of the singlet and of vphi
+      T pns = T(0), pnc0 = T(0), pnc1 = T(0);
+      if constexpr (FULL) {
+        pns = __ldg(src + SPS * V + g) + (A1 * Ls - A3 * (T(2) * qG * r2) * xs0);
+        pnc0 = __ldg(src + SPC * V + g) + (A1 * Dv0 - A3 * (T(2) * qH * r2) * xc0);
+        pnc1 = __ldg(src + (SPC + 1) * V + g) + (A1 * Dv1 - A3 * (T(2) * qH * r2) * xc1);
+        if (P.write) {
+          dst[SPS * V + g] = pns;
+          dst[SPC * V + g] = pnc0;
+          dst[(SPC + 1) * V + g] = pnc1;
+        }
+      }
       if (P.write) {
 #pragma unroll
         for (int c2 = 0; c2 < 4; ++c2) dst[(SP + c2) * V + g] = pn[c2];
@@ -469,6 +555,11 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         acc[3].add(s_mA);
         acc[4].add(s_mB);
         acc[5].add(lam * dd * dd);
+        if constexpr (FULL) {  // the Friedmann kick takes the totals
+          acc[0].add(pns * pns + (pnc0 * pnc0 + pnc1 * pnc1));
+          acc[2].add(s_gs + s_gc);
+          acc[5].add(qG * r2 * xs0 * xs0 + T(2) * qH * r2 * c2v);
+        }
       } else if constexpr (RED == 2) {
 #pragma unroll
         for (int c2 = 0; c2 < 4; ++c2) {
@@ -485,6 +576,15 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
         acc[8].add(s_mB);
         acc[9].add(lam * dd * dd);
         if (!isfinite(s_pA) || !isfinite(s_pB)) nonfinite += 1.f;
+        if constexpr (FULL) {  // per species: singlet, vphi
+          acc[23].add(pns * pns);
+          acc[24].add(pnc0 * pnc0 + pnc1 * pnc1);
+          acc[25].add(s_gs);
+          acc[26].add(s_gc);
+          acc[27].add(qG * r2 * xs0 * xs0);
+          acc[28].add(T(2) * qH * r2 * c2v);
+          if (!isfinite(pns) || !isfinite(pnc0) || !isfinite(pnc1)) nonfinite += 1.f;
+        }
       }
       __syncthreads();  // slot sm is overwritten by the next load
     }
@@ -556,6 +656,11 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
       EGA = red_s[7][0] * mA;
       EGB = red_s[8][0] * mB;
       E.EV = red_s[9][0] * L.inv_V;
+      if (FULL) {  // the Friedmann kicks take the totals of the three scalar species
+        spost += red_s[23][0] + red_s[24][0];
+        E.EG += (red_s[25][0] + red_s[26][0]) * gphi;
+        E.EV += (red_s[27][0] + red_s[28][0]) * L.inv_V;
+      }
     }
     // the two link sectors enter the Friedmann kicks with one coefficient, (alpha - 1)
     E.EKpre = W.pi2 * kphi;
@@ -579,6 +684,17 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
     ob.EK[0] = E.EKpost;
     ob.EG[0] = E.EG;
     ob.EV[0] = E.EV;
+    if (FULL) {  // per species: [0] doublet, [1] singlet, [2] vphi; EV per potential term
+      ob.EK[1] = red_s[23][0] * kphi;
+      ob.EK[2] = red_s[24][0] * kphi;
+      ob.EK[0] = E.EKpost - ob.EK[1] - ob.EK[2];
+      ob.EG[0] = red_s[6][0] * gphi;
+      ob.EG[1] = red_s[25][0] * gphi;
+      ob.EG[2] = red_s[26][0] * gphi;
+      ob.EV[0] = red_s[9][0] * L.inv_V;
+      ob.EV[1] = red_s[27][0] * L.inv_V;
+      ob.EV[2] = red_s[28][0] * L.inv_V;
+    }
     ob.EKA = EKA;
     ob.EGA = EGA;
     ob.EKB = EKB;
@@ -594,17 +710,22 @@ __global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_
 
 typedef void (*PassKernel)(const PassArgs);
 
-PassKernel su2_pass_kernel(int fp32, int red, int TX) {
+PassKernel su2_pass_kernel(int fp32, int red, int TX, int full) {
   static const PassKernel tab[2][2][3] = {
-      {{dk_pass_su2<double, 0, 16>, dk_pass_su2<double, 1, 16>, dk_pass_su2<double, 2, 16>},
-       {dk_pass_su2<float, 0, 16>, dk_pass_su2<float, 1, 16>, dk_pass_su2<float, 2, 16>}},
-      {{dk_pass_su2<double, 0, 32>, dk_pass_su2<double, 1, 32>, dk_pass_su2<double, 2, 32>},
-       {dk_pass_su2<float, 0, 32>, dk_pass_su2<float, 1, 32>, dk_pass_su2<float, 2, 32>}}};
+      {{dk_pass_su2<double, 0, 16, false>, dk_pass_su2<double, 1, 16, false>, dk_pass_su2<double, 2, 16, false>},
+       {dk_pass_su2<float, 0, 16, false>, dk_pass_su2<float, 1, 16, false>, dk_pass_su2<float, 2, 16, false>}},
+      {{dk_pass_su2<double, 0, 32, false>, dk_pass_su2<double, 1, 32, false>, dk_pass_su2<double, 2, 32, false>},
+       {dk_pass_su2<float, 0, 32, false>, dk_pass_su2<float, 1, 32, false>, dk_pass_su2<float, 2, 32, false>}}};
+  static const PassKernel tab_full[2][2][3] = {
+      {{dk_pass_su2<double, 0, 16, true>, dk_pass_su2<double, 1, 16, true>, dk_pass_su2<double, 2, 16, true>},
+       {dk_pass_su2<float, 0, 16, true>, dk_pass_su2<float, 1, 16, true>, dk_pass_su2<float, 2, 16, true>}},
+      {{dk_pass_su2<double, 0, 32, true>, dk_pass_su2<double, 1, 32, true>, dk_pass_su2<double, 2, 32, true>},
+       {dk_pass_su2<float, 0, 32, true>, dk_pass_su2<float, 1, 32, true>, dk_pass_su2<float, 2, 32, true>}}};
   if (red < 0 || red > 2 || (TX != 16 && TX != 32)) return nullptr;
-  return tab[TX == 32 ? 1 : 0][fp32 ? 1 : 0][red];
+  return (full ? tab_full : tab)[TX == 32 ? 1 : 0][fp32 ? 1 : 0][red];
 }
 
-size_t su2_smem_bytes(int TX, int TY, int esz) { return 3 * su2_slot_bytes(TX, TY, esz); }
+size_t su2_smem_bytes(int TX, int TY, int esz, int full) { return 3 * su2_slot_bytes(TX, TY, esz, full != 0); }
 
 // ---------------------------------------------------------------------------
 // Initial state and the Gauss-law monitor of the doublet model.
@@ -641,6 +762,9 @@ __device__ double su2_rho(const LatConst& L, const T* b, int g, long long n) {
   else if (g == 1) im = (f.w * p.z - f.x * p.y) + (f.y * p.x - f.z * p.w);
   else if (g == 2) im = (f.y * p.w + f.z * p.x) - (f.w * p.y + f.x * p.z);
   else im = (f.w * p.x - f.x * p.w) - (f.y * p.z - f.z * p.y);
+  if (g == 0 && L.model == CL_MODEL_LPHI4_SU2U1)  // vphi's charge density, charge Qc in units of the doublet's
+    im += L.Qc * ((double)b[SC * V + n] * (double)b[(SPC + 1) * V + n] -
+                  (double)b[(SC + 1) * V + n] * (double)b[SPC * V + n]);
   return L.fo2 * (g == 0 ? L.gQ : 0.5 * L.gQB) * im;
 }
 

@@ -63,16 +63,14 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 // order of operations on every value is the same; it needs the drift
 // coefficient before the pass's sums are known, so it is taken when a(eta)
 // does not depend on them (no expansion), and saves every neighbour read its
-// momentum load and drift.  Its stages then hold only the five field arrays
-// (momenta are needed at the own site only and are read from global memory,
-// prefetched into L1 a plane ahead), so that twice as many stages fit.
+// momentum load and drift.
 // NC: 0 = lattice size and tile height from the lattice constants; > 0 = the
 // kernel is built for N = NC with full tiles of THREADS threads (every stage
 // offset a compile-time constant).
 template <typename T, int RED, bool KD, int NC>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
   constexpr int VX = U1Vec<T>::n;
-  constexpr int NAR = KD ? 5 : 10;  // arrays in a ring stage: KD the fields (F0, F1, AX, AY, AZ), else all ten
+  constexpr int NAR = 10;  // arrays in a ring stage
   // RED 1: pi_phi^2, pi_A^2, |D+ phi|^2, magnetic, V.
   // RED 2: pi_0^2, pi_1^2, pi_A^2, |D+ phi|^2, magnetic, V, <phi_c>, <phi_c^2>, <pi_c>.
   constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 5 : 12);
@@ -83,7 +81,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sb = P.cta_seg[blockIdx.x], ns = P.cta_seg[blockIdx.x + 1] - sb;
   const bool multi = P.npass > 1;
-  if (tid == 0) ring_setup<NAR, KD ? 2 : 1>(R, P, sb, ns);
+  if (tid == 0) ring_setup<NAR>(R, P, sb, ns);
   __syncthreads();
   const int ptot = R.off[ns];
   const int S = R.S;
@@ -147,12 +145,11 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;
       // output buffer: array a of a lattice buffer starts a * V elements after array 0
       T* const dbase = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
-      const T* const sbase = reinterpret_cast<const T*>(L.buf[parity][0]);
       const long long Vs = L.V;
 
       // drifted vector of field array a (its momentum is a + 1) on stage row `row`
       auto rdv = [&](const T* st, int a, int row, T coef, T (&o)[VX]) {
-        ldv<T>(o, st + (KD ? a >> 1 : a) * ae + row * N + x0);
+        ldv<T>(o, st + a * ae + row * N + x0);
         if (drifting) {
           T m[VX];
           ldv<T>(m, st + (a + 1) * ae + row * N + x0);
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
         }
       };
       auto rds = [&](const T* st, int a, int row, int x, T coef) -> T {
-        const T f = st[(KD ? a >> 1 : a) * ae + row * N + x];
+        const T f = st[a * ae + row * N + x];
         return drifting ? fmaT(coef, st[(a + 1) * ae + row * N + x], f) : f;
       };
       // value at x0 - 1 (x0 + VX) of a row, read from the stage and drifted like
@@ -221,14 +218,6 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
           const int own = (ty + 1) * N + x0;
           // segments march up and never wrap: plane j is z0 + j - 1
           T* const out = dbase + (long long)(sg.z0 + j - 1) * NN + (long long)y * N + x0;
-          // KD: the own momenta of this plane (array a at gmom + a V), and the next plane's into L1
-          const T* const gmom = sbase + (long long)(sg.z0 + j - 1) * NN + (long long)y * N + x0;
-          if constexpr (KD) {
-            if (j < sg.nz) {
-#pragma unroll
-              for (int m = P0; m <= PAZ; m += 2) prefetch_l1(gmom + NN + m * Vs);
-            }
-          }
           T aF[2][VX], aA[3][VX];  // plane above, drifted
           rdv(sa, F0, ty + 1, cd, aF[0]);
           rdv(sa, F1, ty + 1, cd, aF[1]);
@@ -258,13 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             T sxl, cxl;
             sincos_t(gd * ax_l, sxl, cxl);
             T p0[VX], p1[VX], pn0[VX], pn1[VX];
-            if constexpr (KD) {
-              ldv<T>(p0, gmom + P0 * Vs);
-              ldv<T>(p1, gmom + P1 * Vs);
-            } else {
-              ldv<T>(p0, sc + P0 * ae + own);
-              ldv<T>(p1, sc + P1 * ae + own);
-            }
+            ldv<T>(p0, sc + P0 * ae + own);
+            ldv<T>(p1, sc + P1 * ae + own);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
               const T f0 = cF[0][v], f1 = cF[1][v];
@@ -349,15 +333,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             const T az_r = right(sc, AZ, ty + 1, cdA);
             const T ayym_r = right(sc, AY, ty, cdA);
             T pax[VX], pay[VX], paz[VX], pnx[VX], pny[VX], pnz[VX], pxy[VX];
-            if constexpr (KD) {
-              ldv<T>(pax, gmom + PAX * Vs);
-              ldv<T>(pay, gmom + PAY * Vs);
-              ldv<T>(paz, gmom + PAZ * Vs);
-            } else {
-              ldv<T>(pax, sc + PAX * ae + own);
-              ldv<T>(pay, sc + PAY * ae + own);
-              ldv<T>(paz, sc + PAZ * ae + own);
-            }
+            ldv<T>(pax, sc + PAX * ae + own);
+            ldv<T>(pay, sc + PAY * ae + own);
+            ldv<T>(paz, sc + PAZ * ae + own);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
               const T ax = cA[0][v], ay = cA[1][v], az = cA[2][v];

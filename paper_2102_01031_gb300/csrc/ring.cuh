@@ -44,9 +44,8 @@ __device__ __forceinline__ Ring ring_view(unsigned char* smem, const PassArgs& P
 }
 
 // Thread 0: barriers, counts, flags, plane offsets and the copy info of the
-// CTA's `ns` segments starting at segs[sb].  Stage array a is lattice array
-// a * AS (AS = 2: every other array, the fields of a field/momentum layout).
-template <int NA, int AS = 1>
+// CTA's `ns` segments starting at segs[sb].
+template <int NA>
 __device__ void ring_setup(const Ring& R, const PassArgs& P, int sb, int ns) {
   for (int s = 0; s < R.S; ++s) {
     mbar_init(&R.full[s], 1);
@@ -70,8 +69,8 @@ __device__ void ring_setup(const Ring& R, const PassArgs& P, int sb, int ns) {
     in.N = L.N;
     in.rows = L.BY + 2;
     for (int a = 0; a < NA; ++a) {
-      in.src[0][a] = L.buf[0][a * AS];
-      in.src[1][a] = L.buf[1][a * AS];
+      in.src[0][a] = L.buf[0][a];
+      in.src[1][a] = L.buf[1][a];
     }
   }
 }
