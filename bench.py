@@ -551,6 +551,25 @@ def other_workloads(P, torch, stream, peak):
                              "frac": ach / ISSUE_PEAK_LANE_INSTR_PER_S,
                              "ncu_dram_bytes_per_site": NCU_SU2["dram_bytes_per_site"]}
     out["su2u1_doublet_256_fp32_lf"] = row
+    # the lphi4SU2U1 model (doublet, singlet, U(1)-charged scalar, both gauge fields), 256^3, FP32, LF
+    try:
+        lat = P.Lattice(P.MODEL_LPHI4_SU2U1, 256, 0.1, 1.0, 1,
+                        P.make_params(precision=P.FP32, stream=stream, **dict(SU2, v=0.0, qG=1.5, qH=0.8, Qc=0.7)))
+        lat.step(10)
+        torch.cuda.synchronize()
+        lat.pass_timing(reset=True)
+        lat.enable_pass_timing(True)
+        lat.step(200)
+        torch.cuda.synchronize()
+        ms, n = lat.pass_timing(reset=True)
+        rel = lat.gauss()[0]
+        lat.close()
+        gbs = 256 ** 3 * 41 * 2 * 4 / (ms / n * 1e-3) / 1e9
+        out["lphi4su2u1_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+                                         "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 328,
+                                         "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0,32,true>"}
+    except Exception as e:  # noqa: BLE001
+        out["lphi4su2u1_256_fp32_lf"] = {"error": str(e)[:300]}
     # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
     Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
     E = P.Ensemble(P.MODEL_LPHI4_CHI, Ns, [KIR * N_LAT / n for n in Ns], ALPHA, list(range(1, 65)),

@@ -8,7 +8,8 @@ properties:
     then two leapfrog steps of the FP32 pass from the GPU's FP32 state against
     the oracle started from the same values (normwise 1e-5 per array, the FP32
     tolerance of the other parity tests; averages 1e-6).
-  * The SU(2) x U(1) doublet at 256^3: one leapfrog step of the FP32 pass
+  * The SU(2) x U(1) doublet at 256^3, and the lphi4SU2U1 model (with the
+    singlet and the U(1)-charged scalar): one leapfrog step of the FP32 pass
     against the oracle from the same state (normwise 1e-5 per array).
   * The adjoint at 128^3 in FP32 with checkpoints every 50 of 400 VV4 steps,
     against the FP64 GPU adjoint (itself held to the oracle's discrete adjoint
@@ -116,6 +117,37 @@ def test_doublet_256_fp32_leapfrog_matches_oracle(P):
     eg, eo = g.energies(), o.energies()
     for k in ("EKA", "EGA", "EKB", "EGB", "rho"):
         assert abs(eg[k] - eo[k]) <= 1e-5 * abs(eo[k]), (k, eg[k], eo[k])
+    g.close()
+
+
+def test_lphi4su2u1_256_fp32_leapfrog_matches_oracle(P):
+    """The lphi4SU2U1 model at 256^3 (singlet, charged scalar and doublet, both
+    gauge fields): one leapfrog step of the FP32 pass against the oracle from
+    the same state (normwise 1e-5 per array)."""
+    N, kIR, NA = 256, 0.1, 41
+    kw = dict(SU2, v=0.0, qG=1.5, qH=0.8, Qc=0.7)
+    g = P.Lattice(O.MODEL_LPHI4_SU2U1, N, kIR, 1.0, 1, P.make_params(precision=P.FP32, **kw))
+    o = O.Oracle(O.MODEL_LPHI4_SU2U1, N, kIR, 1.0, 1, O.make_params(**dict(kw, fluct_amp2=0.0)))
+    for a in range(NA):
+        o.set_array(a, g.get_array(a))
+    o.set_scalars(*g.scalars())
+    g.step(1)
+    o.step(1)
+    worst = 0.0
+    for a in range(NA):
+        ref = o.get_array(a)
+        got = g.get_array(a)
+        if np.abs(ref).max() == 0.0:
+            assert np.abs(got).max() == 0.0, a
+            continue
+        e = nrel(got, ref)
+        worst = max(worst, e)
+        assert e < 1e-5, (a, e)
+    print("lphi4SU2U1 256^3 FP32, 1 LF step: worst array normwise %.3g" % worst)
+    eg, eo = g.energies(), o.energies()
+    for k in ("EK", "EG", "EV"):
+        for i in range(3):
+            assert abs(eg[k][i] - eo[k][i]) <= 1e-5 * abs(eo[k][i]), (k, i, eg[k][i], eo[k][i])
     g.close()
 
 
