@@ -691,6 +691,12 @@ def profile_case(name):
                         P.make_params(precision=P.FP32, stream=stream, **su2_params(P)))
         for _ in range(4):
             lat.step(1)
+    elif name == "full_128":  # single-pass launches of the leapfrog lphi4SU2U1 pass
+        lat = P.Lattice(P.MODEL_LPHI4_SU2U1, 128, 0.2, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream,
+                                      **dict(su2_params(P), v=0.0, qG=1.5, qH=0.8, Qc=0.7)))
+        for _ in range(4):
+            lat.step(1)
     elif name == "scalar256_fp64":   # the FP64 plain pass: one cooperative launch of a VV4 step
         lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
                         P.make_params(precision=P.FP64, stream=stream, **PARAMS))
@@ -729,8 +735,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="reference arm: site-steps budget / 1e6 that sizes its oracle box")
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "adj128",
-                             "adj128self", "spectrum256"),
+    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "full_128",
+                             "adj128", "adj128self", "spectrum256"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

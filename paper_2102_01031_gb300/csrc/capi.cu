@@ -51,6 +51,8 @@ cudaError_t launch_ic_assemble(int, void*, void*, const double2*, const double2*
                                const LatScalars*, double, double, long long, cudaStream_t);
 cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
 cudaError_t launch_fft_twiddles(double2*, int, cudaStream_t);
+cudaError_t launch_real_spectrum(int fp32, const void* f, double2* H, const FftPlan& pl, double dk, int nb,
+                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st);
 int fft_batch(int N);
 cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
 cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
@@ -272,6 +274,7 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
   pl.sign = sign;
   pl.batch = fft_batch(N);
   pl.tw = c->d_tw;
+  pl.pitch = pl.nu = N;
   fft_radices(N, pl);
   CU(launch_fft_twiddles(c->d_tw, N, c->stream));
   ++c->launches;
@@ -1400,14 +1403,22 @@ cl_status cl_ensemble_spectrum(cl_ctx* c, const int* lats, int nl, int field, in
   double* bins = c->d_spec + (size_t)3 * 2048 * nblk;  // [nl][3 nb]: k, delta, mult
   double* mean = bins + (size_t)nl * 3 * nb;
   double2* F = c->d_cplx;
+  // real fields: the half spectrum (row pairs along x, then the N/2 + 1 columns kept along y and z)
+  FftPlan pl;
+  pl.N = H.N;
+  pl.sign = -1;
+  pl.batch = fft_batch(H.N);
+  pl.tw = c->d_tw;
+  pl.pitch = pl.nu = H.N;
+  pl.axis = 0;
+  fft_radices(H.N, pl);
+  CU(launch_fft_twiddles(c->d_tw, H.N, c->stream));
+  ++c->launches;
   for (int i = 0; i < nl; ++i) {
     const int l = lats[i];
-    CU(launch_to_complex(c->fp32, arr_ptr(c, l, c->parity, a), F, c->lats[l].V, c->stream));
-    ++c->launches;
-    s = fft3d(c, H.N, F, -1);
-    if (s != CL_OK) return s;
-    CU(launch_bins(F, H.N, dk_bin, nb, nblk, part, H.kIR, H.dx, bins + (size_t)i * 3 * nb, c->stream));
-    c->launches += 2;
+    CU(launch_real_spectrum(c->fp32, arr_ptr(c, l, c->parity, a), F, pl, dk_bin, nb, nblk, part, H.kIR, H.dx,
+                            bins + (size_t)i * 3 * nb, c->stream));
+    c->launches += 5;
   }
   CU(launch_spec_mean(bins, nl, nb, mean, c->stream));
   ++c->launches;

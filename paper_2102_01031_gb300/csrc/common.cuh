@@ -166,6 +166,8 @@ struct FftPlan {
   int rad[16];
   int batch;             // lines per CTA (a divisor of N)
   const double2* tw;     // tw[e] = exp(+2 pi i e/N), e < N
+  int pitch;             // x extent of the array in memory (N; N/2 + 1 for a half spectrum)
+  int nu;                // lines along the fastest other index (axes 1, 2: the columns kept, <= pitch)
 };
 
 // ---------------------------------------------------------------------------

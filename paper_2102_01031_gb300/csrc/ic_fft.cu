@@ -285,31 +285,10 @@ __global__ void fft_twiddle_kernel(double2* tw, int N) {
   tw[e] = make_double2(cs, sn);
 }
 
-__global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
-  extern __shared__ double2 fbuf[];
-  const int N = plan.N, B = plan.batch, Pt = N + 1;  // padded line pitch: no bank conflicts across lines
-  const int nt = blockDim.x, tid = threadIdx.x;
-  double2* a = fbuf;
-  double2* b = fbuf + B * Pt;
-  double2* w = fbuf + 2 * B * Pt;
-  const int ng = N / B;
-  const long long u0 = (long long)(blockIdx.x % ng) * B, ww = blockIdx.x / ng;
-  const long long NN = (long long)N * N;
-  for (int e = tid; e < N; e += nt) {
-    const double2 t = plan.tw[e];
-    w[e] = make_double2(t.x, plan.sign * t.y);
-  }
-  // element (line u, position j): axis 0: N (u + N w) + j; axis 1: u + N j + N^2 w;
-  // axis 2: u + N w + N^2 j
-  if (plan.axis == 0) {
-    const double2* src = data + NN * ww + N * u0;  // B whole rows, contiguous
-    for (int t = tid; t < B * N; t += nt) a[(t / N) * Pt + t % N] = src[t];
-  } else {
-    const long long base = plan.axis == 1 ? NN * ww + u0 : N * ww + u0;
-    const long long js = plan.axis == 1 ? N : NN;
-    for (int t = tid; t < B * N; t += nt) a[(t % B) * Pt + t / B] = data[base + (t / B) * js + t % B];
-  }
-  __syncthreads();
+// The Stockham stages on B lines held in shared memory (line pitch Pt), the
+// roots of unity in w; returns the buffer (a or b) that holds the result.
+__device__ double2* stockham_lines(double2* a, double2* b, const double2* w, const FftPlan& plan, int B, int Pt) {
+  const int N = plan.N, nt = blockDim.x, tid = threadIdx.x;
   int Ns = 1;
   for (int s = 0; s < plan.nrad; ++s) {
     const int R = plan.rad[s];
@@ -359,14 +338,146 @@ __global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
     b = t;
     Ns = L;
   }
+  return a;
+}
+
+__device__ __forceinline__ void load_roots(double2* w, const FftPlan& plan) {
+  for (int e = threadIdx.x; e < plan.N; e += blockDim.x) {
+    const double2 t = plan.tw[e];
+    w[e] = make_double2(t.x, plan.sign * t.y);
+  }
+}
+
+// Element (line u, position j) of an array of x extent P = plan.pitch:
+// axis 0: j + P (u + N w) (rows, P = N); axis 1: u + P (j + N w); axis 2: u + P (w + N j).
+// A CTA takes `batch` lines with consecutive u (and one w); lines with u >= nu are
+// not loaded or stored (the last group of a half spectrum's N/2 + 1 columns).
+__global__ void fft_lines_kernel(double2* data, const FftPlan plan) {
+  extern __shared__ double2 fbuf[];
+  const int N = plan.N, B = plan.batch, Pt = N + 1;  // padded line pitch: no bank conflicts across lines
+  const int nt = blockDim.x, tid = threadIdx.x;
+  double2* a = fbuf;
+  double2* b = fbuf + B * Pt;
+  double2* w = fbuf + 2 * B * Pt;
+  const int P = plan.pitch, nu = plan.nu;
+  const int ng = (nu + B - 1) / B;
+  const long long u0 = (long long)(blockIdx.x % ng) * B, ww = blockIdx.x / ng;
+  const long long PN = (long long)P * N;
+  load_roots(w, plan);
   if (plan.axis == 0) {
-    double2* dst = data + NN * ww + N * u0;
+    const double2* src = data + PN * ww + (long long)N * u0;  // B whole rows, contiguous
+    for (int t = tid; t < B * N; t += nt) a[(t / N) * Pt + t % N] = src[t];
+  } else {
+    const long long base = plan.axis == 1 ? PN * ww + u0 : (long long)P * ww + u0;
+    const long long js = plan.axis == 1 ? P : PN;
+    for (int t = tid; t < B * N; t += nt) {
+      const int l = t % B;
+      a[l * Pt + t / B] = u0 + l < nu ? data[base + (t / B) * js + l] : make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  a = stockham_lines(a, b, w, plan, B, Pt);
+  if (plan.axis == 0) {
+    double2* dst = data + PN * ww + (long long)N * u0;
     for (int t = tid; t < B * N; t += nt) dst[t] = a[(t / N) * Pt + t % N];
   } else {
-    const long long base = plan.axis == 1 ? NN * ww + u0 : N * ww + u0;
-    const long long js = plan.axis == 1 ? N : NN;
-    for (int t = tid; t < B * N; t += nt) data[base + (t / B) * js + t % B] = a[(t % B) * Pt + t / B];
+    const long long base = plan.axis == 1 ? PN * ww + u0 : (long long)P * ww + u0;
+    const long long js = plan.axis == 1 ? P : PN;
+    for (int t = tid; t < B * N; t += nt) {
+      const int l = t % B;
+      if (u0 + l < nu) data[base + (t / B) * js + l] = a[l * Pt + t / B];
+    }
   }
+}
+
+// Real-to-complex transform along x of a real N^3 field f into the half
+// spectrum H (x extent N/2 + 1, element kx + (N/2 + 1)(y + N z)): rows 2p and
+// 2p + 1 (the same z, y even and odd) are transformed together as the complex
+// row f_2p + i f_2p+1, Z = X_a + i X_b, and separated by the Hermitian symmetry
+// of real transforms: X_a(k) = (Z(k) + Z^*(N-k))/2, X_b(k) = (Z(k) - Z^*(N-k))/(2i),
+// for k = 0 .. N/2.  A CTA takes `batch` row pairs.
+template <typename T>
+__global__ void rfft_rows_kernel(const T* f, double2* H, const FftPlan plan) {
+  extern __shared__ double2 fbuf[];
+  const int N = plan.N, B = plan.batch, Pt = N + 1, NH = N / 2 + 1;
+  const int nt = blockDim.x, tid = threadIdx.x;
+  double2* a = fbuf;
+  double2* b = fbuf + B * Pt;
+  double2* w = fbuf + 2 * B * Pt;
+  const long long p0 = (long long)blockIdx.x * B;  // first row pair of the CTA
+  load_roots(w, plan);
+  const T* src = f + 2 * p0 * N;  // 2B whole rows, contiguous
+  for (int t = tid; t < 2 * B * N; t += nt) {
+    const int row = t / N, j = t % N;
+    double* slot = reinterpret_cast<double*>(&a[(row >> 1) * Pt + j]);
+    slot[row & 1] = (double)src[t];
+  }
+  __syncthreads();
+  a = stockham_lines(a, b, w, plan, B, Pt);
+  for (int t = tid; t < B * NH; t += nt) {
+    const int l = t / NH, k = t % NH;
+    const double2 Z = a[l * Pt + k], Y = a[l * Pt + (k == 0 ? 0 : N - k)];  // Y = Z(N - k)
+    const double2 Xa = make_double2(0.5 * (Z.x + Y.x), 0.5 * (Z.y - Y.y));
+    const double2 Xb = make_double2(0.5 * (Z.y + Y.y), 0.5 * (Y.x - Z.x));
+    const long long ra = 2 * (p0 + l);
+    H[ra * NH + k] = Xa;
+    H[(ra + 1) * NH + k] = Xb;
+  }
+}
+
+// Shell sums of a half spectrum H (as rfft_rows_kernel writes it, all three
+// axes transformed): each kept mode stands for itself and, for 0 < kx < N/2,
+// for its conjugate partner (-kx, -ky, -kz) with the same |F|^2 and |n|, so it
+// counts twice.  Runs of equal bins along kx are summed before the atomics.
+__global__ void bin_half_kernel(const double2* H, int N, double dk, int nb, double* part) {
+  extern __shared__ double sb[];
+  double* sp = sb;
+  double* sn = sb + nb;
+  double* sc = sb + 2 * nb;
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  constexpr int CH = 8;
+  const int NH = N / 2 + 1, nchr = (NH + CH - 1) / CH;
+  const long long nch = (long long)N * N * nchr;
+  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < nch;
+       ch += (long long)gridDim.x * blockDim.x) {
+    const long long row = ch / nchr;
+    const int x0 = (int)(ch % nchr) * CH;
+    const int y = (int)(row % N), z = (int)(row / N);
+    const int ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+    const int c2 = ny * ny + nz * nz;
+    int cur = -1;
+    double rp = 0.0, rn = 0.0, rc = 0.0;
+    const int x1 = x0 + CH < NH ? x0 + CH : NH;
+    for (int kx = x0; kx < x1; ++kx) {
+      const int m2 = kx * kx + c2;
+      if (m2 == 0) continue;  // the zero mode is in no bin
+      const double nn = sqrt((double)m2);
+      int bb = (int)floor(nn / dk);
+      if (bb >= nb) bb = nb - 1;
+      if (bb != cur) {
+        if (cur >= 0) {
+          atomicAdd(&sp[cur], rp);
+          atomicAdd(&sn[cur], rn);
+          atomicAdd(&sc[cur], rc);
+        }
+        cur = bb;
+        rp = rn = rc = 0.0;
+      }
+      const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+      const double2 v = H[row * NH + kx];
+      rp += wgt * (v.x * v.x + v.y * v.y);
+      rn += wgt * nn;
+      rc += wgt;
+    }
+    if (cur >= 0) {
+      atomicAdd(&sp[cur], rp);
+      atomicAdd(&sn[cur], rn);
+      atomicAdd(&sc[cur], rc);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 3 * nb + i] = sb[i];
 }
 
 template <typename T>
@@ -442,7 +553,10 @@ __global__ void combine_to_complex_kernel(const T* x, double cx, const T* y, dou
 }
 
 // Shell binning of |F(n)|^2, bins b = floor(|n|/dk) over n != 0.  Each block
-// accumulates in shared memory and writes its own partial row (3 x nb).
+// accumulates in shared memory and writes its own partial row (3 x nb).  A
+// thread takes 8 consecutive sites of one x-row (N is a multiple of 8) and
+// sums a run of sites in one bin in registers before its shared-memory atomics
+// (along a row |n| changes slowly, so runs are usually longer than one).
 __global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, double* part) {
   extern __shared__ double sb[];
   double* sp = sb;
@@ -450,19 +564,44 @@ __global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, d
   double* sc = sb + 2 * nb;
   for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) sb[i] = 0.0;
   __syncthreads();
-  const long long V = (long long)N * N * N;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < V;
-       idx += (long long)gridDim.x * blockDim.x) {
-    if (idx == 0) continue;
-    const int x = (int)(idx % N), y = (int)((idx / N) % N), z = (int)(idx / ((long long)N * N));
-    const int nx = x <= N / 2 ? x : x - N, ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
-    const double nn = sqrt((double)(nx * nx + ny * ny + nz * nz));
-    int b = (int)floor(nn / dk);
-    if (b >= nb) b = nb - 1;
-    const double2 v = F[idx];
-    atomicAdd(&sp[b], v.x * v.x + v.y * v.y);
-    atomicAdd(&sn[b], nn);
-    atomicAdd(&sc[b], 1.0);
+  constexpr int CH = 8;
+  const long long NN = (long long)N * N, nch = NN * N / CH;
+  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < nch;
+       ch += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = ch * CH;
+    const int x0 = (int)(i0 % N), y = (int)((i0 / N) % N), z = (int)(i0 / NN);
+    const int ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+    const int c2 = ny * ny + nz * nz;
+    int cur = -1;
+    double rp = 0.0, rn = 0.0, rc = 0.0;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int x = x0 + k;
+      const int nx = x <= N / 2 ? x : x - N;
+      const int m2 = nx * nx + c2;
+      if (m2 == 0) continue;  // the zero mode is in no bin
+      const double nn = sqrt((double)m2);
+      int b = (int)floor(nn / dk);
+      if (b >= nb) b = nb - 1;
+      if (b != cur) {
+        if (cur >= 0) {
+          atomicAdd(&sp[cur], rp);
+          atomicAdd(&sn[cur], rn);
+          atomicAdd(&sc[cur], rc);
+        }
+        cur = b;
+        rp = rn = rc = 0.0;
+      }
+      const double2 v = F[i0 + k];
+      rp += v.x * v.x + v.y * v.y;
+      rn += nn;
+      rc += 1.0;
+    }
+    if (cur >= 0) {
+      atomicAdd(&sp[cur], rp);
+      atomicAdd(&sn[cur], rn);
+      atomicAdd(&sc[cur], rc);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 3 * nb + i] = sb[i];
@@ -566,8 +705,41 @@ cudaError_t launch_fft_axis(double2* data, const FftPlan& pl, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int work = pl.batch * pl.N / 4;
   const int threads = work < 64 ? 64 : (work > 512 ? 512 : (work + 31) / 32 * 32);
-  const unsigned grid = (unsigned)((long long)pl.N * pl.N / pl.batch);
+  const long long ng = pl.axis == 0 ? pl.N / pl.batch : (pl.nu + pl.batch - 1) / pl.batch;
+  const unsigned grid = (unsigned)(ng * pl.N);
   fft_lines_kernel<<<grid, threads, fft_smem_bytes(pl.N), st>>>(data, pl);
+  return cudaGetLastError();
+}
+
+// Binned spectrum of a real field through the half spectrum: x-axis transform of
+// row pairs, y and z transforms of the N/2 + 1 columns kept, shell sums with the
+// conjugate partners counted, then eq. discretePS per bin (as launch_bins).
+// H holds (N/2 + 1) N^2 complex values; pl is the forward plan of N (tw set).
+cudaError_t launch_real_spectrum(int fp32, const void* f, double2* H, const FftPlan& pl, double dk, int nb,
+                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st) {
+  const int N = pl.N;
+  cudaError_t e;
+  const void* kern = fp32 ? (const void*)rfft_rows_kernel<float> : (const void*)rfft_rows_kernel<double>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem_bytes(N));
+  if (e != cudaSuccess) return e;
+  const int work = pl.batch * N / 4;
+  const int threads = work < 64 ? 64 : (work > 512 ? 512 : (work + 31) / 32 * 32);
+  const unsigned grid = (unsigned)((long long)N * N / 2 / pl.batch);
+  if (fp32) rfft_rows_kernel<float><<<grid, threads, fft_smem_bytes(N), st>>>((const float*)f, H, pl);
+  else rfft_rows_kernel<double><<<grid, threads, fft_smem_bytes(N), st>>>((const double*)f, H, pl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  FftPlan ph = pl;
+  ph.pitch = ph.nu = N / 2 + 1;
+  for (int axis = 1; axis < 3; ++axis) {
+    ph.axis = axis;
+    e = launch_fft_axis(H, ph, st);
+    if (e != cudaSuccess) return e;
+  }
+  bin_half_kernel<<<nblk, 256, 3 * nb * sizeof(double), st>>>(H, N, dk, nb, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  bin_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, kIR, dx, N, out, out + nb, out + 2 * nb, 0);
   return cudaGetLastError();
 }
 
