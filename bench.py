@@ -44,7 +44,7 @@ PASSES_PER_STEP = 3
 # DRAM bytes (read + write) per DK pass from one ncu capture of the FP32 pass
 # at 256^3 (one cooperative launch of the three VV4 passes of a step, divided
 # by 3), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "28d4993f1604ce49", "bytes_per_launch": 503003051}}
+NCU_TRAFFIC = {"f32": {"source_hash": "817056deb08b6e20", "bytes_per_launch": 502899797}}
 # FP64 instructions (DFMA, DADD, DMUL) and operations (FMA = 2) per site per pass
 # of the FP64 plain kernel, from one ncu capture of the instruction counters of
 # the FP64 pass at 256^3
@@ -55,7 +55,7 @@ NCU_FP64_OPS = {"source_hash": "28d4993f1604ce49", "instructions_per_site_pass":
 # Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
 # (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture,
 # valid for the kernel source it was taken on.
-NCU_SU2 = {"source_hash": "2a13872a7d1fab04", "thread_instructions_per_site": 2049.4,
+NCU_SU2 = {"source_hash": "1a0743229efd6379", "thread_instructions_per_site": 2051.3,
            "dram_bytes_per_site": 280.1}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
@@ -650,12 +650,14 @@ def other_workloads(P, torch, stream, peak):
         t_spec = (time.perf_counter() - t0) / reps
         lat.close()
         sites = N_LAT ** 3
-        gbs = sites * 132 / t_spec / 1e9
+        gbs = sites * 52 / t_spec / 1e9
         out["ics_and_spectrum_256_fp32"] = {
-            "init_s": t_init, "spectrum_ms": t_spec * 1e3, "model_bytes_per_site": 132,
+            "init_s": t_init, "spectrum_ms": t_spec * 1e3, "model_bytes_per_site": 52,
             "spectrum_gbs": gbs, "frac_hbm": gbs / peak,
-            "note": "host wall time; 132 B/site = complex conversion 20 + three FFT axis passes 96 + "
-                    "shell sums 16; includes the call's read-back and synchronisation"}
+            "note": "host wall time; 52 B/site through the half spectrum = the FP32 field read 4 + the half "
+                    "spectrum written 8 by the x-axis transform + y and z axis passes 16 each + shell sums 8; "
+                    "includes the call's read-back and synchronisation; the transform is bound by its FP64 "
+                    "butterflies, not by memory"}
     except Exception as e:  # noqa: BLE001
         out["ics_and_spectrum_256_fp32"] = {"error": str(e)[:300]}
     return out
