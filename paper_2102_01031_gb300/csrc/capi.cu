@@ -52,7 +52,10 @@ cudaError_t launch_ic_assemble(int, void*, void*, const double2*, const double2*
 cudaError_t launch_fft_axis(double2*, const FftPlan&, cudaStream_t);
 cudaError_t launch_fft_twiddles(double2*, int, cudaStream_t);
 cudaError_t launch_real_spectrum(int fp32, const void* f, double2* H, const FftPlan& pl, double dk, int nb,
-                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st);
+                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st,
+                                 const int* bin_of, const double* geo);
+cudaError_t launch_shell_geometry(int N, double dk, int nb, int nblk, int* bin_of, double* geo, double* part,
+                                  cudaStream_t st);
 int fft_batch(int N);
 cudaError_t launch_to_complex(int, const void*, double2*, long long, cudaStream_t);
 cudaError_t launch_bins(const double2*, int, double, int, int, double*, double, double, double*,
@@ -148,6 +151,10 @@ struct cl_ctx {
   double2* d_tw = nullptr;         // FFT twiddle table (the largest lattice's N entries)
   double* d_spec = nullptr;        // spectrum scratch: block rows (3 x 2048 x nblk), per-lattice bins, mean
   int spec_lats = 0;               // lattices d_spec has room for
+  int* d_bin_of = nullptr;         // cached shell geometry of (geo_N, geo_dk): bin of each |n|^2,
+  double* d_geo = nullptr;         //   sum of |n| and count per bin (2 x 2048)
+  int geo_N = 0;
+  double geo_dk = 0.0;
   unsigned* d_gsync = nullptr;     // arrival counters of multi-pass launches
   bool coop = false;               // multi-pass cooperative launches possible
   bool graphs = true;              // record multi-pass launches in CUDA graphs
@@ -710,6 +717,8 @@ cl_status cl_free(cl_ctx* c) {
   cudaFree(c->d_cplx);
   cudaFree(c->d_tw);
   cudaFree(c->d_spec);
+  cudaFree(c->d_bin_of);
+  cudaFree(c->d_geo);
   cudaFree(c->d_gsync);
   cudaFree(c->adj.lam);
   cudaFree(c->adj.d_lat);
@@ -1414,10 +1423,22 @@ cl_status cl_ensemble_spectrum(cl_ctx* c, const int* lats, int nl, int field, in
   fft_radices(H.N, pl);
   CU(launch_fft_twiddles(c->d_tw, H.N, c->stream));
   ++c->launches;
+  if (c->geo_N != H.N || c->geo_dk != dk_bin) {  // the shells of (N, dk_bin), kept for later calls
+    CU(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_bin_of);
+    c->d_bin_of = nullptr;
+    c->geo_N = 0;
+    if (!c->d_geo) CU(cudaMalloc(&c->d_geo, 2 * 2048 * sizeof(double)));
+    CU(cudaMalloc(&c->d_bin_of, ((size_t)3 * (H.N / 2) * (H.N / 2) + 1) * sizeof(int)));
+    CU(launch_shell_geometry(H.N, dk_bin, nb, nblk, c->d_bin_of, c->d_geo, part, c->stream));
+    c->launches += 3;
+    c->geo_N = H.N;
+    c->geo_dk = dk_bin;
+  }
   for (int i = 0; i < nl; ++i) {
     const int l = lats[i];
     CU(launch_real_spectrum(c->fp32, arr_ptr(c, l, c->parity, a), F, pl, dk_bin, nb, nblk, part, H.kIR, H.dx,
-                            bins + (size_t)i * 3 * nb, c->stream));
+                            bins + (size_t)i * 3 * nb, c->stream, c->d_bin_of, c->d_geo));
     c->launches += 5;
   }
   CU(launch_spec_mean(bins, nl, nb, mean, c->stream));

@@ -607,6 +607,116 @@ __global__ void bin_partial_kernel(const double2* F, int N, double dk, int nb, d
   for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 3 * nb + i] = sb[i];
 }
 
+// Shell geometry of a lattice size and bin width, cached by the caller: the bin
+// of every |n|^2 up to 3 (N/2)^2 (-1 for the zero mode), and per bin the mode
+// count and the sum of |n| over all N^3 - 1 modes (partial rows per block,
+// summed by geo_final_kernel in a fixed order).
+__global__ void geo_table_kernel(int* bin_of, int m2max, double dk, int nb) {
+  for (int m2 = blockIdx.x * blockDim.x + threadIdx.x; m2 <= m2max; m2 += gridDim.x * blockDim.x) {
+    int b = -1;
+    if (m2 > 0) {
+      b = (int)floor(sqrt((double)m2) / dk);
+      if (b >= nb) b = nb - 1;
+    }
+    bin_of[m2] = b;
+  }
+}
+
+__global__ void geo_partial_kernel(const int* bin_of, int N, int nb, double* part) {
+  extern __shared__ double sb[];
+  double* sn = sb;
+  double* sc = sb + nb;
+  for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  const long long NN = (long long)N * N;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < NN; r += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(r % N), z = (int)(r / N);
+    const int ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+    for (int x = 0; x < N; ++x) {  // one whole row per thread (this runs once per lattice size and bin width)
+      const int nx = x <= N / 2 ? x : x - N;
+      const int m2 = nx * nx + ny * ny + nz * nz;
+      const int b = bin_of[m2];
+      if (b < 0) continue;
+      atomicAdd(&sn[b], sqrt((double)m2));
+      atomicAdd(&sc[b], 1.0);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * nb; i += blockDim.x) part[(size_t)blockIdx.x * 2 * nb + i] = sb[i];
+}
+
+__global__ void geo_final_kernel(const double* part, int nblk, int nb, double* geo) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double sn = 0.0, sc = 0.0;
+  for (int i = 0; i < nblk; ++i) {
+    sn += part[(size_t)i * 2 * nb + b];
+    sc += part[(size_t)i * 2 * nb + nb + b];
+  }
+  geo[b] = sn;
+  geo[nb + b] = sc;
+}
+
+// Shell sums of |F|^2 of a half spectrum with the cached bins: each kept mode
+// counts twice for 0 < kx < N/2 (its conjugate partner), runs of equal bins
+// along kx are summed before the atomic.  Partial rows of nb per block.
+__global__ void bin_power_half_kernel(const double2* H, const int* bin_of, int N, int nb, double* part) {
+  extern __shared__ double sb[];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) sb[i] = 0.0;
+  __syncthreads();
+  constexpr int CH = 8;
+  const int NH = N / 2 + 1, nchr = (NH + CH - 1) / CH;
+  const long long nch = (long long)N * N * nchr;
+  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < nch;
+       ch += (long long)gridDim.x * blockDim.x) {
+    const long long row = ch / nchr;
+    const int x0 = (int)(ch % nchr) * CH;
+    const int y = (int)(row % N), z = (int)(row / N);
+    const int ny = y <= N / 2 ? y : y - N, nz = z <= N / 2 ? z : z - N;
+    const int c2 = ny * ny + nz * nz;
+    const int x1 = x0 + CH < NH ? x0 + CH : NH;
+    int cur = -1;
+    double rp = 0.0;
+    for (int kx = x0; kx < x1; ++kx) {
+      const int b = bin_of[kx * kx + c2];
+      if (b < 0) continue;
+      if (b != cur) {
+        if (cur >= 0) atomicAdd(&sb[cur], rp);
+        cur = b;
+        rp = 0.0;
+      }
+      const double2 v = H[row * NH + kx];
+      rp += ((kx == 0 || kx == N / 2) ? 1.0 : 2.0) * (v.x * v.x + v.y * v.y);
+    }
+    if (cur >= 0) atomicAdd(&sb[cur], rp);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) part[(size_t)blockIdx.x * nb + i] = sb[i];
+}
+
+// eq. discretePS per bin from the power rows and the cached geometry (as bin_final_kernel).
+__global__ void bin_final_geo_kernel(const double* part, int nblk, int nb, const double* geo, double kIR, double dx,
+                                     int N, double* k, double* delta, double* mult) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double sp = 0.0;
+  for (int i = 0; i < nblk; ++i) sp += part[(size_t)i * nb + b];
+  const double sn = geo[b], sc = geo[nb + b];
+  if (sc == 0.0) {
+    k[b] = 0.0;
+    delta[b] = 0.0;
+    mult[b] = 0.0;
+    return;
+  }
+  const double nbar = sn / sc;
+  const double kb = kIR * nbar;
+  const double fac = pow(dx / (double)N, 3.0);
+  const double pi = 3.14159265358979323846;
+  k[b] = kb;
+  delta[b] = kb * kb * kb / (2.0 * pi * pi) * fac * sp / (4.0 * pi * nbar * nbar);
+  mult[b] = sc;
+}
+
 // Sum the block rows in a fixed order and form eq. discretePS per bin (raw:
 // the shell sum of |F|^2 instead of delta_b).
 __global__ void bin_final_kernel(const double* part, int nblk, int nb, double kIR, double dx, int N,
@@ -715,8 +825,24 @@ cudaError_t launch_fft_axis(double2* data, const FftPlan& pl, cudaStream_t st) {
 // row pairs, y and z transforms of the N/2 + 1 columns kept, shell sums with the
 // conjugate partners counted, then eq. discretePS per bin (as launch_bins).
 // H holds (N/2 + 1) N^2 complex values; pl is the forward plan of N (tw set).
+// The shell geometry of (N, dk) into bin_of (3 (N/2)^2 + 1 ints) and geo (2 nb
+// doubles: the sum of |n| and the count per bin); part holds 2 nb nblk doubles.
+cudaError_t launch_shell_geometry(int N, double dk, int nb, int nblk, int* bin_of, double* geo, double* part,
+                                  cudaStream_t st) {
+  const int m2max = 3 * (N / 2) * (N / 2);
+  geo_table_kernel<<<(m2max + 256) / 256, 256, 0, st>>>(bin_of, m2max, dk, nb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  geo_partial_kernel<<<nblk, 128, 2 * nb * sizeof(double), st>>>(bin_of, N, nb, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  geo_final_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, geo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_real_spectrum(int fp32, const void* f, double2* H, const FftPlan& pl, double dk, int nb,
-                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st) {
+                                 int nblk, double* part, double kIR, double dx, double* out, cudaStream_t st,
+                                 const int* bin_of, const double* geo) {
   const int N = pl.N;
   cudaError_t e;
   const void* kern = fp32 ? (const void*)rfft_rows_kernel<float> : (const void*)rfft_rows_kernel<double>;
@@ -735,6 +861,14 @@ cudaError_t launch_real_spectrum(int fp32, const void* f, double2* H, const FftP
     ph.axis = axis;
     e = launch_fft_axis(H, ph, st);
     if (e != cudaSuccess) return e;
+  }
+  if (bin_of && geo) {  // the cached shell geometry: only the power is summed
+    bin_power_half_kernel<<<nblk, 256, nb * sizeof(double), st>>>(H, bin_of, N, nb, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bin_final_geo_kernel<<<(nb + 127) / 128, 128, 0, st>>>(part, nblk, nb, geo, kIR, dx, N, out, out + nb,
+                                                            out + 2 * nb);
+    return cudaGetLastError();
   }
   bin_half_kernel<<<nblk, 256, 3 * nb * sizeof(double), st>>>(H, N, dk, nb, part);
   e = cudaGetLastError();
