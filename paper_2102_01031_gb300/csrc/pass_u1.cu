@@ -63,8 +63,7 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 // order of operations on every value is the same; it needs the drift
 // coefficient before the pass's sums are known, so it is taken when a(eta)
 // does not depend on them (no expansion), and saves every neighbour read its
-// momentum load and drift; the momenta are then read at the own sites only, so
-// the stages hold them without halo rows (four stages fit instead of three).
+// momentum load and drift.
 // NC: 0 = lattice size and tile height from the lattice constants; > 0 = the
 // kernel is built for N = NC with full tiles of THREADS threads (every stage
 // offset a compile-time constant).
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
 
   for (int pass = 0; pass < P.npass; ++pass) {
     const int parity = P.parity ^ (pass & 1);
-    if (warp == 0) ring_pass_start<T, NAR, KD>(R, P, pass, ptot, parity, lane);
+    if (warp == 0) ring_pass_start<T, NAR>(R, P, pass, ptot, parity, lane);
     __syncthreads();
     if (R.flag[0]) goto timeout;
 
@@ -109,8 +108,6 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const int x0 = tx * VX;
       const int y = sg.ytile * BY + ty;
       const int ae = (BY + 2) * N;  // elements of one array in a stage
-      // stage offset of array a: KD keeps (field, momentum) pairs of BY + 2 and BY rows
-      auto aoff = [&](int a) { return KD ? (a >> 1) * (2 * BY + 2) * N + (a & 1) * ae : a * ae; };
       const long long NN = (long long)N * N;
       const int g0 = R.off[i];
       // coefficients of the segment: FP64 products formed by one lane (the
@@ -152,17 +149,17 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
 
       // drifted vector of field array a (its momentum is a + 1) on stage row `row`
       auto rdv = [&](const T* st, int a, int row, T coef, T (&o)[VX]) {
-        ldv<T>(o, st + aoff(a) + row * N + x0);
+        ldv<T>(o, st + a * ae + row * N + x0);
         if (drifting) {
           T m[VX];
-          ldv<T>(m, st + aoff(a + 1) + row * N + x0);
+          ldv<T>(m, st + (a + 1) * ae + row * N + x0);
 #pragma unroll
           for (int v = 0; v < VX; ++v) o[v] = fmaT(coef, m[v], o[v]);
         }
       };
       auto rds = [&](const T* st, int a, int row, int x, T coef) -> T {
-        const T f = st[aoff(a) + row * N + x];
-        return drifting ? fmaT(coef, st[aoff(a + 1) + row * N + x], f) : f;
+        const T f = st[a * ae + row * N + x];
+        return drifting ? fmaT(coef, st[(a + 1) * ae + row * N + x], f) : f;
       };
       // value at x0 - 1 (x0 + VX) of a row, read from the stage and drifted like
       // the owning thread's own copy (no shuffles: every lane reads its own
@@ -193,7 +190,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
           sincos_t(gd * azm[v], bSz[v], bCz[v]);
         }
       }
-      ring_release<T, NAR, KD>(R, g0, s_cur, parity, ptot, lane);
+      ring_release<T, NAR>(R, g0, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) {
@@ -250,8 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             T sxl, cxl;
             sincos_t(gd * ax_l, sxl, cxl);
             T p0[VX], p1[VX], pn0[VX], pn1[VX];
-            ldv<T>(p0, sc + aoff(P0) + own - (KD ? N : 0));
-            ldv<T>(p1, sc + aoff(P1) + own - (KD ? N : 0));
+            ldv<T>(p0, sc + P0 * ae + own);
+            ldv<T>(p1, sc + P1 * ae + own);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
               const T f0 = cF[0][v], f1 = cF[1][v];
@@ -336,9 +333,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             const T az_r = right(sc, AZ, ty + 1, cdA);
             const T ayym_r = right(sc, AY, ty, cdA);
             T pax[VX], pay[VX], paz[VX], pnx[VX], pny[VX], pnz[VX], pxy[VX];
-            ldv<T>(pax, sc + aoff(PAX) + own - (KD ? N : 0));
-            ldv<T>(pay, sc + aoff(PAY) + own - (KD ? N : 0));
-            ldv<T>(paz, sc + aoff(PAZ) + own - (KD ? N : 0));
+            ldv<T>(pax, sc + PAX * ae + own);
+            ldv<T>(pay, sc + PAY * ae + own);
+            ldv<T>(paz, sc + PAZ * ae + own);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
               const T ax = cA[0][v], ay = cA[1][v], az = cA[2][v];
@@ -422,12 +419,12 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             bSyz[v] = pyz[v];
           }
         }
-        ring_release<T, NAR, KD>(R, g0 + j, s_cur, parity, ptot, lane);
+        ring_release<T, NAR>(R, g0 + j, s_cur, parity, ptot, lane);
         s_cur = s_nxt;
         p_cur = p_nxt;
         ring_advance(S, s_nxt, p_nxt);
       }
-      ring_release<T, NAR, KD>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
+      ring_release<T, NAR>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
 
       if (!sg.flush) continue;
