@@ -176,7 +176,7 @@ constexpr int SU2_TY = 8;  // tile height of the pass; the width TX (32 or 16) i
 //   pi_c   (doublet) gains - a^{3+alpha} (qG phi_s^2 + 2 qH |vphi|^2) phi_c
 //   pi_A,i gains a^{1+alpha} (f_s/omega_s)^2 Qc (gQ/dx) (vphi_0 u_1 - vphi_1 u_0), u = its hop.
 template <typename T, int RED, int TX, bool FULL>
-__global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8 || FULL) ? 1 : 2) dk_pass_su2(const PassArgs P) {
+__global__ void __launch_bounds__(256, (RED == 2 || sizeof(T) == 8) ? 1 : 2) dk_pass_su2(const PassArgs P) {
   constexpr int NACC = RED == 0 ? 1 : (RED == 1 ? 6 : (FULL ? 29 : 23));
   constexpr int NLD = FULL ? SNARR_FULL : SNARR;  // arrays loaded per halo site
   extern __shared__ __align__(128) unsigned char smem[];
