@@ -37,6 +37,8 @@ PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256);
 PassKernel su2_pass_kernel(int fp32, int red, int TX, int full);
 size_t su2_smem_bytes(int TX, int TY, int esz, int full);
+PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int full);
+size_t su2_kd_smem_bytes(int TX, int esz, int full);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
 cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
                            cudaStream_t st);
@@ -164,6 +166,7 @@ struct cl_ctx {
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
+  size_t smem_kd = 0;               // doublet model: dynamic shared memory of the kick-then-drift passes
   int su2_tx = 0, su2_ty = 0;      // doublet model: CTA tile (x, y) of the pass
   // schedule state
   int parity = 0;
@@ -293,8 +296,16 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
   return CL_OK;
 }
 
+// Doublet models without expansion: kick-then-drift passes (pass_su2_kd.cu),
+// which take no Friedmann sums (RED 1 only arises with expansion).
+bool su2_kd(const cl_ctx* c, int red) { return c->p.expansion == CL_EXP_OFF && red != 1; }
+
 PassKernel pick_kernel(const cl_ctx* c, int red) {
-  if (is_doublet(c->model)) return su2_pass_kernel(c->fp32, red, c->su2_tx, c->model == CL_MODEL_LPHI4_SU2U1);
+  if (is_doublet(c->model)) {
+    const int full = c->model == CL_MODEL_LPHI4_SU2U1;
+    if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, full);
+    return su2_pass_kernel(c->fp32, red, c->su2_tx, full);
+  }
   // without expansion the U(1) passes drift right after their kick (the drift
   // coefficient does not wait for the pass's sums)
   if (c->model == CL_MODEL_U1_HIGGS) {
@@ -516,7 +527,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
       A.dnext = st[i].dnext;
       A.parity = c->parity ^ (write ? (i & 1) : 0);
       A.log_base = log_base + i;
-      if (su2) k<<<c->grid, dim3(c->su2_tx, c->su2_ty), c->smem_bytes, c->stream>>>(A);
+      if (su2) k<<<c->grid, dim3(c->su2_tx, c->su2_ty), su2_kd(c, red) ? c->smem_kd : c->smem_bytes, c->stream>>>(A);
       else k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
       CHECK_LAUNCH();
     }
@@ -1044,14 +1055,32 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   c->su2_ty = 8;
   const int full = c->model == CL_MODEL_LPHI4_SU2U1;
   c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz, full);
-  if (c->smem_bytes > c->smem_optin) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
-  for (int red = 0; red < 3; ++red)
+  c->smem_kd = su2_kd_smem_bytes(c->su2_tx, c->esz, full);
+  if (std::max(c->smem_bytes, c->smem_kd) > c->smem_optin)
+    return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
+  for (int red = 0; red < 3; ++red) {
     CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red, c->su2_tx, full),
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_bytes));
+    if (red != 1) {
+      const void* kk = (const void*)su2_kd_pass_kernel(c->fp32, red, c->su2_tx, full);
+      CU(cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_kd));
+      // the smallest shared-memory carve-out that holds the resident CTAs, so that
+      // the rest of the SM's storage caches the momenta the pass prefetches into L1
+      cudaFuncAttributes fa;
+      CU(cudaFuncGetAttributes(&fa, kk));
+      int smax = 0;
+      CU(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->dev));
+      const int per_cta = (int)(c->smem_kd + fa.sharedSizeBytes) + 1024;
+      const int by_regs = 65536 / std::max(1, fa.numRegs * c->su2_tx * c->su2_ty);
+      const int ctas = std::max(1, std::min(smax / per_cta, by_regs));
+      const int pct = std::min(100, (int)((100LL * ctas * per_cta + smax - 1) / smax));
+      CU(cudaFuncSetAttribute(kk, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
+  }
   int nb = 0;
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, (const void*)su2_pass_kernel(c->fp32, red_for_step(c), c->su2_tx, full), c->su2_tx * c->su2_ty,
-      c->smem_bytes));
+  const int rs = red_for_step(c);
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)pick_kernel(c, rs), c->su2_tx * c->su2_ty,
+                                                   su2_kd(c, rs) ? c->smem_kd : c->smem_bytes));
   // work items (tile, z-chunk) over the resident CTAs (su2_work.h)
   const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);
   const int R = c->nsm * std::max(nb, 1);
