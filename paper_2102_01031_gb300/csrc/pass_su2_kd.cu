@@ -22,15 +22,15 @@
 // refills it with the plane three ahead.
 //
 // Each plaquette is formed once per site (xy, xz, yz at n) and serves the
-// staples of its four links: directly for the two links at n (P and P^dag),
-// rotated by a link for the two links it reaches from below,
-//     m(L_ij(n)) = m(U_j^dag(n-j) P_ij(n-j)^dag U_j(n-j)),
-// which site n - j forms and hands on: across x through a warp shuffle from
-// lane tx - 1, along z in registers to the thread's next plane.  The lower
-// staples across y (another warp) are formed directly.  The same goes for the
-// compact U(1) plaquette sines and for the backward hops W_i^dag(n-i) psi(n-i):
-// across x by shuffle, along z carried, across y direct.  The column tx = 0
-// forms what lane tx - 1 would have handed on from the stage's halo column.
+// staples of its links at n directly (P and P^dag); along z it also serves the
+// two links it reaches from below, rotated by a link,
+//     m(L_iz(n)) = m(U_z^dag(n-z) P_iz(n-z)^dag U_z(n-z)),
+// which the thread forms at plane z - 1 and carries to plane z in registers.
+// The lower staples across x and y are formed directly at each site (handing
+// them on between lanes would leave the tile's edge column to one lane of a
+// warp, which costs the whole warp the work).  The same goes for the compact
+// U(1) plaquette sines and the backward hops W_i^dag(n-i) psi(n-i): carried
+// along z, direct across x and y.
 #include "su2_common.cuh"
 
 namespace clg {
@@ -75,24 +75,6 @@ __device__ __forceinline__ V3<T> neg(const V3<T>& v) {
   r.y = -v.y;
   r.z = -v.z;
   return r;
-}
-
-template <int TX, typename T>
-__device__ __forceinline__ T shfl_up1(T v) {
-  return __shfl_up_sync(0xffffffffu, v, 1, TX);
-}
-template <int TX, typename T>
-__device__ __forceinline__ void shfl_up_q(Q4<T>& q) {
-  q.w = shfl_up1<TX>(q.w);
-  q.x = shfl_up1<TX>(q.x);
-  q.y = shfl_up1<TX>(q.y);
-  q.z = shfl_up1<TX>(q.z);
-}
-template <int TX, typename T>
-__device__ __forceinline__ void shfl_up_v(V3<T>& v) {
-  v.x = shfl_up1<TX>(v.x);
-  v.y = shfl_up1<TX>(v.y);
-  v.z = shfl_up1<TX>(v.z);
 }
 
 // Asynchronous copies global -> shared by each thread (cp.async): 16 bytes (both
@@ -395,17 +377,14 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
       const Q4<T> psi = ld4(C, KF, 0, 0);
       const T ax = ld(C, KA, 0, 0), ay = ld(C, KA + 1, 0, 0), az = ld(C, KA + 2, 0, 0);
 
-      // ---- compact U(1) plaquettes: sines at n, from n - x (lane tx - 1), n - y (direct), n - z (carried) ----
+      // ---- compact U(1) plaquettes: sines at n, at n - x and n - y (direct), at n - z (carried) ----
       const T txy = gd * ((ax + ld(C, KA + 1, 1, 0)) - (ld(C, KA, 0, 1) + ay));
       const T txz = gd * ((ax + ld(C, KA + 2, 1, 0)) - (ld(Pn, KA, 0, 0) + az));
       const T tyz = gd * ((ay + ld(C, KA + 2, 0, 1)) - (ld(Pn, KA + 1, 0, 0) + az));
       const T sxy = sin_t(txy), sxz = sin_t(txz), syz = sin_t(tyz);
-      T sxy_xm = shfl_up1<TX>(sxy), sxz_xm = shfl_up1<TX>(sxz);
-      if (tx == 0) {
-        const T axm = ld(C, KA, -1, 0);
-        sxy_xm = sin_t(gd * ((axm + ay) - (ld(C, KA, -1, 1) + ld(C, KA + 1, -1, 0))));
-        sxz_xm = sin_t(gd * ((axm + az) - (ld(Pn, KA, -1, 0) + ld(C, KA + 2, -1, 0))));
-      }
+      const T axm = ld(C, KA, -1, 0);
+      const T sxy_xm = sin_t(gd * ((axm + ay) - (ld(C, KA, -1, 1) + ld(C, KA + 1, -1, 0))));
+      const T sxz_xm = sin_t(gd * ((axm + az) - (ld(Pn, KA, -1, 0) + ld(C, KA + 2, -1, 0))));
       const T sxy_ym = sin_t(gd * ((ld(C, KA, 0, -1) + ld(C, KA + 1, 1, -1)) - (ax + ld(C, KA + 1, 0, -1))));
       const T syz_ym = sin_t(gd * ((ld(C, KA + 1, 0, -1) + az) - (ld(Pn, KA + 1, 0, -1) + ld(C, KA + 2, 0, -1))));
       const T Cc[3] = {(sxy - sxy_ym) + (sxz - c_sxz), (sxy_xm - sxy) + (syz - c_syz),
@@ -432,15 +411,10 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
                  (pxz.x * pxz.x + pxz.y * pxz.y + pxz.z * pxz.z) / (T(1) + qsca(Axz, Bxz)) +
                  (pyz.x * pyz.x + pyz.y * pyz.y + pyz.z * pyz.z) / (T(1) + qsca(Ayz, Byz));
         }
-        // lower staples of U_y(n), U_z(n) in the x planes: from site n - x
-        V3<T> ryx = rotc(Ux, pxy), rzx = rotc(Ux, pxz);
-        shfl_up_v<TX>(ryx);
-        shfl_up_v<TX>(rzx);
-        if (tx == 0) {
-          const Q4<T> uxm = ld4(C, KU, -1, 0);
-          ryx = qvec(qmul(Uy, qconj(qmul(ld4(C, KU + 4, -1, 0), ld4(C, KU, -1, 1)))), uxm);
-          rzx = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, -1, 0), ld4(Pn, KU, -1, 0)))), uxm);
-        }
+        // lower staples of U_y(n), U_z(n) in the x planes, directly
+        const Q4<T> uxm = ld4(C, KU, -1, 0);
+        const V3<T> ryx = qvec(qmul(Uy, qconj(qmul(ld4(C, KU + 4, -1, 0), ld4(C, KU, -1, 1)))), uxm);
+        const V3<T> rzx = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, -1, 0), ld4(Pn, KU, -1, 0)))), uxm);
         // lower staples of U_x(n), U_z(n) in the y planes, directly
         const Q4<T> uym = ld4(C, KU + 4, 0, -1);
         const V3<T> mxy = qvec(qmul(Ux, qconj(qmul(ld4(C, KU, 0, -1), ld4(C, KU + 4, 1, -1)))), uym);
@@ -487,22 +461,12 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
         Q4<T> chi = umul(Ui, fn);
         phase(chi, ci, si);
         qadd(D, chi);
-        // the backward hop W_i^dag(n) psi(n) of site n + i: across x to lane tx + 1, along z carried
-        if (i == 0) {
-          Q4<T> b = udmul(Ui, psi);
-          phase(b, ci, -si);
-          shfl_up_q<TX>(b);
-          if (tx == 0) {
-            T s, c;
-            sincos_t(gd * ld(C, KA, -1, 0), s, c);
-            b = udmul(ld4(C, KU, -1, 0), ld4(C, KF, -1, 0));
-            phase(b, c, -s);
-          }
-          qadd(D, b);
-        } else if (i == 1) {
+        // the backward hop W_i^dag(n-i) psi(n-i): across x and y directly; along z the
+        // thread's own W_z^dag(n) psi(n) is carried to plane z + 1
+        if (i < 2) {
           T s, c;
-          sincos_t(gd * ld(C, KA + 1, 0, -1), s, c);
-          Q4<T> b = udmul(ld4(C, KU + 4, 0, -1), ld4(C, KF, 0, -1));
+          sincos_t(gd * (i == 0 ? axm : ld(C, KA + 1, 0, -1)), s, c);
+          Q4<T> b = i == 0 ? udmul(ld4(C, KU, -1, 0), ld4(C, KF, -1, 0)) : udmul(ld4(C, KU + 4, 0, -1), ld4(C, KF, 0, -1));
           phase(b, c, -s);
           qadd(D, b);
         } else {
@@ -529,27 +493,18 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
           T sc2, cc;
           sincos_t(gdc * av[i], sc2, cc);
           const T u0 = cc * y0v + sc2 * y1v, u1 = cc * y1v - sc2 * y0v;
-          // backward hop Vc_i^*(n) vphi(n) of site n + i
-          T w0 = cc * xc0 - sc2 * xc1, w1 = cc * xc1 + sc2 * xc0;
-          if (i == 0) {
-            w0 = shfl_up1<TX>(w0);
-            w1 = shfl_up1<TX>(w1);
-            if (tx == 0) {
-              const T b0 = ld(C, KV, -1, 0), b1 = ld(C, KV + 1, -1, 0);
-              sincos_t(gdc * ld(C, KA, -1, 0), sc2, cc);
-              w0 = cc * b0 - sc2 * b1;
-              w1 = cc * b1 + sc2 * b0;
-            }
-            Dv0 += w0;
-            Dv1 += w1;
-          } else if (i == 1) {
-            const T b0 = ld(C, KV, 0, -1), b1 = ld(C, KV + 1, 0, -1);
-            sincos_t(gdc * ld(C, KA + 1, 0, -1), sc2, cc);
-            Dv0 += cc * b0 - sc2 * b1;
-            Dv1 += cc * b1 + sc2 * b0;
+          // backward hop Vc_i^*(n-i) vphi(n-i): across x and y directly; along z the
+          // thread's own Vc_z^*(n) vphi(n) is carried to plane z + 1
+          if (i < 2) {
+            const T b0 = i == 0 ? ld(C, KV, -1, 0) : ld(C, KV, 0, -1);
+            const T b1 = i == 0 ? ld(C, KV + 1, -1, 0) : ld(C, KV + 1, 0, -1);
+            T sb, cb;
+            sincos_t(gdc * (i == 0 ? axm : ld(C, KA + 1, 0, -1)), sb, cb);
+            Dv0 += cb * b0 - sb * b1;
+            Dv1 += cb * b1 + sb * b0;
           } else {
-            c_w0 = w0;
-            c_w1 = w1;
+            c_w0 = cc * xc0 - sc2 * xc1;
+            c_w1 = cc * xc1 + sc2 * xc0;
           }
           Dv0 += u0;
           Dv1 += u1;
