@@ -94,7 +94,7 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_committed() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Stage geometry: field array f of a stage holds HR = 10 rows (the tile's 8
 // and a halo row each side) of RW elements, from EPC = 16 B before the tile to
@@ -206,13 +206,15 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     const int chunk = it / ntiles;
     ptot += (chunk + 1) * N / nzc - chunk * N / nzc + 2;
   }
-  // Each thread copies the same 16-byte piece (column pc, row pr) of arrays
-  // pf0, pf0 + NSET, ... of every plane: pso, its offset in a plane of the lattice
-  // for the producer's current item (periodic in x and y).
-  constexpr int NSET = nth / G::CPA;
-  static_assert(NSET >= 1, "a CTA covers every piece of an array");
-  const bool pcopy = tid < NSET * G::CPA;
-  const int pf0 = tid / G::CPA, pr = (tid % G::CPA) / G::NCOL, pc = tid % G::NCOL;
+  // Each thread copies the same 16-byte piece (column pc, row pr) of a fixed set
+  // of arrays of every plane: with room for two sets, the CTA's two halves
+  // (warp-uniform) take the first and the second half of the arrays, else the
+  // first CPA threads take all of them.  pso: the piece's offset in a plane of the
+  // lattice for the producer's current item (periodic in x and y).
+  constexpr int NH = 2 * G::CPA <= nth ? 2 : 1, FPH = (NFA + NH - 1) / NH;
+  const int ph = tid / (nth / NH), pt = tid - ph * (nth / NH);
+  const bool pcopy = pt < G::CPA;
+  const int pr = pt / G::NCOL, pc = pt - pr * G::NCOL;
   // the producer's item (CTA-uniform): its z-chunk length and the plane the next
   // position copies (pzp) with its index in the item (pj)
   int pit = blockIdx.x, pnz = 0, pzp = 0, pj = 0;
@@ -231,23 +233,35 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     pso = (unsigned)(gy * N + gx);
   };
   producer_item();
-  // Every call closes one commit group (empty past the CTA's last plane), so that
-  // "all groups but the newest" always covers the momenta copied before it.
-  auto produce = [&]() {
-    if (pit >= nitems) {
-      cp_async_commit();
-      return;
-    }
+  // The copies of a position go out in two bursts (part 0, then part 1 later in
+  // the step, so that a thread's pieces do not queue up at once); after part 1
+  // the thread's arrival on the stage's full barrier (once all its copies have
+  // landed) and a commit group.
+  auto produce = [&](int part) {
+    if (pit >= nitems) return;
     const int s = produced % 3;
-    ++produced;
     if (pcopy) {
       T* const d = reinterpret_cast<T*>(smem + (size_t)s * G::STAGE) + pr * RW + pc * EPC;
       const T* const g = src + (size_t)((unsigned)pzp * (unsigned)NN + pso);
+      constexpr int H0 = FPH / 2, H1 = FPH + (NFA - FPH) / 2;
+      if (ph == 0 && part == 0) {
 #pragma unroll
-      for (int f = pf0; f < NFA; f += NSET) cp_async16(d + f * AE, g + (size_t)kd_state_array(f) * (size_t)V);
+        for (int f = 0; f < H0; ++f) cp_async16(d + f * AE, g + (size_t)kd_state_array(f) * (size_t)V);
+      } else if (ph == 0) {
+#pragma unroll
+        for (int f = H0; f < FPH; ++f) cp_async16(d + f * AE, g + (size_t)kd_state_array(f) * (size_t)V);
+      } else if (part == 0) {
+#pragma unroll
+        for (int f = FPH; f < H1; ++f) cp_async16(d + f * AE, g + (size_t)kd_state_array(f) * (size_t)V);
+      } else {
+#pragma unroll
+        for (int f = H1; f < NFA; ++f) cp_async16(d + f * AE, g + (size_t)kd_state_array(f) * (size_t)V);
+      }
     }
+    if (part == 0) return;
     cp_async_arrive(&full_bar[s]);
     cp_async_commit();
+    ++produced;
     pzp = pzp + 1 == N ? 0 : pzp + 1;
     if (++pj == pnz + 2) {
       pit += gridDim.x;
@@ -258,12 +272,12 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     if (tflag) return;
     if (!mbar_wait_bounded(bar, (uint32_t)(phase & 1), P.wait_limit_ns)) tflag = 1;
   };
-  // Step p works on positions p and p + 1: first the copies of position p + 2
-  // go out (into the stage position p - 1 held, once every warp is done with it).
+  // Step p works on positions p and p + 1: the copies of position p + 2 go out
+  // (into the stage position p - 1 held, once every warp is done with it), their
+  // first part at the step's beginning, the second (produce(1)) within the step.
   auto step_begin = [&](int p) {
     if (p >= 1) wait_bar(&empty_bar[(p - 1) % 3], (p - 1) / 3);
-    if (!tflag) produce();
-    else cp_async_commit();
+    if (!tflag) produce(0);
     if (p == 0) wait_bar(&full_bar[0], 0);
     if (p + 1 < ptot) wait_bar(&full_bar[(p + 1) % 3], (p + 1) / 3);
   };
@@ -271,8 +285,10 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty_bar[p % 3]);
   };
-  produce();
-  produce();
+  for (int k = 0; k < 2; ++k) {
+    produce(0);
+    produce(1);
+  }
 
   auto stage = [&](int q) { return reinterpret_cast<const T*>(smem + (size_t)(q % 3) * G::STAGE); };
   const int o = (ty + 1) * RW + EPC + tx;
@@ -363,6 +379,7 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
         c_w1 = c * b1 + s * b0;
       }
     }
+    if (!tflag) produce(1);
     step_end(q);
 
     for (int j = 1; j <= nz; ++j) {
@@ -370,7 +387,8 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
       const unsigned g = (unsigned)z * (unsigned)NN + gown;
       if (FULL && j < nz) prefetch_momenta(g + (unsigned)NN);
       step_begin(q + j);
-      if constexpr (!FULL) cp_async_wait_all_but_one();  // this plane's momenta (all but the copies just issued)
+      // this plane's momenta (the copies begun just now are not committed yet)
+      if constexpr (!FULL) cp_async_wait_committed();
       const T* C = stage(q + j);
       const T* Pn = stage(q + j + 1);
 
@@ -432,6 +450,7 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
         c_xz = neg(rotc(Uz, pxz));
         c_yz = neg(rotc(Uz, pyz));
       }
+      if (!tflag) produce(1);
 
       // ---- hops, currents, link kicks and link drifts, direction by direction ----
       Q4<T> D;
@@ -474,10 +493,10 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
           phase(c_bz, ci, -si);
         }
         // psi = (p, q) = (w + i x, y + i z), chi = (c1, c2)
-        const T ImA = (psi.w * chi.x - psi.x * chi.w) + (psi.y * chi.z - psi.z * chi.y);  // Im psi^dag chi
-        const T Im1 = (psi.w * chi.z - psi.x * chi.y) + (psi.y * chi.x - psi.z * chi.w);  // Im psi^dag s1 chi
-        const T Im2 = (psi.y * chi.w + psi.z * chi.x) - (psi.w * chi.y + psi.x * chi.z);  // Im psi^dag s2 chi
-        const T Im3 = (psi.w * chi.x - psi.x * chi.w) - (psi.y * chi.z - psi.z * chi.y);  // Im psi^dag s3 chi
+        const T ImA = fmaT(psi.w, chi.x, fmaT(-psi.x, chi.w, fmaT(psi.y, chi.z, -psi.z * chi.y)));  // Im psi^dag chi
+        const T Im1 = fmaT(psi.w, chi.z, fmaT(-psi.x, chi.y, fmaT(psi.y, chi.x, -psi.z * chi.w)));  // Im psi^dag s1 chi
+        const T Im2 = fmaT(psi.y, chi.w, fmaT(psi.z, chi.x, fmaT(-psi.w, chi.y, -psi.x * chi.z)));  // Im psi^dag s2 chi
+        const T Im3 = fmaT(psi.w, chi.x, fmaT(-psi.x, chi.w, fmaT(-psi.y, chi.z, psi.z * chi.y)));  // Im psi^dag s3 chi
         if constexpr (RED > 0) {
           const T e0 = chi.w - psi.w, e1 = chi.x - psi.x, e2 = chi.y - psi.y, e3 = chi.z - psi.z;
           s_g += (e0 * e0 + e1 * e1) + (e2 * e2 + e3 * e3);
@@ -611,6 +630,7 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
       step_end(q + j);
     }
     step_begin(q + nz + 1);  // the item's last plane: nothing left to compute on it
+    if (!tflag) produce(1);
     step_end(q + nz + 1);
     q += nz + 2;
   }
