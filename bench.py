@@ -53,17 +53,17 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
 
 
 # Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
-# (dk_pass_su2<float,0,32>, 128^3, one leapfrog pass) from one ncu capture,
-# valid for the kernel source it was taken on.
-NCU_SU2 = {"source_hash": "1a0743229efd6379", "thread_instructions_per_site": 2051.3,
-           "dram_bytes_per_site": 280.1}
+# without expansion (kd_pass_su2<float,0,32,false>, 128^3, one leapfrog pass)
+# from one ncu capture, valid for the kernel source it was taken on.
+NCU_SU2 = {"source_hash": "f5134ee006aa2b49", "thread_instructions_per_site": 1675.8,
+           "dram_bytes_per_site": 268.6}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
 
 
 def su2_source_hash():
     h = hashlib.sha256()
-    for name in ("pass_su2.cu", "common.cuh", "tail.cuh"):
+    for name in ("pass_su2_kd.cu", "su2_common.cuh", "common.cuh", "tail.cuh"):
         with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -542,7 +542,7 @@ def other_workloads(P, torch, stream, peak):
     gbs = 256 ** 3 * 35 * 2 * 4 / (ms / n * 1e-3) / 1e9
     row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
            "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
-           "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0,32>"}
+           "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,false>"}
     if NCU_SU2["source_hash"] == su2_source_hash():
         ipc = NCU_SU2["thread_instructions_per_site"]
         ach = 256 ** 3 * ipc / (ms / n * 1e-3)
@@ -567,7 +567,7 @@ def other_workloads(P, torch, stream, peak):
         gbs = 256 ** 3 * 41 * 2 * 4 / (ms / n * 1e-3) / 1e9
         out["lphi4su2u1_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                          "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 328,
-                                         "gauss_rel_after_210_steps": rel, "kernel": "dk_pass_su2<float,0,32,true>"}
+                                         "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,true>"}
     except Exception as e:  # noqa: BLE001
         out["lphi4su2u1_256_fp32_lf"] = {"error": str(e)[:300]}
     # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
