@@ -37,8 +37,8 @@ PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256);
 PassKernel su2_pass_kernel(int fp32, int red, int TX, int full);
 size_t su2_smem_bytes(int TX, int TY, int esz, int full);
-PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int full);
-size_t su2_kd_smem_bytes(int TX, int esz, int full);
+PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full);
+size_t su2_kd_smem_bytes(int TX, int TY, int esz, int full);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
 cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
                            cudaStream_t st);
@@ -166,7 +166,7 @@ struct cl_ctx {
   int grid = 0, nseg = 0, nslot = 0, stages = 0;
   unsigned stage_bytes = 0;
   size_t smem_bytes = 0;
-  size_t smem_kd = 0;               // doublet model: dynamic shared memory of the kick-then-drift passes
+  int su2_kd_ty = 8;                // doublet models: tile height of the kick-then-drift step pass (RED 0)
   int su2_tx = 0, su2_ty = 0;      // doublet model: CTA tile (x, y) of the pass
   // schedule state
   int parity = 0;
@@ -299,11 +299,19 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
 // Doublet models without expansion: kick-then-drift passes (pass_su2_kd.cu),
 // which take no Friedmann sums (RED 1 only arises with expansion).
 bool su2_kd(const cl_ctx* c, int red) { return c->p.expansion == CL_EXP_OFF && red != 1; }
+// Tile height of the kick-then-drift pass of measurement level red: the step pass's
+// (16 rows for the FP32 lphi4SU2U1 model, else 8), the measurement pass's 8.
+int kd_ty(const cl_ctx* c, int red) { return red == 0 ? c->su2_kd_ty : 8; }
+size_t su2_launch_smem(const cl_ctx* c, int red) {
+  return su2_kd(c, red) ? su2_kd_smem_bytes(c->su2_tx, kd_ty(c, red), c->esz, c->model == CL_MODEL_LPHI4_SU2U1)
+                        : c->smem_bytes;
+}
+int su2_launch_ty(const cl_ctx* c, int red) { return su2_kd(c, red) ? kd_ty(c, red) : c->su2_ty; }
 
 PassKernel pick_kernel(const cl_ctx* c, int red) {
   if (is_doublet(c->model)) {
     const int full = c->model == CL_MODEL_LPHI4_SU2U1;
-    if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, full);
+    if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, kd_ty(c, red), full);
     return su2_pass_kernel(c->fp32, red, c->su2_tx, full);
   }
   // without expansion the U(1) passes drift right after their kick (the drift
@@ -527,7 +535,7 @@ cl_status launch_passes(cl_ctx* c, const PassStep* st, int n, int red, int write
       A.dnext = st[i].dnext;
       A.parity = c->parity ^ (write ? (i & 1) : 0);
       A.log_base = log_base + i;
-      if (su2) k<<<c->grid, dim3(c->su2_tx, c->su2_ty), su2_kd(c, red) ? c->smem_kd : c->smem_bytes, c->stream>>>(A);
+      if (su2) k<<<c->grid, dim3(c->su2_tx, su2_launch_ty(c, red)), su2_launch_smem(c, red), c->stream>>>(A);
       else k<<<c->grid, THREADS, c->smem_bytes, c->stream>>>(A);
       CHECK_LAUNCH();
     }
@@ -1054,24 +1062,33 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   c->su2_tx = N % 32 == 0 ? 32 : 16;
   c->su2_ty = 8;
   const int full = c->model == CL_MODEL_LPHI4_SU2U1;
+  // the FP32 lphi4SU2U1 step pass without expansion takes 32 x 16 tiles: one
+  // 512-thread CTA per SM, with room for its momentum slot beside three stages
+  c->su2_kd_ty = 8;
+  if (full && c->fp32 && c->su2_tx == 32 && N % 16 == 0) {
+    cudaFuncAttributes fa;
+    CU(cudaFuncGetAttributes(&fa, (const void*)su2_kd_pass_kernel(1, 0, 32, 16, 1)));
+    if (su2_kd_smem_bytes(32, 16, 4, 1) + fa.sharedSizeBytes <= c->smem_optin) c->su2_kd_ty = 16;
+  }
   c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz, full);
-  c->smem_kd = su2_kd_smem_bytes(c->su2_tx, c->esz, full);
-  if (std::max(c->smem_bytes, c->smem_kd) > c->smem_optin)
+  if (std::max(c->smem_bytes, std::max(su2_launch_smem(c, 0), su2_launch_smem(c, 2))) > c->smem_optin)
     return fail(c, CL_EUNSUPPORTED, "shared memory too small for the pass");
+  int smax = 0;
+  CU(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->dev));
   for (int red = 0; red < 3; ++red) {
     CU(cudaFuncSetAttribute((const void*)su2_pass_kernel(c->fp32, red, c->su2_tx, full),
                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_bytes));
     if (red != 1) {
-      const void* kk = (const void*)su2_kd_pass_kernel(c->fp32, red, c->su2_tx, full);
-      CU(cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_kd));
+      const int ty = kd_ty(c, red);
+      const size_t sm = su2_kd_smem_bytes(c->su2_tx, ty, c->esz, full);
+      const void* kk = (const void*)su2_kd_pass_kernel(c->fp32, red, c->su2_tx, ty, full);
+      CU(cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       // the smallest shared-memory carve-out that holds the resident CTAs, so that
-      // the rest of the SM's storage caches the momenta the pass prefetches into L1
+      // the rest of the SM's storage caches what the pass reads through L1
       cudaFuncAttributes fa;
       CU(cudaFuncGetAttributes(&fa, kk));
-      int smax = 0;
-      CU(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->dev));
-      const int per_cta = (int)(c->smem_kd + fa.sharedSizeBytes) + 1024;
-      const int by_regs = 65536 / std::max(1, fa.numRegs * c->su2_tx * c->su2_ty);
+      const int per_cta = (int)(sm + fa.sharedSizeBytes) + 1024;
+      const int by_regs = 65536 / std::max(1, fa.numRegs * c->su2_tx * ty);
       const int ctas = std::max(1, std::min(smax / per_cta, by_regs));
       const int pct = std::min(100, (int)((100LL * ctas * per_cta + smax - 1) / smax));
       CU(cudaFuncSetAttribute(kk, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
@@ -1079,10 +1096,10 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   }
   int nb = 0;
   const int rs = red_for_step(c);
-  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)pick_kernel(c, rs), c->su2_tx * c->su2_ty,
-                                                   su2_kd(c, rs) ? c->smem_kd : c->smem_bytes));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)pick_kernel(c, rs),
+                                                   c->su2_tx * su2_launch_ty(c, rs), su2_launch_smem(c, rs)));
   // work items (tile, z-chunk) over the resident CTAs (su2_work.h)
-  const int ntiles = (N / c->su2_tx) * (N / c->su2_ty);
+  const int ntiles = (N / c->su2_tx) * (N / su2_launch_ty(c, rs));
   const int R = c->nsm * std::max(nb, 1);
   const int nzc = su2_z_chunks(ntiles, N, R);
   c->grid = std::min(R, ntiles * nzc);

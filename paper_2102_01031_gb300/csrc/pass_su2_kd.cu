@@ -96,23 +96,26 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_committed() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Stage geometry: field array f of a stage holds HR = 10 rows (the tile's 8
+// Stage geometry: field array f of a stage holds HR = TY + 2 rows (the tile's
 // and a halo row each side) of RW elements, from EPC = 16 B before the tile to
 // 16 B after it; the tile's site (tx, ty) is element (ty + 1) RW + EPC + tx.
-template <typename T, int TX, bool FULL>
+template <typename T, int TX, int TY, bool FULL>
 struct KdGeom {
   static constexpr int EPC = 16 / (int)sizeof(T);
   static constexpr int RW = TX + 2 * EPC;
-  static constexpr int HR = SU2_TY + 2;
+  static constexpr int HR = TY + 2;
   static constexpr int NFA = FULL ? 22 : 19;  // psi (4), A (3), U (12), [phi_s, vphi (2)]
   static constexpr int AE = HR * RW;
   static constexpr size_t STAGE = ((size_t)NFA * AE * sizeof(T) + 127) / 128 * 128;
   // a stage row in 16-byte pieces: NCOL per row, CPA per array
   static constexpr int NCOL = RW / EPC;
   static constexpr int CPA = HR * NCOL;
-  // the doublet pass keeps each thread's own momenta of the next plane in a slot
-  // after the stages (16 arrays x the tile); the lphi4SU2U1 pass has no room for it
-  static constexpr size_t MSLOT = FULL ? 0 : ((size_t)16 * TX * SU2_TY * sizeof(T) + 127) / 128 * 128;
+  // each thread's own momenta of the next plane in a slot after the stages (16
+  // arrays, 19 for lphi4SU2U1); the lphi4SU2U1 pass with 8-row tiles, two CTAs
+  // per SM, has no room for it and reads its momenta through L1
+  static constexpr bool SLOT = !FULL || TY >= 16;
+  static constexpr int NM = FULL ? 19 : 16;
+  static constexpr size_t MSLOT = SLOT ? ((size_t)NM * TX * TY * sizeof(T) + 127) / 128 * 128 : 0;
   static constexpr size_t SMEM = 3 * STAGE + MSLOT;
 };
 
@@ -127,12 +130,13 @@ enum : int { KF = 0, KA = 4, KU = 7, KS = 19, KV = 20 };  // stage arrays
 
 // RED: 0 = no sums, 2 = full measurement (the Friedmann sums of RED 1 are
 // never needed without expansion).  FULL: the lphi4SU2U1 model.
-template <typename T, int RED, int TX, bool FULL>
-__global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 : (TX == 32 ? 2 : 4))
+template <typename T, int RED, int TX, int TY, bool FULL>
+__global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 2048 / (TX * TY * 4))
     kd_pass_su2(const PassArgs P) {
-  using G = KdGeom<T, TX, FULL>;
+  using G = KdGeom<T, TX, TY, FULL>;
   constexpr int EPC = G::EPC, RW = G::RW, NFA = G::NFA, AE = G::AE;
-  constexpr int TY = SU2_TY, nth = TX * TY, NW = nth / 32;
+  constexpr int nth = TX * TY, NW = nth / 32;
+  constexpr bool SLOT = G::SLOT;
   constexpr int NACC = RED == 0 ? 1 : (FULL ? 29 : 23);
   static_assert(RED == 0 || RED == 2, "kick-then-drift passes take no Friedmann sums");
   extern __shared__ __align__(128) unsigned char smem[];
@@ -306,10 +310,10 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
   // own momentum a (one of SP.., SPA.., SPB..) of site g: the slot, or global memory
   T* const mslot = reinterpret_cast<T*>(smem + 3 * G::STAGE);
   auto mom = [&](int a, unsigned g) -> T {
-    if constexpr (FULL) {
+    if constexpr (!SLOT) {
       return __ldg(sa(a) + g);
     } else {
-      const int m = a < SPA ? a - SP : (a < SU ? a - SPA + 4 : a - SPB + 7);
+      const int m = a < SPA ? a - SP : (a < SU ? a - SPA + 4 : (a < SS ? a - SPB + 7 : (a == SPS ? 16 : a - SPC + 17)));
       return mslot[m * nth + tid];
     }
   };
@@ -335,10 +339,11 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     const unsigned gown = (unsigned)((y0 + ty) * N + x0 + tx);
     // the momenta of own site g: into the thread's slot (doublet), or into L1 (lphi4SU2U1)
     auto prefetch_momenta = [&](unsigned g) {
-      if constexpr (!FULL) {
+      if constexpr (SLOT) {
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
-          cp_async_el(mslot + m * nth + tid, sa(m < 4 ? SP + m : (m < 7 ? SPA + m - 4 : SPB + m - 7)) + g);
+        for (int m = 0; m < G::NM; ++m)
+          cp_async_el(mslot + m * nth + tid,
+                      sa(m < 4 ? SP + m : (m < 7 ? SPA + m - 4 : (m < 16 ? SPB + m - 7 : (m == 16 ? SPS : SPC + m - 17)))) + g);
         cp_async_commit();
       } else {
 #pragma unroll
@@ -385,10 +390,10 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
     for (int j = 1; j <= nz; ++j) {
       const int z = z0 + j - 1;
       const unsigned g = (unsigned)z * (unsigned)NN + gown;
-      if (FULL && j < nz) prefetch_momenta(g + (unsigned)NN);
+      if (!SLOT && j < nz) prefetch_momenta(g + (unsigned)NN);
       step_begin(q + j);
       // this plane's momenta (the copies begun just now are not committed yet)
-      if constexpr (!FULL) cp_async_wait_committed();
+      if constexpr (SLOT) cp_async_wait_committed();
       const T* C = stage(q + j);
       const T* Pn = stage(q + j + 1);
 
@@ -581,9 +586,9 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
       for (int c2 = 0; c2 < 4; ++c2) pn[c2] = mom(SP + c2, g) + (A1 * Dc[c2] - A3 * gp * fc[c2]);
       T pns = T(0), pnc0 = T(0), pnc1 = T(0);
       if constexpr (FULL) {
-        pns = __ldg(sa(SPS) + g) + (A1 * Ls - A3 * (T(2) * qG * r2) * xs0);
-        pnc0 = __ldg(sa(SPC) + g) + (A1 * Dv0 - A3 * (T(2) * qH * r2) * xc0);
-        pnc1 = __ldg(sa(SPC + 1) + g) + (A1 * Dv1 - A3 * (T(2) * qH * r2) * xc1);
+        pns = mom(SPS, g) + (A1 * Ls - A3 * (T(2) * qG * r2) * xs0);
+        pnc0 = mom(SPC, g) + (A1 * Dv0 - A3 * (T(2) * qH * r2) * xc0);
+        pnc1 = mom(SPC + 1, g) + (A1 * Dv1 - A3 * (T(2) * qH * r2) * xc1);
       }
       if (P.write) {
 #pragma unroll
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
           if (!isfinite(pns) || !isfinite(pnc0) || !isfinite(pnc1)) nonfinite += 1.f;
         }
       }
-      if (!FULL && j < nz) prefetch_momenta(g + (unsigned)NN);  // the slot is free again
+      if (SLOT && j < nz) prefetch_momenta(g + (unsigned)NN);  // the slot is free again
       step_end(q + j);
     }
     step_begin(q + nz + 1);  // the item's last plane: nothing left to compute on it
@@ -646,30 +651,36 @@ __global__ void __launch_bounds__(TX * SU2_TY, (RED == 2 || sizeof(T) == 8) ? 1 
 
 typedef void (*PassKernel)(const PassArgs);
 
-// Kick-then-drift doublet passes (no expansion): red 0 or 2, TX 16 or 32.
-PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int full) {
+// Kick-then-drift doublet passes (no expansion): red 0 or 2, TX 16 or 32, tiles of
+// 8 rows, and (FP32, 32 wide, red 0) of 16 rows with one 512-thread CTA per SM.
+PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full) {
   static const PassKernel tab[2][2][2][2] = {  // [full][TX == 32][fp32][red == 2]
-      {{{kd_pass_su2<double, 0, 16, false>, kd_pass_su2<double, 2, 16, false>},
-        {kd_pass_su2<float, 0, 16, false>, kd_pass_su2<float, 2, 16, false>}},
-       {{kd_pass_su2<double, 0, 32, false>, kd_pass_su2<double, 2, 32, false>},
-        {kd_pass_su2<float, 0, 32, false>, kd_pass_su2<float, 2, 32, false>}}},
-      {{{kd_pass_su2<double, 0, 16, true>, kd_pass_su2<double, 2, 16, true>},
-        {kd_pass_su2<float, 0, 16, true>, kd_pass_su2<float, 2, 16, true>}},
-       {{kd_pass_su2<double, 0, 32, true>, kd_pass_su2<double, 2, 32, true>},
-        {kd_pass_su2<float, 0, 32, true>, kd_pass_su2<float, 2, 32, true>}}}};
+      {{{kd_pass_su2<double, 0, 16, 8, false>, kd_pass_su2<double, 2, 16, 8, false>},
+        {kd_pass_su2<float, 0, 16, 8, false>, kd_pass_su2<float, 2, 16, 8, false>}},
+       {{kd_pass_su2<double, 0, 32, 8, false>, kd_pass_su2<double, 2, 32, 8, false>},
+        {kd_pass_su2<float, 0, 32, 8, false>, kd_pass_su2<float, 2, 32, 8, false>}}},
+      {{{kd_pass_su2<double, 0, 16, 8, true>, kd_pass_su2<double, 2, 16, 8, true>},
+        {kd_pass_su2<float, 0, 16, 8, true>, kd_pass_su2<float, 2, 16, 8, true>}},
+       {{kd_pass_su2<double, 0, 32, 8, true>, kd_pass_su2<double, 2, 32, 8, true>},
+        {kd_pass_su2<float, 0, 32, 8, true>, kd_pass_su2<float, 2, 32, 8, true>}}}};
   if ((red != 0 && red != 2) || (TX != 16 && TX != 32)) return nullptr;
+  if (TY == 16) {
+    if (!fp32 || TX != 32 || red != 0) return nullptr;
+    return full ? kd_pass_su2<float, 0, 32, 16, true> : kd_pass_su2<float, 0, 32, 16, false>;
+  }
+  if (TY != 8) return nullptr;
   return tab[full ? 1 : 0][TX == 32 ? 1 : 0][fp32 ? 1 : 0][red == 2 ? 1 : 0];
 }
 
-// Dynamic shared memory of a kick-then-drift pass: three stages (and the
-// doublet pass's momentum slot).
-size_t su2_kd_smem_bytes(int TX, int esz, int full) {
+// Dynamic shared memory of a kick-then-drift pass: three stages and the momentum slot.
+size_t su2_kd_smem_bytes(int TX, int TY, int esz, int full) {
+  if (TY == 16) return full ? KdGeom<float, 32, 16, true>::SMEM : KdGeom<float, 32, 16, false>::SMEM;
   if (TX == 32) {
-    if (esz == 4) return full ? KdGeom<float, 32, true>::SMEM : KdGeom<float, 32, false>::SMEM;
-    return full ? KdGeom<double, 32, true>::SMEM : KdGeom<double, 32, false>::SMEM;
+    if (esz == 4) return full ? KdGeom<float, 32, 8, true>::SMEM : KdGeom<float, 32, 8, false>::SMEM;
+    return full ? KdGeom<double, 32, 8, true>::SMEM : KdGeom<double, 32, 8, false>::SMEM;
   }
-  if (esz == 4) return full ? KdGeom<float, 16, true>::SMEM : KdGeom<float, 16, false>::SMEM;
-  return full ? KdGeom<double, 16, true>::SMEM : KdGeom<double, 16, false>::SMEM;
+  if (esz == 4) return full ? KdGeom<float, 16, 8, true>::SMEM : KdGeom<float, 16, 8, false>::SMEM;
+  return full ? KdGeom<double, 16, 8, true>::SMEM : KdGeom<double, 16, 8, false>::SMEM;
 }
 
 }  // namespace clg
