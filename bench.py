@@ -52,11 +52,14 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
                 "flops_per_site_pass": 60.811}
 
 
-# Thread instructions and DRAM bytes per site of the SU(2) x U(1) doublet pass
-# without expansion (kd_pass_su2<float,0,32,false>, 128^3, one leapfrog pass)
-# from one ncu capture, valid for the kernel source it was taken on.
-NCU_SU2 = {"source_hash": "f5134ee006aa2b49", "thread_instructions_per_site": 1675.8,
-           "dram_bytes_per_site": 268.6}
+# Thread instructions and DRAM bytes per site of the doublet passes without
+# expansion (kd_pass_su2<float,0,32,8,false> for the SU(2) x U(1) doublet and
+# kd_pass_su2<float,0,32,16,true> for the lphi4SU2U1 model; 128^3, one leapfrog
+# pass each) from one ncu capture, valid for the kernel source it was taken on.
+NCU_SU2 = {"source_hash": "d961e0d99ebb51af", "thread_instructions_per_site": 1675.8,
+           "dram_bytes_per_site": 268.5}
+NCU_FULL = {"source_hash": "d961e0d99ebb51af", "thread_instructions_per_site": 1913.2,
+            "dram_bytes_per_site": 318.0}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
 
@@ -542,7 +545,7 @@ def other_workloads(P, torch, stream, peak):
     gbs = 256 ** 3 * 35 * 2 * 4 / (ms / n * 1e-3) / 1e9
     row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
            "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
-           "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,false>"}
+           "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,8,false>"}
     if NCU_SU2["source_hash"] == su2_source_hash():
         ipc = NCU_SU2["thread_instructions_per_site"]
         ach = 256 ** 3 * ipc / (ms / n * 1e-3)
@@ -565,9 +568,17 @@ def other_workloads(P, torch, stream, peak):
         rel = lat.gauss()[0]
         lat.close()
         gbs = 256 ** 3 * 41 * 2 * 4 / (ms / n * 1e-3) / 1e9
-        out["lphi4su2u1_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
-                                         "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 328,
-                                         "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,true>"}
+        row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+               "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 328,
+               "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,16,true>"}
+        if NCU_FULL["source_hash"] == su2_source_hash():
+            ipc = NCU_FULL["thread_instructions_per_site"]
+            ach = 256 ** 3 * ipc / (ms / n * 1e-3)
+            row["issue_roof"] = {"thread_instructions_per_site": ipc, "achieved_lane_instr_per_s": ach,
+                                 "peak_lane_instr_per_s": ISSUE_PEAK_LANE_INSTR_PER_S,
+                                 "frac": ach / ISSUE_PEAK_LANE_INSTR_PER_S,
+                                 "ncu_dram_bytes_per_site": NCU_FULL["dram_bytes_per_site"]}
+        out["lphi4su2u1_256_fp32_lf"] = row
     except Exception as e:  # noqa: BLE001
         out["lphi4su2u1_256_fp32_lf"] = {"error": str(e)[:300]}
     # ensemble: 16 each of 32^3, 64^3, 96^3, 128^3, FP32, VV4 with expansion, seeds 1..64
