@@ -52,13 +52,15 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
                 "flops_per_site_pass": 60.811}
 
 
-# Thread instructions and DRAM bytes per site of the doublet passes without
-# expansion (kd_pass_su2<float,0,32,8,false> for the SU(2) x U(1) doublet and
-# kd_pass_su2<float,0,32,16,true> for the lphi4SU2U1 model; 128^3, one leapfrog
-# pass each) from one ncu capture, valid for the kernel source it was taken on.
-NCU_SU2 = {"source_hash": "d961e0d99ebb51af", "thread_instructions_per_site": 1675.8,
+# Thread instructions per site of the doublet passes without expansion at the
+# benchmark size (kd_pass_su2<float,0,32,8,false,256> for the SU(2) x U(1)
+# doublet, kd_pass_su2<float,0,32,16,true,256> for the lphi4SU2U1 model; one
+# leapfrog pass of 256^3 each) and their DRAM bytes per site (the same kernels
+# built for any N, one pass of 128^3), from ncu captures, valid for the kernel
+# source they were taken on.
+NCU_SU2 = {"source_hash": "ffdcb151f9ac05b4", "thread_instructions_per_site": 1546.1,
            "dram_bytes_per_site": 268.5}
-NCU_FULL = {"source_hash": "d961e0d99ebb51af", "thread_instructions_per_site": 1913.2,
+NCU_FULL = {"source_hash": "ffdcb151f9ac05b4", "thread_instructions_per_site": 1777.6,
             "dram_bytes_per_site": 318.0}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
@@ -545,7 +547,7 @@ def other_workloads(P, torch, stream, peak):
     gbs = 256 ** 3 * 35 * 2 * 4 / (ms / n * 1e-3) / 1e9
     row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
            "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 280,
-           "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,8,false>"}
+           "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,8,false,256>"}
     if NCU_SU2["source_hash"] == su2_source_hash():
         ipc = NCU_SU2["thread_instructions_per_site"]
         ach = 256 ** 3 * ipc / (ms / n * 1e-3)
@@ -570,7 +572,7 @@ def other_workloads(P, torch, stream, peak):
         gbs = 256 ** 3 * 41 * 2 * 4 / (ms / n * 1e-3) / 1e9
         row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
                "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 328,
-               "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,16,true>"}
+               "gauss_rel_after_210_steps": rel, "kernel": "kd_pass_su2<float,0,32,16,true,256>"}
         if NCU_FULL["source_hash"] == su2_source_hash():
             ipc = NCU_FULL["thread_instructions_per_site"]
             ach = 256 ** 3 * ipc / (ms / n * 1e-3)
@@ -704,6 +706,17 @@ def profile_case(name):
                         P.make_params(precision=P.FP32, stream=stream, **su2_params(P)))
         for _ in range(4):
             lat.step(1)
+    elif name == "su2_256":   # the doublet pass at the benchmark size (the variant built for N = 256)
+        lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 256, 0.1, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **su2_params(P)))
+        for _ in range(4):
+            lat.step(1)
+    elif name == "full_256":  # the lphi4SU2U1 pass at the benchmark size
+        lat = P.Lattice(P.MODEL_LPHI4_SU2U1, 256, 0.1, ALPHA, SEED,
+                        P.make_params(precision=P.FP32, stream=stream, **dict(su2_params(P), v=0.0, qG=1.5,
+                                                                               qH=0.8, Qc=0.7)))
+        for _ in range(4):
+            lat.step(1)
     elif name == "full_128":  # single-pass launches of the leapfrog lphi4SU2U1 pass
         lat = P.Lattice(P.MODEL_LPHI4_SU2U1, 128, 0.2, ALPHA, SEED,
                         P.make_params(precision=P.FP32, stream=stream,
@@ -748,7 +761,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=150.0,
                     help="reference arm: site-steps budget / 1e6 that sizes its oracle box")
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
-    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "full_128",
+    ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "full_128", "su2_256", "full_256",
                              "adj128", "adj128self", "spectrum256"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()

@@ -37,7 +37,7 @@ PassKernel scalar_pass_kernel(int fp32, int nf, int red);
 PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256);
 PassKernel su2_pass_kernel(int fp32, int red, int TX, int full);
 size_t su2_smem_bytes(int TX, int TY, int esz, int full);
-PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full);
+PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full, int n256);
 size_t su2_kd_smem_bytes(int TX, int TY, int esz, int full);
 cudaError_t launch_su2_identity_links(int fp32, void* base, long long V, cudaStream_t st);
 cudaError_t launch_su2_rho(int fp32, const LatConst* L, int parity, int g, double2* rho, long long V,
@@ -302,6 +302,8 @@ bool su2_kd(const cl_ctx* c, int red) { return c->p.expansion == CL_EXP_OFF && r
 // Tile height of the kick-then-drift pass of measurement level red: the step pass's
 // (16 rows for the FP32 lphi4SU2U1 model, else 8), the measurement pass's 8.
 int kd_ty(const cl_ctx* c, int red) { return red == 0 ? c->su2_kd_ty : 8; }
+// The FP32 32-wide kick-then-drift step pass on a 256^3 lattice runs the variant built for N = 256.
+int kd_n256(const cl_ctx* c, int red) { return red == 0 && c->fp32 && c->su2_tx == 32 && c->lats[0].N == 256; }
 size_t su2_launch_smem(const cl_ctx* c, int red) {
   return su2_kd(c, red) ? su2_kd_smem_bytes(c->su2_tx, kd_ty(c, red), c->esz, c->model == CL_MODEL_LPHI4_SU2U1)
                         : c->smem_bytes;
@@ -311,7 +313,7 @@ int su2_launch_ty(const cl_ctx* c, int red) { return su2_kd(c, red) ? kd_ty(c, r
 PassKernel pick_kernel(const cl_ctx* c, int red) {
   if (is_doublet(c->model)) {
     const int full = c->model == CL_MODEL_LPHI4_SU2U1;
-    if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, kd_ty(c, red), full);
+    if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, kd_ty(c, red), full, kd_n256(c, red));
     return su2_pass_kernel(c->fp32, red, c->su2_tx, full);
   }
   // without expansion the U(1) passes drift right after their kick (the drift
@@ -1067,7 +1069,7 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
   c->su2_kd_ty = 8;
   if (full && c->fp32 && c->su2_tx == 32 && N % 16 == 0) {
     cudaFuncAttributes fa;
-    CU(cudaFuncGetAttributes(&fa, (const void*)su2_kd_pass_kernel(1, 0, 32, 16, 1)));
+    CU(cudaFuncGetAttributes(&fa, (const void*)su2_kd_pass_kernel(1, 0, 32, 16, 1, 0)));
     if (su2_kd_smem_bytes(32, 16, 4, 1) + fa.sharedSizeBytes <= c->smem_optin) c->su2_kd_ty = 16;
   }
   c->smem_bytes = su2_smem_bytes(c->su2_tx, c->su2_ty, c->esz, full);
@@ -1081,7 +1083,7 @@ static cl_status su2_init(cl_ctx* c, int N, double kIR, uint64_t seed) {
     if (red != 1) {
       const int ty = kd_ty(c, red);
       const size_t sm = su2_kd_smem_bytes(c->su2_tx, ty, c->esz, full);
-      const void* kk = (const void*)su2_kd_pass_kernel(c->fp32, red, c->su2_tx, ty, full);
+      const void* kk = (const void*)su2_kd_pass_kernel(c->fp32, red, c->su2_tx, ty, full, kd_n256(c, red));
       CU(cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       // the smallest shared-memory carve-out that holds the resident CTAs, so that
       // the rest of the SM's storage caches what the pass reads through L1

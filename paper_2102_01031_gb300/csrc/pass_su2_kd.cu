@@ -129,8 +129,10 @@ enum : int { KF = 0, KA = 4, KU = 7, KS = 19, KV = 20 };  // stage arrays
 }  // namespace
 
 // RED: 0 = no sums, 2 = full measurement (the Friedmann sums of RED 1 are
-// never needed without expansion).  FULL: the lphi4SU2U1 model.
-template <typename T, int RED, int TX, int TY, bool FULL>
+// never needed without expansion).  FULL: the lphi4SU2U1 model.  NC: 0 = the
+// lattice size from the lattice constants; > 0 = built for N = NC (every array
+// offset a compile-time constant).
+template <typename T, int RED, int TX, int TY, bool FULL, int NC = 0>
 __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 2048 / (TX * TY * 4))
     kd_pass_su2(const PassArgs P) {
   using G = KdGeom<T, TX, TY, FULL>;
@@ -147,10 +149,10 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
   __shared__ volatile int tflag;                   // a wait of this CTA ran out
 
   const LatConst& L = P.lat[0];
-  const int N = L.N;
+  const int N = NC ? NC : L.N;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int lane = tid & 31, warp = tid >> 5;
-  const long long NN = (long long)N * N, V = L.V;
+  const long long NN = (long long)N * N, V = NC ? (long long)NC * NC * NC : L.V;
   const int parity = P.parity;
   const T* const src = reinterpret_cast<const T*>(L.buf[parity][0]);
   T* const dst = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
@@ -652,8 +654,9 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
 typedef void (*PassKernel)(const PassArgs);
 
 // Kick-then-drift doublet passes (no expansion): red 0 or 2, TX 16 or 32, tiles of
-// 8 rows, and (FP32, 32 wide, red 0) of 16 rows with one 512-thread CTA per SM.
-PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full) {
+// 8 rows, and (FP32, 32 wide, red 0) of 16 rows with one 512-thread CTA per SM;
+// n256: the FP32 32-wide step pass built for N = 256.
+PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full, int n256) {
   static const PassKernel tab[2][2][2][2] = {  // [full][TX == 32][fp32][red == 2]
       {{{kd_pass_su2<double, 0, 16, 8, false>, kd_pass_su2<double, 2, 16, 8, false>},
         {kd_pass_su2<float, 0, 16, 8, false>, kd_pass_su2<float, 2, 16, 8, false>}},
@@ -664,10 +667,13 @@ PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full) {
        {{kd_pass_su2<double, 0, 32, 8, true>, kd_pass_su2<double, 2, 32, 8, true>},
         {kd_pass_su2<float, 0, 32, 8, true>, kd_pass_su2<float, 2, 32, 8, true>}}}};
   if ((red != 0 && red != 2) || (TX != 16 && TX != 32)) return nullptr;
+  if (n256 && (!fp32 || TX != 32 || red != 0)) return nullptr;
   if (TY == 16) {
     if (!fp32 || TX != 32 || red != 0) return nullptr;
+    if (n256) return full ? kd_pass_su2<float, 0, 32, 16, true, 256> : kd_pass_su2<float, 0, 32, 16, false, 256>;
     return full ? kd_pass_su2<float, 0, 32, 16, true> : kd_pass_su2<float, 0, 32, 16, false>;
   }
+  if (n256 && TY == 8) return full ? kd_pass_su2<float, 0, 32, 8, true, 256> : kd_pass_su2<float, 0, 32, 8, false, 256>;
   if (TY != 8) return nullptr;
   return tab[full ? 1 : 0][TX == 32 ? 1 : 0][fp32 ? 1 : 0][red == 2 ? 1 : 0];
 }
