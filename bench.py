@@ -503,8 +503,8 @@ def su2_params(P):
 def other_workloads(P, torch, stream, peak):
     """The other hot-path rows, timed briefly with the library's pass-timing hook
     (CUDA events around every launch on the lattice stream): the U(1) and the
-    SU(2) x U(1) passes at 256^3, the 64-lattice ensemble, and the adjoint
-    sweep's cost at 128^3."""
+    SU(2) x U(1) passes at 256^3, the two-field step at 512^3, the 64-lattice
+    ensemble, and the adjoint sweep's cost at 128^3."""
     SU2 = su2_params(P)
     out = {}
     # U(1) Abelian-Higgs, 256^3, FP32, leapfrog dt = 0.01, no expansion
@@ -533,6 +533,25 @@ def other_workloads(P, torch, stream, peak):
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
                                    "gauss_rel_at_start": rel0, "gauss_rel_after_3000_steps": rel,
                                    "kernel": "dk_pass_u1<float,0>", "clocks": clocks}
+    # C2 at its larger size: 512^3, two fields, FP32 storage, VV4, self-consistent expansion
+    try:
+        lat = P.Lattice(P.MODEL_LPHI4_CHI, 512, KIR, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream,
+                                                                               **PARAMS))
+        lat.step(3)
+        torch.cuda.synchronize()
+        lat.pass_timing(reset=True)
+        lat.enable_pass_timing(True)
+        lat.step(20)
+        torch.cuda.synchronize()
+        ms, n = lat.pass_timing(reset=True)
+        lat.close()
+        gbs = 512 ** 3 * PASS_BYTES_PER_SITE["f32"] / (ms / n * 1e-3) / 1e9
+        out["c2_512_fp32_vv4"] = {"site_updates_per_s": 512 ** 3 * (n / PASSES_PER_STEP) / (ms * 1e-3),
+                                  "pass_us": ms / n * 1e3, "achieved_gbs": gbs, "frac_hbm": gbs / peak,
+                                  "bytes_per_site_pass": PASS_BYTES_PER_SITE["f32"],
+                                  "kernel": "dk_pass_scalar<float,2,1>"}
+    except Exception as e:  # noqa: BLE001
+        out["c2_512_fp32_vv4"] = {"error": str(e)[:300]}
     # SU(2) x U(1) doublet, 256^3, FP32, leapfrog dt = 0.01, no expansion
     lat = P.Lattice(P.MODEL_SU2U1_HIGGS, 256, 0.1, 1.0, 1, P.make_params(precision=P.FP32, stream=stream, **SU2))
     lat.step(10)

@@ -174,3 +174,58 @@ def test_adjoint_128_fp32_against_fp64(P, expansion):
     assert eJ < 1e-5
     assert eq < 2e-3
     assert el < 2e-3
+
+
+C2S = dict(dt=0.005, integrator=O.VV4, q=100.0, phi0=[1.0, 0.0], fluct_amp2=1e-4,
+           expansion=O.EXP_SELF, fstar_over_mp=0.5)
+
+
+def test_c2_512_initial_conditions_sampled_modes(P):
+    """C2 at its larger size, 512^3 (two fields, kIR = 0.1): Fourier modes of the
+    GPU's FP64 initial fields and momenta against the oracle's one-by-one values."""
+    N, kIR = 512, 0.1
+    g = P.Lattice(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, P.make_params(precision=P.FP64, **C2S))
+    idx = sampled_indices(N, 300, 11)
+    f, gg = O.ic_sample(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, O.make_params(**C2S), idx)
+    for fld, off in ((0, 1.0), (1, 0.0)):
+        F = np.fft.fftn(g.get(fld, 0) - off).reshape(-1)[idx]
+        assert np.abs(F - f[:, fld]).max() < 1e-9 * np.abs(f[:, fld]).max(), fld
+        G = np.fft.fftn(g.get(fld, 1)).reshape(-1)[idx]
+        assert np.abs(G - gg[:, fld]).max() < 1e-9 * np.abs(gg[:, fld]).max(), fld
+    g.close()
+
+
+def test_c2_512_fp32_against_fp64(P):
+    """C2 at 512^3 in the benchmark's launch configuration (FP32 storage, VV4,
+    self-consistent expansion) against the FP64 path (the same kernels, held to the
+    oracle at smaller sizes) from the same FP32-rounded start: four steps, every
+    array within 1e-5 normwise, the energies within 1e-6, the Hubble violation no
+    larger than 1.05 x the FP64 run's plus the FP32 rounding of the constraint."""
+    N, kIR = 512, 0.1
+    g64 = P.Lattice(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, P.make_params(precision=P.FP64, **C2S))
+    g32 = P.Lattice(O.MODEL_LPHI4_CHI, N, kIR, 1.0, 1, P.make_params(precision=P.FP32, **C2S))
+    for f in range(2):
+        for w in (0, 1):
+            x = g64.get(f, w).astype(np.float32).astype(np.float64)
+            g64.set(f, w, x)
+            g32.set(f, w, x)
+    sc = g64.scalars()
+    g32.set_scalars(*sc)
+    g64.set_scalars(*sc)
+    for g in (g64, g32):
+        g.step(4)
+    for f in range(2):
+        for w in (0, 1):
+            e = nrel(g32.get(f, w), g64.get(f, w))
+            print("C2 512^3 FP32 vs FP64, 4 VV4 steps: field %d %s normwise %.3g" % (f, "pi" if w else "phi", e))
+            assert e < 1e-5, (f, w, e)
+    e32, e64 = g32.energies(), g64.energies()
+    for k in ("EK", "EG", "EV"):
+        for i in range(2):
+            if e64[k][i] != 0.0:
+                assert abs(e32[k][i] - e64[k][i]) <= 1e-6 * abs(e64[k][i]), (k, i, e32[k][i], e64[k][i])
+    for k in ("a", "b", "rho"):
+        assert abs(e32[k] - e64[k]) <= 1e-6 * abs(e64[k]), (k, e32[k], e64[k])
+    assert abs(e32["hubble_viol"]) <= 1.05 * abs(e64["hubble_viol"]) + 1e-6, (e32["hubble_viol"], e64["hubble_viol"])
+    g32.close()
+    g64.close()
