@@ -10,16 +10,21 @@
 // at each site (kick, then drift by the pass's dnext).  The values each site
 // goes through are the same as with the drift deferred to the next pass, but
 // no neighbour needs to be drifted on read: a stage holds the source buffer's
-// raw fields, copied in by the bulk-copy engine.
+// raw fields.
 //
-// Kernel layout.  A work item is a TX x 8 tile of x-y sites over a chunk of
-// z-planes (su2_work.h); the CTA's items form one sequence of planes (each item
-// adds the plane below its chunk) that a three-stage ring of shared memory
-// streams in: per plane, every field array's tile rows plus a halo row on each
-// side, each row from 16 bytes before the tile to 16 bytes after it (bulk
-// copies need 16-byte ends; where the tile touches the periodic x boundary a
-// row comes in two or three pieces).  The warp that releases a stage last
-// refills it with the plane three ahead.
+// Kernel layout.  A work item is a TX x TY tile of x-y sites (32 or 16 wide, 8
+// rows; 16 rows for the FP32 lphi4SU2U1 step pass) over a chunk of z-planes
+// (su2_work.h); the CTA's items form one sequence of planes (each item adds the
+// plane below its chunk) that a three-stage ring of shared memory streams in:
+// per plane, every field array's tile rows plus a halo row on each side, each
+// row from 16 bytes before the tile to 16 bytes after it, in 16-byte pieces the
+// threads copy themselves with cp.async (each thread the same piece of a fixed
+// list of arrays, its place on the lattice, periodic in x and y, found once per
+// item).  A plane's copies are counted on its stage's "full" mbarrier; every
+// warp arrives on the stage's "empty" mbarrier when done with it, and the
+// copies of the plane two ahead go into a stage once it is empty: no CTA
+// barrier.  Each thread's own momenta of the next plane are copied into a slot
+// beside the stages (prefetched into L1 where the slot does not fit).
 //
 // Each plaquette is formed once per site (xy, xz, yz at n) and serves the
 // staples of its links at n directly (P and P^dag); along z it also serves the
@@ -203,10 +208,8 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
   __syncthreads();
 
   // The CTA's planes form one sequence of positions (item by item, each item's
-  // planes z0 - 1 .. z0 + nz); position p lives in stage p mod 3.  Every thread
-  // copies its share of every position: the rows t = tid, tid + nth, ... of the
-  // stage (array t / HR, row t % HR), announcing the bytes on the stage's full
-  // barrier before issuing them.  pk, pj: the item and plane of the next position.
+  // planes z0 - 1 .. z0 + nz); position p lives in stage p mod 3.  produced: the
+  // positions whose copies have gone out; ptot: the positions of the sequence.
   int produced = 0, ptot = 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int chunk = it / ntiles;
@@ -309,7 +312,8 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
     return q;
   };
 
-  // own momentum a (one of SP.., SPA.., SPB..) of site g: the slot, or global memory
+  // own momentum a (one of SP.., SPA.., SPB.., and for lphi4SU2U1 SPS, SPC..) of
+  // site g: from the slot, or from global memory (prefetched into L1)
   T* const mslot = reinterpret_cast<T*>(smem + 3 * G::STAGE);
   auto mom = [&](int a, unsigned g) -> T {
     if constexpr (!SLOT) {
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
     const int z0 = chunk * N / nzc, nz = (chunk + 1) * N / nzc - z0;
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
     const unsigned gown = (unsigned)((y0 + ty) * N + x0 + tx);
-    // the momenta of own site g: into the thread's slot (doublet), or into L1 (lphi4SU2U1)
+    // the momenta of own site g: into the thread's slot, or into L1 where the slot does not fit
     auto prefetch_momenta = [&](unsigned g) {
       if constexpr (SLOT) {
 #pragma unroll
