@@ -58,9 +58,9 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
 # leapfrog pass of 256^3 each) and their DRAM bytes per site (the same kernels
 # built for any N, one pass of 128^3), from ncu captures, valid for the kernel
 # source they were taken on.
-NCU_SU2 = {"source_hash": "ffdcb151f9ac05b4", "thread_instructions_per_site": 1546.1,
+NCU_SU2 = {"source_hash": "f2e435cc44328aca", "thread_instructions_per_site": 1546.1,
            "dram_bytes_per_site": 268.5}
-NCU_FULL = {"source_hash": "ffdcb151f9ac05b4", "thread_instructions_per_site": 1777.6,
+NCU_FULL = {"source_hash": "f2e435cc44328aca", "thread_instructions_per_site": 1777.6,
             "dram_bytes_per_site": 318.0}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
