@@ -58,9 +58,9 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
 # leapfrog pass of 256^3 each) and their DRAM bytes per site (the same kernels
 # built for any N, one pass of 128^3), from ncu captures, valid for the kernel
 # source they were taken on.
-NCU_SU2 = {"source_hash": "f2e435cc44328aca", "thread_instructions_per_site": 1546.1,
+NCU_SU2 = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 1546.3,
            "dram_bytes_per_site": 268.5}
-NCU_FULL = {"source_hash": "f2e435cc44328aca", "thread_instructions_per_site": 1777.6,
+NCU_FULL = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 1777.6,
             "dram_bytes_per_site": 318.0}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
@@ -68,7 +68,7 @@ ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
 
 def su2_source_hash():
     h = hashlib.sha256()
-    for name in ("pass_su2_kd.cu", "su2_common.cuh", "common.cuh", "tail.cuh"):
+    for name in ("pass_su2_kd.cu", "su2_common.cuh", "kd_drift.cuh", "common.cuh", "tail.cuh"):
         with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

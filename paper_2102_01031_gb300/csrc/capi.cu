@@ -296,9 +296,10 @@ cl_status fft3d(cl_ctx* c, int N, double2* data, int sign) {
   return CL_OK;
 }
 
-// Doublet models without expansion: kick-then-drift passes (pass_su2_kd.cu),
-// which take no Friedmann sums (RED 1 only arises with expansion).
-bool su2_kd(const cl_ctx* c, int red) { return c->p.expansion == CL_EXP_OFF && red != 1; }
+// Doublet models without self-consistent expansion (a constant or fixed power-law
+// background): kick-then-drift passes (pass_su2_kd.cu), which take no Friedmann
+// sums (RED 1 only arises with self-consistent expansion).
+bool su2_kd(const cl_ctx* c, int red) { return c->p.expansion != CL_EXP_SELF && red != 1; }
 // Tile height of the kick-then-drift pass of measurement level red: the step pass's
 // (16 rows for the FP32 lphi4SU2U1 model, else 8), the measurement pass's 8.
 int kd_ty(const cl_ctx* c, int red) { return red == 0 ? c->su2_kd_ty : 8; }
@@ -316,11 +317,11 @@ PassKernel pick_kernel(const cl_ctx* c, int red) {
     if (su2_kd(c, red)) return su2_kd_pass_kernel(c->fp32, red, c->su2_tx, kd_ty(c, red), full, kd_n256(c, red));
     return su2_pass_kernel(c->fp32, red, c->su2_tx, full);
   }
-  // without expansion the U(1) passes drift right after their kick (the drift
-  // coefficient does not wait for the pass's sums)
+  // without self-consistent expansion the U(1) passes drift right after their
+  // kick (the drift coefficient does not wait for the pass's sums)
   if (c->model == CL_MODEL_U1_HIGGS) {
     const bool n256 = c->nlat == 1 && c->lats[0].N == 256 && c->lats[0].BY == THREADS / (256 / u1_vx(c->esz));
-    return u1_pass_kernel(c->fp32, red, c->p.expansion == CL_EXP_OFF, n256);
+    return u1_pass_kernel(c->fp32, red, c->p.expansion != CL_EXP_SELF, n256);
   }
   return scalar_pass_kernel(c->fp32, c->nf, red);
 }

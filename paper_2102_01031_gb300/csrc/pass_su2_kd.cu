@@ -1,13 +1,14 @@
-// pass_su2_kd.cu -- the doublet-model pass in kick-then-drift form (no
-// expansion): the kick of the SU(2) x U(1) doublet model (Sec. 4.3 Hamiltonian
+// pass_su2_kd.cu -- the doublet-model pass in kick-then-drift form (without
+// self-consistent expansion): the kick of the SU(2) x U(1) doublet model (Sec. 4.3 Hamiltonian
 // form in temporal gauge, links, plaquettes and covariant derivatives of the
 // U(1) and SU(N) toolkits of Sec. 4.2), and of the lphi4SU2U1 model's singlet
 // and U(1)-charged scalar (Sec. 4.5), each site's drift right after its kick.
 //
 // The equations are those of pass_su2.cu; what differs is where the work is
-// done.  Without expansion a(eta) is constant, so the drift coefficient of a
-// pass is known before its sums and the pass's own drift can follow its kick
-// at each site (kick, then drift by the pass's dnext).  The values each site
+// done.  Without self-consistent expansion a(eta) is constant or a fixed power
+// law, so the drift coefficient of a pass is known before its sums and the
+// pass's own drift can follow its kick at each site (kick, then drift by the
+// pass's dnext).  The values each site
 // goes through are the same as with the drift deferred to the next pass, but
 // no neighbour needs to be drifted on read: a stage holds the source buffer's
 // raw fields.
@@ -37,6 +38,7 @@
 // U(1) plaquette sines and the backward hops W_i^dag(n-i) psi(n-i): carried
 // along z, direct across x and y.
 #include "su2_common.cuh"
+#include "kd_drift.cuh"
 
 namespace clg {
 
@@ -134,7 +136,7 @@ enum : int { KF = 0, KA = 4, KU = 7, KS = 19, KV = 20 };  // stage arrays
 }  // namespace
 
 // RED: 0 = no sums, 2 = full measurement (the Friedmann sums of RED 1 are
-// never needed without expansion).  FULL: the lphi4SU2U1 model.  NC: 0 = the
+// only needed with self-consistent expansion).  FULL: the lphi4SU2U1 model.  NC: 0 = the
 // lattice size from the lattice constants; > 0 = built for N = NC (every array
 // offset a compile-time constant).
 template <typename T, int RED, int TX, int TY, bool FULL, int NC = 0>
@@ -171,8 +173,8 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
   if (lane == 0) {
     const LatScalars* SC = P.sc;
     const double ck = P.ck, ap1 = __ldcg(&SC->apow1), apm1 = __ldcg(&SC->apowm1), dx = L.dx;
-    double kd, kdA;  // this pass's drift, after its kick, at the constant a
-    drift_coefficients(L, __ldcg(&SC->a), P.dnext, kd, kdA);
+    double kd, kdA;  // this pass's drift, after its kick
+    kd_drift_coefficients(L, SC, P.dnext, kd, kdA);
     cf[0] = (T)kd;
     cf[1] = (T)kdA;
     cf[2] = (T)(0.5 * L.gQB * dx * kdA);                         // half the SU(2) drift angle per momentum
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
 
 typedef void (*PassKernel)(const PassArgs);
 
-// Kick-then-drift doublet passes (no expansion): red 0 or 2, TX 16 or 32, tiles of
+// Kick-then-drift doublet passes (no self-consistent expansion): red 0 or 2, TX 16 or 32, tiles of
 // 8 rows, and (FP32, 32 wide, red 0) of 16 rows with one 512-thread CTA per SM;
 // n256: the FP32 32-wide step pass built for N = 256.
 PassKernel su2_kd_pass_kernel(int fp32, int red, int TX, int TY, int full, int n256) {

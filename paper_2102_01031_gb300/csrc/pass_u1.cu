@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "ring.cuh"
 #include "tail.cuh"
+#include "kd_drift.cuh"
 
 namespace clg {
 
@@ -62,8 +63,8 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 // the pass's dnext), instead of being deferred to the next pass's reads.  The
 // order of operations on every value is the same; it needs the drift
 // coefficient before the pass's sums are known, so it is taken when a(eta)
-// does not depend on them (no expansion), and saves every neighbour read its
-// momentum load and drift.
+// does not depend on them (no expansion, or a fixed power law), and saves
+// every neighbour read its momentum load and drift.
 // NC: 0 = lattice size and tile height from the lattice constants; > 0 = the
 // kernel is built for N = NC with full tiles of THREADS threads (every stage
 // offset a compile-time constant).
@@ -118,9 +119,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
         const double ckp = P.steps ? __ldg(&P.steps[pass].ck) : P.ck;
         const double ap1 = __ldcg(&SC->apow1);
         if constexpr (KD) {
-          // no deferred drift to apply on read; this pass's drift, at the constant a
+          // no deferred drift to apply on read; this pass's drift, after its kick
           double kd, kdA;
-          drift_coefficients(L, __ldcg(&SC->a), P.steps ? __ldg(&P.steps[pass].dnext) : P.dnext, kd, kdA);
+          kd_drift_coefficients(L, SC, P.steps ? __ldg(&P.steps[pass].dnext) : P.dnext, kd, kdA);
           cf[0] = cf[1] = T(0);
           cf[8] = (T)kd;
           cf[9] = (T)kdA;
@@ -531,8 +532,8 @@ template __global__ void dk_pass_u1<float, 2, true, 256>(const PassArgs);
 
 typedef void (*PassKernel)(const PassArgs);
 
-// kd: kick-then-drift passes (only without expansion, where the Friedmann sums
-// of RED 1 are not needed).  n256: one FP32 lattice of N = 256 with full
+// kd: kick-then-drift passes (only without self-consistent expansion, where the
+// Friedmann sums of RED 1 are not needed).  n256: one FP32 lattice of N = 256 with full
 // tiles (the tile height THREADS / (N / 2)), built with its sizes as constants.
 PassKernel u1_pass_kernel(int fp32, int red, int kd, int n256) {
   static const PassKernel tab[2][3] = {
