@@ -532,7 +532,7 @@ def other_workloads(P, torch, stream, peak):
     out["u1_higgs_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
                                    "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
                                    "gauss_rel_at_start": rel0, "gauss_rel_after_3000_steps": rel,
-                                   "kernel": "dk_pass_u1<float,0>", "clocks": clocks}
+                                   "kernel": "dk_pass_u1<float,0,true,256>", "clocks": clocks}
     # C2 at its larger size: 512^3, two fields, FP32 storage, VV4, self-consistent expansion
     try:
         lat = P.Lattice(P.MODEL_LPHI4_CHI, 512, KIR, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream,

@@ -328,21 +328,27 @@ PassKernel pick_kernel(const cl_ctx* c, int red) {
 
 int tile_vx(int model, int esz) { return model == CL_MODEL_U1_HIGGS ? u1_vx(esz) : 16 / esz; }
 
-// Bytes of one stage (BY + 2 rows of every array), 128-byte aligned.
-size_t stage_size(int N, int BY, int narr, int esz) {
-  return ((size_t)(BY + 2) * N * narr * esz + 127) / 128 * 128;
+// Bytes of one stage (BY + 2 rows of every array; with mown the momenta, the
+// odd arrays, BY rows only), 128-byte aligned.
+size_t stage_size(int N, int BY, int narr, int esz, bool mown = false) {
+  const size_t rows = mown ? (size_t)(narr / 2) * (2 * BY + 2) : (size_t)(BY + 2) * narr;
+  return (rows * N * esz + 127) / 128 * 128;
 }
+
+// The U(1) kick-then-drift passes (no self-consistent expansion) read the momenta at
+// the own sites only, so their stages hold the momenta without halo rows.
+bool ring_mown(const cl_ctx* c) { return c->model == CL_MODEL_U1_HIGGS && c->p.expansion != CL_EXP_SELF; }
 
 // Tile heights BY admissible for N: BY divides N, the BY rows of N/VX
 // threads fit in one CTA, and at least 3 stages fit in shared memory; the
 // tallest first.
-std::vector<int> tile_candidates(int model, int narr, int esz, int N, size_t smem_optin) {
+std::vector<int> tile_candidates(int model, int narr, int esz, int N, size_t smem_optin, bool mown = false) {
   std::vector<int> out;
   const int TX = N / tile_vx(model, esz);
   if (TX > THREADS) return out;
   for (int by = std::min(N, THREADS / TX); by >= 1; --by) {
     if (N % by) continue;
-    if ((smem_optin - SM_TAIL_BYTES) / stage_size(N, by, narr, esz) >= 3) out.push_back(by);
+    if ((smem_optin - SM_TAIL_BYTES) / stage_size(N, by, narr, esz, mown) >= 3) out.push_back(by);
   }
   return out;
 }
@@ -611,7 +617,7 @@ static cl_status tune_tile(cl_ctx* c, int N, double kIR, int* by_out) {
   CU(cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, c->dev));
   CU(cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, c->dev));
   const TuneKey key(c->model, c->esz, N, c->nsm, ccmaj, ccmin);
-  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin);
+  std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, N, c->smem_optin, ring_mown(c));
   if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", N);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -846,7 +852,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     L.dx = 2.0 * M_PI / ((double)L.N * L.kIR);
     L.seed = seeds[l];
     c->vmax = std::max(c->vmax, L.V);
-    const std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, L.N, c->smem_optin);
+    const std::vector<int> cand = tile_candidates(c->model, c->narr, c->esz, L.N, c->smem_optin, ring_mown(c));
     if (cand.empty()) return fail(c, CL_EUNSUPPORTED, "no tile shape fits shared memory for N=%d", L.N);
     if (c->p.tile_by > 0) {
       if (std::find(cand.begin(), cand.end(), c->p.tile_by) == cand.end())
@@ -871,7 +877,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
     bool ok = false;
     if (c->p.autotune && c->p.tile_by == 0) {
       for (int l = 0; l < c->nlat; ++l) {
-        c->lats[l].BY = tile_candidates(c->model, c->narr, c->esz, c->lats[l].N, c->smem_optin)[0];
+        c->lats[l].BY = tile_candidates(c->model, c->narr, c->esz, c->lats[l].N, c->smem_optin, ring_mown(c))[0];
         tiles[l].BY = c->lats[l].BY;
       }
       ok = build_worklist(tiles, c->grid, u1, segs, cta, sbeg, send);
@@ -882,7 +888,7 @@ static cl_status init_impl(cl_ctx* c, const int* Ns, const double* kIRs, const u
   c->nseg = (int)segs.size();
   c->nslot = send[c->nlat - 1];
   // stage ring: the largest lattice stage, as many stages (3 .. 6) as fit
-  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz));
+  for (const LatHost& L : c->lats) stage = std::max(stage, stage_size(L.N, L.BY, c->narr, c->esz, ring_mown(c)));
   const int S = (int)std::min<size_t>(6, (c->smem_optin - SM_TAIL_BYTES) / stage);
   if (S < 3) return fail(c, CL_EUNSUPPORTED, "shared memory too small for the stage ring");
   c->stages = S;

@@ -17,12 +17,15 @@
 // Sums: |phi|-momenta^2 and link momenta^2 after the kick, sum_i |V_i phi(n+i) - phi(n)|^2,
 // sum_{i<j} (1 - cos theta_ij) (as 2 sin^2(theta_ij/2)), the potential, and means.
 //
-// Same plane ring as the scalar pass (ring.cuh), with all ten arrays in a
-// stage.  Segments march up in z only: the link phase of A_z(n-z) and the
-// plaquette sines theta_xz(n-z), theta_yz(n-z) are those of the plane below,
-// carried in registers, so a plane needs its own stage and the one above.
-// Each thread owns VX consecutive sites of one x-row; x-neighbours come from
-// registers and warp shuffles, y-neighbours from the stage's halo rows.
+// A plane ring (ring.cuh) with all ten arrays in a stage (the momenta without
+// halo rows where the pass kicks, then drifts).  Segments march up in z only:
+// the link phase of A_z(n-z) and the plaquette sines theta_xz(n-z),
+// theta_yz(n-z) are those of the plane below, carried in registers, so a plane
+// needs its own stage and the one above.  Each thread owns VX consecutive sites
+// of one x-row, worked as one value (an FP32 pair in the packed two-lane form);
+// x-neighbours come from registers and the stage, y-neighbours from the stage's
+// halo rows.  The sines and cosines a plane needs are evaluated together, after
+// one range check.
 #include "common.cuh"
 #include "ring.cuh"
 #include "tail.cuh"
@@ -39,21 +42,118 @@ template <> struct U1Vec<float> { typedef float2 type; static constexpr int n = 
 template <> struct U1Vec<double> { typedef double type; static constexpr int n = 1; };
 static_assert(U1Vec<float>::n == u1_vx(4) && U1Vec<double>::n == u1_vx(8), "host and device tile widths");
 
-template <typename T>
-__device__ __forceinline__ void ldv(T (&v)[U1Vec<T>::n], const T* p) {
-  *reinterpret_cast<typename U1Vec<T>::type*>(v) = *reinterpret_cast<const typename U1Vec<T>::type*>(p);
+// Two FP32 angles at once: the polynomials of the scalar FP32 sine and cosine
+// (common.cuh) in the packed two-lane form, one instruction for both lanes and
+// each lane rounded as the scalar form.
+// Where either angle is beyond pi/4 each lane takes the scalar path, so an
+// angle gets the same value whichever angle it is paired with.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sin_taylor2(float2 x2) {
+  float2 p = __ffma2_rn(x2, f2(1.f / 362880.f), f2(-1.f / 5040.f));
+  p = __ffma2_rn(x2, p, f2(1.f / 120.f));
+  p = __ffma2_rn(x2, p, f2(-1.f / 6.f));
+  return __ffma2_rn(x2, p, f2(1.f));
 }
-template <typename T>
-__device__ __forceinline__ void stv(T* p, const T (&v)[U1Vec<T>::n]) {
-  *reinterpret_cast<typename U1Vec<T>::type*>(p) = *reinterpret_cast<const typename U1Vec<T>::type*>(v);
+__device__ __forceinline__ float2 cos_taylor2(float2 x2) {
+  float2 p = __ffma2_rn(x2, f2(-1.f / 3628800.f), f2(1.f / 40320.f));
+  p = __ffma2_rn(x2, p, f2(-1.f / 720.f));
+  p = __ffma2_rn(x2, p, f2(1.f / 24.f));
+  p = __ffma2_rn(x2, p, f2(-0.5f));
+  return __ffma2_rn(x2, p, f2(1.f));
+}
+__device__ __forceinline__ void sincos2_t(float2 x, float2& s, float2& c) {
+  if (fmaxf(fabsf(x.x), fabsf(x.y)) <= 0.78539816f) {
+    const float2 x2 = __fmul2_rn(x, x);
+    s = __fmul2_rn(x, sin_taylor2(x2));
+    c = cos_taylor2(x2);
+  } else {
+    sincos_t(x.x, s.x, c.x);
+    sincos_t(x.y, s.y, c.y);
+  }
+}
+__device__ __forceinline__ float2 sin2_t(float2 x) {
+  if (fmaxf(fabsf(x.x), fabsf(x.y)) <= 0.78539816f) return __fmul2_rn(x, sin_taylor2(__fmul2_rn(x, x)));
+  return make_float2(sin_t(x.x), sin_t(x.y));
 }
 
+// A thread's VX sites of one x-row as one value: an FP32 pair is worked in the
+// packed two-lane form (one instruction for both sites), an FP64 site alone.
+// Every operation is rounded on its own (no contraction), so a value formed by
+// two threads (a link phase or a plaquette sine shared by neighbours) is the same.
+__device__ __forceinline__ float2 vset(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double vset(double a) { return a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+// a - b, exactly rounded (b times -1 is exact)
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, vset(-1.f), a); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+// the row's values one site up (down) in x, given the next thread's first
+// (the previous thread's last) value
+__device__ __forceinline__ float2 vxp(float2 v, float r) { return make_float2(v.y, r); }
+__device__ __forceinline__ double vxp(double, double r) { return r; }
+__device__ __forceinline__ float2 vxm(float2 v, float l) { return make_float2(l, v.x); }
+__device__ __forceinline__ double vxm(double, double l) { return l; }
+__device__ __forceinline__ float vget(float2 v, int i) { return i ? v.y : v.x; }
+__device__ __forceinline__ double vget(double v, int) { return v; }
+__device__ __forceinline__ void vsincos(float2 x, float2& s, float2& c) { sincos2_t(x, s, c); }
+__device__ __forceinline__ void vsincos(double x, double& s, double& c) { sincos_t(x, s, c); }
+__device__ __forceinline__ float2 vsin(float2 x) { return sin2_t(x); }
+__device__ __forceinline__ double vsin(double x) { return sin_t(x); }
+// Sines and cosines of the angle vectors xc[] and of one single angle xs, and
+// sines of the angle vectors xn[]: one range check for all of them, then every
+// polynomial in one block (independent chains the scheduler interleaves).
+// Where any angle is beyond pi/4 each lane of each angle takes the scalar path,
+// which gives an in-range angle the same value.
+template <int NCS, int NSN>
+__device__ __forceinline__ void trig_block(const float2 (&xc)[NCS], float2 (&s)[NCS], float2 (&c)[NCS], float xs,
+                                           float& ss, float& cs, const float2 (&xn)[NSN], float2 (&sn)[NSN]) {
+  float m = fabsf(xs);
+#pragma unroll
+  for (int k = 0; k < NCS; ++k) m = fmaxf(m, fmaxf(fabsf(xc[k].x), fabsf(xc[k].y)));
+#pragma unroll
+  for (int k = 0; k < NSN; ++k) m = fmaxf(m, fmaxf(fabsf(xn[k].x), fabsf(xn[k].y)));
+  if (m <= 0.78539816f) {
+#pragma unroll
+    for (int k = 0; k < NCS; ++k) {
+      const float2 x2 = __fmul2_rn(xc[k], xc[k]);
+      s[k] = __fmul2_rn(xc[k], sin_taylor2(x2));
+      c[k] = cos_taylor2(x2);
+    }
+#pragma unroll
+    for (int k = 0; k < NSN; ++k) sn[k] = __fmul2_rn(xn[k], sin_taylor2(__fmul2_rn(xn[k], xn[k])));
+    const float x2 = __fmul_rn(xs, xs);
+    ss = __fmul_rn(xs, sin_taylor(x2));
+    cs = cos_taylor(x2);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NCS; ++k) {
+      sincos_t(xc[k].x, s[k].x, c[k].x);
+      sincos_t(xc[k].y, s[k].y, c[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < NSN; ++k) sn[k] = make_float2(sin_t(xn[k].x), sin_t(xn[k].y));
+    sincos_t(xs, ss, cs);
+  }
+}
+template <int NCS, int NSN>
+__device__ __forceinline__ void trig_block(const double (&xc)[NCS], double (&s)[NCS], double (&c)[NCS], double xs,
+                                           double& ss, double& cs, const double (&xn)[NSN], double (&sn)[NSN]) {
+#pragma unroll
+  for (int k = 0; k < NCS; ++k) sincos_t(xc[k], s[k], c[k]);
+#pragma unroll
+  for (int k = 0; k < NSN; ++k) sn[k] = sin_t(xn[k]);
+  sincos_t(xs, ss, cs);
+}
 
 // Plaquette angle from its four link fields, one evaluation order everywhere
 // so that a plaquette shared by several sites has one value.
-template <typename T>
-__device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
-  return gd * ((ai_n + aj_npi) - (ai_npj + aj_n));
+template <typename V>
+__device__ __forceinline__ V plaq(V gd, V ai_n, V aj_npi, V ai_npj, V aj_n) {
+  return vmul(gd, vsub(vadd(ai_n, aj_npi), vadd(ai_npj, aj_n)));
 }
 
 }  // namespace
@@ -64,13 +164,16 @@ __device__ __forceinline__ T plaq(T gd, T ai_n, T aj_npi, T ai_npj, T aj_n) {
 // order of operations on every value is the same; it needs the drift
 // coefficient before the pass's sums are known, so it is taken when a(eta)
 // does not depend on them (no expansion, or a fixed power law), and saves
-// every neighbour read its momentum load and drift.
+// every neighbour read its momentum load and drift; the momenta are then read
+// at the own sites only, so the stages hold them without halo rows (four
+// stages fit instead of three).
 // NC: 0 = lattice size and tile height from the lattice constants; > 0 = the
 // kernel is built for N = NC with full tiles of THREADS threads (every stage
 // offset a compile-time constant).
 template <typename T, int RED, bool KD, int NC>
 __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
   constexpr int VX = U1Vec<T>::n;
+  typedef typename U1Vec<T>::type V;
   constexpr int NAR = 10;  // arrays in a ring stage
   // RED 1: pi_phi^2, pi_A^2, |D+ phi|^2, magnetic, V.
   // RED 2: pi_0^2, pi_1^2, pi_A^2, |D+ phi|^2, magnetic, V, <phi_c>, <phi_c^2>, <pi_c>.
@@ -96,7 +199,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
 
   for (int pass = 0; pass < P.npass; ++pass) {
     const int parity = P.parity ^ (pass & 1);
-    if (warp == 0) ring_pass_start<T, NAR>(R, P, pass, ptot, parity, lane);
+    if (warp == 0) ring_pass_start<T, NAR, KD>(R, P, pass, ptot, parity, lane);
     __syncthreads();
     if (R.flag[0]) goto timeout;
 
@@ -109,6 +212,9 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const int x0 = tx * VX;
       const int y = sg.ytile * BY + ty;
       const int ae = (BY + 2) * N;  // elements of one array in a stage
+      // stage offset of array a: KD keeps (field, momentum) pairs of BY + 2 and BY rows
+      auto aoff = [&](int a) { return KD ? (a >> 1) * (2 * BY + 2) * N + (a & 1) * ae : a * ae; };
+      const int mrow = KD ? -N : 0;  // KD: a momentum's stage rows start at the tile's first row
       const long long NN = (long long)N * N;
       const int g0 = R.off[i];
       // coefficients of the segment: FP64 products formed by one lane (the
@@ -143,69 +249,59 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
       const T kd = cf[8], kdA = cf[9];  // KD: the drift after the kick
       const bool drifting = !KD && (cd != T(0) || cdA != T(0));
       const T lam = (T)L.lam;
+      const V gdv = vset(gd);
       const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + VX == N ? 0 : x0 + VX;
       // output buffer: array a of a lattice buffer starts a * V elements after array 0
       T* const dbase = reinterpret_cast<T*>(L.buf[parity ^ 1][0]);
       const long long Vs = L.V;
 
-      // drifted vector of field array a (its momentum is a + 1) on stage row `row`
-      auto rdv = [&](const T* st, int a, int row, T coef, T (&o)[VX]) {
-        ldv<T>(o, st + a * ae + row * N + x0);
-        if (drifting) {
-          T m[VX];
-          ldv<T>(m, st + (a + 1) * ae + row * N + x0);
-#pragma unroll
-          for (int v = 0; v < VX; ++v) o[v] = fmaT(coef, m[v], o[v]);
-        }
+      // the thread's sites of field array a (its momentum is a + 1) on stage row `row`, drifted
+      auto rdv = [&](const T* st, int a, int row, T coef) -> V {
+        const V o = *reinterpret_cast<const V*>(st + aoff(a) + row * N + x0);
+        return drifting ? vfma(vset(coef), *reinterpret_cast<const V*>(st + aoff(a + 1) + row * N + x0), o) : o;
       };
       auto rds = [&](const T* st, int a, int row, int x, T coef) -> T {
-        const T f = st[a * ae + row * N + x];
-        return drifting ? fmaT(coef, st[(a + 1) * ae + row * N + x], f) : f;
+        const T f = st[aoff(a) + row * N + x];
+        return drifting ? fmaT(coef, st[aoff(a + 1) + row * N + x], f) : f;
       };
       // value at x0 - 1 (x0 + VX) of a row, read from the stage and drifted like
       // the owning thread's own copy (no shuffles: every lane reads its own
       // neighbour, with no divergent edge branch)
       auto left = [&](const T* st, int a, int row, T coef) -> T { return rds(st, a, row, xl, coef); };
       auto right = [&](const T* st, int a, int row, T coef) -> T { return rds(st, a, row, xr, coef); };
+      auto stv = [&](T* p, V v) { *reinterpret_cast<V*>(p) = v; };
 
       // carried from the plane below: phi, the z-link phase, theta_xz and theta_yz sines
-      T bF[2][VX], bCz[VX], bSz[VX], bSxz[VX], bSyz[VX];
+      V bF0, bF1, bCz, bSz, bSxz, bSyz;
       // current plane, drifted
-      T cF[2][VX], cA[3][VX];
+      V cF0, cF1, cA0, cA1, cA2;
 
       // ---- planes 0 and 1 of the segment ----
-      T axm[VX], aym[VX], azm[VX], azm_xp[VX], azm_yp[VX];
+      V axm, aym, azm, azm_xp, azm_yp;
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) {
         const T* st = ring_stage<T>(R, s_cur);
-        rdv(st, F0, ty + 1, cd, bF[0]);
-        rdv(st, F1, ty + 1, cd, bF[1]);
-        rdv(st, AX, ty + 1, cdA, axm);
-        rdv(st, AY, ty + 1, cdA, aym);
-        rdv(st, AZ, ty + 1, cdA, azm);
-        rdv(st, AZ, ty + 2, cdA, azm_yp);
-        const T r = right(st, AZ, ty + 1, cdA);
-#pragma unroll
-        for (int v = 0; v < VX; ++v) {
-          azm_xp[v] = v + 1 < VX ? azm[v + 1] : r;
-          sincos_t(gd * azm[v], bSz[v], bCz[v]);
-        }
+        bF0 = rdv(st, F0, ty + 1, cd);
+        bF1 = rdv(st, F1, ty + 1, cd);
+        axm = rdv(st, AX, ty + 1, cdA);
+        aym = rdv(st, AY, ty + 1, cdA);
+        azm = rdv(st, AZ, ty + 1, cdA);
+        azm_yp = rdv(st, AZ, ty + 2, cdA);
+        azm_xp = vxp(azm, right(st, AZ, ty + 1, cdA));
+        vsincos(vmul(gdv, azm), bSz, bCz);
       }
-      ring_release<T, NAR>(R, g0, s_cur, parity, ptot, lane);
+      ring_release<T, NAR, KD>(R, g0, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
       ring_wait(R, s_cur, p_cur, P.wait_limit_ns);
       if (active && !R.flag[0]) {
         const T* st = ring_stage<T>(R, s_cur);
-        rdv(st, F0, ty + 1, cd, cF[0]);
-        rdv(st, F1, ty + 1, cd, cF[1]);
-        rdv(st, AX, ty + 1, cdA, cA[0]);
-        rdv(st, AY, ty + 1, cdA, cA[1]);
-        rdv(st, AZ, ty + 1, cdA, cA[2]);
-#pragma unroll
-        for (int v = 0; v < VX; ++v) {
-          bSxz[v] = sin_t(plaq(gd, axm[v], azm_xp[v], cA[0][v], azm[v]));
-          bSyz[v] = sin_t(plaq(gd, aym[v], azm_yp[v], cA[1][v], azm[v]));
-        }
+        cF0 = rdv(st, F0, ty + 1, cd);
+        cF1 = rdv(st, F1, ty + 1, cd);
+        cA0 = rdv(st, AX, ty + 1, cdA);
+        cA1 = rdv(st, AY, ty + 1, cdA);
+        cA2 = rdv(st, AZ, ty + 1, cdA);
+        bSxz = vsin(plaq(gdv, axm, azm_xp, cA0, azm));
+        bSyz = vsin(plaq(gdv, aym, azm_yp, cA1, azm));
       }
       int s_nxt = s_cur;
       uint32_t p_nxt = p_cur;
@@ -219,178 +315,156 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
           const int own = (ty + 1) * N + x0;
           // segments march up and never wrap: plane j is z0 + j - 1
           T* const out = dbase + (long long)(sg.z0 + j - 1) * NN + (long long)y * N + x0;
-          T aF[2][VX], aA[3][VX];  // plane above, drifted
-          rdv(sa, F0, ty + 1, cd, aF[0]);
-          rdv(sa, F1, ty + 1, cd, aF[1]);
-          // link phases of this plane's sites, and of the x- and y-links into them
-          T cxv[VX], sxv[VX], cyv[VX], syv[VX], czv[VX], szv[VX], ay_ym[VX];
-#pragma unroll
-          for (int v = 0; v < VX; ++v) {
-            sincos_t(gd * cA[0][v], sxv[v], cxv[v]);
-            sincos_t(gd * cA[1][v], syv[v], cyv[v]);
-            sincos_t(gd * cA[2][v], szv[v], czv[v]);
+          const V aF0 = rdv(sa, F0, ty + 1, cd), aF1 = rdv(sa, F1, ty + 1, cd);  // plane above, drifted
+          const V aA0 = rdv(sa, AX, ty + 1, cdA), aA1 = rdv(sa, AY, ty + 1, cdA);
+          const V ay_ym = rdv(sc, AY, ty, cdA), ay_ymzp = rdv(sa, AY, ty, cdA);
+          const V ax_yp = rdv(sc, AX, ty + 2, cdA), ax_ym = rdv(sc, AX, ty, cdA);
+          const V az_yp = rdv(sc, AZ, ty + 2, cdA), az_ym = rdv(sc, AZ, ty, cdA);
+          const T ax_l = left(sc, AX, ty + 1, cdA), axzp_l = left(sa, AX, ty + 1, cdA);
+          const T ay_l = left(sc, AY, ty + 1, cdA), az_l = left(sc, AZ, ty + 1, cdA);
+          const T axyp_l = left(sc, AX, ty + 2, cdA);
+          const V ayxp = vxp(cA1, right(sc, AY, ty + 1, cdA));
+          const V azxp = vxp(cA2, right(sc, AZ, ty + 1, cdA));
+          const V ayxpym = vxp(ay_ym, right(sc, AY, ty, cdA));
+          // link phases of this plane's sites and of the y-links into them (cosine
+          // and sine), of the x-link into the first site; plaquette sines at n, at
+          // n-y, and at n-x of the first site (n-z: carried)
+          const V txy = plaq(gdv, cA0, ayxp, ax_yp, cA1);
+          const V txz = plaq(gdv, cA0, azxp, aA0, cA2);
+          const V tyz = plaq(gdv, cA1, az_yp, aA1, cA2);
+          constexpr int NE = VX == 2 ? 1 : 2;  // the first site's two n-x plaquettes: one FP32 pair, two FP64 values
+          V xc[4], sc4[4], cc4[4], xn[5 + NE], sn[5 + NE];
+          xc[0] = vmul(gdv, cA0);
+          xc[1] = vmul(gdv, cA1);
+          xc[2] = vmul(gdv, cA2);
+          xc[3] = vmul(gdv, ay_ym);
+          xn[0] = txy;
+          xn[1] = txz;
+          xn[2] = tyz;
+          xn[3] = plaq(gdv, ax_ym, ayxpym, cA0, ay_ym);
+          xn[4] = plaq(gdv, ay_ym, cA2, ay_ymzp, az_ym);
+          {
+            const T ay0 = vget(cA1, 0), az0 = vget(cA2, 0);
+            const T e_xy = gd * ((ax_l + ay0) - (axyp_l + ay_l)), e_xz = gd * ((ax_l + az0) - (axzp_l + az_l));
+            if constexpr (VX == 2) {
+              xn[5] = V{e_xy, e_xz};
+            } else {
+              xn[5] = V{e_xy};
+              xn[4 + NE] = V{e_xz};
+            }
           }
-          rdv(sc, AY, ty, cdA, ay_ym);
-          const T ax_l = left(sc, AX, ty + 1, cdA);
+          T sxl, cxl;
+          trig_block(xc, sc4, cc4, gd * ax_l, sxl, cxl, xn, sn);
+          const V sx = sc4[0], cx = cc4[0], sy = sc4[1], cy = cc4[1], sz = sc4[2], cz = cc4[2];
+          const V sym = sc4[3], cym = cc4[3];
+          const V pxy = sn[0], pxz = sn[1], pyz = sn[2], sxy_ym = sn[3], syz_ym = sn[4];
+          const V sxy_xm = vxm(pxy, vget(sn[5], 0)), sxz_xm = vxm(pxz, vget(sn[4 + NE], VX - 1));
           T s_g = T(0), s_v = T(0), s_pi = T(0);
-          T Jx[VX], Jy[VX], Jz[VX];
+          V Jx, Jy, Jz;
           // ---- charged scalar: covariant Laplacian, currents, potential, kick ----
           {
-            T fym[2][VX], fyp[2][VX];
-            rdv(sc, F0, ty, cd, fym[0]);
-            rdv(sc, F1, ty, cd, fym[1]);
-            rdv(sc, F0, ty + 2, cd, fyp[0]);
-            rdv(sc, F1, ty + 2, cd, fyp[1]);
-            const T f0_l = left(sc, F0, ty + 1, cd);
-            const T f1_l = left(sc, F1, ty + 1, cd);
-            const T f0_r = right(sc, F0, ty + 1, cd);
-            const T f1_r = right(sc, F1, ty + 1, cd);
-            T sxl, cxl;
-            sincos_t(gd * ax_l, sxl, cxl);
-            T p0[VX], p1[VX], pn0[VX], pn1[VX];
-            ldv<T>(p0, sc + P0 * ae + own);
-            ldv<T>(p1, sc + P1 * ae + own);
+            const V fym0 = rdv(sc, F0, ty, cd), fym1 = rdv(sc, F1, ty, cd);
+            const V fyp0 = rdv(sc, F0, ty + 2, cd), fyp1 = rdv(sc, F1, ty + 2, cd);
+            const V f0xp = vxp(cF0, right(sc, F0, ty + 1, cd)), f1xp = vxp(cF1, right(sc, F1, ty + 1, cd));
+            const V f0xm = vxm(cF0, left(sc, F0, ty + 1, cd)), f1xm = vxm(cF1, left(sc, F1, ty + 1, cd));
+            const V cxm = vxm(cx, cxl), sxm = vxm(sx, sxl);
+            const V p0 = *reinterpret_cast<const V*>(sc + aoff(P0) + own + mrow);
+            const V p1 = *reinterpret_cast<const V*>(sc + aoff(P1) + own + mrow);
+            const V f0 = cF0, f1 = cF1;
+            // V_i(n) phi(n+i) = u and V_i^*(n-i) phi(n-i) = w, with V = c - i s
+            const V ux0 = vfma(cx, f0xp, vmul(sx, f1xp)), ux1 = vsub(vmul(cx, f1xp), vmul(sx, f0xp));
+            const V uy0 = vfma(cy, fyp0, vmul(sy, fyp1)), uy1 = vsub(vmul(cy, fyp1), vmul(sy, fyp0));
+            const V uz0 = vfma(cz, aF0, vmul(sz, aF1)), uz1 = vsub(vmul(cz, aF1), vmul(sz, aF0));
+            const V wx0 = vsub(vmul(cxm, f0xm), vmul(sxm, f1xm)), wx1 = vfma(cxm, f1xm, vmul(sxm, f0xm));
+            const V wy0 = vsub(vmul(cym, fym0), vmul(sym, fym1)), wy1 = vfma(cym, fym1, vmul(sym, fym0));
+            const V wz0 = vsub(vmul(bCz, bF0), vmul(bSz, bF1)), wz1 = vfma(bCz, bF1, vmul(bSz, bF0));
+            const V m2 = vset(T(-2));
+            const V D0 = vadd(vadd(vfma(m2, f0, vadd(ux0, wx0)), vfma(m2, f0, vadd(uy0, wy0))), vfma(m2, f0, vadd(uz0, wz0)));
+            const V D1 = vadd(vadd(vfma(m2, f1, vadd(ux1, wx1)), vfma(m2, f1, vadd(uy1, wy1))), vfma(m2, f1, vadd(uz1, wz1)));
+            Jx = vsub(vmul(f0, ux1), vmul(f1, ux0));
+            Jy = vsub(vmul(f0, uy1), vmul(f1, uy0));
+            Jz = vsub(vmul(f0, uz1), vmul(f1, uz0));
+            // potential lam (|phi|^2 - v^2)^2 and its force 2 lam (|phi|^2 - v^2) phi_c
+            const V dd = vfma(vset(T(0.5)), vfma(f0, f0, vmul(f1, f1)), vset(-v2));
+            const V ngp = vmul(vset(-A3 * T(2) * lam), dd);  // -A3 2 lam (|phi|^2 - v^2)
+            const V pn0 = vadd(p0, vfma(ngp, f0, vmul(vset(A1), D0)));
+            const V pn1 = vadd(p1, vfma(ngp, f1, vmul(vset(A1), D1)));
+            if constexpr (RED > 0) {
+              const V g0 = vsub(ux0, f0), g1 = vsub(ux1, f1), g2 = vsub(uy0, f0), g3 = vsub(uy1, f1);
+              const V g4 = vsub(uz0, f0), g5 = vsub(uz1, f1);
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              const T f0 = cF[0][v], f1 = cF[1][v];
-              const T f0xp = v + 1 < VX ? cF[0][v + 1] : f0_r, f1xp = v + 1 < VX ? cF[1][v + 1] : f1_r;
-              const T f0xm = v > 0 ? cF[0][v - 1] : f0_l, f1xm = v > 0 ? cF[1][v - 1] : f1_l;
-              // V_i(n) phi(n+i) and V_i^*(n-i) phi(n-i), with V = c - i s
-              const T cxm = v > 0 ? cxv[v - 1] : cxl, sxm = v > 0 ? sxv[v - 1] : sxl;
-              T sym, cym;
-              sincos_t(gd * ay_ym[v], sym, cym);
-              const T ux0 = cxv[v] * f0xp + sxv[v] * f1xp, ux1 = cxv[v] * f1xp - sxv[v] * f0xp;
-              const T uy0 = cyv[v] * fyp[0][v] + syv[v] * fyp[1][v];
-              const T uy1 = cyv[v] * fyp[1][v] - syv[v] * fyp[0][v];
-              const T uz0 = czv[v] * aF[0][v] + szv[v] * aF[1][v], uz1 = czv[v] * aF[1][v] - szv[v] * aF[0][v];
-              const T wx0 = cxm * f0xm - sxm * f1xm, wx1 = cxm * f1xm + sxm * f0xm;
-              const T wy0 = cym * fym[0][v] - sym * fym[1][v], wy1 = cym * fym[1][v] + sym * fym[0][v];
-              const T wz0 = bCz[v] * bF[0][v] - bSz[v] * bF[1][v], wz1 = bCz[v] * bF[1][v] + bSz[v] * bF[0][v];
-              const T D0 = ((ux0 + wx0) - T(2) * f0) + ((uy0 + wy0) - T(2) * f0) + ((uz0 + wz0) - T(2) * f0);
-              const T D1 = ((ux1 + wx1) - T(2) * f1) + ((uy1 + wy1) - T(2) * f1) + ((uz1 + wz1) - T(2) * f1);
-              Jx[v] = f0 * ux1 - f1 * ux0;
-              Jy[v] = f0 * uy1 - f1 * uy0;
-              Jz[v] = f0 * uz1 - f1 * uz0;
-              // potential lam (|phi|^2 - v^2)^2 and its force 2 lam (|phi|^2 - v^2) phi_c
-              const T dd = T(0.5) * (f0 * f0 + f1 * f1) - v2;
-              const T gp = T(2) * lam * dd;
-              pn0[v] = p0[v] + (A1 * D0 - A3 * gp * f0);
-              pn1[v] = p1[v] + (A1 * D1 - A3 * gp * f1);
-              if constexpr (RED > 0) {
-                const T g0 = ux0 - f0, g1 = ux1 - f1, g2 = uy0 - f0, g3 = uy1 - f1, g4 = uz0 - f0, g5 = uz1 - f1;
-                s_g += g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3 + g4 * g4 + g5 * g5;
-                s_v += lam * dd * dd;
+              for (int v = 0; v < VX; ++v) {
+                const T e0 = vget(g0, v), e1 = vget(g1, v), e2 = vget(g2, v), e3 = vget(g3, v), e4 = vget(g4, v),
+                        e5 = vget(g5, v);
+                const T q0 = vget(pn0, v), q1 = vget(pn1, v), h0 = vget(f0, v), h1 = vget(f1, v), d = vget(dd, v);
+                s_g += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3 + e4 * e4 + e5 * e5;
+                s_v += lam * d * d;
                 if constexpr (RED == 1) {
-                  s_pi += pn0[v] * pn0[v] + pn1[v] * pn1[v];
+                  s_pi += q0 * q0 + q1 * q1;
                 } else {
-                  acc[0].add(pn0[v] * pn0[v]);
-                  acc[1].add(pn1[v] * pn1[v]);
-                  acc[6].add(f0);
-                  acc[7].add(f1);
-                  acc[8].add(f0 * f0);
-                  acc[9].add(f1 * f1);
-                  acc[10].add(pn0[v]);
-                  acc[11].add(pn1[v]);
-                  if (!isfinite(pn0[v]) || !isfinite(pn1[v])) nonfinite += 1.f;
+                  acc[0].add(q0 * q0);
+                  acc[1].add(q1 * q1);
+                  acc[6].add(h0);
+                  acc[7].add(h1);
+                  acc[8].add(h0 * h0);
+                  acc[9].add(h1 * h1);
+                  acc[10].add(q0);
+                  acc[11].add(q1);
+                  if (!isfinite(q0) || !isfinite(q1)) nonfinite += 1.f;
                 }
               }
             }
             if (P.write) {
               if constexpr (KD) {
-                T d0[VX], d1[VX];
-#pragma unroll
-                for (int v = 0; v < VX; ++v) {
-                  d0[v] = fmaT(kd, pn0[v], cF[0][v]);
-                  d1[v] = fmaT(kd, pn1[v], cF[1][v]);
-                }
-                stv<T>(out + F0 * Vs, d0);
-                stv<T>(out + F1 * Vs, d1);
+                stv(out + F0 * Vs, vfma(vset(kd), pn0, f0));
+                stv(out + F1 * Vs, vfma(vset(kd), pn1, f1));
               } else {
-                stv<T>(out + F0 * Vs, cF[0]);
-                stv<T>(out + F1 * Vs, cF[1]);
+                stv(out + F0 * Vs, f0);
+                stv(out + F1 * Vs, f1);
               }
-              stv<T>(out + P0 * Vs, pn0);
-              stv<T>(out + P1 * Vs, pn1);
+              stv(out + P0 * Vs, pn0);
+              stv(out + P1 * Vs, pn1);
             }
           }
           // ---- links: currents, compact curl from plaquettes, kick ----
-          T pxz[VX], pyz[VX];
           T s_piA = T(0), s_m = T(0);
           {
-            T ay_ymzp[VX], ax_yp[VX], ax_ym[VX], az_yp[VX], az_ym[VX];
-            rdv(sa, AX, ty + 1, cdA, aA[0]);
-            rdv(sa, AY, ty + 1, cdA, aA[1]);
-            rdv(sa, AZ, ty + 1, cdA, aA[2]);
-            rdv(sa, AY, ty, cdA, ay_ymzp);
-            rdv(sc, AX, ty + 2, cdA, ax_yp);
-            rdv(sc, AX, ty, cdA, ax_ym);
-            rdv(sc, AZ, ty + 2, cdA, az_yp);
-            rdv(sc, AZ, ty, cdA, az_ym);
-            const T axzp_l = left(sa, AX, ty + 1, cdA);
-            const T ay_l = left(sc, AY, ty + 1, cdA);
-            const T az_l = left(sc, AZ, ty + 1, cdA);
-            const T axyp_l = left(sc, AX, ty + 2, cdA);
-            const T ay_r = right(sc, AY, ty + 1, cdA);
-            const T az_r = right(sc, AZ, ty + 1, cdA);
-            const T ayym_r = right(sc, AY, ty, cdA);
-            T pax[VX], pay[VX], paz[VX], pnx[VX], pny[VX], pnz[VX], pxy[VX];
-            ldv<T>(pax, sc + PAX * ae + own);
-            ldv<T>(pay, sc + PAY * ae + own);
-            ldv<T>(paz, sc + PAZ * ae + own);
+            const V pax = *reinterpret_cast<const V*>(sc + aoff(PAX) + own + mrow);
+            const V pay = *reinterpret_cast<const V*>(sc + aoff(PAY) + own + mrow);
+            const V paz = *reinterpret_cast<const V*>(sc + aoff(PAZ) + own + mrow);
+            const V Cx = vadd(vsub(pxy, sxy_ym), vsub(pxz, bSxz));
+            const V Cy = vadd(vsub(sxy_xm, pxy), vsub(pyz, bSyz));
+            const V Cz = vadd(vsub(sxz_xm, pxz), vsub(syz_ym, pyz));
+            const V AJv = vset(AJ), ACv = vset(AC);
+            const V pnx = vadd(pax, vfma(AJv, Jx, vmul(ACv, Cx)));
+            const V pny = vadd(pay, vfma(AJv, Jy, vmul(ACv, Cy)));
+            const V pnz = vadd(paz, vfma(AJv, Jz, vmul(ACv, Cz)));
+            if constexpr (RED > 0) {
+              const V hxy = vsin(vmul(vset(T(0.5)), txy)), hxz = vsin(vmul(vset(T(0.5)), txz));
+              const V hyz = vsin(vmul(vset(T(0.5)), tyz));
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              const T ax = cA[0][v], ay = cA[1][v], az = cA[2][v];
-              const T axxm = v > 0 ? cA[0][v - 1] : ax_l;
-              const T ayxp = v + 1 < VX ? cA[1][v + 1] : ay_r, ayxm = v > 0 ? cA[1][v - 1] : ay_l;
-              const T azxp = v + 1 < VX ? cA[2][v + 1] : az_r, azxm = v > 0 ? cA[2][v - 1] : az_l;
-              const T axxmyp = v > 0 ? ax_yp[v - 1] : axyp_l;
-              const T ayxpym = v + 1 < VX ? ay_ym[v + 1] : ayym_r;
-              const T axxmzp = v > 0 ? aA[0][v - 1] : axzp_l;
-              // plaquette sines at n and at its lower neighbours (n-z: carried)
-              const T txy = plaq(gd, ax, ayxp, ax_yp[v], ay);
-              const T txz = plaq(gd, ax, azxp, aA[0][v], az);
-              const T tyz = plaq(gd, ay, az_yp[v], aA[1][v], az);
-              pxy[v] = sin_t(txy);
-              pxz[v] = sin_t(txz);
-              pyz[v] = sin_t(tyz);
-              const T sxy_xm = v > 0 ? pxy[v - 1] : sin_t(plaq(gd, axxm, ay, axxmyp, ayxm));
-              const T sxz_xm = v > 0 ? pxz[v - 1] : sin_t(plaq(gd, axxm, az, axxmzp, azxm));
-              const T sxy_ym = sin_t(plaq(gd, ax_ym[v], ayxpym, ax, ay_ym[v]));
-              const T syz_ym = sin_t(plaq(gd, ay_ym[v], az, ay_ymzp[v], az_ym[v]));
-              const T Cx = (pxy[v] - sxy_ym) + (pxz[v] - bSxz[v]);
-              const T Cy = (sxy_xm - pxy[v]) + (pyz[v] - bSyz[v]);
-              const T Cz = (sxz_xm - pxz[v]) + (syz_ym - pyz[v]);
-              pnx[v] = pax[v] + (AJ * Jx[v] + AC * Cx);
-              pny[v] = pay[v] + (AJ * Jy[v] + AC * Cy);
-              pnz[v] = paz[v] + (AJ * Jz[v] + AC * Cz);
-              if constexpr (RED > 0) {
-                const T hx = sin_t(T(0.5) * txy), hy = sin_t(T(0.5) * txz), hz = sin_t(T(0.5) * tyz);
+              for (int v = 0; v < VX; ++v) {
+                const T hx = vget(hxy, v), hy = vget(hxz, v), hz = vget(hyz, v);
+                const T qx = vget(pnx, v), qy = vget(pny, v), qz = vget(pnz, v);
                 s_m += T(2) * (hx * hx + hy * hy + hz * hz);
-                s_piA += pnx[v] * pnx[v] + pny[v] * pny[v] + pnz[v] * pnz[v];
+                s_piA += qx * qx + qy * qy + qz * qz;
                 if constexpr (RED == 2)
-                  if (!isfinite(pnx[v]) || !isfinite(pny[v]) || !isfinite(pnz[v])) nonfinite += 1.f;
+                  if (!isfinite(qx) || !isfinite(qy) || !isfinite(qz)) nonfinite += 1.f;
               }
             }
             if (P.write) {
               if constexpr (KD) {
-                T dx_[VX], dy_[VX], dz_[VX];
-#pragma unroll
-                for (int v = 0; v < VX; ++v) {
-                  dx_[v] = fmaT(kdA, pnx[v], cA[0][v]);
-                  dy_[v] = fmaT(kdA, pny[v], cA[1][v]);
-                  dz_[v] = fmaT(kdA, pnz[v], cA[2][v]);
-                }
-                stv<T>(out + AX * Vs, dx_);
-                stv<T>(out + AY * Vs, dy_);
-                stv<T>(out + AZ * Vs, dz_);
+                stv(out + AX * Vs, vfma(vset(kdA), pnx, cA0));
+                stv(out + AY * Vs, vfma(vset(kdA), pny, cA1));
+                stv(out + AZ * Vs, vfma(vset(kdA), pnz, cA2));
               } else {
-                stv<T>(out + AX * Vs, cA[0]);
-                stv<T>(out + AY * Vs, cA[1]);
-                stv<T>(out + AZ * Vs, cA[2]);
+                stv(out + AX * Vs, cA0);
+                stv(out + AY * Vs, cA1);
+                stv(out + AZ * Vs, cA2);
               }
-              stv<T>(out + PAX * Vs, pnx);
-              stv<T>(out + PAY * Vs, pny);
-              stv<T>(out + PAZ * Vs, pnz);
+              stv(out + PAX * Vs, pnx);
+              stv(out + PAY * Vs, pny);
+              stv(out + PAZ * Vs, pnz);
             }
           }
           if constexpr (RED == 1) {
@@ -405,27 +479,24 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_u1(const PassArgs P) {
             acc[4].add(s_m);
             acc[5].add(s_v);
           }
-#pragma unroll
-          for (int v = 0; v < VX; ++v) {
-            bF[0][v] = cF[0][v];
-            bF[1][v] = cF[1][v];
-            cF[0][v] = aF[0][v];
-            cF[1][v] = aF[1][v];
-            cA[0][v] = aA[0][v];
-            cA[1][v] = aA[1][v];
-            cA[2][v] = aA[2][v];
-            bCz[v] = czv[v];
-            bSz[v] = szv[v];
-            bSxz[v] = pxz[v];
-            bSyz[v] = pyz[v];
-          }
+          bF0 = cF0;
+          bF1 = cF1;
+          cF0 = aF0;
+          cF1 = aF1;
+          cA0 = aA0;
+          cA1 = aA1;
+          cA2 = rdv(sa, AZ, ty + 1, cdA);
+          bCz = cz;
+          bSz = sz;
+          bSxz = pxz;
+          bSyz = pyz;
         }
-        ring_release<T, NAR>(R, g0 + j, s_cur, parity, ptot, lane);
+        ring_release<T, NAR, KD>(R, g0 + j, s_cur, parity, ptot, lane);
         s_cur = s_nxt;
         p_cur = p_nxt;
         ring_advance(S, s_nxt, p_nxt);
       }
-      ring_release<T, NAR>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
+      ring_release<T, NAR, KD>(R, g0 + sg.nz + 1, s_cur, parity, ptot, lane);
       ring_advance(S, s_cur, p_cur);
 
       if (!sg.flush) continue;

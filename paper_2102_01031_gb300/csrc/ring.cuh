@@ -83,10 +83,13 @@ __device__ __forceinline__ const T* ring_stage(const Ring& R, int s) {
 // Bulk copies of plane g (of the current pass) into stage s, issued by a
 // whole warp (warp-uniform call): lane a + NA k copies run k of array a (a
 // tile's rows form up to three runs where they wrap around the periodic y
-// boundary).
+// boundary).  MOWN: the odd arrays (momenta of a field/momentum layout) are
+// copied without their halo rows -- the tile's own rows only, one run -- and
+// each (field, momentum) pair occupies rows + (rows - 2) rows of the stage,
+// the field's first.
 // Stage memory is only read through the generic proxy and its reuse is
 // ordered by the release count, so no proxy fence precedes the copies.
-template <typename T, int NA>
+template <typename T, int NA, bool MOWN = false>
 __device__ void ring_issue_warp(const Ring& R, int g, int s, int parity, int lane) {
   static_assert(3 * NA <= 32, "one lane per copy");
   int i = 0;
@@ -101,14 +104,20 @@ __device__ void ring_issue_warp(const Ring& R, int g, int s, int parity, int lan
   const int y0 = in.ylo - 1;
   const int y1 = y0 < 0 ? y0 + N : y0;
   const int r1 = min(rows, N - y1), r2 = min(rows - r1, N), r3 = rows - r1 - r2;
-  if (lane == 0) mbar_arrive_expect_tx(&R.full[s], (uint32_t)((size_t)NA * arr_elems * sizeof(T)));
+  const size_t stage_elems = MOWN ? (size_t)(NA / 2) * (2 * rows - 2) * N : (size_t)NA * arr_elems;
+  if (lane == 0) mbar_arrive_expect_tx(&R.full[s], (uint32_t)(stage_elems * sizeof(T)));
   __syncwarp();
   if (lane < 3 * NA) {
     const int run = lane / NA, a = lane - run * NA;
-    const int nr = run == 0 ? r1 : (run == 1 ? r2 : r3);
+    const bool own_only = MOWN && (a & 1);
+    int nr = run == 0 ? r1 : (run == 1 ? r2 : r3);
+    if (own_only) nr = run == 0 ? rows - 2 : 0;  // rows ylo .. ylo + BY - 1 never wrap
     if (nr > 0) {
-      const int d = run == 0 ? 0 : (run == 1 ? r1 : r1 + r2), ys = run == 0 ? y1 : 0;
-      T* st = reinterpret_cast<T*>(R.stages + (size_t)s * R.stage_bytes) + (size_t)a * arr_elems;
+      const int d = own_only ? 0 : (run == 0 ? 0 : (run == 1 ? r1 : r1 + r2));
+      const int ys = own_only ? in.ylo : (run == 0 ? y1 : 0);
+      const size_t aoff = MOWN ? (size_t)(a >> 1) * (2 * rows - 2) * N + (a & 1) * (size_t)rows * N
+                               : (size_t)a * arr_elems;
+      T* st = reinterpret_cast<T*>(R.stages + (size_t)s * R.stage_bytes) + aoff;
       const T* src = reinterpret_cast<const T*>(in.src[parity][a]) + (long long)zp * N * N;
       bulk_g2s(st + (size_t)d * N, src + (long long)ys * N, (uint32_t)(nr * N * sizeof(T)), &R.full[s]);
     }
@@ -117,7 +126,7 @@ __device__ void ring_issue_warp(const Ring& R, int g, int s, int parity, int lan
 
 // A warp is done with plane g (in stage s); the last of the CTA's warps
 // refills s with plane g + S of the same pass (which belongs in the same stage).
-template <typename T, int NA>
+template <typename T, int NA, bool MOWN = false>
 __device__ __forceinline__ void ring_release(const Ring& R, int g, int s, int parity, int ptot, int lane) {
   __syncwarp();
   int refill = 0;
@@ -129,7 +138,7 @@ __device__ __forceinline__ void ring_release(const Ring& R, int g, int s, int pa
       refill = g + R.S < ptot && !R.flag[0];
     }
   }
-  if (__shfl_sync(0xffffffffu, refill, 0)) ring_issue_warp<T, NA>(R, g + R.S, s, parity, lane);
+  if (__shfl_sync(0xffffffffu, refill, 0)) ring_issue_warp<T, NA, MOWN>(R, g + R.S, s, parity, lane);
   __syncwarp();
 }
 
@@ -212,7 +221,7 @@ __device__ void ring_slot_sums(const Ring& R, const PassArgs& P, const LatConst&
 // Between two passes of one launch (warp 0, all lanes): the previous pass's
 // writes are all done before any of its planes is read; the first planes of
 // the pass are issued; then the updated scalars are awaited.
-template <typename T, int NA>
+template <typename T, int NA, bool MOWN = false>
 __device__ void ring_pass_start(const Ring& R, const PassArgs& P, int pass, int ptot, int parity, int lane) {
   int go = 0;
   if (lane == 0) {
@@ -223,7 +232,8 @@ __device__ void ring_pass_start(const Ring& R, const PassArgs& P, int pass, int 
   go = __shfl_sync(0xffffffffu, go, 0);
   if (pass > 0) fence_proxy_async_global();
   if (go)
-    for (int g = 0; g < R.S && g < ptot; ++g) ring_issue_warp<T, NA>(R, g, (pass * ptot + g) % R.S, parity, lane);
+    for (int g = 0; g < R.S && g < ptot; ++g)
+      ring_issue_warp<T, NA, MOWN>(R, g, (pass * ptot + g) % R.S, parity, lane);
   if (lane == 0 && pass > 0 && !R.flag[0] &&
       !wait_counter(&P.gsync[1], (unsigned)P.nlat * (unsigned)pass, P.wait_limit_ns))
     R.flag[0] = 1;
