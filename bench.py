@@ -62,8 +62,20 @@ NCU_SU2 = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 15
            "dram_bytes_per_site": 268.5}
 NCU_FULL = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 1777.6,
             "dram_bytes_per_site": 318.0}
+# The same for the U(1) pass without expansion at the benchmark size
+# (dk_pass_u1<float,0,true,256>, one leapfrog pass of 256^3).
+NCU_U1 = {"source_hash": "c3909a78b7299032", "thread_instructions_per_site": 255.8,
+          "dram_bytes_per_site": 80.4}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
+
+
+def u1_source_hash():
+    h = hashlib.sha256()
+    for name in ("pass_u1.cu", "ring.cuh", "kd_drift.cuh", "common.cuh", "tail.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def su2_source_hash():
@@ -529,10 +541,18 @@ def other_workloads(P, torch, stream, peak):
     rel = lat.gauss()[0]
     lat.close()
     gbs = 256 ** 3 * 10 * 2 * 4 / (ms / n * 1e-3) / 1e9
-    out["u1_higgs_256_fp32_lf"] = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
-                                   "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
-                                   "gauss_rel_at_start": rel0, "gauss_rel_after_3000_steps": rel,
-                                   "kernel": "dk_pass_u1<float,0,true,256>", "clocks": clocks}
+    row = {"site_updates_per_s": 256 ** 3 * n / (ms * 1e-3), "pass_us": ms / n * 1e3,
+           "achieved_gbs": gbs, "frac_hbm": gbs / peak, "bytes_per_site_pass": 80,
+           "gauss_rel_at_start": rel0, "gauss_rel_after_3000_steps": rel,
+           "kernel": "dk_pass_u1<float,0,true,256>", "clocks": clocks}
+    if NCU_U1["source_hash"] == u1_source_hash():
+        ipc = NCU_U1["thread_instructions_per_site"]
+        ach = 256 ** 3 * ipc / (ms / n * 1e-3)
+        row["issue_roof"] = {"thread_instructions_per_site": ipc, "achieved_lane_instr_per_s": ach,
+                             "peak_lane_instr_per_s": ISSUE_PEAK_LANE_INSTR_PER_S,
+                             "frac": ach / ISSUE_PEAK_LANE_INSTR_PER_S,
+                             "ncu_dram_bytes_per_site": NCU_U1["dram_bytes_per_site"]}
+    out["u1_higgs_256_fp32_lf"] = row
     # C2 at its larger size: 512^3, two fields, FP32 storage, VV4, self-consistent expansion
     try:
         lat = P.Lattice(P.MODEL_LPHI4_CHI, 512, KIR, ALPHA, SEED, P.make_params(precision=P.FP32, stream=stream,
