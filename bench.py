@@ -58,13 +58,13 @@ NCU_FP64_OPS = {"source_hash": "817056deb08b6e20", "instructions_per_site_pass":
 # leapfrog pass of 256^3 each) and their DRAM bytes per site (the same kernels
 # built for any N, one pass of 128^3), from ncu captures, valid for the kernel
 # source they were taken on.
-NCU_SU2 = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 1546.3,
+NCU_SU2 = {"source_hash": "13bb525708db73c0", "thread_instructions_per_site": 1503.3,
            "dram_bytes_per_site": 268.5}
-NCU_FULL = {"source_hash": "a6c94958fe48e083", "thread_instructions_per_site": 1777.6,
+NCU_FULL = {"source_hash": "13bb525708db73c0", "thread_instructions_per_site": 1734.6,
             "dram_bytes_per_site": 318.0}
 # The same for the U(1) pass without expansion at the benchmark size
 # (dk_pass_u1<float,0,true,256>, one leapfrog pass of 256^3).
-NCU_U1 = {"source_hash": "c3909a78b7299032", "thread_instructions_per_site": 255.8,
+NCU_U1 = {"source_hash": "7aabe44e7989e483", "thread_instructions_per_site": 255.8,
           "dram_bytes_per_site": 80.4}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
@@ -72,7 +72,7 @@ ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9
 
 def u1_source_hash():
     h = hashlib.sha256()
-    for name in ("pass_u1.cu", "ring.cuh", "kd_drift.cuh", "common.cuh", "tail.cuh"):
+    for name in ("pass_u1.cu", "ring.cuh", "kd_drift.cuh", "trig2.cuh", "common.cuh", "tail.cuh"):
         with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -80,7 +80,7 @@ def u1_source_hash():
 
 def su2_source_hash():
     h = hashlib.sha256()
-    for name in ("pass_su2_kd.cu", "su2_common.cuh", "kd_drift.cuh", "common.cuh", "tail.cuh"):
+    for name in ("pass_su2_kd.cu", "su2_common.cuh", "kd_drift.cuh", "trig2.cuh", "common.cuh", "tail.cuh"):
         with open(os.path.join(ROOT, "paper_2102_01031_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

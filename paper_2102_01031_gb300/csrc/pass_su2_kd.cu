@@ -39,6 +39,7 @@
 // along z, direct across x and y.
 #include "su2_common.cuh"
 #include "kd_drift.cuh"
+#include "trig2.cuh"
 
 namespace clg {
 
@@ -373,8 +374,8 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
       const T* C = stage(q);
       const T* Pn = stage(q + 1);
       const T ax = ld(C, KA, 0, 0), ay = ld(C, KA + 1, 0, 0), az = ld(C, KA + 2, 0, 0);
-      c_sxz = sin_t(gd * ((ax + ld(C, KA + 2, 1, 0)) - (ld(Pn, KA, 0, 0) + az)));
-      c_syz = sin_t(gd * ((ay + ld(C, KA + 2, 0, 1)) - (ld(Pn, KA + 1, 0, 0) + az)));
+      c_sxz = sin_rn(gd * ((ax + ld(C, KA + 2, 1, 0)) - (ld(Pn, KA, 0, 0) + az)));
+      c_syz = sin_rn(gd * ((ay + ld(C, KA + 2, 0, 1)) - (ld(Pn, KA + 1, 0, 0) + az)));
       const Q4<T> Ux = ld4(C, KU, 0, 0), Uy = ld4(C, KU + 4, 0, 0), Uz = ld4(C, KU + 8, 0, 0);
       const V3<T> pxz = qvec(qmul(Ux, ld4(C, KU + 8, 1, 0)), qconj(qmul(Uz, ld4(Pn, KU, 0, 0))));
       const V3<T> pyz = qvec(qmul(Uy, ld4(C, KU + 8, 0, 1)), qconj(qmul(Uz, ld4(Pn, KU + 4, 0, 0))));
@@ -412,12 +413,15 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
       const T txy = gd * ((ax + ld(C, KA + 1, 1, 0)) - (ld(C, KA, 0, 1) + ay));
       const T txz = gd * ((ax + ld(C, KA + 2, 1, 0)) - (ld(Pn, KA, 0, 0) + az));
       const T tyz = gd * ((ay + ld(C, KA + 2, 0, 1)) - (ld(Pn, KA + 1, 0, 0) + az));
-      const T sxy = sin_t(txy), sxz = sin_t(txz), syz = sin_t(tyz);
       const T axm = ld(C, KA, -1, 0);
-      const T sxy_xm = sin_t(gd * ((axm + ay) - (ld(C, KA, -1, 1) + ld(C, KA + 1, -1, 0))));
-      const T sxz_xm = sin_t(gd * ((axm + az) - (ld(Pn, KA, -1, 0) + ld(C, KA + 2, -1, 0))));
-      const T sxy_ym = sin_t(gd * ((ld(C, KA, 0, -1) + ld(C, KA + 1, 1, -1)) - (ax + ld(C, KA + 1, 0, -1))));
-      const T syz_ym = sin_t(gd * ((ld(C, KA + 1, 0, -1) + az) - (ld(Pn, KA + 1, 0, -1) + ld(C, KA + 2, 0, -1))));
+      // the seven sines in one block (FP32: two at a time, one range check)
+      const T ts[7] = {txy, txz, tyz, gd * ((axm + ay) - (ld(C, KA, -1, 1) + ld(C, KA + 1, -1, 0))),
+                       gd * ((axm + az) - (ld(Pn, KA, -1, 0) + ld(C, KA + 2, -1, 0))),
+                       gd * ((ld(C, KA, 0, -1) + ld(C, KA + 1, 1, -1)) - (ax + ld(C, KA + 1, 0, -1))),
+                       gd * ((ld(C, KA + 1, 0, -1) + az) - (ld(Pn, KA + 1, 0, -1) + ld(C, KA + 2, 0, -1)))};
+      T sn[7];
+      sin_many(ts, sn);
+      const T sxy = sn[0], sxz = sn[1], syz = sn[2], sxy_xm = sn[3], sxz_xm = sn[4], sxy_ym = sn[5], syz_ym = sn[6];
       const T Cc[3] = {(sxy - sxy_ym) + (sxz - c_sxz), (sxy_xm - sxy) + (syz - c_syz),
                        (sxz_xm - sxz) + (syz_ym - syz)};
       c_sxz = sxz;

@@ -30,6 +30,7 @@
 #include "ring.cuh"
 #include "tail.cuh"
 #include "kd_drift.cuh"
+#include "trig2.cuh"
 
 namespace clg {
 
@@ -41,40 +42,6 @@ template <typename T> struct U1Vec;
 template <> struct U1Vec<float> { typedef float2 type; static constexpr int n = 2; };
 template <> struct U1Vec<double> { typedef double type; static constexpr int n = 1; };
 static_assert(U1Vec<float>::n == u1_vx(4) && U1Vec<double>::n == u1_vx(8), "host and device tile widths");
-
-// Two FP32 angles at once: the polynomials of the scalar FP32 sine and cosine
-// (common.cuh) in the packed two-lane form, one instruction for both lanes and
-// each lane rounded as the scalar form.
-// Where either angle is beyond pi/4 each lane takes the scalar path, so an
-// angle gets the same value whichever angle it is paired with.
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 sin_taylor2(float2 x2) {
-  float2 p = __ffma2_rn(x2, f2(1.f / 362880.f), f2(-1.f / 5040.f));
-  p = __ffma2_rn(x2, p, f2(1.f / 120.f));
-  p = __ffma2_rn(x2, p, f2(-1.f / 6.f));
-  return __ffma2_rn(x2, p, f2(1.f));
-}
-__device__ __forceinline__ float2 cos_taylor2(float2 x2) {
-  float2 p = __ffma2_rn(x2, f2(-1.f / 3628800.f), f2(1.f / 40320.f));
-  p = __ffma2_rn(x2, p, f2(-1.f / 720.f));
-  p = __ffma2_rn(x2, p, f2(1.f / 24.f));
-  p = __ffma2_rn(x2, p, f2(-0.5f));
-  return __ffma2_rn(x2, p, f2(1.f));
-}
-__device__ __forceinline__ void sincos2_t(float2 x, float2& s, float2& c) {
-  if (fmaxf(fabsf(x.x), fabsf(x.y)) <= 0.78539816f) {
-    const float2 x2 = __fmul2_rn(x, x);
-    s = __fmul2_rn(x, sin_taylor2(x2));
-    c = cos_taylor2(x2);
-  } else {
-    sincos_t(x.x, s.x, c.x);
-    sincos_t(x.y, s.y, c.y);
-  }
-}
-__device__ __forceinline__ float2 sin2_t(float2 x) {
-  if (fmaxf(fabsf(x.x), fabsf(x.y)) <= 0.78539816f) return __fmul2_rn(x, sin_taylor2(__fmul2_rn(x, x)));
-  return make_float2(sin_t(x.x), sin_t(x.y));
-}
 
 // A thread's VX sites of one x-row as one value: an FP32 pair is worked in the
 // packed two-lane form (one instruction for both sites), an FP64 site alone.
@@ -116,7 +83,7 @@ __device__ __forceinline__ void trig_block(const float2 (&xc)[NCS], float2 (&s)[
   for (int k = 0; k < NCS; ++k) m = fmaxf(m, fmaxf(fabsf(xc[k].x), fabsf(xc[k].y)));
 #pragma unroll
   for (int k = 0; k < NSN; ++k) m = fmaxf(m, fmaxf(fabsf(xn[k].x), fabsf(xn[k].y)));
-  if (m <= 0.78539816f) {
+  if (m <= TRIG_PI4) {
 #pragma unroll
     for (int k = 0; k < NCS; ++k) {
       const float2 x2 = __fmul2_rn(xc[k], xc[k]);
@@ -131,12 +98,12 @@ __device__ __forceinline__ void trig_block(const float2 (&xc)[NCS], float2 (&s)[
   } else {
 #pragma unroll
     for (int k = 0; k < NCS; ++k) {
-      sincos_t(xc[k].x, s[k].x, c[k].x);
-      sincos_t(xc[k].y, s[k].y, c[k].y);
+      sincos_rn(xc[k].x, s[k].x, c[k].x);
+      sincos_rn(xc[k].y, s[k].y, c[k].y);
     }
 #pragma unroll
-    for (int k = 0; k < NSN; ++k) sn[k] = make_float2(sin_t(xn[k].x), sin_t(xn[k].y));
-    sincos_t(xs, ss, cs);
+    for (int k = 0; k < NSN; ++k) sn[k] = make_float2(sin_rn(xn[k].x), sin_rn(xn[k].y));
+    sincos_rn(xs, ss, cs);
   }
 }
 template <int NCS, int NSN>
