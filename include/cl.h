@@ -15,8 +15,9 @@
  *   - Status codes only (cl_status); nothing aborts or traps.  A failed call
  *     leaves a message retrievable with cl_last_error(ctx).
  *   - All device memory is owned by the context: allocated by cl_init,
- *     released by cl_free.  Host arrays passed in or out are owned by the
- *     caller and must hold the stated number of elements.
+ *     released by cl_free; the one exception is state memory the caller
+ *     binds with cl_bind_buffers.  Host arrays passed in or out are owned by
+ *     the caller and must hold the stated number of elements.
  *   - The state and gradient transfers (cl_get_state, cl_set_state and their
  *     cl_lattice_ forms, cl_get_array, cl_set_array, cl_upload_state,
  *     cl_download_state, cl_adjoint's dJ_dstate, cl_ic_amplitude_grad) also
@@ -238,6 +239,29 @@ cl_status cl_set_scalars(cl_ctx* ctx, double eta, double a, double b);
 cl_status cl_state_bytes(cl_ctx* ctx, size_t* bytes);
 cl_status cl_upload_state(cl_ctx* ctx, const void* host, size_t bytes);
 cl_status cl_download_state(cl_ctx* ctx, void* host, size_t bytes);
+
+/* Caller-owned state memory (the lattice state of Sec. 3: fields and momenta
+ * on the sites, and for the gauge models the links and their momenta): lattice
+ * `lat` keeps the two buffers a pass reads and writes in buf0 and buf1 instead
+ * of in memory of its own, e.g. two torch CUDA tensors.  Each is a device
+ * pointer on the context's device, 256-byte aligned, to `bytes` bytes, at least
+ * the lattice's state (narr arrays of N^3 values in the storage precision,
+ * array a at a * N^3 values, in the order of cl_upload_state; cl_state_bytes
+ * gives the size for a single lattice); the two must not overlap.  The state
+ * moves with the binding: both buffers are copied into buf0 and buf1 on the
+ * context stream, and the lattice's own state memory is released.  buf0 = buf1 =
+ * NULL moves the state back into new memory of the lattice's own.  The caller
+ * keeps ownership; the buffers must stay allocated while bound (until cl_free or
+ * a later cl_bind_buffers of the lattice) and must not be written while the
+ * context uses them.  Synchronises the stream.  CL_EINVAL for a bad lattice
+ * index, pointer, size, alignment or overlap (nothing changes); CL_ENOMEM when
+ * memory of the lattice's own cannot be made again (the binding stays). */
+cl_status cl_bind_buffers(cl_ctx* ctx, int lat, void* buf0, void* buf1, size_t bytes);
+/* The buffer (0 or 1) that holds the state once the passes enqueued so far
+ * have run: the one to read through a binding after the stream has reached
+ * them (after cl_sync it holds what cl_get_state returns).  Each pass reads
+ * one buffer and writes the other.  Host bookkeeping only. */
+cl_status cl_state_buffer(cl_ctx* ctx, int* which);
 
 /* Checkpoint and resume (single lattice): cl_checkpoint_save writes the state
  * arrays and the evolving scalars (a, a', eta, drift coefficients, carried sums,

@@ -37,7 +37,7 @@ EXPORTS = (
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
     "cl_set_tune_cache", "cl_selftest_wait", "cl_pass_weights", "cl_philox_draws",
-    "cl_adjoint_pass_timing",
+    "cl_adjoint_pass_timing", "cl_bind_buffers", "cl_state_buffer",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -141,6 +141,8 @@ def lib():
     L.cl_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.cl_upload_state.argtypes = [vp, vp, ctypes.c_size_t]
     L.cl_download_state.argtypes = [vp, vp, ctypes.c_size_t]
+    L.cl_bind_buffers.argtypes = [vp, ip, vp, vp, ctypes.c_size_t]
+    L.cl_state_buffer.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.cl_nfields.argtypes = [vp]
     L.cl_kernel_launches.argtypes = [vp]
     L.cl_kernel_launches.restype = ctypes.c_int64
@@ -460,6 +462,33 @@ class Lattice:
         _check(self.L, self.h, self.L.cl_state_bytes(self.h, ctypes.byref(n)), "cl_state_bytes")
         return n.value
 
+    def bind_buffers(self, buf0, buf1, lat=0):
+        """cl_bind_buffers: two caller-owned CUDA tensors (contiguous, on the
+        context's device, 256-byte aligned, each at least the lattice's state
+        size) become the lattice's two state buffers, the state copied into
+        them.  They stay referenced here while bound.  bind_buffers(None, None)
+        moves the state back into memory of the lattice's own."""
+        bound = self.__dict__.setdefault("_bound", {})
+        if buf0 is None and buf1 is None:
+            _check(self.L, self.h, self.L.cl_bind_buffers(self.h, lat, None, None, 0), "cl_bind_buffers")
+            bound.pop(lat, None)
+            return
+        for t in (buf0, buf1):
+            if not t.is_contiguous():
+                raise ValueError("bound buffers must be contiguous")
+        nbytes = min(buf0.numel() * buf0.element_size(), buf1.numel() * buf1.element_size())
+        _check(self.L, self.h, self.L.cl_bind_buffers(self.h, lat, ctypes.c_void_p(buf0.data_ptr()),
+                                                      ctypes.c_void_p(buf1.data_ptr()), nbytes),
+               "cl_bind_buffers")
+        bound[lat] = (buf0, buf1)
+
+    def state_buffer(self):
+        """cl_state_buffer: 0 or 1, the buffer that holds the state once the
+        passes enqueued so far have run."""
+        w = ctypes.c_int()
+        _check(self.L, self.h, self.L.cl_state_buffer(self.h, ctypes.byref(w)), "cl_state_buffer")
+        return w.value
+
     def upload(self, host_ptr, nbytes):
         _check(self.L, self.h, self.L.cl_upload_state(self.h, ctypes.c_void_p(host_ptr), nbytes),
                "cl_upload_state")
@@ -541,6 +570,10 @@ class Ensemble:
         if rc != CL_OK:
             raise ClError(rc, "cl_ensemble_init: " + self.L.cl_last_error(None).decode(errors="replace"))
         self.h = h
+
+    # caller-owned state buffers of lattice `lat` (cl_bind_buffers, cl_state_buffer)
+    bind_buffers = Lattice.bind_buffers
+    state_buffer = Lattice.state_buffer
 
     def close(self):
         if getattr(self, "h", None):

@@ -98,6 +98,7 @@ struct LatHost {
   double kIR = 0.0, dx = 0.0;
   uint64_t seed = 0;
   void* slab = nullptr;  // 2 buffers x narr arrays of V values, array-major
+  void* bound[2] = {nullptr, nullptr};  // caller-owned buffers (cl_bind_buffers), in place of slab
   ICArgs ic;             // what the initial conditions were drawn with
 };
 
@@ -117,6 +118,7 @@ struct AdjPlan {
   unsigned* d_cnt = nullptr;
   double* d_out = nullptr;       // J and the explicit dJ/dq of the objective
   int nslot = 0;
+  LatConst hl;                   // host copy of *d_lat
 };
 
 // A multi-pass launch recorded in a CUDA graph, replayed when the same
@@ -275,6 +277,7 @@ void fft_radices(int N, FftPlan& pl) {
 
 void* arr_ptr(cl_ctx* c, int lat, int parity, int a) {
   const LatHost& L = c->lats[lat];
+  if (L.bound[0]) return (char*)L.bound[parity] + (size_t)a * L.V * c->esz;
   return (char*)L.slab + ((size_t)parity * c->narr + a) * (size_t)L.V * c->esz;
 }
 
@@ -1797,6 +1800,68 @@ cl_status cl_state_bytes(cl_ctx* c, size_t* bytes) {
   return CL_OK;
 }
 
+cl_status cl_bind_buffers(cl_ctx* c, int lat, void* buf0, void* buf1, size_t bytes) {
+  Range range_("cl_bind_buffers");
+  if (!c) return CL_EINVAL;
+  if (lat < 0 || lat >= c->nlat) return fail(c, CL_EINVAL, "lattice %d of %d", lat, c->nlat);
+  LatHost& L = c->lats[lat];
+  const size_t need = (size_t)c->narr * L.V * c->esz;
+  const bool unbind = !buf0 && !buf1;
+  void* buf[2] = {buf0, buf1};
+  if (!unbind) {
+    if (!buf0 || !buf1) return fail(c, CL_EINVAL, "two buffers, or none");
+    if (bytes < need) return fail(c, CL_EINVAL, "buffers of %zu bytes, the state needs %zu", bytes, need);
+    const uintptr_t p0 = (uintptr_t)buf0, p1 = (uintptr_t)buf1;
+    if (p0 % 256 || p1 % 256) return fail(c, CL_EINVAL, "buffers must be 256-byte aligned");
+    if (p0 < p1 + need && p1 < p0 + need) return fail(c, CL_EINVAL, "the two buffers overlap");
+    for (int k = 0; k < 2; ++k) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, buf[k]) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, CL_EINVAL, "buffer %d is not device memory", k);
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != c->dev)
+        return fail(c, CL_EINVAL, "buffer %d is not memory of the context's device", k);
+    }
+  }
+  void* fresh = nullptr;  // memory of the lattice's own, when the binding ends
+  if (unbind) {
+    if (!L.bound[0]) return CL_OK;
+    CU(cudaMalloc(&fresh, 2 * need));
+    buf[0] = fresh;
+    buf[1] = (char*)fresh + need;
+  }
+  // the state moves with the binding: both buffers, on the context stream
+  for (int par = 0; par < 2; ++par)
+    CU(cudaMemcpyAsync(buf[par], arr_ptr(c, lat, par, 0), need, cudaMemcpyDeviceToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (L.slab) CU(cudaFree(L.slab));
+  L.slab = fresh;
+  L.bound[0] = unbind ? nullptr : buf0;
+  L.bound[1] = unbind ? nullptr : buf1;
+  // every device-side copy of the array addresses (the doublet models keep the
+  // first MAX_ARR and address the rest from array 0)
+  LatConst& H = c->hlat[lat];
+  for (int par = 0; par < 2; ++par)
+    for (int a = 0; a < std::min(c->narr, MAX_ARR); ++a) H.buf[par][a] = arr_ptr(c, lat, par, a);
+  CU(cudaMemcpyAsync(c->d_lat + lat, &H, sizeof(LatConst), cudaMemcpyHostToDevice, c->stream));
+  if (c->adj.ready) {
+    for (int par = 0; par < 2; ++par)
+      for (int a = 0; a < 2 * c->nf; ++a) c->adj.hl.buf[par][a] = arr_ptr(c, 0, par, a);
+    CU(cudaMemcpyAsync(c->adj.d_lat, &c->adj.hl, sizeof(LatConst), cudaMemcpyHostToDevice, c->stream));
+  }
+  for (auto& g : c->graph_cache) cudaGraphExecDestroy(g.exec);
+  c->graph_cache.clear();
+  CU(cudaStreamSynchronize(c->stream));
+  return CL_OK;
+}
+
+cl_status cl_state_buffer(cl_ctx* c, int* which) {
+  if (!c || !which) return fail(c, CL_EINVAL, "NULL argument");
+  *which = c->parity;
+  return CL_OK;
+}
+
 cl_status cl_checkpoint_save(cl_ctx* c, const char* path) {
   Range range_("cl_checkpoint_save");
   if (!c || !path) return fail(c, CL_EINVAL, "NULL argument");
@@ -1962,7 +2027,8 @@ static cl_status adjoint_plan(cl_ctx* c) {
       L.buf[par][a] = arr_ptr(c, 0, par, a);
       L.buf[par][2 * c->nf + a] = (char*)A.lam + ((size_t)par * 2 * c->nf + a) * ab;
     }
-  CU(cudaMemcpyAsync(A.d_lat, &L, sizeof(L), cudaMemcpyHostToDevice, c->stream));
+  A.hl = L;
+  CU(cudaMemcpyAsync(A.d_lat, &A.hl, sizeof(L), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(A.d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(A.d_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   int coop = 0, nb = 0;
