@@ -762,6 +762,12 @@ def profile_case(name):
                                       **dict(su2_params(P), v=0.0, qG=1.5, qH=0.8, Qc=0.7)))
         for _ in range(4):
             lat.step(1)
+    elif name == "ensemble64":   # the 64-lattice ensemble: one cooperative launch of a VV4 step
+        Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
+        E = P.Ensemble(P.MODEL_LPHI4_CHI, Ns, [KIR * N_LAT / n for n in Ns], ALPHA, list(range(1, 65)),
+                       P.make_params(precision=P.FP32, stream=stream, **PARAMS))
+        for _ in range(4):
+            E.step(1)
     elif name == "scalar256_fp64":   # the FP64 plain pass: one cooperative launch of a VV4 step
         lat = P.Lattice(P.MODEL_LPHI4_CHI, N_LAT, KIR, ALPHA, SEED,
                         P.make_params(precision=P.FP64, stream=stream, **PARAMS))
@@ -801,7 +807,7 @@ def main():
                     help="reference arm: site-steps budget / 1e6 that sizes its oracle box")
     ap.add_argument("--no-extra", action="store_true", help="skip the U(1), ensemble and adjoint rows")
     ap.add_argument("--profile-case", choices=("scalar256", "scalar256_fp64", "u1_128", "u1_256", "su2_128", "full_128", "su2_256", "full_256",
-                             "adj128", "adj128self", "spectrum256"),
+                             "adj128", "adj128self", "spectrum256", "ensemble64"),
                     help="run one small case for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:
