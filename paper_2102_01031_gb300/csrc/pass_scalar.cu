@@ -56,7 +56,10 @@ template <> struct ScalarPot<2> {
   template <typename T>
   __device__ __forceinline__ static void eval(const T (&f)[2], T q, T (&d)[2], T (&t)[2]) {
     const T p2 = f[0] * f[0], c2 = f[1] * f[1];
-    d[0] = p2 * f[0] + q * f[0] * c2;
+    if constexpr (sizeof(T) == 8)
+      d[0] = f[0] * fmaT(q, c2, p2);  // phi (phi^2 + q chi^2): one operation fewer on the FP64 pipe
+    else
+      d[0] = p2 * f[0] + q * f[0] * c2;
     d[1] = q * p2 * f[1];
     t[0] = T(0.25) * p2 * p2;
     t[1] = T(0.5) * q * p2 * c2;
@@ -452,8 +455,15 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
               const T xl = v == 0 ? left : cur[f][v - 1];
               const T xr = v == VX - 1 ? right : cur[f][v + 1];
               const T zl = below[f][v], zh = above[f][v];
-              lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
-                          ((zl + zh) - T(2) * c);
+              if constexpr (sizeof(T) == 8) {
+                // FP64: the six neighbours summed, then -6 c in one FMA (the fewest
+                // operations on the narrow FP64 pipe); FP32 keeps each direction's
+                // small difference from its own pair sum
+                lap[f][v] = fmaT(T(-6), c, ((xl + xr) + (yl[v] + yh[v])) + (zl + zh));
+              } else {
+                lap[f][v] = ((xl + xr) - T(2) * c) + ((yl[v] + yh[v]) - T(2) * c) +
+                            ((zl + zh) - T(2) * c);
+              }
               if (RED == 2) {  // forward differences (eq. EK_EG_EV with grad^+)
                 const T zp = sg.dir > 0 ? zh : zl;
                 const T gx = xr - c, gy = yh[v] - c, gz = zp - c;
@@ -477,7 +487,14 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             for (int f = 0; f < NF; ++f) fv[f] = cur[f][v];
             ScalarPot<NF>::eval(fv, q, dv, tv);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
+            for (int f = 0; f < NF; ++f) {
+              // FP32 adds the small increment last (one rounding at the momentum's
+              // size); FP64 takes two FMAs
+              if constexpr (sizeof(T) == 8)
+                pn[f][v] = fmaT(-A3, dv[f], fmaT(A1, lap[f][v], pic[f][v]));
+              else
+                pn[f][v] = pic[f][v] + (A1 * lap[f][v] - A3 * dv[f]);
+            }
             if (RED == 1) {
 #pragma unroll
               for (int f = 0; f < NF; ++f) spost = fmaT(pn[f][v], pn[f][v], spost);
