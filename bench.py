@@ -44,12 +44,12 @@ PASSES_PER_STEP = 3
 # DRAM bytes (read + write) per DK pass from one ncu capture of the FP32 pass
 # at 256^3 (one cooperative launch of the three VV4 passes of a step, divided
 # by 3), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"f32": {"source_hash": "14eda5d453a47013", "bytes_per_launch": 502850901}}
+NCU_TRAFFIC = {"f32": {"source_hash": "e0b8777e15c09017", "bytes_per_launch": 503365461}}
 # FP64 instructions (DFMA, DADD, DMUL) and operations (FMA = 2) per site per pass
 # of the FP64 plain kernel, from one ncu capture of the instruction counters of
 # the FP64 pass at 256^3
-NCU_FP64_OPS = {"source_hash": "14eda5d453a47013", "instructions_per_site_pass": 37.443,
-                "flops_per_site_pass": 55.811}
+NCU_FP64_OPS = {"source_hash": "e0b8777e15c09017", "instructions_per_site_pass": 34.109,
+                "flops_per_site_pass": 49.144}
 
 
 # Thread instructions per site of the doublet passes without expansion at the

@@ -401,6 +401,34 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
         }
       };
 
+      // FP64 (bound by its arithmetic, not by memory): a site's drifted fields are
+      // formed once and written back into its stage, where the next plane reads
+      // them as y- and x-neighbours; all threads drift the tile's two halo rows in
+      // place; then a proxy fence (bulk copies refill the stage later) and one CTA
+      // barrier per plane.  `drifting` is the same in every thread of the CTA.
+      constexpr bool SHARE = sizeof(T) == 8;
+      const bool share = SHARE && drifting;
+      auto share_own = [&](int s, const T (&ph)[NF][VX]) {  // active threads
+        T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) st_vec<T, VX>(st + (size_t)(2 * f) * arr_elems + own, ph[f]);
+      };
+      auto share_halo = [&](int s) {  // every thread of the CTA
+        if (!flag[0]) {
+          T* st = reinterpret_cast<T*>(smem + (size_t)s * P.stage_bytes_max);
+          for (int k = tid; k < 2 * N; k += THREADS) {
+            const int e = k < N ? k : (BY + 1) * N + (k - N);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              T* ph = st + (size_t)(2 * f) * arr_elems;
+              ph[e] = fmaT(cd, st[(size_t)(2 * f + 1) * arr_elems + e], ph[e]);
+            }
+          }
+          fence_proxy_async_smem();
+        }
+        __syncthreads();
+      };
+
       // drifted fields of three consecutive planes; the roles below / current /
       // above rotate through b0, b1, b2 (the march is unrolled by three, so the
       // rotation costs no register moves)
@@ -411,7 +439,11 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
       release(g0, s_cur);
       advance(s_cur, p_cur);
       wait_full(s_cur, p_cur);
-      if (active && !flag[0]) read_own(stage_ptr(s_cur), b1);
+      if (active && !flag[0]) {
+        read_own(stage_ptr(s_cur), b1);
+        if (share) share_own(s_cur, b1);
+      }
+      if (share) share_halo(s_cur);
       int s_nxt = s_cur;
       uint32_t p_nxt = p_cur;
       advance(s_nxt, p_nxt);
@@ -424,6 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
           const T* sa = stage_ptr(s_nxt);
           const T* sc = stage_ptr(s_cur);
           read_own(sa, above);
+          if (share && j < sg.nz) share_own(s_nxt, above);
           T lap[NF][VX], g2[VX];
 #pragma unroll
           for (int v = 0; v < VX; ++v) g2[v] = T(0);
@@ -434,7 +467,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             T yl[VX], yh[VX];
             ld_vec<T, VX>(yl, ph + ty * N + x0);
             ld_vec<T, VX>(yh, ph + (ty + 2) * N + x0);
-            if (drifting) {
+            if (drifting && !SHARE) {
               T ml[VX], mh[VX];
               ld_vec<T, VX>(ml, pm + ty * N + x0);
               ld_vec<T, VX>(mh, pm + (ty + 2) * N + x0);
@@ -446,8 +479,8 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             }
             // x-neighbours beyond this thread's sites, read from the stage and
             // drifted like the owner's copy (no shuffle, no divergent edge branch)
-            const T left = drifting ? fmaT(cd, pm[exl], ph[exl]) : ph[exl];
-            const T right = drifting ? fmaT(cd, pm[exr], ph[exr]) : ph[exr];
+            const T left = drifting && !SHARE ? fmaT(cd, pm[exl], ph[exl]) : ph[exl];
+            const T right = drifting && !SHARE ? fmaT(cd, pm[exr], ph[exr]) : ph[exr];
             T gf = T(0);
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
@@ -528,6 +561,7 @@ __global__ void __launch_bounds__(THREADS, 1) dk_pass_scalar(const PassArgs P) {
             }
           }
         }
+        if (share && j < sg.nz) share_halo(s_nxt);
         release(g0 + j, s_cur);
         s_cur = s_nxt;
         p_cur = p_nxt;
