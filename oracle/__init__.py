@@ -126,6 +126,9 @@ def lib():
             L.clo_norm_spectrum.argtypes = [c_p, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]
+            L.clo_norm_spectrum_of.argtypes = [c_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]
             L.clo_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
             L.clo_philox4x32_10.restype = None
             L.clo_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
@@ -326,17 +329,17 @@ class Oracle:
         n = nb.value
         return k[:n].copy(), nk[:n].copy(), m[:n].copy()
 
-    def norm_spectrum(self, dk_bin=1.0, fo2=None):
+    def norm_spectrum(self, dk_bin=1.0, fo2=None, which=0):
         """(k, Delta_r, Delta_r', n, multiplicity) of the charged field's modulus r = |phi|
         (gauge models; n is that of the canonical modulus sqrt2 r); fo2 = (f*/omega*)^2,
-        default 1/fluct_amp2."""
+        default 1/fluct_amp2.  which = 1: lphi4SU2U1's U(1)-charged scalar."""
         if fo2 is None:
             fo2 = 1.0 / self.params.fluct_amp2
         cap = 4096
         k, d1, d2, n = (np.zeros(cap) for _ in range(4))
         m = np.zeros(cap, dtype=np.int64)
         nb = ctypes.c_int()
-        rc = self.L.clo_norm_spectrum(self.h, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
+        rc = self.L.clo_norm_spectrum_of(self.h, which, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
                                       m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
         if rc != 0:
             raise ValueError("clo_norm_spectrum failed (%d)" % rc)

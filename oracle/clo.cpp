@@ -1653,25 +1653,52 @@ int clo_occupation(const clo_ctx* c, int field, double dk_bin, double fo2, doubl
 // is written for a canonically normalised field.
 int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
                       double* n, int64_t* mult, int cap, int* nbins) {
-  if (!c || !c->gauge() || c->full() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
+  return clo_norm_spectrum_of(c, 0, dk_bin, fo2, k, df, dfp, n, mult, cap, nbins);
+}
+
+// which = 0: the model's charged field (the U(1) scalar, or the doublet); which = 1:
+// lphi4SU2U1's U(1)-charged scalar vphi.  The mass of eq. OccuppationNum is the
+// volume average of the potential's curvature along the canonical modulus
+// rho = sqrt2 r, d^2V/drho^2 = (1/2) d^2V/dr^2, at the other fields' values:
+//   U(1) scalar, doublet: V = lam (r^2 - v^2)^2 -> lam (6 r^2 - 2 v^2);
+//   lphi4SU2U1 doublet (eq. PotGauge): + q_G r^2 phi_s^2 + 2 q_H r^2 |vphi|^2
+//     -> lam (6 r^2 - 2 v^2) + q_G phi_s^2 + 2 q_H |vphi|^2;
+//   lphi4SU2U1 vphi, r = |vphi|: 2 q_H |Phi|^2 r^2 -> 2 q_H |Phi|^2.
+int clo_norm_spectrum_of(const clo_ctx* c, int which, double dk_bin, double fo2, double* k, double* df,
+                         double* dfp, double* n, int64_t* mult, int cap, int* nbins) {
+  if (!c || !c->gauge() || !(dk_bin > 0.0) || !(fo2 > 0.0)) return -1;
+  if (which != 0 && !(which == 1 && c->full())) return -1;
   const int nb = (int)std::floor(std::sqrt(3.0) * (c->N / 2) / dk_bin) + 1;
   if (nbins) *nbins = nb;
   if (nb > cap) return -2;
   const double V = (double)c->V, a = c->a, H = c->b / c->a, al = c->alpha;
   const double apm = std::pow(a, al - 3.0);
+  const int nc = which == 1 ? 2 : c->nf;
+  const std::vector<double>* fq = which == 1 ? c->cph : c->phi;
+  const std::vector<double>* pq = which == 1 ? c->cpi : c->pi;
   std::vector<cplx> R(c->V), Rp(c->V), G(c->V);
   double m2 = 0.0;
   for (long s = 0; s < c->V; ++s) {
     double r2 = 0.0, rr = 0.0;
-    for (int q = 0; q < c->nf; ++q) {
-      r2 += 0.5 * c->phi[q][s] * c->phi[q][s];
-      rr += 0.5 * c->phi[q][s] * apm * c->pi[q][s];
+    for (int q = 0; q < nc; ++q) {
+      r2 += 0.5 * fq[q][s] * fq[q][s];
+      rr += 0.5 * fq[q][s] * apm * pq[q][s];
     }
     const double r = std::sqrt(r2), rp = r > 0.0 ? rr / r : 0.0;
     R[s] = cplx(r, 0.0);
     Rp[s] = cplx(rp, 0.0);
     G[s] = cplx(rp + H * r, 0.0);
-    m2 += c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v);
+    if (which == 1) {
+      double d2 = 0.0;  // |Phi|^2
+      for (int q = 0; q < 4; ++q) d2 += 0.5 * c->phi[q][s] * c->phi[q][s];
+      m2 += 2.0 * c->p.qH * d2;
+    } else {
+      m2 += c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v);
+      if (c->full()) {
+        const double v2 = 0.5 * (c->cph[0][s] * c->cph[0][s] + c->cph[1][s] * c->cph[1][s]);
+        m2 += c->p.qG * c->sph[s] * c->sph[s] + 2.0 * c->p.qH * v2;
+      }
+    }
   }
   m2 /= V;
   fft3d(R, c->N, -1);

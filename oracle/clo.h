@@ -130,6 +130,11 @@ void clo_su2_exp(const double theta[3], double u[4]);
  * fo2 = (f_s/omega_s)^2.  -1 for scalar models, -2 if cap < nbins. */
 int clo_norm_spectrum(const clo_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp,
                       double* n, int64_t* mult, int cap, int* nbins);
+/* which = 0: the model's charged field (as clo_norm_spectrum; the doublet of
+ * lphi4SU2U1 with the mass q_G phi_s^2 + 2 q_H |vphi|^2 added); which = 1: the
+ * U(1)-charged scalar vphi of lphi4SU2U1 (mass 2 q_H |Phi|^2).  -1 otherwise. */
+int clo_norm_spectrum_of(const clo_ctx* c, int which, double dk_bin, double fo2, double* k, double* df,
+                         double* dfp, double* n, int64_t* mult, int cap, int* nbins);
 int clo_ic_sample(int model, int N, double kIR, double alpha, uint64_t seed, const clo_params* p,
                   int n, const int64_t* idx, double* out);
 
