@@ -209,9 +209,19 @@ cl_status cl_set_state(cl_ctx* ctx, int field, int what, const double* host_in);
  * spectrum outputs of the charged scalars, Sec. 4.5, with its `norm`: the
  * modulus, which is gauge invariant).  fo2 = (f_s/omega_s)^2; fo2 <= 0 takes 1/fluct_amp2.  k, df, dfp,
  * n, mult hold `cap` entries; *nbins receives the bin count.  CL_EUNSUPPORTED for
- * scalar models and ensembles.  Closes the stream of kicks; synchronises. */
+ * scalar models and ensembles.  Closes the stream of kicks; synchronises.  For
+ * CL_MODEL_LPHI4_SU2U1 it is the doublet's (see cl_norm_spectrum_of). */
 cl_status cl_norm_spectrum(cl_ctx* ctx, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,
                            int64_t* mult, int cap, int* nbins);
+/* As cl_norm_spectrum for the charged field `which` (Sec. 4.5 outputs
+ * spectra_norm_SU2Doublet_scalar and spectra_norm_cmplx_scalar): which = 0 the
+ * model's charged field (cl_norm_spectrum); which = 1 the U(1)-charged scalar
+ * vphi of CL_MODEL_LPHI4_SU2U1.  The mass of n is the potential's curvature
+ * along the field's canonical modulus, averaged over the lattice (eq. PotGauge):
+ * for lphi4SU2U1's doublet lam (6 <r^2> - 2 v^2) + q_G <phi_s^2> + 2 q_H <|vphi|^2>,
+ * for its vphi 2 q_H <|Phi|^2>.  CL_EINVAL for which = 1 in other models. */
+cl_status cl_norm_spectrum_of(cl_ctx* ctx, int which, double dk_bin, double fo2, double* k, double* df,
+                              double* dfp, double* n, int64_t* mult, int cap, int* nbins);
 
 /* Doublet model: whole arrays by index, in the order
  *   0..3 phi_c, 4..7 pi_c, 8..10 A_i, 11..13 pi_A,i,

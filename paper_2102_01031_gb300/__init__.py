@@ -37,7 +37,7 @@ EXPORTS = (
     "cl_adjoint", "cl_ic_amplitude_grad", "cl_occupation", "cl_measure_fp64_rate", "cl_em_spectrum",
     "cl_get_array", "cl_set_array", "cl_norm_spectrum", "cl_checkpoint_save", "cl_checkpoint_load",
     "cl_set_tune_cache", "cl_selftest_wait", "cl_pass_weights", "cl_philox_draws",
-    "cl_adjoint_pass_timing", "cl_bind_buffers", "cl_state_buffer",
+    "cl_adjoint_pass_timing", "cl_bind_buffers", "cl_state_buffer", "cl_norm_spectrum_of",
 )
 OBJ_CHI_FRACTION, OBJ_SPECTRUM_BIN = 0, 1
 
@@ -134,6 +134,8 @@ def lib():
     L.cl_set_tune_cache.argtypes = [ctypes.c_char_p]
     L.cl_checkpoint_load.argtypes = [vp, ctypes.c_char_p]
     L.cl_norm_spectrum.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
+                                   ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
+    L.cl_norm_spectrum_of.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp,
                                    ctypes.POINTER(ctypes.c_int64), ip, ctypes.POINTER(ctypes.c_int)]
     L.cl_set_array.argtypes = [vp, ip, dp]
     L.cl_get_scalars.argtypes = [vp, dp, dp, dp]
@@ -416,17 +418,17 @@ class Lattice:
         n = nb.value
         return k[:n].copy(), d[:n].copy(), m[:n].copy()
 
-    def norm_spectrum(self, dk_bin=1.0, fo2=0.0):
-        """cl_norm_spectrum (gauge models): (k, Delta_r, Delta_r', n, multiplicity) of the
-        charged field's modulus r = |phi| (n: that of the canonical modulus sqrt2 r);
-        fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2)."""
+    def norm_spectrum(self, dk_bin=1.0, fo2=0.0, which=0):
+        """cl_norm_spectrum_of (gauge models): (k, Delta_r, Delta_r', n, multiplicity) of
+        the charged field's modulus r = |phi| (n: that of the canonical modulus sqrt2 r);
+        fo2 = (f*/omega*)^2 (<= 0: 1/fluct_amp2); which = 1: lphi4SU2U1's vphi."""
         cap = 4096
         k, d1, d2, n = (np.zeros(cap) for _ in range(4))
         m = np.zeros(cap, dtype=np.int64)
         nb = ctypes.c_int()
-        rc = self.L.cl_norm_spectrum(self.h, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
-                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
-        _check(self.L, self.h, rc, "cl_norm_spectrum")
+        rc = self.L.cl_norm_spectrum_of(self.h, which, dk_bin, fo2, _dp(k), _dp(d1), _dp(d2), _dp(n),
+                                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap, ctypes.byref(nb))
+        _check(self.L, self.h, rc, "cl_norm_spectrum_of")
         b = nb.value
         return k[:b].copy(), d1[:b].copy(), d2[:b].copy(), n[:b].copy(), m[:b].copy()
 

@@ -72,6 +72,8 @@ cudaError_t launch_su2_plaquette_field(int fp32, const void* Uj, const void* Ul,
 cudaError_t launch_norm_field(int fp32, const void* const* f, const void* const* p, int nc, double apm, double H,
                               int mode, double2* out, long long V, cudaStream_t st);
 cudaError_t launch_convert(int, int, const void*, void*, long long, cudaStream_t);
+cudaError_t launch_sum_sq(int fp32, const void* f0, const void* f1, const void* f2, double w0, double w1,
+                          double w2, long long V, int nblk, double* part, cudaStream_t st);
 cudaError_t launch_u1_gauss_init(const LatConst*, int, double2*, double2*, int, int, double, int,
                                  void*, long long, int, cudaStream_t);
 cudaError_t launch_u1_gauss_monitor(const LatConst*, int, double*, int, long long, cudaStream_t);
@@ -1596,10 +1598,18 @@ cl_status cl_occupation(cl_ctx* c, int field, double dk_bin, double fo2, double*
 
 cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, double* df, double* dfp, double* n,
                            int64_t* mult, int cap, int* nbins) {
+  return cl_norm_spectrum_of(c, 0, dk_bin, fo2, k, df, dfp, n, mult, cap, nbins);
+}
+
+cl_status cl_norm_spectrum_of(cl_ctx* c, int which, double dk_bin, double fo2, double* k, double* df, double* dfp,
+                              double* n, int64_t* mult, int cap, int* nbins) {
   Range range_("cl_norm_spectrum");
   if (!c || !k || !df || !dfp || !n || !mult || !nbins) return fail(c, CL_EINVAL, "NULL argument");
-  if (c->nlat != 1 || (c->model != CL_MODEL_U1_HIGGS && c->model != CL_MODEL_SU2U1_HIGGS))
+  if (c->nlat != 1 || (c->model != CL_MODEL_U1_HIGGS && !is_doublet(c->model)))
     return fail(c, CL_EUNSUPPORTED, "modulus spectra cover single lattices of the gauge models");
+  const bool full = c->model == CL_MODEL_LPHI4_SU2U1;
+  if (which != 0 && !(which == 1 && full))
+    return fail(c, CL_EINVAL, "which must be 0 (the charged field)%s", full ? " or 1 (vphi)" : "");
   if (!(dk_bin > 0.0)) return fail(c, CL_EINVAL, "dk_bin must be positive");
   if (!(fo2 > 0.0)) {
     if (!(c->p.fluct_amp2 > 0.0)) return fail(c, CL_EINVAL, "need (f*/omega*)^2 > 0 (fluct_amp2 is 0)");
@@ -1629,12 +1639,28 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
   CU(cudaStreamSynchronize(c->stream));
   const double a = S.a, Hc = S.b / S.a, al = c->alpha;
   const bool u1 = c->model == CL_MODEL_U1_HIGGS;
-  const int nc = u1 ? 2 : 4;
+  const int nc = u1 || which == 1 ? 2 : 4;
   const void* f[4];
   const void* p[4];
   for (int q = 0; q < nc; ++q) {
-    f[q] = arr_ptr(c, 0, c->parity, u1 ? 2 * q : q);
-    p[q] = arr_ptr(c, 0, c->parity, u1 ? 2 * q + 1 : 4 + q);
+    // the U(1) model: phi_q, pi_q at 2q, 2q + 1; the doublet: 0..3, momenta 4..7;
+    // lphi4SU2U1's vphi: 37, 38, momenta 39, 40
+    f[q] = arr_ptr(c, 0, c->parity, which == 1 ? 37 + q : (u1 ? 2 * q : q));
+    p[q] = arr_ptr(c, 0, c->parity, which == 1 ? 39 + q : (u1 ? 2 * q + 1 : 4 + q));
+  }
+  // lphi4SU2U1's doublet: the couplings' part of its mass, <q_G phi_s^2 + 2 q_H |vphi|^2>
+  // (phi_s at 35), which the measurement does not keep
+  double mfull = 0.0;
+  if (full && which == 0) {
+    const int nsum = 2 * c->nsm;
+    CU(launch_sum_sq(c->fp32, arr_ptr(c, 0, c->parity, 35), arr_ptr(c, 0, c->parity, 37),
+                     arr_ptr(c, 0, c->parity, 38), c->p.qG, c->p.qH, c->p.qH, H.V, nsum, part, c->stream));
+    ++c->launches;
+    std::vector<double> ps(nsum);
+    CU(cudaMemcpyAsync(ps.data(), part, nsum * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nsum; ++b) mfull += ps[b];
+    mfull /= (double)H.V;
   }
   // rows: 0 Delta_r, 1 shell sums |r_k|^2, 2 Delta_r', 3 shell sums |r'_k + (a'/a) r_k|^2
   for (int mode = 0; mode < 3; ++mode) {
@@ -1656,10 +1682,12 @@ cl_status cl_norm_spectrum(cl_ctx* c, double dk_bin, double fo2, double* k, doub
   CU(cudaMemcpyAsync(h.data(), bins, 12 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   // n is that of the canonical modulus rho = sqrt2 r (|rho_k|^2 = 2 |r_k|^2), whose
-  // mass is <d^2V/drho^2> = <V''(r)>/2 = lam (6 <r^2> - 2 v^2), <r^2> = sum_c <phi_c^2>/2
+  // mass is <d^2V/drho^2> = <V''(r)>/2: lam (6 <r^2> - 2 v^2), <r^2> = sum_c <phi_c^2>/2,
+  // for the U(1) field and the doublet, plus <q_G phi_s^2 + 2 q_H |vphi|^2> for
+  // lphi4SU2U1's doublet; 2 q_H <|Phi|^2> for its vphi (eq. PotGauge)
   double r2 = 0.0;
-  for (int q = 0; q < nc; ++q) r2 += 0.5 * S.obs.mean_phi2[q];
-  const double m2 = c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v);
+  for (int q = 0; q < (which == 1 ? 4 : nc); ++q) r2 += 0.5 * S.obs.mean_phi2[q];
+  const double m2 = which == 1 ? 2.0 * c->p.qH * r2 : c->p.lam * (6.0 * r2 - 2.0 * c->p.v * c->p.v) + mfull;
   const double V = (double)H.V, L = H.N * H.dx;
   const double C = a * a * L * L * L / (2.0 * V * V) * fo2, a2p = std::pow(a, 2.0 * (1.0 - al));
   for (int b = 0; b < nb; ++b) {

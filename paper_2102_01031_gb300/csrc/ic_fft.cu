@@ -998,6 +998,43 @@ cudaError_t launch_norm_field(int fp32, const void* const* f, const void* const*
   return cudaGetLastError();
 }
 
+// Per-block partial sums of w0 f0^2 + w1 f1^2 + w2 f2^2 over the lattice (volume
+// averages a spectrum needs that the measurement does not keep).  A fixed grid and
+// a fixed order of every sum, so the result does not depend on timing; the host
+// adds the blocks' partials in order.
+template <typename T>
+__global__ void sum_sq_kernel(const T* f0, const T* f1, const T* f2, double w0, double w1, double w2, long long V,
+                              double* part) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < V;
+       n += (long long)gridDim.x * blockDim.x) {
+    const double a = (double)f0[n], b = (double)f1[n], c = (double)f2[n];
+    s += w0 * a * a + w1 * b * b + w2 * c * c;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_sum_sq(int fp32, const void* f0, const void* f1, const void* f2, double w0, double w1,
+                          double w2, long long V, int nblk, double* part, cudaStream_t st) {
+  const int tb = 256;
+  if (fp32)
+    sum_sq_kernel<float><<<nblk, tb, 0, st>>>(reinterpret_cast<const float*>(f0), reinterpret_cast<const float*>(f1),
+                                              reinterpret_cast<const float*>(f2), w0, w1, w2, V, part);
+  else
+    sum_sq_kernel<double><<<nblk, tb, 0, st>>>(reinterpret_cast<const double*>(f0),
+                                               reinterpret_cast<const double*>(f1),
+                                               reinterpret_cast<const double*>(f2), w0, w1, w2, V, part);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(int fp32, int to_double, const void* in, void* out, long long V, cudaStream_t st) {
   const int tb = 256;
   if (to_double) {

@@ -131,6 +131,25 @@ def test_singlet_and_charged_spectra(P):
             assert_bins(dg, do, 1e-10, (field, w))
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_modulus_spectra_of_both_charged_fields(P, precision, tol):
+    """cl_norm_spectrum_of against the oracle, bin by bin: Delta of the doublet's
+    modulus |Phi| and of vphi's |vphi|, of their rates, and their occupation
+    numbers (the doublet's mass with its couplings to phi_s and vphi, vphi's from
+    the doublet), with self-consistent expansion (a != 1)."""
+    g, o = both(P, 32, 0.8, 2, precision=precision, integrator=O.VV2, expansion=O.EXP_SELF)
+    g.step(10)
+    o.step(10)
+    for which in (0, 1):
+        rg, ro = g.norm_spectrum(which=which), o.norm_spectrum(which=which)
+        assert np.array_equal(rg[4], ro[4])
+        assert np.abs(rg[0] - ro[0]).max() < 1e-12
+        for i, (x, y) in enumerate(zip(rg[1:4], ro[1:4])):
+            assert_bins(x, y, tol, (which, i))
+    # the two fields' occupation numbers differ (different masses and spectra)
+    assert np.abs(g.norm_spectrum(which=0)[3] - g.norm_spectrum(which=1)[3]).max() > 0
+
+
 def test_time_reversal(P):
     g = P.Lattice(O.MODEL_LPHI4_SU2U1, 16, 0.8, 1.0, 4,
                   P.make_params(**dict(FULL, integrator=O.VV4, expansion=O.EXP_SELF, fstar_over_mp=2.0)))
@@ -152,8 +171,8 @@ def test_state_access_and_errors(P):
         g.get_array(41)
     assert e.value.status == P.CL_EINVAL
     with pytest.raises(P.ClError) as e:
-        g.norm_spectrum()
-    assert e.value.status == P.CL_EUNSUPPORTED
+        g.norm_spectrum(which=2)
+    assert e.value.status == P.CL_EINVAL
     with pytest.raises(P.ClError) as e:
         P.Lattice(O.MODEL_LPHI4_SU2U1, 24, 0.8, 1.0, 1, P.make_params(**FULL))   # N % 16
     assert e.value.status == P.CL_EUNSUPPORTED
