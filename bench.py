@@ -64,7 +64,7 @@ NCU_FULL = {"source_hash": "13bb525708db73c0", "thread_instructions_per_site": 1
             "dram_bytes_per_site": 318.0}
 # The same for the U(1) pass without expansion at the benchmark size
 # (dk_pass_u1<float,0,true,256>, one leapfrog pass of 256^3).
-NCU_U1 = {"source_hash": "7aabe44e7989e483", "thread_instructions_per_site": 255.8,
+NCU_U1 = {"source_hash": "68ec87c02aca2e4a", "thread_instructions_per_site": 255.8,
           "dram_bytes_per_site": 80.4}
 # instruction issue of the whole GPU: 152 SMs x 4 schedulers x 32 lanes at the 2070 MHz maximum SM clock
 ISSUE_PEAK_LANE_INSTR_PER_S = 152 * 4 * 32 * 2.070e9

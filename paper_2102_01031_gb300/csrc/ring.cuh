@@ -7,7 +7,8 @@
 // A CTA's segments form one sequence of planes (each segment adds a halo
 // plane at both ends); plane g of pass p lives in stage (p * ptot + g) mod S.
 // A stage holds, for every array, the plane's BY rows of the segment's y-tile
-// plus one halo row on each side, each row complete in x.
+// plus one halo row on each side, each row complete in x (with MOWN the momenta,
+// read at the tile's own sites only, without the halo rows).
 #pragma once
 
 #include "common.cuh"
