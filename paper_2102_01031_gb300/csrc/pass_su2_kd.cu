@@ -85,6 +85,58 @@ __device__ __forceinline__ V3<T> neg(const V3<T>& v) {
   return r;
 }
 
+// Two independent quaternion products at once (FP32, the packed two-lane form):
+// lane 0 and lane 1 of every component are the two products, each lane rounded
+// exactly as qmul / qvec round one product (a conjugated operand enters by exact
+// sign changes, (-a)(-b) = ab), so the pass's results are the same bits.
+struct Q2 {
+  float2 w, x, y, z;
+};
+struct P3 {
+  float2 x, y, z;
+};
+__device__ __forceinline__ Q2 q2(const Q4<float>& a, const Q4<float>& b) {
+  return Q2{make_float2(a.w, b.w), make_float2(a.x, b.x), make_float2(a.y, b.y), make_float2(a.z, b.z)};
+}
+__device__ __forceinline__ float2 ng(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ Q4<float> lane_of(const Q2& a, int l) {
+  return l ? Q4<float>{a.w.y, a.x.y, a.y.y, a.z.y} : Q4<float>{a.w.x, a.x.x, a.y.x, a.z.x};
+}
+__device__ __forceinline__ V3<float> lane_of(const P3& a, int l) {
+  return l ? V3<float>{a.x.y, a.y.y, a.z.y} : V3<float>{a.x.x, a.y.x, a.z.x};
+}
+// a b (qmul)
+__device__ __forceinline__ Q2 qmul2(const Q2& a, const Q2& b) {
+  Q2 r;
+  r.w = __ffma2_rn(ng(a.z), b.z, __ffma2_rn(ng(a.y), b.y, __ffma2_rn(ng(a.x), b.x, __fmul2_rn(a.w, b.w))));
+  r.x = __ffma2_rn(a.y, b.z, __ffma2_rn(ng(a.z), b.y, __ffma2_rn(b.w, a.x, __fmul2_rn(a.w, b.x))));
+  r.y = __ffma2_rn(a.z, b.x, __ffma2_rn(ng(a.x), b.z, __ffma2_rn(b.w, a.y, __fmul2_rn(a.w, b.y))));
+  r.z = __ffma2_rn(a.x, b.y, __ffma2_rn(ng(a.y), b.x, __ffma2_rn(b.w, a.z, __fmul2_rn(a.w, b.z))));
+  return r;
+}
+// a b^dag (qmul(a, qconj(b)))
+__device__ __forceinline__ Q2 qmul2_cb(const Q2& a, const Q2& b) {
+  Q2 r;
+  r.w = __ffma2_rn(a.z, b.z, __ffma2_rn(a.y, b.y, __ffma2_rn(a.x, b.x, __fmul2_rn(a.w, b.w))));
+  r.x = __ffma2_rn(ng(a.y), b.z, __ffma2_rn(a.z, b.y, __ffma2_rn(b.w, a.x, __fmul2_rn(ng(a.w), b.x))));
+  r.y = __ffma2_rn(ng(a.z), b.x, __ffma2_rn(a.x, b.z, __ffma2_rn(b.w, a.y, __fmul2_rn(ng(a.w), b.y))));
+  r.z = __ffma2_rn(ng(a.x), b.y, __ffma2_rn(a.y, b.x, __ffma2_rn(b.w, a.z, __fmul2_rn(ng(a.w), b.z))));
+  return r;
+}
+// vector part of a b (qvec)
+__device__ __forceinline__ P3 qvec2(const Q2& a, const Q2& b) {
+  P3 r;
+  r.x = __ffma2_rn(a.y, b.z, __ffma2_rn(ng(a.z), b.y, __ffma2_rn(b.w, a.x, __fmul2_rn(a.w, b.x))));
+  r.y = __ffma2_rn(a.z, b.x, __ffma2_rn(ng(a.x), b.z, __ffma2_rn(b.w, a.y, __fmul2_rn(a.w, b.y))));
+  r.z = __ffma2_rn(a.x, b.y, __ffma2_rn(ng(a.y), b.x, __ffma2_rn(b.w, a.z, __fmul2_rn(a.w, b.z))));
+  return r;
+}
+// vector part of a b^dag (qvec(a, qconj(b)))
+__device__ __forceinline__ P3 qvec2_cb(const Q2& a, const Q2& b) {
+  const Q2 r = qmul2_cb(a, b);
+  return P3{r.x, r.y, r.z};
+}
+
 // Asynchronous copies global -> shared by each thread (cp.async): 16 bytes (both
 // addresses 16-byte aligned), or one element; completion either counted on an
 // mbarrier (arrive once all of the thread's earlier copies landed) or awaited
@@ -437,23 +489,48 @@ __global__ void __launch_bounds__(TX * TY, (RED == 2 || sizeof(T) == 8) ? 1 : 20
       V3<T> M[3];
       T s_mB = T(0);
       {
-        const Q4<T> Axy = qmul(Ux, ld4(C, KU + 4, 1, 0)), Bxy = qconj(qmul(Uy, ld4(C, KU, 0, 1)));
-        const Q4<T> Axz = qmul(Ux, ld4(C, KU + 8, 1, 0)), Bxz = qconj(qmul(Uz, ld4(Pn, KU, 0, 0)));
-        const Q4<T> Ayz = qmul(Uy, ld4(C, KU + 8, 0, 1)), Byz = qconj(qmul(Uz, ld4(Pn, KU + 4, 0, 0)));
-        const V3<T> pxy = qvec(Axy, Bxy), pxz = qvec(Axz, Bxz), pyz = qvec(Ayz, Byz);
-        if constexpr (RED > 0) {
-          s_mB = (pxy.x * pxy.x + pxy.y * pxy.y + pxy.z * pxy.z) / (T(1) + qsca(Axy, Bxy)) +
-                 (pxz.x * pxz.x + pxz.y * pxz.y + pxz.z * pxz.z) / (T(1) + qsca(Axz, Bxz)) +
-                 (pyz.x * pyz.x + pyz.y * pyz.y + pyz.z * pyz.z) / (T(1) + qsca(Ayz, Byz));
+        V3<T> pxy, pxz, pyz, ryx, rzx, mxy, mzy;
+        if constexpr (sizeof(T) == 4 && RED == 0) {
+          // the step passes (FP32): products paired lane-wise, the same bits as below
+          const Q2 UyUz = q2(Uy, Uz);
+          const Q2 A = qmul2(q2(Ux, Ux), q2(ld4(C, KU + 4, 1, 0), ld4(C, KU + 8, 1, 0)));  // Axy, Axz
+          const Q2 B = qmul2(UyUz, q2(ld4(C, KU, 0, 1), ld4(Pn, KU, 0, 0)));             // Bxy, Bxz (unconjugated)
+          const Q2 Cp = qmul2(UyUz, q2(ld4(C, KU + 8, 0, 1), ld4(Pn, KU + 4, 0, 0)));    // Ayz, Byz (unconjugated)
+          const P3 pp = qvec2_cb(A, B);
+          pxy = lane_of(pp, 0);
+          pxz = lane_of(pp, 1);
+          pyz = qvec(lane_of(Cp, 0), qconj(lane_of(Cp, 1)));
+          // lower staples in the x planes (of U_y, U_z) and in the y planes (of U_x, U_z)
+          const Q4<T> uxm = ld4(C, KU, -1, 0), uym = ld4(C, KU + 4, 0, -1);
+          const Q2 ix = qmul2(q2(ld4(C, KU + 4, -1, 0), ld4(C, KU + 8, -1, 0)), q2(ld4(C, KU, -1, 1), ld4(Pn, KU, -1, 0)));
+          const P3 rr = qvec2(qmul2_cb(UyUz, ix), q2(uxm, uxm));
+          const Q2 iy = qmul2(q2(ld4(C, KU, 0, -1), ld4(C, KU + 8, 0, -1)), q2(ld4(C, KU + 4, 1, -1), ld4(Pn, KU + 4, 0, -1)));
+          const P3 mm = qvec2(qmul2_cb(q2(Ux, Uz), iy), q2(uym, uym));
+          ryx = lane_of(rr, 0);
+          rzx = lane_of(rr, 1);
+          mxy = lane_of(mm, 0);
+          mzy = lane_of(mm, 1);
+        } else {
+          const Q4<T> Axy = qmul(Ux, ld4(C, KU + 4, 1, 0)), Bxy = qconj(qmul(Uy, ld4(C, KU, 0, 1)));
+          const Q4<T> Axz = qmul(Ux, ld4(C, KU + 8, 1, 0)), Bxz = qconj(qmul(Uz, ld4(Pn, KU, 0, 0)));
+          const Q4<T> Ayz = qmul(Uy, ld4(C, KU + 8, 0, 1)), Byz = qconj(qmul(Uz, ld4(Pn, KU + 4, 0, 0)));
+          pxy = qvec(Axy, Bxy);
+          pxz = qvec(Axz, Bxz);
+          pyz = qvec(Ayz, Byz);
+          if constexpr (RED > 0) {
+            s_mB = (pxy.x * pxy.x + pxy.y * pxy.y + pxy.z * pxy.z) / (T(1) + qsca(Axy, Bxy)) +
+                   (pxz.x * pxz.x + pxz.y * pxz.y + pxz.z * pxz.z) / (T(1) + qsca(Axz, Bxz)) +
+                   (pyz.x * pyz.x + pyz.y * pyz.y + pyz.z * pyz.z) / (T(1) + qsca(Ayz, Byz));
+          }
+          // lower staples of U_y(n), U_z(n) in the x planes, directly
+          const Q4<T> uxm = ld4(C, KU, -1, 0);
+          ryx = qvec(qmul(Uy, qconj(qmul(ld4(C, KU + 4, -1, 0), ld4(C, KU, -1, 1)))), uxm);
+          rzx = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, -1, 0), ld4(Pn, KU, -1, 0)))), uxm);
+          // lower staples of U_x(n), U_z(n) in the y planes, directly
+          const Q4<T> uym = ld4(C, KU + 4, 0, -1);
+          mxy = qvec(qmul(Ux, qconj(qmul(ld4(C, KU, 0, -1), ld4(C, KU + 4, 1, -1)))), uym);
+          mzy = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, 0, -1), ld4(Pn, KU + 4, 0, -1)))), uym);
         }
-        // lower staples of U_y(n), U_z(n) in the x planes, directly
-        const Q4<T> uxm = ld4(C, KU, -1, 0);
-        const V3<T> ryx = qvec(qmul(Uy, qconj(qmul(ld4(C, KU + 4, -1, 0), ld4(C, KU, -1, 1)))), uxm);
-        const V3<T> rzx = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, -1, 0), ld4(Pn, KU, -1, 0)))), uxm);
-        // lower staples of U_x(n), U_z(n) in the y planes, directly
-        const Q4<T> uym = ld4(C, KU + 4, 0, -1);
-        const V3<T> mxy = qvec(qmul(Ux, qconj(qmul(ld4(C, KU, 0, -1), ld4(C, KU + 4, 1, -1)))), uym);
-        const V3<T> mzy = qvec(qmul(Uz, qconj(qmul(ld4(C, KU + 8, 0, -1), ld4(Pn, KU + 4, 0, -1)))), uym);
         M[0].x = (pxy.x + pxz.x) + (mxy.x + c_xz.x);
         M[0].y = (pxy.y + pxz.y) + (mxy.y + c_xz.y);
         M[0].z = (pxy.z + pxz.z) + (mxy.z + c_xz.z);
