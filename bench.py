@@ -58,9 +58,9 @@ NCU_FP64_OPS = {"source_hash": "e0b8777e15c09017", "instructions_per_site_pass":
 # leapfrog pass of 256^3 each) and their DRAM bytes per site (the same kernels
 # built for any N, one pass of 128^3), from ncu captures, valid for the kernel
 # source they were taken on.
-NCU_SU2 = {"source_hash": "28330cea22dacacc", "thread_instructions_per_site": 1400.0,
+NCU_SU2 = {"source_hash": "85bf812048b7f8dc", "thread_instructions_per_site": 1400.0,
            "dram_bytes_per_site": 268.8}
-NCU_FULL = {"source_hash": "28330cea22dacacc", "thread_instructions_per_site": 1616.3,
+NCU_FULL = {"source_hash": "85bf812048b7f8dc", "thread_instructions_per_site": 1616.3,
             "dram_bytes_per_site": 318.0}
 # The same for the U(1) pass without expansion at the benchmark size
 # (dk_pass_u1<float,0,true,256>, one leapfrog pass of 256^3).

@@ -36,7 +36,10 @@
 // them on between lanes would leave the tile's edge column to one lane of a
 // warp, which costs the whole warp the work).  The same goes for the compact
 // U(1) plaquette sines and the backward hops W_i^dag(n-i) psi(n-i): carried
-// along z, direct across x and y.
+// along z, direct across x and y.  In the FP32 step passes the seven U(1)
+// plaquette sines are evaluated two at a time and the six plaquette products and
+// four lower staples are formed two at a time, in the packed two-lane FP32 form,
+// each lane rounded as the single evaluation (trig2.cuh, Q2 below).
 #include "su2_common.cuh"
 #include "kd_drift.cuh"
 #include "trig2.cuh"
